@@ -1,0 +1,609 @@
+"""FP64 oracle: truncated decompositions and the first-order approximate product.
+
+TEST INFRASTRUCTURE ONLY.  Imported by tests/, __graft_entry__.smoke() and the CPU
+baseline of bench.py; never by the product package.
+
+Paper: Kar, Hariprasad, Sai Gowri, Venkatapathi, "Efficient approximations of matrix
+multiplication using truncated decompositions" (arXiv 2504.19308).  Section numbers,
+equations and algorithm numbers below are the paper's.
+
+Readings taken where the paper is silent or inconsistent (each also listed in the design doc):
+  R1  omega = e^{+2 pi i/n} as in Thm 2.1 (Lemma 3.10 uses the opposite sign).
+  R2  The shift identity is W D^k W^* = C^k (Remark after Thm 2.1); the form printed in
+      Section 2.3.2 with W^* and W swapped is taken as a typo.
+  R3  Cycle form A = sum_j C^j Lambda_j (Eq. "rightdecomp", Alg. 7), not Lambda_j C^j.
+  R4  FFT unnormalised forward, IFFT with 1/n; R = F A_cyc / n, L = F R (Alg. 2, Alg. 3).
+  R5  For real A the components t and n-t are complex conjugates and tie exactly; top-k may
+      split a pair, making M complex.  The product returned is Re(M); ||Im M|| is reported.
+  R6  Top-k order is (key descending, index ascending).  Keys of conjugate partners are
+      computed once (index <= n/2) and mirrored so the tie is exact.
+  R7  rSVD: phi ~ N(0,1) supplied by the caller, no oversampling, no power iteration
+      (Alg. 1 as printed).  Only A~ = Q Q^T A enters M, so QR/SVD signs do not matter.
+  R8  Fourier sparsifier: top-k per ROW of A W^* and per COLUMN of W B (Section 2.4 text),
+      constant k; magnitudes of conjugate partners mirrored as in R6.
+  R9  Cycle sparsifier key: ||diag Lambda_j||_2 (by analogy with Alg. 3 Step 2).
+  R10 Backward: selections, Q factors and masks are frozen; the gradient is that of the
+      resulting bilinear map.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Basic objects (Section 1.2.2, Thm 2.1)
+# ---------------------------------------------------------------------------
+
+
+def omega(n: int) -> complex:
+    """omega = e^{+2 pi i / n} (Thm 2.1, reading R1)."""
+    return np.exp(2j * np.pi / n)
+
+
+def cycle_perm(n: int) -> np.ndarray:
+    """C = [[0, 1], [I_{n-1}, 0]] (Eq. (1.1)): C[i, (i-1) mod n] = 1."""
+    c = np.zeros((n, n))
+    for i in range(n):
+        c[i, (i - 1) % n] = 1.0
+    return c
+
+
+def diag_D(n: int, k: int = 1) -> np.ndarray:
+    """D^k with D(q, q) = omega^q (Thm 2.1)."""
+    q = np.arange(n)
+    return np.diag(np.exp(2j * np.pi * ((k * q) % n) / n))
+
+
+def dft_matrix(n: int) -> np.ndarray:
+    """Unnormalised forward DFT F(p, q) = e^{-2 pi i pq / n} = sqrt(n) W (Section 2.3.1).
+
+    The exponent is reduced mod n before the exponential so entries are exact to rounding.
+    """
+    p = np.arange(n)
+    return np.exp(-2j * np.pi * ((p[:, None] * p[None, :]) % n) / n)
+
+
+def unitary_W(n: int) -> np.ndarray:
+    """W(p, q) = n^{-1/2} e^{-2 pi i pq/n} (Remark after Thm 2.1)."""
+    return dft_matrix(n) / math.sqrt(n)
+
+
+def fft_cols(x: np.ndarray) -> np.ndarray:
+    """F x along axis 0.  Explicit DFT matrix for small n, library FFT otherwise."""
+    n = x.shape[0]
+    if n <= 64:
+        return dft_matrix(n) @ x
+    return np.fft.fft(x, axis=0)
+
+
+def ifft_cols(x: np.ndarray) -> np.ndarray:
+    """F^{-1} x along axis 0 (1/n scaling, MATLAB convention)."""
+    n = x.shape[0]
+    if n <= 64:
+        return np.conj(dft_matrix(n)) @ x / n
+    return np.fft.ifft(x, axis=0)
+
+
+def circulant(col: np.ndarray) -> np.ndarray:
+    """Circulant matrix sum_j col[j] C^j: X[r, q] = col[(r - q) mod n] (first column = col)."""
+    n = len(col)
+    r = np.arange(n)[:, None]
+    q = np.arange(n)[None, :]
+    return np.asarray(col)[(r - q) % n]
+
+
+# ---------------------------------------------------------------------------
+# Cycle decomposition (Section 1.2.2; Appendix, Alg. 7 and the 4x4 example)
+# ---------------------------------------------------------------------------
+
+
+def cycle_layout(a: np.ndarray) -> np.ndarray:
+    """A_cyc[l, j] = A((l + j) mod n, l): column j holds the cycle Lambda_j of A = sum_j C^j Lambda_j.
+
+    Appendix Alg. 7: A_cyc[i, j] = A^T[i, (i + j) mod n].  Written as the plain loop.
+    """
+    n = a.shape[0]
+    assert a.shape == (n, n)
+    if n > 64:  # same index map, written with index arrays for large n
+        l = np.arange(n)[:, None]
+        j = np.arange(n)[None, :]
+        return a[(l + j) % n, l]
+    out = np.zeros((n, n), dtype=a.dtype)
+    for j in range(n):
+        for l in range(n):
+            out[l, j] = a[(l + j) % n, l]
+    return out
+
+
+def cycle_layout_left(a: np.ndarray) -> np.ndarray:
+    """Cycles for the other form A = sum_j Lambda_j C^j (Appendix Eq. get_At1): [l, j] = A(l, (l-j) mod n)."""
+    n = a.shape[0]
+    out = np.zeros((n, n), dtype=a.dtype)
+    for j in range(n):
+        for l in range(n):
+            out[l, j] = a[l, (l - j) % n]
+    return out
+
+
+def from_cycle_layout(acyc: np.ndarray) -> np.ndarray:
+    """Inverse of cycle_layout: A((l + j) mod n, l) = A_cyc[l, j]."""
+    n = acyc.shape[0]
+    out = np.zeros((n, n), dtype=acyc.dtype)
+    if n > 64:
+        l = np.arange(n)[:, None]
+        j = np.arange(n)[None, :]
+        out[(l + j) % n, l] = acyc
+        return out
+    for j in range(n):
+        for l in range(n):
+            out[(l + j) % n, l] = acyc[l, j]
+    return out
+
+
+def cycle_matrices(a: np.ndarray):
+    """[(C^j, Lambda_j)] with A = sum_j C^j Lambda_j (Eq. rightdecomp)."""
+    n = a.shape[0]
+    c = cycle_perm(n)
+    acyc = cycle_layout(a)
+    out = []
+    cj = np.eye(n)
+    for j in range(n):
+        out.append((cj.copy(), np.diag(acyc[:, j])))
+        cj = c @ cj
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Circulant decomposition (Thm 2.1, Thm 2.5, Alg. 2)
+# ---------------------------------------------------------------------------
+
+
+def circulant_spectrum(a: np.ndarray) -> np.ndarray:
+    """R[k, j] = r_{j,k} = (1/n) sum_l e^{-2 pi i k l/n} Lambda_j(l, l)  (Thm 2.1 proof, Alg. 2).
+
+    Column FFTs of the cycle layout divided by n.  Row k is R_A[k], the first column of R_k.
+    Works for complex input as well (used by the backward projector).
+    """
+    n = a.shape[0]
+    return fft_cols(cycle_layout(a).astype(np.complex128)) / n
+
+
+def component_dense(R: np.ndarray, k: int) -> np.ndarray:
+    """R_k D^k as a dense complex matrix, R_k = sum_j r_{j,k} C^j (Thm 2.1)."""
+    n = R.shape[0]
+    return circulant(R[k]) @ diag_D(n, k)
+
+
+def reconstruct_explicit(R: np.ndarray, sel) -> np.ndarray:
+    """sum_{t in sel} R_t D^t, summing explicitly formed dense components (Thm 2.1)."""
+    n = R.shape[0]
+    out = np.zeros((n, n), dtype=np.complex128)
+    for t in sel:
+        out += component_dense(R, int(t))
+    return out
+
+
+def reconstruct(R: np.ndarray, sel) -> np.ndarray:
+    """sum_{t in sel} R_t D^t via the cycles: Lambda_j(c) = sum_{t in sel} r_{j,t} omega^{t c}.
+
+    Same definition as reconstruct_explicit, evaluated cycle by cycle (a matrix product with
+    the Vandermonde rows omega^{t c}); used where n is too large for dense components.
+    """
+    n = R.shape[0]
+    sel = np.asarray(list(sel), dtype=np.int64)
+    if sel.size == 0:
+        return np.zeros((n, n), dtype=np.complex128)
+    c = np.arange(n)
+    vand = np.exp(2j * np.pi * ((sel[:, None] * c[None, :]) % n) / n)  # [t, c] = omega^{t c}
+    lam = R[sel].T @ vand                                                 # [j, c] = Lambda_j(c)
+    return from_cycle_layout(lam.T)                                       # cycle layout is [l=c, j]
+
+
+def component_keys(R: np.ndarray) -> np.ndarray:
+    """T[k] = ||R_A[k]||_2 (Alg. 3 Step 2), evaluated for k <= n/2 and mirrored (reading R6)."""
+    n = R.shape[0]
+    t = np.zeros(n)
+    for k in range(n // 2 + 1):
+        t[k] = math.sqrt(float(np.sum(np.abs(R[k]) ** 2)))
+    for k in range(n // 2 + 1, n):
+        t[k] = t[n - k]
+    return t
+
+
+def eigen_spectrum(R: np.ndarray, t: int) -> np.ndarray:
+    """L_t = sqrt(n) W R_A[t] = F R_A[t], the eigenvalues of R_t (Alg. 3 Step 4)."""
+    return fft_cols(R[t].reshape(-1, 1)).ravel()
+
+
+# ---------------------------------------------------------------------------
+# Selection (Alg. 3 Step 3, Alg. 4) -- reading R6
+# ---------------------------------------------------------------------------
+
+
+def top_k(keys: np.ndarray, k: int) -> np.ndarray:
+    """Indices of the k largest keys, ordered by (key descending, index ascending)."""
+    keys = np.asarray(keys, dtype=np.float64)
+    idx = np.arange(len(keys))
+    order = np.lexsort((idx, -keys))  # last key is primary
+    return order[: min(k, len(keys))].astype(np.int64)
+
+
+def boundary_gap(keys: np.ndarray, k: int) -> float:
+    """Relative gap between the k-th and (k+1)-th largest keys (0 for an exact tie).
+
+    A selection is only bit-reproducible across precisions when this gap exceeds the key
+    error of the lower precision; the GPU parity tests use it to flag near-ties.
+    """
+    s = np.sort(np.asarray(keys, dtype=np.float64))[::-1]
+    if k <= 0 or k >= len(s):
+        return float("inf")
+    top = max(s[k - 1], 1e-300)
+    return float((s[k - 1] - s[k]) / top)
+
+
+def near_tie_sets(keys: np.ndarray, k: int, tau: float):
+    """(must, maybe): indices certainly selected, and the ambiguous set around the boundary.
+
+    Keys within relative distance tau of the k-th largest key are 'maybe'.
+    """
+    keys = np.asarray(keys, dtype=np.float64)
+    order = top_k(keys, len(keys))
+    if k >= len(keys):
+        return set(order.tolist()), set()
+    kth = keys[order[k - 1]]
+    band = np.abs(keys - kth) <= tau * max(abs(kth), 1e-300)
+    maybe = set(np.nonzero(band)[0].tolist())
+    must = set(i for i in order[:k].tolist() if i not in maybe)
+    return must, maybe
+
+
+# ---------------------------------------------------------------------------
+# Truncations
+# ---------------------------------------------------------------------------
+
+
+class Truncation:
+    """A = A~ + dA for one operand, with the data the product and backward need."""
+
+    def __init__(self, method, a, approx, sel=None, **extra):
+        self.method = method
+        self.a = a
+        self.approx = approx            # A~ (complex for circulant / Fourier)
+        self.resid = a - approx         # dA
+        self.sel = sel
+        self.__dict__.update(extra)
+
+
+def truncate_circulant(a: np.ndarray, k: int, selection=None) -> Truncation:
+    """A~ = sum_{t in S} R_t D^t with S = top-k of T (Alg. 2 + Alg. 3 Steps 1-3)."""
+    R = circulant_spectrum(a)
+    keys = component_keys(R)
+    sel = np.asarray(selection, dtype=np.int64) if selection is not None else top_k(keys, k)
+    approx = reconstruct(R, sel) if a.shape[0] > 32 else reconstruct_explicit(R, sel)
+    return Truncation("circulant", a, approx, sel, R=R, keys=keys)
+
+
+def rsvd(a: np.ndarray, k: int, phi: np.ndarray):
+    """Randomized partial SVD, Alg. 1: Y = A phi; Q R = qr(Y); X = Q^T A; U S V^T = svd(X); U <- Q U."""
+    y = a @ phi
+    q, _ = np.linalg.qr(y)
+    x = q.T @ a
+    ux, s, vt = np.linalg.svd(x, full_matrices=False)
+    return q @ ux, s, vt.T, q
+
+
+def truncate_rsvd(a: np.ndarray, k: int, phi: np.ndarray) -> Truncation:
+    """A~ = U Sigma V^T from Alg. 1 (Section 2.2)."""
+    u, s, v, q = rsvd(a, k, phi)
+    approx = (u * s[None, :]) @ v.T
+    return Truncation("svd", a, approx, None, U=u, S=s, V=v, Q=q)
+
+
+def truncate_svd_exact(a: np.ndarray, k: int) -> Truncation:
+    """Best rank-k approximation from the full SVD (Section 1.2.1, Eckart-Young)."""
+    u, s, vt = np.linalg.svd(a)
+    approx = (u[:, :k] * s[None, :k]) @ vt[:k]
+    return Truncation("svd_exact", a, approx, None, U=u[:, :k], S=s, V=vt[:k].T, Q=u[:, :k])
+
+
+def magnitudes_mirrored_rows(x: np.ndarray) -> np.ndarray:
+    """|x[i, q]| with q > n/2 copied from n - q (conjugate partners of a real signal; R6/R8)."""
+    n = x.shape[1]
+    mag = np.abs(x)
+    for q in range(n // 2 + 1, n):
+        mag[:, q] = mag[:, n - q]
+    return mag
+
+
+def topk_mask_rows(mag: np.ndarray, k: int, forced=None) -> np.ndarray:
+    """Alg. 4: keep the k largest entries of every row (ties: lower index first)."""
+    m, n = mag.shape
+    mask = np.zeros((m, n), dtype=bool)
+    for i in range(m):
+        sel = forced[i] if forced is not None else top_k(mag[i], k)
+        mask[i, np.asarray(sel, dtype=np.int64)] = True
+    return mask
+
+
+def truncate_fourier_left(a: np.ndarray, k: int, forced=None) -> Truncation:
+    """A~ = A W^* kept on its top-k entries per row (Alg. 5 lines 1, 3; Alg. 4)."""
+    n = a.shape[1]
+    at = a @ np.conj(unitary_W(n)).T
+    mask = topk_mask_rows(magnitudes_mirrored_rows(at), k, forced)
+    at_a = np.where(mask, at, 0)
+    # space-domain form A_s = A~_a W, so that A_s B = A~_a (W B) (Alg. 5 line 5)
+    return Truncation("fourier", a, at_a @ unitary_W(n), None, T=at, mask=mask, T_a=at_a)
+
+
+def truncate_fourier_right(b: np.ndarray, k: int, forced=None) -> Truncation:
+    """B~ = W B kept on its top-k entries per column (Alg. 5 lines 2, 4; reading R8)."""
+    n = b.shape[0]
+    bt = unitary_W(n) @ b
+    mask = topk_mask_rows(magnitudes_mirrored_rows(bt.T), k, forced).T
+    bt_a = np.where(mask, bt, 0)
+    # space-domain form B_s = W^* B~_a, so that dA B_s = (A~ - A~_a) B~_a (Alg. 5 line 6)
+    return Truncation("fourier", b, np.conj(unitary_W(n)).T @ bt_a, None, T=bt, mask=mask, T_a=bt_a)
+
+
+def cycle_keys(a: np.ndarray) -> np.ndarray:
+    """||diag Lambda_j||_2 for each cycle j (reading R9)."""
+    acyc = cycle_layout(a)
+    return np.sqrt(np.sum(np.abs(acyc) ** 2, axis=0))
+
+
+def truncate_cycles(a: np.ndarray, k: int, selection=None) -> Truncation:
+    """A_s = sum_{j in S} C^j Lambda_j, S = the k dominant cycles (Section 1.2.2, Section 4.3)."""
+    n = a.shape[0]
+    keys = cycle_keys(a)
+    sel = np.asarray(selection, dtype=np.int64) if selection is not None else top_k(keys, k)
+    acyc = cycle_layout(a)
+    kept = np.zeros_like(acyc)
+    kept[:, sel] = acyc[:, sel]
+    return Truncation("cycle", a, from_cycle_layout(kept), sel, keys=keys)
+
+
+# ---------------------------------------------------------------------------
+# First-order products (Eq. (2.1)-(2.3); Section 2.2, Alg. 3, Alg. 5)
+# ---------------------------------------------------------------------------
+
+
+def exact_product_loops(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """The triple loop A B (reference for the library matmul at small sizes)."""
+    m, n = a.shape
+    n2, p = b.shape
+    assert n == n2
+    out = np.zeros((m, p), dtype=np.result_type(a, b))
+    for i in range(m):
+        for j in range(p):
+            s = 0.0
+            for l in range(n):
+                s += a[i, l] * b[l, j]
+            out[i, j] = s
+    return out
+
+
+def first_order(ta: Truncation, tb: Truncation) -> np.ndarray:
+    """M = A~ B + dA B~ (Eq. (2.3)); complex in general."""
+    return ta.approx @ tb.a + ta.resid @ tb.approx
+
+
+def cd_matmul(a, b, ka, kb=None, sel_a=None, sel_b=None, full=False):
+    """Circulant first-order product (Alg. 3) evaluated with explicitly formed components.
+
+    Returns Re(M) (reading R5), or (Re M, M, ta, tb) with full=True.
+    """
+    ta = truncate_circulant(a, ka, sel_a)
+    tb = truncate_circulant(b, ka if kb is None else kb, sel_b)
+    m = first_order(ta, tb)
+    return (m.real, m, ta, tb) if full else m.real
+
+
+def cd_matmul_alg3(a, b, ka, kb=None, sel_a=None, sel_b=None) -> np.ndarray:
+    """Alg. 3 evaluated as printed (FFT form); returns the complex M.
+
+    Step 5: M = IFFT( sum_t diag(L_A[t]) C^{In_A[t]} FFT(B) ),
+    Step 6: M += ( IFFT( sum_t (C^{In_B[t]})^* diag(conj L_B[t]) FFT(dA^*) ) )^*.
+    (C^t Y)(p, :) = Y((p - t) mod n, :), i.e. np.roll(Y, t, axis=0).
+    """
+    n = a.shape[0]
+    kb = ka if kb is None else kb
+    ta = truncate_circulant(a, ka, sel_a)
+    tb = truncate_circulant(b, kb, sel_b)
+    fb = fft_cols(b.astype(np.complex128))
+    acc = np.zeros((n, b.shape[1]), dtype=np.complex128)
+    for t in ta.sel:
+        la = eigen_spectrum(ta.R, int(t))
+        acc += la[:, None] * np.roll(fb, int(t), axis=0)
+    m = ifft_cols(acc)
+    fda = fft_cols(np.conj(ta.resid).T)
+    acc = np.zeros_like(fda)
+    for t in tb.sel:
+        lb = eigen_spectrum(tb.R, int(t))
+        acc += np.roll(np.conj(lb)[:, None] * fda, -int(t), axis=0)
+    m = m + np.conj(ifft_cols(acc)).T
+    return m
+
+
+def svd_matmul(a, b, k, phi_a, phi_b, full=False, exact=False):
+    """SVD first-order product (Section 2.2): M = A~ B + dA B~ with Alg. 1 on A and on B."""
+    if exact:
+        ta, tb = truncate_svd_exact(a, k), truncate_svd_exact(b, k)
+    else:
+        ta, tb = truncate_rsvd(a, k, phi_a), truncate_rsvd(b, k, phi_b)
+    m = first_order(ta, tb)
+    return (m, m, ta, tb) if full else m
+
+
+def fourier_matmul(a, b, k, forced_a=None, forced_b=None, full=False):
+    """Alg. 5: M = A~_a B~ + (A~ - A~_a) B~_a with A~ = A W^*, B~ = W B; returns Re(M)."""
+    ta = truncate_fourier_left(a, k, forced_a)
+    tb = truncate_fourier_right(b, k, forced_b)
+    m = ta.T_a @ tb.T + (ta.T - ta.T_a) @ tb.T_a
+    return (m.real, m, ta, tb) if full else m.real
+
+
+def cycle_matmul(a, b, ka, kb=None, sel_a=None, sel_b=None, full=False):
+    """Cycle sparsification: M = A_s B + dA B_s (Eq. (2.4)-(2.5) with the cycles of Section 1.2.2)."""
+    ta = truncate_cycles(a, ka, sel_a)
+    tb = truncate_cycles(b, ka if kb is None else kb, sel_b)
+    m = first_order(ta, tb)
+    return (m, m, ta, tb) if full else m
+
+
+# ---------------------------------------------------------------------------
+# Error quantities (Section 2.1, Section 3)
+# ---------------------------------------------------------------------------
+
+
+def rel_fro(x, ref) -> float:
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def mu_circulant(R: np.ndarray, sel, resid_fro2: float) -> float:
+    """Spectral concentration mu (Def. 3.11): max_i X_i / (||dA||_F^2 / n), X_i = sum_{j not in S} |lambda_i(R_j)|^2."""
+    n = R.shape[0]
+    keep = np.ones(n, dtype=bool)
+    keep[np.asarray(sel, dtype=np.int64)] = False
+    lam = fft_cols(R.T)  # [i, j] = lambda_i(R_j)
+    x = np.sum(np.abs(lam[:, keep]) ** 2, axis=1)
+    return float(x.max() / (resid_fro2 / n))
+
+
+def posterior_estimate(resid_a_fro, resid_b_fro, m_fro, n) -> float:
+    """Cor. 3.7: E[||dA dB|| / ||AB||] ~ ||dA|| ||dB|| / (sqrt(n) ||M||)."""
+    return float(resid_a_fro * resid_b_fro / (math.sqrt(n) * m_fro))
+
+
+# ---------------------------------------------------------------------------
+# Backward of the frozen first-order map (reading R10)
+# ---------------------------------------------------------------------------
+
+
+def project_circulant(z: np.ndarray, sel) -> np.ndarray:
+    """P_S(Z) = sum_{t in S} R_t(Z) D^t: orthogonal projection onto the selected components."""
+    return reconstruct(circulant_spectrum(z), sel)
+
+
+def mirror(sel, n):
+    return np.array([(n - int(t)) % n for t in sel], dtype=np.int64)
+
+
+def cd_backward(ta: Truncation, tb: Truncation, g: np.ndarray):
+    """Gradients of <G, Re M> for M = A~ B + dA B~ with frozen selections S_A, S_B.
+
+    dA = Re[ G B~^T + P_{S_A-bar}(G dB^T) ],  dB = Re[ A~^T G + P_{S_B-bar}(dA^T G) ],
+    where S-bar = {n - t} (the bilinear adjoint of P_S) and ^T is the plain transpose.
+    """
+    n = ta.a.shape[0]
+    da = g @ tb.approx.T + project_circulant(g @ tb.resid.T, mirror(ta.sel, n))
+    db = ta.approx.T @ g + project_circulant(ta.resid.T @ g, mirror(tb.sel, n))
+    return da.real, db.real
+
+
+def svd_backward(ta: Truncation, tb: Truncation, g: np.ndarray):
+    """Same map for the SVD truncation: P_A(X) = Q_A Q_A^T X, P_B(X) = Q_B Q_B^T X (real, self-adjoint)."""
+    qa, qb = ta.Q, tb.Q
+    da = g @ tb.approx.T + qa @ (qa.T @ (g @ tb.resid.T))
+    db = ta.approx.T @ g + qb @ (qb.T @ (ta.resid.T @ g))
+    return da, db
+
+
+def project_cycles(z: np.ndarray, sel) -> np.ndarray:
+    """Orthogonal projection onto the selected cycles."""
+    zc = cycle_layout(z)
+    kept = np.zeros_like(zc)
+    kept[:, sel] = zc[:, sel]
+    return from_cycle_layout(kept)
+
+
+def cycle_backward(ta: Truncation, tb: Truncation, g: np.ndarray):
+    da = g @ tb.approx.T + project_cycles(g @ tb.resid.T, ta.sel)
+    db = ta.approx.T @ g + project_cycles(ta.resid.T @ g, tb.sel)
+    return da, db
+
+
+def fourier_backward(ta: Truncation, tb: Truncation, g: np.ndarray):
+    """For M = P_A(A W^*) W B + (A W^* - P_A(A W^*)) P_B(W B) with frozen element masks.
+
+    dA = Re[ (P_A(G dB~^T) + G B~_a^T) conj(W) ],  dB = Re[ W (A~_a^T G + P_B(dA~^T G)) ].
+    """
+    n = ta.a.shape[1]
+    w = unitary_W(n)
+    dbt = tb.T - tb.T_a
+    dat = ta.T - ta.T_a
+    da = (np.where(ta.mask, g @ dbt.T, 0) + g @ tb.T_a.T) @ np.conj(w)
+    db = w @ (ta.T_a.T @ g + np.where(tb.mask, dat.T @ g, 0))
+    return da.real, db.real
+
+
+def frozen_product(method: str, ta: Truncation, tb: Truncation, a, b) -> np.ndarray:
+    """Evaluate the frozen first-order map at new operands (a, b); real part.
+
+    The projectors of ta/tb (selections, Q factors, masks) are kept; only the operands change.
+    Used for finite differences and brute-force gradients.
+    """
+    n = a.shape[1]
+    if method == "circulant":
+        pa = project_circulant(a.astype(np.complex128), ta.sel)
+        pb = project_circulant(b.astype(np.complex128), tb.sel)
+    elif method == "svd":
+        pa = ta.Q @ (ta.Q.T @ a)
+        pb = tb.Q @ (tb.Q.T @ b)
+    elif method == "cycle":
+        pa = project_cycles(a, ta.sel)
+        pb = project_cycles(b, tb.sel)
+    elif method == "fourier":
+        w = unitary_W(n)
+        at = a @ np.conj(w).T
+        bt = w @ b
+        at_a = np.where(ta.mask, at, 0)
+        bt_a = np.where(tb.mask, bt, 0)
+        return (at_a @ bt + (at - at_a) @ bt_a).real
+    else:
+        raise ValueError(method)
+    return (pa @ b + (a - pa) @ pb).real
+
+
+def truncate(method: str, a, k, phi=None, selection=None, side="left"):
+    if method == "circulant":
+        return truncate_circulant(a, k, selection)
+    if method == "svd":
+        return truncate_rsvd(a, k, phi)
+    if method == "cycle":
+        return truncate_cycles(a, k, selection)
+    if method == "fourier":
+        return truncate_fourier_left(a, k, selection) if side == "left" else truncate_fourier_right(a, k, selection)
+    raise ValueError(method)
+
+
+def product(method: str, ta: Truncation, tb: Truncation) -> np.ndarray:
+    """Re(M) for any method from its two truncations."""
+    if method == "fourier":
+        return (ta.T_a @ tb.T + (ta.T - ta.T_a) @ tb.T_a).real
+    return first_order(ta, tb).real
+
+
+def backward(method: str, ta, tb, g):
+    return {"circulant": cd_backward, "svd": svd_backward, "cycle": cycle_backward,
+            "fourier": fourier_backward}[method](ta, tb, g)
+
+
+def brute_force_gradient(method, ta, tb, g):
+    """d<G, M>/dA and d/dB by evaluating the frozen map on every basis matrix (tiny n only)."""
+    a, b = ta.a, tb.a
+    da = np.zeros_like(a, dtype=np.float64)
+    db = np.zeros_like(b, dtype=np.float64)
+    zb = np.zeros_like(b)
+    za = np.zeros_like(a)
+    for i, j in itertools.product(range(a.shape[0]), range(a.shape[1])):
+        e = np.zeros_like(a)
+        e[i, j] = 1.0
+        # the map is bilinear: M(a, b) = M1(a) b-terms; isolate the a-linear part at fixed b
+        da[i, j] = np.sum(g * (frozen_product(method, ta, tb, e, b) - frozen_product(method, ta, tb, za, b)))
+    for i, j in itertools.product(range(b.shape[0]), range(b.shape[1])):
+        e = np.zeros_like(b)
+        e[i, j] = 1.0
+        db[i, j] = np.sum(g * (frozen_product(method, ta, tb, a, e) - frozen_product(method, ta, tb, a, zb)))
+    return da, db

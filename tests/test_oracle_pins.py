@@ -1,0 +1,458 @@
+"""Pins of the FP64 oracle to facts fixed by the paper or by mathematics (CPU only).
+
+Each test names the passage it checks.  Together they are chosen so that a plausible
+mistake in the oracle (a sign of omega, a transposed cycle layout, a dropped first-order
+term, a wrong projector in the backward) fails at least one of them; test_planted_mistakes
+demonstrates this by planting such mistakes into the oracle on the CPU.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.amm as OA
+import synth as S
+from conftest import GOLDEN
+
+
+def _rand(n, seed=0, m=None):
+    return S.rng(seed, 9).standard_normal((m or n, n))
+
+
+# --------------------------------------------------------------------------- cycles
+
+def _read_example():
+    grids, cur, cpow = {}, None, []
+    with open(os.path.join(GOLDEN, "cycle_example_4x4.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line in ("right", "left", "Cpow"):
+                cur = line
+                grids.setdefault(cur, [])
+                continue
+            if cur == "Cpow":
+                cpow.append(tuple(int(v) for v in line.split()))
+            else:
+                grids[cur].append(line.split())
+    return grids, cpow
+
+
+def test_cycle_layout_matches_worked_example():
+    """Appendix 4x4 example: both printed cycle layouts, entry for entry."""
+    grids, _ = _read_example()
+    n = 4
+    a = np.array([[100 + 10 * r + c for c in range(n)] for r in range(n)], dtype=np.float64)
+    label = lambda v: "%d%d" % ((int(v) - 100) // 10, (int(v) - 100) % 10)
+    right = [[label(v) for v in row] for row in O.cycle_layout(a)]
+    left = [[label(v) for v in row] for row in O.cycle_layout_left(a)]
+    assert right == grids["right"]
+    assert left == grids["left"]
+
+
+def test_cycle_power_nonzeros():
+    """Appendix: row r of C^k has its nonzero in column (r - k) mod n."""
+    _, cpow = _read_example()
+    c = O.cycle_perm(4)
+    for k, r, col in cpow:
+        ck = np.linalg.matrix_power(c, k)
+        assert ck[r, col] == 1.0 and ck[r].sum() == 1.0
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 16])
+def test_cycle_decomposition_sums_to_A(n):
+    """Section 1.2.2 / Eq. rightdecomp: A = sum_j C^j Lambda_j with explicit C^j."""
+    a = _rand(n)
+    total = sum(cj @ lam for cj, lam in O.cycle_matrices(a))
+    assert np.allclose(total, a, atol=1e-14, rtol=0)
+    assert np.array_equal(O.from_cycle_layout(O.cycle_layout(a)), a)
+
+
+# --------------------------------------------------------------------------- circulant decomposition
+
+@pytest.mark.parametrize("n", [4, 6, 8, 12, 16])
+def test_thm21_components_sum_to_A(n):
+    """Thm 2.1: A = sum_k R_k D^k, with dense explicitly formed components."""
+    a = _rand(n, 1)
+    R = O.circulant_spectrum(a)
+    assert np.abs(O.reconstruct_explicit(R, range(n)) - a).max() < 1e-13
+    assert np.abs(O.reconstruct(R, range(n)) - a).max() < 1e-13
+
+
+def test_components_frobenius_orthogonal():
+    """Remark after Thm 2.1: <R_i D^i, R_j D^j>_F = 0 (i != j) and = ||R_i||_F^2."""
+    n = 8
+    R = O.circulant_spectrum(_rand(n, 2))
+    comps = [O.component_dense(R, k) for k in range(n)]
+    gram = np.array([[np.vdot(x, y) for y in comps] for x in comps])
+    diag = np.array([np.linalg.norm(O.circulant(R[k])) ** 2 for k in range(n)])
+    assert np.abs(gram - np.diag(diag)).max() < 1e-13
+
+
+@pytest.mark.parametrize("n", [8, 9, 64, 128])
+def test_parseval_keys(n):
+    """||R_k D^k||_F^2 = n T[k]^2 and sum_k n T[k]^2 = ||A||_F^2 (Remark, Alg. 3 Step 2)."""
+    a = _rand(n, 3)
+    keys = O.component_keys(O.circulant_spectrum(a))
+    assert abs(n * np.sum(keys ** 2) - np.sum(a * a)) < 1e-10 * np.sum(a * a)
+
+
+def test_circulant_input_has_one_component():
+    """A circulant matrix times D^t is the single component t: ||R_k|| = 0 for k != t."""
+    n = 16
+    col = S.rng(4, 1).standard_normal(n)
+    for t in (0, 3, 8):
+        R = O.circulant_spectrum(O.circulant(col) @ O.diag_D(n, t))
+        norms = np.linalg.norm(R, axis=1)
+        assert norms[t] > 0.1 and np.delete(norms, t).max() < 1e-14
+        assert np.abs(R[t] - col).max() < 1e-14
+
+
+def test_thm25_least_squares():
+    """Thm 2.5: R_k minimises ||A - M D^k||_F over circulant M (basis C^j, lstsq)."""
+    n = 6
+    a = _rand(n, 5)
+    R = O.circulant_spectrum(a)
+    c = O.cycle_perm(n)
+    for k in range(n):
+        basis = [np.linalg.matrix_power(c, j) @ O.diag_D(n, k) for j in range(n)]
+        mat = np.stack([b.ravel() for b in basis], axis=1)
+        coef, *_ = np.linalg.lstsq(mat, a.ravel().astype(np.complex128), rcond=None)
+        assert np.abs(coef - R[k]).max() < 1e-13
+
+
+def test_eigen_spectrum_diagonalises_component():
+    """Alg. 3 Step 4: L_t = F R_A[t] are the eigenvalues of R_t: R_t = F^{-1} diag(L_t) F."""
+    n = 16
+    R = O.circulant_spectrum(_rand(n, 6))
+    f = O.dft_matrix(n)
+    for t in (0, 1, 5):
+        lt = O.eigen_spectrum(R, t)
+        assert np.abs(np.linalg.inv(f) @ np.diag(lt) @ f - O.circulant(R[t])).max() < 1e-13
+
+
+def test_shift_identity():
+    """Remark after Thm 2.1 / Section 2.3.2 (reading R2): W D^k W^* = C^k and F D^k b = C^k F b."""
+    n = 8
+    w = O.unitary_W(n)
+    c = O.cycle_perm(n)
+    for k in range(n):
+        assert np.abs(w @ O.diag_D(n, k) @ w.conj().T - np.linalg.matrix_power(c, k)).max() < 1e-13
+
+
+def test_library_fft_matches_dft_definition():
+    n = 128
+    x = S.rng(7, 0).standard_normal((n, 3))
+    assert np.abs(O.fft_cols(x) - O.dft_matrix(n) @ x).max() < 1e-11
+
+
+# --------------------------------------------------------------------------- selection
+
+def test_topk_tie_rule():
+    """Reading R6: (key descending, index ascending); conjugate partners tie exactly."""
+    assert O.top_k(np.array([1.0, 3.0, 3.0, 2.0, 3.0]), 3).tolist() == [1, 2, 4]
+    # a single nonzero entry has a flat spectrum: its cycle is a delta, every key is 1/n
+    n = 8
+    e00 = np.zeros((n, n))
+    e00[0, 0] = 1.0
+    keys = O.component_keys(O.circulant_spectrum(e00))
+    assert np.allclose(keys, 1 / n, rtol=1e-14, atol=0)
+    assert O.top_k(keys, 3).tolist() == [0, 1, 2]
+    # real input: T[k] == T[n-k] bit for bit
+    keys = O.component_keys(O.circulant_spectrum(_rand(12, 8)))
+    assert all(keys[k] == keys[12 - k] for k in range(1, 12))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_topk_minimises_residual_bruteforce(k):
+    """Section 2.3 (orthogonality): the top-k components minimise ||dA||_F over all k-subsets."""
+    n = 7
+    a = _rand(n, 10)
+    R = O.circulant_spectrum(a)
+    best = min(np.linalg.norm(a - O.reconstruct_explicit(R, sub)) for sub in itertools.combinations(range(n), k))
+    got = np.linalg.norm(O.truncate_circulant(a, k).resid)
+    assert got <= best * (1 + 1e-12)
+
+
+def test_truncation_error_from_keys():
+    """||dA||_F^2 = ||A||_F^2 - n sum_{t in S} T[t]^2 (orthogonality)."""
+    n = 32
+    a = _rand(n, 11)
+    tr = O.truncate_circulant(a, 5)
+    pred = np.sum(a * a) - n * np.sum(tr.keys[tr.sel] ** 2)
+    assert abs(np.linalg.norm(tr.resid) ** 2 - pred) < 1e-10 * np.sum(a * a)
+
+
+# --------------------------------------------------------------------------- products
+
+@pytest.mark.parametrize("n,k", [(16, 1), (16, 3), (16, 4), (16, 8), (32, 5), (32, 12)])
+def test_alg3_fft_form_equals_explicit(n, k):
+    """Alg. 3 (FFT form, shifts and conjugates as printed) equals the explicit dense A~B + dA B~."""
+    a, b = _rand(n, 12), S.rng(12, 1).uniform(0, 1, (n, n))
+    _, m, _, _ = O.cd_matmul(a, b, k, full=True)
+    m3 = O.cd_matmul_alg3(a, b, k)
+    assert np.abs(m - m3).max() < 1e-12 * np.abs(m).max()
+
+
+def _truncs(method, a, b, k, seed=0):
+    n = a.shape[1]
+    if method == "svd":
+        return O.truncate_rsvd(a, k, S.sketch(a.shape[1], k, seed, 0)), O.truncate_rsvd(b, k, S.sketch(b.shape[1], k, seed, 1))
+    if method == "fourier":
+        return O.truncate_fourier_left(a, k), O.truncate_fourier_right(b, k)
+    return O.truncate(method, a, k), O.truncate(method, b, k)
+
+
+@pytest.mark.parametrize("method", ["circulant", "svd", "fourier", "cycle"])
+def test_untruncated_is_exact(method):
+    """k = n keeps every component: M = AB for every decomposition."""
+    n = 16
+    a, b = _rand(n, 13), _rand(n, 14)
+    ta, tb = _truncs(method, a, b, n)
+    assert np.abs(O.product(method, ta, tb) - O.exact_product_loops(a, b)).max() < 1e-12 * np.abs(a @ b).max()
+
+
+@pytest.mark.parametrize("method", ["circulant", "svd", "fourier", "cycle"])
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_first_order_identity(method, k):
+    """Eq. (2.1)-(2.3): AB - M = dA dB exactly (the dropped second-order term)."""
+    n = 12
+    a, b = _rand(n, 15), S.rng(15, 1).uniform(0, 1, (n, n))
+    ta, tb = _truncs(method, a, b, k)
+    m = O.first_order(ta, tb)
+    assert np.abs((a @ b - m) - ta.resid @ tb.resid).max() < 1e-12 * np.abs(a @ b).max()
+
+
+def test_exact_product_loops():
+    a, b = _rand(5, 16, m=3), _rand(4, 17, m=5)
+    assert np.abs(O.exact_product_loops(a, b) - a @ b).max() < 1e-14
+
+
+# --------------------------------------------------------------------------- SVD
+
+def test_rsvd_rank_r_is_exact():
+    """Alg. 1 on a rank-r matrix with k >= r reproduces it (range finder captures the range)."""
+    n, r = 40, 5
+    g = S.rng(18, 0)
+    a = g.standard_normal((n, r)) @ g.standard_normal((r, n))
+    tr = O.truncate_rsvd(a, 8, S.sketch(n, 8, 18, 0))
+    assert np.abs(tr.resid).max() < 1e-11 * np.abs(a).max()
+
+
+def test_exact_svd_eckart_young_tail():
+    """Section 2.2: ||dA||_F = (||A||_F^2 - sum_{i<=k} sigma_i^2)^{1/2}, sigma known from the generator."""
+    n = 60
+    sig = np.exp(-np.arange(n) / 8.0)
+    a = S.spectrum_matrix(sig, S.rng(19, 0))
+    for k in (3, 10, 25):
+        tr = O.truncate_svd_exact(a, k)
+        assert abs(np.linalg.norm(tr.resid) - math.sqrt(np.sum(sig[k:] ** 2))) < 1e-12
+        assert np.allclose(tr.S, sig, atol=1e-12)
+
+
+def test_rsvd_sigma_interlacing():
+    """Alg. 1: singular values of Q^T A never exceed those of A."""
+    n = 64
+    sig = np.exp(-np.arange(n) / 6.0)
+    a = S.spectrum_matrix(sig, S.rng(20, 0))
+    u, s, v, q = O.rsvd(a, 10, S.sketch(n, 10, 20, 0))
+    assert np.all(s <= sig[:10] * (1 + 1e-12))
+    assert np.abs(q.T @ q - np.eye(10)).max() < 1e-13
+
+
+# --------------------------------------------------------------------------- bounds
+
+def test_thm38_svd_residual_bound():
+    """Thm 3.8: ||dA dB||_F^2 <= ||dA||_2 ||dB||_2 ||dA||_F ||dB||_F for best rank-k residuals."""
+    n = 50
+    a = S.type2(n, S.rng(21, 0))
+    b = S.type2(n, S.rng(21, 1))
+    for k in (2, 8, 20):
+        ta, tb = O.truncate_svd_exact(a, k), O.truncate_svd_exact(b, k)
+        lhs = np.linalg.norm(ta.resid @ tb.resid) ** 2
+        rhs = (np.linalg.norm(ta.resid, 2) * np.linalg.norm(tb.resid, 2) *
+               np.linalg.norm(ta.resid) * np.linalg.norm(tb.resid))
+        assert lhs <= rhs * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_thm312_cd_residual_bound(seed):
+    """Thm 3.12: ||dA dB||_F <= (mu_A mu_B)^{1/4} n^{-1/2} ||dA||_F ||dB||_F (Def. 3.11 for mu)."""
+    n = 32
+    g = S.rng(22 + seed, 0)
+    a = g.standard_normal((n, n)) + 2.0
+    b = S.toeplitz_uniform(n, g) + 0.1 * g.standard_normal((n, n))
+    for k in (1, 4, 9):
+        _, _, ta, tb = O.cd_matmul(a, b, k, full=True)
+        na, nb = np.linalg.norm(ta.resid), np.linalg.norm(tb.resid)
+        mua = O.mu_circulant(ta.R, ta.sel, na ** 2)
+        mub = O.mu_circulant(tb.R, tb.sel, nb ** 2)
+        assert np.linalg.norm(ta.resid @ tb.resid) <= (mua * mub) ** 0.25 / math.sqrt(n) * na * nb * (1 + 1e-12)
+
+
+# --------------------------------------------------------------------------- sparsifiers
+
+def test_fourier_unitary_parseval():
+    """Thm 2.3 / Section 2.4: A W^* preserves the Frobenius norm (sum_k a_k^2 = ||A||_F^2)."""
+    a = _rand(10, 23, m=7)
+    assert abs(np.linalg.norm(a @ O.unitary_W(10).conj().T) - np.linalg.norm(a)) < 1e-13
+
+
+def test_fourier_topk_rows_optimal():
+    """Alg. 4: per row the kept k entries minimise the row residual (unitary W => ||dA|| = ||dA~||)."""
+    n, k = 7, 3
+    a = _rand(n, 24, m=4)
+    tr = O.truncate_fourier_left(a, k)
+    for i in range(4):
+        row = tr.T[i]
+        best = min(np.linalg.norm(np.delete(row, list(sub))) for sub in itertools.combinations(range(n), k))
+        assert np.linalg.norm(row[~tr.mask[i]]) <= best * (1 + 1e-12)
+        assert np.linalg.norm(tr.resid[i]) == pytest.approx(np.linalg.norm(row[~tr.mask[i]]), rel=1e-12)
+
+
+def test_fourier_conjugate_ties_mirrored():
+    """Reading R8: |A~(i,q)| and |A~(i,n-q)| tie exactly; the lower index wins the tie."""
+    n = 8
+    a = _rand(n, 25, m=3)
+    tr = O.truncate_fourier_left(a, 1)
+    mag = O.magnitudes_mirrored_rows(tr.T)
+    assert all(mag[i, q] == mag[i, n - q] for i in range(3) for q in range(1, n))
+    for i in range(3):
+        q = int(np.nonzero(tr.mask[i])[0][0])
+        assert q <= n // 2
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_cycle_topk_optimal(k):
+    """Cycles are orthogonal (disjoint supports): the k largest cycles minimise ||dA||_F."""
+    n = 6
+    a = _rand(n, 26)
+    acyc = O.cycle_layout(a)
+    best = min(np.linalg.norm(np.delete(acyc, list(sub), axis=1)) for sub in itertools.combinations(range(n), k))
+    assert np.linalg.norm(O.truncate_cycles(a, k).resid) <= best * (1 + 1e-12)
+
+
+def test_cycle_apply_is_shift_and_scale():
+    """Section 1.2.2: C^j Lambda_j B = row shift of B by j, rows scaled by the cycle entries."""
+    n = 9
+    a, b = _rand(n, 27), _rand(n, 28)
+    acyc = O.cycle_layout(a)
+    j = 4
+    direct = O.cycle_matrices(a)[j][0] @ O.cycle_matrices(a)[j][1] @ b
+    shifted = np.zeros_like(b)
+    for r in range(n):
+        shifted[r] = acyc[(r - j) % n, j] * b[(r - j) % n]
+    assert np.abs(direct - shifted).max() < 1e-14
+
+
+# --------------------------------------------------------------------------- backward
+
+@pytest.mark.parametrize("method", ["circulant", "svd", "fourier", "cycle"])
+def test_backward_matches_bruteforce(method):
+    """Reading R10: closed-form gradients equal <G, M(E_ij)> over every basis matrix E_ij."""
+    n, k = 5, 2
+    g = S.rng(29, 0)
+    a, b, gr = g.standard_normal((n, n)), g.standard_normal((n, n)), g.standard_normal((n, n))
+    ta, tb = _truncs(method, a, b, k, seed=29)
+    da, db = O.backward(method, ta, tb, gr)
+    bda, bdb = O.brute_force_gradient(method, ta, tb, gr)
+    assert np.abs(da - bda).max() < 1e-12 and np.abs(db - bdb).max() < 1e-12
+
+
+@pytest.mark.parametrize("method", ["circulant", "svd"])
+def test_backward_finite_differences_n64(method):
+    """Central finite differences of the frozen map at n = 64 (FP64) along random directions."""
+    n, k = 64, 6
+    g = S.rng(30, 0)
+    a, b, gr = g.standard_normal((n, n)), g.standard_normal((n, n)), g.standard_normal((n, n))
+    ta, tb = _truncs(method, a, b, k, seed=30)
+    da, db = O.backward(method, ta, tb, gr)
+    for _ in range(2):
+        ea, eb = g.standard_normal((n, n)), g.standard_normal((n, n))
+        h = 1e-3
+        f = lambda x, y: np.sum(gr * O.frozen_product(method, ta, tb, x, y))
+        fd_a = (f(a + h * ea, b) - f(a - h * ea, b)) / (2 * h)
+        fd_b = (f(a, b + h * eb) - f(a, b - h * eb)) / (2 * h)
+        assert fd_a == pytest.approx(np.sum(da * ea), rel=1e-9)
+        assert fd_b == pytest.approx(np.sum(db * eb), rel=1e-9)
+
+
+# --------------------------------------------------------------------------- printed tables
+
+def _table_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_tables_n700.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                t, pair, method, order, tol, s, expect = line.split()
+                rows.append((int(t), pair, method, order, float(tol), int(s), expect))
+    return rows
+
+
+_MAKERS = {"general": S.general_uniform, "toeplitz": S.toeplitz_uniform, "type1": S.type1}
+
+
+@pytest.mark.slow
+def test_paper_tables_n700():
+    """Tables 1 and 2 (n = 700, k = ceil(s log2 n)): the printed error thresholds."""
+    n = 700
+    cache = {}
+    for table, pair, method, order, tol, s, expect in _table_rows():
+        if pair not in cache:
+            x, y = pair.split(",")
+            a, b = _MAKERS[x](n, S.rng(0, 0)), _MAKERS[y](n, S.rng(0, 1))
+            cache[pair] = (a, b, a @ b)
+        a, b, ex = cache[pair]
+        k = math.ceil(s * math.log2(n))
+        if method == "circulant":
+            ta, tb = O.truncate_circulant(a, k), O.truncate_circulant(b, k)
+        elif method == "rsvd":
+            ta, tb = O.truncate_rsvd(a, k, S.sketch(n, k, 0, 0)), O.truncate_rsvd(b, k, S.sketch(n, k, 0, 1))
+        else:
+            ta, tb = O.truncate_svd_exact(a, k), O.truncate_svd_exact(b, k)
+        m = O.first_order(ta, tb) if order == "first" else ta.approx @ tb.approx
+        err = O.rel_fro(m.real, ex)
+        ok = err <= tol if expect == "le" else err > tol
+        assert ok, (table, pair, method, order, tol, s, expect, err)
+
+
+# --------------------------------------------------------------------------- planted mistakes
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Plant plausible mistakes in the oracle (CPU) and check that a pin above fails for each."""
+    n = 8
+    a = _rand(n, 31)
+
+    # 1) wrong sign of omega in D: Thm 2.1 reconstruction breaks
+    good_D = OA.diag_D
+    monkeypatch.setattr(OA, "diag_D", lambda nn, k=1: np.conj(good_D(nn, k)))
+    R = O.circulant_spectrum(a)
+    assert np.abs(O.reconstruct_explicit(R, range(n)) - a).max() > 1e-3
+    monkeypatch.setattr(OA, "diag_D", good_D)
+
+    # 2) cycle layout of the other form (Lambda_j C^j): the worked example pin breaks
+    grids, _ = _read_example()
+    aa = np.array([[100 + 10 * r + c for c in range(4)] for r in range(4)], dtype=np.float64)
+    label = lambda v: "%d%d" % ((int(v) - 100) // 10, (int(v) - 100) % 10)
+    assert [[label(v) for v in row] for row in O.cycle_layout_left(aa)] != grids["right"]
+
+    # 3) dropped first-order term: the first-order identity breaks
+    b = _rand(n, 32)
+    ta, tb = O.truncate_circulant(a, 2), O.truncate_circulant(b, 2)
+    zeroth = ta.approx @ tb.approx
+    assert np.abs((a @ b - zeroth) - ta.resid @ tb.resid).max() > 1e-3
+
+    # 4) backward projecting onto S instead of S-bar: brute force disagrees (unpaired selection)
+    g = _rand(n, 33)
+    k = next(k for k in range(1, n) if set(O.truncate_circulant(a, k).sel.tolist()) !=
+             set(O.mirror(O.truncate_circulant(a, k).sel, n).tolist()))
+    ta, tb = O.truncate_circulant(a, k), O.truncate_circulant(b, k)
+    monkeypatch.setattr(OA, "mirror", lambda sel, nn: np.asarray(sel))
+    da, _ = O.cd_backward(ta, tb, g)
+    monkeypatch.undo()
+    bda, _ = O.brute_force_gradient("circulant", ta, tb, g)
+    assert np.abs(da - bda).max() > 1e-6
