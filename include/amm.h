@@ -1,0 +1,190 @@
+/*
+ * amm.h -- C ABI of libamm: approximate matrix multiplication from truncated
+ * decompositions, evaluated in the first-order form
+ *
+ *        A B  ~=  M = A~ B + dA B~        (A = A~ + dA,  B = B~ + dB)
+ *
+ * of Kar, Hariprasad, Sai Gowri, Venkatapathi, "Efficient approximations of matrix
+ * multiplication using truncated decompositions", arXiv 2504.19308, Eq. (2.1)-(2.3).
+ * The dropped term is dA dB.  Implemented for one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are row-major.  A "leading dimension" is the distance in elements
+ *    between the starts of consecutive rows and must be >= the number of columns.
+ *  - Every matrix pointer is a DEVICE pointer unless the argument name starts
+ *    with host_.  The caller owns every matrix it passes in or out.
+ *  - Calls are asynchronous on the CUDA stream passed as `stream` (a cudaStream_t;
+ *    NULL is the legacy default stream).  Argument errors are detected on the host
+ *    and returned before anything is launched; nothing is then modified.
+ *  - No C++ exception crosses this boundary.  A non-OK status leaves a one-line
+ *    reason readable with amm_last_error() (thread-local).
+ *  - Device memory that a handle owns is allocated stream-ordered on the stream
+ *    of amm_decompose() and released by amm_handle_destroy().
+ *  - The product written to C (and the gradients) are real FP32.  Where a
+ *    truncation keeps one of two complex-conjugate components but not the other,
+ *    M is complex; the library returns Re(M) (real inputs make A B real, so the
+ *    real part is never a worse approximation).
+ */
+#ifndef AMM_H
+#define AMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMM_VERSION 1
+
+typedef enum {
+  AMM_OK = 0,
+  AMM_ERR_INVALID_ARG = 1,      /* NULL pointer, bad enum, bad leading dimension, k out of range */
+  AMM_ERR_UNSUPPORTED_SIZE = 2, /* size the kernels do not implement (e.g. non power-of-two FFT length) */
+  AMM_ERR_OOM = 3,              /* a device allocation failed (or an injected failure fired) */
+  AMM_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed */
+  AMM_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up (batch scheduler) */
+  AMM_ERR_STATE = 6,            /* handles do not fit together (role, shape, method) */
+  AMM_ERR_NOT_IMPLEMENTED = 7   /* valid request for a feature this build does not provide */
+} amm_status_t;
+
+/* The truncated decompositions of the paper. */
+typedef enum {
+  AMM_SVD = 0,            /* randomized rank-k SVD, Alg. 1 (Section 2.2)                      */
+  AMM_CIRCULANT = 1,      /* k leading circulant components R_t D^t, Thm 2.1, Alg. 2-3 (Sec. 2.3) */
+  AMM_SPARSE_FOURIER = 2, /* top-k entries per row of A W^* / per column of W B, Alg. 4-5 (Sec. 2.4) */
+  AMM_SPARSE_CYCLE = 3    /* k dominant cycles C^j Lambda_j (Section 1.2.2)                   */
+} amm_method_t;
+
+/* Element type of an input matrix, and arithmetic mode of the low-rank GEMMs. */
+typedef enum { AMM_F32 = 0, AMM_BF16 = 1 } amm_dtype_t;
+
+/* Which side of the product a handle stands for.  The first-order form is not
+ * symmetric in A and B (A~ multiplies B; dA multiplies B~), so a decomposition
+ * is made for one side. */
+typedef enum { AMM_LEFT = 1, AMM_RIGHT = 2 } amm_role_t;
+
+typedef struct amm_opts {
+  uint32_t struct_size;           /* sizeof(amm_opts_t); set by amm_opts_init()             */
+  int32_t role;                   /* amm_role_t; default AMM_LEFT                            */
+  int32_t compute;                /* amm_dtype_t of the SVD GEMMs; default AMM_F32           */
+  uint64_t seed;                  /* seed of the rSVD test matrix when `sketch` is NULL      */
+  const float* sketch;            /* optional DEVICE pointer to phi (cols x k, row-major,
+                                     N(0,1) entries) for AMM_SVD; copied at decompose time   */
+  int32_t store_spectra;          /* reserved: 1 keeps spectra for the backward (default)    */
+  const int32_t* forced_selection;/* optional HOST array of k component indices that replaces
+                                     the top-k selection (AMM_CIRCULANT, AMM_SPARSE_CYCLE);
+                                     used to evaluate a selection exported elsewhere          */
+} amm_opts_t;
+
+typedef struct amm_info {
+  int32_t method, role, dtype;
+  int64_t rows, cols, k;
+  int64_t n_union;       /* circulant: |S u S-bar|, components applied with weights 1 or 1/2 */
+  int64_t n_unpaired;    /* circulant: selected components whose conjugate partner was not   */
+  double fro2;           /* ||A||_F^2 as seen by the decomposition (Parseval for circulant)  */
+  double resid_fro2;     /* ||dA||_F^2 = ||A||_F^2 - ||A~||_F^2 (orthogonality, Sec. 2.3)    */
+  double boundary_gap;   /* relative gap between the k-th and (k+1)-th keys (0 = exact tie)  */
+} amm_info_t;
+
+typedef struct amm_handle* amm_handle_t;
+
+/* Human-readable name of a status.  Never NULL. */
+const char* amm_status_string(amm_status_t status);
+
+/* One-line reason for the last non-OK status returned on this thread ("" if none). */
+const char* amm_last_error(void);
+
+/* AMM_VERSION of the loaded library. */
+int32_t amm_version(void);
+
+/* Fill `opts` with defaults (role LEFT, F32, seed 0, no sketch, no forced selection). */
+amm_status_t amm_opts_init(amm_opts_t* opts);
+
+/*
+ * Truncated decomposition of one operand (Section 2: A = sum_{i<k} A_i + dA).
+ *
+ *   A       device pointer, rows x cols row-major, leading dimension lda, element type
+ *           `dtype`.  BORROWED: the handle keeps the pointer (the residual terms and the
+ *           backward read A again), so A must stay allocated and unchanged until
+ *           amm_handle_destroy().
+ *   method  AMM_CIRCULANT and AMM_SPARSE_CYCLE need rows == cols (square, Section 2.3:
+ *           rectangular matrices are handled blockwise by the caller); the FFT length n
+ *           must be a power of two in [16, 8192].
+ *   k       number of kept components (1 <= k <= min(rows, cols) for AMM_SVD; <= n else).
+ *   opts    may be NULL (defaults).
+ *   stream  cudaStream_t for all work and allocations of this handle.
+ *   out     receives the handle; unchanged on error.
+ *
+ * Circulant: computes the cycle spectrum R (Alg. 2), keys T[t] = ||R_A[t]||_2 (Alg. 3
+ * Step 2), the top-k selection ordered by (key desc, index asc) (Step 3), the eigen-
+ * spectra L_t = F R_A[t] of the selected components (Step 4), and, for the RIGHT role,
+ * the dense residual dB (Step 6, for the other operand).
+ * SVD: Y = A phi, Q = orth(Y), X = Q^T A (Alg. 1, without the small SVD, which does not
+ * change A~ = Q Q^T A).
+ */
+amm_status_t amm_decompose(const void* A, int64_t rows, int64_t cols, int64_t lda,
+                           amm_dtype_t dtype, amm_method_t method, int64_t k,
+                           const amm_opts_t* opts, void* stream, amm_handle_t* out);
+
+/*
+ * C = Re(M) = Re(A~ B + dA B~)  (Eq. (2.3); Alg. 3 for circulant; Section 2.2 for SVD).
+ *
+ *   hA      handle of A (role AMM_LEFT), hB handle of B (role AMM_RIGHT); A is m x n,
+ *           B is n x p (inner dimensions must match, methods must be equal).
+ *   C       device pointer, m x p FP32 row-major, leading dimension ldc >= p.  Overwritten.
+ *   stream  stream of the call; must be ordered after the decompositions' streams.
+ */
+amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, float* C, int64_t ldc,
+                               void* stream);
+
+/*
+ * Gradients of L = <dC, Re M> with the truncation frozen (selections, Q factors and
+ * masks held fixed; M is then bilinear in A and B):
+ *     dA = Re[ dC B~^T + P_A'(dC dB^T) ],   dB = Re[ A~^T dC + P_B'(dA^T dC) ]
+ * where P' is the adjoint projector onto the kept components.
+ *   dC  device m x p FP32 (lddc).  dA (m x n, ldda) and dB (n x p, lddb) are overwritten;
+ *   either may be NULL to skip it.
+ */
+amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const float* dC,
+                                        int64_t lddc, float* dA, int64_t ldda, float* dB,
+                                        int64_t lddb, void* stream);
+
+/* Sizes, norms and selection statistics.  Synchronises the handle's stream. */
+amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info);
+
+/*
+ * Copy the selection to host memory: circulant component indices / cycle indices in
+ * selection order (k entries).  `cap` is the capacity of host_idx in elements; *count
+ * receives k.  Synchronises the handle's stream.
+ */
+amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t cap,
+                                      int64_t* count);
+
+/* Copy the rSVD test matrix phi (cols x k, row-major) to host memory.  Synchronises. */
+amm_status_t amm_handle_get_sketch(amm_handle_t h, float* host_phi, int64_t cap);
+
+/* Release every device buffer the handle owns (stream-ordered) and the handle. */
+amm_status_t amm_handle_destroy(amm_handle_t h);
+
+/*
+ * Launch tracing for measurement.  While enabled, every kernel launch the library makes is
+ * bracketed by two CUDA events on the launch's own stream.  amm_trace_collect() waits for
+ * the recorded launches, writes a JSON object {"kernel name": [launches, total_ms], ...} of
+ * everything recorded since the previous collect into host_json (capacity `cap` bytes,
+ * NUL-terminated) and the number of launches into *launches (may be NULL).
+ */
+amm_status_t amm_trace_enable(int32_t on);
+amm_status_t amm_trace_collect(char* host_json, int64_t cap, int64_t* launches);
+
+/*
+ * Fault injection for tests: the n-th device allocation from now on (1-based) fails with
+ * AMM_ERR_OOM; 0 disables.  Affects only this process.
+ */
+amm_status_t amm_debug_fail_alloc_after(int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMM_H */

@@ -1,0 +1,6 @@
+"""GB300-native first-order approximate matrix multiplication from truncated decompositions.
+
+Python front end of libamm (include/amm.h): arXiv 2504.19308, M = A~ B + dA B~.
+"""
+from .amm import (AmmError, ApproxMatmulFn, Handle, approx_matmul, approx_matmul_autograd,  # noqa: F401
+                  approx_matmul_backward, decompose, load_library, LIB_PATH)

@@ -1,0 +1,240 @@
+"""Python binding of libamm (include/amm.h): argument marshalling only.
+
+Every numerical step runs in the CUDA kernels behind the C ABI.  PyTorch supplies device
+memory and the current CUDA stream.  There is no CPU fallback: if libamm.so is missing or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamm.so")
+
+METHODS = {"svd": 0, "circulant": 1, "fourier": 2, "cycle": 3}
+DTYPES = {torch.float32: 0, torch.bfloat16: 1}
+ROLES = {"left": 1, "right": 2}
+STATUS = ["AMM_OK", "AMM_ERR_INVALID_ARG", "AMM_ERR_UNSUPPORTED_SIZE", "AMM_ERR_OOM", "AMM_ERR_CUDA",
+          "AMM_ERR_TIMEOUT", "AMM_ERR_STATE", "AMM_ERR_NOT_IMPLEMENTED"]
+
+
+class AmmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__("%s failed: %s (%s)" % (where, name, detail))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("role", ctypes.c_int32), ("compute", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("sketch", ctypes.c_void_p), ("store_spectra", ctypes.c_int32),
+                ("forced_selection", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("role", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("n_union", ctypes.c_int64), ("n_unpaired", ctypes.c_int64), ("fro2", ctypes.c_double),
+                ("resid_fro2", ctypes.c_double), ("boundary_gap", ctypes.c_double)]
+
+
+# every exported symbol of include/amm.h with its ctypes signature
+SIGNATURES = {
+    "amm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "amm_last_error": (ctypes.c_char_p, []),
+    "amm_version": (ctypes.c_int32, []),
+    "amm_opts_init": (ctypes.c_int, [ctypes.POINTER(Opts)]),
+    "amm_decompose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int64, ctypes.POINTER(Opts), ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_void_p)]),
+    "amm_approx_matmul": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p]),
+    "amm_approx_matmul_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                                  ctypes.c_void_p]),
+    "amm_handle_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
+    "amm_handle_get_selection": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                                ctypes.POINTER(ctypes.c_int64)]),
+    "amm_handle_get_sketch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    "amm_handle_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "amm_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int32]),
+    "amm_trace_enable": (ctypes.c_int, [ctypes.c_int32]),
+    "amm_trace_collect": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libamm.so (built by paper_2504_19308_gb300.build).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libamm.so not found at %s: run __graft_entry__.build() (nvcc, sm_103a) first" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise AmmError(status, where, load_library().amm_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _require_cuda(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor (the library has no CPU path)" % name)
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("%s must be a 2-D row-major tensor with unit column stride" % name)
+
+
+class Handle:
+    """Truncated decomposition of one operand; keeps the operand alive (the library borrows it)."""
+
+    def __init__(self, ptr: int, source: torch.Tensor, method: str, role: str, k: int, extras=()):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.source = source
+        self.method = method
+        self.role = role
+        self.k = k
+        self._extras = extras  # tensors that must outlive the launch (sketch)
+
+    @property
+    def shape(self):
+        return tuple(self.source.shape)
+
+    def info(self) -> dict:
+        info = Info()
+        _check(load_library().amm_handle_info(self.ptr, ctypes.byref(info)), "amm_handle_info")
+        return {f: getattr(info, f) for f, _ in Info._fields_}
+
+    def selection(self) -> np.ndarray:
+        buf = (ctypes.c_int32 * self.k)()
+        cnt = ctypes.c_int64(0)
+        _check(load_library().amm_handle_get_selection(self.ptr, buf, self.k, ctypes.byref(cnt)),
+               "amm_handle_get_selection")
+        return np.frombuffer(buf, dtype=np.int32, count=cnt.value).copy()
+
+    def sketch(self) -> np.ndarray:
+        n = self.source.shape[1]
+        buf = (ctypes.c_float * (n * self.k))()
+        _check(load_library().amm_handle_get_sketch(self.ptr, buf, n * self.k), "amm_handle_get_sketch")
+        return np.frombuffer(buf, dtype=np.float32).reshape(n, self.k).copy()
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            _check(load_library().amm_handle_destroy(self.ptr), "amm_handle_destroy")
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            if self.ptr is not None and self.ptr.value and _lib is not None:
+                _lib.amm_handle_destroy(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+
+def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: Optional[torch.Tensor] = None,
+              seed: int = 0, forced_selection=None) -> Handle:
+    """amm_decompose: truncated decomposition of A (method 'circulant' | 'svd' | 'fourier' | 'cycle')."""
+    lib = load_library()
+    _require_cuda(A, "A")
+    if A.dtype not in DTYPES:
+        raise ValueError("A must be float32 or bfloat16")
+    opts = Opts()
+    _check(lib.amm_opts_init(ctypes.byref(opts)), "amm_opts_init")
+    opts.role = ROLES[role]
+    opts.seed = seed
+    extras = []
+    if sketch is not None:
+        _require_cuda(sketch, "sketch")
+        sketch = sketch.to(torch.float32).contiguous()
+        opts.sketch = sketch.data_ptr()
+        extras.append(sketch)
+    forced = None
+    if forced_selection is not None:
+        forced = (ctypes.c_int32 * k)(*[int(v) for v in forced_selection])
+        opts.forced_selection = ctypes.cast(forced, ctypes.POINTER(ctypes.c_int32))
+    out = ctypes.c_void_p(0)
+    _check(lib.amm_decompose(A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), DTYPES[A.dtype], METHODS[method], k,
+                             ctypes.byref(opts), _stream_ptr(A.device), ctypes.byref(out)), "amm_decompose")
+    return Handle(out.value, A, method, role, k, tuple(extras))
+
+
+def approx_matmul(hA: Handle, hB: Handle, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """amm_approx_matmul: Re(A~ B + dA B~) as an FP32 tensor."""
+    m, p = hA.shape[0], hB.shape[1]
+    if out is None:
+        out = torch.empty((m, p), dtype=torch.float32, device=hA.source.device)
+    _require_cuda(out, "out")
+    _check(load_library().amm_approx_matmul(hA.ptr, hB.ptr, out.data_ptr(), out.stride(0),
+                                            _stream_ptr(out.device)), "amm_approx_matmul")
+    return out
+
+
+def approx_matmul_backward(hA: Handle, hB: Handle, dC: torch.Tensor, need_dA: bool = True, need_dB: bool = True):
+    """amm_approx_matmul_backward: gradients of <dC, Re M> with the truncation frozen."""
+    _require_cuda(dC, "dC")
+    dC = dC.to(torch.float32).contiguous()
+    dev = dC.device
+    dA = torch.empty(hA.shape, dtype=torch.float32, device=dev) if need_dA else None
+    dB = torch.empty(hB.shape, dtype=torch.float32, device=dev) if need_dB else None
+    _check(load_library().amm_approx_matmul_backward(
+        hA.ptr, hB.ptr, dC.data_ptr(), dC.stride(0), dA.data_ptr() if dA is not None else None,
+        dA.stride(0) if dA is not None else 0, dB.data_ptr() if dB is not None else None,
+        dB.stride(0) if dB is not None else 0, _stream_ptr(dev)), "amm_approx_matmul_backward")
+    return dA, dB
+
+
+class ApproxMatmulFn(torch.autograd.Function):
+    """Autograd layer: forward decomposes both operands and evaluates the first-order product;
+    backward calls the hand-written adjoint kernels with the truncation frozen."""
+
+    @staticmethod
+    def forward(ctx, A, B, method: str, k: int, sketch_a=None, sketch_b=None):
+        hA = decompose(A.detach(), method, k, "left", sketch=sketch_a)
+        hB = decompose(B.detach(), method, k, "right", sketch=sketch_b)
+        ctx.handles = (hA, hB)
+        return approx_matmul(hA, hB)
+
+    @staticmethod
+    def backward(ctx, grad):
+        hA, hB = ctx.handles
+        dA, dB = approx_matmul_backward(hA, hB, grad, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return dA, dB, None, None, None, None
+
+
+def approx_matmul_autograd(A, B, method: str, k: int, sketch_a=None, sketch_b=None):
+    return ApproxMatmulFn.apply(A, B, method, k, sketch_a, sketch_b)
+
+
+def trace_enable(on: bool = True):
+    _check(load_library().amm_trace_enable(1 if on else 0), "amm_trace_enable")
+
+
+def trace_collect():
+    """{kernel name: (launches, total_ms)} since the previous collect, and the launch count."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    n = ctypes.c_int64(0)
+    _check(load_library().amm_trace_collect(buf, len(buf), ctypes.byref(n)), "amm_trace_collect")
+    return {k: tuple(v) for k, v in json.loads(buf.value.decode()).items()}, n.value
+
+
+def debug_fail_alloc_after(n: int):
+    _check(load_library().amm_debug_fail_alloc_after(n), "amm_debug_fail_alloc_after")

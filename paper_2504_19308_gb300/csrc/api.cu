@@ -1,0 +1,365 @@
+// C ABI of libamm (include/amm.h): argument checking, handle ownership, launch order.
+// Every step of the numerical path runs in the kernels of circulant.cu / svd.cu; this
+// file only validates, allocates (stream-ordered) and launches.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "../../include/amm.h"
+#include "api_internal.h"
+#include "kernels.h"
+
+using namespace amm;
+
+// ----------------------------------------------------------------------------- errors
+static thread_local char g_last_error[512] = "";
+
+amm_status_t amm::fail(amm_status_t s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+amm_status_t amm::cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(AMM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(AMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ----------------------------------------------------------------------------- allocation
+static std::atomic<int> g_fail_after{0};
+
+cudaError_t amm::dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+  int f = g_fail_after.load();
+  if (f > 0) {
+    if (f == 1) {
+      g_fail_after.store(0);
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    g_fail_after.store(f - 1);
+  }
+  if (bytes == 0) bytes = 16;
+  return cudaMallocAsync(p, bytes, st);
+}
+
+void amm::dev_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+// Per (device, n) twiddle table e^{-2 pi i m/n}, built once and kept for the process.
+static std::mutex g_tw_mu;
+static std::map<std::pair<int, int>, float2*> g_tw;
+
+cudaError_t amm::twiddles(int n, cudaStream_t st, const float2** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto it = g_tw.find({dev, n});
+  if (it != g_tw.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  float2* tw = nullptr;
+  e = cudaMalloc(&tw, sizeof(float2) * (size_t)n);
+  if (e != cudaSuccess) return e;
+  e = cd_twiddles(tw, n, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(tw);
+    return e;
+  }
+  g_tw[{dev, n}] = tw;
+  *out = tw;
+  return cudaSuccess;
+}
+
+// ----------------------------------------------------------------------------- small public calls
+extern "C" const char* amm_status_string(amm_status_t s) {
+  switch (s) {
+    case AMM_OK: return "AMM_OK";
+    case AMM_ERR_INVALID_ARG: return "AMM_ERR_INVALID_ARG";
+    case AMM_ERR_UNSUPPORTED_SIZE: return "AMM_ERR_UNSUPPORTED_SIZE";
+    case AMM_ERR_OOM: return "AMM_ERR_OOM";
+    case AMM_ERR_CUDA: return "AMM_ERR_CUDA";
+    case AMM_ERR_TIMEOUT: return "AMM_ERR_TIMEOUT";
+    case AMM_ERR_STATE: return "AMM_ERR_STATE";
+    case AMM_ERR_NOT_IMPLEMENTED: return "AMM_ERR_NOT_IMPLEMENTED";
+  }
+  return "AMM_ERR_UNKNOWN";
+}
+
+extern "C" const char* amm_last_error(void) { return g_last_error; }
+extern "C" int32_t amm_version(void) { return AMM_VERSION; }
+
+extern "C" amm_status_t amm_opts_init(amm_opts_t* o) {
+  if (!o) return fail(AMM_ERR_INVALID_ARG, "amm_opts_init: opts is NULL");
+  memset(o, 0, sizeof(*o));
+  o->struct_size = sizeof(amm_opts_t);
+  o->role = AMM_LEFT;
+  o->compute = AMM_F32;
+  o->store_spectra = 1;
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_debug_fail_alloc_after(int32_t n) {
+  if (n < 0) return fail(AMM_ERR_INVALID_ARG, "amm_debug_fail_alloc_after: n < 0");
+  g_fail_after.store(n);
+  return AMM_OK;
+}
+
+// ----------------------------------------------------------------------------- handles
+static bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+void amm::Handle::release() {
+  for (void* p : owned) dev_free(p, stream);
+  owned.clear();
+}
+
+cudaError_t amm::Handle::alloc(void** p, size_t bytes) {
+  cudaError_t e = dev_alloc(p, bytes, stream);
+  if (e == cudaSuccess) owned.push_back(*p);
+  return e;
+}
+
+static amm_status_t decompose_circulant(Handle* h, const amm_opts_t* o) {
+  const int n = (int)h->rows;
+  if (!pow2(n) || n < 16 || n > 8192)
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: n=%d must be a power of two in [16, 8192]", n);
+  auto& c = h->cd;
+  const int J = cd_cols_per_cta(n);
+  c.nparts = n / J;
+  c.cap = (int)std::min<int64_t>(2 * h->k, n);
+  cudaError_t e = twiddles(n, h->stream, &c.tw);
+  if (e != cudaSuccess) return cuda_fail(e, "twiddle table");
+  const size_t kh = (size_t)n / 2 + 1;
+#define AL(ptr, bytes)                                                              \
+  do {                                                                              \
+    e = h->alloc((void**)&(ptr), (bytes));                                          \
+    if (e != cudaSuccess) return cuda_fail(e, "amm_decompose: device allocation");  \
+  } while (0)
+  AL(c.R, sizeof(float2) * kh * n);
+  AL(c.kpart, sizeof(float) * kh * c.nparts);
+  AL(c.so.keys, sizeof(double) * n);
+  AL(c.so.norms, sizeof(double) * 4);
+  AL(c.so.sel, sizeof(int32_t) * h->k);
+  AL(c.so.ulist, sizeof(int32_t) * c.cap);
+  AL(c.so.uw, sizeof(float) * c.cap);
+  AL(c.so.dlist, sizeof(int32_t) * c.cap);
+  AL(c.so.dv, sizeof(float) * c.cap);
+  AL(c.so.wfull, sizeof(float) * n);
+  AL(c.so.vfull, sizeof(float) * n);
+  AL(c.so.counts, sizeof(int32_t) * 2);
+  AL(c.Lw, sizeof(float2) * (size_t)c.cap * n);
+  AL(c.Ld, sizeof(float2) * (size_t)c.cap * n);
+  if (h->role == AMM_RIGHT) {
+    AL(c.resid, sizeof(float) * (size_t)n * n);
+    AL(c.imag, sizeof(float) * (size_t)n * n);
+  }
+  int32_t* forced = nullptr;
+  if (o && o->forced_selection) {
+    std::set<int32_t> seen;
+    for (int64_t i = 0; i < h->k; ++i) {
+      int32_t t = o->forced_selection[i];
+      if (t < 0 || t >= n || !seen.insert(t).second)
+        return fail(AMM_ERR_INVALID_ARG, "forced_selection[%lld]=%d out of range or repeated", (long long)i, t);
+    }
+    AL(forced, sizeof(int32_t) * h->k);
+    e = cudaMemcpyAsync(forced, o->forced_selection, sizeof(int32_t) * h->k, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host array may be freed after return
+    if (e != cudaSuccess) return cuda_fail(e, "forced selection upload");
+  }
+#undef AL
+  const bool bf16 = h->dtype == AMM_BF16;
+  if ((e = cd_spectrum(n, h->A, h->lda, bf16, c.tw, c.R, c.kpart, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "cd_spectrum launch");
+  if ((e = cd_select(n, (int)h->k, c.kpart, c.nparts, forced, c.so, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "cd_select launch");
+  if ((e = cd_eigen(n, c.R, c.tw, c.so.ulist, c.so.uw, c.so.counts, c.cap, 0, c.Lw, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "cd_eigen launch");
+  if ((e = cd_eigen(n, c.R, c.tw, c.so.dlist, c.so.dv, c.so.counts + 1, c.cap, 1, c.Ld, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "cd_eigen launch");
+  if (h->role == AMM_RIGHT) {
+    if ((e = cd_residual(n, c.R, c.tw, c.so.wfull, 0, nullptr, c.resid, h->stream)) != cudaSuccess)
+      return cuda_fail(e, "cd_residual launch");
+    if ((e = cd_residual(n, c.R, c.tw, c.so.vfull, 1, c.so.counts + 1, c.imag, h->stream)) != cudaSuccess)
+      return cuda_fail(e, "cd_residual launch");
+  }
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_decompose(const void* A, int64_t rows, int64_t cols, int64_t lda, amm_dtype_t dtype,
+                                      amm_method_t method, int64_t k, const amm_opts_t* opts, void* stream,
+                                      amm_handle_t* out) {
+  if (!out) return fail(AMM_ERR_INVALID_ARG, "amm_decompose: out is NULL");
+  if (!A) return fail(AMM_ERR_INVALID_ARG, "amm_decompose: A is NULL");
+  if (rows <= 0 || cols <= 0) return fail(AMM_ERR_INVALID_ARG, "amm_decompose: empty matrix %lldx%lld",
+                                          (long long)rows, (long long)cols);
+  if (lda < cols) return fail(AMM_ERR_INVALID_ARG, "amm_decompose: lda=%lld < cols=%lld", (long long)lda,
+                              (long long)cols);
+  if (dtype != AMM_F32 && dtype != AMM_BF16) return fail(AMM_ERR_INVALID_ARG, "amm_decompose: bad dtype %d", dtype);
+  if (opts && opts->struct_size != sizeof(amm_opts_t))
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose: opts->struct_size=%u, expected %zu", opts->struct_size,
+                sizeof(amm_opts_t));
+  const int role = opts ? opts->role : AMM_LEFT;
+  if (role != AMM_LEFT && role != AMM_RIGHT) return fail(AMM_ERR_INVALID_ARG, "amm_decompose: bad role %d", role);
+  const int64_t kmax = (method == AMM_SVD) ? std::min(rows, cols) : cols;
+  if (k < 1 || k > kmax)
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose: k=%lld outside [1, %lld]", (long long)k, (long long)kmax);
+  Handle* h = new (std::nothrow) Handle();
+  if (!h) return fail(AMM_ERR_OOM, "amm_decompose: host allocation");
+  h->A = A;
+  h->rows = rows;
+  h->cols = cols;
+  h->lda = lda;
+  h->dtype = dtype;
+  h->method = method;
+  h->role = role;
+  h->k = k;
+  h->stream = (cudaStream_t)stream;
+  amm_status_t s;
+  switch (method) {
+    case AMM_CIRCULANT:
+      if (rows != cols) {
+        s = fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: matrix must be square (got %lldx%lld)", (long long)rows,
+                 (long long)cols);
+        break;
+      }
+      s = decompose_circulant(h, opts);
+      break;
+    case AMM_SVD:
+      s = decompose_svd(h, opts);
+      break;
+    case AMM_SPARSE_FOURIER:
+    case AMM_SPARSE_CYCLE:
+      s = fail(AMM_ERR_NOT_IMPLEMENTED, "method %d is not built yet", (int)method);
+      break;
+    default:
+      s = fail(AMM_ERR_INVALID_ARG, "amm_decompose: bad method %d", (int)method);
+  }
+  if (s != AMM_OK) {
+    h->release();
+    delete h;
+    return s;
+  }
+  *out = h;
+  return AMM_OK;
+}
+
+static amm_status_t check_pair(Handle* a, Handle* b) {
+  if (!a || !b) return fail(AMM_ERR_INVALID_ARG, "NULL handle");
+  if (a->role != AMM_LEFT || b->role != AMM_RIGHT)
+    return fail(AMM_ERR_STATE, "hA must have role LEFT and hB role RIGHT (got %d, %d)", a->role, b->role);
+  if (a->cols != b->rows)
+    return fail(AMM_ERR_STATE, "inner dimensions differ: A is %lldx%lld, B is %lldx%lld", (long long)a->rows,
+                (long long)a->cols, (long long)b->rows, (long long)b->cols);
+  if (a->method != b->method) return fail(AMM_ERR_NOT_IMPLEMENTED, "mixed methods are not built yet");
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, float* C, int64_t ldc, void* stream) {
+  Handle* a = hA;
+  Handle* b = hB;
+  amm_status_t s = check_pair(a, b);
+  if (s != AMM_OK) return s;
+  if (!C) return fail(AMM_ERR_INVALID_ARG, "amm_approx_matmul: C is NULL");
+  if (ldc < b->cols) return fail(AMM_ERR_INVALID_ARG, "amm_approx_matmul: ldc=%lld < %lld", (long long)ldc,
+                                 (long long)b->cols);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (a->method == AMM_CIRCULANT) {
+    const int n = (int)a->rows;
+    if ((ldc & 1) != 0 || ((uintptr_t)C & 7) != 0)
+      return fail(AMM_ERR_INVALID_ARG, "circulant: C must be 8-byte aligned with an even ldc");
+    auto &ca = a->cd, &cb = b->cd;
+    // Re M = A~_w dB_w  +  Y V  +  A B~_w
+    if ((e = cd_apply(n, false, cb.resid, n, false, n, ca.tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr, nullptr, C,
+                      ldc, 0, st)) != cudaSuccess)
+      return cuda_fail(e, "cd_apply (column) launch");
+    if ((e = cd_apply(n, false, cb.imag, n, false, n, ca.tw, ca.so.dlist, ca.Ld, ca.so.counts + 1, ca.so.counts + 1,
+                      cb.so.counts + 1, C, ldc, 1, st)) != cudaSuccess)
+      return cuda_fail(e, "cd_apply (unpaired) launch");
+    if ((e = cd_apply(n, true, a->A, a->lda, a->dtype == AMM_BF16, n, ca.tw, cb.so.ulist, cb.Lw, cb.so.counts,
+                      nullptr, nullptr, C, ldc, 1, st)) != cudaSuccess)
+      return cuda_fail(e, "cd_apply (row) launch");
+    return AMM_OK;
+  }
+  if (a->method == AMM_SVD) return svd_matmul(a, b, C, ldc, st);
+  return fail(AMM_ERR_NOT_IMPLEMENTED, "method %d", a->method);
+}
+
+extern "C" amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const float* dC, int64_t lddc,
+                                                   float* dA, int64_t ldda, float* dB, int64_t lddb, void* stream) {
+  Handle* a = hA;
+  Handle* b = hB;
+  amm_status_t s = check_pair(a, b);
+  if (s != AMM_OK) return s;
+  if (!dC) return fail(AMM_ERR_INVALID_ARG, "backward: dC is NULL");
+  if (lddc < b->cols || (dA && ldda < a->cols) || (dB && lddb < b->cols))
+    return fail(AMM_ERR_INVALID_ARG, "backward: leading dimension too small");
+  if (a->method == AMM_SVD) return svd_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
+  return fail(AMM_ERR_NOT_IMPLEMENTED, "backward for method %d is not built yet", a->method);
+}
+
+extern "C" amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info) {
+  if (!h || !info) return fail(AMM_ERR_INVALID_ARG, "amm_handle_info: NULL argument");
+  memset(info, 0, sizeof(*info));
+  info->method = h->method;
+  info->role = h->role;
+  info->dtype = h->dtype;
+  info->rows = h->rows;
+  info->cols = h->cols;
+  info->k = h->k;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "amm_handle_info: stream");
+  if (h->method == AMM_CIRCULANT) {
+    double nr[3];
+    int32_t cnt[2];
+    if ((e = cudaMemcpy(nr, h->cd.so.norms, sizeof(nr), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(cnt, h->cd.so.counts, sizeof(cnt), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "amm_handle_info: copy");
+    info->fro2 = nr[0];
+    info->resid_fro2 = nr[1];
+    info->boundary_gap = nr[2];
+    info->n_union = cnt[0];
+    info->n_unpaired = (cnt[1] + 1) / 2;
+  } else if (h->method == AMM_SVD) {
+    return svd_info(h, info);
+  }
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t cap, int64_t* count) {
+  if (!h || !host_idx || !count) return fail(AMM_ERR_INVALID_ARG, "amm_handle_get_selection: NULL argument");
+  if (h->method != AMM_CIRCULANT) return fail(AMM_ERR_STATE, "handle has no component selection");
+  if (cap < h->k) return fail(AMM_ERR_INVALID_ARG, "cap=%lld < k=%lld", (long long)cap, (long long)h->k);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(host_idx, h->cd.so.sel, sizeof(int32_t) * h->k, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "amm_handle_get_selection");
+  *count = h->k;
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_handle_get_sketch(amm_handle_t h, float* host_phi, int64_t cap) {
+  if (!h || !host_phi) return fail(AMM_ERR_INVALID_ARG, "amm_handle_get_sketch: NULL argument");
+  if (h->method != AMM_SVD) return fail(AMM_ERR_STATE, "handle has no sketch");
+  return svd_get_sketch(h, host_phi, cap);
+}
+
+extern "C" amm_status_t amm_handle_destroy(amm_handle_t h) {
+  if (!h) return fail(AMM_ERR_INVALID_ARG, "amm_handle_destroy: NULL handle");
+  h->release();
+  delete h;
+  return AMM_OK;
+}

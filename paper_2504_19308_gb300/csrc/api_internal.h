@@ -1,0 +1,57 @@
+// Handle layout and helpers shared by the C ABI implementation files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/amm.h"
+#include "kernels.h"
+
+struct amm_handle {
+  // what was decomposed (borrowed pointer, see amm_decompose)
+  const void* A = nullptr;
+  int64_t rows = 0, cols = 0, lda = 0, k = 0;
+  int dtype = AMM_F32, method = AMM_CIRCULANT, role = AMM_LEFT, compute = AMM_F32;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> owned;  // device buffers released by amm_handle_destroy
+
+  struct Circulant {
+    const float2* tw = nullptr;   // twiddle table (process-wide cache, not owned)
+    float2* R = nullptr;          // (n/2+1) x n half spectrum
+    float* kpart = nullptr;       // per-CTA key partials
+    int nparts = 0, cap = 0;      // cap = min(2k, n) rows of Lw / Ld
+    amm::SelectOut so{};
+    float2* Lw = nullptr;         // w_t L_t for t in S u S-bar
+    float2* Ld = nullptr;         // -i v_t L_t for unpaired t
+    float* resid = nullptr;       // right operand: dB_w (n x n)
+    float* imag = nullptr;        // right operand: Im B~_S (n x n)
+  } cd;
+
+  struct Svd {
+    float* phi = nullptr;    // cols x k test matrix
+    float* Q = nullptr;      // rows x k, orthonormal columns spanning A phi
+    float* X = nullptr;      // k x cols, Q^T A
+    double* norms = nullptr; // ||A||_F^2, ||X||_F^2
+  } svd;
+
+  void release();
+  cudaError_t alloc(void** p, size_t bytes);
+};
+
+namespace amm {
+using Handle = ::amm_handle;
+
+amm_status_t fail(amm_status_t s, const char* fmt, ...);
+amm_status_t cuda_fail(cudaError_t e, const char* what);
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+cudaError_t twiddles(int n, cudaStream_t st, const float2** out);
+
+// svd.cu
+amm_status_t decompose_svd(Handle* h, const amm_opts_t* o);
+amm_status_t svd_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st);
+amm_status_t svd_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, float* dB,
+                          int64_t lddb, cudaStream_t st);
+amm_status_t svd_info(Handle* h, amm_info_t* info);
+amm_status_t svd_get_sketch(Handle* h, float* host_phi, int64_t cap);
+}  // namespace amm

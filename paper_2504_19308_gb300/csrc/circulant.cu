@@ -1,0 +1,489 @@
+// Circulant-decomposition kernels (Thm 2.1, Alg. 2, Alg. 3 of arXiv 2504.19308) for sm_103a.
+//
+// Notation (paper): cycles A = sum_j C^j Lambda_j with Lambda_j(l) = A((l+j) mod n, l);
+// spectrum r_{j,k} = (1/n) sum_l e^{-2 pi i k l/n} Lambda_j(l) stored as R[k][j] (row k = R_A[k]);
+// eigen-spectra L_t = F R_A[t]; omega = e^{+2 pi i/n}.
+//
+// Data layout in HBM (n = FFT length, row-major everywhere):
+//   R        (n/2+1) x n complex  -- half spectrum; R[n-k][j] = conj(R[k][j]) for real A
+//   kpart    (n/J) x (n/2+1) f32  -- per-CTA partial sums of |r_{j,k}|^2 (deterministic keys)
+//   Lw       cap x n complex      -- w_u L_{t_u} for the applied components t_u
+//   resid    n x n f32            -- dB_w (right operand only)
+//
+// Product used (reading R5, real output):  with S the selection, S-bar = {n-t}, weights
+// w_t = (1[t in S] + 1[n-t in S]) / 2 and v_t = (1[t in S] - 1[n-t in S]) / 2,
+//   Re(A~_S B + dA_S B~_S) = A~_w dB_w + Y V + A B~_w,
+//   A~_w = sum_t w_t R_t D^t (= Re A~_S),  Y = Im A~_S = sum_t (-i v_t) R_t D^t,  V = Im B~_S.
+// The three terms are spectral applies (k complex MACs per output spectrum entry):
+//   column apply  (Alg. 3 Step 5): F(sum_t c_t R_t D^t X)(p,:) = sum_t c_t L_t(p) (F X)((p-t) mod n, :)
+//   row apply     (X B~ by rows):  F_row(X sum_s c_s R_s D^s)(:,p) = sum_s c_s L_s((s-p) mod n) (F_row X)(:, (p-s) mod n)
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+#include "trace.h"
+
+namespace amm {
+
+template <typename T> AMM_DEV float ld_as_float(const T* p);
+template <> AMM_DEV float ld_as_float<float>(const float* p) { return __ldg(p); }
+template <> AMM_DEV float ld_as_float<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// ============================================================================ twiddles
+__global__ void twiddle_kernel(float2* tw, int n) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < n) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)n, &s, &c);
+    tw[m] = make_float2((float)c, (float)-s);  // e^{-2 pi i m/n}
+  }
+}
+
+// ============================================================================ K1: cycle spectrum
+// CTA b handles cycles j0 = b*J .. j0+J-1 (J = 2S), packed in pairs as complex signals.
+// Reads row r of A at columns (r - j) mod n for the J cycles (a contiguous, wrapping segment).
+template <int N, int S, int NT, typename T>
+__global__ void __launch_bounds__(NT) cd_spectrum_kernel(const T* __restrict__ A, int64_t lda,
+                                                         const float2* __restrict__ tw,
+                                                         float2* __restrict__ R, float* __restrict__ kpart) {
+  extern __shared__ float2 smem[];
+  constexpr int J = 2 * S;
+  constexpr int LD = fft_padded_len(N);
+  const int j0 = blockIdx.x * J;
+  float* fs = reinterpret_cast<float*>(smem);
+  // gather: element (r, q): column c = (r - j0 - (J-1) + q) mod n holds cycle m = J-1-q at l = c
+  for (int e = threadIdx.x; e < N * J; e += NT) {
+    const int r = e / J, q = e % J;
+    const int c = (r - j0 - (J - 1) + q) & (N - 1);
+    const int m = J - 1 - q;
+    const float v = ld_as_float<T>(A + (int64_t)r * lda + c);
+    fs[2 * ((m >> 1) * LD + fpad(c)) + (m & 1)] = v;
+  }
+  __syncthreads();
+  fft_smem<N, S, NT, false>(smem, tw);
+  // separate the two real spectra of each packed signal, scale by 1/n, store k = 0..n/2
+  constexpr float inv_n = 1.0f / (float)N;
+  constexpr int KH = N / 2 + 1;
+  constexpr int ITER = (KH * J + NT - 1) / NT;  // whole warps iterate together (shuffles below)
+  for (int it = 0; it < ITER; ++it) {
+    const int e = threadIdx.x + it * NT;
+    const bool valid = e < KH * J;
+    const int k = e / J, m = e % J;
+    float p = 0.f;
+    if (valid) {
+      const float2* z = smem + (m >> 1) * LD;
+      const float2 a = z[fpad(k)];
+      const float2 b = cconj(z[fpad((N - k) & (N - 1))]);
+      float2 x;
+      if ((m & 1) == 0) x = cscale(cadd(a, b), 0.5f * inv_n);  // (Z + conj Z(-k)) / 2
+      else { float2 d = csub(a, b); x = make_float2(0.5f * inv_n * d.y, -0.5f * inv_n * d.x); }  // (Z - conj Z(-k)) / 2i
+      R[(int64_t)k * N + j0 + m] = x;
+      p = x.x * x.x + x.y * x.y;
+    }
+    // J consecutive lanes share k (J divides 32): reduce to the first of them
+    constexpr unsigned MASK = (NT >= 32) ? 0xffffffffu : ((1u << NT) - 1u);  // CTAs of 16 threads at n = 16
+#pragma unroll
+    for (int o = J / 2; o > 0; o >>= 1) p += __shfl_xor_sync(MASK, p, o, J);
+    if (valid && m == 0) kpart[(int64_t)blockIdx.x * KH + k] = p;
+  }
+}
+
+// ============================================================================ K2: keys, top-k, weights
+// One CTA.  keys2[k] = sum over CTAs of kpart (fixed order, double); mirrored to n-k.
+// Sort (key desc, index asc) with a bitonic network in shared memory; first k = selection.
+__global__ void __launch_bounds__(1024) cd_select_kernel(const float* __restrict__ kpart, int nparts, int n,
+                                                         int k, const int32_t* __restrict__ forced,
+                                                         SelectOut out) {
+  extern __shared__ unsigned char sm[];
+  double* key = reinterpret_cast<double*>(sm);                  // n
+  int32_t* idx = reinterpret_cast<int32_t*>(key + n);           // n
+  unsigned char* in_s = reinterpret_cast<unsigned char*>(idx + n);  // n
+  __shared__ double red[32];
+  __shared__ int cnt_u, cnt_d;
+  const int kh = n / 2 + 1;
+  for (int t = threadIdx.x; t < kh; t += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nparts; ++c) s += (double)kpart[(int64_t)c * kh + t];
+    key[t] = s;
+    if (t > 0 && t < n - t) key[n - t] = s;
+  }
+  __syncthreads();
+  // ||A||_F^2 = n sum_k T[k]^2 (Parseval), deterministic block reduction
+  double part = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) part += key[t];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    out.norms[0] = s * (double)n;
+  }
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    out.keys[t] = sqrt(key[t]);
+    idx[t] = t;
+    in_s[t] = 0;
+  }
+  __syncthreads();
+  if (forced == nullptr) {
+    // bitonic sort, descending by key, ascending by index on ties
+    for (int size = 2; size <= n; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          int p = i ^ stride;
+          if (p > i) {
+            bool up = ((i & size) == 0);  // this half sorts "descending-first" order
+            double ki = key[i], kp = key[p];
+            int ii = idx[i], ip = idx[p];
+            bool i_first = (ki > kp) || (ki == kp && ii < ip);  // i should precede p
+            if (up ? !i_first : i_first) {
+              key[i] = kp; key[p] = ki; idx[i] = ip; idx[p] = ii;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int t = threadIdx.x; t < k; t += blockDim.x) out.sel[t] = idx[t];
+    if (threadIdx.x == 0) {
+      double a = sqrt(key[k - 1]);
+      out.norms[2] = (k < n) ? (a > 0 ? (a - sqrt(key[k])) / a : 0.0) : 1e300;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k; t += blockDim.x) in_s[idx[t]] = 1;
+  } else {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) {
+      out.sel[t] = forced[t];
+      in_s[forced[t]] = 1;
+    }
+    if (threadIdx.x == 0) out.norms[2] = -1.0;
+  }
+  __syncthreads();
+  // restore unsorted keys^2 for the residual norm
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    double tt = out.keys[t];
+    key[t] = tt * tt;
+  }
+  if (threadIdx.x == 0) { cnt_u = 0; cnt_d = 0; }
+  __syncthreads();
+  part = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) if (in_s[t]) part += key[t];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    out.norms[1] = out.norms[0] - s * (double)n;
+  }
+  // union S u S-bar with weights, and the unpaired set with v; compact in index order
+  // (single-thread compaction keeps the order deterministic; n <= 8192 so this is cheap)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nu = 0, nd = 0;
+    for (int t = 0; t < n; ++t) {
+      int a = in_s[t], b = in_s[(n - t) & (n - 1)];
+      out.wfull[t] = 0.5f * (float)(a + b);
+      out.vfull[t] = 0.5f * (float)(a - b);
+      if (a | b) { out.ulist[nu] = t; out.uw[nu] = 0.5f * (float)(a + b); ++nu; }
+      if (a != b) { out.dlist[nd] = t; out.dv[nd] = 0.5f * (float)(a - b); ++nd; }
+    }
+    out.counts[0] = nu;
+    out.counts[1] = nd;
+  }
+}
+
+// ============================================================================ K3: eigen-spectra
+// CTA u: L = F R_A[t_u] for t_u in the union (coefficient w) or in the unpaired set
+// (coefficient -i v).  Writes coef * L_t.
+template <int N, int NT>
+__global__ void __launch_bounds__(NT) cd_eigen_kernel(const float2* __restrict__ R, const float2* __restrict__ tw,
+                                                      const int32_t* __restrict__ list, const float* __restrict__ coef,
+                                                      const int32_t* __restrict__ count, int imag_coef,
+                                                      float2* __restrict__ L) {
+  extern __shared__ float2 smem[];
+  const int u = blockIdx.x;
+  if (u >= *count) return;
+  const int t = list[u];
+  const bool mir = t > N / 2;
+  const int tr = mir ? N - t : t;
+  for (int j = threadIdx.x; j < N; j += NT) {
+    float2 v = R[(int64_t)tr * N + j];
+    smem[fpad(j)] = mir ? cconj(v) : v;
+  }
+  __syncthreads();
+  fft_smem<N, 1, NT, false>(smem, tw);
+  const float c = coef[u];
+  for (int p = threadIdx.x; p < N; p += NT) {
+    float2 l = smem[fpad(p)];
+    L[(int64_t)u * N + p] = imag_coef ? make_float2(c * l.y, -c * l.x) /* -i c l */ : cscale(l, c);
+  }
+}
+
+// ============================================================================ K6: dense residual
+// For cycles j0..j0+J-1: Lambda_j(c) = sum_k g_k r_{j,k} omega^{k c}, with g_k = 1 - w_k (mode 0,
+// gfull = w, giving dB_w) or g_k = -i v_k (mode 1, gfull = v, giving V = Im B~_S).
+// Writes X((c+j) mod n, c).
+template <int N, int S, int NT>
+__global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restrict__ R, const float2* __restrict__ tw,
+                                                         const float* __restrict__ gfull, int mode,
+                                                         const int32_t* __restrict__ dcount,
+                                                         float* __restrict__ X) {
+  extern __shared__ float2 smem[];
+  if (mode == 1 && *dcount == 0) return;
+  constexpr int J = 2 * S;
+  constexpr int LD = fft_padded_len(N);
+  const int j0 = blockIdx.x * J;
+  // packed signal s: Z(k) = g_k (r_{j0+2s,k} + i r_{j0+2s+1,k}), k in [0, n)
+  for (int e = threadIdx.x; e < N * S; e += NT) {
+    const int k = e / S, s = e % S;
+    const bool mir = k > N / 2;
+    const int kr = mir ? N - k : k;
+    const float4 rr = *reinterpret_cast<const float4*>(R + (int64_t)kr * N + j0 + 2 * s);
+    float2 r1 = make_float2(rr.x, rr.y), r2 = make_float2(rr.z, rr.w);
+    if (mir) { r1 = cconj(r1); r2 = cconj(r2); }
+    float2 z = make_float2(r1.x - r2.y, r1.y + r2.x);
+    const float g = gfull[k];
+    z = (mode == 0) ? cscale(z, 1.f - g) : make_float2(g * z.y, -g * z.x);  // (1 - w_k) or -i v_k
+    smem[s * LD + fpad(k)] = z;
+  }
+  __syncthreads();
+  fft_smem<N, S, NT, true>(smem, tw);
+  const float* fs = reinterpret_cast<const float*>(smem);
+  for (int e = threadIdx.x; e < N * J; e += NT) {
+    const int r = e / J, q = e % J;
+    const int c = (r - j0 - (J - 1) + q) & (N - 1);
+    const int m = J - 1 - q;
+    X[(int64_t)r * N + c] = fs[2 * ((m >> 1) * LD + fpad(c)) + (m & 1)];
+  }
+}
+
+// ============================================================================ K5: spectral apply
+// COL: out(:, c0..c0+2S) (+)= (sum_u Lc_u-weighted) applied to X's columns (Alg. 3 Step 5).
+// ROW: out(r0..r0+2S, :) (+)= rows of X times (sum_s c_s R_s D^s).
+// Packed pairs of real columns/rows form complex signals; the output pair comes out of one
+// inverse FFT as (real, imag).  Coefficients Lc[u][p] = c_u L_{t_u}(p) (c conjugate-symmetric).
+template <int N, int S, int NT, bool ROW, typename T>
+__global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, int64_t ldx,
+                                                      const float2* __restrict__ tw,
+                                                      const int32_t* __restrict__ list, const float2* __restrict__ Lc,
+                                                      const int32_t* __restrict__ count,
+                                                      const int32_t* __restrict__ gate0,
+                                                      const int32_t* __restrict__ gate1, float* __restrict__ out,
+                                                      int64_t ldo, int accumulate) {
+  extern __shared__ float2 smem[];
+  if (gate0 != nullptr && (*gate0 == 0 || *gate1 == 0)) return;
+  constexpr int LD = fft_padded_len(N);
+  constexpr int PT = N / NT;  // output frequencies per thread
+  static_assert(N % NT == 0, "NT must divide N");
+  const int base = blockIdx.x * 2 * S;
+  if (!ROW) {
+    for (int e = threadIdx.x; e < N * S; e += NT) {
+      const int l = e / S, s = e % S;
+      const T* p = X + (int64_t)l * ldx + base + 2 * s;
+      smem[s * LD + fpad(l)] = make_float2(ld_as_float<T>(p), ld_as_float<T>(p + 1));
+    }
+  } else {
+    for (int e = threadIdx.x; e < N * S; e += NT) {
+      const int s = e / N, l = e % N;
+      const T* p = X + (int64_t)(base + 2 * s) * ldx + l;
+      smem[s * LD + fpad(l)] = make_float2(ld_as_float<T>(p), ld_as_float<T>(p + ldx));
+    }
+  }
+  __syncthreads();
+  fft_smem<N, S, NT, false>(smem, tw);
+  float2 acc[PT][S];
+#pragma unroll
+  for (int i = 0; i < PT; ++i)
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[i][s] = make_float2(0.f, 0.f);
+  const int nu = *count;
+  for (int u = 0; u < nu; ++u) {
+    const int t = __ldg(list + u);
+    const float2* lrow = Lc + (int64_t)u * N;
+#pragma unroll
+    for (int i = 0; i < PT; ++i) {
+      const int p = threadIdx.x + i * NT;
+      const float2 l = __ldg(lrow + (ROW ? ((t - p) & (N - 1)) : p));
+      const int q = fpad((p - t) & (N - 1));
+#pragma unroll
+      for (int s = 0; s < S; ++s) cmac(acc[i][s], l, smem[s * LD + q]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PT; ++i)
+#pragma unroll
+    for (int s = 0; s < S; ++s) smem[s * LD + fpad(threadIdx.x + i * NT)] = acc[i][s];
+  __syncthreads();
+  fft_smem<N, S, NT, true>(smem, tw);
+  constexpr float inv_n = 1.0f / (float)N;
+  if (!ROW) {
+    for (int e = threadIdx.x; e < N * S; e += NT) {
+      const int l = e / S, s = e % S;
+      float2 z = cscale(smem[s * LD + fpad(l)], inv_n);
+      float2* o = reinterpret_cast<float2*>(out + (int64_t)l * ldo + base + 2 * s);
+      if (accumulate) { float2 old = *o; z.x += old.x; z.y += old.y; }
+      *o = z;
+    }
+  } else {
+    for (int e = threadIdx.x; e < N * S; e += NT) {
+      const int s = e / N, l = e % N;
+      float2 z = cscale(smem[s * LD + fpad(l)], inv_n);
+      float* o0 = out + (int64_t)(base + 2 * s) * ldo + l;
+      float* o1 = o0 + ldo;
+      if (accumulate) { z.x += *o0; z.y += *o1; }
+      *o0 = z.x;
+      *o1 = z.y;
+    }
+  }
+}
+
+// ============================================================================ host launchers
+template <int N> struct CdCfg {
+  static constexpr int S = (N >= 8192) ? 2 : 4;       // packed signals per CTA
+  static constexpr int NT = (N >= 512) ? 512 : N;     // threads per CTA
+  static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
+  static constexpr int NT1 = (N >= 1024) ? 256 : (N >= 64 ? 64 : N);  // eigen-spectrum kernel
+};
+
+template <int N> static cudaError_t set_smem_attrs() {
+  using C = CdCfg<N>;
+  cudaError_t e = cudaSuccess;
+  auto s = [&](const void* f, size_t b) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+  };
+  s((const void*)cd_spectrum_kernel<N, C::S, C::NT, float>, C::SMEM);
+  s((const void*)cd_spectrum_kernel<N, C::S, C::NT, __nv_bfloat16>, C::SMEM);
+  s((const void*)cd_residual_kernel<N, C::S, C::NT>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, false, float>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, true, float>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, true, __nv_bfloat16>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, false, __nv_bfloat16>, C::SMEM);
+  s((const void*)cd_eigen_kernel<N, CdCfg<N>::NT1>, sizeof(float2) * fft_padded_len(N));
+  return e;
+}
+
+template <int N> struct CdOps {
+  using C = CdCfg<N>;
+  static cudaError_t spectrum(const void* A, int64_t lda, bool bf16, const float2* tw, float2* R, float* kpart,
+                              cudaStream_t st) {
+    static cudaError_t attr = set_smem_attrs<N>();
+    if (attr != cudaSuccess) return attr;
+    dim3 grid(N / (2 * C::S));
+    if (bf16)
+      cd_spectrum_kernel<N, C::S, C::NT, __nv_bfloat16><<<grid, C::NT, C::SMEM, st>>>(
+          (const __nv_bfloat16*)A, lda, tw, R, kpart);
+    else
+      cd_spectrum_kernel<N, C::S, C::NT, float><<<grid, C::NT, C::SMEM, st>>>((const float*)A, lda, tw, R, kpart);
+    return cudaGetLastError();
+  }
+  static cudaError_t eigen(const float2* R, const float2* tw, const int32_t* list, const float* coef,
+                           const int32_t* count, int cap, int imag_coef, float2* L, cudaStream_t st) {
+    static cudaError_t attr = set_smem_attrs<N>();
+    if (attr != cudaSuccess) return attr;
+    constexpr int NT1 = C::NT1;
+    size_t sm = sizeof(float2) * fft_padded_len(N);
+    if (cap <= 0) return cudaSuccess;
+    cd_eigen_kernel<N, NT1><<<cap, NT1, sm, st>>>(R, tw, list, coef, count, imag_coef, L);
+    return cudaGetLastError();
+  }
+  static cudaError_t residual(const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
+                              float* X, cudaStream_t st) {
+    static cudaError_t attr = set_smem_attrs<N>();
+    if (attr != cudaSuccess) return attr;
+    cd_residual_kernel<N, C::S, C::NT><<<N / (2 * C::S), C::NT, C::SMEM, st>>>(R, tw, g, mode, dcount, X);
+    return cudaGetLastError();
+  }
+  static cudaError_t apply(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
+                           const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
+                           const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st) {
+    static cudaError_t attr = set_smem_attrs<N>();
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((unsigned)(nvec / (2 * C::S)));
+    if (row) {
+      if (bf16)
+        cd_apply_kernel<N, C::S, C::NT, true, __nv_bfloat16><<<grid, C::NT, C::SMEM, st>>>(
+            (const __nv_bfloat16*)X, ldx, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate);
+      else
+        cd_apply_kernel<N, C::S, C::NT, true, float><<<grid, C::NT, C::SMEM, st>>>(
+            (const float*)X, ldx, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate);
+    } else {
+      if (bf16)
+        cd_apply_kernel<N, C::S, C::NT, false, __nv_bfloat16><<<grid, C::NT, C::SMEM, st>>>(
+            (const __nv_bfloat16*)X, ldx, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate);
+      else
+        cd_apply_kernel<N, C::S, C::NT, false, float><<<grid, C::NT, C::SMEM, st>>>(
+            (const float*)X, ldx, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate);
+    }
+    return cudaGetLastError();
+  }
+};
+
+#define AMM_DISPATCH_N(n, EXPR)                         \
+  switch (n) {                                          \
+    case 16: { constexpr int NN = 16; EXPR; }           \
+    case 32: { constexpr int NN = 32; EXPR; }           \
+    case 64: { constexpr int NN = 64; EXPR; }           \
+    case 128: { constexpr int NN = 128; EXPR; }         \
+    case 256: { constexpr int NN = 256; EXPR; }         \
+    case 512: { constexpr int NN = 512; EXPR; }         \
+    case 1024: { constexpr int NN = 1024; EXPR; }       \
+    case 2048: { constexpr int NN = 2048; EXPR; }       \
+    case 4096: { constexpr int NN = 4096; EXPR; }       \
+    case 8192: { constexpr int NN = 8192; EXPR; }       \
+    default: return cudaErrorInvalidValue;              \
+  }
+
+int cd_cols_per_cta(int n) { return n >= 8192 ? 4 : 8; }
+
+cudaError_t cd_twiddles(float2* tw, int n, cudaStream_t st) {
+  AMM_TRACE("twiddle", st);
+  twiddle_kernel<<<(n + 255) / 256, 256, 0, st>>>(tw, n);
+  return cudaGetLastError();
+}
+
+cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const float2* tw, float2* R, float* kpart,
+                        cudaStream_t st) {
+  AMM_TRACE("cd_spectrum", st);
+  AMM_DISPATCH_N(n, return CdOps<NN>::spectrum(A, lda, bf16, tw, R, kpart, st));
+}
+
+cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_t* forced, const SelectOut& o,
+                      cudaStream_t st) {
+  AMM_TRACE("cd_select", st);
+  size_t sm = (size_t)n * (sizeof(double) + sizeof(int32_t) + 1);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)cd_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)8192 * (sizeof(double) + sizeof(int32_t) + 1)));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  cd_select_kernel<<<1, 1024, sm, st>>>(kpart, nparts, n, k, forced, o);
+  return cudaGetLastError();
+}
+
+cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* list, const float* coef,
+                     const int32_t* count, int cap, int imag_coef, float2* L, cudaStream_t st) {
+  AMM_TRACE("cd_eigen", st);
+  AMM_DISPATCH_N(n, return CdOps<NN>::eigen(R, tw, list, coef, count, cap, imag_coef, L, st));
+}
+
+cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
+                        float* X, cudaStream_t st) {
+  AMM_TRACE("cd_residual", st);
+  AMM_DISPATCH_N(n, return CdOps<NN>::residual(R, tw, g, mode, dcount, X, st));
+}
+
+cudaError_t cd_apply(int n, bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
+                     const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
+                     const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st) {
+  AMM_TRACE(row ? "cd_apply_row" : "cd_apply_col", st);
+  AMM_DISPATCH_N(n, return CdOps<NN>::apply(row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out, ldo,
+                                            accumulate, st));
+}
+
+}  // namespace amm

@@ -1,0 +1,30 @@
+// Shared device helpers for libamm (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define AMM_DEV __device__ __forceinline__
+
+// ---------------------------------------------------------------- complex float2 arithmetic
+AMM_DEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+AMM_DEV float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+AMM_DEV float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+AMM_DEV float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+AMM_DEV float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// acc += a * b
+AMM_DEV void cmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+// multiply by -i (s=-1) or +i (s=+1)
+AMM_DEV float2 cmul_i(float2 a, int s) { return s > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x); }
+
+// Padded shared-memory index for FFT buffers: one float2 of padding every 16 elements.
+// Makes the stride-R stores of the first radix-R Stockham pass bank-conflict free.
+AMM_DEV int fpad(int e) { return e + (e >> 4); }
+__host__ __device__ constexpr int fft_padded_len(int n) { return n + n / 16; }
+
+constexpr int ilog2_c(int n) { return n <= 1 ? 0 : 1 + ilog2_c(n / 2); }

@@ -1,0 +1,68 @@
+"""The C ABI on the CPU: the library loads without a GPU and exports every declared symbol;
+argument errors are reported before anything is launched."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "amm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(amm_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_19308_gb300 import build as b
+    b.build()
+    import paper_2504_19308_gb300.amm as amm
+    return amm.load_library()
+
+
+def test_header_declares_the_boundary():
+    syms = _declared_symbols()
+    for s in ["amm_decompose", "amm_approx_matmul", "amm_approx_matmul_backward", "amm_handle_destroy",
+              "amm_handle_info", "amm_handle_get_selection", "amm_status_string"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import paper_2504_19308_gb300.amm as amm
+    for s in _declared_symbols():
+        assert hasattr(lib, s), s
+        assert s in amm.SIGNATURES, "binding lacks " + s
+
+
+def test_status_strings(lib):
+    assert lib.amm_status_string(0) == b"AMM_OK"
+    assert lib.amm_status_string(5) == b"AMM_ERR_TIMEOUT"
+    assert lib.amm_version() == 1
+
+
+def test_argument_errors_without_gpu(lib):
+    import paper_2504_19308_gb300.amm as amm
+    opts = amm.Opts()
+    assert lib.amm_opts_init(ctypes.byref(opts)) == 0
+    out = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails validation first
+    # NULL A
+    assert lib.amm_decompose(None, 64, 64, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
+    # k = 0
+    assert lib.amm_decompose(fake, 64, 64, 64, 0, 1, 0, ctypes.byref(opts), None, ctypes.byref(out)) == 1
+    # lda < cols
+    assert lib.amm_decompose(fake, 64, 64, 32, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
+    # circulant needs a square power-of-two
+    assert lib.amm_decompose(fake, 64, 32, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
+    assert lib.amm_decompose(fake, 48, 48, 48, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
+    # bad struct size
+    opts.struct_size = 3
+    assert lib.amm_decompose(fake, 64, 64, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
+    assert out.value in (0, None)
+    assert b"struct_size" in lib.amm_last_error()
+    # NULL handles
+    assert lib.amm_approx_matmul(None, None, fake, 64, None) == 1
+    assert lib.amm_handle_destroy(None) == 1
