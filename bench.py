@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput of the first-order approximate product on GB300 (one JSON line on rank 0).
+
+Workload (n = 4096, FP32, synthetic): A, B = Q1 diag(i^-1.5) Q2^T + N(0, 1e-4) noise (Haar Q from
+QR of N(0,1), i = 1..n).  One step = the whole hot path over that pair for every product of
+the sweep: decompose A and B, evaluate Re(A~ B + dA B~), and run the backward where the method
+has one.  The metric is effective throughput: the FLOPs of the exact products the step stands
+for (2 n^3 per forward, 4 n^3 per backward) divided by the step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amm|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+Multi-GPU: replicas (each rank runs the same independent step; no collective in the data
+path); value = work of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "effective 2n³/t TFLOP/s at ≤1% rel. error; BF16/batched vs plain FP32 fwd+bwd"
+UNIT = "TFLOP/s"
+N = 4096
+# (method, k, backward) -- the sweep of the n = 4096 workload
+PRODUCTS = [("circulant", 16, False), ("circulant", 64, False), ("circulant", 256, False),
+            ("svd", 32, True), ("svd", 128, True)]
+FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x 2 (FMA) x max SM clock
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def work_flops(products):
+    fl = 0.0
+    for _, _, bwd in products:
+        fl += 2.0 * N ** 3 + (4.0 * N ** 3 if bwd else 0.0)
+    return fl
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs():
+    a, b = synth.powerlaw_pair(N, seed=0)
+    phis = {k: (synth.sketch(N, k, 0, 0).astype(np.float32), synth.sketch(N, k, 0, 1).astype(np.float32))
+            for _, k, _ in PRODUCTS}
+    g = synth.upstream_grad(N, N, seed=0).astype(np.float32)
+    return a.astype(np.float32), b.astype(np.float32), phis, g
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_amm(args, rank, world, local_rank):
+    import torch
+    import paper_2504_19308_gb300 as amm
+    from paper_2504_19308_gb300.amm import trace_collect, trace_enable
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    amm.load_library()
+    a, b, phis, g = make_inputs()
+    A = torch.from_numpy(a).to(dev)
+    B = torch.from_numpy(b).to(dev)
+    G = torch.from_numpy(g).to(dev)
+    PH = {k: (torch.from_numpy(pa).to(dev), torch.from_numpy(pb).to(dev)) for k, (pa, pb) in phis.items()}
+    C = torch.empty((N, N), dtype=torch.float32, device=dev)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def step(A, B, outs=None):
+        for i, (method, k, bwd) in enumerate(PRODUCTS):
+            sa, sb = PH[k] if method == "svd" else (None, None)
+            hA = amm.decompose(A, method, k, "left", sketch=sa)
+            hB = amm.decompose(B, method, k, "right", sketch=sb)
+            out = C if outs is None else outs[i]
+            amm.approx_matmul(hA, hB, out=out)
+            if bwd:
+                amm.approx_matmul_backward(hA, hB, G)
+            hA.close()
+            hB.close()
+
+    # accuracy of every product of the step against the exact FP64 product (outside timing)
+    exact = (A.double() @ B.double())
+    errs = {}
+    for method, k, _ in PRODUCTS:
+        sa, sb = PH[k] if method == "svd" else (None, None)
+        hA = amm.decompose(A, method, k, "left", sketch=sa)
+        hB = amm.decompose(B, method, k, "right", sketch=sb)
+        Ck = amm.approx_matmul(hA, hB)
+        errs["%s_k%d" % (method, k)] = float(torch.linalg.norm(Ck.double() - exact) / torch.linalg.norm(exact))
+    del exact
+
+    for _ in range(args.warmup):
+        step(A, B)
+    torch.cuda.synchronize()
+    trace_collect()  # drop anything recorded so far
+
+    # ---- timed region (device-resident inputs)
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    trace_enable(True)
+    with ClockSampler(local_rank) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record()
+        for _ in range(args.steps):
+            step(A, B)
+        ev1.record()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+    trace_enable(False)
+    if dist:
+        tdist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    kernels, launches = trace_collect()
+    clocks = clk.summary()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the public API with host buffers (H2D inputs, D2H results)
+    a_h = torch.from_numpy(a).pin_memory()
+    b_h = torch.from_numpy(b).pin_memory()
+    outs = [torch.empty((N, N), dtype=torch.float32, device=dev) for _ in PRODUCTS]
+    outs_h = [torch.empty((N, N), dtype=torch.float32).pin_memory() for _ in PRODUCTS]
+    A2 = torch.empty_like(A)
+    B2 = torch.empty_like(B)
+
+    def e2e_step():
+        A2.copy_(a_h, non_blocking=True)
+        B2.copy_(b_h, non_blocking=True)
+        step(A2, B2, outs)
+        for o, oh in zip(outs, outs_h):
+            oh.copy_(o, non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    fl = work_flops(PRODUCTS)
+    value = world * fl * args.steps / (ms * 1e-3) / 1e12
+    e2e_value = world * fl * args.steps / (e2e_ms * 1e-3) / 1e12
+    roof = roofline(kernels, clocks)
+    return {
+        "value": value, "ms_per_step": ms / args.steps, "errs": errs, "kernels": kernels,
+        "launches": launches, "clocks": clocks, "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N * N * 4,
+                "d2h_bytes_per_step": len(PRODUCTS) * N * N * 4, "ms_per_step": e2e_ms / args.steps},
+    }
+
+
+# dram bytes per launch from the ncu capture summarised in profiles/ (None = not captured for
+# the kernel as it stands)
+NCU_TRAFFIC = {}
+
+
+def roofline(kernels, clocks):
+    """Roofline of the kernel that takes most of the timed region."""
+    pk, src = peaks()
+    name, (launches, ms, flops, bytes_) = max(kernels.items(), key=lambda kv: kv[1][1])
+    hbm_kernels = {"cd_spectrum", "cd_residual"}
+    if name in hbm_kernels:
+        achieved = bytes_ / (ms * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": NCU_TRAFFIC.get(name),
+                "launches": launches, "avg_launch_ms": ms / launches, "peak_source": src}
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK, "unit": "TFLOP/s",
+            "frac": achieved / FP32_ALU_PEAK, "traffic": NCU_TRAFFIC.get(name), "launches": launches,
+            "avg_launch_ms": ms / launches,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+            "algorithmic_bytes_per_launch": bytes_ / launches}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(seconds_hint: float = 20.0):
+    """Time the FP64 oracle on one forward circulant product (k = 16) of the same n = 4096 pair."""
+    import oracle
+    a, b, _, _ = make_inputs()
+    a64, b64 = a.astype(np.float64), b.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.cd_matmul(a64, b64, 16)
+    dt = time.perf_counter() - t0
+    return dt, 2.0 * N ** 3 / dt / 1e12
+
+
+def cpu_cores():
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    import oracle
+    a, b, _, _ = make_inputs()
+    a64, b64 = a.astype(np.float64), b.astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.cd_matmul(a64, b64, 16)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.cd_matmul(a64, b64, 16)
+    dt = time.perf_counter() - t0
+    value = 2.0 * N ** 3 * args.steps / dt / 1e12
+    sample = "one forward circulant product (k=16) of the n=4096 pair per step, FP64 oracle (numpy)"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def config_block():
+    return {"workload": "powerlaw n=4096 FP32: A,B = Q1 diag(i^-1.5) Q2^T + N(0,1e-4); sweep circulant "
+                        "k=16/64/256 fwd, rSVD k=32/128 fwd+bwd",
+            "n": N, "products": ["%s k=%d %s" % (m, k, "fwd+bwd" if b else "fwd") for m, k, b in PRODUCTS],
+            "l2": "no flush: each step touches ~2 GB (inputs, spectra, residuals, GEMM panels) > 129 MB L2",
+            "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="amm", choices=["amm", "reference"])
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = run_amm(args, rank, world, local_rank)
+    if rank == 0:
+        cpu = None
+        if world == 1:
+            dt, val = oracle_sample()
+            cpu = {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                   "sample": "one forward circulant product (k=16) of the same n=4096 pair, FP64 oracle, "
+                             "%.1f s" % dt}
+        cfg = config_block()
+        cfg["approx_rel_err_vs_exact"] = r["errs"]
+        cfg["kernels_ms"] = {k: round(v[1] / args.steps, 4) for k, v in r["kernels"].items()}
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+                "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
+                "clocks": r["clocks"]}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

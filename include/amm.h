@@ -155,8 +155,10 @@ amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info);
 
 /*
  * Copy the selection to host memory: circulant component indices / cycle indices in
- * selection order (k entries).  `cap` is the capacity of host_idx in elements; *count
- * receives k.  Synchronises the handle's stream.
+ * selection order (k entries); for AMM_SPARSE_FOURIER the kept frequencies of every row
+ * (left operand, rows x k) or column (right operand, cols x k), ascending within each.
+ * `cap` is the capacity of host_idx in elements; *count receives the number written.
+ * Synchronises the handle's stream.
  */
 amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t cap,
                                       int64_t* count);

@@ -123,11 +123,17 @@ class Handle:
         return {f: getattr(info, f) for f, _ in Info._fields_}
 
     def selection(self) -> np.ndarray:
-        buf = (ctypes.c_int32 * self.k)()
+        """Selected components (k,), or per-row / per-column kept frequencies (rows, k) for 'fourier'."""
+        rows = 1
+        if self.method == "fourier":
+            rows = self.shape[0] if self.role == "left" else self.shape[1]
+        cap = self.k * rows
+        buf = (ctypes.c_int32 * cap)()
         cnt = ctypes.c_int64(0)
-        _check(load_library().amm_handle_get_selection(self.ptr, buf, self.k, ctypes.byref(cnt)),
+        _check(load_library().amm_handle_get_selection(self.ptr, buf, cap, ctypes.byref(cnt)),
                "amm_handle_get_selection")
-        return np.frombuffer(buf, dtype=np.int32, count=cnt.value).copy()
+        out = np.frombuffer(buf, dtype=np.int32, count=cnt.value).copy()
+        return out.reshape(rows, self.k) if self.method == "fourier" else out
 
     def sketch(self) -> np.ndarray:
         n = self.source.shape[1]

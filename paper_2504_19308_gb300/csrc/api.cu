@@ -199,6 +199,93 @@ static amm_status_t decompose_circulant(Handle* h, const amm_opts_t* o) {
   return AMM_OK;
 }
 
+static amm_status_t decompose_cycle(Handle* h, const amm_opts_t* o) {
+  const int n = (int)h->rows;
+  if (!pow2(n) || n < 16 || n > 8192)
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "cycle: n=%d must be a power of two in [16, 8192]", n);
+  if (h->dtype != AMM_F32) return fail(AMM_ERR_NOT_IMPLEMENTED, "cycle: BF16 inputs are not built yet");
+  auto& c = h->cy;
+  const int rp = cyc_rows_per_part(n);
+  c.nparts = (n + rp - 1) / rp;
+  const int cap = (int)std::min<int64_t>(2 * h->k, n);
+  cudaError_t e;
+#define AL(ptr, bytes)                                                              \
+  do {                                                                              \
+    e = h->alloc((void**)&(ptr), (bytes));                                          \
+    if (e != cudaSuccess) return cuda_fail(e, "amm_decompose: device allocation");  \
+  } while (0)
+  AL(c.kpart, sizeof(float) * (size_t)c.nparts * n);
+  AL(c.so.keys, sizeof(double) * n);
+  AL(c.so.norms, sizeof(double) * 4);
+  AL(c.so.sel, sizeof(int32_t) * h->k);
+  AL(c.so.ulist, sizeof(int32_t) * cap);
+  AL(c.so.uw, sizeof(float) * cap);
+  AL(c.so.dlist, sizeof(int32_t) * cap);
+  AL(c.so.dv, sizeof(float) * cap);
+  AL(c.so.wfull, sizeof(float) * n);
+  AL(c.so.vfull, sizeof(float) * n);
+  AL(c.so.counts, sizeof(int32_t) * 2);
+  AL(c.cyc, sizeof(float) * (size_t)h->k * n);
+  AL(c.insel, (size_t)n);
+  int32_t* forced = nullptr;
+  if (o && o->forced_selection) {
+    std::set<int32_t> seen;
+    for (int64_t i = 0; i < h->k; ++i) {
+      int32_t t = o->forced_selection[i];
+      if (t < 0 || t >= n || !seen.insert(t).second)
+        return fail(AMM_ERR_INVALID_ARG, "forced_selection[%lld]=%d out of range or repeated", (long long)i, t);
+    }
+    AL(forced, sizeof(int32_t) * h->k);
+    e = cudaMemcpyAsync(forced, o->forced_selection, sizeof(int32_t) * h->k, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "forced selection upload");
+  }
+#undef AL
+  const float* A = (const float*)h->A;
+  if ((e = cyc_keys(n, A, h->lda, c.kpart, h->stream)) != cudaSuccess) return cuda_fail(e, "cyc_keys launch");
+  if ((e = cd_select(n, (int)h->k, c.kpart, c.nparts, forced, c.so, h->stream, false)) != cudaSuccess)
+    return cuda_fail(e, "cycle select launch");
+  if ((e = cyc_gather(n, (int)h->k, A, h->lda, c.so.sel, c.cyc, c.insel, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "cyc_gather launch");
+  return AMM_OK;
+}
+
+static amm_status_t decompose_fourier(Handle* h, const amm_opts_t* o) {
+  auto& f = h->ft;
+  const bool left = h->role == AMM_LEFT;
+  f.n = (int)(left ? h->cols : h->rows);
+  f.nvec = (int)(left ? h->rows : h->cols);
+  if (!pow2(f.n) || f.n < 16 || f.n > 8192)
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "fourier: inner dimension %d must be a power of two in [16, 8192]", f.n);
+  if (h->dtype != AMM_F32) return fail(AMM_ERR_NOT_IMPLEMENTED, "fourier: BF16 inputs are not built yet");
+  if (o && o->forced_selection) return fail(AMM_ERR_NOT_IMPLEMENTED, "fourier: forced selection is not built");
+  if (h->k > f.n) return fail(AMM_ERR_INVALID_ARG, "fourier: k=%lld > n=%d", (long long)h->k, f.n);
+  cudaError_t e = twiddles(f.n, h->stream, &f.tw);
+  if (e != cudaSuccess) return cuda_fail(e, "twiddle table");
+  const size_t kh = (size_t)f.n / 2 + 1;
+  f.mask_words = (f.nvec + 31) / 32;
+#define AL(ptr, bytes)                                                              \
+  do {                                                                              \
+    e = h->alloc((void**)&(ptr), (bytes));                                          \
+    if (e != cudaSuccess) return cuda_fail(e, "amm_decompose: device allocation");  \
+  } while (0)
+  AL(f.T, sizeof(float2) * kh * f.nvec);
+  AL(f.mag, sizeof(float) * kh * f.nvec);
+  AL(f.sel, sizeof(int32_t) * (size_t)h->k * f.nvec);
+  if (left) {
+    AL(f.TT, sizeof(float2) * kh * f.nvec);
+    AL(f.maskT, sizeof(uint32_t) * (size_t)f.n * f.mask_words);
+  }
+#undef AL
+  if ((e = ft_transform(f.n, left, (const float*)h->A, h->lda, f.nvec, f.tw, f.T, f.TT, f.mag, h->stream)) !=
+      cudaSuccess)
+    return cuda_fail(e, "ft_transform launch");
+  if ((e = ft_select(f.n, (int)h->k, f.nvec, f.mag, f.sel, left ? f.maskT : nullptr, f.mask_words, h->stream)) !=
+      cudaSuccess)
+    return cuda_fail(e, "ft_select launch");
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_decompose(const void* A, int64_t rows, int64_t cols, int64_t lda, amm_dtype_t dtype,
                                       amm_method_t method, int64_t k, const amm_opts_t* opts, void* stream,
                                       amm_handle_t* out) {
@@ -241,9 +328,16 @@ extern "C" amm_status_t amm_decompose(const void* A, int64_t rows, int64_t cols,
     case AMM_SVD:
       s = decompose_svd(h, opts);
       break;
-    case AMM_SPARSE_FOURIER:
     case AMM_SPARSE_CYCLE:
-      s = fail(AMM_ERR_NOT_IMPLEMENTED, "method %d is not built yet", (int)method);
+      if (rows != cols) {
+        s = fail(AMM_ERR_UNSUPPORTED_SIZE, "cycle: matrix must be square (got %lldx%lld)", (long long)rows,
+                 (long long)cols);
+        break;
+      }
+      s = decompose_cycle(h, opts);
+      break;
+    case AMM_SPARSE_FOURIER:
+      s = decompose_fourier(h, opts);
       break;
     default:
       s = fail(AMM_ERR_INVALID_ARG, "amm_decompose: bad method %d", (int)method);
@@ -296,6 +390,19 @@ extern "C" amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, floa
     return AMM_OK;
   }
   if (a->method == AMM_SVD) return svd_matmul(a, b, C, ldc, st);
+  if (a->method == AMM_SPARSE_FOURIER) {
+    e = ft_product(a->ft.n, (int)a->rows, (int)b->cols, (int)a->k, (int)b->k, a->ft.T, a->ft.TT, a->ft.sel,
+                   a->ft.maskT, a->ft.mask_words, b->ft.T, b->ft.sel, C, ldc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fourier product launch");
+    return AMM_OK;
+  }
+  if (a->method == AMM_SPARSE_CYCLE) {
+    const int n = (int)a->rows;
+    e = cyc_apply(n, (const float*)a->A, a->lda, (const float*)b->A, b->lda, a->cy.so.sel, (int)a->k, a->cy.cyc,
+                  a->cy.insel, b->cy.so.sel, (int)b->k, b->cy.cyc, C, ldc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cycle product launch");
+    return AMM_OK;
+  }
   return fail(AMM_ERR_NOT_IMPLEMENTED, "method %d", a->method);
 }
 
@@ -323,17 +430,20 @@ extern "C" amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info) {
   info->k = h->k;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "amm_handle_info: stream");
-  if (h->method == AMM_CIRCULANT) {
+  if (h->method == AMM_CIRCULANT || h->method == AMM_SPARSE_CYCLE) {
+    const SelectOut& so = h->method == AMM_CIRCULANT ? h->cd.so : h->cy.so;
     double nr[3];
     int32_t cnt[2];
-    if ((e = cudaMemcpy(nr, h->cd.so.norms, sizeof(nr), cudaMemcpyDeviceToHost)) != cudaSuccess ||
-        (e = cudaMemcpy(cnt, h->cd.so.counts, sizeof(cnt), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpy(nr, so.norms, sizeof(nr), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(cnt, so.counts, sizeof(cnt), cudaMemcpyDeviceToHost)) != cudaSuccess)
       return cuda_fail(e, "amm_handle_info: copy");
     info->fro2 = nr[0];
     info->resid_fro2 = nr[1];
     info->boundary_gap = nr[2];
-    info->n_union = cnt[0];
-    info->n_unpaired = (cnt[1] + 1) / 2;
+    if (h->method == AMM_CIRCULANT) {
+      info->n_union = cnt[0];
+      info->n_unpaired = (cnt[1] + 1) / 2;
+    }
   } else if (h->method == AMM_SVD) {
     return svd_info(h, info);
   }
@@ -342,10 +452,21 @@ extern "C" amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info) {
 
 extern "C" amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t cap, int64_t* count) {
   if (!h || !host_idx || !count) return fail(AMM_ERR_INVALID_ARG, "amm_handle_get_selection: NULL argument");
-  if (h->method != AMM_CIRCULANT) return fail(AMM_ERR_STATE, "handle has no component selection");
+  if (h->method == AMM_SPARSE_FOURIER) {
+    const int64_t cnt = h->k * h->ft.nvec;
+    if (cap < cnt) return fail(AMM_ERR_INVALID_ARG, "cap=%lld < rows*k=%lld", (long long)cap, (long long)cnt);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(host_idx, h->ft.sel, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "amm_handle_get_selection");
+    *count = cnt;
+    return AMM_OK;
+  }
+  if (h->method != AMM_CIRCULANT && h->method != AMM_SPARSE_CYCLE)
+    return fail(AMM_ERR_STATE, "handle has no component selection");
   if (cap < h->k) return fail(AMM_ERR_INVALID_ARG, "cap=%lld < k=%lld", (long long)cap, (long long)h->k);
+  const int32_t* sel = h->method == AMM_CIRCULANT ? h->cd.so.sel : h->cy.so.sel;
   cudaError_t e = cudaStreamSynchronize(h->stream);
-  if (e == cudaSuccess) e = cudaMemcpy(host_idx, h->cd.so.sel, sizeof(int32_t) * h->k, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(host_idx, sel, sizeof(int32_t) * h->k, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "amm_handle_get_selection");
   *count = h->k;
   return AMM_OK;

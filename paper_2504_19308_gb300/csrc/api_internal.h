@@ -27,6 +27,24 @@ struct amm_handle {
     float* imag = nullptr;        // right operand: Im B~_S (n x n)
   } cd;
 
+  struct Cycle {
+    float* kpart = nullptr;       // per row-block partial cycle norms
+    int nparts = 0;
+    amm::SelectOut so{};
+    float* cyc = nullptr;         // k x n, the selected cycles Lambda_t
+    unsigned char* insel = nullptr;  // n flags
+  } cy;
+
+  struct Fourier {
+    const float2* tw = nullptr;
+    int n = 0, nvec = 0, mask_words = 0;  // transform length, rows (left) / columns (right)
+    float2* T = nullptr;          // left: A~ [m][n/2+1]; right: B~ [n/2+1][p]
+    float2* TT = nullptr;         // left: A~^T [n/2+1][m]
+    float* mag = nullptr;         // [nvec][n/2+1] |.|^2
+    int32_t* sel = nullptr;       // [nvec][k] kept frequencies, ascending
+    uint32_t* maskT = nullptr;    // left: [n][ceil(m/32)] kept-entry bits
+  } ft;
+
   struct Svd {
     float* phi = nullptr;    // cols x k test matrix
     float* Q = nullptr;      // rows x k, orthonormal columns spanning A phi

@@ -93,21 +93,23 @@ __global__ void __launch_bounds__(NT) cd_spectrum_kernel(const T* __restrict__ A
 // ============================================================================ K2: keys, top-k, weights
 // One CTA.  keys2[k] = sum over CTAs of kpart (fixed order, double); mirrored to n-k.
 // Sort (key desc, index asc) with a bitonic network in shared memory; first k = selection.
+// Circulant keys (mirror = 1): partial rows hold t = 0..n/2, T[n-t] = T[t], ||A||^2 = n sum T^2.
+// Cycle keys (mirror = 0): partial rows hold all n cycles, ||A||^2 = sum T^2 (scale = 1).
 __global__ void __launch_bounds__(1024) cd_select_kernel(const float* __restrict__ kpart, int nparts, int n,
                                                          int k, const int32_t* __restrict__ forced,
-                                                         SelectOut out) {
+                                                         SelectOut out, int mirror, double scale) {
   extern __shared__ unsigned char sm[];
   double* key = reinterpret_cast<double*>(sm);                  // n
   int32_t* idx = reinterpret_cast<int32_t*>(key + n);           // n
   unsigned char* in_s = reinterpret_cast<unsigned char*>(idx + n);  // n
   __shared__ double red[32];
   __shared__ int cnt_u, cnt_d;
-  const int kh = n / 2 + 1;
+  const int kh = mirror ? n / 2 + 1 : n;
   for (int t = threadIdx.x; t < kh; t += blockDim.x) {
     double s = 0.0;
     for (int c = 0; c < nparts; ++c) s += (double)kpart[(int64_t)c * kh + t];
     key[t] = s;
-    if (t > 0 && t < n - t) key[n - t] = s;
+    if (mirror && t > 0 && t < n - t) key[n - t] = s;
   }
   __syncthreads();
   // ||A||_F^2 = n sum_k T[k]^2 (Parseval), deterministic block reduction
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(1024) cd_select_kernel(const float* __restrict
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    out.norms[0] = s * (double)n;
+    out.norms[0] = s * scale;
   }
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     out.keys[t] = sqrt(key[t]);
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(1024) cd_select_kernel(const float* __restrict
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    out.norms[1] = out.norms[0] - s * (double)n;
+    out.norms[1] = out.norms[0] - s * scale;
   }
   // union S u S-bar with weights, and the unpaired set with v; compact in index order
   // (single-thread compaction keeps the order deterministic; n <= 8192 so this is cheap)
@@ -447,12 +449,14 @@ cudaError_t cd_twiddles(float2* tw, int n, cudaStream_t st) {
 
 cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const float2* tw, float2* R, float* kpart,
                         cudaStream_t st) {
-  AMM_TRACE("cd_spectrum", st);
+  const int J = cd_cols_per_cta(n);
+  AMM_TRACE_W("cd_spectrum", st, 0.0,
+              (double)n * n * (bf16 ? 2 : 4) + (n / 2 + 1.0) * n * 8 + (double)(n / J) * (n / 2 + 1) * 4, nullptr);
   AMM_DISPATCH_N(n, return CdOps<NN>::spectrum(A, lda, bf16, tw, R, kpart, st));
 }
 
 cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_t* forced, const SelectOut& o,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool mirror) {
   AMM_TRACE("cd_select", st);
   size_t sm = (size_t)n * (sizeof(double) + sizeof(int32_t) + 1);
   static bool attr_done = false;
@@ -462,7 +466,8 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  cd_select_kernel<<<1, 1024, sm, st>>>(kpart, nparts, n, k, forced, o);
+  cd_select_kernel<<<1, 1024, sm, st>>>(kpart, nparts, n, k, forced, o, mirror ? 1 : 0,
+                                        mirror ? (double)n : 1.0);
   return cudaGetLastError();
 }
 
@@ -474,14 +479,17 @@ cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* li
 
 cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
                         float* X, cudaStream_t st) {
-  AMM_TRACE("cd_residual", st);
+  AMM_TRACE_W(mode == 0 ? "cd_residual" : "cd_residual_imag", st, 0.0,
+              mode == 0 ? (n / 2 + 1.0) * n * 8 + (double)n * n * 4 : 0.0, nullptr);
   AMM_DISPATCH_N(n, return CdOps<NN>::residual(R, tw, g, mode, dcount, X, st));
 }
 
 cudaError_t cd_apply(int n, bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
                      const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
                      const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st) {
-  AMM_TRACE(row ? "cd_apply_row" : "cd_apply_col", st);
+  // work: 8 flops per complex MAC, n frequencies x nvec/2 packed signals per applied component
+  AMM_TRACE_W(gate0 ? "cd_apply_unpaired" : (row ? "cd_apply_row" : "cd_apply_col"), st, 4.0 * n * (double)nvec,
+              (double)n * nvec * (bf16 ? 2 : 4) + (double)n * nvec * 4 * (accumulate ? 2 : 1), count);
   AMM_DISPATCH_N(n, return CdOps<NN>::apply(row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out, ldo,
                                             accumulate, st));
 }

@@ -1,0 +1,340 @@
+// Fourier-domain sparsification (Section 2.4, Alg. 4 and Alg. 5 of arXiv 2504.19308), sm_103a.
+//
+//   A~ = A W^*  (row transforms),  B~ = W B  (column transforms),  W(p,q) = n^{-1/2} e^{-2 pi i pq/n}
+//   A~_a keeps the k largest |A~(i, q)| of each row, B~_a the k largest |B~(q, c)| of each column
+//   M = A~_a B~ + (A~ - A~_a) B~_a,   C = Re(M)
+// Real inputs make each transformed row/column Hermitian, so only q = 0..n/2 is stored and the
+// magnitudes of q and n-q are the same number (exact tie, lower index first).
+//
+// HBM layout (kh = n/2 + 1):  At [m][kh] c64, AtT [kh][m] c64, magA [m][kh] f32,
+//   Bt [kh][p] c64, magBT [p][kh] f32, sel [rows][k] i32 (ascending q), maskT [n][ceil(m/32)] u32.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+#include "trace.h"
+
+namespace amm {
+
+// ============================================================================ transforms
+// ROW: rows r0..r0+2S of A (m x n); COL: columns c0..c0+2S of B (n x p).  Packed pairs.
+template <int N, int S, int NT, bool ROW>
+__global__ void __launch_bounds__(NT) ft_transform_kernel(const float* __restrict__ X, int64_t ldx, int nvec,
+                                                          const float2* __restrict__ tw, float2* __restrict__ T,
+                                                          float2* __restrict__ TT, float* __restrict__ mag) {
+  extern __shared__ float2 smem[];
+  constexpr int LD = fft_padded_len(N);
+  constexpr int KH = N / 2 + 1;
+  const int base = blockIdx.x * 2 * S;
+  for (int e = threadIdx.x; e < N * S; e += NT) {
+    int s, l;
+    if (ROW) { s = e / N; l = e % N; } else { l = e / S; s = e % S; }
+    const int v0 = base + 2 * s, v1 = v0 + 1;
+    float x0 = 0.f, x1 = 0.f;
+    if (ROW) {
+      if (v0 < nvec) x0 = __ldg(X + (int64_t)v0 * ldx + l);
+      if (v1 < nvec) x1 = __ldg(X + (int64_t)v1 * ldx + l);
+    } else {
+      if (v0 < nvec) x0 = __ldg(X + (int64_t)l * ldx + v0);
+      if (v1 < nvec) x1 = __ldg(X + (int64_t)l * ldx + v1);
+    }
+    smem[s * LD + fpad(l)] = make_float2(x0, x1);
+  }
+  __syncthreads();
+  fft_smem<N, S, NT, false>(smem, tw);
+  const float sc = rsqrtf((float)N);
+  for (int e = threadIdx.x; e < KH * 2 * S; e += NT) {
+    int q, m;
+    if (ROW) { m = e / KH; q = e % KH; } else { q = e / (2 * S); m = e % (2 * S); }
+    const int v = base + m;
+    if (v >= nvec) continue;
+    const float2* z = smem + (m >> 1) * LD;
+    const float2 a = z[fpad(q)];
+    const float2 b = cconj(z[fpad((N - q) & (N - 1))]);
+    float2 x;
+    if ((m & 1) == 0) x = cscale(cadd(a, b), 0.5f * sc);
+    else { float2 d = csub(a, b); x = make_float2(0.5f * sc * d.y, -0.5f * sc * d.x); }
+    if (ROW) x = cconj(x);  // A W^* = conj(F A^T)^T / sqrt(n) for real rows
+    const float mg = x.x * x.x + x.y * x.y;
+    if (ROW) {
+      T[(int64_t)v * KH + q] = x;
+      TT[(int64_t)q * nvec + v] = x;
+      mag[(int64_t)v * KH + q] = mg;
+    } else {
+      T[(int64_t)q * nvec + v] = x;
+      mag[(int64_t)v * KH + q] = mg;
+    }
+  }
+}
+
+// ============================================================================ exact top-k per row
+// Keys are the float bit patterns of |z|^2 (non-negative, so unsigned order = numeric order) of
+// the virtual row q = 0..n-1 with key(q) = mag[min(q, n-q)].  Four 8-bit MSB radix passes find
+// the k-th largest key tau exactly; the selection is {key > tau} plus the lowest-index entries
+// with key == tau, written in ascending q.
+constexpr int SEL_NT = 256;
+
+__global__ void __launch_bounds__(SEL_NT) ft_select_kernel(const float* __restrict__ mag, int n, int k,
+                                                           int32_t* __restrict__ sel, uint32_t* __restrict__ maskT,
+                                                           int mask_words) {
+  extern __shared__ uint32_t keys[];  // kh
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_prefix, s_need;
+  __shared__ int scan[SEL_NT];
+  const int row = blockIdx.x;
+  const int kh = n / 2 + 1;
+  for (int q = threadIdx.x; q < kh; q += SEL_NT) keys[q] = __float_as_uint(mag[(int64_t)row * kh + q]);
+  if (threadIdx.x == 0) { s_prefix = 0; s_need = (uint32_t)k; }
+  __syncthreads();
+  uint32_t mask = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int b = threadIdx.x; b < 256; b += SEL_NT) hist[b] = 0;
+    __syncthreads();
+    const uint32_t prefix = s_prefix;
+    for (int q = threadIdx.x; q < n; q += SEL_NT) {
+      const uint32_t key = keys[q <= n / 2 ? q : n - q];
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t need = s_need, acc = 0;
+      int b = 255;
+      for (; b > 0; --b) {
+        if (acc + hist[b] >= need) break;
+        acc += hist[b];
+      }
+      s_need = need - acc;
+      s_prefix = prefix | ((uint32_t)b << shift);
+    }
+    mask |= 255u << shift;
+    __syncthreads();
+  }
+  const uint32_t tau = s_prefix;
+  const uint32_t need_eq = s_need;  // how many entries equal to tau are taken (lowest q first)
+  // each thread owns a contiguous chunk of q
+  const int chunk = (n + SEL_NT - 1) / SEL_NT;
+  const int q0 = threadIdx.x * chunk, q1 = min(n, q0 + chunk);
+  int eq = 0;
+  for (int q = q0; q < q1; ++q) eq += keys[q <= n / 2 ? q : n - q] == tau;
+  // exclusive scan of eq counts
+  scan[threadIdx.x] = eq;
+  __syncthreads();
+  for (int o = 1; o < SEL_NT; o <<= 1) {
+    int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+    __syncthreads();
+    scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int eq_before = scan[threadIdx.x] - eq;
+  __syncthreads();
+  // count taken entries in the chunk
+  int taken = 0;
+  {
+    int e = eq_before;
+    for (int q = q0; q < q1; ++q) {
+      const uint32_t key = keys[q <= n / 2 ? q : n - q];
+      if (key > tau) ++taken;
+      else if (key == tau) { if ((uint32_t)e < need_eq) ++taken; ++e; }
+    }
+  }
+  scan[threadIdx.x] = taken;
+  __syncthreads();
+  for (int o = 1; o < SEL_NT; o <<= 1) {
+    int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
+    __syncthreads();
+    scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int pos = scan[threadIdx.x] - taken;
+  int e = eq_before;
+  for (int q = q0; q < q1; ++q) {
+    const uint32_t key = keys[q <= n / 2 ? q : n - q];
+    bool take = false;
+    if (key > tau) take = true;
+    else if (key == tau) { take = (uint32_t)e < need_eq; ++e; }
+    if (take) {
+      if (pos < k) sel[(int64_t)row * k + pos] = q;
+      ++pos;
+      if (maskT) atomicOr(maskT + (int64_t)q * mask_words + (row >> 5), 1u << (row & 31));
+    }
+  }
+}
+
+// ============================================================================ T1 = Re(A~_a B~)
+// CTA: RB rows x 256 columns; thread per column, RB accumulators.
+constexpr int T1_RB = 8;
+__global__ void __launch_bounds__(256) ft_t1_kernel(const float2* __restrict__ At, const int32_t* __restrict__ selA,
+                                                    int k, const float2* __restrict__ Bt, int n, int m, int p,
+                                                    float* __restrict__ C, int64_t ldc) {
+  extern __shared__ unsigned char sm[];
+  int32_t* qs = reinterpret_cast<int32_t*>(sm);                   // RB x k
+  float2* as = reinterpret_cast<float2*>(qs + T1_RB * k + (T1_RB * k & 1));  // RB x k
+  const int kh = n / 2 + 1;
+  const int i0 = blockIdx.y * T1_RB;
+  const int c = blockIdx.x * 256 + threadIdx.x;
+  for (int e = threadIdx.x; e < T1_RB * k; e += 256) {
+    const int rr = e / k, i = i0 + rr;
+    int q = 0;
+    float2 a = make_float2(0.f, 0.f);
+    if (i < m) {
+      q = selA[(int64_t)i * k + (e % k)];
+      const bool mir = q > n / 2;
+      a = At[(int64_t)i * kh + (mir ? n - q : q)];
+      if (mir) a = cconj(a);
+    }
+    qs[e] = q;
+    as[e] = a;
+  }
+  __syncthreads();
+  if (c >= p) return;
+  float acc[T1_RB];
+#pragma unroll
+  for (int rr = 0; rr < T1_RB; ++rr) acc[rr] = 0.f;
+#pragma unroll
+  for (int rr = 0; rr < T1_RB; ++rr) {
+    for (int u = 0; u < k; ++u) {
+      const int q = qs[rr * k + u];
+      const float2 a = as[rr * k + u];
+      const bool mir = q > n / 2;
+      float2 b = __ldg(Bt + (int64_t)(mir ? n - q : q) * p + c);
+      if (mir) b.y = -b.y;
+      acc[rr] = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[rr]));
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < T1_RB; ++rr)
+    if (i0 + rr < m) C[(int64_t)(i0 + rr) * ldc + c] = acc[rr];
+}
+
+// ============================================================================ T2 = Re((A~ - A~_a) B~_a)
+// CTA: CB columns x 256 rows; thread per row i, CB accumulators; A~(i, q) read from At^T.
+constexpr int T2_CB = 8;
+__global__ void __launch_bounds__(256) ft_t2_kernel(const float2* __restrict__ AtT, const uint32_t* __restrict__ maskT,
+                                                    int mask_words, const int32_t* __restrict__ selB, int k,
+                                                    const float2* __restrict__ Bt, int n, int m, int p,
+                                                    float* __restrict__ C, int64_t ldc) {
+  extern __shared__ unsigned char sm[];
+  int32_t* qs = reinterpret_cast<int32_t*>(sm);                   // CB x k
+  float2* bs = reinterpret_cast<float2*>(qs + T2_CB * k + (T2_CB * k & 1));
+  const int c0 = blockIdx.x * T2_CB;
+  const int i = blockIdx.y * 256 + threadIdx.x;
+  for (int e = threadIdx.x; e < T2_CB * k; e += 256) {
+    const int cc = e / k, c = c0 + cc;
+    int q = 0;
+    float2 b = make_float2(0.f, 0.f);
+    if (c < p) {
+      q = selB[(int64_t)c * k + (e % k)];
+      const bool mir = q > n / 2;
+      b = Bt[(int64_t)(mir ? n - q : q) * p + c];
+      if (mir) b = cconj(b);
+    }
+    qs[e] = q;
+    bs[e] = b;
+  }
+  __syncthreads();
+  if (i >= m) return;
+  float acc[T2_CB];
+#pragma unroll
+  for (int cc = 0; cc < T2_CB; ++cc) acc[cc] = 0.f;
+#pragma unroll
+  for (int cc = 0; cc < T2_CB; ++cc) {
+    for (int u = 0; u < k; ++u) {
+      const int q = qs[cc * k + u];
+      const uint32_t w = __ldg(maskT + (int64_t)q * mask_words + (i >> 5));
+      if ((w >> (i & 31)) & 1u) continue;  // (i, q) kept in A~_a: not part of the residue
+      const bool mir = q > n / 2;
+      float2 a = __ldg(AtT + (int64_t)(mir ? n - q : q) * m + i);
+      if (mir) a.y = -a.y;
+      const float2 b = bs[cc * k + u];
+      acc[cc] = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[cc]));
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < T2_CB; ++cc)
+    if (c0 + cc < p) C[(int64_t)i * ldc + c0 + cc] += acc[cc];
+}
+
+// ============================================================================ launchers
+template <int N> struct FtCfg {
+  static constexpr int S = (N >= 8192) ? 2 : 4;
+  static constexpr int NT = (N >= 512) ? 512 : N;
+  static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
+};
+
+template <int N> struct FtOps {
+  using C = FtCfg<N>;
+  static cudaError_t transform(bool row, const float* X, int64_t ldx, int nvec, const float2* tw, float2* T,
+                               float2* TT, float* mag, cudaStream_t st) {
+    static cudaError_t attr = [] {
+      cudaError_t e = cudaFuncSetAttribute((const void*)ft_transform_kernel<N, C::S, C::NT, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)ft_transform_kernel<N, C::S, C::NT, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      return e;
+    }();
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((nvec + 2 * C::S - 1) / (2 * C::S));
+    if (row)
+      ft_transform_kernel<N, C::S, C::NT, true><<<grid, C::NT, C::SMEM, st>>>(X, ldx, nvec, tw, T, TT, mag);
+    else
+      ft_transform_kernel<N, C::S, C::NT, false><<<grid, C::NT, C::SMEM, st>>>(X, ldx, nvec, tw, T, TT, mag);
+    return cudaGetLastError();
+  }
+};
+
+#define AMM_FT_DISPATCH(n, EXPR)                  \
+  switch (n) {                                    \
+    case 16: { constexpr int NN = 16; EXPR; }     \
+    case 32: { constexpr int NN = 32; EXPR; }     \
+    case 64: { constexpr int NN = 64; EXPR; }     \
+    case 128: { constexpr int NN = 128; EXPR; }   \
+    case 256: { constexpr int NN = 256; EXPR; }   \
+    case 512: { constexpr int NN = 512; EXPR; }   \
+    case 1024: { constexpr int NN = 1024; EXPR; } \
+    case 2048: { constexpr int NN = 2048; EXPR; } \
+    case 4096: { constexpr int NN = 4096; EXPR; } \
+    case 8192: { constexpr int NN = 8192; EXPR; } \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+cudaError_t ft_transform(int n, bool row, const float* X, int64_t ldx, int nvec, const float2* tw, float2* T,
+                         float2* TT, float* mag, cudaStream_t st) {
+  AMM_TRACE_W(row ? "ft_row_transform" : "ft_col_transform", st, 0.0,
+              (double)n * nvec * 4 + (n / 2 + 1.0) * nvec * (row ? 20 : 12), nullptr);
+  AMM_FT_DISPATCH(n, return FtOps<NN>::transform(row, X, ldx, nvec, tw, T, TT, mag, st));
+}
+
+cudaError_t ft_select(int n, int k, int rows, const float* mag, int32_t* sel, uint32_t* maskT, int mask_words,
+                      cudaStream_t st) {
+  AMM_TRACE_W("ft_select", st, 0.0, (double)rows * (n / 2 + 1) * 4, nullptr);
+  if (maskT) {
+    cudaError_t e = cudaMemsetAsync(maskT, 0, sizeof(uint32_t) * (size_t)n * mask_words, st);
+    if (e != cudaSuccess) return e;
+  }
+  ft_select_kernel<<<rows, SEL_NT, sizeof(uint32_t) * (n / 2 + 1), st>>>(mag, n, k, sel, maskT, mask_words);
+  return cudaGetLastError();
+}
+
+cudaError_t ft_product(int n, int m, int p, int k_a, int k_b, const float2* At, const float2* AtT,
+                       const int32_t* selA, const uint32_t* maskT, int mask_words, const float2* Bt,
+                       const int32_t* selB, float* C, int64_t ldc, cudaStream_t st) {
+  {
+    AMM_TRACE_W("ft_t1", st, 8.0 * m * (double)p * k_a, 8.0 * m * (double)p * k_a + 4.0 * m * p, nullptr);
+    dim3 grid((p + 255) / 256, (m + T1_RB - 1) / T1_RB);
+    size_t sm = (size_t)T1_RB * k_a * (4 + 8) + 8;
+    ft_t1_kernel<<<grid, 256, sm, st>>>(At, selA, k_a, Bt, n, m, p, C, ldc);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  {
+    AMM_TRACE_W("ft_t2", st, 8.0 * m * (double)p * k_b, 12.0 * m * (double)p * k_b + 8.0 * m * p, nullptr);
+    dim3 grid((p + T2_CB - 1) / T2_CB, (m + 255) / 256);
+    size_t sm = (size_t)T2_CB * k_b * (4 + 8) + 8;
+    ft_t2_kernel<<<grid, 256, sm, st>>>(AtT, maskT, mask_words, selB, k_b, Bt, n, m, p, C, ldc);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace amm

@@ -166,7 +166,8 @@ static cudaError_t sgemm(bool ta, bool tb, int M, int N, int K, float alpha, con
   }
   dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M, splits);
   {
-  AMM_TRACE("sgemm", st);
+  AMM_TRACE_W("sgemm", st, 2.0 * M * N * (double)K,
+              4.0 * ((double)M * K + (double)K * N + (double)M * N * (beta != 0.f ? 2 : 1)), nullptr);
 #define AMM_SGEMM_LAUNCH(TA_, TB_) \
   sgemm_kernel<TA_, TB_, TIn><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, ws)
   if (!ta && !tb) AMM_SGEMM_LAUNCH(false, false);
@@ -253,7 +254,7 @@ static cudaError_t dgemm_small(int M, int N, int K, const TA_t* A, int64_t lda, 
   if (e != cudaSuccess) return e;
   dim3 grid((N + 31) / 32, (M + 31) / 32, splits);
   {
-    AMM_TRACE("dgemm_small", st);
+    AMM_TRACE_W("dgemm_small", st, 2.0 * M * N * (double)K, 0.0, nullptr);
     dgemm_small_kernel<TA, TB, TA_t, TB_t><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, kchunk, ws);
   }
   e = cudaGetLastError();

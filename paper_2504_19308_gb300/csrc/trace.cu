@@ -21,7 +21,11 @@ static std::mutex g_trace_mu;
 struct Rec {
   const char* name;
   cudaEvent_t a, b;
+  double flops, bytes;
+  int slot;  // index into the pinned count slots, -1 if the work is fixed
 };
+static int32_t* g_slots = nullptr;  // pinned host memory receiving device-side counts
+static int g_nslots = 0, g_used = 0;
 static std::vector<Rec> g_recs;
 static std::vector<cudaEvent_t> g_pool;
 
@@ -36,7 +40,8 @@ static cudaEvent_t take_event() {
   return e;
 }
 
-TraceScope::TraceScope(const char* name, cudaStream_t st) : name_(name), st_(st) {
+TraceScope::TraceScope(const char* name, cudaStream_t st, double flops, double bytes, const int32_t* dev_count)
+    : name_(name), st_(st), flops_(flops), bytes_(bytes), dev_count_(dev_count) {
   if (!g_trace_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_trace_mu);
   a_ = take_event();
@@ -49,7 +54,18 @@ TraceScope::~TraceScope() {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   cudaEvent_t b = take_event();
   cudaEventRecord(b, st_);
-  g_recs.push_back({name_, (cudaEvent_t)a_, b});
+  int slot = -1;
+  if (dev_count_) {
+    if (!g_slots) {
+      g_nslots = 1 << 16;
+      if (cudaMallocHost((void**)&g_slots, sizeof(int32_t) * g_nslots) != cudaSuccess) g_slots = nullptr;
+    }
+    if (g_slots && g_used < g_nslots) {
+      slot = g_used++;
+      cudaMemcpyAsync(g_slots + slot, dev_count_, sizeof(int32_t), cudaMemcpyDeviceToHost, st_);
+    }
+  }
+  g_recs.push_back({name_, (cudaEvent_t)a_, b, flops_, bytes_, slot});
 }
 
 }  // namespace amm
@@ -64,27 +80,40 @@ extern "C" amm_status_t amm_trace_enable(int32_t on) {
 extern "C" amm_status_t amm_trace_collect(char* host_json, int64_t cap, int64_t* launches) {
   if (!host_json || cap <= 0) return fail(AMM_ERR_INVALID_ARG, "amm_trace_collect: bad buffer");
   std::lock_guard<std::mutex> lk(g_trace_mu);
-  std::map<std::string, std::pair<long, double>> agg;
+  struct Agg {
+    long n = 0;
+    double ms = 0, flops = 0, bytes = 0;
+  };
+  std::map<std::string, Agg> agg;
   long total = 0;
+  if (!g_recs.empty()) {
+    cudaError_t e = cudaDeviceSynchronize();  // the count copies ride on the launches' streams
+    if (e != cudaSuccess) return cuda_fail(e, "amm_trace_collect");
+  }
   for (auto& r : g_recs) {
     cudaError_t e = cudaEventSynchronize(r.b);
     if (e != cudaSuccess) return cuda_fail(e, "amm_trace_collect");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, r.a, r.b);
     auto& v = agg[r.name];
-    v.first += 1;
-    v.second += ms;
+    double mult = 1.0;
+    if (r.slot >= 0) mult = (double)g_slots[r.slot];
+    v.n += 1;
+    v.ms += ms;
+    v.flops += r.flops * mult;
+    v.bytes += r.bytes;
     ++total;
     g_pool.push_back(r.a);
     g_pool.push_back(r.b);
   }
   g_recs.clear();
+  g_used = 0;
   std::string s = "{";
   bool first = true;
   for (auto& kv : agg) {
     char buf[256];
-    snprintf(buf, sizeof(buf), "%s\"%s\": [%ld, %.6f]", first ? "" : ", ", kv.first.c_str(), kv.second.first,
-             kv.second.second);
+    snprintf(buf, sizeof(buf), "%s\"%s\": [%ld, %.6f, %.6e, %.6e]", first ? "" : ", ", kv.first.c_str(), kv.second.n,
+             kv.second.ms, kv.second.flops, kv.second.bytes);
     s += buf;
     first = false;
   }

@@ -1,0 +1,71 @@
+"""GPU parity of the cycle-sparsified first-order product (Section 1.2.2, Eq. (2.4)-(2.5))."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from gpu_util import TOL, as64, check_selection, dev32, rel, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(torch, amm, a, b, ka, kb=None):
+    A, B = dev32(torch, a), dev32(torch, b)
+    hA = amm.decompose(A, "cycle", ka, "left")
+    hB = amm.decompose(B, "cycle", kb or ka, "right")
+    C = amm.approx_matmul(hA, hB)
+    a64, b64 = as64(A), as64(B)
+    # cycles are real and have no conjugate partners: the plain near-tie rule applies
+    check_selection(hA.selection(), O.cycle_keys(a64), ka, "A")
+    check_selection(hB.selection(), O.cycle_keys(b64), kb or ka, "B")
+    ref, _, ta, _ = O.cycle_matmul(a64, b64, ka, kb, sel_a=hA.selection(), sel_b=hB.selection(), full=True)
+    err = rel(C.double().cpu().numpy(), ref.real)
+    assert err <= TOL, (a.shape, ka, err)
+    info = hA.info()
+    assert info["fro2"] == pytest.approx(float(np.sum(a64 * a64)), rel=1e-5)
+    assert info["resid_fro2"] == pytest.approx(float(np.sum(ta.resid ** 2)), rel=1e-4, abs=1e-6 * info["fro2"])
+    return err
+
+
+@pytest.mark.parametrize("n", [16, 64, 256, 1024])
+@pytest.mark.parametrize("k", [1, 3, 10])
+def test_cycle_small(n, k):
+    torch, amm = torch_cuda()
+    g = S.rng(n + k, 0)
+    a = g.standard_normal((n, n)) + np.diag(np.full(n, 3.0))   # the main cycle dominates
+    b = S.toeplitz_uniform(n, g)
+    _check(torch, amm, a, b, k, k + 1 if k < n else k)
+
+
+@pytest.mark.parametrize("k", [41, 128])
+def test_cycle_powerlaw_n4096(k):
+    """k = ceil(0.01 n) = 41 cycles (1% of the entries) on the n = 4096 power-law pair."""
+    torch, amm = torch_cuda()
+    a, b = S.powerlaw_pair(4096, seed=0)
+    _check(torch, amm, a, b, k)
+
+
+def test_cycle_untruncated_exact():
+    torch, amm = torch_cuda()
+    n = 64
+    a, b = S.exp32_pair(n, seed=2)
+    A, B = dev32(torch, a), dev32(torch, b)
+    C = amm.approx_matmul(amm.decompose(A, "cycle", n, "left"), amm.decompose(B, "cycle", n, "right"))
+    assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= TOL
+
+
+def test_cycle_banded_is_exact():
+    """A banded matrix with k nonzero cycles is reproduced exactly: A_s = A, dA = 0."""
+    torch, amm = torch_cuda()
+    n = 128
+    g = S.rng(3, 0)
+    a = np.zeros((n, n))
+    for j in (0, 1, n - 1):
+        for l in range(n):
+            a[(l + j) % n, l] = g.standard_normal()
+    b = g.standard_normal((n, n))
+    A, B = dev32(torch, a), dev32(torch, b)
+    hA = amm.decompose(A, "cycle", 3, "left")
+    assert sorted(hA.selection().tolist()) == [0, 1, n - 1]
+    C = amm.approx_matmul(hA, amm.decompose(B, "cycle", 5, "right"))
+    assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= TOL

@@ -1,0 +1,77 @@
+"""GPU parity of the Fourier-sparsified first-order product (Alg. 4, Alg. 5)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from gpu_util import TOL, as64, check_selection, dev32, rel, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(torch, amm, a, b, k, check_rows=64):
+    A, B = dev32(torch, a), dev32(torch, b)
+    hA = amm.decompose(A, "fourier", k, "left")
+    hB = amm.decompose(B, "fourier", k, "right")
+    C = amm.approx_matmul(hA, hB)
+    a64, b64 = as64(A), as64(B)
+    sa, sb = hA.selection(), hB.selection()
+    n = a.shape[1]
+    # per-row / per-column selection against the oracle's magnitudes (near-tie rule per row)
+    magA = O.magnitudes_mirrored_rows(a64 @ np.conj(O.unitary_W(n)).T)
+    magB = O.magnitudes_mirrored_rows((O.unitary_W(n) @ b64).T)
+    for i in np.linspace(0, a.shape[0] - 1, min(check_rows, a.shape[0])).astype(int):
+        check_selection(sa[i], magA[i], k, "A row %d" % i)
+    for c in np.linspace(0, b.shape[1] - 1, min(check_rows, b.shape[1])).astype(int):
+        check_selection(sb[c], magB[c], k, "B col %d" % c)
+    ref = O.fourier_matmul(a64, b64, k, forced_a=sa, forced_b=sb)
+    err = rel(C.double().cpu().numpy(), ref)
+    assert err <= TOL, (a.shape, b.shape, k, err)
+    return err
+
+
+@pytest.mark.parametrize("n", [16, 64, 256, 1024])
+@pytest.mark.parametrize("k", [1, 2, 5, 16])
+def test_fourier_small(n, k):
+    torch, amm = torch_cuda()
+    a, b = S.general_times_toeplitz(n, seed=n + k)
+    _check(torch, amm, a, b, min(k, n))
+
+
+@pytest.mark.parametrize("m,n,p,k", [(100, 64, 37, 3), (257, 128, 300, 7), (33, 512, 65, 6)])
+def test_fourier_rectangular_ragged(m, n, p, k):
+    torch, amm = torch_cuda()
+    g = S.rng(m + p, 0)
+    _check(torch, amm, g.standard_normal((m, n)), g.uniform(0, 1, (n, p)), k)
+
+
+def test_fourier_powerlaw_n4096_top1pct():
+    """Top 1% of the entries (k = ceil(0.01 n) = 41 per row / column) on the n = 4096 pair."""
+    torch, amm = torch_cuda()
+    a, b = S.powerlaw_pair(4096, seed=0)
+    _check(torch, amm, a, b, 41, check_rows=128)
+
+
+def test_fourier_untruncated_exact():
+    torch, amm = torch_cuda()
+    n = 32
+    a, b = S.exp32_pair(n, seed=5)
+    A, B = dev32(torch, a), dev32(torch, b)
+    C = amm.approx_matmul(amm.decompose(A, "fourier", n, "left"), amm.decompose(B, "fourier", n, "right"))
+    assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= TOL
+
+
+def test_fourier_single_tone_rows_exact():
+    """Rows that are single real tones cos(2 pi f l / n) have two nonzero frequencies: k = 2 keeps them."""
+    torch, amm = torch_cuda()
+    n, m = 128, 64
+    l = np.arange(n)
+    g = S.rng(6, 0)
+    a = np.stack([np.cos(2 * np.pi * (i % 17 + 1) * l / n) * (1 + i) for i in range(m)])
+    b = g.standard_normal((n, 40))
+    A, B = dev32(torch, a), dev32(torch, b)
+    hA = amm.decompose(A, "fourier", 2, "left")
+    sel = hA.selection()
+    assert all(sorted(sel[i].tolist()) == [i % 17 + 1, n - (i % 17 + 1)] for i in range(m))
+    C = amm.approx_matmul(hA, amm.decompose(B, "fourier", 3, "right"))
+    assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= 1e-5
