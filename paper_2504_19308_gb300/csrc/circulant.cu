@@ -27,6 +27,8 @@
 
 namespace amm {
 
+constexpr int SEL_SORT_MAX = 4096;  // selections up to this size are returned in key order
+
 template <typename T> AMM_DEV float ld_as_float(const T* p);
 template <> AMM_DEV float ld_as_float<float>(const float* p) { return __ldg(p); }
 template <> AMM_DEV float ld_as_float<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
@@ -91,109 +93,210 @@ __global__ void __launch_bounds__(NT) cd_spectrum_kernel(const T* __restrict__ A
 }
 
 // ============================================================================ K2: keys, top-k, weights
-// One CTA.  keys2[k] = sum over CTAs of kpart (fixed order, double); mirrored to n-k.
-// Sort (key desc, index asc) with a bitonic network in shared memory; first k = selection.
+// One CTA of 1024 threads.  key2[t] = sum over the partial rows (fixed order, double).
+// Top-k by (key desc, index asc): an exact MSB radix select over the 64-bit patterns of the
+// non-negative double keys (8 passes of 8 bits) finds the k-th key tau; the selection is
+// {key > tau} plus the lowest-index entries equal to tau.  The k winners are then ordered by
+// a bitonic sort in shared memory.  Union / unpaired lists are compacted with block scans.
+constexpr int SEL_T = 1024;
+
+// exclusive block scan of one int per thread (SEL_T threads); returns the block total in *tot
+__device__ int block_excl_scan(int v, int* wsum, int* tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int y = lane < (SEL_T / 32) ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    wsum[lane] = y;  // inclusive warp-sum prefix
+  }
+  __syncthreads();
+  const int before = (w > 0 ? wsum[w - 1] : 0) + x - v;
+  *tot = wsum[SEL_T / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < SEL_T / 32; ++w) s += red[w];
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
 // Circulant keys (mirror = 1): partial rows hold t = 0..n/2, T[n-t] = T[t], ||A||^2 = n sum T^2.
 // Cycle keys (mirror = 0): partial rows hold all n cycles, ||A||^2 = sum T^2 (scale = 1).
-__global__ void __launch_bounds__(1024) cd_select_kernel(const float* __restrict__ kpart, int nparts, int n,
-                                                         int k, const int32_t* __restrict__ forced,
-                                                         SelectOut out, int mirror, double scale) {
+__global__ void __launch_bounds__(SEL_T) cd_select_kernel(const float* __restrict__ kpart, int nparts, int n,
+                                                          int k, const int32_t* __restrict__ forced,
+                                                          SelectOut out, int mirror, double scale) {
   extern __shared__ unsigned char sm[];
-  double* key = reinterpret_cast<double*>(sm);                  // n
-  int32_t* idx = reinterpret_cast<int32_t*>(key + n);           // n
-  unsigned char* in_s = reinterpret_cast<unsigned char*>(idx + n);  // n
+  double* key = reinterpret_cast<double*>(sm);                        // n (later: k sorted keys)
+  unsigned char* in_s = reinterpret_cast<unsigned char*>(key + n);    // n
   __shared__ double red[32];
-  __shared__ int cnt_u, cnt_d;
+  __shared__ int wsum[32];
+  __shared__ unsigned int hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ unsigned int s_need;
+  __shared__ double s_kth, s_next;
   const int kh = mirror ? n / 2 + 1 : n;
-  for (int t = threadIdx.x; t < kh; t += blockDim.x) {
+  for (int t = threadIdx.x; t < kh; t += SEL_T) {
     double s = 0.0;
     for (int c = 0; c < nparts; ++c) s += (double)kpart[(int64_t)c * kh + t];
     key[t] = s;
     if (mirror && t > 0 && t < n - t) key[n - t] = s;
   }
+  for (int t = threadIdx.x; t < n; t += SEL_T) in_s[t] = 0;
   __syncthreads();
-  // ||A||_F^2 = n sum_k T[k]^2 (Parseval), deterministic block reduction
   double part = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) part += key[t];
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    out.norms[0] = s * scale;
-  }
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+  for (int t = threadIdx.x; t < n; t += SEL_T) {
+    part += key[t];
     out.keys[t] = sqrt(key[t]);
-    idx[t] = t;
-    in_s[t] = 0;
+  }
+  const double total = block_sum(part, red);
+  if (threadIdx.x == 0) out.norms[0] = total * scale;
+  // chunk ownership for compactions: thread owns [c0, c1)
+  const int chunk = (n + SEL_T - 1) / SEL_T;
+  const int c0 = min(n, threadIdx.x * chunk), c1 = min(n, c0 + chunk);
+  if (forced == nullptr) {
+    if (threadIdx.x == 0) { s_prefix = 0ull; s_need = (unsigned)k; }
+    __syncthreads();
+    unsigned long long mask = 0ull;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      for (int b = threadIdx.x; b < 256; b += SEL_T) hist[b] = 0;
+      __syncthreads();
+      const unsigned long long prefix = s_prefix;
+      for (int t = threadIdx.x; t < n; t += SEL_T) {
+        const unsigned long long kb = (unsigned long long)__double_as_longlong(key[t]);
+        if ((kb & mask) == prefix) atomicAdd(&hist[(kb >> shift) & 255ull], 1u);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned need = s_need, acc = 0;
+        int b = 255;
+        for (; b > 0; --b) {
+          if (acc + hist[b] >= need) break;
+          acc += hist[b];
+        }
+        s_need = need - acc;
+        s_prefix = prefix | ((unsigned long long)b << shift);
+      }
+      mask |= 255ull << shift;
+      __syncthreads();
+    }
+    const unsigned long long tau = s_prefix;
+    const unsigned need_eq = s_need;
+    int eq = 0;
+    for (int t = c0; t < c1; ++t) eq += (unsigned long long)__double_as_longlong(key[t]) == tau;
+    int tot;
+    int e = block_excl_scan(eq, wsum, &tot);
+    for (int t = c0; t < c1; ++t) {
+      const unsigned long long kb = (unsigned long long)__double_as_longlong(key[t]);
+      if (kb > tau) in_s[t] = 1;
+      else if (kb == tau) { if ((unsigned)e < need_eq) in_s[t] = 1; ++e; }
+    }
+    __syncthreads();
+    // boundary gap: the k-th key is tau; the next key is the largest key not selected
+    if (threadIdx.x == 0) { s_kth = __longlong_as_double((long long)tau); s_next = -1.0; }
+    __syncthreads();
+    double nxt = -1.0;
+    for (int t = threadIdx.x; t < n; t += SEL_T) if (!in_s[t]) nxt = fmax(nxt, key[t]);
+    for (int o = 16; o > 0; o >>= 1) nxt = fmax(nxt, __shfl_xor_sync(0xffffffffu, nxt, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nxt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = -1.0;
+      for (int w = 0; w < SEL_T / 32; ++w) m = fmax(m, red[w]);
+      const double a = sqrt(s_kth);
+      out.norms[2] = (m < 0.0) ? 1e300 : (a > 0 ? (a - sqrt(m)) / a : 0.0);
+    }
+    __syncthreads();
+  } else {
+    for (int t = threadIdx.x; t < k; t += SEL_T) in_s[forced[t]] = 1;
+    if (threadIdx.x == 0) out.norms[2] = -1.0;
+    __syncthreads();
+  }
+  // ||dA||^2 = ||A||^2 - scale * sum_{t in S} T[t]^2
+  part = 0.0;
+  for (int t = threadIdx.x; t < n; t += SEL_T) if (in_s[t]) part += key[t];
+  const double kept = block_sum(part, red);
+  if (threadIdx.x == 0) out.norms[1] = total * scale - kept * scale;
+  // compact the selection (ascending index), then order it by (key desc, index asc)
+  int cnt = 0;
+  for (int t = c0; t < c1; ++t) cnt += in_s[t];
+  int tot;
+  int pos = block_excl_scan(cnt, wsum, &tot);
+  // stash (key, index) of the winners after the n keys are no longer needed: use idx area
+  double* skey = reinterpret_cast<double*>(in_s + n + ((8 - (n & 7)) & 7));  // kp doubles
+  int32_t* sidx = reinterpret_cast<int32_t*>(skey + SEL_SORT_MAX);           // kp ints
+  int kp = 1;
+  while (kp < k) kp <<= 1;
+  const bool sortable = kp <= SEL_SORT_MAX;
+  for (int t = c0; t < c1; ++t) {
+    if (in_s[t]) {
+      if (sortable) { skey[pos] = key[t]; sidx[pos] = t; }
+      else out.sel[pos] = t;
+      ++pos;
+    }
   }
   __syncthreads();
-  if (forced == nullptr) {
-    // bitonic sort, descending by key, ascending by index on ties
-    for (int size = 2; size <= n; size <<= 1) {
+  if (sortable && forced == nullptr) {
+    for (int t = k + threadIdx.x; t < kp; t += SEL_T) { skey[t] = -1.0; sidx[t] = 0x7fffffff; }
+    __syncthreads();
+    for (int size = 2; size <= kp; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          int p = i ^ stride;
+        for (int i = threadIdx.x; i < kp; i += SEL_T) {
+          const int p = i ^ stride;
           if (p > i) {
-            bool up = ((i & size) == 0);  // this half sorts "descending-first" order
-            double ki = key[i], kp = key[p];
-            int ii = idx[i], ip = idx[p];
-            bool i_first = (ki > kp) || (ki == kp && ii < ip);  // i should precede p
-            if (up ? !i_first : i_first) {
-              key[i] = kp; key[p] = ki; idx[i] = ip; idx[p] = ii;
-            }
+            const bool up = (i & size) == 0;
+            const double ki = skey[i], kq = skey[p];
+            const int ii = sidx[i], iq = sidx[p];
+            const bool i_first = (ki > kq) || (ki == kq && ii < iq);
+            if (up ? !i_first : i_first) { skey[i] = kq; skey[p] = ki; sidx[i] = iq; sidx[p] = ii; }
           }
         }
         __syncthreads();
       }
     }
-    for (int t = threadIdx.x; t < k; t += blockDim.x) out.sel[t] = idx[t];
-    if (threadIdx.x == 0) {
-      double a = sqrt(key[k - 1]);
-      out.norms[2] = (k < n) ? (a > 0 ? (a - sqrt(key[k])) / a : 0.0) : 1e300;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < k; t += blockDim.x) in_s[idx[t]] = 1;
-  } else {
-    for (int t = threadIdx.x; t < k; t += blockDim.x) {
-      out.sel[t] = forced[t];
-      in_s[forced[t]] = 1;
-    }
-    if (threadIdx.x == 0) out.norms[2] = -1.0;
+    for (int t = threadIdx.x; t < k; t += SEL_T) out.sel[t] = sidx[t];
+  } else if (forced != nullptr) {
+    for (int t = threadIdx.x; t < k; t += SEL_T) out.sel[t] = forced[t];
+  } else if (sortable) {
+    for (int t = threadIdx.x; t < k; t += SEL_T) out.sel[t] = sidx[t];
   }
-  __syncthreads();
-  // restore unsorted keys^2 for the residual norm
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    double tt = out.keys[t];
-    key[t] = tt * tt;
+  // union S u S-bar (weight w_t) and unpaired set (v_t), compacted in index order
+  int nu = 0, nd = 0;
+  for (int t = c0; t < c1; ++t) {
+    const int a = in_s[t], b = in_s[(n - t) & (n - 1)];
+    out.wfull[t] = 0.5f * (float)(a + b);
+    out.vfull[t] = 0.5f * (float)(a - b);
+    nu += (a | b);
+    nd += (a != b);
   }
-  if (threadIdx.x == 0) { cnt_u = 0; cnt_d = 0; }
-  __syncthreads();
-  part = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) if (in_s[t]) part += key[t];
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-  __syncthreads();
+  int totu, totd;
+  int pu = block_excl_scan(nu, wsum, &totu);
+  int pd = block_excl_scan(nd, wsum, &totd);
+  for (int t = c0; t < c1; ++t) {
+    const int a = in_s[t], b = in_s[(n - t) & (n - 1)];
+    if (a | b) { out.ulist[pu] = t; out.uw[pu] = 0.5f * (float)(a + b); ++pu; }
+    if (a != b) { out.dlist[pd] = t; out.dv[pd] = 0.5f * (float)(a - b); ++pd; }
+  }
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    out.norms[1] = out.norms[0] - s * scale;
-  }
-  // union S u S-bar with weights, and the unpaired set with v; compact in index order
-  // (single-thread compaction keeps the order deterministic; n <= 8192 so this is cheap)
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int nu = 0, nd = 0;
-    for (int t = 0; t < n; ++t) {
-      int a = in_s[t], b = in_s[(n - t) & (n - 1)];
-      out.wfull[t] = 0.5f * (float)(a + b);
-      out.vfull[t] = 0.5f * (float)(a - b);
-      if (a | b) { out.ulist[nu] = t; out.uw[nu] = 0.5f * (float)(a + b); ++nu; }
-      if (a != b) { out.dlist[nd] = t; out.dv[nd] = 0.5f * (float)(a - b); ++nd; }
-    }
-    out.counts[0] = nu;
-    out.counts[1] = nd;
+    out.counts[0] = totu;
+    out.counts[1] = totd;
   }
 }
 
@@ -458,16 +561,18 @@ cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const floa
 cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_t* forced, const SelectOut& o,
                       cudaStream_t st, bool mirror) {
   AMM_TRACE("cd_select", st);
-  size_t sm = (size_t)n * (sizeof(double) + sizeof(int32_t) + 1);
+  auto bytes = [](int nn) {
+    return (size_t)nn * (sizeof(double) + 1) + 8 + (size_t)SEL_SORT_MAX * (sizeof(double) + sizeof(int32_t));
+  };
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute((const void*)cd_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)8192 * (sizeof(double) + sizeof(int32_t) + 1)));
+                                         (int)bytes(8192));
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  cd_select_kernel<<<1, 1024, sm, st>>>(kpart, nparts, n, k, forced, o, mirror ? 1 : 0,
-                                        mirror ? (double)n : 1.0);
+  cd_select_kernel<<<1, SEL_T, bytes(n), st>>>(kpart, nparts, n, k, forced, o, mirror ? 1 : 0,
+                                               mirror ? (double)n : 1.0);
   return cudaGetLastError();
 }
 

@@ -271,51 +271,78 @@ static cudaError_t dgemm_small(int M, int N, int K, const TA_t* A, int64_t lda, 
 // ============================================================================ Cholesky + inverse (FP64, one CTA)
 // G (k x k, symmetric positive semi-definite) -> Linv = L^{-1} with G + s I = L L^T,
 // s = 1e-15 trace(G) / k (keeps rank-deficient sketches factorisable; the second CholQR pass
-// restores orthonormality).  W is k x k scratch.
-__global__ void __launch_bounds__(1024) chol_inv_kernel(int k, const double* __restrict__ G, double* __restrict__ W,
-                                                        double* __restrict__ L, double* __restrict__ Linv) {
-  __shared__ double shift;
-  __shared__ double dj;
+// restores orthonormality).  For k <= CHOL_SMEM_K the work matrix lives in shared memory:
+// L in the lower triangle, L^{-1} transposed in the strict upper triangle, 1/L_ii aside.
+// Larger k use the global scratch W the same way.
+constexpr int CHOL_SMEM_K = 128;
+constexpr int CHOL_T = 1024;
+
+__global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const double* __restrict__ G,
+                                                          double* __restrict__ Wg, double* __restrict__ Linv) {
+  extern __shared__ double sW[];
+  __shared__ double dinv_s[CHOL_SMEM_K];
+  __shared__ double red[32];
+  __shared__ double shift_s;
+  const bool in_smem = k <= CHOL_SMEM_K;
+  double* W = in_smem ? sW : Wg;
+  double* dinv = in_smem ? dinv_s : Linv;  // global case: diagonal stashed in Linv's first row
   const int tid = threadIdx.x;
+  double tr = 0.0;
+  for (int i = tid; i < k; i += CHOL_T) tr += G[(int64_t)i * k + i];
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if ((tid & 31) == 0) red[tid >> 5] = tr;
+  __syncthreads();
   if (tid == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < k; ++i) tr += G[(int64_t)i * k + i];
-    shift = 1e-15 * tr / k + 1e-300;
+    double t = 0.0;
+    for (int w = 0; w < CHOL_T / 32; ++w) t += red[w];
+    shift_s = 1e-15 * t / k + 1e-300;
   }
   __syncthreads();
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    int i = e / k, j = e % k;
+  const double shift = shift_s;
+  for (int e = tid; e < k * k; e += CHOL_T) {
+    const int i = e / k, j = e % k;
     W[e] = G[e] + (i == j ? shift : 0.0);
-    L[e] = 0.0;
-    Linv[e] = 0.0;
   }
   __syncthreads();
+  // right-looking Cholesky, L overwrites the lower triangle
   for (int j = 0; j < k; ++j) {
-    if (tid == 0) {
-      double d = W[(int64_t)j * k + j];
-      d = sqrt(d > shift ? d : shift);
-      dj = d;
-      L[(int64_t)j * k + j] = d;
-    }
+    const double djj = sqrt(fmax(W[(int64_t)j * k + j], shift));
     __syncthreads();
-    for (int i = j + 1 + tid; i < k; i += blockDim.x) L[(int64_t)i * k + j] = W[(int64_t)i * k + j] / dj;
+    for (int i = j + 1 + tid; i < k; i += CHOL_T) W[(int64_t)i * k + j] /= djj;
+    if (tid == 0) W[(int64_t)j * k + j] = djj;
     __syncthreads();
     const int rem = k - j - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      int i = j + 1 + e / rem, l = j + 1 + e % rem;
-      if (l <= i) W[(int64_t)i * k + l] -= L[(int64_t)i * k + j] * L[(int64_t)l * k + j];
+    for (int e = tid; e < rem * rem; e += CHOL_T) {
+      const int i = j + 1 + e / rem, l = j + 1 + e % rem;
+      if (l <= i) W[(int64_t)i * k + l] -= W[(int64_t)i * k + j] * W[(int64_t)l * k + j];
     }
     __syncthreads();
   }
-  // forward substitution, one column of the inverse per thread
-  for (int c = tid; c < k; c += blockDim.x) {
-    Linv[(int64_t)c * k + c] = 1.0 / L[(int64_t)c * k + c];
-    for (int i = c + 1; i < k; ++i) {
-      double s = 0.0;
-      for (int l = c; l < i; ++l) s += L[(int64_t)i * k + l] * Linv[(int64_t)l * k + c];
-      Linv[(int64_t)i * k + c] = -s / L[(int64_t)i * k + i];
-    }
+  // L^{-1} row by row: Linv[i][c] = -(sum_{l=c}^{i-1} L[i][l] Linv[l][c]) / L[i][i]; stored at W[c][i]
+  double* dv = in_smem ? dinv_s : nullptr;
+  for (int i = tid; i < k; i += CHOL_T) {
+    const double d = 1.0 / W[(int64_t)i * k + i];
+    if (in_smem) dv[i] = d;
+    else Linv[(int64_t)i * k + i] = d;
   }
+  __syncthreads();
+  for (int i = 1; i < k; ++i) {
+    const double di = in_smem ? dv[i] : Linv[(int64_t)i * k + i];
+    for (int c = tid; c < i; c += CHOL_T) {
+      double s = W[(int64_t)i * k + c] * (in_smem ? dv[c] : Linv[(int64_t)c * k + c]);
+      for (int l = c + 1; l < i; ++l) s += W[(int64_t)i * k + l] * W[(int64_t)c * k + l];
+      W[(int64_t)c * k + i] = -s * di;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < k * k; e += CHOL_T) {
+    const int i = e / k, c = e % k;
+    double v = 0.0;
+    if (c < i) v = W[(int64_t)c * k + i];
+    else if (c == i) v = in_smem ? dv[i] : Linv[(int64_t)i * k + i];
+    if (in_smem || c != i) Linv[e] = v;
+  }
+  (void)dinv;
 }
 
 // ============================================================================ Philox sketch
@@ -407,29 +434,60 @@ static cudaError_t sumsq(const T* X, int64_t rows, int64_t cols, int64_t ld, dou
   return e;
 }
 
+static cudaError_t chol_inv(int k, const double* G, double* W, double* Li, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         CHOL_SMEM_K * CHOL_SMEM_K * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0, 0.0, nullptr);
+  const size_t sm = k <= CHOL_SMEM_K ? sizeof(double) * k * k : 0;
+  chol_inv_kernel<<<1, CHOL_T, sm, st>>>(k, G, W, Li);
+  return cudaGetLastError();
+}
+
 // ============================================================================ orth(Y) by CholeskyQR2
 // Y (m x k, FP32) -> Q (m x k, FP32 with orthonormal columns, same span).
+// Each pass: G = Y^T Y accumulated in FP64, G + sI = L L^T and L^{-1} in FP64 (one CTA),
+// then Y <- Y L^{-T} with the FP32 GEMM.  Any invertible triangular factor keeps span(Y);
+// the FP32 rounding of the apply only costs orthogonality, which the second pass restores.
+__global__ void d2f_kernel(const double* __restrict__ x, float* __restrict__ y, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
 static cudaError_t cholqr2(int64_t m, int k, const float* Y, float* Q, cudaStream_t st) {
-  double *G = nullptr, *W = nullptr, *L = nullptr, *Li = nullptr, *Q1 = nullptr;
+  double *G = nullptr, *W = nullptr, *Li = nullptr;
+  float *Lf = nullptr, *Q1 = nullptr;
   cudaError_t e = cudaSuccess;
-  auto al = [&](double** p, size_t n) {
-    if (e == cudaSuccess) e = dev_alloc((void**)p, sizeof(double) * n, st);
+  auto al = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = dev_alloc(p, bytes, st);
   };
-  al(&G, (size_t)k * k);
-  al(&W, (size_t)k * k);
-  al(&L, (size_t)k * k);
-  al(&Li, (size_t)k * k);
-  al(&Q1, (size_t)m * k);
-  if (e == cudaSuccess) e = dgemm_small<true, false>((int)k, k, (int)m, Y, k, Y, k, G, k, st);  // Y^T Y
-  if (e == cudaSuccess) { AMM_TRACE("chol_inv", st); chol_inv_kernel<<<1, 1024, 0, st>>>(k, G, W, L, Li); e = cudaGetLastError(); }
-  if (e == cudaSuccess) e = dgemm_small<false, true>((int)m, k, k, Y, k, Li, k, Q1, k, st);  // Y Linv^T
-  if (e == cudaSuccess) e = dgemm_small<true, false>((int)k, k, (int)m, Q1, k, Q1, k, G, k, st);
-  if (e == cudaSuccess) { AMM_TRACE("chol_inv", st); chol_inv_kernel<<<1, 1024, 0, st>>>(k, G, W, L, Li); e = cudaGetLastError(); }
-  if (e == cudaSuccess) e = dgemm_small<false, true>((int)m, k, k, Q1, k, Li, k, Q, k, st);
+  al((void**)&G, sizeof(double) * k * k);
+  al((void**)&W, sizeof(double) * k * k);
+  al((void**)&Li, sizeof(double) * k * k);
+  al((void**)&Lf, sizeof(float) * k * k);
+  al((void**)&Q1, sizeof(float) * m * k);
+  const float* src = Y;
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+    float* dst = pass == 0 ? Q1 : Q;
+    e = dgemm_small<true, false>((int)k, k, (int)m, src, k, src, k, G, k, st);  // src^T src
+    if (e == cudaSuccess) e = chol_inv(k, G, W, Li, st);
+    if (e == cudaSuccess) {
+      AMM_TRACE("d2f", st);
+      d2f_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(Li, Lf, k * k);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = sgemm<float>(false, true, (int)m, k, k, 1.f, src, k, Lf, k, 0.f, dst, k, st);  // src Linv^T
+    src = dst;
+  }
   dev_free(G, st);
   dev_free(W, st);
-  dev_free(L, st);
   dev_free(Li, st);
+  dev_free(Lf, st);
   dev_free(Q1, st);
   return e;
 }
