@@ -170,6 +170,28 @@ amm_status_t amm_handle_get_sketch(amm_handle_t h, float* host_phi, int64_t cap)
 amm_status_t amm_handle_destroy(amm_handle_t h);
 
 /*
+ * Cycle spectrum and component keys of one square FP32 matrix WITHOUT allocating device memory.
+ * The paper has no counterpart: this is an interface for callers that cannot call cudaMalloc,
+ * e.g. code running while a framework captures a CUDA graph and forbids allocation there, or a
+ * process whose device memory is owned entirely by another allocator.  It computes what
+ * amm_decompose(..., AMM_CIRCULANT, ...) computes first (Alg. 2 and Alg. 3 Step 2):
+ *   R     DEVICE output, (n/2+1) x n complex64 (interleaved float pairs), row k = R_A[k],
+ *         16-byte aligned; caller-owned
+ *   keys  DEVICE output, n doubles, keys[t] = ||R_A[t]||_2 (t and n-t bit-identical)
+ *   A     DEVICE input, n x n FP32 row-major, leading dimension lda >= n
+ *   n     power of two in [16, AMM_NOALLOC_MAX_N]; larger n returns AMM_ERR_UNSUPPORTED_SIZE
+ * Its scratch (twiddles and per-block partial sums) is a fixed AMM_NOALLOC_SCRATCH_BYTES array
+ * in device memory that every GPU loading the library holds until the process exits.  The
+ * first call on a device looks up that array's address (cudaGetSymbolAddress) with the device
+ * current: make that first call before any stream capture.  All calls share the array, so
+ * calls that overlap on the GPU race; issue them in order on one stream.
+ */
+#define AMM_NOALLOC_MAX_N 4096
+#define AMM_NOALLOC_SCRATCH_BYTES 4456448
+amm_status_t amm_circulant_spectrum_noalloc(const float* A, int64_t n, int64_t lda, void* R,
+                                            double* keys, void* stream);
+
+/*
  * Launch tracing for measurement.  While enabled, every kernel launch the library makes is
  * bracketed by two CUDA events on the launch's own stream.  amm_trace_collect() waits for
  * the recorded launches, writes a JSON object {"kernel name": [launches, total_ms], ...} of

@@ -63,6 +63,8 @@ SIGNATURES = {
     "amm_handle_get_sketch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
     "amm_handle_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "amm_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int32]),
+    "amm_circulant_spectrum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "amm_trace_enable": (ctypes.c_int, [ctypes.c_int32]),
     "amm_trace_collect": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
 }

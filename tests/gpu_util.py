@@ -27,7 +27,10 @@ def as64(t):
 
 
 def rel(x, ref):
-    return float(np.linalg.norm(np.asarray(x, dtype=np.float64) - ref) / max(np.linalg.norm(ref), 1e-300))
+    """Relative Frobenius error; complex arrays stay complex."""
+    x = np.asarray(x)
+    x = x.astype(np.complex128) if np.iscomplexobj(x) else x.astype(np.float64)
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
 
 
 def check_selection(gpu_sel, keys, k, what=""):
