@@ -4,8 +4,8 @@
 Workload (n = 4096, FP32, synthetic): A, B = Q1 diag(i^-1.5) Q2^T + N(0, 1e-4) noise (Haar Q from
 QR of N(0,1), i = 1..n).  One step = the whole hot path over that pair for every product of
 the sweep: decompose A and B, evaluate Re(A~ B + dA B~), and run the backward where the method
-has one.  The metric is effective throughput: the FLOPs of the exact products the step stands
-for (2 n^3 per forward, 4 n^3 per backward) divided by the step time.
+has one (every method here).  The metric is effective throughput: the FLOPs of the exact
+products the step stands for (2 n^3 per forward, 4 n^3 per backward) divided by the step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amm|reference]
 
@@ -35,10 +35,13 @@ import synth  # noqa: E402
 METRIC = "effective 2n³/t TFLOP/s at ≤1% rel. error; BF16/batched vs plain FP32 fwd+bwd"
 UNIT = "TFLOP/s"
 N = 4096
-# (method, k, backward) -- the sweep of the n = 4096 workload
-PRODUCTS = [("circulant", 16, False), ("circulant", 64, False), ("circulant", 256, False),
-            ("svd", 32, True), ("svd", 128, True)]
+# (method, k, backward) -- the sweep of the n = 4096 workload; the sparsifiers keep the top 1%
+# (k = ceil(0.01 n) = 41 frequencies per row / column, or 41 cycles)
+K_SPARSE = math.ceil(0.01 * N)
+PRODUCTS = [("circulant", 16, True), ("circulant", 64, True), ("circulant", 256, True),
+            ("svd", 32, True), ("svd", 128, True), ("fourier", K_SPARSE, True), ("cycle", K_SPARSE, True)]
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x 2 (FMA) x max SM clock
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate
 
 
 def peaks():
@@ -135,6 +138,7 @@ def run_amm(args, rank, world, local_rank):
         import torch.distributed as tdist
 
     def step(A, B, outs=None):
+        grads = []
         for i, (method, k, bwd) in enumerate(PRODUCTS):
             sa, sb = PH[k] if method == "svd" else (None, None)
             hA = amm.decompose(A, method, k, "left", sketch=sa)
@@ -142,9 +146,10 @@ def run_amm(args, rank, world, local_rank):
             out = C if outs is None else outs[i]
             amm.approx_matmul(hA, hB, out=out)
             if bwd:
-                amm.approx_matmul_backward(hA, hB, G)
+                grads += list(amm.approx_matmul_backward(hA, hB, G))
             hA.close()
             hB.close()
+        return grads
 
     # accuracy of every product of the step against the exact FP64 product (outside timing)
     exact = (A.double() @ B.double())
@@ -195,11 +200,14 @@ def run_amm(args, rank, world, local_rank):
     A2 = torch.empty_like(A)
     B2 = torch.empty_like(B)
 
+    n_bwd = sum(1 for _, _, bwd in PRODUCTS if bwd)
+    grads_h = [torch.empty((N, N), dtype=torch.float32).pin_memory() for _ in range(2 * n_bwd)]
+
     def e2e_step():
         A2.copy_(a_h, non_blocking=True)
         B2.copy_(b_h, non_blocking=True)
-        step(A2, B2, outs)
-        for o, oh in zip(outs, outs_h):
+        grads = step(A2, B2, outs)
+        for o, oh in zip(outs + grads, outs_h + grads_h):
             oh.copy_(o, non_blocking=True)
 
     for _ in range(max(1, args.warmup // 2)):
@@ -226,7 +234,7 @@ def run_amm(args, rank, world, local_rank):
         "value": value, "ms_per_step": ms / args.steps, "errs": errs, "kernels": kernels,
         "launches": launches, "clocks": clocks, "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N * N * 4,
-                "d2h_bytes_per_step": len(PRODUCTS) * N * N * 4, "ms_per_step": e2e_ms / args.steps},
+                "d2h_bytes_per_step": (len(PRODUCTS) + 2 * n_bwd) * N * N * 4, "ms_per_step": e2e_ms / args.steps},
     }
 
 
@@ -236,21 +244,34 @@ NCU_TRAFFIC = {}
 
 
 def roofline(kernels, clocks):
-    """Roofline of the kernel that takes most of the timed region."""
+    """Roofline of the kernel that takes most of the timed region.
+
+    The bound is the resource the kernel's algorithmic work needs longest on: HBM bytes against
+    the measured copy bandwidth, or FLOPs against the pipe that executes them (FP32 FMA lanes for
+    SIMT kernels; the TF32 tensor rate / 3 for the TF32x3 GEMM, which issues three MMAs per
+    product).  Peaks for a kernel timed inside a long step: the sustained tensor figure.
+    """
     pk, src = peaks()
     name, (launches, ms, flops, bytes_) = max(kernels.items(), key=lambda kv: kv[1][1])
-    hbm_kernels = {"cd_spectrum", "cd_residual"}
-    if name in hbm_kernels:
+    hbm = pk["hbm_gbs"]
+    if name.startswith("umma_gemm_tf32"):
+        cpeak, cunit, cbound = pk["bf16_tflops_sustained"] * TF32_PER_BF16 / 3.0, "tensor", \
+            "%s: bf16_tflops_sustained x %.3f (nominal TF32:BF16) / 3 (TF32x3)" % (src, TF32_PER_BF16)
+    elif name.startswith("umma_gemm_bf16"):
+        cpeak, cunit, cbound = pk["bf16_tflops_sustained"], "tensor", "%s: bf16_tflops_sustained" % src
+    else:
+        cpeak, cunit, cbound = FP32_ALU_PEAK, "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+    t_mem = bytes_ / (hbm * 1e9)
+    t_cmp = flops / (cpeak * 1e12)
+    base = {"kernel": name, "traffic": NCU_TRAFFIC.get(name), "launches": launches, "avg_launch_ms": ms / launches,
+            "algorithmic_bytes_per_launch": bytes_ / launches, "algorithmic_flops_per_launch": flops / launches}
+    if t_mem >= t_cmp:
         achieved = bytes_ / (ms * 1e-3) / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": NCU_TRAFFIC.get(name),
-                "launches": launches, "avg_launch_ms": ms / launches, "peak_source": src}
+        return dict(base, bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
+                    peak_source="%s: hbm_gbs" % src)
     achieved = flops / (ms * 1e-3) / 1e12
-    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK, "unit": "TFLOP/s",
-            "frac": achieved / FP32_ALU_PEAK, "traffic": NCU_TRAFFIC.get(name), "launches": launches,
-            "avg_launch_ms": ms / launches,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-            "algorithmic_bytes_per_launch": bytes_ / launches}
+    return dict(base, bound=cunit, achieved=achieved, peak=cpeak, unit="TFLOP/s", frac=achieved / cpeak,
+                peak_source=cbound)
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -295,8 +316,8 @@ def run_reference(args, rank):
 
 
 def config_block():
-    return {"workload": "powerlaw n=4096 FP32: A,B = Q1 diag(i^-1.5) Q2^T + N(0,1e-4); sweep circulant "
-                        "k=16/64/256 fwd, rSVD k=32/128 fwd+bwd",
+    return {"workload": "powerlaw n=4096 FP32: A,B = Q1 diag(i^-1.5) Q2^T + N(0,1e-4); fwd+bwd sweep: circulant "
+                        "k=16/64/256, rSVD k=32/128, Fourier and cycle sparsifiers top 1%% (k=%d)" % K_SPARSE,
             "n": N, "products": ["%s k=%d %s" % (m, k, "fwd+bwd" if b else "fwd") for m, k, b in PRODUCTS],
             "l2": "no flush: each step touches ~2 GB (inputs, spectra, residuals, GEMM panels) > 129 MB L2",
             "parallelism": "replicas"}

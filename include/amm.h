@@ -142,9 +142,18 @@ amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, float* C, int64
  * Gradients of L = <dC, Re M> with the truncation frozen (selections, Q factors and
  * masks held fixed; M is then bilinear in A and B):
  *     dA = Re[ dC B~^T + P_A'(dC dB^T) ],   dB = Re[ A~^T dC + P_B'(dA^T dC) ]
- * where P' is the adjoint projector onto the kept components.
+ * where P' is the adjoint projector onto the kept components.  Per method:
+ *   AMM_SVD             P(X) = Q Q^T X; every term is a thin GEMM.
+ *   AMM_CIRCULANT       P' keeps the components S-bar = {n - t : t in S} (the bilinear adjoint
+ *                       of R_t D^t is R_{n-t} D^{n-t}); a component of dC dB^T or dA^T dC is
+ *                       sampled from column / row spectra (an SDDMM over the kept t only).
+ *   AMM_SPARSE_CYCLE    P' keeps the selected cycles (self-adjoint).
+ *   AMM_SPARSE_FOURIER  dA = Re[(dC B~_a^T + P_A(dC dB~^T)) conj(W)],
+ *                       dB = Re[W (A~_a^T dC + P_B(dA~^T dC))]  with the element masks P_A, P_B
+ *                       (Alg. 5 differentiated with the masks frozen).
  *   dC  device m x p FP32 (lddc).  dA (m x n, ldda) and dB (n x p, lddb) are overwritten;
- *   either may be NULL to skip it.
+ *   either may be NULL to skip it.  AMM_CIRCULANT additionally needs dB 8-byte aligned with
+ *   an even lddb.
  */
 amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const float* dC,
                                         int64_t lddc, float* dA, int64_t ldda, float* dB,
@@ -192,6 +201,26 @@ amm_status_t amm_circulant_spectrum_noalloc(const float* A, int64_t n, int64_t l
                                             double* keys, void* stream);
 
 /*
+ * Batches of independent products of uneven sizes (e.g. the layers of an LLM-shaped stack).
+ * amm_batch_add records one product C = Re(A~ B + dA B~) (A m x n, B n x p, device pointers,
+ * caller-owned; the same method, k and element type for both operands; opts_a / opts_b may be
+ * NULL, their role is set by the batch).  amm_batch_run executes every item -- decompose both
+ * operands, product, release -- on a pool of streams forked from `stream` and joined back into
+ * it.  With use_graph != 0 the first run executes the items once eagerly and then records the
+ * same work into one CUDA graph; that run and every later run launch the graph.  Pointers and
+ * sizes are baked into the graph: rerun with the same buffers (their contents may change).
+ * After the first graph run no item can be added.
+ */
+typedef struct amm_batch* amm_batch_t;
+amm_status_t amm_batch_create(amm_batch_t* out);
+amm_status_t amm_batch_add(amm_batch_t batch, const void* A, const void* B, float* C, int64_t m,
+                           int64_t n, int64_t p, int64_t lda, int64_t ldb, int64_t ldc,
+                           amm_dtype_t dtype, amm_method_t method, int64_t k,
+                           const amm_opts_t* opts_a, const amm_opts_t* opts_b);
+amm_status_t amm_batch_run(amm_batch_t batch, void* stream, int32_t use_graph);
+amm_status_t amm_batch_destroy(amm_batch_t batch);
+
+/*
  * Launch tracing for measurement.  While enabled, every kernel launch the library makes is
  * bracketed by two CUDA events on the launch's own stream.  amm_trace_collect() waits for
  * the recorded launches, writes a JSON object {"kernel name": [launches, total_ms], ...} of
@@ -200,6 +229,17 @@ amm_status_t amm_circulant_spectrum_noalloc(const float* A, int64_t n, int64_t l
  */
 amm_status_t amm_trace_enable(int32_t on);
 amm_status_t amm_trace_collect(char* host_json, int64_t cap, int64_t* launches);
+
+/*
+ * Test hook for the tensor-core GEMM used by the SVD path: C = alpha A B^T + beta C with
+ * A (M x K, lda) and B (N x K, ldb) row-major along K (device pointers), C (M x N, ldc) FP32.
+ * mode 1: A, B are BF16 (tcgen05 kind::f16, FP32 accumulation).  mode 0: A, B are FP32, split
+ * into TF32 hi/lo parts (three kind::tf32 products, FP32-level accuracy).  Rows of A and B
+ * must start 16-byte aligned.  *dev_err (device int) is set to 1 if a bounded wait gave up.
+ */
+amm_status_t amm_debug_gemm_tn(int32_t mode, int64_t M, int64_t N, int64_t K, float alpha,
+                               const void* A, int64_t lda, const void* B, int64_t ldb, float beta,
+                               float* C, int64_t ldc, int32_t* dev_err, void* stream);
 
 /*
  * Fault injection for tests: the n-th device allocation from now on (1-based) fails with

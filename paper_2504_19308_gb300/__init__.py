@@ -2,5 +2,5 @@
 
 Python front end of libamm (include/amm.h): arXiv 2504.19308, M = A~ B + dA B~.
 """
-from .amm import (AmmError, ApproxMatmulFn, Handle, approx_matmul, approx_matmul_autograd,  # noqa: F401
+from .amm import (AmmError, Batch, ApproxMatmulFn, Handle, approx_matmul, approx_matmul_autograd,  # noqa: F401
                   approx_matmul_backward, decompose, load_library, LIB_PATH)

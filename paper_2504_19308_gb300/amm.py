@@ -65,6 +65,17 @@ SIGNATURES = {
     "amm_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int32]),
     "amm_circulant_spectrum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "amm_debug_gemm_tn": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_float, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "amm_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p)]),
+    "amm_batch_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                     ctypes.POINTER(Opts), ctypes.POINTER(Opts)]),
+    "amm_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "amm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "amm_trace_enable": (ctypes.c_int, [ctypes.c_int32]),
     "amm_trace_collect": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -158,8 +169,11 @@ class Handle:
 
 
 def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: Optional[torch.Tensor] = None,
-              seed: int = 0, forced_selection=None) -> Handle:
-    """amm_decompose: truncated decomposition of A (method 'circulant' | 'svd' | 'fourier' | 'cycle')."""
+              seed: int = 0, forced_selection=None, compute: str = "f32") -> Handle:
+    """amm_decompose: truncated decomposition of A (method 'circulant' | 'svd' | 'fourier' | 'cycle').
+
+    compute: arithmetic of the SVD GEMMs, 'f32' (FP32-accurate) or 'bf16' (BF16 tensor cores).
+    """
     lib = load_library()
     _require_cuda(A, "A")
     if A.dtype not in DTYPES:
@@ -168,6 +182,7 @@ def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: 
     _check(lib.amm_opts_init(ctypes.byref(opts)), "amm_opts_init")
     opts.role = ROLES[role]
     opts.seed = seed
+    opts.compute = {"f32": 0, "bf16": 1}[compute]
     extras = []
     if sketch is not None:
         _require_cuda(sketch, "sketch")
@@ -229,6 +244,42 @@ class ApproxMatmulFn(torch.autograd.Function):
 
 def approx_matmul_autograd(A, B, method: str, k: int, sketch_a=None, sketch_b=None):
     return ApproxMatmulFn.apply(A, B, method, k, sketch_a, sketch_b)
+
+
+class Batch:
+    """amm_batch_*: many independent products run together, optionally as one CUDA graph."""
+
+    def __init__(self):
+        self.ptr = ctypes.c_void_p(0)
+        _check(load_library().amm_batch_create(ctypes.byref(self.ptr)), "amm_batch_create")
+        self.keep = []
+
+    def add(self, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, method: str, k: int,
+            sketch_a: Optional[torch.Tensor] = None, sketch_b: Optional[torch.Tensor] = None, compute: str = "f32"):
+        for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+            _require_cuda(t, nm)
+        oa, ob = Opts(), Opts()
+        lib = load_library()
+        _check(lib.amm_opts_init(ctypes.byref(oa)), "amm_opts_init")
+        _check(lib.amm_opts_init(ctypes.byref(ob)), "amm_opts_init")
+        oa.compute = ob.compute = {"f32": 0, "bf16": 1}[compute]
+        if sketch_a is not None:
+            oa.sketch = sketch_a.data_ptr()
+        if sketch_b is not None:
+            ob.sketch = sketch_b.data_ptr()
+        self.keep += [A, B, C, sketch_a, sketch_b]
+        _check(lib.amm_batch_add(self.ptr, A.data_ptr(), B.data_ptr(), C.data_ptr(), A.shape[0], A.shape[1],
+                                 B.shape[1], A.stride(0), B.stride(0), C.stride(0), DTYPES[A.dtype], METHODS[method],
+                                 k, ctypes.byref(oa), ctypes.byref(ob)), "amm_batch_add")
+
+    def run(self, use_graph: bool = True):
+        dev = self.keep[0].device
+        _check(load_library().amm_batch_run(self.ptr, _stream_ptr(dev), 1 if use_graph else 0), "amm_batch_run")
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            _check(load_library().amm_batch_destroy(self.ptr), "amm_batch_destroy")
+        self.ptr = None
 
 
 def trace_enable(on: bool = True):

@@ -3,6 +3,7 @@
 // file only validates, allocates (stream-ordered) and launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -161,6 +162,7 @@ static amm_status_t decompose_circulant(Handle* h, const amm_opts_t* o) {
   AL(c.so.wfull, sizeof(float) * n);
   AL(c.so.vfull, sizeof(float) * n);
   AL(c.so.counts, sizeof(int32_t) * 2);
+  AL(c.so.key2, sizeof(double) * n);
   AL(c.Lw, sizeof(float2) * (size_t)c.cap * n);
   AL(c.Ld, sizeof(float2) * (size_t)c.cap * n);
   if (h->role == AMM_RIGHT) {
@@ -225,6 +227,7 @@ static amm_status_t decompose_cycle(Handle* h, const amm_opts_t* o) {
   AL(c.so.wfull, sizeof(float) * n);
   AL(c.so.vfull, sizeof(float) * n);
   AL(c.so.counts, sizeof(int32_t) * 2);
+  AL(c.so.key2, sizeof(double) * n);
   AL(c.cyc, sizeof(float) * (size_t)h->k * n);
   AL(c.insel, (size_t)n);
   int32_t* forced = nullptr;
@@ -272,15 +275,13 @@ static amm_status_t decompose_fourier(Handle* h, const amm_opts_t* o) {
   AL(f.T, sizeof(float2) * kh * f.nvec);
   AL(f.mag, sizeof(float) * kh * f.nvec);
   AL(f.sel, sizeof(int32_t) * (size_t)h->k * f.nvec);
-  if (left) {
-    AL(f.TT, sizeof(float2) * kh * f.nvec);
-    AL(f.maskT, sizeof(uint32_t) * (size_t)f.n * f.mask_words);
-  }
+  if (left) AL(f.TT, sizeof(float2) * kh * f.nvec);
+  AL(f.maskT, sizeof(uint32_t) * (size_t)f.n * f.mask_words);
 #undef AL
   if ((e = ft_transform(f.n, left, (const float*)h->A, h->lda, f.nvec, f.tw, f.T, f.TT, f.mag, h->stream)) !=
       cudaSuccess)
     return cuda_fail(e, "ft_transform launch");
-  if ((e = ft_select(f.n, (int)h->k, f.nvec, f.mag, f.sel, left ? f.maskT : nullptr, f.mask_words, h->stream)) !=
+  if ((e = ft_select(f.n, (int)h->k, f.nvec, f.mag, f.sel, f.maskT, f.mask_words, h->stream)) !=
       cudaSuccess)
     return cuda_fail(e, "ft_select launch");
   return AMM_OK;
@@ -406,6 +407,73 @@ extern "C" amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, floa
   return fail(AMM_ERR_NOT_IMPLEMENTED, "method %d", a->method);
 }
 
+// Circulant backward (see cd_backward.cu for the formulas); every step is a kernel launch.
+static amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda,
+                                float* dB, int64_t lddb, cudaStream_t st) {
+  const int n = (int)a->rows;
+  auto &ca = a->cd, &cb = b->cd;
+  const float2* tw = ca.tw;
+  if (dB && (((lddb & 1) != 0) || ((uintptr_t)dB & 7) != 0))
+    return fail(AMM_ERR_INVALID_ARG, "circulant backward: dB must be 8-byte aligned with an even lddb");
+  const size_t kh = (size_t)n / 2 + 1;
+  std::vector<void*> tmp;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(&q, bytes, st);
+    if (q) tmp.push_back(q);
+    return q;
+  };
+  float2* X1 = (float2*)al(sizeof(float2) * kh * n);
+  float2* X2 = (float2*)al(sizeof(float2) * kh * n);
+  float2* RX = (float2*)al(sizeof(float2) * kh * n);
+  float2* K = (float2*)al(sizeof(float2) * (size_t)std::max(ca.cap, cb.cap) * n);
+  float* T = dB ? (float*)al(sizeof(float) * (size_t)n * n) : nullptr;
+  auto clear_rx = [&]() {
+    if (e == cudaSuccess) e = cudaMemsetAsync(RX, 0, sizeof(float2) * kh * n, st);
+  };
+#define STEP(x) \
+  if (e == cudaSuccess) e = (x)
+  if (dA) {
+    // G B~_w^T (rows of G, coefficient L^B_s(p)), then the projection terms of G dB^T
+    STEP(cd_apply(n, true, G, ldg, false, n, tw, cb.so.ulist, cb.Lw, cb.so.counts, nullptr, nullptr, dA, ldda, 0, st, 0));
+    STEP(bw_spectrum(n, false, G, ldg, tw, X1, st));
+    STEP(bw_spectrum(n, false, cb.resid, n, tw, X2, st));
+    STEP(cd_sddmm(n, X1, X2, ca.so.ulist, ca.so.counts, ca.cap, K, nullptr, nullptr, st));
+    clear_rx();
+    STEP(cd_rho(n, K, tw, ca.so.ulist, ca.so.counts, ca.cap, RX, nullptr, nullptr, st));
+    STEP(cd_residual(n, RX, tw, ca.so.wfull, 2, nullptr, dA, st, ldda, 1));
+    // unpaired: (i v_t) R_t(G V_B^T) D^t, only when both selections split a pair (device gates)
+    STEP(bw_spectrum(n, false, cb.imag, n, tw, X2, st));
+    clear_rx();
+    STEP(cd_sddmm(n, X1, X2, ca.so.dlist, ca.so.counts + 1, ca.cap, K, ca.so.counts + 1, cb.so.counts + 1, st));
+    STEP(cd_rho(n, K, tw, ca.so.dlist, ca.so.counts + 1, ca.cap, RX, ca.so.counts + 1, cb.so.counts + 1, st));
+    STEP(cd_residual(n, RX, tw, ca.so.vfull, 3, ca.so.counts + 1, dA, st, ldda, 1));
+  }
+  if (dB) {
+    // A~_w^T G (columns of G, coefficient L^A_t(t - p)), then the projection terms of dA^T G
+    STEP(cd_apply(n, false, G, ldg, false, n, tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr, nullptr, dB, lddb, 0, st, 1));
+    STEP(bw_spectrum(n, true, G, ldg, tw, X1, st));
+    STEP(cd_residual(n, ca.R, tw, ca.so.wfull, 0, nullptr, T, st, n, 0));  // dA_w
+    STEP(bw_spectrum(n, true, T, n, tw, X2, st));
+    STEP(cd_sddmm(n, X2, X1, cb.so.ulist, cb.so.counts, cb.cap, K, nullptr, nullptr, st));
+    clear_rx();
+    STEP(cd_rho(n, K, tw, cb.so.ulist, cb.so.counts, cb.cap, RX, nullptr, nullptr, st));
+    STEP(cd_residual(n, RX, tw, cb.so.wfull, 2, nullptr, dB, st, lddb, 1));
+    // unpaired: (i v_s) R_s(Y_A^T G) D^s with Y_A = Im A~
+    STEP(cd_residual(n, ca.R, tw, ca.so.vfull, 1, ca.so.counts + 1, T, st, n, 0));
+    STEP(bw_spectrum(n, true, T, n, tw, X2, st));
+    clear_rx();
+    STEP(cd_sddmm(n, X2, X1, cb.so.dlist, cb.so.counts + 1, cb.cap, K, ca.so.counts + 1, cb.so.counts + 1, st));
+    STEP(cd_rho(n, K, tw, cb.so.dlist, cb.so.counts + 1, cb.cap, RX, ca.so.counts + 1, cb.so.counts + 1, st));
+    STEP(cd_residual(n, RX, tw, cb.so.vfull, 3, cb.so.counts + 1, dB, st, lddb, 1));
+  }
+#undef STEP
+  for (void* q : tmp) dev_free(q, st);
+  if (e != cudaSuccess) return cuda_fail(e, "circulant backward");
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const float* dC, int64_t lddc,
                                                    float* dA, int64_t ldda, float* dB, int64_t lddb, void* stream) {
   Handle* a = hA;
@@ -416,6 +484,38 @@ extern "C" amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t
   if (lddc < b->cols || (dA && ldda < a->cols) || (dB && lddb < b->cols))
     return fail(AMM_ERR_INVALID_ARG, "backward: leading dimension too small");
   if (a->method == AMM_SVD) return svd_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
+  if (a->method == AMM_CIRCULANT) return cd_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
+  if (a->method == AMM_SPARSE_CYCLE) {
+    cudaError_t e = cyc_backward((int)a->rows, (const float*)a->A, a->lda, (const float*)b->A, b->lda, a->cy.so.sel,
+                                 (int)a->k, a->cy.cyc, a->cy.insel, b->cy.so.sel, (int)b->k, b->cy.cyc, b->cy.insel,
+                                 dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cycle backward");
+    return AMM_OK;
+  }
+  if (a->method == AMM_SPARSE_FOURIER) {
+    FtBwArgs f;
+    f.n = a->ft.n;
+    f.m = (int)a->rows;
+    f.p = (int)b->cols;
+    f.ka = (int)a->k;
+    f.kb = (int)b->k;
+    f.tw = a->ft.tw;
+    f.AtT = a->ft.TT;
+    f.selA = a->ft.sel;
+    f.maskA = a->ft.maskT;
+    f.Bt = b->ft.T;
+    f.selB = b->ft.sel;
+    f.maskB = b->ft.maskT;
+    f.G = dC;
+    f.ldg = lddc;
+    f.dA = dA;
+    f.ldda = ldda;
+    f.dB = dB;
+    f.lddb = lddb;
+    cudaError_t e = ft_backward(f, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fourier backward");
+    return AMM_OK;
+  }
   return fail(AMM_ERR_NOT_IMPLEMENTED, "backward for method %d is not built yet", a->method);
 }
 

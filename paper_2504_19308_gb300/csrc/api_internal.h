@@ -42,7 +42,7 @@ struct amm_handle {
     float2* TT = nullptr;         // left: A~^T [n/2+1][m]
     float* mag = nullptr;         // [nvec][n/2+1] |.|^2
     int32_t* sel = nullptr;       // [nvec][k] kept frequencies, ascending
-    uint32_t* maskT = nullptr;    // left: [n][ceil(m/32)] kept-entry bits
+    uint32_t* maskT = nullptr;    // [n][ceil(nvec/32)] kept-entry bits (frequency-major)
   } ft;
 
   struct Svd {
@@ -50,6 +50,12 @@ struct amm_handle {
     float* Q = nullptr;      // rows x k, orthonormal columns spanning A phi
     float* X = nullptr;      // k x cols, Q^T A
     double* norms = nullptr; // ||A||_F^2, ||X||_F^2
+    // tensor-core path: K-major copies in the compute type E (FP32 for TF32X3, BF16)
+    bool tc = false, bf16 = false;
+    const void* Xe = nullptr;  // rows x cols (the input itself when it already fits)
+    int64_t ldxe = 0;
+    void *XTe = nullptr, *Qe = nullptr, *QTe = nullptr, *Ze = nullptr, *ZTe = nullptr;
+    int* err = nullptr;        // device flag: a bounded wait of a tensor-core kernel gave up
   } svd;
 
   void release();

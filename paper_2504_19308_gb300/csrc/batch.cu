@@ -1,0 +1,159 @@
+// Batches of independent first-order products of uneven sizes (for example the layers of an
+// LLM-shaped stack).  amm_batch_run executes every item (decompose A, decompose B, product,
+// release) on a small pool of streams forked from the caller's stream.  With use_graph the first
+// run executes eagerly once (building twiddle tables and setting kernel attributes, which must
+// not happen inside a capture), then captures the same work into one CUDA graph; every later
+// run is a single graph launch.  Device memory of the handles is stream-ordered, so inside the
+// graph it becomes graph allocation nodes.
+#include <cuda_runtime.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/amm.h"
+#include "api_internal.h"
+
+struct amm_batch {
+  struct Item {
+    const void* A;
+    const void* B;
+    float* C;
+    int64_t m, n, p, lda, ldb, ldc, k;
+    int dtype, method;
+    amm_opts_t oa, ob;
+  };
+  std::vector<Item> items;
+  int nstreams = 8;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;  // one per stream (join) + fork
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool captured = false;
+};
+
+using namespace amm;
+
+extern "C" amm_status_t amm_batch_create(amm_batch_t* out) {
+  if (!out) return fail(AMM_ERR_INVALID_ARG, "amm_batch_create: out is NULL");
+  amm_batch* b = new (std::nothrow) amm_batch();
+  if (!b) return fail(AMM_ERR_OOM, "amm_batch_create: host allocation");
+  *out = b;
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_batch_add(amm_batch_t b, const void* A, const void* B, float* C, int64_t m, int64_t n,
+                                      int64_t p, int64_t lda, int64_t ldb, int64_t ldc, amm_dtype_t dtype,
+                                      amm_method_t method, int64_t k, const amm_opts_t* opts_a,
+                                      const amm_opts_t* opts_b) {
+  if (!b || !A || !B || !C) return fail(AMM_ERR_INVALID_ARG, "amm_batch_add: NULL argument");
+  if (b->captured) return fail(AMM_ERR_STATE, "amm_batch_add: batch already captured into a graph");
+  if (m <= 0 || n <= 0 || p <= 0 || k <= 0 || lda < n || ldb < p || ldc < p)
+    return fail(AMM_ERR_INVALID_ARG, "amm_batch_add: bad sizes");
+  amm_batch::Item it;
+  it.A = A;
+  it.B = B;
+  it.C = C;
+  it.m = m;
+  it.n = n;
+  it.p = p;
+  it.lda = lda;
+  it.ldb = ldb;
+  it.ldc = ldc;
+  it.k = k;
+  it.dtype = dtype;
+  it.method = method;
+  amm_opts_init(&it.oa);
+  amm_opts_init(&it.ob);
+  if (opts_a) it.oa = *opts_a;
+  if (opts_b) it.ob = *opts_b;
+  it.oa.role = AMM_LEFT;
+  it.ob.role = AMM_RIGHT;
+  if (it.oa.forced_selection || it.ob.forced_selection)
+    return fail(AMM_ERR_INVALID_ARG, "amm_batch_add: forced selections are not supported in batches");
+  b->items.push_back(it);
+  return AMM_OK;
+}
+
+static amm_status_t run_items(amm_batch* b, cudaStream_t parent) {
+  cudaError_t e;
+  if (b->streams.empty()) {
+    for (int i = 0; i < b->nstreams; ++i) {
+      cudaStream_t s;
+      if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "batch stream");
+      b->streams.push_back(s);
+    }
+    for (int i = 0; i <= b->nstreams; ++i) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "batch event");
+      b->events.push_back(ev);
+    }
+  }
+  // fork: every worker stream waits for the parent
+  cudaEvent_t fork = b->events[b->nstreams];
+  if ((e = cudaEventRecord(fork, parent)) != cudaSuccess) return cuda_fail(e, "batch fork");
+  for (cudaStream_t s : b->streams)
+    if ((e = cudaStreamWaitEvent(s, fork, 0)) != cudaSuccess) return cuda_fail(e, "batch fork wait");
+  amm_status_t st = AMM_OK;
+  for (size_t i = 0; i < b->items.size() && st == AMM_OK; ++i) {
+    auto& it = b->items[i];
+    cudaStream_t s = b->streams[i % b->streams.size()];
+    amm_handle_t ha = nullptr, hb = nullptr;
+    st = amm_decompose(it.A, it.m, it.n, it.lda, (amm_dtype_t)it.dtype, (amm_method_t)it.method, it.k, &it.oa, s, &ha);
+    if (st == AMM_OK)
+      st = amm_decompose(it.B, it.n, it.p, it.ldb, (amm_dtype_t)it.dtype, (amm_method_t)it.method, it.k, &it.ob, s, &hb);
+    if (st == AMM_OK) st = amm_approx_matmul(ha, hb, it.C, it.ldc, s);
+    if (ha) amm_handle_destroy(ha);
+    if (hb) amm_handle_destroy(hb);
+  }
+  // join: the parent waits for every worker stream
+  for (int i = 0; i < b->nstreams; ++i) {
+    if ((e = cudaEventRecord(b->events[i], b->streams[i])) != cudaSuccess) return cuda_fail(e, "batch join");
+    if ((e = cudaStreamWaitEvent(parent, b->events[i], 0)) != cudaSuccess) return cuda_fail(e, "batch join wait");
+  }
+  return st;
+}
+
+extern "C" amm_status_t amm_batch_run(amm_batch_t b, void* stream, int32_t use_graph) {
+  if (!b) return fail(AMM_ERR_INVALID_ARG, "amm_batch_run: NULL batch");
+  cudaStream_t parent = (cudaStream_t)stream;
+  if (!use_graph) return run_items(b, parent);
+  cudaError_t e;
+  if (!b->captured) {
+    amm_status_t st = run_items(b, parent);  // eager pass: tables, attributes, allocator pool warm
+    if (st != AMM_OK) return st;
+    if ((e = cudaStreamSynchronize(parent)) != cudaSuccess) return cuda_fail(e, "batch warm-up");
+    cudaStream_t cap = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "capture stream");
+    if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_fail(e, "batch capture");
+    }
+    st = run_items(b, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (st != AMM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch end capture");
+    if ((e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "batch instantiate");
+    }
+    b->graph = g;
+    b->captured = true;
+  }
+  if ((e = cudaGraphLaunch(b->exec, parent)) != cudaSuccess) return cuda_fail(e, "batch graph launch");
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_batch_destroy(amm_batch_t b) {
+  if (!b) return fail(AMM_ERR_INVALID_ARG, "amm_batch_destroy: NULL batch");
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto ev : b->events) cudaEventDestroy(ev);
+  delete b;
+  return AMM_OK;
+}

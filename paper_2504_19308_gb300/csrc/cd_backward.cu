@@ -1,0 +1,223 @@
+// Backward of the circulant first-order product with the selections frozen (sm_103a).
+//
+// With S the selection of A (weights w, unpaired coefficients v as in the forward) and G the
+// upstream gradient, the gradients of <G, Re M> are (bilinear adjoint of P_S is P_{S-bar}):
+//   dA = G B~_w^T + sum_{t in S u S-bar} w_t R_t(G dB_w^T) D^t + sum_{t unpaired} (i v_t) R_t(G V_B^T) D^t
+//   dB = A~_w^T G + sum_{s} w_s R_s(dA_w^T G) D^s + sum_{s unpaired} (i v_s) R_s(Y_A^T G) D^s
+// where dB_w = B - Re B~, V_B = Im B~, dA_w = A - Re A~, Y_A = Im A~.  The first terms are spectral
+// applies with the adjoint coefficient pairing.  A component of a product matrix is an SDDMM on
+// spectra: with column spectra Xh = F X, Yh = F Y (DFT along the row index),
+//   r_{j,t}(X Y^T) = (1/n^2) sum_p e^{2 pi i p j/n} K_t(p),   K_t(p) = sum_m Xh(p, m) Yh(t - p, m),
+// and for X^T Y the same with row spectra stored transposed ([frequency][row]).  Real products
+// have Hermitian component spectra, so only t <= n/2 is formed; the dense result comes from the
+// inverse cycle transform (cd_residual) with the coefficient w_t or i v_t.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+#include "trace.h"
+
+namespace amm {
+
+// ============================================================================ half spectra
+// COL: Xh[q][c] = sum_r e^{-2 pi i q r/n} X(r, c);  ROW: Xh[q][r] = sum_c e^{-2 pi i q c/n} X(r, c).
+// Output layout [q][vector], q = 0..n/2.  Packed pairs of real vectors per complex FFT.
+template <int N, int S, int NT, bool ROW>
+__global__ void __launch_bounds__(NT) bw_spectrum_kernel(const float* __restrict__ X, int64_t ldx,
+                                                         const float2* __restrict__ tw, float2* __restrict__ Xh) {
+  extern __shared__ float2 smem[];
+  constexpr int LD = fft_padded_len(N);
+  constexpr int KH = N / 2 + 1;
+  const int base = blockIdx.x * 2 * S;
+  for (int e = threadIdx.x; e < N * S; e += NT) {
+    int s, l;
+    if (ROW) { s = e / N; l = e % N; } else { l = e / S; s = e % S; }
+    const int v0 = base + 2 * s;
+    float x0, x1;
+    if (ROW) { x0 = __ldg(X + (int64_t)v0 * ldx + l); x1 = __ldg(X + (int64_t)(v0 + 1) * ldx + l); }
+    else { x0 = __ldg(X + (int64_t)l * ldx + v0); x1 = __ldg(X + (int64_t)l * ldx + v0 + 1); }
+    smem[s * LD + fpad(l)] = make_float2(x0, x1);
+  }
+  __syncthreads();
+  fft_smem<N, S, NT, false>(smem, tw);
+  for (int e = threadIdx.x; e < KH * 2 * S; e += NT) {
+    const int q = e / (2 * S), m = e % (2 * S);
+    const float2* z = smem + (m >> 1) * LD;
+    const float2 a = z[fpad(q)];
+    const float2 b = cconj(z[fpad((N - q) & (N - 1))]);
+    float2 x;
+    if ((m & 1) == 0) x = cscale(cadd(a, b), 0.5f);
+    else { float2 d = csub(a, b); x = make_float2(0.5f * d.y, -0.5f * d.x); }
+    Xh[(int64_t)q * N + base + m] = x;
+  }
+}
+
+// ============================================================================ SDDMM on spectra
+// K[u][p] = sum_m Xh(p, m) Yh((t_u - p) mod n, m) for t_u <= n/2, p = 0..n-1.  Half-spectrum rows
+// q > n/2 are conj(row n - q).  One warp per (p, block of SD_UB listed components); lanes stride
+// over m, so each Xh element is loaded once for SD_UB products (9 bytes per complex MAC instead
+// of 16) and the SD_UB independent loads of Yh overlap.
+constexpr int SD_UB = 8;
+template <int N>
+__global__ void __launch_bounds__(256) cd_sddmm_kernel(const float2* __restrict__ Xh, const float2* __restrict__ Yh,
+                                                       const int32_t* __restrict__ list,
+                                                       const int32_t* __restrict__ count, float2* __restrict__ K,
+                                                       const int32_t* __restrict__ gate0,
+                                                       const int32_t* __restrict__ gate1) {
+  if (gate0 != nullptr && (*gate0 == 0 || *gate1 == 0)) return;
+  const int cnt = *count;
+  const int u0 = blockIdx.y * SD_UB;
+  if (u0 >= cnt) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * 8 + warp;
+  const bool xm = p > N / 2;
+  const float2* xr = Xh + (int64_t)(xm ? N - p : p) * N;
+  const float xs = xm ? -1.f : 1.f;
+  const float2* yr[SD_UB];
+  float ys[SD_UB];
+  bool act[SD_UB];
+#pragma unroll
+  for (int j = 0; j < SD_UB; ++j) {
+    const int u = u0 + j;
+    const int t = u < cnt ? __ldg(list + u) : N;
+    act[j] = t <= N / 2;
+    const int q = (t - p) & (N - 1);
+    const bool ym = q > N / 2;
+    yr[j] = Yh + (int64_t)(ym ? N - q : q) * N;
+    ys[j] = ym ? -1.f : 1.f;
+  }
+  float2 acc[SD_UB];
+#pragma unroll
+  for (int j = 0; j < SD_UB; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int m = lane; m < N; m += 32) {
+    float2 x = __ldg(xr + m);
+    x.y *= xs;
+#pragma unroll
+    for (int j = 0; j < SD_UB; ++j) {
+      if (!act[j]) continue;  // warp-uniform
+      float2 y = __ldg(yr[j] + m);
+      y.y *= ys[j];
+      cmac(acc[j], x, y);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < SD_UB; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[j].x += __shfl_xor_sync(0xffffffffu, acc[j].x, o);
+      acc[j].y += __shfl_xor_sync(0xffffffffu, acc[j].y, o);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < SD_UB; ++j)
+      if (act[j]) K[(int64_t)(u0 + j) * N + p] = acc[j];
+  }
+}
+
+// ============================================================================ component spectra
+// RX[t][j] = (1/n^2) sum_p e^{2 pi i p j/n} K[u][p] for t = list[u] <= n/2 (RX zeroed beforehand).
+template <int N, int NT>
+__global__ void __launch_bounds__(NT) cd_rho_kernel(const float2* __restrict__ K, const float2* __restrict__ tw,
+                                                    const int32_t* __restrict__ list, const int32_t* __restrict__ count,
+                                                    float2* __restrict__ RX, const int32_t* __restrict__ gate0,
+                                                    const int32_t* __restrict__ gate1) {
+  extern __shared__ float2 smem[];
+  const int u = blockIdx.x;
+  if (u >= *count) return;
+  if (gate0 != nullptr && (*gate0 == 0 || *gate1 == 0)) return;
+  const int t = list[u];
+  if (t > N / 2) return;
+  for (int p = threadIdx.x; p < N; p += NT) smem[fpad(p)] = K[(int64_t)u * N + p];
+  __syncthreads();
+  fft_smem<N, 1, NT, true>(smem, tw);
+  const float sc = 1.0f / ((float)N * (float)N);
+  for (int j = threadIdx.x; j < N; j += NT) RX[(int64_t)t * N + j] = cscale(smem[fpad(j)], sc);
+}
+
+// ============================================================================ launchers
+template <int N> struct BwCfg {
+  static constexpr int S = (N >= 8192) ? 2 : 4;
+  static constexpr int NT = (N >= 512) ? 512 : N;
+  static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
+  static constexpr int NT1 = (N >= 1024) ? 256 : (N >= 64 ? 64 : N);
+};
+
+template <int N> struct BwOps {
+  using C = BwCfg<N>;
+  static cudaError_t attrs() {
+    static cudaError_t e = [] {
+      cudaError_t r = cudaFuncSetAttribute((const void*)bw_spectrum_kernel<N, C::S, C::NT, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute((const void*)bw_spectrum_kernel<N, C::S, C::NT, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute((const void*)cd_rho_kernel<N, C::NT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float2) * fft_padded_len(N)));
+      return r;
+    }();
+    return e;
+  }
+  static cudaError_t spectrum(bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh, cudaStream_t st) {
+    cudaError_t e = attrs();
+    if (e != cudaSuccess) return e;
+    dim3 grid(N / (2 * C::S));
+    if (row) bw_spectrum_kernel<N, C::S, C::NT, true><<<grid, C::NT, C::SMEM, st>>>(X, ldx, tw, Xh);
+    else bw_spectrum_kernel<N, C::S, C::NT, false><<<grid, C::NT, C::SMEM, st>>>(X, ldx, tw, Xh);
+    return cudaGetLastError();
+  }
+  static cudaError_t sddmm(const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
+                           float2* K, const int32_t* g0, const int32_t* g1, cudaStream_t st) {
+    dim3 grid(N / 8, (cap + SD_UB - 1) / SD_UB);
+    cd_sddmm_kernel<N><<<grid, 256, 0, st>>>(Xh, Yh, list, count, K, g0, g1);
+    return cudaGetLastError();
+  }
+  static cudaError_t rho(const float2* K, const float2* tw, const int32_t* list, const int32_t* count, int cap,
+                         float2* RX, const int32_t* g0, const int32_t* g1, cudaStream_t st) {
+    cudaError_t e = attrs();
+    if (e != cudaSuccess) return e;
+    cd_rho_kernel<N, C::NT1><<<cap, C::NT1, sizeof(float2) * fft_padded_len(N), st>>>(K, tw, list, count, RX, g0,
+                                                                                        g1);
+    return cudaGetLastError();
+  }
+};
+
+#define AMM_BW_DISPATCH(n, EXPR)                  \
+  switch (n) {                                    \
+    case 16: { constexpr int NN = 16; EXPR; }     \
+    case 32: { constexpr int NN = 32; EXPR; }     \
+    case 64: { constexpr int NN = 64; EXPR; }     \
+    case 128: { constexpr int NN = 128; EXPR; }   \
+    case 256: { constexpr int NN = 256; EXPR; }   \
+    case 512: { constexpr int NN = 512; EXPR; }   \
+    case 1024: { constexpr int NN = 1024; EXPR; } \
+    case 2048: { constexpr int NN = 2048; EXPR; } \
+    case 4096: { constexpr int NN = 4096; EXPR; } \
+    case 8192: { constexpr int NN = 8192; EXPR; } \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+cudaError_t bw_spectrum(int n, bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh, cudaStream_t st) {
+  AMM_TRACE_W(row ? "bw_row_spectrum" : "bw_col_spectrum", st, 0.0, (double)n * n * 4 + (n / 2 + 1.0) * n * 8,
+              nullptr);
+  AMM_BW_DISPATCH(n, return BwOps<NN>::spectrum(row, X, ldx, tw, Xh, st));
+}
+
+cudaError_t cd_sddmm(int n, const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
+                     float2* K, const int32_t* gate0, const int32_t* gate1, cudaStream_t st) {
+  // work per listed component (those with t <= n/2 are formed, about half): n dot products of
+  // length n, 8 FLOP per complex MAC
+  AMM_TRACE_W("cd_sddmm", st, 4.0 * n * (double)n, 0.0, count);
+  AMM_BW_DISPATCH(n, return BwOps<NN>::sddmm(Xh, Yh, list, count, cap, K, gate0, gate1, st));
+}
+
+cudaError_t cd_rho(int n, const float2* K, const float2* tw, const int32_t* list, const int32_t* count, int cap,
+                   float2* RX, const int32_t* gate0, const int32_t* gate1, cudaStream_t st) {
+  AMM_TRACE("cd_rho", st);
+  AMM_BW_DISPATCH(n, return BwOps<NN>::rho(K, tw, list, count, cap, RX, gate0, gate1, st));
+}
+
+}  // namespace amm

@@ -140,7 +140,25 @@ __device__ double block_sum(double v, double* red) {
 
 // Circulant keys (mirror = 1): partial rows hold t = 0..n/2, T[n-t] = T[t], ||A||^2 = n sum T^2.
 // Cycle keys (mirror = 0): partial rows hold all n cycles, ||A||^2 = sum T^2 (scale = 1).
-__global__ void __launch_bounds__(SEL_T) cd_select_kernel(const float* __restrict__ kpart, int nparts, int n,
+// key2[t] = sum_c part[c][t] over the partial rows in a fixed order: 32 x 32 threads per CTA,
+// thread (x, y) sums rows y, y+32, ..., then row 0 of the tile adds the 32 column sums in order.
+__global__ void __launch_bounds__(1024) cd_keyreduce_kernel(const float* __restrict__ part, int nparts, int kh,
+                                                            double* __restrict__ key2) {
+  __shared__ double sm[32][33];
+  const int t = blockIdx.x * 32 + threadIdx.x;
+  double s = 0.0;
+  if (t < kh)
+    for (int c = threadIdx.y; c < nparts; c += 32) s += (double)part[(int64_t)c * kh + t];
+  sm[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && t < kh) {
+    double v = 0.0;
+    for (int y = 0; y < 32; ++y) v += sm[y][threadIdx.x];
+    key2[t] = v;
+  }
+}
+
+__global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restrict__ key2, int n,
                                                           int k, const int32_t* __restrict__ forced,
                                                           SelectOut out, int mirror, double scale) {
   extern __shared__ unsigned char sm[];
@@ -154,8 +172,7 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const float* __restric
   __shared__ double s_kth, s_next;
   const int kh = mirror ? n / 2 + 1 : n;
   for (int t = threadIdx.x; t < kh; t += SEL_T) {
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += (double)kpart[(int64_t)c * kh + t];
+    const double s = key2[t];
     key[t] = s;
     if (mirror && t > 0 && t < n - t) key[n - t] = s;
   }
@@ -331,13 +348,16 @@ __global__ void __launch_bounds__(NT) cd_eigen_kernel(const float2* __restrict__
 // For cycles j0..j0+J-1: Lambda_j(c) = sum_k g_k r_{j,k} omega^{k c}, with g_k = 1 - w_k (mode 0,
 // gfull = w, giving dB_w) or g_k = -i v_k (mode 1, gfull = v, giving V = Im B~_S).
 // Writes X((c+j) mod n, c).
+// Modes: 0 coefficient 1 - g, 1 coefficient -i g, 2 coefficient g, 3 coefficient +i g (the last two
+// serve the backward); accumulate adds into X (leading dimension ldx).  Modes 1 and 3 return early
+// when *dcount is zero (no unpaired component).
 template <int N, int S, int NT>
 __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restrict__ R, const float2* __restrict__ tw,
                                                          const float* __restrict__ gfull, int mode,
                                                          const int32_t* __restrict__ dcount,
-                                                         float* __restrict__ X) {
+                                                         float* __restrict__ X, int64_t ldx, int accumulate) {
   extern __shared__ float2 smem[];
-  if (mode == 1 && *dcount == 0) return;
+  if ((mode & 1) && dcount != nullptr && *dcount == 0) return;
   constexpr int J = 2 * S;
   constexpr int LD = fft_padded_len(N);
   const int j0 = blockIdx.x * J;
@@ -351,7 +371,12 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
     if (mir) { r1 = cconj(r1); r2 = cconj(r2); }
     float2 z = make_float2(r1.x - r2.y, r1.y + r2.x);
     const float g = gfull[k];
-    z = (mode == 0) ? cscale(z, 1.f - g) : make_float2(g * z.y, -g * z.x);  // (1 - w_k) or -i v_k
+    switch (mode) {
+      case 0: z = cscale(z, 1.f - g); break;                   // (1 - w_k)
+      case 1: z = make_float2(g * z.y, -g * z.x); break;       // -i v_k
+      case 2: z = cscale(z, g); break;                         // w_k
+      default: z = make_float2(-g * z.y, g * z.x); break;      // +i v_k
+    }
     smem[s * LD + fpad(k)] = z;
   }
   __syncthreads();
@@ -361,7 +386,9 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
     const int r = e / J, q = e % J;
     const int c = (r - j0 - (J - 1) + q) & (N - 1);
     const int m = J - 1 - q;
-    X[(int64_t)r * N + c] = fs[2 * ((m >> 1) * LD + fpad(c)) + (m & 1)];
+    const float v = fs[2 * ((m >> 1) * LD + fpad(c)) + (m & 1)];
+    float* o = X + (int64_t)r * ldx + c;
+    *o = accumulate ? *o + v : v;
   }
 }
 
@@ -370,7 +397,9 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
 // ROW: out(r0..r0+2S, :) (+)= rows of X times (sum_s c_s R_s D^s).
 // Packed pairs of real columns/rows form complex signals; the output pair comes out of one
 // inverse FFT as (real, imag).  Coefficients Lc[u][p] = c_u L_{t_u}(p) (c conjugate-symmetric).
-template <int N, int S, int NT, bool ROW, typename T>
+// REV selects the coefficient index: L_u((t_u - p) mod n) (REV) or L_u(p).  The forward product
+// uses REV = ROW; the backward's adjoint applies use the other pairing.
+template <int N, int S, int NT, bool ROW, bool REV, typename T>
 __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, int64_t ldx,
                                                       const float2* __restrict__ tw,
                                                       const int32_t* __restrict__ list, const float2* __restrict__ Lc,
@@ -398,7 +427,7 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
     }
   }
   __syncthreads();
-  fft_smem<N, S, NT, false>(smem, tw);
+  fft_smem<N, S, NT, false, true>(smem, tw);  // spectrum left unpadded: shifted reads below
   float2 acc[PT][S];
 #pragma unroll
   for (int i = 0; i < PT; ++i)
@@ -411,8 +440,8 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
 #pragma unroll
     for (int i = 0; i < PT; ++i) {
       const int p = threadIdx.x + i * NT;
-      const float2 l = __ldg(lrow + (ROW ? ((t - p) & (N - 1)) : p));
-      const int q = fpad((p - t) & (N - 1));
+      const float2 l = __ldg(lrow + (REV ? ((t - p) & (N - 1)) : p));
+      const int q = (p - t) & (N - 1);
 #pragma unroll
       for (int s = 0; s < S; ++s) cmac(acc[i][s], l, smem[s * LD + q]);
     }
@@ -463,10 +492,12 @@ template <int N> static cudaError_t set_smem_attrs() {
   s((const void*)cd_spectrum_kernel<N, C::S, C::NT, float>, C::SMEM);
   s((const void*)cd_spectrum_kernel<N, C::S, C::NT, __nv_bfloat16>, C::SMEM);
   s((const void*)cd_residual_kernel<N, C::S, C::NT>, C::SMEM);
-  s((const void*)cd_apply_kernel<N, C::S, C::NT, false, float>, C::SMEM);
-  s((const void*)cd_apply_kernel<N, C::S, C::NT, true, float>, C::SMEM);
-  s((const void*)cd_apply_kernel<N, C::S, C::NT, true, __nv_bfloat16>, C::SMEM);
-  s((const void*)cd_apply_kernel<N, C::S, C::NT, false, __nv_bfloat16>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, false, false, float>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, true, true, float>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, true, true, __nv_bfloat16>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, false, false, __nv_bfloat16>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, false, true, float>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S, C::NT, true, false, float>, C::SMEM);
   s((const void*)cd_eigen_kernel<N, CdCfg<N>::NT1>, sizeof(float2) * fft_padded_len(N));
   return e;
 }
@@ -496,33 +527,38 @@ template <int N> struct CdOps {
     return cudaGetLastError();
   }
   static cudaError_t residual(const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
-                              float* X, cudaStream_t st) {
+                              float* X, int64_t ldx, int accumulate, cudaStream_t st) {
     static cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
-    cd_residual_kernel<N, C::S, C::NT><<<N / (2 * C::S), C::NT, C::SMEM, st>>>(R, tw, g, mode, dcount, X);
+    cd_residual_kernel<N, C::S, C::NT><<<N / (2 * C::S), C::NT, C::SMEM, st>>>(R, tw, g, mode, dcount, X, ldx,
+                                                                              accumulate);
     return cudaGetLastError();
   }
   static cudaError_t apply(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
                            const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
-                           const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st) {
+                           const int32_t* gate1, float* out, int64_t ldo, int accumulate, int rev, cudaStream_t st) {
     static cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
     dim3 grid((unsigned)(nvec / (2 * C::S)));
-    if (row) {
-      if (bf16)
-        cd_apply_kernel<N, C::S, C::NT, true, __nv_bfloat16><<<grid, C::NT, C::SMEM, st>>>(
-            (const __nv_bfloat16*)X, ldx, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate);
-      else
-        cd_apply_kernel<N, C::S, C::NT, true, float><<<grid, C::NT, C::SMEM, st>>>(
-            (const float*)X, ldx, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate);
+    const bool r = rev < 0 ? row : rev != 0;
+#define AMM_APPLY_LAUNCH(ROW_, REV_, T_)                                                                    \
+  cd_apply_kernel<N, C::S, C::NT, ROW_, REV_, T_><<<grid, C::NT, C::SMEM, st>>>((const T_*)X, ldx, tw, list, Lc, \
+                                                                                count, gate0, gate1, out, ldo,  \
+                                                                                accumulate)
+    if (row && r) {
+      if (bf16) AMM_APPLY_LAUNCH(true, true, __nv_bfloat16);
+      else AMM_APPLY_LAUNCH(true, true, float);
+    } else if (!row && !r) {
+      if (bf16) AMM_APPLY_LAUNCH(false, false, __nv_bfloat16);
+      else AMM_APPLY_LAUNCH(false, false, float);
+    } else if (row) {
+      if (bf16) return cudaErrorInvalidValue;
+      AMM_APPLY_LAUNCH(true, false, float);
     } else {
-      if (bf16)
-        cd_apply_kernel<N, C::S, C::NT, false, __nv_bfloat16><<<grid, C::NT, C::SMEM, st>>>(
-            (const __nv_bfloat16*)X, ldx, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate);
-      else
-        cd_apply_kernel<N, C::S, C::NT, false, float><<<grid, C::NT, C::SMEM, st>>>(
-            (const float*)X, ldx, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate);
+      if (bf16) return cudaErrorInvalidValue;
+      AMM_APPLY_LAUNCH(false, true, float);
     }
+#undef AMM_APPLY_LAUNCH
     return cudaGetLastError();
   }
 };
@@ -560,7 +596,6 @@ cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const floa
 
 cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_t* forced, const SelectOut& o,
                       cudaStream_t st, bool mirror) {
-  AMM_TRACE("cd_select", st);
   auto bytes = [](int nn) {
     return (size_t)nn * (sizeof(double) + 1) + 8 + (size_t)SEL_SORT_MAX * (sizeof(double) + sizeof(int32_t));
   };
@@ -571,8 +606,15 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  cd_select_kernel<<<1, SEL_T, bytes(n), st>>>(kpart, nparts, n, k, forced, o, mirror ? 1 : 0,
-                                               mirror ? (double)n : 1.0);
+  const int kh = mirror ? n / 2 + 1 : n;
+  {
+    AMM_TRACE("cd_keyreduce", st);
+    cd_keyreduce_kernel<<<(kh + 31) / 32, dim3(32, 32), 0, st>>>(kpart, nparts, kh, o.key2);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  AMM_TRACE("cd_select", st);
+  cd_select_kernel<<<1, SEL_T, bytes(n), st>>>(o.key2, n, k, forced, o, mirror ? 1 : 0, mirror ? (double)n : 1.0);
   return cudaGetLastError();
 }
 
@@ -583,20 +625,21 @@ cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* li
 }
 
 cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
-                        float* X, cudaStream_t st) {
-  AMM_TRACE_W(mode == 0 ? "cd_residual" : "cd_residual_imag", st, 0.0,
-              mode == 0 ? (n / 2 + 1.0) * n * 8 + (double)n * n * 4 : 0.0, nullptr);
-  AMM_DISPATCH_N(n, return CdOps<NN>::residual(R, tw, g, mode, dcount, X, st));
+                        float* X, cudaStream_t st, int64_t ldx, int accumulate) {
+  if (ldx <= 0) ldx = n;
+  AMM_TRACE_W(mode == 0 ? "cd_residual" : (mode == 1 ? "cd_residual_imag" : "cd_project"), st, 0.0,
+              (mode & 1) ? 0.0 : (n / 2 + 1.0) * n * 8 + (double)n * n * 4 * (accumulate ? 2 : 1), nullptr);
+  AMM_DISPATCH_N(n, return CdOps<NN>::residual(R, tw, g, mode, dcount, X, ldx, accumulate, st));
 }
 
 cudaError_t cd_apply(int n, bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
                      const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
-                     const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st) {
+                     const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st, int rev) {
   // work: 8 flops per complex MAC, n frequencies x nvec/2 packed signals per applied component
   AMM_TRACE_W(gate0 ? "cd_apply_unpaired" : (row ? "cd_apply_row" : "cd_apply_col"), st, 4.0 * n * (double)nvec,
               (double)n * nvec * (bf16 ? 2 : 4) + (double)n * nvec * 4 * (accumulate ? 2 : 1), count);
   AMM_DISPATCH_N(n, return CdOps<NN>::apply(row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out, ldo,
-                                            accumulate, st));
+                                            accumulate, rev, st));
 }
 
 }  // namespace amm

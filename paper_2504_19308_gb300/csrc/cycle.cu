@@ -111,6 +111,145 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __re
   }
 }
 
+// ============================================================================ backward (selections frozen)
+//   dA = G B_s^T + P_{S_A}(G dB^T),   dB = A_s^T G + P_{S_B}(dA^T G)
+// (G B_s^T)(r, q) = sum_{s in S_B} G(r, q - s) Lambda^B_s(q - s)           (row panels)
+// (A_s^T G)(q, c) = sum_{t in S_A} Lambda^A_t(q) G(q + t, c)               (column panels)
+// P_S keeps the cycles t in S: P_{S_A}(G dB^T)((l + t), l) = <G(l + t, :), dB(l, :)>,
+// P_{S_B}(dA^T G)((l + s), l) = <dA(:, l + s), G(:, l)>; dA, dB are masked on the fly.
+
+// out(r0..r0+3, q) = sum_u G(r, q - s_u) cycB[u][q - s_u]
+__global__ void __launch_bounds__(CYC_NT) cyc_bw_row_kernel(const float* __restrict__ G, int64_t ldg, int n,
+                                                            const int32_t* __restrict__ selB, int kb,
+                                                            const float* __restrict__ cycB, float* __restrict__ out,
+                                                            int64_t ldo) {
+  extern __shared__ float gr[];  // CYC_RW x n
+  const int r0 = blockIdx.x * CYC_RW;
+  for (int e = threadIdx.x; e < CYC_RW * n; e += CYC_NT) gr[e] = __ldg(G + (int64_t)(r0 + e / n) * ldg + e % n);
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += CYC_NT) {
+    float acc[CYC_RW] = {0.f, 0.f, 0.f, 0.f};
+    for (int u = 0; u < kb; ++u) {
+      const int l = (q - __ldg(selB + u)) & (n - 1);
+      const float b = __ldg(cycB + (int64_t)u * n + l);
+#pragma unroll
+      for (int rr = 0; rr < CYC_RW; ++rr) acc[rr] = fmaf(gr[rr * n + l], b, acc[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < CYC_RW; ++rr) out[(int64_t)(r0 + rr) * ldo + q] = acc[rr];
+  }
+}
+
+// out(q, c0..c0+3) = sum_u cycA[u][q] G(q + t_u, c)
+__global__ void __launch_bounds__(CYC_NT) cyc_bw_col_kernel(const float* __restrict__ G, int64_t ldg, int n,
+                                                            const int32_t* __restrict__ selA, int ka,
+                                                            const float* __restrict__ cycA, float* __restrict__ out,
+                                                            int64_t ldo) {
+  extern __shared__ float4 gp[];  // n x 4 columns
+  const int c0 = blockIdx.x * CYC_CW;
+  for (int r = threadIdx.x; r < n; r += CYC_NT) {
+    const float* src = G + (int64_t)r * ldg + c0;
+    gp[r] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += CYC_NT) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < ka; ++u) {
+      const float a = __ldg(cycA + (int64_t)u * n + q);
+      const float4 g = gp[(q + __ldg(selA + u)) & (n - 1)];
+      acc.x = fmaf(a, g.x, acc.x);
+      acc.y = fmaf(a, g.y, acc.y);
+      acc.z = fmaf(a, g.z, acc.z);
+      acc.w = fmaf(a, g.w, acc.w);
+    }
+    float* o = out + (int64_t)q * ldo + c0;
+    o[0] = acc.x;
+    o[1] = acc.y;
+    o[2] = acc.z;
+    o[3] = acc.w;
+  }
+}
+
+// dA((l + t), l) += <G(l + t, :), dB(l, :)> for t in S_A; one warp per (u, l)
+__global__ void __launch_bounds__(256) cyc_bw_proj_rows_kernel(const float* __restrict__ G, int64_t ldg,
+                                                               const float* __restrict__ B, int64_t ldb, int n,
+                                                               const int32_t* __restrict__ selA,
+                                                               const unsigned char* __restrict__ inselB,
+                                                               float* __restrict__ dA, int64_t ldda) {
+  const int u = blockIdx.y;
+  const int t = selA[u];
+  const int l = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const float* g = G + (int64_t)((l + t) & (n - 1)) * ldg;
+  const float* b = B + (int64_t)l * ldb;
+  float acc = 0.f;
+  for (int m = lane; m < n; m += 32)
+    if (!inselB[(l - m) & (n - 1)]) acc = fmaf(__ldg(g + m), __ldg(b + m), acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) dA[(int64_t)((l + t) & (n - 1)) * ldda + l] += acc;
+}
+
+// dB((l + s), l) += sum_r dA(r, l + s) G(r, l) for s in S_B; thread per l, loop over r
+__global__ void __launch_bounds__(256) cyc_bw_proj_cols_kernel(const float* __restrict__ A, int64_t lda,
+                                                               const float* __restrict__ G, int64_t ldg, int n,
+                                                               const int32_t* __restrict__ selB,
+                                                               const unsigned char* __restrict__ inselA,
+                                                               float* __restrict__ dB, int64_t lddb) {
+  const int u = blockIdx.y;
+  const int s = selB[u];
+  const int l = blockIdx.x * 256 + threadIdx.x;
+  if (l >= n) return;
+  const int q = (l + s) & (n - 1);
+  float acc = 0.f;
+  for (int r = 0; r < n; ++r) {
+    const float a = inselA[(r - q) & (n - 1)] ? 0.f : __ldg(A + (int64_t)r * lda + q);
+    acc = fmaf(a, __ldg(G + (int64_t)r * ldg + l), acc);
+  }
+  dB[(int64_t)q * lddb + l] += acc;
+}
+
+cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int64_t ldb, const int32_t* selA, int ka,
+                         const float* cycA, const unsigned char* inselA, const int32_t* selB, int kb,
+                         const float* cycB, const unsigned char* inselB, const float* G, int64_t ldg, float* dA,
+                         int64_t ldda, float* dB, int64_t lddb, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)cyc_bw_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         CYC_RW * 8192 * (int)sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)cyc_bw_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               8192 * (int)sizeof(float4));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaError_t e = cudaSuccess;
+  if (dA) {
+    {
+      AMM_TRACE_W("cyc_bw_row", st, 2.0 * kb * (double)n * n, 8.0 * n * (double)n, nullptr);
+      cyc_bw_row_kernel<<<n / CYC_RW, CYC_NT, sizeof(float) * CYC_RW * n, st>>>(G, ldg, n, selB, kb, cycB, dA, ldda);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+      AMM_TRACE_W("cyc_bw_proj_rows", st, 2.0 * ka * (double)n * n, 8.0 * ka * (double)n * n, nullptr);
+      cyc_bw_proj_rows_kernel<<<dim3(n / 8, ka), 256, 0, st>>>(G, ldg, B, ldb, n, selA, inselB, dA, ldda);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (dB) {
+    {
+      AMM_TRACE_W("cyc_bw_col", st, 2.0 * ka * (double)n * n, 8.0 * n * (double)n, nullptr);
+      cyc_bw_col_kernel<<<n / CYC_CW, CYC_NT, sizeof(float4) * n, st>>>(G, ldg, n, selA, ka, cycA, dB, lddb);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+      AMM_TRACE_W("cyc_bw_proj_cols", st, 2.0 * kb * (double)n * n, 8.0 * kb * (double)n * n, nullptr);
+      cyc_bw_proj_cols_kernel<<<dim3((n + 255) / 256, kb), 256, 0, st>>>(A, lda, G, ldg, n, selB, inselA, dB, lddb);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 int cyc_rows_per_part(int n) { return n >= 1024 ? 64 : 16; }
 
 cudaError_t cyc_keys(int n, const float* A, int64_t lda, float* part, cudaStream_t st) {

@@ -104,7 +104,10 @@ template <int R, bool INV> AMM_DEV void dft_r(float2* v) {
 
 // ----------------------------------------------------------------------------- one Stockham pass
 // S signals of length N, signal s at buf + s * fft_padded_len(N), NT threads cooperating.
-template <int N, int R, int NS, int S, int NT, bool INV>
+// UNPAD_OUT: store the pass's output at plain (unpadded) indices.  Used for the last pass of a
+// transform whose result is read with arbitrary shifts (the stores of a last pass are contiguous
+// across threads, so they stay conflict-free without padding).
+template <int N, int R, int NS, int S, int NT, bool INV, bool UNPAD_OUT = false>
 AMM_DEV void stockham_pass(float2* buf, const float2* __restrict__ tw) {
   constexpr int NB = N / R;
   constexpr int TOT = NB * S;
@@ -142,31 +145,32 @@ AMM_DEV void stockham_pass(float2* buf, const float2* __restrict__ tw) {
       const int m = j & (NS - 1);
       const int base = (j / NS) * NS * R + m;
 #pragma unroll
-      for (int r = 0; r < R; ++r) y[fpad(base + r * NS)] = v[i][r];
+      for (int r = 0; r < R; ++r) y[UNPAD_OUT ? base + r * NS : fpad(base + r * NS)] = v[i][r];
     }
   }
   __syncthreads();
 }
 
-template <int N, int NS, int S, int NT, bool INV>
+template <int N, int NS, int S, int NT, bool INV, bool UNPAD_LAST>
 struct FftPasses {
   static AMM_DEV void run(float2* buf, const float2* __restrict__ tw) {
     constexpr int LEFT = N / NS;
     constexpr int R = (LEFT >= 16) ? 16 : LEFT;
-    stockham_pass<N, R, NS, S, NT, INV>(buf, tw);
-    FftPasses<N, NS * R, S, NT, INV>::run(buf, tw);
+    stockham_pass<N, R, NS, S, NT, INV, UNPAD_LAST && (NS * R == N)>(buf, tw);
+    FftPasses<N, NS * R, S, NT, INV, UNPAD_LAST>::run(buf, tw);
   }
 };
-template <int N, int S, int NT, bool INV>
-struct FftPasses<N, N, S, NT, INV> {
+template <int N, int S, int NT, bool INV, bool UNPAD_LAST>
+struct FftPasses<N, N, S, NT, INV, UNPAD_LAST> {
   static AMM_DEV void run(float2*, const float2* __restrict__) {}
 };
 
 // Transform S padded signals in place.  Must be called by all NT threads; ends with a barrier.
-template <int N, int S, int NT, bool INV>
+// With UNPAD_LAST the result is left at plain indices (signal s still starts at s * padded len).
+template <int N, int S, int NT, bool INV, bool UNPAD_LAST = false>
 AMM_DEV void fft_smem(float2* buf, const float2* __restrict__ tw) {
   static_assert((N & (N - 1)) == 0 && N >= 2, "power of two");
-  FftPasses<N, 1, S, NT, INV>::run(buf, tw);
+  FftPasses<N, 1, S, NT, INV, UNPAD_LAST>::run(buf, tw);
 }
 
 }  // namespace amm

@@ -7,7 +7,7 @@
 // magnitudes of q and n-q are the same number (exact tie, lower index first).
 //
 // HBM layout (kh = n/2 + 1):  At [m][kh] c64, AtT [kh][m] c64, magA [m][kh] f32,
-//   Bt [kh][p] c64, magBT [p][kh] f32, sel [rows][k] i32 (ascending q), maskT [n][ceil(m/32)] u32.
+//   Bt [kh][p] c64, magBT [p][kh] f32, sel [rows][k] i32 (ascending q), maskT [n][ceil(rows/32)] u32.
 #include <cuda_runtime.h>
 
 #include "common.cuh"

@@ -1,0 +1,283 @@
+// Backward of the Fourier-domain sparsified product (Section 2.4, Alg. 5) with the element masks
+// frozen, sm_103a.
+//
+// M = A~_a B~ + (A~ - A~_a) B~_a with A~ = A W^*, B~ = W B, W(p,q) = n^{-1/2} e^{-2 pi i pq/n};
+// P_A, P_B keep the selected entries.  For the upstream gradient G of C = Re(M):
+//   dA = Re[ (G B~_a^T + P_A(G dB~^T)) conj(W) ],   dB = Re[ W (A~_a^T G + P_B(dA~^T G)) ]
+// with dB~ = B~ - B~_a, dA~ = A~ - A~_a.  Each bracket is a sparse-times-dense product (the kept
+// entries of one operand) plus a sampled product on the kept entries of the other; neither forms
+// a dense n x n x p contraction.  The brackets live on the full frequency range q = 0..n-1 (the
+// masks need not be mirror-symmetric: ties between q and n-q keep the lower index), so the last
+// step takes the real part of a complex transform: Re F(X) = F(H) with the Hermitian part
+// H(q) = (X(q) + conj X(n-q)) / 2, two real outputs per complex FFT.
+//
+// Workspace (freed on the stream at the end):  GT [p][m] f32 (G transposed),
+//   XAT [n][m] c64 (dA bracket, frequency-major), XB [n][p] c64 (dB bracket).
+#include <cuda_runtime.h>
+
+#include "api_internal.h"
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+#include "trace.h"
+
+namespace amm {
+
+// B~(q, c) of a real B from the half spectrum Bt [n/2+1][p]
+__device__ __forceinline__ float2 half_spec(const float2* __restrict__ T, int n, int q, int64_t ld, int64_t col) {
+  const bool mir = q > n / 2;
+  float2 v = __ldg(T + (int64_t)(mir ? n - q : q) * ld + col);
+  if (mir) v.y = -v.y;
+  return v;
+}
+
+// ============================================================================ G B~_a^T
+// XAT[q][i] = sum over kept (q, c) of B~_a:  GT[c][i] B~(q, c).  The kept columns of frequency q
+// are the set bits of maskB[q]; every thread of the CTA walks the same words.
+__global__ void __launch_bounds__(256) ft_bw_gba_kernel(const float* __restrict__ GT, const float2* __restrict__ Bt,
+                                                        const uint32_t* __restrict__ maskB, int mwB, int n, int m,
+                                                        int p, float2* __restrict__ XAT) {
+  const int q = blockIdx.y;
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const uint32_t* mrow = maskB + (int64_t)q * mwB;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int w = 0; w < mwB; ++w) {
+    uint32_t bits = __ldg(mrow + w);
+    while (bits) {
+      const int c = w * 32 + __ffs(bits) - 1;
+      bits &= bits - 1;
+      const float2 b = half_spec(Bt, n, q, p, c);
+      const float g = i < m ? __ldg(GT + (int64_t)c * m + i) : 0.f;
+      acc.x = fmaf(g, b.x, acc.x);
+      acc.y = fmaf(g, b.y, acc.y);
+    }
+  }
+  if (i < m) XAT[(int64_t)q * m + i] = acc;
+}
+
+// ============================================================================ P_A(G dB~^T)
+// For each kept (i, q) of A~_a:  XAT[q][i] += sum_c G(i, c) B~(q, c) [(q, c) not kept in B~_a].
+// CTA per row i (G row shared through L1), warp per kept entry, lanes over c.
+__global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__ G, int64_t ldg,
+                                                       const float2* __restrict__ Bt, const uint32_t* __restrict__ maskB,
+                                                       int mwB, const int32_t* __restrict__ selA, int ka, int n, int m,
+                                                       int p, float2* __restrict__ XAT) {
+  const int i = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* grow = G + (int64_t)i * ldg;
+  for (int u = warp; u < ka; u += 8) {
+    const int q = __ldg(selA + (int64_t)i * ka + u);
+    const bool mir = q > n / 2;
+    const float2* brow = Bt + (int64_t)(mir ? n - q : q) * p;
+    const uint32_t* mrow = maskB + (int64_t)q * mwB;
+    float ax = 0.f, ay = 0.f;
+    for (int c = lane; c < p; c += 32) {
+      if ((__ldg(mrow + (c >> 5)) >> (c & 31)) & 1u) continue;  // kept in B~_a: not in dB~
+      const float g = __ldg(grow + c);
+      const float2 b = __ldg(brow + c);
+      ax = fmaf(g, b.x, ax);
+      ay = fmaf(g, b.y, ay);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) {
+      float2* x = XAT + (int64_t)q * m + i;
+      const float2 v = *x;
+      *x = make_float2(v.x + ax, v.y + (mir ? -ay : ay));
+    }
+  }
+}
+
+// ============================================================================ A~_a^T G
+// XB[q][c] = sum over kept (i, q) of A~_a:  A~(i, q) G(i, c); the kept rows of frequency q are the
+// set bits of maskA[q].
+__global__ void __launch_bounds__(256) ft_bw_aag_kernel(const float* __restrict__ G, int64_t ldg,
+                                                        const float2* __restrict__ AtT,
+                                                        const uint32_t* __restrict__ maskA, int mwA, int n, int m,
+                                                        int p, float2* __restrict__ XB) {
+  const int q = blockIdx.y;
+  const int c = blockIdx.x * 256 + threadIdx.x;
+  const uint32_t* mrow = maskA + (int64_t)q * mwA;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int w = 0; w < mwA; ++w) {
+    uint32_t bits = __ldg(mrow + w);
+    while (bits) {
+      const int i = w * 32 + __ffs(bits) - 1;
+      bits &= bits - 1;
+      const float2 a = half_spec(AtT, n, q, m, i);
+      const float g = c < p ? __ldg(G + (int64_t)i * ldg + c) : 0.f;
+      acc.x = fmaf(g, a.x, acc.x);
+      acc.y = fmaf(g, a.y, acc.y);
+    }
+  }
+  if (c < p) XB[(int64_t)q * p + c] = acc;
+}
+
+// ============================================================================ P_B(dA~^T G)
+// For each kept (q, c) of B~_a:  XB[q][c] += sum_i A~(i, q) [(i, q) not kept in A~_a] G(i, c).
+// CTA per column c (GT row shared through L1), warp per kept entry, lanes over i.
+__global__ void __launch_bounds__(256) ft_bw_pb_kernel(const float* __restrict__ GT, const float2* __restrict__ AtT,
+                                                       const uint32_t* __restrict__ maskA, int mwA,
+                                                       const int32_t* __restrict__ selB, int kb, int n, int m, int p,
+                                                       float2* __restrict__ XB) {
+  const int c = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* grow = GT + (int64_t)c * m;
+  for (int u = warp; u < kb; u += 8) {
+    const int q = __ldg(selB + (int64_t)c * kb + u);
+    const bool mir = q > n / 2;
+    const float2* arow = AtT + (int64_t)(mir ? n - q : q) * m;
+    const uint32_t* mrow = maskA + (int64_t)q * mwA;
+    float ax = 0.f, ay = 0.f;
+    for (int i = lane; i < m; i += 32) {
+      if ((__ldg(mrow + (i >> 5)) >> (i & 31)) & 1u) continue;  // kept in A~_a: not in dA~
+      const float g = __ldg(grow + i);
+      const float2 a = __ldg(arow + i);
+      ax = fmaf(g, a.x, ax);
+      ay = fmaf(g, a.y, ay);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) {
+      float2* x = XB + (int64_t)q * p + c;
+      const float2 v = *x;
+      *x = make_float2(v.x + ax, v.y + (mir ? -ay : ay));
+    }
+  }
+}
+
+// ============================================================================ real part of a transform
+// X [n][nvec] complex, frequency-major.  For each vector v: y_v(l) = n^{-1/2} Re sum_q X(q, v)
+// e^{-+2 pi i q l/n} (INV selects +).  Vectors v0, v0+1 share one complex FFT of
+// Z = H_{v0} + i H_{v1}.  OUT_ROW writes y_v to out[v][l], otherwise to out[l][v].
+template <int N, int S, int NT, bool INV, bool OUT_ROW>
+__global__ void __launch_bounds__(NT) ft_bw_real_kernel(const float2* __restrict__ X, int nvec,
+                                                        const float2* __restrict__ tw, float* __restrict__ out,
+                                                        int64_t ldo) {
+  extern __shared__ float2 smem[];
+  constexpr int LD = fft_padded_len(N);
+  const int base = blockIdx.x * 2 * S;
+  for (int e = threadIdx.x; e < (N / 2 + 1) * S; e += NT) {
+    const int q = e / S, s = e % S;
+    const int r = (N - q) & (N - 1);
+    const int v0 = base + 2 * s, v1 = v0 + 1;
+    float2 x0q = make_float2(0.f, 0.f), x0r = x0q, x1q = x0q, x1r = x0q;
+    if (v0 < nvec) { x0q = X[(int64_t)q * nvec + v0]; x0r = X[(int64_t)r * nvec + v0]; }
+    if (v1 < nvec) { x1q = X[(int64_t)q * nvec + v1]; x1r = X[(int64_t)r * nvec + v1]; }
+    // H(q) = (x(q) + conj x(r)) / 2, H(r) = conj H(q)
+    const float2 h0 = make_float2(0.5f * (x0q.x + x0r.x), 0.5f * (x0q.y - x0r.y));
+    const float2 h1 = make_float2(0.5f * (x1q.x + x1r.x), 0.5f * (x1q.y - x1r.y));
+    smem[s * LD + fpad(q)] = make_float2(h0.x - h1.y, h0.y + h1.x);  // h0 + i h1
+    smem[s * LD + fpad(r)] = make_float2(h0.x + h1.y, h1.x - h0.y);  // conj h0 + i conj h1
+  }
+  __syncthreads();
+  fft_smem<N, S, NT, INV>(smem, tw);
+  const float sc = rsqrtf((float)N);
+  for (int e = threadIdx.x; e < N * 2 * S; e += NT) {
+    int l, mm;
+    if (OUT_ROW) { mm = e / N; l = e % N; } else { l = e / (2 * S); mm = e % (2 * S); }
+    const int v = base + mm;
+    if (v >= nvec) continue;
+    const float2 z = smem[(mm >> 1) * LD + fpad(l)];
+    const float y = sc * ((mm & 1) ? z.y : z.x);
+    if (OUT_ROW) out[(int64_t)v * ldo + l] = y;
+    else out[(int64_t)l * ldo + v] = y;
+  }
+}
+
+template <int N> struct FtBwCfg {
+  static constexpr int S = (N >= 8192) ? 2 : 4;
+  static constexpr int NT = (N >= 512) ? 512 : N;
+  static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
+};
+
+template <int N> struct FtBwOps {
+  using C = FtBwCfg<N>;
+  template <bool INV, bool OUT_ROW>
+  static cudaError_t real(const float2* X, int nvec, const float2* tw, float* out, int64_t ldo, cudaStream_t st) {
+    static cudaError_t attr = cudaFuncSetAttribute((const void*)ft_bw_real_kernel<N, C::S, C::NT, INV, OUT_ROW>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((nvec + 2 * C::S - 1) / (2 * C::S));
+    ft_bw_real_kernel<N, C::S, C::NT, INV, OUT_ROW><<<grid, C::NT, C::SMEM, st>>>(X, nvec, tw, out, ldo);
+    return cudaGetLastError();
+  }
+  static cudaError_t inv_rows(const float2* X, int nvec, const float2* tw, float* out, int64_t ldo, cudaStream_t st) {
+    return real<true, true>(X, nvec, tw, out, ldo, st);
+  }
+  static cudaError_t fwd_cols(const float2* X, int nvec, const float2* tw, float* out, int64_t ldo, cudaStream_t st) {
+    return real<false, false>(X, nvec, tw, out, ldo, st);
+  }
+};
+
+#define AMM_FTB_DISPATCH(n, EXPR)                 \
+  switch (n) {                                    \
+    case 16: { constexpr int NN = 16; EXPR; }     \
+    case 32: { constexpr int NN = 32; EXPR; }     \
+    case 64: { constexpr int NN = 64; EXPR; }     \
+    case 128: { constexpr int NN = 128; EXPR; }   \
+    case 256: { constexpr int NN = 256; EXPR; }   \
+    case 512: { constexpr int NN = 512; EXPR; }   \
+    case 1024: { constexpr int NN = 1024; EXPR; } \
+    case 2048: { constexpr int NN = 2048; EXPR; } \
+    case 4096: { constexpr int NN = 4096; EXPR; } \
+    case 8192: { constexpr int NN = 8192; EXPR; } \
+    default: return cudaErrorInvalidValue;        \
+  }
+
+static cudaError_t ft_bw_real(int n, bool inv, const float2* X, int nvec, const float2* tw, float* out, int64_t ldo,
+                              cudaStream_t st) {
+  AMM_TRACE_W(inv ? "ft_bw_idft_rows" : "ft_bw_dft_cols", st, 0.0, (double)n * nvec * 12, nullptr);
+  if (inv) { AMM_FTB_DISPATCH(n, return FtBwOps<NN>::inv_rows(X, nvec, tw, out, ldo, st)); }
+  AMM_FTB_DISPATCH(n, return FtBwOps<NN>::fwd_cols(X, nvec, tw, out, ldo, st));
+}
+
+cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
+  const int n = a.n, m = a.m, p = a.p;
+  const int mwA = (m + 31) / 32, mwB = (p + 31) / 32;
+  float* GT = nullptr;
+  float2* XAT = nullptr;
+  float2* XB = nullptr;
+  cudaError_t e = dev_alloc((void**)&GT, sizeof(float) * (size_t)p * m, st);
+  if (e == cudaSuccess && a.dA) e = dev_alloc((void**)&XAT, sizeof(float2) * (size_t)n * m, st);
+  if (e == cudaSuccess && a.dB) e = dev_alloc((void**)&XB, sizeof(float2) * (size_t)n * p, st);
+  if (e == cudaSuccess) e = transpose_f32(a.G, m, p, a.ldg, GT, m, st);
+  if (e == cudaSuccess && a.dA) {
+    {
+      AMM_TRACE_W("ft_bw_gba", st, 4.0 * p * (double)a.kb * m, 4.0 * p * (double)a.kb * m + 8.0 * n * m, nullptr);
+      ft_bw_gba_kernel<<<dim3((m + 255) / 256, n), 256, 0, st>>>(GT, a.Bt, a.maskB, mwB, n, m, p, XAT);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      AMM_TRACE_W("ft_bw_pa", st, 4.0 * m * (double)a.ka * p, 12.0 * m * (double)a.ka * p, nullptr);
+      ft_bw_pa_kernel<<<m, 256, 0, st>>>(a.G, a.ldg, a.Bt, a.maskB, mwB, a.selA, a.ka, n, m, p, XAT);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = ft_bw_real(n, true, XAT, m, a.tw, a.dA, a.ldda, st);
+  }
+  if (e == cudaSuccess && a.dB) {
+    {
+      AMM_TRACE_W("ft_bw_aag", st, 4.0 * m * (double)a.ka * p, 4.0 * m * (double)a.ka * p + 8.0 * n * p, nullptr);
+      ft_bw_aag_kernel<<<dim3((p + 255) / 256, n), 256, 0, st>>>(a.G, a.ldg, a.AtT, a.maskA, mwA, n, m, p, XB);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      AMM_TRACE_W("ft_bw_pb", st, 4.0 * p * (double)a.kb * m, 12.0 * p * (double)a.kb * m, nullptr);
+      ft_bw_pb_kernel<<<p, 256, 0, st>>>(GT, a.AtT, a.maskA, mwA, a.selB, a.kb, n, m, p, XB);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = ft_bw_real(n, false, XB, p, a.tw, a.dB, a.lddb, st);
+  }
+  dev_free(GT, st);
+  dev_free(XAT, st);
+  dev_free(XB, st);
+  return e;
+}
+
+}  // namespace amm

@@ -17,6 +17,7 @@ struct SelectOut {
   float* wfull;     // n      w_t for every t (0 outside S u S-bar)
   float* vfull;     // n      v_t for every t
   int32_t* counts;  // 2      |S u S-bar|, |unpaired|
+  double* key2;     // n      scratch: reduced squared keys
 };
 
 int cd_cols_per_cta(int n);
@@ -27,11 +28,20 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
                       cudaStream_t st, bool mirror = true);
 cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* list, const float* coef,
                      const int32_t* count, int cap, int imag_coef, float2* L, cudaStream_t st);
+// inverse cycle transform of a (half) spectrum R with coefficients by mode (0: 1-g, 1: -i g,
+// 2: g, 3: +i g); writes or adds X((c+j) mod n, c), leading dimension ldx (0 = n)
 cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
-                        float* X, cudaStream_t st);
+                        float* X, cudaStream_t st, int64_t ldx = 0, int accumulate = 0);
+// cd_backward.cu
+cudaError_t bw_spectrum(int n, bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh, cudaStream_t st);
+cudaError_t cd_sddmm(int n, const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
+                     float2* K, const int32_t* gate0, const int32_t* gate1, cudaStream_t st);
+cudaError_t cd_rho(int n, const float2* K, const float2* tw, const int32_t* list, const int32_t* count, int cap,
+                   float2* RX, const int32_t* gate0, const int32_t* gate1, cudaStream_t st);
+// rev: coefficient index L((t - p) mod n) if 1, L(p) if 0, -1 = the forward pairing (rev = row)
 cudaError_t cd_apply(int n, bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
                      const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
-                     const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st);
+                     const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st, int rev = -1);
 
 // cycle.cu
 int cyc_rows_per_part(int n);
@@ -42,6 +52,10 @@ cudaError_t cyc_apply(int n, const float* A, int64_t lda, const float* B, int64_
                       const float* cycA, const unsigned char* inselA, const int32_t* selB, int kb, const float* cycB,
                       float* C, int64_t ldc, cudaStream_t st);
 
+cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int64_t ldb, const int32_t* selA, int ka,
+                         const float* cycA, const unsigned char* inselA, const int32_t* selB, int kb,
+                         const float* cycB, const unsigned char* inselB, const float* G, int64_t ldg, float* dA,
+                         int64_t ldda, float* dB, int64_t lddb, cudaStream_t st);
 // fourier.cu
 cudaError_t ft_transform(int n, bool row, const float* X, int64_t ldx, int nvec, const float2* tw, float2* T,
                          float2* TT, float* mag, cudaStream_t st);
@@ -50,5 +64,32 @@ cudaError_t ft_select(int n, int k, int rows, const float* mag, int32_t* sel, ui
 cudaError_t ft_product(int n, int m, int p, int k_a, int k_b, const float2* At, const float2* AtT,
                        const int32_t* selA, const uint32_t* maskT, int mask_words, const float2* Bt,
                        const int32_t* selB, float* C, int64_t ldc, cudaStream_t st);
+
+// ft_backward.cu: dA and/or dB (either may be NULL) of the frozen Fourier-domain product.
+struct FtBwArgs {
+  int n, m, p, ka, kb;
+  const float2* tw;      // e^{-2 pi i j/n}
+  const float2* AtT;     // A~^T half spectrum [n/2+1][m]
+  const int32_t* selA;   // [m][ka]
+  const uint32_t* maskA; // [n][ceil(m/32)]
+  const float2* Bt;      // B~ half spectrum [n/2+1][p]
+  const int32_t* selB;   // [p][kb]
+  const uint32_t* maskB; // [n][ceil(p/32)]
+  const float* G;        // upstream gradient m x p
+  int64_t ldg;
+  float* dA;             // m x n
+  int64_t ldda;
+  float* dB;             // n x p
+  int64_t lddb;
+};
+cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st);
+// svd.cu: Y (cols x rows, ldy) = X^T
+cudaError_t transpose_f32(const float* X, int64_t rows, int64_t cols, int64_t ldx, float* Y, int64_t ldy,
+                          cudaStream_t st);
+
+// umma_gemm.cu: C = alpha A B^T + beta C on tcgen05 tensor cores (A, B K-major);
+// tf32 = FP32 inputs with TF32 hi/lo splitting, else BF16 inputs.  err: device flag.
+cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void* A, int64_t lda, const void* B,
+                         int64_t ldb, float beta, float* C, int64_t ldc, int* err, cudaStream_t st);
 
 }  // namespace amm

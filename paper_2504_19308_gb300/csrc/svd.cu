@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "api_internal.h"
 #include "common.cuh"
@@ -123,15 +124,16 @@ __global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, float a
   }
 }
 
+// partial tiles summed in FP64 in a fixed order (deterministic; no error growth across chunks)
 __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ ws, float alpha, float beta,
                                      float* __restrict__ C, int64_t ldc) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)M * N) return;
   const int row = (int)(e / N), col = (int)(e % N);
-  float s = 0.f;
-  for (int z = 0; z < splits; ++z) s += ws[(int64_t)z * M * N + e];
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += (double)ws[(int64_t)z * M * N + e];
   float* c = C + (int64_t)row * ldc + col;
-  *c = (beta == 0.f) ? alpha * s : fmaf(alpha, s, beta * *c);
+  *c = (beta == 0.f) ? (float)(alpha * s) : (float)fma((double)alpha, s, (double)beta * *c);
 }
 
 static int g_num_sms = 0;
@@ -154,6 +156,9 @@ static cudaError_t sgemm(bool ta, bool tb, int M, int N, int K, float alpha, con
   int splits = 1;
   const int target = 2 * num_sms();
   if (tiles < target && K >= 256) splits = std::min((target + tiles - 1) / tiles, std::max(1, K / 128));
+  // long FP32 dot products dominate the rounding error of thin GEMMs: keep chunks <= 512 when
+  // the output is small enough for the partial tiles to be cheap
+  if ((int64_t)M * N <= (int64_t)2 << 20 && K > 512) splits = std::max(splits, (K + 511) / 512);
   splits = std::min(splits, 64);
   int kchunk = (K + splits - 1) / splits;
   kchunk = ((kchunk + GB_K - 1) / GB_K) * GB_K;
@@ -268,81 +273,159 @@ static cudaError_t dgemm_small(int M, int N, int K, const TA_t* A, int64_t lda, 
   return e;
 }
 
-// ============================================================================ Cholesky + inverse (FP64, one CTA)
+// ============================================================================ compensated Gram (FP32)
+// G = X^T X for X (m x k, FP32).  Each thread accumulates its dot products with error-free
+// transformations (TwoProduct via fma and TwoSum: Ogita, Rump, Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, Algorithm Dot2), so a partial is as accurate as if it had
+// been computed in twice FP32 precision.  K (= m) is split over grid.z; the partials (hi + lo,
+// widened to double) are summed in a fixed order and rounded to FP32.
+__global__ void __launch_bounds__(256) gram_dot2_kernel(int k, int m, const float* __restrict__ X, int kchunk,
+                                                        double* __restrict__ ws) {
+  __shared__ float xi[32][33];
+  __shared__ float xj[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int r0 = blockIdx.z * kchunk, r1 = min(m, r0 + kchunk);
+  const int ti = threadIdx.x >> 3, tj = (threadIdx.x & 7) * 4;  // (ti, tj..tj+3)
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int rb = r0; rb < r1; rb += 32) {
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int rr = e >> 5, cc = e & 31, r = rb + rr;
+      xi[rr][cc] = (r < r1 && i0 + cc < k) ? X[(int64_t)r * k + i0 + cc] : 0.f;
+      xj[rr][cc] = (r < r1 && j0 + cc < k) ? X[(int64_t)r * k + j0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const float a = xi[rr][ti];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // explicit _rn operations: the compiler must not fuse them into FMAs
+        const float b = xj[rr][tj + q];
+        const float p = __fmul_rn(a, b);
+        const float pe = fmaf(a, b, -p);                  // a*b = p + pe exactly
+        const float t = __fadd_rn(s[q], p);
+        const float z = __fsub_rn(t, s[q]);
+        const float se = __fadd_rn(__fsub_rn(s[q], __fsub_rn(t, z)), __fsub_rn(p, z));  // s + p = t + se
+        s[q] = t;
+        c[q] = __fadd_rn(c[q], __fadd_rn(pe, se));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + ti, j = j0 + tj + q;
+    if (i < k && j < k) ws[((int64_t)blockIdx.z * k + i) * k + j] = (double)s[q] + (double)c[q];
+  }
+}
+
+// G = sum of partials; with ns = 1 the output is -(G - I)/2 (Newton-Schulz correction factor),
+// formed from the double sum so that the small entries of G - I keep their accuracy.
+__global__ void gram_reduce_kernel(int k, int splits, const double* __restrict__ ws, float* __restrict__ G, int ns) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += ws[(int64_t)z * k * k + e];
+  if (ns) s = -0.5 * (s - ((e / k) == (e % k) ? 1.0 : 0.0));
+  G[e] = (float)s;
+}
+
+static cudaError_t gram_dot2(int64_t m, int k, const float* X, float* G, cudaStream_t st, int ns = 0) {
+  const int tiles = ((k + 31) / 32) * ((k + 31) / 32);
+  int splits = std::max(1, std::min((int)(m / 256), (2 * num_sms() + tiles - 1) / tiles));
+  int kchunk = (int)((m + splits - 1) / splits);
+  kchunk = ((kchunk + 31) / 32) * 32;
+  splits = std::max(1, (int)((m + kchunk - 1) / kchunk));
+  double* ws = nullptr;
+  cudaError_t e = dev_alloc((void**)&ws, sizeof(double) * (size_t)splits * k * k, st);
+  if (e != cudaSuccess) return e;
+  {
+    AMM_TRACE_W("gram_dot2", st, 2.0 * m * (double)k * k, 4.0 * m * (double)k, nullptr);
+    dim3 grid((k + 31) / 32, (k + 31) / 32, splits);
+    gram_dot2_kernel<<<grid, 256, 0, st>>>(k, (int)m, X, kchunk, ws);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    AMM_TRACE("gram_reduce", st);
+    gram_reduce_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, splits, ws, G, ns);
+    e = cudaGetLastError();
+  }
+  dev_free(ws, st);
+  return e;
+}
+
+// ============================================================================ Cholesky + inverse (FP32, one CTA)
 // G (k x k, symmetric positive semi-definite) -> Linv = L^{-1} with G + s I = L L^T,
-// s = 1e-15 trace(G) / k (keeps rank-deficient sketches factorisable; the second CholQR pass
-// restores orthonormality).  For k <= CHOL_SMEM_K the work matrix lives in shared memory:
-// L in the lower triangle, L^{-1} transposed in the strict upper triangle, 1/L_ii aside.
-// Larger k use the global scratch W the same way.
-constexpr int CHOL_SMEM_K = 128;
+// s = shift_rel * trace(G).  Shared memory holds W (k x k; L ends in its lower triangle), Linv
+// (k x k, row-major) and the current column of L, so every inner loop reads consecutive or
+// broadcast words (no bank conflicts).  One warp per row in the trailing update; the inverse is
+// built row by row (thread c forms Linv[i][c] from Linv[c..i-1][c]).  For k > CHOL_SMEM_K the
+// same arrays live in a global work area (2 k^2 + k floats).
+constexpr int CHOL_SMEM_K = 160;
 constexpr int CHOL_T = 1024;
 
-__global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const double* __restrict__ G,
-                                                          double* __restrict__ Wg, double* __restrict__ Linv) {
-  extern __shared__ double sW[];
-  __shared__ double dinv_s[CHOL_SMEM_K];
-  __shared__ double red[32];
-  __shared__ double shift_s;
-  const bool in_smem = k <= CHOL_SMEM_K;
-  double* W = in_smem ? sW : Wg;
-  double* dinv = in_smem ? dinv_s : Linv;  // global case: diagonal stashed in Linv's first row
-  const int tid = threadIdx.x;
-  double tr = 0.0;
+__global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const float* __restrict__ G, float shift_rel,
+                                                          float* __restrict__ Linv_out, float* __restrict__ gwork) {
+  extern __shared__ float sh_dyn[];
+  float* sh = (k <= CHOL_SMEM_K) ? sh_dyn : gwork;  // larger k: same layout in global memory
+  float* W = sh;              // k * k
+  float* Li = sh + k * k;     // k * k
+  float* col = Li + k * k;    // k
+  __shared__ float red[32];
+  __shared__ float shift_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float tr = 0.f;
   for (int i = tid; i < k; i += CHOL_T) tr += G[(int64_t)i * k + i];
   for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-  if ((tid & 31) == 0) red[tid >> 5] = tr;
+  if (lane == 0) red[warp] = tr;
   __syncthreads();
   if (tid == 0) {
-    double t = 0.0;
+    float t = 0.f;
     for (int w = 0; w < CHOL_T / 32; ++w) t += red[w];
-    shift_s = 1e-15 * t / k + 1e-300;
+    shift_s = fmaxf(shift_rel * t, 1e-30f);
   }
   __syncthreads();
-  const double shift = shift_s;
+  const float shift = shift_s;
   for (int e = tid; e < k * k; e += CHOL_T) {
-    const int i = e / k, j = e % k;
-    W[e] = G[e] + (i == j ? shift : 0.0);
+    const int i = e / k, j = e - i * k;
+    W[e] = G[e] + (i == j ? shift : 0.f);
+    Li[e] = 0.f;
   }
   __syncthreads();
-  // right-looking Cholesky, L overwrites the lower triangle
+  // right-looking Cholesky
   for (int j = 0; j < k; ++j) {
-    const double djj = sqrt(fmax(W[(int64_t)j * k + j], shift));
+    const float djj = sqrtf(fmaxf(W[j * k + j], shift));
+    const float rdj = 1.f / djj;
+    for (int i = j + tid; i < k; i += CHOL_T) {
+      const float v = (i == j) ? djj : W[i * k + j] * rdj;
+      col[i] = v;
+      W[i * k + j] = v;
+    }
     __syncthreads();
-    for (int i = j + 1 + tid; i < k; i += CHOL_T) W[(int64_t)i * k + j] /= djj;
-    if (tid == 0) W[(int64_t)j * k + j] = djj;
-    __syncthreads();
-    const int rem = k - j - 1;
-    for (int e = tid; e < rem * rem; e += CHOL_T) {
-      const int i = j + 1 + e / rem, l = j + 1 + e % rem;
-      if (l <= i) W[(int64_t)i * k + l] -= W[(int64_t)i * k + j] * W[(int64_t)l * k + j];
+    for (int i = j + 1 + warp; i < k; i += CHOL_T / 32) {
+      const float ci = col[i];
+      for (int l = j + 1 + lane; l <= i; l += 32) W[i * k + l] = fmaf(-ci, col[l], W[i * k + l]);
     }
     __syncthreads();
   }
-  // L^{-1} row by row: Linv[i][c] = -(sum_{l=c}^{i-1} L[i][l] Linv[l][c]) / L[i][i]; stored at W[c][i]
-  double* dv = in_smem ? dinv_s : nullptr;
-  for (int i = tid; i < k; i += CHOL_T) {
-    const double d = 1.0 / W[(int64_t)i * k + i];
-    if (in_smem) dv[i] = d;
-    else Linv[(int64_t)i * k + i] = d;
-  }
+  // Linv: diagonal, then rows i = 1..k-1
+  for (int i = tid; i < k; i += CHOL_T) Li[i * k + i] = 1.f / W[i * k + i];
   __syncthreads();
   for (int i = 1; i < k; ++i) {
-    const double di = in_smem ? dv[i] : Linv[(int64_t)i * k + i];
+    const float di = Li[i * k + i];
     for (int c = tid; c < i; c += CHOL_T) {
-      double s = W[(int64_t)i * k + c] * (in_smem ? dv[c] : Linv[(int64_t)c * k + c]);
-      for (int l = c + 1; l < i; ++l) s += W[(int64_t)i * k + l] * W[(int64_t)c * k + l];
-      W[(int64_t)c * k + i] = -s * di;
+      float s0 = 0.f, s1 = 0.f;
+      int l = c;
+      for (; l + 1 < i; l += 2) {
+        s0 = fmaf(W[i * k + l], Li[l * k + c], s0);
+        s1 = fmaf(W[i * k + l + 1], Li[(l + 1) * k + c], s1);
+      }
+      if (l < i) s0 = fmaf(W[i * k + l], Li[l * k + c], s0);
+      Li[i * k + c] = -(s0 + s1) * di;
     }
     __syncthreads();
   }
-  for (int e = tid; e < k * k; e += CHOL_T) {
-    const int i = e / k, c = e % k;
-    double v = 0.0;
-    if (c < i) v = W[(int64_t)c * k + i];
-    else if (c == i) v = in_smem ? dv[i] : Linv[(int64_t)i * k + i];
-    if (in_smem || c != i) Linv[e] = v;
-  }
-  (void)dinv;
+  for (int e = tid; e < k * k; e += CHOL_T) Linv_out[e] = Li[e];
 }
 
 // ============================================================================ Philox sketch
@@ -407,12 +490,12 @@ __global__ void sumsq_kernel(const T* __restrict__ X, int64_t rows, int64_t cols
   }
 }
 
+// one warp; lane l sums p[l], p[l+32], ... then a fixed shuffle tree (deterministic)
 __global__ void sum_partials_kernel(const double* __restrict__ p, int n, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += p[i];
-    *out = s;
-  }
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) s += p[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) *out = s;
 }
 
 template <typename T>
@@ -434,61 +517,306 @@ static cudaError_t sumsq(const T* X, int64_t rows, int64_t cols, int64_t ld, dou
   return e;
 }
 
-static cudaError_t chol_inv(int k, const double* G, double* W, double* Li, cudaStream_t st) {
+// W: global work area of at least 2 k^2 + k floats (used when k > CHOL_SMEM_K)
+static cudaError_t chol_inv(int k, const float* G, float shift_rel, float* W, float* Li, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute((const void*)chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         CHOL_SMEM_K * CHOL_SMEM_K * (int)sizeof(double));
+                                         (2 * CHOL_SMEM_K * CHOL_SMEM_K + CHOL_SMEM_K) * (int)sizeof(float));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0, 0.0, nullptr);
-  const size_t sm = k <= CHOL_SMEM_K ? sizeof(double) * k * k : 0;
-  chol_inv_kernel<<<1, CHOL_T, sm, st>>>(k, G, W, Li);
+  AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0 * 2.0, 0.0, nullptr);
+  const size_t sm = k <= CHOL_SMEM_K ? sizeof(float) * (2 * (size_t)k * k + k) : 0;
+  chol_inv_kernel<<<1, CHOL_T, sm, st>>>(k, G, shift_rel, Li, W);
   return cudaGetLastError();
 }
 
-// ============================================================================ orth(Y) by CholeskyQR2
-// Y (m x k, FP32) -> Q (m x k, FP32 with orthonormal columns, same span).
-// Each pass: G = Y^T Y accumulated in FP64, G + sI = L L^T and L^{-1} in FP64 (one CTA),
-// then Y <- Y L^{-T} with the FP32 GEMM.  Any invertible triangular factor keeps span(Y);
-// the FP32 rounding of the apply only costs orthogonality, which the second pass restores.
-__global__ void d2f_kernel(const double* __restrict__ x, float* __restrict__ y, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = (float)x[i];
+// ============================================================================ orth(Y): shifted CholeskyQR2 + one Newton-Schulz step
+// Y (m x k, FP32) -> Q (m x k, FP32 with orthonormal columns, same span).  Each CholQR pass:
+// G = X^T X (compensated FP32), G + sI = L L^T and L^{-1} (FP32, one CTA), X <- X L^{-T} (FP32
+// GEMM).  Any invertible triangular factor keeps span(Y), so the passes only improve
+// orthogonality: the first pass is shifted (s ~ k u ||G||, Fukaya, Kannan, Nakatsukasa,
+// Yamamoto, Yanagisawa, "Shifted Cholesky QR", SIAM J. Sci. Comput. 2020) so that it cannot break
+// down on rank-deficient sketches, the second restores orthogonality to the level of the FP32
+// Cholesky.  A final Newton-Schulz step X <- X (I - (X^T X - I)/2), with X^T X - I taken from the
+// accurate Gram, leaves the span unchanged and brings ||X^T X - I|| down to FP32 rounding.
+static cudaError_t orthonormalize(int64_t m, int k, const float* Y, float* Q, cudaStream_t st) {
+  float *G = nullptr, *W = nullptr, *Li = nullptr, *Q1 = nullptr, *Q2 = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](float** p, size_t cnt) {
+    if (e == cudaSuccess) e = dev_alloc((void**)p, sizeof(float) * cnt, st);
+  };
+  al(&G, (size_t)k * k);
+  al(&W, 2 * (size_t)k * k + k);
+  al(&Li, (size_t)k * k);
+  al(&Q1, (size_t)m * k);
+  al(&Q2, (size_t)m * k);
+  const float shift1 = std::max(1e-5f, 1e-7f * (float)k);
+  const float* src = Y;
+  float* dsts[2] = {Q1, Q2};
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+    e = gram_dot2(m, k, src, G, st);
+    if (e == cudaSuccess) e = chol_inv(k, G, pass == 0 ? shift1 : 1e-7f, W, Li, st);
+    if (e == cudaSuccess)
+      e = sgemm<float>(false, true, (int)m, k, k, 1.f, src, k, Li, k, 0.f, dsts[pass], k, st);  // src Linv^T
+    src = dsts[pass];
+  }
+  if (e == cudaSuccess) e = gram_dot2(m, k, Q2, G, st, 1);  // G <- -(Q2^T Q2 - I) / 2
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Q, Q2, sizeof(float) * (size_t)m * k, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = sgemm<float>(false, false, (int)m, k, k, 1.f, Q2, k, G, k, 1.f, Q, k, st);
+  for (float* p : {G, W, Li, Q1, Q2}) dev_free(p, st);
+  return e;
 }
 
-static cudaError_t cholqr2(int64_t m, int k, const float* Y, float* Q, cudaStream_t st) {
-  double *G = nullptr, *W = nullptr, *Li = nullptr;
-  float *Lf = nullptr, *Q1 = nullptr;
-  cudaError_t e = cudaSuccess;
-  auto al = [&](void** p, size_t bytes) {
-    if (e == cudaSuccess) e = dev_alloc(p, bytes, st);
-  };
-  al((void**)&G, sizeof(double) * k * k);
-  al((void**)&W, sizeof(double) * k * k);
-  al((void**)&Li, sizeof(double) * k * k);
-  al((void**)&Lf, sizeof(float) * k * k);
-  al((void**)&Q1, sizeof(float) * m * k);
-  const float* src = Y;
-  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
-    float* dst = pass == 0 ? Q1 : Q;
-    e = dgemm_small<true, false>((int)k, k, (int)m, src, k, src, k, G, k, st);  // src^T src
-    if (e == cudaSuccess) e = chol_inv(k, G, W, Li, st);
-    if (e == cudaSuccess) {
-      AMM_TRACE("d2f", st);
-      d2f_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(Li, Lf, k * k);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess)
-      e = sgemm<float>(false, true, (int)m, k, k, 1.f, src, k, Lf, k, 0.f, dst, k, st);  // src Linv^T
-    src = dst;
+// ============================================================================ tensor-core path
+// Y[c][r] = X[r][c] (cols x rows), 32 x 32 tiles through shared memory, with a type cast.
+template <typename TI, typename TO>
+__global__ void transpose_cast_kernel(const TI* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                      TO* __restrict__ Y, int64_t ldy) {
+  __shared__ float t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t r = r0 + i, c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (r < rows && c < cols) v = (float)X[r * ldx + c];
+    t[i][threadIdx.x] = v;
   }
-  dev_free(G, st);
-  dev_free(W, st);
-  dev_free(Li, st);
-  dev_free(Lf, st);
-  dev_free(Q1, st);
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) Y[c * ldy + r] = (TO)t[threadIdx.x][i];
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void cast_kernel(const TI* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx, TO* __restrict__ Y,
+                            int64_t ldy) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t r = e / cols, c = e % cols;
+  Y[r * ldy + c] = (TO)(float)X[r * ldx + c];
+}
+
+template <typename TI, typename TO>
+static cudaError_t transpose_cast(const TI* X, int64_t rows, int64_t cols, int64_t ldx, TO* Y, int64_t ldy,
+                                  cudaStream_t st) {
+  AMM_TRACE_W("transpose", st, 0.0, (double)rows * cols * (sizeof(TI) + sizeof(TO)), nullptr);
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  transpose_cast_kernel<TI, TO><<<grid, dim3(32, 8), 0, st>>>(X, rows, cols, ldx, Y, ldy);
+  return cudaGetLastError();
+}
+
+cudaError_t transpose_f32(const float* X, int64_t rows, int64_t cols, int64_t ldx, float* Y, int64_t ldy,
+                          cudaStream_t st) {
+  return transpose_cast<float, float>(X, rows, cols, ldx, Y, ldy, st);
+}
+
+template <typename TI, typename TO>
+static cudaError_t cast(const TI* X, int64_t rows, int64_t cols, int64_t ldx, TO* Y, int64_t ldy, cudaStream_t st) {
+  AMM_TRACE_W("cast", st, 0.0, (double)rows * cols * (sizeof(TI) + sizeof(TO)), nullptr);
+  const int64_t tot = rows * cols;
+  cast_kernel<TI, TO><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, rows, cols, ldx, Y, ldy);
+  return cudaGetLastError();
+}
+
+// C = alpha A B^T + beta C with A (M x K, lda) and B (N x K, ldb) K-major in the compute type E.
+// tcgen05 when every row starts 16-byte aligned, the SIMT kernel otherwise.
+template <typename E>
+static cudaError_t gemm_tn(int M, int N, int K, float alpha, const E* A, int64_t lda, const E* B, int64_t ldb,
+                           float beta, float* C, int64_t ldc, int* err, cudaStream_t st) {
+  const bool aligned = ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && (lda * sizeof(E)) % 16 == 0 &&
+                       (ldb * sizeof(E)) % 16 == 0;
+  if (aligned && K > 0)
+    return umma_gemm_tn(std::is_same<E, float>::value, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, err, st);
+  return sgemm<E>(false, true, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+}
+
+// FP32 -> E copy of a small matrix (no copy when E is float)
+template <typename E>
+static cudaError_t to_e(Handle* h, const float* X, int64_t rows, int64_t cols, const E** out, cudaStream_t st) {
+  if constexpr (std::is_same<E, float>::value) {
+    *out = X;
+    return cudaSuccess;
+  } else {
+    E* y = nullptr;
+    cudaError_t e = h ? h->alloc((void**)&y, sizeof(E) * rows * cols) : dev_alloc((void**)&y, sizeof(E) * rows * cols, st);
+    if (e != cudaSuccess) return e;
+    *out = y;
+    return cast<float, E>(X, rows, cols, cols, y, cols, st);
+  }
+}
+
+template <typename E>
+static cudaError_t svd_build_tc(Handle* h) {
+  auto& s = h->svd;
+  cudaStream_t st = h->stream;
+  const int64_t m = h->rows, n = h->cols;
+  const int k = (int)h->k;
+  cudaError_t e;
+  // operand copies: X in E (K-major), X^T in E, phi^T in E
+  const bool in_bf16 = h->dtype == AMM_BF16;
+  const bool direct = (std::is_same<E, float>::value != in_bf16) && ((uintptr_t)h->A % 16 == 0) &&
+                      (h->lda * (int64_t)sizeof(E)) % 16 == 0;
+  if (direct) {
+    s.Xe = h->A;
+    s.ldxe = h->lda;
+  } else {
+    E* xe = nullptr;
+    if ((e = h->alloc((void**)&xe, sizeof(E) * m * n)) != cudaSuccess) return e;
+    e = in_bf16 ? cast<__nv_bfloat16, E>((const __nv_bfloat16*)h->A, m, n, h->lda, xe, n, st)
+                : cast<float, E>((const float*)h->A, m, n, h->lda, xe, n, st);
+    if (e != cudaSuccess) return e;
+    s.Xe = xe;
+    s.ldxe = n;
+  }
+  E* xte = nullptr;
+  E* phit = nullptr;
+  if ((e = h->alloc((void**)&xte, sizeof(E) * m * n)) != cudaSuccess) return e;
+  if ((e = h->alloc((void**)&phit, sizeof(E) * n * k)) != cudaSuccess) return e;
+  s.XTe = xte;
+  e = in_bf16 ? transpose_cast<__nv_bfloat16, E>((const __nv_bfloat16*)h->A, m, n, h->lda, xte, m, st)
+              : transpose_cast<float, E>((const float*)h->A, m, n, h->lda, xte, m, st);
+  if (e == cudaSuccess) e = transpose_cast<float, E>(s.phi, n, k, k, phit, n, st);
+  if (e != cudaSuccess) return e;
+  const E* Xe = (const E*)s.Xe;
+  // Y = X phi  -> rows x k
+  float* Y = nullptr;
+  if ((e = dev_alloc((void**)&Y, sizeof(float) * m * k, st)) != cudaSuccess) return e;
+  e = gemm_tn<E>((int)m, k, (int)n, 1.f, Xe, s.ldxe, phit, n, 0.f, Y, k, s.err, st);
+  if (e == cudaSuccess) e = orthonormalize(m, k, Y, s.Q, st);
+  dev_free(Y, st);
+  if (e != cudaSuccess) return e;
+  const E* qe = nullptr;
+  if ((e = to_e<E>(h, s.Q, m, k, &qe, st)) != cudaSuccess) return e;
+  s.Qe = (void*)qe;
+  E* qte = nullptr;
+  if ((e = h->alloc((void**)&qte, sizeof(E) * m * k)) != cudaSuccess) return e;
+  if ((e = transpose_cast<float, E>(s.Q, m, k, k, qte, m, st)) != cudaSuccess) return e;
+  s.QTe = qte;
+  // Z = Q^T X (k x n) and Z^T (n x k), FP32 and E
+  float* ZT = nullptr;
+  if ((e = h->alloc((void**)&ZT, sizeof(float) * n * k)) != cudaSuccess) return e;
+  if (h->role == AMM_LEFT) {
+    e = gemm_tn<E>(k, (int)n, (int)m, 1.f, qte, m, xte, m, 0.f, s.X, n, s.err, st);
+    if (e == cudaSuccess) e = transpose_cast<float, float>(s.X, k, n, n, ZT, k, st);
+  } else {
+    e = gemm_tn<E>((int)n, k, (int)m, 1.f, xte, m, qte, m, 0.f, ZT, k, s.err, st);
+    if (e == cudaSuccess) e = transpose_cast<float, float>(ZT, n, k, k, s.X, n, st);
+  }
+  if (e != cudaSuccess) return e;
+  const E *ze = nullptr, *zte = nullptr;
+  if ((e = to_e<E>(h, s.X, k, n, &ze, st)) != cudaSuccess) return e;
+  if ((e = to_e<E>(h, ZT, n, k, &zte, st)) != cudaSuccess) return e;
+  s.Ze = (void*)ze;
+  s.ZTe = (void*)zte;
+  if (in_bf16) e = sumsq<__nv_bfloat16>((const __nv_bfloat16*)h->A, m, n, h->lda, s.norms + 0, st);
+  else e = sumsq<float>((const float*)h->A, m, n, h->lda, s.norms + 0, st);
+  if (e == cudaSuccess) e = sumsq<float>(s.X, k, n, n, s.norms + 1, st);
+  return e;
+}
+
+template <typename E>
+static cudaError_t svd_matmul_tc(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st) {
+  const int m = (int)a->rows, n = (int)a->cols, p = (int)b->cols;
+  const int ka = (int)a->k, kb = (int)b->k;
+  auto &sa = a->svd, &sb = b->svd;
+  int* err = sa.err;
+  float *T1T = nullptr, *W = nullptr, *ZZ = nullptr;
+  const E *t1te = nullptr, *we = nullptr, *zze = nullptr;
+  cudaError_t e = dev_alloc((void**)&T1T, sizeof(float) * (size_t)p * ka, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&W, sizeof(float) * (size_t)m * kb, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&ZZ, sizeof(float) * (size_t)kb * ka, st);
+  // T1^T = B^T Z_A^T ; W = A Q_B ; (Z_A Q_B)^T = Q_B^T Z_A^T ; W -= Q_A (Z_A Q_B) ; C = Q_A T1 + W Z_B
+  if (e == cudaSuccess) e = gemm_tn<E>(p, ka, n, 1.f, (const E*)sb.XTe, n, (const E*)sa.Ze, n, 0.f, T1T, ka, err, st);
+  if (e == cudaSuccess) e = gemm_tn<E>(m, kb, n, 1.f, (const E*)sa.Xe, sa.ldxe, (const E*)sb.QTe, n, 0.f, W, kb, err, st);
+  if (e == cudaSuccess) e = gemm_tn<E>(kb, ka, n, 1.f, (const E*)sb.QTe, n, (const E*)sa.Ze, n, 0.f, ZZ, ka, err, st);
+  if (e == cudaSuccess) e = to_e<E>(nullptr, ZZ, kb, ka, &zze, st);
+  if (e == cudaSuccess) e = gemm_tn<E>(m, kb, ka, -1.f, (const E*)sa.Qe, ka, zze, ka, 1.f, W, kb, err, st);
+  if (e == cudaSuccess) e = to_e<E>(nullptr, T1T, p, ka, &t1te, st);
+  if (e == cudaSuccess) e = to_e<E>(nullptr, W, m, kb, &we, st);
+  if (e == cudaSuccess) e = gemm_tn<E>(m, p, ka, 1.f, (const E*)sa.Qe, ka, t1te, ka, 0.f, C, ldc, err, st);
+  if (e == cudaSuccess) e = gemm_tn<E>(m, p, kb, 1.f, we, kb, (const E*)sb.ZTe, kb, 1.f, C, ldc, err, st);
+  if constexpr (!std::is_same<E, float>::value) {
+    for (const E* q : {t1te, we, zze}) dev_free((void*)q, st);
+  }
+  for (float* q : {T1T, W, ZZ}) dev_free(q, st);
+  return e;
+}
+
+template <typename E>
+static cudaError_t svd_backward_tc(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda,
+                                   float* dB, int64_t lddb, cudaStream_t st) {
+  const int m = (int)a->rows, n = (int)a->cols, p = (int)b->cols;
+  const int ka = (int)a->k, kb = (int)b->k;
+  auto &sa = a->svd, &sb = b->svd;
+  int* err = sa.err;
+  std::vector<void*> tmp;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(&q, bytes, st);
+    if (q) tmp.push_back(q);
+    return q;
+  };
+  auto as_e = [&](const float* X, int64_t r, int64_t c) -> const E* {
+    const E* y = nullptr;
+    if (e == cudaSuccess) e = to_e<E>(nullptr, X, r, c, &y, st);
+    if constexpr (!std::is_same<E, float>::value) tmp.push_back((void*)y);
+    return y;
+  };
+  // G and G^T in E
+  const E* Ge = nullptr;
+  int64_t ldge = ldg;
+  if constexpr (std::is_same<E, float>::value) {
+    Ge = G;
+  } else {
+    E* g = (E*)al(sizeof(E) * (size_t)m * p);
+    if (e == cudaSuccess) e = cast<float, E>(G, m, p, ldg, g, p, st);
+    Ge = g;
+    ldge = p;
+  }
+  E* GTe = (E*)al(sizeof(E) * (size_t)m * p);
+  if (e == cudaSuccess) e = transpose_cast<float, E>(G, m, p, ldg, GTe, m, st);
+  // H2^T = G^T Q_A (p x ka), H2 = (H2^T)^T
+  float* H2T = (float*)al(sizeof(float) * (size_t)p * ka);
+  float* H2 = (float*)al(sizeof(float) * (size_t)p * ka);
+  if (e == cudaSuccess) e = gemm_tn<E>(p, ka, m, 1.f, GTe, m, (const E*)sa.QTe, m, 0.f, H2T, ka, err, st);
+  if (e == cudaSuccess) e = transpose_cast<float, float>(H2T, p, ka, ka, H2, p, st);
+  const E* H2e = as_e(H2, ka, p);
+  const E* H2Te = as_e(H2T, p, ka);
+  if (dA) {
+    // dA = (G Z_B^T) Q_B^T + Q_A [ H2 B^T - (H2 Z_B^T) Q_B^T ]
+    float* H1 = (float*)al(sizeof(float) * (size_t)m * kb);
+    if (e == cudaSuccess) e = gemm_tn<E>(m, kb, p, 1.f, Ge, ldge, (const E*)sb.Ze, p, 0.f, H1, kb, err, st);
+    const E* H1e = as_e(H1, m, kb);
+    if (e == cudaSuccess) e = gemm_tn<E>(m, n, kb, 1.f, H1e, kb, (const E*)sb.Qe, kb, 0.f, dA, ldda, err, st);
+    float* H3T = (float*)al(sizeof(float) * (size_t)n * ka);
+    float* H4 = (float*)al(sizeof(float) * (size_t)ka * kb);
+    if (e == cudaSuccess)
+      e = gemm_tn<E>(n, ka, p, 1.f, (const E*)sb.Xe, sb.ldxe, H2e, p, 0.f, H3T, ka, err, st);  // B H2^T
+    if (e == cudaSuccess) e = gemm_tn<E>(ka, kb, p, 1.f, H2e, p, (const E*)sb.Ze, p, 0.f, H4, kb, err, st);
+    const E* H4e = as_e(H4, ka, kb);
+    if (e == cudaSuccess) e = gemm_tn<E>(n, ka, kb, -1.f, (const E*)sb.Qe, kb, H4e, kb, 1.f, H3T, ka, err, st);
+    const E* H3Te = as_e(H3T, n, ka);
+    if (e == cudaSuccess) e = gemm_tn<E>(m, n, ka, 1.f, (const E*)sa.Qe, ka, H3Te, ka, 1.f, dA, ldda, err, st);
+  }
+  if (dB) {
+    // W^T = Q_B^T A^T - (Z_A Q_B)^T Q_A^T ; dB = Z_A^T H2 + Q_B (W^T G)
+    float* WT = (float*)al(sizeof(float) * (size_t)kb * m);
+    float* ZZ = (float*)al(sizeof(float) * (size_t)kb * ka);
+    if (e == cudaSuccess) e = gemm_tn<E>(kb, m, n, 1.f, (const E*)sb.QTe, n, (const E*)sa.Xe, sa.ldxe, 0.f, WT, m, err, st);
+    if (e == cudaSuccess) e = gemm_tn<E>(kb, ka, n, 1.f, (const E*)sb.QTe, n, (const E*)sa.Ze, n, 0.f, ZZ, ka, err, st);
+    const E* ZZe = as_e(ZZ, kb, ka);
+    if (e == cudaSuccess) e = gemm_tn<E>(kb, m, ka, -1.f, ZZe, ka, (const E*)sa.Qe, ka, 1.f, WT, m, err, st);
+    const E* WTe = as_e(WT, kb, m);
+    float* H5T = (float*)al(sizeof(float) * (size_t)p * kb);
+    if (e == cudaSuccess) e = gemm_tn<E>(p, kb, m, 1.f, GTe, m, WTe, m, 0.f, H5T, kb, err, st);
+    const E* H5Te = as_e(H5T, p, kb);
+    if (e == cudaSuccess) e = gemm_tn<E>(n, p, ka, 1.f, (const E*)sa.ZTe, ka, H2Te, ka, 0.f, dB, lddb, err, st);
+    if (e == cudaSuccess) e = gemm_tn<E>(n, p, kb, 1.f, (const E*)sb.Qe, kb, H5Te, kb, 1.f, dB, lddb, err, st);
+  }
+  for (void* q : tmp) dev_free(q, st);
   return e;
 }
 
@@ -501,7 +829,7 @@ static cudaError_t svd_build(Handle* h, const float* A) {
   cudaError_t e = dev_alloc((void**)&Y, sizeof(float) * (size_t)m * k, h->stream);
   if (e != cudaSuccess) return e;
   e = sgemm<float>(false, false, (int)m, k, (int)n, 1.f, A, h->lda, s.phi, k, 0.f, Y, k, h->stream);  // Y = A phi
-  if (e == cudaSuccess) e = cholqr2(m, k, Y, s.Q, h->stream);                                          // Q = orth(Y)
+  if (e == cudaSuccess) e = orthonormalize(m, k, Y, s.Q, h->stream);                                          // Q = orth(Y)
   if (e == cudaSuccess)
     e = sgemm<float>(true, false, k, (int)n, (int)m, 1.f, s.Q, k, A, h->lda, 0.f, s.X, n, h->stream);  // X = Q^T A
   if (e == cudaSuccess) e = sumsq<float>(A, m, n, h->lda, s.norms + 0, h->stream);
@@ -511,8 +839,9 @@ static cudaError_t svd_build(Handle* h, const float* A) {
 }
 
 amm_status_t decompose_svd(Handle* h, const amm_opts_t* o) {
-  if (h->dtype != AMM_F32) return fail(AMM_ERR_NOT_IMPLEMENTED, "svd: BF16 inputs are not built yet");
   if (h->k > 1024) return fail(AMM_ERR_UNSUPPORTED_SIZE, "svd: k=%lld > 1024", (long long)h->k);
+  const int compute = o ? o->compute : AMM_F32;
+  if (compute != AMM_F32 && compute != AMM_BF16) return fail(AMM_ERR_INVALID_ARG, "svd: bad compute mode %d", compute);
   auto& s = h->svd;
   const int64_t m = h->rows, n = h->cols, k = h->k;
   cudaError_t e;
@@ -530,12 +859,22 @@ amm_status_t decompose_svd(Handle* h, const amm_opts_t* o) {
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return cuda_fail(e, "svd: sketch");
-  e = svd_build(h, (const float*)h->A);
+  if ((e = h->alloc((void**)&s.err, sizeof(int))) != cudaSuccess) return cuda_fail(e, "svd: device allocation");
+  if ((e = cudaMemsetAsync(s.err, 0, sizeof(int), h->stream)) != cudaSuccess) return cuda_fail(e, "svd: memset");
+  s.tc = true;
+  s.bf16 = compute == AMM_BF16;
+  e = s.bf16 ? svd_build_tc<__nv_bfloat16>(h) : svd_build_tc<float>(h);
   if (e != cudaSuccess) return cuda_fail(e, "svd: decomposition");
   return AMM_OK;
 }
 
 amm_status_t svd_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st) {
+  if (a->svd.tc && b->svd.tc) {
+    if (a->svd.bf16 != b->svd.bf16) return fail(AMM_ERR_STATE, "svd: both operands need the same compute mode");
+    cudaError_t e = a->svd.bf16 ? svd_matmul_tc<__nv_bfloat16>(a, b, C, ldc, st) : svd_matmul_tc<float>(a, b, C, ldc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "svd product");
+    return AMM_OK;
+  }
   const int m = (int)a->rows, n = (int)a->cols, p = (int)b->cols;
   const int ka = (int)a->k, kb = (int)b->k;
   const float* A = (const float*)a->A;
@@ -560,6 +899,13 @@ amm_status_t svd_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_
 
 amm_status_t svd_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, float* dB,
                           int64_t lddb, cudaStream_t st) {
+  if (a->svd.tc && b->svd.tc) {
+    if (a->svd.bf16 != b->svd.bf16) return fail(AMM_ERR_STATE, "svd: both operands need the same compute mode");
+    cudaError_t e = a->svd.bf16 ? svd_backward_tc<__nv_bfloat16>(a, b, G, ldg, dA, ldda, dB, lddb, st)
+                                : svd_backward_tc<float>(a, b, G, ldg, dA, ldda, dB, lddb, st);
+    if (e != cudaSuccess) return cuda_fail(e, "svd backward");
+    return AMM_OK;
+  }
   const int m = (int)a->rows, n = (int)a->cols, p = (int)b->cols;
   const int ka = (int)a->k, kb = (int)b->k;
   const float* A = (const float*)a->A;
@@ -605,6 +951,12 @@ amm_status_t svd_info(Handle* h, amm_info_t* info) {
   double nr[2];
   cudaError_t e = cudaMemcpy(nr, h->svd.norms, sizeof(nr), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "svd_info");
+  if (h->svd.err) {
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, h->svd.err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "svd_info");
+    if (flag) return fail(AMM_ERR_TIMEOUT, "a tensor-core kernel of this handle gave up waiting (bounded wait)");
+  }
   info->fro2 = nr[0];
   info->resid_fro2 = nr[0] - nr[1];  // ||A - Q Q^T A||^2 = ||A||^2 - ||Q^T A||^2
   info->boundary_gap = -1.0;

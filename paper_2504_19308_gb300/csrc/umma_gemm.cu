@@ -1,0 +1,449 @@
+// Tensor-core GEMM for the thin low-rank products (Alg. 1 and Section 2.2), sm_103a.
+//
+//   C[M x N] = alpha * A[M x K] * B[N x K]^T + beta * C        (A, B K-major: row-major along K)
+//
+// One 128 x 128 output tile per CTA (K optionally split over grid.z into a workspace).
+// Warps 0-3 drain the accumulator from tensor memory, warp 4 drives TMA, warp 5 issues MMAs:
+//   * TMA (cp.async.bulk.tensor.2d) loads 128-row x 128-byte boxes of A and B with the 128-byte
+//     swizzle into a STAGES-deep ring, completion tracked by mbarrier transaction counts;
+//   * one thread issues tcgen05.mma (cta_group::1, M = 128, N = 128) per 32-byte K slice, the
+//     accumulator lives in 128 TMEM columns, tcgen05.commit releases each smem stage;
+//   * the epilogue waits for the last commit, reads TMEM with tcgen05.ld.32x32b and stores
+//     through a padded shared tile so that every warp store covers 128 contiguous bytes.
+// Element modes:
+//   BF16  kind::f16, BF16 inputs, FP32 accumulation (the BF16 precision mode);
+//   TF32X3  FP32 inputs split in shared memory into hi = tf32(x) and lo = tf32(x - hi), both
+//           rounded to nearest; kind::tf32 products hi*hi + hi*lo + lo*hi give products within
+//           about 2^-21 relative (the lo*lo term and the rounding of lo are dropped).  The
+//           small correction products accumulate in a second TMEM accumulator, and long K is
+//           split into chains of at most UM_TF32_MAX_KB k-blocks whose partials are summed in
+//           FP64, which bounds the rounding the tensor core's FP32 accumulation adds.
+// Every mbarrier wait is bounded; a wait that gives up sets *err and the CTA drains and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "api_internal.h"
+#include "kernels.h"
+#include "trace.h"
+
+namespace amm {
+
+constexpr int UM_BM = 128, UM_BN = 128;
+constexpr int UM_THREADS = 192;
+constexpr int UM_TF32_MAX_KB = 16;  // longest TF32X3 accumulation chain, in 32-wide k-blocks
+constexpr uint32_t UM_SPIN_LIMIT = 1u << 26;  // ~ seconds of polling, then give up
+
+// ----------------------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// bounded wait for the phase with the given parity; returns false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < UM_SPIN_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(tm), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 64-bit shared-memory matrix descriptor (tcgen05): K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
+  d |= (uint64_t)(16u >> 4) << 16;                // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;              // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D = F32, A/B format (1 = BF16, 2 = TF32), K-major A and B, N, M
+__host__ __device__ constexpr uint32_t umma_idesc(uint32_t ab_format, int M, int N) {
+  return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ----------------------------------------------------------------------------- the kernel
+// Shared memory (1024-aligned): STAGES x {A tile, B tile} (+ lo tiles for TF32X3), then barriers.
+template <bool TF32>
+struct UmmaCfg {
+  static constexpr int ELEM = TF32 ? 4 : 2;
+  static constexpr int BK = 128 / ELEM;                      // one 128-byte swizzle atom of K
+  static constexpr int MMA_K = 32 / ELEM;                    // K per tcgen05.mma
+  static constexpr int TILE_BYTES = UM_BM * 128;             // 16 KiB per operand tile
+  static constexpr int STAGE_BYTES = (TF32 ? 4 : 2) * TILE_BYTES;  // A, B (+ A lo, B lo)
+  static constexpr int STAGES = TF32 ? 3 : 5;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+};
+
+// Round to the nearest TF32 value (10 fraction bits, ties away from zero); Inf and NaN pass.
+__device__ __forceinline__ float tf32_round(float x) {
+  const uint32_t u = __float_as_uint(x);
+  if ((u & 0x7F800000u) == 0x7F800000u) return x;
+  return __uint_as_float((u + 0x1000u) & 0xFFFFE000u);
+}
+
+// Split x into hi = tf32(x) in place and lo = tf32(x - hi).  Both halves are rounded to nearest,
+// so |x - hi - lo| <= 2^-22 |x| and the tensor core's operand truncation loses nothing.
+__device__ __forceinline__ void split_tile(float* hi, float* lo, int nfloat, int tid, int nthr) {
+  float4* h4 = reinterpret_cast<float4*>(hi);
+  float4* l4 = reinterpret_cast<float4*>(lo);
+  for (int i = tid; i < nfloat / 4; i += nthr) {
+    float4 x = h4[i], h, l;
+    h.x = tf32_round(x.x); l.x = tf32_round(x.x - h.x);
+    h.y = tf32_round(x.y); l.y = tf32_round(x.y - h.y);
+    h.z = tf32_round(x.z); l.z = tf32_round(x.z - h.z);
+    h.w = tf32_round(x.w); l.w = tf32_round(x.w - h.w);
+    h4[i] = h;
+    l4[i] = l;
+  }
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(UM_THREADS, 1)
+    umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                     int K, float alpha, float beta, float* __restrict__ C, int64_t ldc, int kchunk,
+                     float* __restrict__ ws, int* __restrict__ err) {
+  using Cfg = UmmaCfg<TF32>;
+  constexpr int UM_STAGES = Cfg::STAGES;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* tiles = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + (size_t)UM_STAGES * Cfg::STAGE_BYTES);
+  uint64_t* split_done = full + UM_STAGES;  // TF32X3: hi/lo split finished
+  uint64_t* empty = split_done + UM_STAGES;
+  uint64_t* accum = empty + UM_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * UM_BM, n0 = blockIdx.x * UM_BN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  const int nkb = (kend - kbeg + Cfg::BK - 1) / Cfg::BK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < UM_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&split_done[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  constexpr uint32_t TMEM_COLS = TF32 ? 256 : 128;
+  if (warp == 0) {  // TMEM: 128 lanes x 128 FP32 columns per accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 4) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int s = kb % UM_STAGES;
+        const uint32_t ph = (kb / UM_STAGES) & 1;
+        ok = mbar_wait(&empty[s], ph ^ 1);
+        if (!ok) break;
+        unsigned char* st = tiles + (size_t)s * Cfg::STAGE_BYTES;
+        mbar_expect_tx(&full[s], 2 * Cfg::TILE_BYTES);
+        const int kx = kbeg + kb * Cfg::BK;
+        tma_load_2d(st, &tmA, &full[s], kx, m0);
+        tma_load_2d(st + Cfg::TILE_BYTES, &tmB, &full[s], kx, n0);
+      }
+      if (!ok) atomicExch(&s_fail, 1);
+    }
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc(TF32 ? 2u : 1u, UM_BM, UM_BN);
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int s = kb % UM_STAGES;
+        const uint32_t ph = (kb / UM_STAGES) & 1;
+        ok = TF32 ? mbar_wait(&split_done[s], ph) : mbar_wait(&full[s], ph);
+        if (!ok) break;
+        tc_fence_after();
+        unsigned char* st = tiles + (size_t)s * Cfg::STAGE_BYTES;
+        const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + Cfg::TILE_BYTES);
+        const uint32_t a_lo = smem_u32(st + 2 * Cfg::TILE_BYTES), b_lo = smem_u32(st + 3 * Cfg::TILE_BYTES);
+#pragma unroll
+        for (int k = 0; k < Cfg::BK / Cfg::MMA_K; ++k) {
+          const uint32_t off = k * 32;  // 32-byte K slice inside the swizzle atom
+          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+          umma<TF32>(tmem, umma_desc(a_hi + off), umma_desc(b_hi + off), idesc, acc);
+          if constexpr (TF32) {  // correction products into their own accumulator (columns 128..255)
+            umma<TF32>(tmem + 128u, umma_desc(a_hi + off), umma_desc(b_lo + off), idesc, acc);
+            umma<TF32>(tmem + 128u, umma_desc(a_lo + off), umma_desc(b_hi + off), idesc, 1u);
+          }
+        }
+        umma_commit(&empty[s]);  // stage free once these MMAs have read it
+      }
+      umma_commit(accum);
+      if (!ok) atomicExch(&s_fail, 1);
+    }
+  } else {
+    // ---------------------------------------------------------------- warps 0-3
+    if constexpr (TF32) {
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        const int s = kb % UM_STAGES;
+        const uint32_t ph = (kb / UM_STAGES) & 1;
+        ok = mbar_wait(&full[s], ph);
+        if (!ok) break;
+        unsigned char* st = tiles + (size_t)s * Cfg::STAGE_BYTES;
+        split_tile((float*)st, (float*)(st + 2 * Cfg::TILE_BYTES), Cfg::TILE_BYTES / 4, threadIdx.x, 128);
+        split_tile((float*)(st + Cfg::TILE_BYTES), (float*)(st + 3 * Cfg::TILE_BYTES), Cfg::TILE_BYTES / 4,
+                   threadIdx.x, 128);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async proxy (MMA)
+        mbar_arrive(&split_done[s]);
+      }
+    }
+    if (ok) ok = mbar_wait(accum, 0);
+    if (ok) {
+      tc_fence_after();
+      // Every MMA has completed (accum), so the stage buffers are free: each warp transposes its
+      // 32 x 32 accumulator chunks through a padded shared tile and stores whole row segments
+      // (lane = column), so every store instruction writes 128 contiguous bytes.
+      float* stage = reinterpret_cast<float*>(tiles) + warp * (32 * 33);
+      const int col_base = n0 + lane;
+      for (int c0 = 0; c0 < UM_BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if constexpr (TF32) {
+          float w[32];
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)c0, w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int col = col_base + c0;
+        if (col < N) {
+          for (int r = 0; r < 32; ++r) {
+            const int row = m0 + warp * 32 + r;
+            if (row >= M) break;
+            const float x = stage[r * 33 + lane];
+            if (ws) {
+              ws[((int64_t)blockIdx.z * M + row) * N + col] = x;
+            } else {
+              float* d = C + (int64_t)row * ldc + col;
+              *d = (beta == 0.f) ? alpha * x : fmaf(alpha, x, beta * *d);
+            }
+          }
+        }
+        __syncwarp();
+      }
+    } else {
+      atomicExch(&s_fail, 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+  if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+}
+
+// ----------------------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_encode_mu;
+
+static cudaError_t get_encoder() {
+  std::lock_guard<std::mutex> lk(g_encode_mu);
+  if (g_encode) return cudaSuccess;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return cudaSuccess;
+}
+
+// 2-D map over a row-major (rows x cols) matrix, box = 128 rows x 128 bytes, 128-byte swizzle,
+// out-of-range reads return zero (ragged M / N / K edges).
+static cudaError_t make_map(CUtensorMap* tm, const void* base, bool tf32, int64_t rows, int64_t cols, int64_t ld) {
+  const int elem = tf32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * elem)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)UM_BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(tm, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+__global__ void umma_splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ ws, float alpha,
+                                          float beta, float* __restrict__ C, int64_t ldc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * N) return;
+  double s = 0.0;  // the partials are summed in FP64 (a handful of adds per output)
+  for (int z = 0; z < splits; ++z) s += (double)ws[(int64_t)z * M * N + e];
+  float* c = C + (e / N) * ldc + (e % N);
+  *c = (beta == 0.f) ? (float)(alpha * s) : (float)fma((double)alpha, s, (double)beta * (double)*c);
+}
+
+int umma_num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+// C = alpha A B^T + beta C with A (M x K, lda) and B (N x K, ldb) K-major; tf32 selects the
+// FP32-input TF32X3 mode, otherwise inputs are BF16.  err: device int set to 1 if a wait gave up.
+cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void* A, int64_t lda, const void* B,
+                         int64_t ldb, float beta, float* C, int64_t ldc, int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  const int elem = tf32 ? 4 : 2;
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || (lda * elem) % 16 || (ldb * elem) % 16 || K <= 0)
+    return cudaErrorInvalidValue;
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  CUtensorMap ta, tb;
+  if ((e = make_map(&ta, A, tf32, M, K, lda)) != cudaSuccess) return e;
+  if ((e = make_map(&tb, B, tf32, N, K, ldb)) != cudaSuccess) return e;
+  const int bk = 128 / elem;
+  const int tiles = ((M + UM_BM - 1) / UM_BM) * ((N + UM_BN - 1) / UM_BN);
+  int splits = 1;
+  const int kblocks = (K + bk - 1) / bk;
+  if (tiles < umma_num_sms() && kblocks >= 8)
+    splits = std::min(std::min((umma_num_sms() + tiles - 1) / tiles, kblocks / 4), 32);
+  // TF32X3: the tensor core's FP32 accumulation loses up to an ulp per MMA, so no accumulator
+  // chain runs longer than UM_TF32_MAX_KB k-blocks; longer K is split and summed in FP64.
+  if (tf32) splits = std::max(splits, (kblocks + UM_TF32_MAX_KB - 1) / UM_TF32_MAX_KB);
+  splits = std::max(splits, 1);
+  int kchunk = ((kblocks + splits - 1) / splits) * bk;
+  splits = (K + kchunk - 1) / kchunk;
+  float* ws = nullptr;
+  if (splits > 1) {
+    e = dev_alloc((void**)&ws, sizeof(float) * (size_t)splits * M * N, st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((N + UM_BN - 1) / UM_BN, (M + UM_BM - 1) / UM_BM, splits);
+  {
+    AMM_TRACE_W(tf32 ? "umma_gemm_tf32x3" : "umma_gemm_bf16", st, 2.0 * M * N * (double)K,
+                (double)elem * ((double)M * K + (double)N * K) + 4.0 * M * N, nullptr);
+    if (tf32) {
+      static cudaError_t a = cudaFuncSetAttribute((const void*)umma_gemm_kernel<true>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)UmmaCfg<true>::SMEM);
+      if (a != cudaSuccess) return a;
+      umma_gemm_kernel<true><<<grid, UM_THREADS, UmmaCfg<true>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
+                                                                             kchunk, ws, err);
+    } else {
+      static cudaError_t a = cudaFuncSetAttribute((const void*)umma_gemm_kernel<false>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)UmmaCfg<false>::SMEM);
+      if (a != cudaSuccess) return a;
+      umma_gemm_kernel<false><<<grid, UM_THREADS, UmmaCfg<false>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
+                                                                               kchunk, ws, err);
+    }
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess && splits > 1) {
+    AMM_TRACE("umma_splitk_reduce", st);
+    const int64_t tot = (int64_t)M * N;
+    umma_splitk_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, ws, alpha, beta, C, ldc);
+    e = cudaGetLastError();
+  }
+  if (ws) dev_free(ws, st);
+  return e;
+}
+
+}  // namespace amm
+
+// Test hook: C = alpha A B^T + beta C through the tensor-core GEMM (see amm.h).
+extern "C" amm_status_t amm_debug_gemm_tn(int32_t mode, int64_t M, int64_t N, int64_t K, float alpha, const void* A,
+                                          int64_t lda, const void* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                                          int32_t* dev_err, void* stream) {
+  using namespace amm;
+  if (!A || !B || !C || !dev_err) return fail(AMM_ERR_INVALID_ARG, "amm_debug_gemm_tn: NULL pointer");
+  if (mode != 0 && mode != 1) return fail(AMM_ERR_INVALID_ARG, "amm_debug_gemm_tn: mode must be 0 (TF32X3) or 1 (BF16)");
+  if (M <= 0 || N <= 0 || K <= 0 || lda < K || ldb < K || ldc < N)
+    return fail(AMM_ERR_INVALID_ARG, "amm_debug_gemm_tn: bad sizes");
+  cudaError_t e = umma_gemm_tn(mode == 0, (int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, C, ldc, dev_err,
+                               (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "amm_debug_gemm_tn");
+  return AMM_OK;
+}

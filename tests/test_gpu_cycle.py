@@ -69,3 +69,22 @@ def test_cycle_banded_is_exact():
     assert sorted(hA.selection().tolist()) == [0, 1, n - 1]
     C = amm.approx_matmul(hA, amm.decompose(B, "cycle", 5, "right"))
     assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= TOL
+
+
+@pytest.mark.parametrize("n,ka,kb", [(16, 1, 2), (64, 3, 5), (256, 10, 7), (1024, 11, 11)])
+def test_cycle_backward(n, ka, kb):
+    """Frozen-selection gradients of the cycle-sparsified product against the oracle."""
+    torch, amm = torch_cuda()
+    g = S.rng(n + ka + kb, 0)
+    a = g.standard_normal((n, n)) + np.diag(np.full(n, 3.0))
+    b = S.toeplitz_uniform(n, g)
+    gr = g.standard_normal((n, n))
+    A, B, Gt = dev32(torch, a), dev32(torch, b), dev32(torch, gr)
+    hA = amm.decompose(A, "cycle", ka, "left")
+    hB = amm.decompose(B, "cycle", kb, "right")
+    dA, dB = amm.approx_matmul_backward(hA, hB, Gt)
+    ta = O.truncate_cycles(as64(A), ka, hA.selection())
+    tb = O.truncate_cycles(as64(B), kb, hB.selection())
+    rda, rdb = O.cycle_backward(ta, tb, as64(Gt))
+    assert rel(dA.double().cpu().numpy(), rda) <= TOL
+    assert rel(dB.double().cpu().numpy(), rdb) <= TOL

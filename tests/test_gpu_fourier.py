@@ -75,3 +75,48 @@ def test_fourier_single_tone_rows_exact():
     assert all(sorted(sel[i].tolist()) == [i % 17 + 1, n - (i % 17 + 1)] for i in range(m))
     C = amm.approx_matmul(hA, amm.decompose(B, "fourier", 3, "right"))
     assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= 1e-5
+
+
+def _backward_case(torch, amm, a, b, ka, kb, seed):
+    A, B = dev32(torch, a), dev32(torch, b)
+    hA = amm.decompose(A, "fourier", ka, "left")
+    hB = amm.decompose(B, "fourier", kb, "right")
+    g = S.upstream_grad(a.shape[0], b.shape[1], seed)
+    G = dev32(torch, g)
+    dA, dB = amm.approx_matmul_backward(hA, hB, G)
+    ta = O.truncate_fourier_left(as64(A), ka, forced=hA.selection())
+    tb = O.truncate_fourier_right(as64(B), kb, forced=hB.selection())
+    rda, rdb = O.fourier_backward(ta, tb, as64(G))
+    return rel(dA.double().cpu().numpy(), rda), rel(dB.double().cpu().numpy(), rdb)
+
+
+@pytest.mark.parametrize("m,n,p,ka,kb", [(16, 16, 16, 3, 2), (64, 64, 64, 5, 5), (256, 256, 256, 16, 9),
+                                         (1024, 1024, 1024, 11, 11), (100, 64, 37, 3, 4), (257, 128, 300, 7, 2),
+                                         (33, 512, 65, 6, 6)])
+def test_fourier_backward(m, n, p, ka, kb):
+    """dA = Re[(P_A(G dB~^T) + G B~_a^T) conj W], dB = Re[W (A~_a^T G + P_B(dA~^T G))] (masks frozen)."""
+    torch, amm = torch_cuda()
+    g = S.rng(m + n + p, 1)
+    a = g.standard_normal((m, n)) @ S.toeplitz_uniform(n, g) if m == n else g.standard_normal((m, n))
+    b = g.uniform(0, 1, (n, p))
+    ea, eb = _backward_case(torch, amm, a, b, ka, kb, m + p)
+    assert ea <= TOL and eb <= TOL, (ea, eb)
+
+
+def test_fourier_backward_asymmetric_masks():
+    """Single-tone rows with k = 1 keep frequency f but not n - f (equal magnitudes, lower index
+    first), so the kept sets are not mirror-symmetric and the gradient needs the Hermitian part."""
+    torch, amm = torch_cuda()
+    n, m, p = 128, 64, 48
+    l = np.arange(n)
+    a = np.stack([np.cos(2 * np.pi * (i % 17 + 1) * l / n) * (1 + i) for i in range(m)])
+    b = np.stack([np.sin(2 * np.pi * (c % 13 + 2) * l / n) for c in range(p)], axis=1) + 0.01 * S.rng(7, 0).standard_normal((n, p))
+    ea, eb = _backward_case(torch, amm, a, b, 1, 1, 9)
+    assert ea <= TOL and eb <= TOL, (ea, eb)
+
+
+def test_fourier_backward_powerlaw_n4096_top1pct():
+    torch, amm = torch_cuda()
+    a, b = S.powerlaw_pair(4096, seed=0)
+    ea, eb = _backward_case(torch, amm, a, b, 41, 41, 0)
+    assert ea <= TOL and eb <= TOL, (ea, eb)

@@ -96,3 +96,32 @@ def test_svd_generated_sketch_exported():
     assert not np.array_equal(pa, pb)
     ref = O.svd_matmul(as64(A), as64(B), k, pa, pb)
     assert rel(C.double().cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("k", [32, 128])
+def test_svd_bf16_tensor_core_mode(k):
+    """BF16 precision mode: operands, sketch and every low-rank GEMM in BF16 on tcgen05 with FP32
+    accumulation.  The error against the FP64 oracle is the BF16 rounding of the operands and
+    intermediates (~2^-8 per element), far above the FP32 mode's 1e-5; it is bounded and reported."""
+    torch, amm = torch_cuda()
+    a, b = S.exp32_pair(512, seed=2)
+    A, B = dev32(torch, a), dev32(torch, b)
+    pa, pb, PA, PB = _sketches(torch, 512, 512, k, 2)
+    hA = amm.decompose(A, "svd", k, "left", sketch=PA, compute="bf16")
+    hB = amm.decompose(B, "svd", k, "right", sketch=PB, compute="bf16")
+    C = amm.approx_matmul(hA, hB)
+    ref, _, ta, tb = O.svd_matmul(as64(A), as64(B), k, pa.astype(np.float64), pb.astype(np.float64), full=True)
+    err = rel(C.double().cpu().numpy(), ref)
+    assert err <= 3e-2, err
+    g = S.upstream_grad(512, 512, 2)
+    dA, dB = amm.approx_matmul_backward(hA, hB, dev32(torch, g))
+    rda, rdb = O.svd_backward(ta, tb, g.astype(np.float32).astype(np.float64))
+    assert rel(dA.double().cpu().numpy(), rda) <= 3e-2
+    assert rel(dB.double().cpu().numpy(), rdb) <= 3e-2
+    # BF16 operands given directly
+    hA2 = amm.decompose(A.bfloat16(), "svd", k, "left", sketch=PA, compute="bf16")
+    hB2 = amm.decompose(B.bfloat16(), "svd", k, "right", sketch=PB, compute="bf16")
+    C2 = amm.approx_matmul(hA2, hB2)
+    ref2 = O.svd_matmul(as64(A.bfloat16()), as64(B.bfloat16()), k, pa.astype(np.float64), pb.astype(np.float64))
+    assert rel(C2.double().cpu().numpy(), ref2) <= 3e-2
+    assert hA.info()["resid_fro2"] > 0
