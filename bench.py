@@ -230,12 +230,122 @@ def run_amm(args, rank, world, local_rank):
     value = world * fl * args.steps / (ms * 1e-3) / 1e12
     e2e_value = world * fl * args.steps / (e2e_ms * 1e-3) / 1e12
     roof = roofline(kernels, clocks)
+    bf16 = bf16_form(args, A, B, G, PH, ms / args.steps, dist)
+    batched = batched_form(args, dev, dist)
     return {
         "value": value, "ms_per_step": ms / args.steps, "errs": errs, "kernels": kernels,
-        "launches": launches, "clocks": clocks, "roofline": roof,
+        "launches": launches, "clocks": clocks, "roofline": roof, "bf16": bf16, "batched": batched,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N * N * 4,
                 "d2h_bytes_per_step": (len(PRODUCTS) + 2 * n_bwd) * N * N * 4, "ms_per_step": e2e_ms / args.steps},
     }
+
+
+def _device_ms(fn, steps, warmup, dist):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    if dist:
+        import torch.distributed as tdist
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def bf16_form(args, A, B, G, PH, fp32_ms, dist):
+    """The same fwd+bwd step in the BF16 precision mode: BF16 operands for the circulant and rSVD
+    products and BF16 tensor-core GEMMs (FP32 accumulation) for the rSVD; the sparsifiers keep FP32
+    operands (their BF16 inputs are not built).  Reported beside the FP32 step with the
+    approximation error of each product against the exact FP64 product."""
+    import torch
+    import paper_2504_19308_gb300 as amm
+    A16, B16 = A.bfloat16(), B.bfloat16()
+
+    def operands(method):
+        return (A16, B16) if method in ("circulant", "svd") else (A, B)
+
+    def step():
+        for method, k, bwd in PRODUCTS:
+            sa, sb = PH[k] if method == "svd" else (None, None)
+            x, y = operands(method)
+            hA = amm.decompose(x, method, k, "left", sketch=sa, compute="bf16" if method == "svd" else "f32")
+            hB = amm.decompose(y, method, k, "right", sketch=sb, compute="bf16" if method == "svd" else "f32")
+            amm.approx_matmul(hA, hB)
+            if bwd:
+                amm.approx_matmul_backward(hA, hB, G)
+            hA.close()
+            hB.close()
+
+    exact = A.double() @ B.double()
+    errs = {}
+    for method, k, _ in PRODUCTS:
+        sa, sb = PH[k] if method == "svd" else (None, None)
+        x, y = operands(method)
+        hA = amm.decompose(x, method, k, "left", sketch=sa, compute="bf16" if method == "svd" else "f32")
+        hB = amm.decompose(y, method, k, "right", sketch=sb, compute="bf16" if method == "svd" else "f32")
+        Ck = amm.approx_matmul(hA, hB)
+        errs["%s_k%d" % (method, k)] = float(torch.linalg.norm(Ck.double() - exact) / torch.linalg.norm(exact))
+    del exact
+    ms = _device_ms(step, args.steps, args.warmup, dist)
+    fl = work_flops(PRODUCTS)
+    return {"ms_per_step": ms, "value": fl / (ms * 1e-3) / 1e12, "unit": UNIT, "speedup_vs_fp32": fp32_ms / ms,
+            "approx_rel_err_vs_exact": errs,
+            "modes": "circulant: BF16 operands; rSVD: BF16 operands + BF16 tcgen05 GEMMs; sparsifiers: FP32"}
+
+
+def batched_form(args, dev, dist, count=256):
+    """256 independent forward products of log-uniform sizes n in [128, 4096] (powers of two),
+    methods in rotation, k = ceil(n/32), FP32: one at a time on one stream versus one CUDA-graph
+    launch of the batch scheduler.  Operands: N(0,1) plus a rank-8 part, drawn on the device."""
+    import torch
+    import paper_2504_19308_gb300 as amm
+    sizes = synth.batch_sizes(count, seed=0)
+    methods = ["circulant", "svd", "fourier", "cycle"]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    items = []
+    for i, n in enumerate(sizes):
+        k = max(1, math.ceil(n / 32))
+        mk = lambda: (torch.randn((n, n), generator=gen, device=dev) +
+                      torch.randn((n, 8), generator=gen, device=dev) @ torch.randn((8, n), generator=gen, device=dev))
+        A, B = mk(), mk()
+        C = torch.empty((n, n), device=dev)
+        sk = ((torch.randn((n, k), generator=gen, device=dev), torch.randn((n, k), generator=gen, device=dev))
+              if methods[i % 4] == "svd" else (None, None))
+        items.append((A, B, C, methods[i % 4], k, sk[0], sk[1]))
+
+    def eager():
+        for A, B, C, method, k, sa, sb in items:
+            hA = amm.decompose(A, method, k, "left", sketch=sa)
+            hB = amm.decompose(B, method, k, "right", sketch=sb)
+            amm.approx_matmul(hA, hB, out=C)
+            hA.close()
+            hB.close()
+
+    batch = amm.Batch()
+    for A, B, C, method, k, sa, sb in items:
+        batch.add(A, B, C, method, k, sketch_a=sa, sketch_b=sb)
+    batch.run(use_graph=True)  # eager pass + capture
+    torch.cuda.synchronize()
+    eager_ms = _device_ms(eager, max(1, args.steps // 5), 1, dist)
+    graph_ms = _device_ms(lambda: batch.run(use_graph=True), max(1, args.steps // 5), 1, dist)
+    batch.close()
+    fl = sum(2.0 * n ** 3 for n in sizes)
+    return {"products": count, "sizes": "n = 2^round(log2 U(ln 128, ln 4096)) (%d..%d), k = ceil(n/32), "
+            "methods in rotation, forward" % (min(sizes), max(sizes)),
+            "eager_ms": eager_ms, "graph_ms": graph_ms, "speedup": eager_ms / graph_ms,
+            "value": fl / (graph_ms * 1e-3) / 1e12, "unit": UNIT}
 
 
 # dram bytes per launch from the ncu capture summarised in profiles/ (None = not captured for
@@ -354,6 +464,8 @@ def main():
         cfg = config_block()
         cfg["approx_rel_err_vs_exact"] = r["errs"]
         cfg["kernels_ms"] = {k: round(v[1] / args.steps, 4) for k, v in r["kernels"].items()}
+        cfg["bf16_form"] = r["bf16"]
+        cfg["batched_form"] = r["batched"]
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,

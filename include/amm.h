@@ -131,7 +131,10 @@ amm_status_t amm_decompose(const void* A, int64_t rows, int64_t cols, int64_t ld
  * C = Re(M) = Re(A~ B + dA B~)  (Eq. (2.3); Alg. 3 for circulant; Section 2.2 for SVD).
  *
  *   hA      handle of A (role AMM_LEFT), hB handle of B (role AMM_RIGHT); A is m x n,
- *           B is n x p (inner dimensions must match, methods must be equal).
+ *           B is n x p (inner dimensions must match).  The two methods may differ (the
+ *           paper lets each operand use its own decomposition): C is then evaluated as
+ *           Re(A~) B + (A - Re A~) Re(B~) + Im(A~) Im(B~), each term one operand's truncation
+ *           applied to a dense matrix.  Mixed products need FP32 operands.
  *   C       device pointer, m x p FP32 row-major, leading dimension ldc >= p.  Overwritten.
  *   stream  stream of the call; must be ordered after the decompositions' streams.
  */
@@ -152,8 +155,8 @@ amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, float* C, int64
  *                       dB = Re[W (A~_a^T dC + P_B(dA~^T dC))]  with the element masks P_A, P_B
  *                       (Alg. 5 differentiated with the masks frozen).
  *   dC  device m x p FP32 (lddc).  dA (m x n, ldda) and dB (n x p, lddb) are overwritten;
- *   either may be NULL to skip it.  AMM_CIRCULANT additionally needs dB 8-byte aligned with
- *   an even lddb.
+ *   either may be NULL to skip it.  Handles of different methods return
+ *   AMM_ERR_NOT_IMPLEMENTED.
  */
 amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const float* dC,
                                         int64_t lddc, float* dA, int64_t ldda, float* dB,

@@ -585,6 +585,13 @@ def product(method: str, ta: Truncation, tb: Truncation) -> np.ndarray:
     return first_order(ta, tb).real
 
 
+def mixed_product(ta: Truncation, tb: Truncation) -> np.ndarray:
+    """Re(M) when A and B are truncated by different methods (Section 1: the decompositions of the
+    two operands may differ).  Eq. (2.3) with each side's space-domain truncation; for the
+    Fourier sparsifier that is A_s = A~_a W (left) or B_s = W^* B~_a (right)."""
+    return first_order(ta, tb).real
+
+
 def backward(method: str, ta, tb, g):
     return {"circulant": cd_backward, "svd": svd_backward, "cycle": cycle_backward,
             "fourier": fourier_backward}[method](ta, tb, g)

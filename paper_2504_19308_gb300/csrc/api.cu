@@ -359,7 +359,6 @@ static amm_status_t check_pair(Handle* a, Handle* b) {
   if (a->cols != b->rows)
     return fail(AMM_ERR_STATE, "inner dimensions differ: A is %lldx%lld, B is %lldx%lld", (long long)a->rows,
                 (long long)a->cols, (long long)b->rows, (long long)b->cols);
-  if (a->method != b->method) return fail(AMM_ERR_NOT_IMPLEMENTED, "mixed methods are not built yet");
   return AMM_OK;
 }
 
@@ -373,10 +372,9 @@ extern "C" amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, floa
                                  (long long)b->cols);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
+  if (a->method != b->method) return mixed_matmul(a, b, C, ldc, st);
   if (a->method == AMM_CIRCULANT) {
     const int n = (int)a->rows;
-    if ((ldc & 1) != 0 || ((uintptr_t)C & 7) != 0)
-      return fail(AMM_ERR_INVALID_ARG, "circulant: C must be 8-byte aligned with an even ldc");
     auto &ca = a->cd, &cb = b->cd;
     // Re M = A~_w dB_w  +  Y V  +  A B~_w
     if ((e = cd_apply(n, false, cb.resid, n, false, n, ca.tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr, nullptr, C,
@@ -413,8 +411,6 @@ static amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ld
   const int n = (int)a->rows;
   auto &ca = a->cd, &cb = b->cd;
   const float2* tw = ca.tw;
-  if (dB && (((lddb & 1) != 0) || ((uintptr_t)dB & 7) != 0))
-    return fail(AMM_ERR_INVALID_ARG, "circulant backward: dB must be 8-byte aligned with an even lddb");
   const size_t kh = (size_t)n / 2 + 1;
   std::vector<void*> tmp;
   cudaError_t e = cudaSuccess;
@@ -429,9 +425,6 @@ static amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ld
   float2* RX = (float2*)al(sizeof(float2) * kh * n);
   float2* K = (float2*)al(sizeof(float2) * (size_t)std::max(ca.cap, cb.cap) * n);
   float* T = dB ? (float*)al(sizeof(float) * (size_t)n * n) : nullptr;
-  auto clear_rx = [&]() {
-    if (e == cudaSuccess) e = cudaMemsetAsync(RX, 0, sizeof(float2) * kh * n, st);
-  };
 #define STEP(x) \
   if (e == cudaSuccess) e = (x)
   if (dA) {
@@ -440,15 +433,13 @@ static amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ld
     STEP(bw_spectrum(n, false, G, ldg, tw, X1, st));
     STEP(bw_spectrum(n, false, cb.resid, n, tw, X2, st));
     STEP(cd_sddmm(n, X1, X2, ca.so.ulist, ca.so.counts, ca.cap, K, nullptr, nullptr, st));
-    clear_rx();
     STEP(cd_rho(n, K, tw, ca.so.ulist, ca.so.counts, ca.cap, RX, nullptr, nullptr, st));
     STEP(cd_residual(n, RX, tw, ca.so.wfull, 2, nullptr, dA, st, ldda, 1));
     // unpaired: (i v_t) R_t(G V_B^T) D^t, only when both selections split a pair (device gates)
-    STEP(bw_spectrum(n, false, cb.imag, n, tw, X2, st));
-    clear_rx();
+    STEP(bw_spectrum(n, false, cb.imag, n, tw, X2, st, ca.so.counts + 1, cb.so.counts + 1));
     STEP(cd_sddmm(n, X1, X2, ca.so.dlist, ca.so.counts + 1, ca.cap, K, ca.so.counts + 1, cb.so.counts + 1, st));
     STEP(cd_rho(n, K, tw, ca.so.dlist, ca.so.counts + 1, ca.cap, RX, ca.so.counts + 1, cb.so.counts + 1, st));
-    STEP(cd_residual(n, RX, tw, ca.so.vfull, 3, ca.so.counts + 1, dA, st, ldda, 1));
+    STEP(cd_residual(n, RX, tw, ca.so.vfull, 3, ca.so.counts + 1, dA, st, ldda, 1, cb.so.counts + 1));
   }
   if (dB) {
     // A~_w^T G (columns of G, coefficient L^A_t(t - p)), then the projection terms of dA^T G
@@ -457,16 +448,14 @@ static amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ld
     STEP(cd_residual(n, ca.R, tw, ca.so.wfull, 0, nullptr, T, st, n, 0));  // dA_w
     STEP(bw_spectrum(n, true, T, n, tw, X2, st));
     STEP(cd_sddmm(n, X2, X1, cb.so.ulist, cb.so.counts, cb.cap, K, nullptr, nullptr, st));
-    clear_rx();
     STEP(cd_rho(n, K, tw, cb.so.ulist, cb.so.counts, cb.cap, RX, nullptr, nullptr, st));
     STEP(cd_residual(n, RX, tw, cb.so.wfull, 2, nullptr, dB, st, lddb, 1));
     // unpaired: (i v_s) R_s(Y_A^T G) D^s with Y_A = Im A~
-    STEP(cd_residual(n, ca.R, tw, ca.so.vfull, 1, ca.so.counts + 1, T, st, n, 0));
-    STEP(bw_spectrum(n, true, T, n, tw, X2, st));
-    clear_rx();
+    STEP(cd_residual(n, ca.R, tw, ca.so.vfull, 1, ca.so.counts + 1, T, st, n, 0, cb.so.counts + 1));
+    STEP(bw_spectrum(n, true, T, n, tw, X2, st, ca.so.counts + 1, cb.so.counts + 1));
     STEP(cd_sddmm(n, X2, X1, cb.so.dlist, cb.so.counts + 1, cb.cap, K, ca.so.counts + 1, cb.so.counts + 1, st));
     STEP(cd_rho(n, K, tw, cb.so.dlist, cb.so.counts + 1, cb.cap, RX, ca.so.counts + 1, cb.so.counts + 1, st));
-    STEP(cd_residual(n, RX, tw, cb.so.vfull, 3, cb.so.counts + 1, dB, st, lddb, 1));
+    STEP(cd_residual(n, RX, tw, cb.so.vfull, 3, cb.so.counts + 1, dB, st, lddb, 1, ca.so.counts + 1));
   }
 #undef STEP
   for (void* q : tmp) dev_free(q, st);
@@ -483,6 +472,8 @@ extern "C" amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t
   if (!dC) return fail(AMM_ERR_INVALID_ARG, "backward: dC is NULL");
   if (lddc < b->cols || (dA && ldda < a->cols) || (dB && lddb < b->cols))
     return fail(AMM_ERR_INVALID_ARG, "backward: leading dimension too small");
+  if (a->method != b->method)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "backward of a mixed-method product is not built");
   if (a->method == AMM_SVD) return svd_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
   if (a->method == AMM_CIRCULANT) return cd_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
   if (a->method == AMM_SPARSE_CYCLE) {

@@ -50,8 +50,8 @@ struct amm_handle {
     float* Q = nullptr;      // rows x k, orthonormal columns spanning A phi
     float* X = nullptr;      // k x cols, Q^T A
     double* norms = nullptr; // ||A||_F^2, ||X||_F^2
-    // tensor-core path: K-major copies in the compute type E (FP32 for TF32X3, BF16)
-    bool tc = false, bf16 = false;
+    // K-major copies in the compute type E of the tensor-core GEMMs (FP32 for TF32X3, BF16)
+    bool bf16 = false;
     const void* Xe = nullptr;  // rows x cols (the input itself when it already fits)
     int64_t ldxe = 0;
     void *XTe = nullptr, *Qe = nullptr, *QTe = nullptr, *Ze = nullptr, *ZTe = nullptr;
@@ -77,5 +77,13 @@ amm_status_t svd_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_
 amm_status_t svd_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, float* dB,
                           int64_t lddb, cudaStream_t st);
 amm_status_t svd_info(Handle* h, amm_info_t* info);
+cudaError_t svd_left_apply(Handle* a, const float* X, int64_t ldx, int64_t p, float* C, int64_t ldc, float beta,
+                           cudaStream_t st);
+cudaError_t svd_right_apply(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc, float beta,
+                            cudaStream_t st);
+cudaError_t svd_residual(Handle* a, float* D, int64_t ldd, cudaStream_t st);
+// mixed.cu
+amm_status_t mixed_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st);
+
 amm_status_t svd_get_sketch(Handle* h, float* host_phi, int64_t cap);
 }  // namespace amm

@@ -25,12 +25,17 @@ namespace amm {
 // Output layout [q][vector], q = 0..n/2.  Packed pairs of real vectors per complex FFT.
 template <int N, int S, int NT, bool ROW>
 __global__ void __launch_bounds__(NT) bw_spectrum_kernel(const float* __restrict__ X, int64_t ldx,
-                                                         const float2* __restrict__ tw, float2* __restrict__ Xh) {
+                                                         const float2* __restrict__ tw, float2* __restrict__ Xh,
+                                                         const int32_t* __restrict__ gate0,
+                                                         const int32_t* __restrict__ gate1) {
   extern __shared__ float2 smem[];
+  if (gate0 != nullptr && (*gate0 == 0 || *gate1 == 0)) return;
   constexpr int LD = fft_padded_len(N);
   constexpr int KH = N / 2 + 1;
   const int base = blockIdx.x * 2 * S;
-  for (int e = threadIdx.x; e < N * S; e += NT) {
+#pragma unroll 8
+  for (int it = 0; it < N * S / NT; ++it) {
+    const int e = threadIdx.x + it * NT;
     int s, l;
     if (ROW) { s = e / N; l = e % N; } else { l = e / S; s = e % S; }
     const int v0 = base + 2 * s;
@@ -57,7 +62,10 @@ __global__ void __launch_bounds__(NT) bw_spectrum_kernel(const float* __restrict
 // K[u][p] = sum_m Xh(p, m) Yh((t_u - p) mod n, m) for t_u <= n/2, p = 0..n-1.  Half-spectrum rows
 // q > n/2 are conj(row n - q).  One warp per (p, block of SD_UB listed components); lanes stride
 // over m, so each Xh element is loaded once for SD_UB products (9 bytes per complex MAC instead
-// of 16) and the SD_UB independent loads of Yh overlap.
+// of 16) and the SD_UB independent loads of Yh overlap.  The component blocks are the fast grid
+// dimension: the CTAs in flight share a narrow window of p, so the Xh rows of the window and
+// the Yh rows t - p (each used by every t whose window covers it) stay in L2 while the spectra
+// themselves (2 x 64 MiB at n = 4096) do not fit.
 constexpr int SD_UB = 8;
 template <int N>
 __global__ void __launch_bounds__(256) cd_sddmm_kernel(const float2* __restrict__ Xh, const float2* __restrict__ Yh,
@@ -67,10 +75,10 @@ __global__ void __launch_bounds__(256) cd_sddmm_kernel(const float2* __restrict_
                                                        const int32_t* __restrict__ gate1) {
   if (gate0 != nullptr && (*gate0 == 0 || *gate1 == 0)) return;
   const int cnt = *count;
-  const int u0 = blockIdx.y * SD_UB;
+  const int u0 = blockIdx.x * SD_UB;
   if (u0 >= cnt) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.x * 8 + warp;
+  const int p = blockIdx.y * 8 + warp;
   const bool xm = p > N / 2;
   const float2* xr = Xh + (int64_t)(xm ? N - p : p) * N;
   const float xs = xm ? -1.f : 1.f;
@@ -161,17 +169,18 @@ template <int N> struct BwOps {
     }();
     return e;
   }
-  static cudaError_t spectrum(bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh, cudaStream_t st) {
+  static cudaError_t spectrum(bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh,
+                              const int32_t* g0, const int32_t* g1, cudaStream_t st) {
     cudaError_t e = attrs();
     if (e != cudaSuccess) return e;
     dim3 grid(N / (2 * C::S));
-    if (row) bw_spectrum_kernel<N, C::S, C::NT, true><<<grid, C::NT, C::SMEM, st>>>(X, ldx, tw, Xh);
-    else bw_spectrum_kernel<N, C::S, C::NT, false><<<grid, C::NT, C::SMEM, st>>>(X, ldx, tw, Xh);
+    if (row) bw_spectrum_kernel<N, C::S, C::NT, true><<<grid, C::NT, C::SMEM, st>>>(X, ldx, tw, Xh, g0, g1);
+    else bw_spectrum_kernel<N, C::S, C::NT, false><<<grid, C::NT, C::SMEM, st>>>(X, ldx, tw, Xh, g0, g1);
     return cudaGetLastError();
   }
   static cudaError_t sddmm(const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
                            float2* K, const int32_t* g0, const int32_t* g1, cudaStream_t st) {
-    dim3 grid(N / 8, (cap + SD_UB - 1) / SD_UB);
+    dim3 grid((cap + SD_UB - 1) / SD_UB, N / 8);
     cd_sddmm_kernel<N><<<grid, 256, 0, st>>>(Xh, Yh, list, count, K, g0, g1);
     return cudaGetLastError();
   }
@@ -200,10 +209,11 @@ template <int N> struct BwOps {
     default: return cudaErrorInvalidValue;        \
   }
 
-cudaError_t bw_spectrum(int n, bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh, cudaStream_t st) {
+cudaError_t bw_spectrum(int n, bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh, cudaStream_t st,
+                        const int32_t* gate0, const int32_t* gate1) {
   AMM_TRACE_W(row ? "bw_row_spectrum" : "bw_col_spectrum", st, 0.0, (double)n * n * 4 + (n / 2 + 1.0) * n * 8,
               nullptr);
-  AMM_BW_DISPATCH(n, return BwOps<NN>::spectrum(row, X, ldx, tw, Xh, st));
+  AMM_BW_DISPATCH(n, return BwOps<NN>::spectrum(row, X, ldx, tw, Xh, gate0, gate1, st));
 }
 
 cudaError_t cd_sddmm(int n, const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,

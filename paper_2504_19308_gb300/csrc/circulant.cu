@@ -56,7 +56,10 @@ __global__ void __launch_bounds__(NT) cd_spectrum_kernel(const T* __restrict__ A
   const int j0 = blockIdx.x * J;
   float* fs = reinterpret_cast<float*>(smem);
   // gather: element (r, q): column c = (r - j0 - (J-1) + q) mod n holds cycle m = J-1-q at l = c
-  for (int e = threadIdx.x; e < N * J; e += NT) {
+  static_assert((N * J) % NT == 0, "whole iterations");
+#pragma unroll 8
+  for (int it = 0; it < N * J / NT; ++it) {  // unrolled: several loads in flight per thread
+    const int e = threadIdx.x + it * NT;
     const int r = e / J, q = e % J;
     const int c = (r - j0 - (J - 1) + q) & (N - 1);
     const int m = J - 1 - q;
@@ -355,34 +358,45 @@ template <int N, int S, int NT>
 __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restrict__ R, const float2* __restrict__ tw,
                                                          const float* __restrict__ gfull, int mode,
                                                          const int32_t* __restrict__ dcount,
+                                                         const int32_t* __restrict__ dcount2,
                                                          float* __restrict__ X, int64_t ldx, int accumulate) {
   extern __shared__ float2 smem[];
   if ((mode & 1) && dcount != nullptr && *dcount == 0) return;
+  if (dcount2 != nullptr && *dcount2 == 0) return;
   constexpr int J = 2 * S;
   constexpr int LD = fft_padded_len(N);
   const int j0 = blockIdx.x * J;
   // packed signal s: Z(k) = g_k (r_{j0+2s,k} + i r_{j0+2s+1,k}), k in [0, n)
-  for (int e = threadIdx.x; e < N * S; e += NT) {
+#pragma unroll 8
+  for (int it = 0; it < N * S / NT; ++it) {
+    const int e = threadIdx.x + it * NT;
     const int k = e / S, s = e % S;
-    const bool mir = k > N / 2;
-    const int kr = mir ? N - k : k;
-    const float4 rr = *reinterpret_cast<const float4*>(R + (int64_t)kr * N + j0 + 2 * s);
-    float2 r1 = make_float2(rr.x, rr.y), r2 = make_float2(rr.z, rr.w);
-    if (mir) { r1 = cconj(r1); r2 = cconj(r2); }
-    float2 z = make_float2(r1.x - r2.y, r1.y + r2.x);
     const float g = gfull[k];
-    switch (mode) {
-      case 0: z = cscale(z, 1.f - g); break;                   // (1 - w_k)
-      case 1: z = make_float2(g * z.y, -g * z.x); break;       // -i v_k
-      case 2: z = cscale(z, g); break;                         // w_k
-      default: z = make_float2(-g * z.y, g * z.x); break;      // +i v_k
+    const float c = mode == 0 ? 1.f - g : g;
+    float2 z = make_float2(0.f, 0.f);
+    if (c != 0.f) {  // rows with a zero coefficient are neither read nor required to be set
+      const bool mir = k > N / 2;
+      const int kr = mir ? N - k : k;
+      const float4 rr = *reinterpret_cast<const float4*>(R + (int64_t)kr * N + j0 + 2 * s);
+      float2 r1 = make_float2(rr.x, rr.y), r2 = make_float2(rr.z, rr.w);
+      if (mir) { r1 = cconj(r1); r2 = cconj(r2); }
+      z = make_float2(r1.x - r2.y, r1.y + r2.x);
+      switch (mode) {
+        case 0: z = cscale(z, c); break;                         // (1 - w_k)
+        case 1: z = make_float2(c * z.y, -c * z.x); break;       // -i v_k
+        case 2: z = cscale(z, c); break;                         // w_k
+        default: z = make_float2(-c * z.y, c * z.x); break;      // +i v_k
+      }
     }
     smem[s * LD + fpad(k)] = z;
   }
   __syncthreads();
   fft_smem<N, S, NT, true>(smem, tw);
   const float* fs = reinterpret_cast<const float*>(smem);
-  for (int e = threadIdx.x; e < N * J; e += NT) {
+  static_assert((N * J) % NT == 0, "whole iterations");
+#pragma unroll 8
+  for (int it = 0; it < N * J / NT; ++it) {  // unrolled: several loads in flight per thread
+    const int e = threadIdx.x + it * NT;
     const int r = e / J, q = e % J;
     const int c = (r - j0 - (J - 1) + q) & (N - 1);
     const int m = J - 1 - q;
@@ -406,7 +420,7 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
                                                       const int32_t* __restrict__ count,
                                                       const int32_t* __restrict__ gate0,
                                                       const int32_t* __restrict__ gate1, float* __restrict__ out,
-                                                      int64_t ldo, int accumulate) {
+                                                      int64_t ldo, int accumulate, int nvec) {
   extern __shared__ float2 smem[];
   if (gate0 != nullptr && (*gate0 == 0 || *gate1 == 0)) return;
   constexpr int LD = fft_padded_len(N);
@@ -414,16 +428,22 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
   static_assert(N % NT == 0, "NT must divide N");
   const int base = blockIdx.x * 2 * S;
   if (!ROW) {
-    for (int e = threadIdx.x; e < N * S; e += NT) {
+#pragma unroll 8
+    for (int it = 0; it < N * S / NT; ++it) {
+      const int e = threadIdx.x + it * NT;
       const int l = e / S, s = e % S;
-      const T* p = X + (int64_t)l * ldx + base + 2 * s;
-      smem[s * LD + fpad(l)] = make_float2(ld_as_float<T>(p), ld_as_float<T>(p + 1));
+      const int v = base + 2 * s;
+      const T* p = X + (int64_t)l * ldx + v;
+      smem[s * LD + fpad(l)] = make_float2(v < nvec ? ld_as_float<T>(p) : 0.f, v + 1 < nvec ? ld_as_float<T>(p + 1) : 0.f);
     }
   } else {
-    for (int e = threadIdx.x; e < N * S; e += NT) {
+#pragma unroll 8
+    for (int it = 0; it < N * S / NT; ++it) {
+      const int e = threadIdx.x + it * NT;
       const int s = e / N, l = e % N;
-      const T* p = X + (int64_t)(base + 2 * s) * ldx + l;
-      smem[s * LD + fpad(l)] = make_float2(ld_as_float<T>(p), ld_as_float<T>(p + ldx));
+      const int v = base + 2 * s;
+      const T* p = X + (int64_t)v * ldx + l;
+      smem[s * LD + fpad(l)] = make_float2(v < nvec ? ld_as_float<T>(p) : 0.f, v + 1 < nvec ? ld_as_float<T>(p + ldx) : 0.f);
     }
   }
   __syncthreads();
@@ -455,22 +475,30 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
   fft_smem<N, S, NT, true>(smem, tw);
   constexpr float inv_n = 1.0f / (float)N;
   if (!ROW) {
+    const bool vec2 = ((ldo & 1) == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);  // pairs as float2
     for (int e = threadIdx.x; e < N * S; e += NT) {
       const int l = e / S, s = e % S;
+      const int v = base + 2 * s;
       float2 z = cscale(smem[s * LD + fpad(l)], inv_n);
-      float2* o = reinterpret_cast<float2*>(out + (int64_t)l * ldo + base + 2 * s);
-      if (accumulate) { float2 old = *o; z.x += old.x; z.y += old.y; }
-      *o = z;
+      float* o = out + (int64_t)l * ldo + v;
+      if (v + 1 < nvec && vec2) {
+        float2* o2 = reinterpret_cast<float2*>(o);
+        if (accumulate) { float2 old = *o2; z.x += old.x; z.y += old.y; }
+        *o2 = z;
+      } else {
+        if (v < nvec) o[0] = accumulate ? o[0] + z.x : z.x;
+        if (v + 1 < nvec) o[1] = accumulate ? o[1] + z.y : z.y;
+      }
     }
   } else {
     for (int e = threadIdx.x; e < N * S; e += NT) {
       const int s = e / N, l = e % N;
+      const int v = base + 2 * s;
       float2 z = cscale(smem[s * LD + fpad(l)], inv_n);
-      float* o0 = out + (int64_t)(base + 2 * s) * ldo + l;
+      float* o0 = out + (int64_t)v * ldo + l;
       float* o1 = o0 + ldo;
-      if (accumulate) { z.x += *o0; z.y += *o1; }
-      *o0 = z.x;
-      *o1 = z.y;
+      if (v < nvec) *o0 = accumulate ? *o0 + z.x : z.x;
+      if (v + 1 < nvec) *o1 = accumulate ? *o1 + z.y : z.y;
     }
   }
 }
@@ -527,11 +555,11 @@ template <int N> struct CdOps {
     return cudaGetLastError();
   }
   static cudaError_t residual(const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
-                              float* X, int64_t ldx, int accumulate, cudaStream_t st) {
+                              const int32_t* dcount2, float* X, int64_t ldx, int accumulate, cudaStream_t st) {
     static cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
-    cd_residual_kernel<N, C::S, C::NT><<<N / (2 * C::S), C::NT, C::SMEM, st>>>(R, tw, g, mode, dcount, X, ldx,
-                                                                              accumulate);
+    cd_residual_kernel<N, C::S, C::NT><<<N / (2 * C::S), C::NT, C::SMEM, st>>>(R, tw, g, mode, dcount, dcount2, X,
+                                                                              ldx, accumulate);
     return cudaGetLastError();
   }
   static cudaError_t apply(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
@@ -539,12 +567,12 @@ template <int N> struct CdOps {
                            const int32_t* gate1, float* out, int64_t ldo, int accumulate, int rev, cudaStream_t st) {
     static cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
-    dim3 grid((unsigned)(nvec / (2 * C::S)));
+    dim3 grid((unsigned)((nvec + 2 * C::S - 1) / (2 * C::S)));
     const bool r = rev < 0 ? row : rev != 0;
 #define AMM_APPLY_LAUNCH(ROW_, REV_, T_)                                                                    \
   cd_apply_kernel<N, C::S, C::NT, ROW_, REV_, T_><<<grid, C::NT, C::SMEM, st>>>((const T_*)X, ldx, tw, list, Lc, \
                                                                                 count, gate0, gate1, out, ldo,  \
-                                                                                accumulate)
+                                                                                accumulate, (int)nvec)
     if (row && r) {
       if (bf16) AMM_APPLY_LAUNCH(true, true, __nv_bfloat16);
       else AMM_APPLY_LAUNCH(true, true, float);
@@ -625,11 +653,11 @@ cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* li
 }
 
 cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
-                        float* X, cudaStream_t st, int64_t ldx, int accumulate) {
+                        float* X, cudaStream_t st, int64_t ldx, int accumulate, const int32_t* dcount2) {
   if (ldx <= 0) ldx = n;
   AMM_TRACE_W(mode == 0 ? "cd_residual" : (mode == 1 ? "cd_residual_imag" : "cd_project"), st, 0.0,
               (mode & 1) ? 0.0 : (n / 2 + 1.0) * n * 8 + (double)n * n * 4 * (accumulate ? 2 : 1), nullptr);
-  AMM_DISPATCH_N(n, return CdOps<NN>::residual(R, tw, g, mode, dcount, X, ldx, accumulate, st));
+  AMM_DISPATCH_N(n, return CdOps<NN>::residual(R, tw, g, mode, dcount, dcount2, X, ldx, accumulate, st));
 }
 
 cudaError_t cd_apply(int n, bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,

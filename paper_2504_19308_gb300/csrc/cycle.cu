@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __re
   __syncthreads();
   for (int r = threadIdx.x; r < n; r += CYC_NT) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
     for (int u = 0; u < k; ++u) {
       const int l = (r - __ldg(sel + u)) & (n - 1);
       const float a = __ldg(cyc + (int64_t)u * n + l);
@@ -82,7 +83,8 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __re
   }
 }
 
-// out(r0..r0+3, :) += sum_u dA(r, c + s_u) cycB[u][c]
+// out(r0..r0+3, :) += sum_u dA(r, c + s_u) cycB[u][c]; dA = A with the kept cycles of A masked
+// (inselA), or A itself when inselA is NULL
 __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __restrict__ A, int64_t lda, int n,
                                                                const unsigned char* __restrict__ inselA,
                                                                const int32_t* __restrict__ selB, int kb,
@@ -93,12 +95,13 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __re
   for (int e = threadIdx.x; e < CYC_RW * n; e += CYC_NT) {
     const int rr = e / n, q = e % n, r = r0 + rr;
     float v = 0.f;
-    if (r < nrows && !inselA[(r - q) & (n - 1)]) v = __ldg(A + (int64_t)r * lda + q);
+    if (r < nrows && (inselA == nullptr || !inselA[(r - q) & (n - 1)])) v = __ldg(A + (int64_t)r * lda + q);
     ar[e] = v;
   }
   __syncthreads();
   for (int c = threadIdx.x; c < n; c += CYC_NT) {
     float acc[CYC_RW] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
     for (int u = 0; u < kb; ++u) {
       const int q = (c + __ldg(selB + u)) & (n - 1);
       const float b = __ldg(cycB + (int64_t)u * n + c);
@@ -129,6 +132,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_row_kernel(const float* __restr
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += CYC_NT) {
     float acc[CYC_RW] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
     for (int u = 0; u < kb; ++u) {
       const int l = (q - __ldg(selB + u)) & (n - 1);
       const float b = __ldg(cycB + (int64_t)u * n + l);
@@ -154,6 +158,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_col_kernel(const float* __restr
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += CYC_NT) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
     for (int u = 0; u < ka; ++u) {
       const float a = __ldg(cycA + (int64_t)u * n + q);
       const float4 g = gp[(q + __ldg(selA + u)) & (n - 1)];
@@ -182,6 +187,7 @@ __global__ void __launch_bounds__(256) cyc_bw_proj_rows_kernel(const float* __re
   const float* g = G + (int64_t)((l + t) & (n - 1)) * ldg;
   const float* b = B + (int64_t)l * ldb;
   float acc = 0.f;
+#pragma unroll 8
   for (int m = lane; m < n; m += 32)
     if (!inselB[(l - m) & (n - 1)]) acc = fmaf(__ldg(g + m), __ldg(b + m), acc);
 #pragma unroll
@@ -201,6 +207,7 @@ __global__ void __launch_bounds__(256) cyc_bw_proj_cols_kernel(const float* __re
   if (l >= n) return;
   const int q = (l + s) & (n - 1);
   float acc = 0.f;
+#pragma unroll 8
   for (int r = 0; r < n; ++r) {
     const float a = inselA[(r - q) & (n - 1)] ? 0.f : __ldg(A + (int64_t)r * lda + q);
     acc = fmaf(a, __ldg(G + (int64_t)r * ldg + l), acc);
@@ -295,6 +302,58 @@ cudaError_t cyc_apply(int n, const float* A, int64_t lda, const float* B, int64_
     cyc_apply_row_kernel<<<(n + CYC_RW - 1) / CYC_RW, CYC_NT, sizeof(float) * CYC_RW * n, st>>>(
         A, lda, n, inselA, selB, kb, cycB, C, ldc, n);
   }
+  return cudaGetLastError();
+}
+
+// ============================================================================ mixed-method pieces
+// D = A with the kept cycles zeroed (the dense residual dA = A - A_s)
+__global__ void cyc_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
+                                    const unsigned char* __restrict__ insel, float* __restrict__ D, int64_t ldd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int r = (int)(e / n), c = (int)(e % n);
+  D[(int64_t)r * ldd + c] = insel[(r - c) & (n - 1)] ? 0.f : __ldg(A + (int64_t)r * lda + c);
+}
+
+static cudaError_t cyc_attrs() {
+  static cudaError_t e = [] {
+    cudaError_t r = cudaFuncSetAttribute((const void*)cyc_apply_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8192 * (int)sizeof(float4));
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute((const void*)cyc_apply_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               CYC_RW * 8192 * (int)sizeof(float));
+    return r;
+  }();
+  return e;
+}
+
+// C = A_s X for X (n x p)
+cudaError_t cyc_left_apply(int n, const int32_t* selA, int ka, const float* cycA, const float* X, int64_t ldx,
+                           int64_t p, float* C, int64_t ldc, cudaStream_t st) {
+  cudaError_t e = cyc_attrs();
+  if (e != cudaSuccess) return e;
+  AMM_TRACE_W("cyc_apply_col", st, 2.0 * ka * (double)n * p, 8.0 * n * (double)p, nullptr);
+  cyc_apply_col_kernel<<<(unsigned)((p + CYC_CW - 1) / CYC_CW), CYC_NT, sizeof(float4) * n, st>>>(X, ldx, n, selA, ka,
+                                                                                                  cycA, C, ldc, (int)p);
+  return cudaGetLastError();
+}
+
+// C += Y B_s for Y (m x n)
+cudaError_t cyc_right_apply(int n, const int32_t* selB, int kb, const float* cycB, const float* Y, int64_t ldy,
+                            int64_t m, float* C, int64_t ldc, cudaStream_t st) {
+  cudaError_t e = cyc_attrs();
+  if (e != cudaSuccess) return e;
+  AMM_TRACE_W("cyc_apply_row", st, 2.0 * kb * (double)n * m, 12.0 * n * (double)m, nullptr);
+  cyc_apply_row_kernel<<<(unsigned)((m + CYC_RW - 1) / CYC_RW), CYC_NT, sizeof(float) * CYC_RW * n, st>>>(
+      Y, ldy, n, nullptr, selB, kb, cycB, C, ldc, (int)m);
+  return cudaGetLastError();
+}
+
+cudaError_t cyc_residual(int n, const float* A, int64_t lda, const unsigned char* insel, float* D, int64_t ldd,
+                         cudaStream_t st) {
+  AMM_TRACE_W("cyc_residual", st, 0.0, 8.0 * n * (double)n, nullptr);
+  const int64_t tot = (int64_t)n * n;
+  cyc_residual_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A, lda, n, insel, D, ldd);
   return cudaGetLastError();
 }
 

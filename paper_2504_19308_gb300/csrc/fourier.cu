@@ -10,6 +10,7 @@
 //   Bt [kh][p] c64, magBT [p][kh] f32, sel [rows][k] i32 (ascending q), maskT [n][ceil(rows/32)] u32.
 #include <cuda_runtime.h>
 
+#include "api_internal.h"
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.h"
@@ -27,7 +28,9 @@ __global__ void __launch_bounds__(NT) ft_transform_kernel(const float* __restric
   constexpr int LD = fft_padded_len(N);
   constexpr int KH = N / 2 + 1;
   const int base = blockIdx.x * 2 * S;
-  for (int e = threadIdx.x; e < N * S; e += NT) {
+#pragma unroll 8
+  for (int it = 0; it < N * S / NT; ++it) {
+    const int e = threadIdx.x + it * NT;
     int s, l;
     if (ROW) { s = e / N; l = e % N; } else { l = e / S; s = e % S; }
     const int v0 = base + 2 * s, v1 = v0 + 1;
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(256) ft_t1_kernel(const float2* __restrict__ A
   for (int rr = 0; rr < T1_RB; ++rr) acc[rr] = 0.f;
 #pragma unroll
   for (int rr = 0; rr < T1_RB; ++rr) {
+#pragma unroll 8
     for (int u = 0; u < k; ++u) {
       const int q = qs[rr * k + u];
       const float2 a = as[rr * k + u];
@@ -209,7 +213,10 @@ __global__ void __launch_bounds__(256) ft_t1_kernel(const float2* __restrict__ A
 
 // ============================================================================ T2 = Re((A~ - A~_a) B~_a)
 // CTA: CB columns x 256 rows; thread per row i, CB accumulators; A~(i, q) read from At^T.
+// maskT NULL: nothing of A~ is excluded (the dense left operand of a mixed product).  IMAG: the
+// imaginary part instead of the real part.
 constexpr int T2_CB = 8;
+template <bool IMAG>
 __global__ void __launch_bounds__(256) ft_t2_kernel(const float2* __restrict__ AtT, const uint32_t* __restrict__ maskT,
                                                     int mask_words, const int32_t* __restrict__ selB, int k,
                                                     const float2* __restrict__ Bt, int n, int m, int p,
@@ -239,15 +246,19 @@ __global__ void __launch_bounds__(256) ft_t2_kernel(const float2* __restrict__ A
   for (int cc = 0; cc < T2_CB; ++cc) acc[cc] = 0.f;
 #pragma unroll
   for (int cc = 0; cc < T2_CB; ++cc) {
+#pragma unroll 8
     for (int u = 0; u < k; ++u) {
       const int q = qs[cc * k + u];
-      const uint32_t w = __ldg(maskT + (int64_t)q * mask_words + (i >> 5));
-      if ((w >> (i & 31)) & 1u) continue;  // (i, q) kept in A~_a: not part of the residue
+      if (maskT != nullptr) {
+        const uint32_t w = __ldg(maskT + (int64_t)q * mask_words + (i >> 5));
+        if ((w >> (i & 31)) & 1u) continue;  // (i, q) kept in A~_a: not part of the residue
+      }
       const bool mir = q > n / 2;
       float2 a = __ldg(AtT + (int64_t)(mir ? n - q : q) * m + i);
       if (mir) a.y = -a.y;
       const float2 b = bs[cc * k + u];
-      acc[cc] = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[cc]));
+      if (IMAG) acc[cc] = fmaf(a.x, b.y, fmaf(a.y, b.x, acc[cc]));
+      else acc[cc] = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[cc]));
     }
   }
 #pragma unroll
@@ -332,9 +343,126 @@ cudaError_t ft_product(int n, int m, int p, int k_a, int k_b, const float2* At, 
     AMM_TRACE_W("ft_t2", st, 8.0 * m * (double)p * k_b, 12.0 * m * (double)p * k_b + 8.0 * m * p, nullptr);
     dim3 grid((p + T2_CB - 1) / T2_CB, (m + 255) / 256);
     size_t sm = (size_t)T2_CB * k_b * (4 + 8) + 8;
-    ft_t2_kernel<<<grid, 256, sm, st>>>(AtT, maskT, mask_words, selB, k_b, Bt, n, m, p, C, ldc);
+    ft_t2_kernel<false><<<grid, 256, sm, st>>>(AtT, maskT, mask_words, selB, k_b, Bt, n, m, p, C, ldc);
   }
   return cudaGetLastError();
+}
+
+// ============================================================================ mixed-method pieces
+// Dense real or imaginary part of A_s = A~_a W (the sparse rows back in the space domain):
+// part 0: y = Re(A~_a W) through the Hermitian part H(q) = (X(q) + conj X(-q))/2 of each row;
+// part 1: y = Im(A~_a W) through K(q) = -i (X(q) - conj X(-q))/2.  Two rows share one complex
+// FFT (Z = P_{v0} + i P_{v1}).  D = A - y when A is given, else D = y.
+template <int N, int S, int NT>
+__global__ void __launch_bounds__(NT) ft_dense_kernel(const float2* __restrict__ At, const int32_t* __restrict__ sel,
+                                                      int k, int m, const float2* __restrict__ tw, int part,
+                                                      const float* __restrict__ A, int64_t lda, float* __restrict__ D,
+                                                      int64_t ldd) {
+  extern __shared__ float2 smem[];
+  constexpr int LD = fft_padded_len(N);
+  constexpr int KH = N / 2 + 1;
+  const int base = blockIdx.x * 2 * S;
+  for (int e = threadIdx.x; e < S * LD; e += NT) smem[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  if (threadIdx.x < S) {  // one thread per packed pair: its two rows' entries, in order
+    const int s = threadIdx.x;
+    for (int h = 0; h < 2; ++h) {
+      const int r = base + 2 * s + h;
+      if (r >= m) break;
+      for (int u = 0; u < k; ++u) {
+        const int q = __ldg(sel + (int64_t)r * k + u);
+        const bool mir = q > N / 2;
+        float2 x = __ldg(At + (int64_t)r * KH + (mir ? N - q : q));
+        if (mir) x.y = -x.y;
+        float2 cq, cn;  // contributions at q and at -q
+        if (part == 0) { cq = cscale(x, 0.5f); cn = cscale(cconj(x), 0.5f); }
+        else { cq = make_float2(0.5f * x.y, -0.5f * x.x); cn = make_float2(0.5f * x.y, 0.5f * x.x); }
+        if (h == 1) {  // times i
+          cq = make_float2(-cq.y, cq.x);
+          cn = make_float2(-cn.y, cn.x);
+        }
+        float2* zq = smem + s * LD + fpad(q);
+        float2* zn = smem + s * LD + fpad((N - q) & (N - 1));
+        *zq = cadd(*zq, cq);
+        *zn = cadd(*zn, cn);
+      }
+    }
+  }
+  __syncthreads();
+  fft_smem<N, S, NT, false>(smem, tw);
+  const float sc = rsqrtf((float)N);
+  for (int e = threadIdx.x; e < N * 2 * S; e += NT) {
+    const int mm = e / N, l = e % N;
+    const int v = base + mm;
+    if (v >= m) continue;
+    const float2 z = smem[(mm >> 1) * LD + fpad(l)];
+    const float y = sc * ((mm & 1) ? z.y : z.x);
+    D[(int64_t)v * ldd + l] = A ? __ldg(A + (int64_t)v * lda + l) - y : y;
+  }
+}
+
+template <int N> struct FtMixOps {
+  using C = FtCfg<N>;
+  static cudaError_t dense(const float2* At, const int32_t* sel, int k, int m, const float2* tw, int part,
+                           const float* A, int64_t lda, float* D, int64_t ldd, cudaStream_t st) {
+    static cudaError_t attr = cudaFuncSetAttribute((const void*)ft_dense_kernel<N, C::S, C::NT>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (attr != cudaSuccess) return attr;
+    ft_dense_kernel<N, C::S, C::NT><<<(m + 2 * C::S - 1) / (2 * C::S), C::NT, C::SMEM, st>>>(At, sel, k, m, tw, part,
+                                                                                             A, lda, D, ldd);
+    return cudaGetLastError();
+  }
+};
+
+cudaError_t ft_dense(int n, const float2* At, const int32_t* sel, int k, int m, const float2* tw, int part,
+                     const float* A, int64_t lda, float* D, int64_t ldd, cudaStream_t st) {
+  AMM_TRACE_W(part ? "ft_dense_imag" : "ft_dense_real", st, 0.0, (double)m * n * (A ? 8 : 4), nullptr);
+  AMM_FT_DISPATCH(n, return FtMixOps<NN>::dense(At, sel, k, m, tw, part, A, lda, D, ldd, st));
+}
+
+// C = Re(A~_a (W X)) for X (n x p): column transforms of X, then T1
+cudaError_t ft_left_apply(int n, int m, const float2* At, const int32_t* selA, int ka, const float2* tw,
+                          const float* X, int64_t ldx, int p, float* C, int64_t ldc, cudaStream_t st) {
+  const size_t kh = (size_t)n / 2 + 1;
+  float2* Xt = nullptr;
+  float* mag = nullptr;
+  cudaError_t e = dev_alloc((void**)&Xt, sizeof(float2) * kh * p, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&mag, sizeof(float) * kh * p, st);
+  if (e == cudaSuccess) e = ft_transform(n, false, X, ldx, p, tw, Xt, nullptr, mag, st);
+  if (e == cudaSuccess) {
+    AMM_TRACE_W("ft_t1", st, 8.0 * m * (double)p * ka, 8.0 * m * (double)p * ka + 4.0 * m * p, nullptr);
+    dim3 grid((p + 255) / 256, (m + T1_RB - 1) / T1_RB);
+    ft_t1_kernel<<<grid, 256, (size_t)T1_RB * ka * (4 + 8) + 8, st>>>(At, selA, ka, Xt, n, m, p, C, ldc);
+    e = cudaGetLastError();
+  }
+  dev_free(Xt, st);
+  dev_free(mag, st);
+  return e;
+}
+
+// C += Re (or Im) of (Y W^*) B~_a for Y (m x n): row transforms of Y, then T2 without a mask
+cudaError_t ft_right_apply(int n, int p, const float2* Bt, const int32_t* selB, int kb, const float2* tw,
+                           const float* Y, int64_t ldy, int m, bool imag, float* C, int64_t ldc, cudaStream_t st) {
+  const size_t kh = (size_t)n / 2 + 1;
+  float2 *Yt = nullptr, *YtT = nullptr;
+  float* mag = nullptr;
+  cudaError_t e = dev_alloc((void**)&Yt, sizeof(float2) * kh * m, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&YtT, sizeof(float2) * kh * m, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&mag, sizeof(float) * kh * m, st);
+  if (e == cudaSuccess) e = ft_transform(n, true, Y, ldy, m, tw, Yt, YtT, mag, st);
+  if (e == cudaSuccess) {
+    AMM_TRACE_W(imag ? "ft_t2_imag" : "ft_t2", st, 8.0 * m * (double)p * kb, 12.0 * m * (double)p * kb + 8.0 * m * p,
+                nullptr);
+    dim3 grid((p + T2_CB - 1) / T2_CB, (m + 255) / 256);
+    const size_t sm = (size_t)T2_CB * kb * (4 + 8) + 8;
+    if (imag) ft_t2_kernel<true><<<grid, 256, sm, st>>>(YtT, nullptr, 0, selB, kb, Bt, n, m, p, C, ldc);
+    else ft_t2_kernel<false><<<grid, 256, sm, st>>>(YtT, nullptr, 0, selB, kb, Bt, n, m, p, C, ldc);
+    e = cudaGetLastError();
+  }
+  dev_free(Yt, st);
+  dev_free(YtT, st);
+  dev_free(mag, st);
+  return e;
 }
 
 }  // namespace amm

@@ -31,28 +31,79 @@ __device__ __forceinline__ float2 half_spec(const float2* __restrict__ T, int n,
   return v;
 }
 
-// ============================================================================ G B~_a^T
-// XAT[q][i] = sum over kept (q, c) of B~_a:  GT[c][i] B~(q, c).  The kept columns of frequency q
-// are the set bits of maskB[q]; every thread of the CTA walks the same words.
-__global__ void __launch_bounds__(256) ft_bw_gba_kernel(const float* __restrict__ GT, const float2* __restrict__ Bt,
-                                                        const uint32_t* __restrict__ maskB, int mwB, int n, int m,
-                                                        int p, float2* __restrict__ XAT) {
+// ============================================================================ sparse x dense
+// out[q][v] = sum over the set bits x of mask[q]:  T~(q, x) D[x][v]   (T~ from a half spectrum).
+//   G B~_a^T :  D = G^T [p][m], T = B~ [n/2+1][p], mask = B~_a bits  -> XAT[q][i]
+//   A~_a^T G :  D = G [m][p],   T = A~^T [n/2+1][m], mask = A~_a bits -> XB[q][c]
+// CTA per (q, 1024 outputs): the mask row is compacted in shared memory chunk by chunk (index and
+// coefficient per set bit), then every thread streams the selected rows of D for its 4 outputs.
+constexpr int MW_CHUNK = 64;  // mask words per chunk (2048 bits)
+constexpr int MW_RPT = 4;     // outputs per thread
+__global__ void __launch_bounds__(256) ft_bw_maskwalk_kernel(const float* __restrict__ D, int64_t ldd, int nout,
+                                                             const float2* __restrict__ T, int64_t ldt,
+                                                             const uint32_t* __restrict__ mask, int mw, int n,
+                                                             float2* __restrict__ out) {
+  __shared__ int32_t s_idx[MW_CHUNK * 32];
+  __shared__ float2 s_val[MW_CHUNK * 32];
+  __shared__ int32_t s_off[MW_CHUNK + 1];
   const int q = blockIdx.y;
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  const uint32_t* mrow = maskB + (int64_t)q * mwB;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int w = 0; w < mwB; ++w) {
-    uint32_t bits = __ldg(mrow + w);
-    while (bits) {
-      const int c = w * 32 + __ffs(bits) - 1;
-      bits &= bits - 1;
-      const float2 b = half_spec(Bt, n, q, p, c);
-      const float g = i < m ? __ldg(GT + (int64_t)c * m + i) : 0.f;
-      acc.x = fmaf(g, b.x, acc.x);
-      acc.y = fmaf(g, b.y, acc.y);
+  const int v0 = blockIdx.x * (256 * MW_RPT) + threadIdx.x;
+  const uint32_t* mrow = mask + (int64_t)q * mw;
+  float2 acc[MW_RPT];
+#pragma unroll
+  for (int r = 0; r < MW_RPT; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int w0 = 0; w0 < mw; w0 += MW_CHUNK) {
+    uint32_t bits = 0;
+    if (threadIdx.x < MW_CHUNK && w0 + threadIdx.x < mw) bits = __ldg(mrow + w0 + threadIdx.x);
+    if (threadIdx.x < 32) {  // exclusive scan of the popcounts of 64 words (two per lane)
+      const uint32_t b0 = __ldg(mrow + min(w0 + 2 * (int)threadIdx.x, mw - 1));
+      const uint32_t b1 = __ldg(mrow + min(w0 + 2 * (int)threadIdx.x + 1, mw - 1));
+      const int c0 = (w0 + 2 * (int)threadIdx.x < mw) ? __popc(b0) : 0;
+      const int c1 = (w0 + 2 * (int)threadIdx.x + 1 < mw) ? __popc(b1) : 0;
+      int x = c0 + c1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)threadIdx.x >= o) x += y;
+      }
+      s_off[2 * threadIdx.x] = x - c0 - c1;
+      s_off[2 * threadIdx.x + 1] = x - c1;
+      if (threadIdx.x == 31) s_off[MW_CHUNK] = x;
     }
+    __syncthreads();
+    if (threadIdx.x < MW_CHUNK) {
+      int o = s_off[threadIdx.x];
+      while (bits) {
+        const int x = (w0 + threadIdx.x) * 32 + __ffs(bits) - 1;
+        bits &= bits - 1;
+        s_idx[o] = x;
+        s_val[o] = half_spec(T, n, q, ldt, x);
+        ++o;
+      }
+    }
+    __syncthreads();
+    const int cnt = s_off[MW_CHUNK];
+    for (int e = 0; e < cnt; ++e) {
+      const int x = s_idx[e];
+      const float2 c = s_val[e];
+      const float* drow = D + (int64_t)x * ldd;
+#pragma unroll
+      for (int r = 0; r < MW_RPT; ++r) {
+        const int v = v0 + r * 256;
+        if (v < nout) {
+          const float d = __ldg(drow + v);
+          acc[r].x = fmaf(d, c.x, acc[r].x);
+          acc[r].y = fmaf(d, c.y, acc[r].y);
+        }
+      }
+    }
+    __syncthreads();
   }
-  if (i < m) XAT[(int64_t)q * m + i] = acc;
+#pragma unroll
+  for (int r = 0; r < MW_RPT; ++r) {
+    const int v = v0 + r * 256;
+    if (v < nout) out[(int64_t)q * nout + v] = acc[r];
+  }
 }
 
 // ============================================================================ P_A(G dB~^T)
@@ -89,31 +140,6 @@ __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__
       *x = make_float2(v.x + ax, v.y + (mir ? -ay : ay));
     }
   }
-}
-
-// ============================================================================ A~_a^T G
-// XB[q][c] = sum over kept (i, q) of A~_a:  A~(i, q) G(i, c); the kept rows of frequency q are the
-// set bits of maskA[q].
-__global__ void __launch_bounds__(256) ft_bw_aag_kernel(const float* __restrict__ G, int64_t ldg,
-                                                        const float2* __restrict__ AtT,
-                                                        const uint32_t* __restrict__ maskA, int mwA, int n, int m,
-                                                        int p, float2* __restrict__ XB) {
-  const int q = blockIdx.y;
-  const int c = blockIdx.x * 256 + threadIdx.x;
-  const uint32_t* mrow = maskA + (int64_t)q * mwA;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int w = 0; w < mwA; ++w) {
-    uint32_t bits = __ldg(mrow + w);
-    while (bits) {
-      const int i = w * 32 + __ffs(bits) - 1;
-      bits &= bits - 1;
-      const float2 a = half_spec(AtT, n, q, m, i);
-      const float g = c < p ? __ldg(G + (int64_t)i * ldg + c) : 0.f;
-      acc.x = fmaf(g, a.x, acc.x);
-      acc.y = fmaf(g, a.y, acc.y);
-    }
-  }
-  if (c < p) XB[(int64_t)q * p + c] = acc;
 }
 
 // ============================================================================ P_B(dA~^T G)
@@ -251,7 +277,8 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
   if (e == cudaSuccess && a.dA) {
     {
       AMM_TRACE_W("ft_bw_gba", st, 4.0 * p * (double)a.kb * m, 4.0 * p * (double)a.kb * m + 8.0 * n * m, nullptr);
-      ft_bw_gba_kernel<<<dim3((m + 255) / 256, n), 256, 0, st>>>(GT, a.Bt, a.maskB, mwB, n, m, p, XAT);
+      ft_bw_maskwalk_kernel<<<dim3((m + 256 * MW_RPT - 1) / (256 * MW_RPT), n), 256, 0, st>>>(
+          GT, m, m, a.Bt, p, a.maskB, mwB, n, XAT);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -264,7 +291,8 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
   if (e == cudaSuccess && a.dB) {
     {
       AMM_TRACE_W("ft_bw_aag", st, 4.0 * m * (double)a.ka * p, 4.0 * m * (double)a.ka * p + 8.0 * n * p, nullptr);
-      ft_bw_aag_kernel<<<dim3((p + 255) / 256, n), 256, 0, st>>>(a.G, a.ldg, a.AtT, a.maskA, mwA, n, m, p, XB);
+      ft_bw_maskwalk_kernel<<<dim3((p + 256 * MW_RPT - 1) / (256 * MW_RPT), n), 256, 0, st>>>(
+          a.G, a.ldg, p, a.AtT, m, a.maskA, mwA, n, XB);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

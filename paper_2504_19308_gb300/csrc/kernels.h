@@ -29,11 +29,15 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
 cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* list, const float* coef,
                      const int32_t* count, int cap, int imag_coef, float2* L, cudaStream_t st);
 // inverse cycle transform of a (half) spectrum R with coefficients by mode (0: 1-g, 1: -i g,
-// 2: g, 3: +i g); writes or adds X((c+j) mod n, c), leading dimension ldx (0 = n)
+// 2: g, 3: +i g); writes or adds X((c+j) mod n, c), leading dimension ldx (0 = n).  Rows of R
+// whose coefficient is zero are not read.  Odd modes skip when *dcount == 0; any mode skips
+// when dcount2 is given and *dcount2 == 0.
 cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
-                        float* X, cudaStream_t st, int64_t ldx = 0, int accumulate = 0);
+                        float* X, cudaStream_t st, int64_t ldx = 0, int accumulate = 0,
+                        const int32_t* dcount2 = nullptr);
 // cd_backward.cu
-cudaError_t bw_spectrum(int n, bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh, cudaStream_t st);
+cudaError_t bw_spectrum(int n, bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh, cudaStream_t st,
+                        const int32_t* gate0 = nullptr, const int32_t* gate1 = nullptr);
 cudaError_t cd_sddmm(int n, const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
                      float2* K, const int32_t* gate0, const int32_t* gate1, cudaStream_t st);
 cudaError_t cd_rho(int n, const float2* K, const float2* tw, const int32_t* list, const int32_t* count, int cap,
@@ -86,6 +90,20 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st);
 // svd.cu: Y (cols x rows, ldy) = X^T
 cudaError_t transpose_f32(const float* X, int64_t rows, int64_t cols, int64_t ldx, float* Y, int64_t ldy,
                           cudaStream_t st);
+
+// mixed-method pieces (cycle.cu, fourier.cu)
+cudaError_t cyc_left_apply(int n, const int32_t* selA, int ka, const float* cycA, const float* X, int64_t ldx,
+                           int64_t p, float* C, int64_t ldc, cudaStream_t st);
+cudaError_t cyc_right_apply(int n, const int32_t* selB, int kb, const float* cycB, const float* Y, int64_t ldy,
+                            int64_t m, float* C, int64_t ldc, cudaStream_t st);
+cudaError_t cyc_residual(int n, const float* A, int64_t lda, const unsigned char* insel, float* D, int64_t ldd,
+                         cudaStream_t st);
+cudaError_t ft_dense(int n, const float2* At, const int32_t* sel, int k, int m, const float2* tw, int part,
+                     const float* A, int64_t lda, float* D, int64_t ldd, cudaStream_t st);
+cudaError_t ft_left_apply(int n, int m, const float2* At, const int32_t* selA, int ka, const float2* tw,
+                          const float* X, int64_t ldx, int p, float* C, int64_t ldc, cudaStream_t st);
+cudaError_t ft_right_apply(int n, int p, const float2* Bt, const int32_t* selB, int kb, const float2* tw,
+                           const float* Y, int64_t ldy, int m, bool imag, float* C, int64_t ldc, cudaStream_t st);
 
 // umma_gemm.cu: C = alpha A B^T + beta C on tcgen05 tensor cores (A, B K-major);
 // tf32 = FP32 inputs with TF32 hi/lo splitting, else BF16 inputs.  err: device flag.

@@ -1,0 +1,125 @@
+// First-order product of two operands truncated by DIFFERENT methods (the paper allows the two
+// decompositions to differ; Section 1 and Section 5).  With A~ from A's method and B~ from B's,
+//
+//   Re M = Re(A~ B + dA B~) = Re(A~) B + (A - Re A~) Re(B~) + Im(A~) Im(B~)
+//
+// (dA = A - A~, Im dA = -Im A~, A and B real).  Each term is one operand's truncation applied to
+// a dense real matrix from the left or the right, so the product needs, per method, a left
+// apply, a right apply, the dense real residual and, for the methods whose truncation can be
+// complex (circulant with a split conjugate pair, the Fourier sparsifier), the dense imaginary
+// part and the right apply of Im(B~).  SVD and cycle truncations are real: the last term then
+// vanishes and is skipped.
+#include <cuda_runtime.h>
+
+#include "api_internal.h"
+#include "kernels.h"
+#include "trace.h"
+
+namespace amm {
+
+static bool can_be_complex(const Handle* h) {
+  return h->method == AMM_CIRCULANT || h->method == AMM_SPARSE_FOURIER;
+}
+
+// C = Re(A~) X for X (n x p)
+static cudaError_t left_apply(Handle* a, const float* X, int64_t ldx, int64_t p, float* C, int64_t ldc,
+                              cudaStream_t st) {
+  const int n = (int)a->cols;
+  switch (a->method) {
+    case AMM_SVD:
+      return svd_left_apply(a, X, ldx, p, C, ldc, 0.f, st);
+    case AMM_CIRCULANT:
+      return cd_apply(n, false, X, ldx, false, p, a->cd.tw, a->cd.so.ulist, a->cd.Lw, a->cd.so.counts, nullptr,
+                      nullptr, C, ldc, 0, st);
+    case AMM_SPARSE_CYCLE:
+      return cyc_left_apply(n, a->cy.so.sel, (int)a->k, a->cy.cyc, X, ldx, p, C, ldc, st);
+    case AMM_SPARSE_FOURIER:
+      return ft_left_apply(n, (int)a->rows, a->ft.T, a->ft.sel, (int)a->k, a->ft.tw, X, ldx, (int)p, C, ldc, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// C += Y Re(B~) for Y (m x n)
+static cudaError_t right_apply(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc,
+                               cudaStream_t st) {
+  const int n = (int)b->rows;
+  switch (b->method) {
+    case AMM_SVD:
+      return svd_right_apply(b, Y, ldy, m, C, ldc, 1.f, st);
+    case AMM_CIRCULANT:
+      return cd_apply(n, true, Y, ldy, false, m, b->cd.tw, b->cd.so.ulist, b->cd.Lw, b->cd.so.counts, nullptr,
+                      nullptr, C, ldc, 1, st);
+    case AMM_SPARSE_CYCLE:
+      return cyc_right_apply(n, b->cy.so.sel, (int)b->k, b->cy.cyc, Y, ldy, m, C, ldc, st);
+    case AMM_SPARSE_FOURIER:
+      return ft_right_apply(n, (int)b->cols, b->ft.T, b->ft.sel, (int)b->k, b->ft.tw, Y, ldy, (int)m, false, C, ldc,
+                            st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// C += Y Im(B~) for Y (m x n); circulant: the unpaired coefficients -i v_s L_s, skipped on the
+// device when B's selection has no unpaired component
+static cudaError_t right_apply_imag(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc,
+                                    cudaStream_t st) {
+  const int n = (int)b->rows;
+  if (b->method == AMM_CIRCULANT)
+    return cd_apply(n, true, Y, ldy, false, m, b->cd.tw, b->cd.so.dlist, b->cd.Ld, b->cd.so.counts + 1,
+                    b->cd.so.counts + 1, b->cd.so.counts + 1, C, ldc, 1, st);
+  if (b->method == AMM_SPARSE_FOURIER)
+    return ft_right_apply(n, (int)b->cols, b->ft.T, b->ft.sel, (int)b->k, b->ft.tw, Y, ldy, (int)m, true, C, ldc, st);
+  return cudaErrorInvalidValue;
+}
+
+// D = A - Re(A~), m x n
+static cudaError_t residual(Handle* a, float* D, int64_t ldd, cudaStream_t st) {
+  const int n = (int)a->cols;
+  switch (a->method) {
+    case AMM_SVD:
+      return svd_residual(a, D, ldd, st);
+    case AMM_CIRCULANT:
+      return cd_residual(n, a->cd.R, a->cd.tw, a->cd.so.wfull, 0, nullptr, D, st, ldd, 0);
+    case AMM_SPARSE_CYCLE:
+      return cyc_residual(n, (const float*)a->A, a->lda, a->cy.insel, D, ldd, st);
+    case AMM_SPARSE_FOURIER:
+      return ft_dense(n, a->ft.T, a->ft.sel, (int)a->k, (int)a->rows, a->ft.tw, 0, (const float*)a->A, a->lda, D, ldd,
+                      st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// D = Im(A~), m x n (zero for a circulant selection without unpaired components)
+static cudaError_t imag_part(Handle* a, float* D, int64_t ldd, cudaStream_t st) {
+  const int n = (int)a->cols;
+  if (a->method == AMM_CIRCULANT) {
+    cudaError_t e = cudaMemset2DAsync(D, sizeof(float) * ldd, 0, sizeof(float) * n, n, st);
+    if (e != cudaSuccess) return e;
+    return cd_residual(n, a->cd.R, a->cd.tw, a->cd.so.vfull, 1, a->cd.so.counts + 1, D, st, ldd, 0);
+  }
+  if (a->method == AMM_SPARSE_FOURIER)
+    return ft_dense(n, a->ft.T, a->ft.sel, (int)a->k, (int)a->rows, a->ft.tw, 1, nullptr, 0, D, ldd, st);
+  return cudaErrorInvalidValue;
+}
+
+amm_status_t mixed_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st) {
+  const int64_t m = a->rows, n = a->cols, p = b->cols;
+  if (a->dtype != AMM_F32 || b->dtype != AMM_F32)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "mixed methods: BF16 operands are not built (use FP32 inputs)");
+  float* D = nullptr;
+  cudaError_t e = dev_alloc((void**)&D, sizeof(float) * (size_t)m * n, st);
+  // C = Re(A~) B
+  if (e == cudaSuccess) e = left_apply(a, (const float*)b->A, b->lda, p, C, ldc, st);
+  // C += (A - Re A~) Re(B~)
+  if (e == cudaSuccess) e = residual(a, D, n, st);
+  if (e == cudaSuccess) e = right_apply(b, D, n, m, C, ldc, st);
+  // C += Im(A~) Im(B~)
+  if (e == cudaSuccess && can_be_complex(a) && can_be_complex(b)) {
+    e = imag_part(a, D, n, st);
+    if (e == cudaSuccess) e = right_apply_imag(b, D, n, m, C, ldc, st);
+  }
+  dev_free(D, st);
+  if (e != cudaSuccess) return cuda_fail(e, "mixed-method product");
+  return AMM_OK;
+}
+
+}  // namespace amm

@@ -192,87 +192,6 @@ static cudaError_t sgemm(bool ta, bool tb, int M, int N, int K, float alpha, con
   return e;
 }
 
-// ============================================================================ FP64 small GEMM
-// C[M x N] = sum_l opA(i, l) opB(l, j), FP64 accumulation, 32 x 32 tiles, K split over grid.z
-// (partials to ws, reduced in fixed order).  Used for Gram matrices and triangular applies.
-template <bool TA, bool TB, typename TA_t, typename TB_t>
-__global__ void __launch_bounds__(256) dgemm_small_kernel(int M, int N, int K, const TA_t* __restrict__ A,
-                                                          int64_t lda, const TB_t* __restrict__ B, int64_t ldb,
-                                                          int kchunk, double* __restrict__ ws) {
-  __shared__ double As[32][33];
-  __shared__ double Bs[32][33];
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-  double acc[4] = {0, 0, 0, 0};
-  const int ci = tid >> 3, cj = (tid & 7) * 4;  // thread computes (ci, cj..cj+3)
-  for (int k0 = kbeg; k0 < kend; k0 += 32) {
-    for (int e = tid; e < 32 * 32; e += 256) {
-      int r = e >> 5, c = e & 31;
-      // As[i][l]
-      int gi = i0 + r, gl = k0 + c;
-      double va = 0.0;
-      if (gi < M && gl < kend) va = (double)(TA ? A[(int64_t)gl * lda + gi] : A[(int64_t)gi * lda + gl]);
-      As[r][c] = va;
-      // Bs[l][j]
-      int bl = k0 + r, bj = j0 + c;
-      double vb = 0.0;
-      if (bj < N && bl < kend) vb = (double)(TB ? B[(int64_t)bj * ldb + bl] : B[(int64_t)bl * ldb + bj]);
-      Bs[r][c] = vb;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int l = 0; l < 32; ++l) {
-      double a = As[ci][l];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fma(a, Bs[l][cj + q], acc[q]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int i = i0 + ci, j = j0 + cj + q;
-    if (i < M && j < N) ws[((int64_t)blockIdx.z * M + i) * N + j] = acc[q];
-  }
-}
-
-template <typename TOut>
-__global__ void dreduce_kernel(int M, int N, int splits, const double* __restrict__ ws, TOut* __restrict__ C,
-                               int64_t ldc) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)M * N) return;
-  double s = 0.0;
-  for (int z = 0; z < splits; ++z) s += ws[(int64_t)z * M * N + e];
-  C[(e / N) * ldc + (e % N)] = (TOut)s;
-}
-
-template <bool TA, bool TB, typename TA_t, typename TB_t, typename TOut>
-static cudaError_t dgemm_small(int M, int N, int K, const TA_t* A, int64_t lda, const TB_t* B, int64_t ldb, TOut* C,
-                               int64_t ldc, cudaStream_t st) {
-  const int tiles = ((M + 31) / 32) * ((N + 31) / 32);
-  int splits = std::max(1, std::min(K / 256, (2 * num_sms() + tiles - 1) / tiles));
-  int kchunk = (K + splits - 1) / splits;
-  kchunk = ((kchunk + 31) / 32) * 32;
-  splits = std::max(1, (K + kchunk - 1) / kchunk);
-  double* ws = nullptr;
-  cudaError_t e = dev_alloc((void**)&ws, sizeof(double) * (size_t)splits * M * N, st);
-  if (e != cudaSuccess) return e;
-  dim3 grid((N + 31) / 32, (M + 31) / 32, splits);
-  {
-    AMM_TRACE_W("dgemm_small", st, 2.0 * M * N * (double)K, 0.0, nullptr);
-    dgemm_small_kernel<TA, TB, TA_t, TB_t><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, kchunk, ws);
-  }
-  e = cudaGetLastError();
-  if (e == cudaSuccess) {
-    const int64_t tot = (int64_t)M * N;
-    AMM_TRACE("dreduce", st);
-    dreduce_kernel<TOut><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, ws, C, ldc);
-    e = cudaGetLastError();
-  }
-  dev_free(ws, st);
-  return e;
-}
-
 // ============================================================================ compensated Gram (FP32)
 // G = X^T X for X (m x k, FP32).  Each thread accumulates its dot products with error-free
 // transformations (TwoProduct via fma and TwoSum: Ogita, Rump, Oishi, "Accurate sum and dot
@@ -356,11 +275,12 @@ static cudaError_t gram_dot2(int64_t m, int k, const float* X, float* G, cudaStr
 
 // ============================================================================ Cholesky + inverse (FP32, one CTA)
 // G (k x k, symmetric positive semi-definite) -> Linv = L^{-1} with G + s I = L L^T,
-// s = shift_rel * trace(G).  Shared memory holds W (k x k; L ends in its lower triangle), Linv
-// (k x k, row-major) and the current column of L, so every inner loop reads consecutive or
-// broadcast words (no bank conflicts).  One warp per row in the trailing update; the inverse is
-// built row by row (thread c forms Linv[i][c] from Linv[c..i-1][c]).  For k > CHOL_SMEM_K the
-// same arrays live in a global work area (2 k^2 + k floats).
+// s = shift_rel * trace(G).  Shared memory holds W (k x k; L ends in its lower triangle), the
+// inverse TRANSPOSED (LiT[c][l] = Linv[l][c]) and the current column of L, so every inner loop
+// reads consecutive or broadcast words (no bank conflicts).  One warp per row in the trailing
+// update.  The inverse is built row by row: Linv[i][c] = -sum_{l=c}^{i-1} L[i][l] Linv[l][c] /
+// L[i][i], one warp per column c with the lanes splitting the sum over l.  For k > CHOL_SMEM_K
+// the same arrays live in a global work area (2 k^2 + k floats).
 constexpr int CHOL_SMEM_K = 160;
 constexpr int CHOL_T = 1024;
 
@@ -408,24 +328,26 @@ __global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const float* __
     }
     __syncthreads();
   }
-  // Linv: diagonal, then rows i = 1..k-1
+  // Linv (held transposed in Li): diagonal, then rows i = 1..k-1, one warp per column c < i
   for (int i = tid; i < k; i += CHOL_T) Li[i * k + i] = 1.f / W[i * k + i];
   __syncthreads();
   for (int i = 1; i < k; ++i) {
     const float di = Li[i * k + i];
-    for (int c = tid; c < i; c += CHOL_T) {
-      float s0 = 0.f, s1 = 0.f;
-      int l = c;
-      for (; l + 1 < i; l += 2) {
-        s0 = fmaf(W[i * k + l], Li[l * k + c], s0);
-        s1 = fmaf(W[i * k + l + 1], Li[(l + 1) * k + c], s1);
-      }
-      if (l < i) s0 = fmaf(W[i * k + l], Li[l * k + c], s0);
-      Li[i * k + c] = -(s0 + s1) * di;
+    const float* wrow = W + i * k;
+    for (int c = warp; c < i; c += CHOL_T / 32) {
+      const float* lcol = Li + c * k;  // Linv[.][c]
+      float s = 0.f;
+      for (int l = c + lane; l < i; l += 32) s = fmaf(wrow[l], lcol[l], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) Li[c * k + i] = -s * di;
     }
     __syncthreads();
   }
-  for (int e = tid; e < k * k; e += CHOL_T) Linv_out[e] = Li[e];
+  for (int e = tid; e < k * k; e += CHOL_T) {
+    const int i = e / k, c = e - i * k;
+    Linv_out[e] = Li[c * k + i];
+  }
 }
 
 // ============================================================================ Philox sketch
@@ -620,6 +542,32 @@ static cudaError_t cast(const TI* X, int64_t rows, int64_t cols, int64_t ldx, TO
   return cudaGetLastError();
 }
 
+// Y = [X1 | X2 | 0] (rows x kpad, E): two thin matrices side by side, zero-padded to kpad columns,
+// so that one K-major GEMM evaluates X1 Z1^T + X2 Z2^T with a single pass over its output.
+template <typename T1, typename T2, typename E>
+__global__ void concat_cols_kernel(const T1* __restrict__ X1, int64_t ld1, int c1, const T2* __restrict__ X2,
+                                   int64_t ld2, int c2, int64_t rows, E* __restrict__ Y, int kpad) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * kpad) return;
+  const int64_t r = e / kpad;
+  const int c = (int)(e % kpad);
+  float v = 0.f;
+  if (c < c1) v = (float)X1[r * ld1 + c];
+  else if (c < c1 + c2) v = (float)X2[r * ld2 + (c - c1)];
+  Y[e] = (E)v;
+}
+
+template <typename T1, typename T2, typename E>
+static cudaError_t concat_cols(const T1* X1, int64_t ld1, int c1, const T2* X2, int64_t ld2, int c2, int64_t rows,
+                               E* Y, int kpad, cudaStream_t st) {
+  AMM_TRACE_W("concat", st, 0.0, (double)rows * (c1 * sizeof(T1) + c2 * sizeof(T2) + kpad * sizeof(E)), nullptr);
+  const int64_t tot = rows * kpad;
+  concat_cols_kernel<T1, T2, E><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X1, ld1, c1, X2, ld2, c2, rows, Y, kpad);
+  return cudaGetLastError();
+}
+
+static int pad8(int k) { return (k + 7) / 8 * 8; }
+
 // C = alpha A B^T + beta C with A (M x K, lda) and B (N x K, ldb) K-major in the compute type E.
 // tcgen05 when every row starts 16-byte aligned, the SIMT kernel otherwise.
 template <typename E>
@@ -710,37 +658,37 @@ static cudaError_t svd_build_tc(Handle* h) {
   if ((e = to_e<E>(h, ZT, n, k, &zte, st)) != cudaSuccess) return e;
   s.Ze = (void*)ze;
   s.ZTe = (void*)zte;
-  if (in_bf16) e = sumsq<__nv_bfloat16>((const __nv_bfloat16*)h->A, m, n, h->lda, s.norms + 0, st);
-  else e = sumsq<float>((const float*)h->A, m, n, h->lda, s.norms + 0, st);
-  if (e == cudaSuccess) e = sumsq<float>(s.X, k, n, n, s.norms + 1, st);
-  return e;
+  return e;  // the norms of amm_handle_info are computed when asked (svd_info)
 }
 
 template <typename E>
 static cudaError_t svd_matmul_tc(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st) {
   const int m = (int)a->rows, n = (int)a->cols, p = (int)b->cols;
-  const int ka = (int)a->k, kb = (int)b->k;
+  const int ka = (int)a->k, kb = (int)b->k, kk = pad8(ka + kb);
   auto &sa = a->svd, &sb = b->svd;
   int* err = sa.err;
   float *T1T = nullptr, *W = nullptr, *ZZ = nullptr;
-  const E *t1te = nullptr, *we = nullptr, *zze = nullptr;
+  E *L = nullptr, *R = nullptr;
+  const E* zze = nullptr;
   cudaError_t e = dev_alloc((void**)&T1T, sizeof(float) * (size_t)p * ka, st);
   if (e == cudaSuccess) e = dev_alloc((void**)&W, sizeof(float) * (size_t)m * kb, st);
   if (e == cudaSuccess) e = dev_alloc((void**)&ZZ, sizeof(float) * (size_t)kb * ka, st);
-  // T1^T = B^T Z_A^T ; W = A Q_B ; (Z_A Q_B)^T = Q_B^T Z_A^T ; W -= Q_A (Z_A Q_B) ; C = Q_A T1 + W Z_B
+  if (e == cudaSuccess) e = dev_alloc((void**)&L, sizeof(E) * (size_t)m * kk, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&R, sizeof(E) * (size_t)p * kk, st);
+  // T1^T = B^T Z_A^T ; W = A Q_B ; (Z_A Q_B)^T = Q_B^T Z_A^T ; W -= Q_A (Z_A Q_B)
   if (e == cudaSuccess) e = gemm_tn<E>(p, ka, n, 1.f, (const E*)sb.XTe, n, (const E*)sa.Ze, n, 0.f, T1T, ka, err, st);
   if (e == cudaSuccess) e = gemm_tn<E>(m, kb, n, 1.f, (const E*)sa.Xe, sa.ldxe, (const E*)sb.QTe, n, 0.f, W, kb, err, st);
   if (e == cudaSuccess) e = gemm_tn<E>(kb, ka, n, 1.f, (const E*)sb.QTe, n, (const E*)sa.Ze, n, 0.f, ZZ, ka, err, st);
   if (e == cudaSuccess) e = to_e<E>(nullptr, ZZ, kb, ka, &zze, st);
   if (e == cudaSuccess) e = gemm_tn<E>(m, kb, ka, -1.f, (const E*)sa.Qe, ka, zze, ka, 1.f, W, kb, err, st);
-  if (e == cudaSuccess) e = to_e<E>(nullptr, T1T, p, ka, &t1te, st);
-  if (e == cudaSuccess) e = to_e<E>(nullptr, W, m, kb, &we, st);
-  if (e == cudaSuccess) e = gemm_tn<E>(m, p, ka, 1.f, (const E*)sa.Qe, ka, t1te, ka, 0.f, C, ldc, err, st);
-  if (e == cudaSuccess) e = gemm_tn<E>(m, p, kb, 1.f, we, kb, (const E*)sb.ZTe, kb, 1.f, C, ldc, err, st);
-  if constexpr (!std::is_same<E, float>::value) {
-    for (const E* q : {t1te, we, zze}) dev_free((void*)q, st);
-  }
+  // C = Q_A T1 + W Z_B = [Q_A | W] [T1^T | Z_B^T]^T: one pass over C
+  if (e == cudaSuccess) e = concat_cols<E, float, E>((const E*)sa.Qe, ka, ka, W, kb, kb, m, L, kk, st);
+  if (e == cudaSuccess) e = concat_cols<float, E, E>(T1T, ka, ka, (const E*)sb.ZTe, kb, kb, p, R, kk, st);
+  if (e == cudaSuccess) e = gemm_tn<E>(m, p, kk, 1.f, L, kk, R, kk, 0.f, C, ldc, err, st);
+  if constexpr (!std::is_same<E, float>::value) dev_free((void*)zze, st);
   for (float* q : {T1T, W, ZZ}) dev_free(q, st);
+  dev_free(L, st);
+  dev_free(R, st);
   return e;
 }
 
@@ -784,13 +732,10 @@ static cudaError_t svd_backward_tc(Handle* a, Handle* b, const float* G, int64_t
   if (e == cudaSuccess) e = gemm_tn<E>(p, ka, m, 1.f, GTe, m, (const E*)sa.QTe, m, 0.f, H2T, ka, err, st);
   if (e == cudaSuccess) e = transpose_cast<float, float>(H2T, p, ka, ka, H2, p, st);
   const E* H2e = as_e(H2, ka, p);
-  const E* H2Te = as_e(H2T, p, ka);
   if (dA) {
     // dA = (G Z_B^T) Q_B^T + Q_A [ H2 B^T - (H2 Z_B^T) Q_B^T ]
     float* H1 = (float*)al(sizeof(float) * (size_t)m * kb);
     if (e == cudaSuccess) e = gemm_tn<E>(m, kb, p, 1.f, Ge, ldge, (const E*)sb.Ze, p, 0.f, H1, kb, err, st);
-    const E* H1e = as_e(H1, m, kb);
-    if (e == cudaSuccess) e = gemm_tn<E>(m, n, kb, 1.f, H1e, kb, (const E*)sb.Qe, kb, 0.f, dA, ldda, err, st);
     float* H3T = (float*)al(sizeof(float) * (size_t)n * ka);
     float* H4 = (float*)al(sizeof(float) * (size_t)ka * kb);
     if (e == cudaSuccess)
@@ -798,8 +743,13 @@ static cudaError_t svd_backward_tc(Handle* a, Handle* b, const float* G, int64_t
     if (e == cudaSuccess) e = gemm_tn<E>(ka, kb, p, 1.f, H2e, p, (const E*)sb.Ze, p, 0.f, H4, kb, err, st);
     const E* H4e = as_e(H4, ka, kb);
     if (e == cudaSuccess) e = gemm_tn<E>(n, ka, kb, -1.f, (const E*)sb.Qe, kb, H4e, kb, 1.f, H3T, ka, err, st);
-    const E* H3Te = as_e(H3T, n, ka);
-    if (e == cudaSuccess) e = gemm_tn<E>(m, n, ka, 1.f, (const E*)sa.Qe, ka, H3Te, ka, 1.f, dA, ldda, err, st);
+    // dA = [H1 | Q_A] [Q_B | H3^T]^T: one pass over dA
+    const int kk = pad8(ka + kb);
+    E* Lc = (E*)al(sizeof(E) * (size_t)m * kk);
+    E* Rc = (E*)al(sizeof(E) * (size_t)n * kk);
+    if (e == cudaSuccess) e = concat_cols<float, E, E>(H1, kb, kb, (const E*)sa.Qe, ka, ka, m, Lc, kk, st);
+    if (e == cudaSuccess) e = concat_cols<E, float, E>((const E*)sb.Qe, kb, kb, H3T, ka, ka, n, Rc, kk, st);
+    if (e == cudaSuccess) e = gemm_tn<E>(m, n, kk, 1.f, Lc, kk, Rc, kk, 0.f, dA, ldda, err, st);
   }
   if (dB) {
     // W^T = Q_B^T A^T - (Z_A Q_B)^T Q_A^T ; dB = Z_A^T H2 + Q_B (W^T G)
@@ -812,32 +762,107 @@ static cudaError_t svd_backward_tc(Handle* a, Handle* b, const float* G, int64_t
     const E* WTe = as_e(WT, kb, m);
     float* H5T = (float*)al(sizeof(float) * (size_t)p * kb);
     if (e == cudaSuccess) e = gemm_tn<E>(p, kb, m, 1.f, GTe, m, WTe, m, 0.f, H5T, kb, err, st);
-    const E* H5Te = as_e(H5T, p, kb);
-    if (e == cudaSuccess) e = gemm_tn<E>(n, p, ka, 1.f, (const E*)sa.ZTe, ka, H2Te, ka, 0.f, dB, lddb, err, st);
-    if (e == cudaSuccess) e = gemm_tn<E>(n, p, kb, 1.f, (const E*)sb.Qe, kb, H5Te, kb, 1.f, dB, lddb, err, st);
+    // dB = Z_A^T H2 + Q_B H5 = [Z_A^T | Q_B] [H2^T | H5^T]^T: one pass over dB
+    const int kk = pad8(ka + kb);
+    E* Lc = (E*)al(sizeof(E) * (size_t)n * kk);
+    E* Rc = (E*)al(sizeof(E) * (size_t)p * kk);
+    if (e == cudaSuccess) e = concat_cols<E, E, E>((const E*)sa.ZTe, ka, ka, (const E*)sb.Qe, kb, kb, n, Lc, kk, st);
+    if (e == cudaSuccess) e = concat_cols<float, float, E>(H2T, ka, ka, H5T, kb, kb, p, Rc, kk, st);
+    if (e == cudaSuccess) e = gemm_tn<E>(n, p, kk, 1.f, Lc, kk, Rc, kk, 0.f, dB, lddb, err, st);
   }
   for (void* q : tmp) dev_free(q, st);
   return e;
 }
 
-// ============================================================================ ABI glue
-static cudaError_t svd_build(Handle* h, const float* A) {
-  auto& s = h->svd;
-  const int64_t m = h->rows, n = h->cols;
-  const int k = (int)h->k;
-  float* Y = nullptr;
-  cudaError_t e = dev_alloc((void**)&Y, sizeof(float) * (size_t)m * k, h->stream);
+// ============================================================================ mixed-method pieces
+// Applies of one SVD truncation to a dense FP32 matrix, for products whose other operand uses a
+// different method.  A~ = Q_A Z_A with Z_A = Q_A^T A (k x n); B~ = Q_B Z_B.
+template <typename E>
+static cudaError_t as_kmajor(const float* X, int64_t rows, int64_t cols, int64_t ldx, const E** out, E** owned,
+                             cudaStream_t st) {
+  *owned = nullptr;
+  if (std::is_same<E, float>::value && ((uintptr_t)X % 16) == 0 && (ldx * 4) % 16 == 0) {
+    *out = (const E*)X;
+    return cudaSuccess;
+  }
+  E* y = nullptr;
+  cudaError_t e = dev_alloc((void**)&y, sizeof(E) * rows * cols, st);
   if (e != cudaSuccess) return e;
-  e = sgemm<float>(false, false, (int)m, k, (int)n, 1.f, A, h->lda, s.phi, k, 0.f, Y, k, h->stream);  // Y = A phi
-  if (e == cudaSuccess) e = orthonormalize(m, k, Y, s.Q, h->stream);                                          // Q = orth(Y)
+  *owned = y;
+  *out = y;
+  return cast<float, E>(X, rows, cols, ldx, y, cols, st);
+}
+
+// C = Q_A (Z_A X) + beta C for X (n x p)
+template <typename E>
+static cudaError_t svd_left_apply_t(Handle* a, const float* X, int64_t ldx, int64_t p, float* C, int64_t ldc, float beta,
+                                    cudaStream_t st) {
+  const int m = (int)a->rows, n = (int)a->cols, k = (int)a->k;
+  E* xt = nullptr;
+  float* TT = nullptr;
+  const E* tte = nullptr;
+  cudaError_t e = dev_alloc((void**)&xt, sizeof(E) * (size_t)p * n, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&TT, sizeof(float) * (size_t)p * k, st);
+  if (e == cudaSuccess) e = transpose_cast<float, E>(X, n, p, ldx, xt, n, st);  // X^T, K-major over n
+  if (e == cudaSuccess) e = gemm_tn<E>((int)p, k, n, 1.f, xt, n, (const E*)a->svd.Ze, n, 0.f, TT, k, a->svd.err, st);
+  if (e == cudaSuccess) e = to_e<E>(nullptr, TT, p, k, &tte, st);
   if (e == cudaSuccess)
-    e = sgemm<float>(true, false, k, (int)n, (int)m, 1.f, s.Q, k, A, h->lda, 0.f, s.X, n, h->stream);  // X = Q^T A
-  if (e == cudaSuccess) e = sumsq<float>(A, m, n, h->lda, s.norms + 0, h->stream);
-  if (e == cudaSuccess) e = sumsq<float>(s.X, k, n, n, s.norms + 1, h->stream);
-  dev_free(Y, h->stream);
+    e = gemm_tn<E>(m, (int)p, k, 1.f, (const E*)a->svd.Qe, k, tte, k, beta, C, ldc, a->svd.err, st);
+  if constexpr (!std::is_same<E, float>::value) dev_free((void*)tte, st);
+  dev_free(xt, st);
+  dev_free(TT, st);
   return e;
 }
 
+// C = (Y Q_B) Z_B + beta C for Y (m x n)
+template <typename E>
+static cudaError_t svd_right_apply_t(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc,
+                                     float beta, cudaStream_t st) {
+  const int n = (int)b->rows, p = (int)b->cols, k = (int)b->k;
+  const E* ye = nullptr;
+  E* yown = nullptr;
+  float* W = nullptr;
+  const E* we = nullptr;
+  cudaError_t e = as_kmajor<E>(Y, m, n, ldy, &ye, &yown, st);
+  const int64_t ldye = yown ? n : ldy;
+  if (e == cudaSuccess) e = dev_alloc((void**)&W, sizeof(float) * (size_t)m * k, st);
+  if (e == cudaSuccess) e = gemm_tn<E>((int)m, k, n, 1.f, ye, ldye, (const E*)b->svd.QTe, n, 0.f, W, k, b->svd.err, st);
+  if (e == cudaSuccess) e = to_e<E>(nullptr, W, m, k, &we, st);
+  if (e == cudaSuccess)
+    e = gemm_tn<E>((int)m, p, k, 1.f, we, k, (const E*)b->svd.ZTe, k, beta, C, ldc, b->svd.err, st);
+  if constexpr (!std::is_same<E, float>::value) dev_free((void*)we, st);
+  dev_free(yown, st);
+  dev_free(W, st);
+  return e;
+}
+
+// D = A - Q_A Z_A (m x n, FP32)
+template <typename E>
+static cudaError_t svd_residual_t(Handle* a, float* D, int64_t ldd, cudaStream_t st) {
+  const int m = (int)a->rows, n = (int)a->cols, k = (int)a->k;
+  cudaError_t e = a->dtype == AMM_BF16
+                      ? cast<__nv_bfloat16, float>((const __nv_bfloat16*)a->A, m, n, a->lda, D, ldd, st)
+                      : cast<float, float>((const float*)a->A, m, n, a->lda, D, ldd, st);
+  if (e == cudaSuccess)
+    e = gemm_tn<E>(m, n, k, -1.f, (const E*)a->svd.Qe, k, (const E*)a->svd.ZTe, k, 1.f, D, ldd, a->svd.err, st);
+  return e;
+}
+
+cudaError_t svd_left_apply(Handle* a, const float* X, int64_t ldx, int64_t p, float* C, int64_t ldc, float beta,
+                           cudaStream_t st) {
+  return a->svd.bf16 ? svd_left_apply_t<__nv_bfloat16>(a, X, ldx, p, C, ldc, beta, st)
+                     : svd_left_apply_t<float>(a, X, ldx, p, C, ldc, beta, st);
+}
+cudaError_t svd_right_apply(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc, float beta,
+                            cudaStream_t st) {
+  return b->svd.bf16 ? svd_right_apply_t<__nv_bfloat16>(b, Y, ldy, m, C, ldc, beta, st)
+                     : svd_right_apply_t<float>(b, Y, ldy, m, C, ldc, beta, st);
+}
+cudaError_t svd_residual(Handle* a, float* D, int64_t ldd, cudaStream_t st) {
+  return a->svd.bf16 ? svd_residual_t<__nv_bfloat16>(a, D, ldd, st) : svd_residual_t<float>(a, D, ldd, st);
+}
+
+// ============================================================================ ABI glue
 amm_status_t decompose_svd(Handle* h, const amm_opts_t* o) {
   if (h->k > 1024) return fail(AMM_ERR_UNSUPPORTED_SIZE, "svd: k=%lld > 1024", (long long)h->k);
   const int compute = o ? o->compute : AMM_F32;
@@ -861,7 +886,6 @@ amm_status_t decompose_svd(Handle* h, const amm_opts_t* o) {
   if (e != cudaSuccess) return cuda_fail(e, "svd: sketch");
   if ((e = h->alloc((void**)&s.err, sizeof(int))) != cudaSuccess) return cuda_fail(e, "svd: device allocation");
   if ((e = cudaMemsetAsync(s.err, 0, sizeof(int), h->stream)) != cudaSuccess) return cuda_fail(e, "svd: memset");
-  s.tc = true;
   s.bf16 = compute == AMM_BF16;
   e = s.bf16 ? svd_build_tc<__nv_bfloat16>(h) : svd_build_tc<float>(h);
   if (e != cudaSuccess) return cuda_fail(e, "svd: decomposition");
@@ -869,87 +893,31 @@ amm_status_t decompose_svd(Handle* h, const amm_opts_t* o) {
 }
 
 amm_status_t svd_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st) {
-  if (a->svd.tc && b->svd.tc) {
-    if (a->svd.bf16 != b->svd.bf16) return fail(AMM_ERR_STATE, "svd: both operands need the same compute mode");
-    cudaError_t e = a->svd.bf16 ? svd_matmul_tc<__nv_bfloat16>(a, b, C, ldc, st) : svd_matmul_tc<float>(a, b, C, ldc, st);
-    if (e != cudaSuccess) return cuda_fail(e, "svd product");
-    return AMM_OK;
-  }
-  const int m = (int)a->rows, n = (int)a->cols, p = (int)b->cols;
-  const int ka = (int)a->k, kb = (int)b->k;
-  const float* A = (const float*)a->A;
-  const float* B = (const float*)b->A;
-  float *T1 = nullptr, *W = nullptr, *Z = nullptr;
-  cudaError_t e = dev_alloc((void**)&T1, sizeof(float) * (size_t)ka * p, st);
-  if (e == cudaSuccess) e = dev_alloc((void**)&W, sizeof(float) * (size_t)m * kb, st);
-  if (e == cudaSuccess) e = dev_alloc((void**)&Z, sizeof(float) * (size_t)ka * kb, st);
-  // T1 = Z_A B ; W = A Q_B - Q_A (Z_A Q_B) ; C = Q_A T1 + W Z_B
-  if (e == cudaSuccess) e = sgemm<float>(false, false, ka, p, n, 1.f, a->svd.X, n, B, b->lda, 0.f, T1, p, st);
-  if (e == cudaSuccess) e = sgemm<float>(false, false, m, kb, n, 1.f, A, a->lda, b->svd.Q, kb, 0.f, W, kb, st);
-  if (e == cudaSuccess) e = sgemm<float>(false, false, ka, kb, n, 1.f, a->svd.X, n, b->svd.Q, kb, 0.f, Z, kb, st);
-  if (e == cudaSuccess) e = sgemm<float>(false, false, m, kb, ka, -1.f, a->svd.Q, ka, Z, kb, 1.f, W, kb, st);
-  if (e == cudaSuccess) e = sgemm<float>(false, false, m, p, ka, 1.f, a->svd.Q, ka, T1, p, 0.f, C, ldc, st);
-  if (e == cudaSuccess) e = sgemm<float>(false, false, m, p, kb, 1.f, W, kb, b->svd.X, p, 1.f, C, ldc, st);
-  dev_free(T1, st);
-  dev_free(W, st);
-  dev_free(Z, st);
+  if (a->svd.bf16 != b->svd.bf16) return fail(AMM_ERR_STATE, "svd: both operands need the same compute mode");
+  cudaError_t e = a->svd.bf16 ? svd_matmul_tc<__nv_bfloat16>(a, b, C, ldc, st) : svd_matmul_tc<float>(a, b, C, ldc, st);
   if (e != cudaSuccess) return cuda_fail(e, "svd product");
   return AMM_OK;
 }
 
 amm_status_t svd_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, float* dB,
                           int64_t lddb, cudaStream_t st) {
-  if (a->svd.tc && b->svd.tc) {
-    if (a->svd.bf16 != b->svd.bf16) return fail(AMM_ERR_STATE, "svd: both operands need the same compute mode");
-    cudaError_t e = a->svd.bf16 ? svd_backward_tc<__nv_bfloat16>(a, b, G, ldg, dA, ldda, dB, lddb, st)
-                                : svd_backward_tc<float>(a, b, G, ldg, dA, ldda, dB, lddb, st);
-    if (e != cudaSuccess) return cuda_fail(e, "svd backward");
-    return AMM_OK;
-  }
-  const int m = (int)a->rows, n = (int)a->cols, p = (int)b->cols;
-  const int ka = (int)a->k, kb = (int)b->k;
-  const float* A = (const float*)a->A;
-  const float* B = (const float*)b->A;
-  const float *QA = a->svd.Q, *ZA = a->svd.X, *QB = b->svd.Q, *ZB = b->svd.X;
-  float *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H4 = nullptr, *W = nullptr, *Z = nullptr, *H5 = nullptr;
-  cudaError_t e = cudaSuccess;
-  auto al = [&](float** ptr, size_t cnt) {
-    if (e == cudaSuccess) e = dev_alloc((void**)ptr, sizeof(float) * cnt, st);
-  };
-  al(&H2, (size_t)ka * p);  // Q_A^T G
-  if (e == cudaSuccess) e = sgemm<float>(true, false, ka, p, m, 1.f, QA, ka, G, ldg, 0.f, H2, p, st);
-  if (dA) {
-    al(&H1, (size_t)m * kb);
-    al(&H3, (size_t)ka * n);
-    al(&H4, (size_t)ka * kb);
-    // dA = (G Z_B^T) Q_B^T + Q_A [ H2 B^T - (H2 Z_B^T) Q_B^T ]
-    if (e == cudaSuccess) e = sgemm<float>(false, true, m, kb, p, 1.f, G, ldg, ZB, p, 0.f, H1, kb, st);
-    if (e == cudaSuccess) e = sgemm<float>(false, true, m, n, kb, 1.f, H1, kb, QB, kb, 0.f, dA, ldda, st);
-    if (e == cudaSuccess) e = sgemm<float>(false, true, ka, n, p, 1.f, H2, p, B, b->lda, 0.f, H3, n, st);
-    if (e == cudaSuccess) e = sgemm<float>(false, true, ka, kb, p, 1.f, H2, p, ZB, p, 0.f, H4, kb, st);
-    if (e == cudaSuccess) e = sgemm<float>(false, true, ka, n, kb, -1.f, H4, kb, QB, kb, 1.f, H3, n, st);
-    if (e == cudaSuccess) e = sgemm<float>(false, false, m, n, ka, 1.f, QA, ka, H3, n, 1.f, dA, ldda, st);
-  }
-  if (dB) {
-    al(&W, (size_t)m * kb);
-    al(&Z, (size_t)ka * kb);
-    al(&H5, (size_t)kb * p);
-    // W = A Q_B - Q_A (Z_A Q_B) ; dB = Z_A^T H2 + Q_B (W^T G)
-    if (e == cudaSuccess) e = sgemm<float>(false, false, m, kb, n, 1.f, A, a->lda, QB, kb, 0.f, W, kb, st);
-    if (e == cudaSuccess) e = sgemm<float>(false, false, ka, kb, n, 1.f, ZA, n, QB, kb, 0.f, Z, kb, st);
-    if (e == cudaSuccess) e = sgemm<float>(false, false, m, kb, ka, -1.f, QA, ka, Z, kb, 1.f, W, kb, st);
-    if (e == cudaSuccess) e = sgemm<float>(true, false, kb, p, m, 1.f, W, kb, G, ldg, 0.f, H5, p, st);
-    if (e == cudaSuccess) e = sgemm<float>(true, false, n, p, ka, 1.f, ZA, n, H2, p, 0.f, dB, lddb, st);
-    if (e == cudaSuccess) e = sgemm<float>(false, false, n, p, kb, 1.f, QB, kb, H5, p, 1.f, dB, lddb, st);
-  }
-  for (float* ptr : {H1, H2, H3, H4, W, Z, H5}) dev_free(ptr, st);
+  if (a->svd.bf16 != b->svd.bf16) return fail(AMM_ERR_STATE, "svd: both operands need the same compute mode");
+  cudaError_t e = a->svd.bf16 ? svd_backward_tc<__nv_bfloat16>(a, b, G, ldg, dA, ldda, dB, lddb, st)
+                              : svd_backward_tc<float>(a, b, G, ldg, dA, ldda, dB, lddb, st);
   if (e != cudaSuccess) return cuda_fail(e, "svd backward");
   return AMM_OK;
 }
 
 amm_status_t svd_info(Handle* h, amm_info_t* info) {
+  // ||A||_F^2 and ||Q^T A||_F^2, on the handle's stream (A is borrowed and still alive)
+  const int64_t m = h->rows, n = h->cols;
+  cudaError_t e = h->dtype == AMM_BF16
+                      ? sumsq<__nv_bfloat16>((const __nv_bfloat16*)h->A, m, n, h->lda, h->svd.norms + 0, h->stream)
+                      : sumsq<float>((const float*)h->A, m, n, h->lda, h->svd.norms + 0, h->stream);
+  if (e == cudaSuccess) e = sumsq<float>(h->svd.X, h->k, n, n, h->svd.norms + 1, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   double nr[2];
-  cudaError_t e = cudaMemcpy(nr, h->svd.norms, sizeof(nr), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(nr, h->svd.norms, sizeof(nr), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "svd_info");
   if (h->svd.err) {
     int flag = 0;

@@ -2,7 +2,9 @@
 //
 //   C[M x N] = alpha * A[M x K] * B[N x K]^T + beta * C        (A, B K-major: row-major along K)
 //
-// One 128 x 128 output tile per CTA (K optionally split over grid.z into a workspace).
+// One 128 x 128 output tile per CTA.  K may be split over grid.z: every split stores its partial
+// tile in a workspace and the CTA that finishes a tile last (a per-tile counter) sums the
+// partials in split order, in FP64, into C; no separate reduction launch.
 // Warps 0-3 drain the accumulator from tensor memory, warp 4 drives TMA, warp 5 issues MMAs:
 //   * TMA (cp.async.bulk.tensor.2d) loads 128-row x 128-byte boxes of A and B with the 128-byte
 //     swizzle into a STAGES-deep ring, completion tracked by mbarrier transaction counts;
@@ -37,6 +39,7 @@ namespace amm {
 constexpr int UM_BM = 128, UM_BN = 128;
 constexpr int UM_THREADS = 192;
 constexpr int UM_TF32_MAX_KB = 16;  // longest TF32X3 accumulation chain, in 32-wide k-blocks
+constexpr int UM_CTA_FIXED_KB = 8;  // per-CTA set-up and epilogue cost, in k-blocks (split choice)
 constexpr uint32_t UM_SPIN_LIMIT = 1u << 26;  // ~ seconds of polling, then give up
 
 // ----------------------------------------------------------------------------- PTX wrappers
@@ -129,16 +132,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 // ----------------------------------------------------------------------------- the kernel
-// Shared memory (1024-aligned): STAGES x {A tile, B tile} (+ lo tiles for TF32X3), then barriers.
+// Shared memory (1024-aligned): a ring of RAW stages {A tile, B tile} written by TMA; for TF32X3
+// also a ring of SLOTS split slots {A hi, B hi, A lo, B lo} read by the MMAs; then barriers.
+// BF16 tiles go from the TMA ring straight to the MMAs.  TF32X3 tiles are split into hi/lo by
+// the four epilogue warps, which release the raw stage as soon as it is read, so TMA keeps
+// RAW stages in flight while the MMAs work from the split ring.
 template <bool TF32>
 struct UmmaCfg {
   static constexpr int ELEM = TF32 ? 4 : 2;
   static constexpr int BK = 128 / ELEM;                      // one 128-byte swizzle atom of K
   static constexpr int MMA_K = 32 / ELEM;                    // K per tcgen05.mma
   static constexpr int TILE_BYTES = UM_BM * 128;             // 16 KiB per operand tile
-  static constexpr int STAGE_BYTES = (TF32 ? 4 : 2) * TILE_BYTES;  // A, B (+ A lo, B lo)
-  static constexpr int STAGES = TF32 ? 3 : 5;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+  static constexpr int RAW = TF32 ? 3 : 5;                   // TMA stages
+  static constexpr int RAW_BYTES = 2 * TILE_BYTES;           // A, B
+  static constexpr int SLOTS = TF32 ? 2 : 0;                 // split slots
+  static constexpr int SLOT_BYTES = 4 * TILE_BYTES;          // A hi, B hi, A lo, B lo
+  static constexpr size_t SMEM = 1024 + (size_t)RAW * RAW_BYTES + (size_t)SLOTS * SLOT_BYTES + 256;
 };
 
 // Round to the nearest TF32 value (10 fraction bits, ties away from zero); Inf and NaN pass.
@@ -148,13 +157,16 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float((u + 0x1000u) & 0xFFFFE000u);
 }
 
-// Split x into hi = tf32(x) in place and lo = tf32(x - hi).  Both halves are rounded to nearest,
-// so |x - hi - lo| <= 2^-22 |x| and the tensor core's operand truncation loses nothing.
-__device__ __forceinline__ void split_tile(float* hi, float* lo, int nfloat, int tid, int nthr) {
+// Split raw x into hi = tf32(x) and lo = tf32(x - hi).  Both halves are rounded to nearest, so
+// |x - hi - lo| <= 2^-22 |x| and the tensor core's operand truncation loses nothing.  The copy
+// keeps byte offsets, so the 128-byte-swizzled layout of the TMA tile carries over.
+__device__ __forceinline__ void split_tile(const float* raw, float* hi, float* lo, int nfloat, int tid, int nthr) {
+  const float4* r4 = reinterpret_cast<const float4*>(raw);
   float4* h4 = reinterpret_cast<float4*>(hi);
   float4* l4 = reinterpret_cast<float4*>(lo);
+#pragma unroll 4
   for (int i = tid; i < nfloat / 4; i += nthr) {
-    float4 x = h4[i], h, l;
+    float4 x = r4[i], h, l;
     h.x = tf32_round(x.x); l.x = tf32_round(x.x - h.x);
     h.y = tf32_round(x.y); l.y = tf32_round(x.y - h.y);
     h.z = tf32_round(x.z); l.z = tf32_round(x.z - h.z);
@@ -167,32 +179,39 @@ __device__ __forceinline__ void split_tile(float* hi, float* lo, int nfloat, int
 template <bool TF32>
 __global__ void __launch_bounds__(UM_THREADS, 1)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                     int K, float alpha, float beta, float* __restrict__ C, int64_t ldc, int kchunk,
-                     float* __restrict__ ws, int* __restrict__ err) {
+                     int K, float alpha, float beta, float* __restrict__ C, int64_t ldc,
+                     float* __restrict__ ws, int* __restrict__ tile_count, int* __restrict__ err) {
   using Cfg = UmmaCfg<TF32>;
-  constexpr int UM_STAGES = Cfg::STAGES;
+  constexpr int RAW = Cfg::RAW;
+  constexpr int SLOTS = Cfg::SLOTS > 0 ? Cfg::SLOTS : 1;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* tiles = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + (size_t)UM_STAGES * Cfg::STAGE_BYTES);
-  uint64_t* split_done = full + UM_STAGES;  // TF32X3: hi/lo split finished
-  uint64_t* empty = split_done + UM_STAGES;
-  uint64_t* accum = empty + UM_STAGES;
+  unsigned char* tiles = smem;                                           // raw ring
+  unsigned char* slots = tiles + (size_t)RAW * Cfg::RAW_BYTES;          // split ring (TF32X3)
+  uint64_t* full = reinterpret_cast<uint64_t*>(slots + (size_t)Cfg::SLOTS * Cfg::SLOT_BYTES);
+  uint64_t* empty = full + RAW;
+  uint64_t* sfull = empty + RAW;   // split slot written
+  uint64_t* sempty = sfull + SLOTS;  // split slot consumed by the MMAs
+  uint64_t* accum = sempty + SLOTS;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * UM_BM, n0 = blockIdx.x * UM_BN;
-  const int kbeg = blockIdx.z * kchunk;
-  const int kend = min(K, kbeg + kchunk);
-  const int nkb = (kend - kbeg + Cfg::BK - 1) / Cfg::BK;
+  // split z takes the k-blocks z, z + Z, z + 2Z, ... (Z = gridDim.z): the Z CTAs of a tile read
+  // adjacent 128-byte segments of the same rows at about the same time (DRAM page locality)
+  const int kblocks = (K + Cfg::BK - 1) / Cfg::BK;
+  const int nkb = (kblocks - (int)blockIdx.z + (int)gridDim.z - 1) / (int)gridDim.z;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int s = 0; s < UM_STAGES; ++s) {
+    for (int s = 0; s < RAW; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&split_done[s], 128);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], TF32 ? 128 : 1);  // TF32X3: the splitters release it; BF16: the MMA commit
+    }
+    for (int t = 0; t < SLOTS; ++t) {
+      mbar_init(&sfull[t], 128);
+      mbar_init(&sempty[t], 1);
     }
     mbar_init(accum, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -213,13 +232,13 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
       for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % UM_STAGES;
-        const uint32_t ph = (kb / UM_STAGES) & 1;
+        const int s = kb % RAW;
+        const uint32_t ph = (kb / RAW) & 1;
         ok = mbar_wait(&empty[s], ph ^ 1);
         if (!ok) break;
-        unsigned char* st = tiles + (size_t)s * Cfg::STAGE_BYTES;
+        unsigned char* st = tiles + (size_t)s * Cfg::RAW_BYTES;
         mbar_expect_tx(&full[s], 2 * Cfg::TILE_BYTES);
-        const int kx = kbeg + kb * Cfg::BK;
+        const int kx = ((int)blockIdx.z + kb * (int)gridDim.z) * Cfg::BK;
         tma_load_2d(st, &tmA, &full[s], kx, m0);
         tma_load_2d(st + Cfg::TILE_BYTES, &tmB, &full[s], kx, n0);
       }
@@ -230,12 +249,18 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = umma_idesc(TF32 ? 2u : 1u, UM_BM, UM_BN);
       for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % UM_STAGES;
-        const uint32_t ph = (kb / UM_STAGES) & 1;
-        ok = TF32 ? mbar_wait(&split_done[s], ph) : mbar_wait(&full[s], ph);
+        unsigned char* st;
+        if constexpr (TF32) {
+          const int t = kb % SLOTS;
+          ok = mbar_wait(&sfull[t], (kb / SLOTS) & 1);
+          st = slots + (size_t)t * Cfg::SLOT_BYTES;
+        } else {
+          const int s = kb % RAW;
+          ok = mbar_wait(&full[s], (kb / RAW) & 1);
+          st = tiles + (size_t)s * Cfg::RAW_BYTES;
+        }
         if (!ok) break;
         tc_fence_after();
-        unsigned char* st = tiles + (size_t)s * Cfg::STAGE_BYTES;
         const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + Cfg::TILE_BYTES);
         const uint32_t a_lo = smem_u32(st + 2 * Cfg::TILE_BYTES), b_lo = smem_u32(st + 3 * Cfg::TILE_BYTES);
 #pragma unroll
@@ -248,7 +273,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
             umma<TF32>(tmem + 128u, umma_desc(a_lo + off), umma_desc(b_hi + off), idesc, 1u);
           }
         }
-        umma_commit(&empty[s]);  // stage free once these MMAs have read it
+        // the slot / stage is free once these MMAs have read it
+        if constexpr (TF32) umma_commit(&sempty[kb % SLOTS]);
+        else umma_commit(&empty[kb % RAW]);
       }
       umma_commit(accum);
       if (!ok) atomicExch(&s_fail, 1);
@@ -257,16 +284,18 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     // ---------------------------------------------------------------- warps 0-3
     if constexpr (TF32) {
       for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % UM_STAGES;
-        const uint32_t ph = (kb / UM_STAGES) & 1;
-        ok = mbar_wait(&full[s], ph);
+        const int s = kb % RAW, t = kb % SLOTS;
+        ok = mbar_wait(&full[s], (kb / RAW) & 1);
+        if (ok) ok = mbar_wait(&sempty[t], ((kb / SLOTS) & 1) ^ 1);
         if (!ok) break;
-        unsigned char* st = tiles + (size_t)s * Cfg::STAGE_BYTES;
-        split_tile((float*)st, (float*)(st + 2 * Cfg::TILE_BYTES), Cfg::TILE_BYTES / 4, threadIdx.x, 128);
-        split_tile((float*)(st + Cfg::TILE_BYTES), (float*)(st + 3 * Cfg::TILE_BYTES), Cfg::TILE_BYTES / 4,
-                   threadIdx.x, 128);
+        const float* raw = reinterpret_cast<const float*>(tiles + (size_t)s * Cfg::RAW_BYTES);
+        float* slot = reinterpret_cast<float*>(slots + (size_t)t * Cfg::SLOT_BYTES);
+        constexpr int TF = Cfg::TILE_BYTES / 4;
+        split_tile(raw, slot, slot + 2 * TF, TF, threadIdx.x, 128);                // A -> A hi, A lo
+        split_tile(raw + TF, slot + TF, slot + 3 * TF, TF, threadIdx.x, 128);      // B -> B hi, B lo
+        mbar_arrive(&empty[s]);                                                    // raw stage read
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async proxy (MMA)
-        mbar_arrive(&split_done[s]);
+        mbar_arrive(&sfull[t]);
       }
     }
     if (ok) ok = mbar_wait(accum, 0);
@@ -316,6 +345,28 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
   if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+  if (ws != nullptr) {
+    // split K: the CTA that stores the last partial of this tile sums all of them, in split
+    // order and in FP64, into C (the partials are published with a fence before the count)
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) s_last = atomicAdd(&tile_count[tile], 1) == (int)gridDim.z - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      for (int e = threadIdx.x; e < UM_BM * UM_BN; e += UM_THREADS) {
+        const int row = m0 + e / UM_BN, col = n0 + e % UM_BN;
+        if (row >= M || col >= N) continue;
+        double acc = 0.0;
+        for (int z = 0; z < (int)gridDim.z; ++z) acc += (double)__ldcg(ws + ((int64_t)z * M + row) * N + col);
+        float* c = C + (int64_t)row * ldc + col;
+        *c = (beta == 0.f) ? (float)(alpha * acc) : (float)fma((double)alpha, acc, (double)beta * (double)*c);
+      }
+      if (threadIdx.x == 0) tile_count[tile] = 0;
+    }
+  }
 }
 
 // ----------------------------------------------------------------------------- host side
@@ -349,16 +400,6 @@ static cudaError_t make_map(CUtensorMap* tm, const void* base, bool tf32, int64_
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-__global__ void umma_splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ ws, float alpha,
-                                          float beta, float* __restrict__ C, int64_t ldc) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)M * N) return;
-  double s = 0.0;  // the partials are summed in FP64 (a handful of adds per output)
-  for (int z = 0; z < splits; ++z) s += (double)ws[(int64_t)z * M * N + e];
-  float* c = C + (e / N) * ldc + (e % N);
-  *c = (beta == 0.f) ? (float)(alpha * s) : (float)fma((double)alpha, s, (double)beta * (double)*c);
-}
-
 int umma_num_sms() {
   static int n = 0;
   if (!n) {
@@ -385,20 +426,35 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
   if ((e = make_map(&tb, B, tf32, N, K, ldb)) != cudaSuccess) return e;
   const int bk = 128 / elem;
   const int tiles = ((M + UM_BM - 1) / UM_BM) * ((N + UM_BN - 1) / UM_BN);
-  int splits = 1;
   const int kblocks = (K + bk - 1) / bk;
-  if (tiles < umma_num_sms() && kblocks >= 8)
-    splits = std::min(std::min((umma_num_sms() + tiles - 1) / tiles, kblocks / 4), 32);
-  // TF32X3: the tensor core's FP32 accumulation loses up to an ulp per MMA, so no accumulator
-  // chain runs longer than UM_TF32_MAX_KB k-blocks; longer K is split and summed in FP64.
-  if (tf32) splits = std::max(splits, (kblocks + UM_TF32_MAX_KB - 1) / UM_TF32_MAX_KB);
-  splits = std::max(splits, 1);
-  int kchunk = ((kblocks + splits - 1) / splits) * bk;
-  splits = (K + kchunk - 1) / kchunk;
+  // K splits: minimise waves x per-CTA time (chain of k-blocks + a fixed prologue / epilogue cost of
+  // about UM_CTA_FIXED_KB k-blocks) + the partial sums, with TF32X3 chains of at most
+  // UM_TF32_MAX_KB k-blocks (the tensor core's FP32 accumulation loses up to an ulp per MMA; longer
+  // K is split and the partials are summed in FP64)
+  const int nsm = umma_num_sms();
+  const int smin = tf32 ? std::max(1, (kblocks + UM_TF32_MAX_KB - 1) / UM_TF32_MAX_KB) : 1;
+  const int smax = std::max(smin, std::min(32, kblocks / 2));
+  int splits = smin;
+  int64_t best = -1;
+  for (int s = smin; s <= smax; ++s) {
+    const int64_t waves = ((int64_t)tiles * s + nsm - 1) / nsm;
+    const int64_t cost = waves * ((kblocks + s - 1) / s + UM_CTA_FIXED_KB) + (s > 1 ? s : 0);
+    if (best < 0 || cost < best) {
+      best = cost;
+      splits = s;
+    }
+  }
   float* ws = nullptr;
+  int* tile_count = nullptr;
   if (splits > 1) {
     e = dev_alloc((void**)&ws, sizeof(float) * (size_t)splits * M * N, st);
-    if (e != cudaSuccess) return e;
+    if (e == cudaSuccess) e = dev_alloc((void**)&tile_count, sizeof(int) * (size_t)tiles, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tile_count, 0, sizeof(int) * (size_t)tiles, st);
+    if (e != cudaSuccess) {
+      dev_free(ws, st);
+      dev_free(tile_count, st);
+      return e;
+    }
   }
   dim3 grid((N + UM_BN - 1) / UM_BN, (M + UM_BM - 1) / UM_BM, splits);
   {
@@ -410,24 +466,19 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
                                                   (int)UmmaCfg<true>::SMEM);
       if (a != cudaSuccess) return a;
       umma_gemm_kernel<true><<<grid, UM_THREADS, UmmaCfg<true>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
-                                                                             kchunk, ws, err);
+                                                                             ws, tile_count, err);
     } else {
       static cudaError_t a = cudaFuncSetAttribute((const void*)umma_gemm_kernel<false>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)UmmaCfg<false>::SMEM);
       if (a != cudaSuccess) return a;
       umma_gemm_kernel<false><<<grid, UM_THREADS, UmmaCfg<false>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
-                                                                               kchunk, ws, err);
+                                                                               ws, tile_count, err);
     }
   }
   e = cudaGetLastError();
-  if (e == cudaSuccess && splits > 1) {
-    AMM_TRACE("umma_splitk_reduce", st);
-    const int64_t tot = (int64_t)M * N;
-    umma_splitk_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, splits, ws, alpha, beta, C, ldc);
-    e = cudaGetLastError();
-  }
-  if (ws) dev_free(ws, st);
+  dev_free(ws, st);
+  dev_free(tile_count, st);
   return e;
 }
 

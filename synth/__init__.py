@@ -152,6 +152,14 @@ def llm_shaped(seed: int = 0, m: int = 2048, d: int = 4096, f: int = 11008):
     return x, w
 
 
+def differentiation_case(seed: int = 0, n: int = 8192, p: int = 4096, decay: float = 256.0):
+    """The autograd-layer workload: A n x n = Q1 diag(e^{-i/decay}) Q2^T (noise-free), B n x p and
+    the upstream gradient m x p both N(0, 1)."""
+    a = spectrum_matrix(np.exp(-np.arange(n) / decay), rng(seed, STREAM_A))
+    b = rng(seed, STREAM_B).standard_normal((n, p))
+    return a, b, upstream_grad(n, p, seed)
+
+
 def upstream_grad(m: int, p: int, seed: int = 0) -> np.ndarray:
     return rng(seed, STREAM_G).standard_normal((m, p))
 

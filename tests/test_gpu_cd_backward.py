@@ -45,7 +45,7 @@ def test_cd_backward_unpaired_on_both_sides():
     assert ea <= TOL and eb <= TOL, (ea, eb)
 
 
-@pytest.mark.parametrize("k", [16, 64])
+@pytest.mark.parametrize("k", [16, 64, 256])
 def test_cd_backward_powerlaw_n4096(k):
     torch, amm = torch_cuda()
     a, b = S.powerlaw_pair(4096, seed=0)

@@ -1,0 +1,86 @@
+"""GPU parity of products whose operands are truncated by different methods (Eq. (2.3) with
+each side's own truncation; the two decompositions may differ, Section 1)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from gpu_util import TOL, as64, dev32, rel, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+METHODS = ("circulant", "svd", "fourier", "cycle")
+PAIRS = [(x, y) for x in METHODS for y in METHODS if x != y]
+
+
+def _handle(torch, amm, X, method, k, side, seed):
+    """GPU handle and the oracle truncation of the same operand (GPU selection / sketch)."""
+    x64 = as64(X)
+    if method == "svd":
+        phi = S.sketch(X.shape[1], k, seed, 0 if side == "left" else 1).astype(np.float32)
+        h = amm.decompose(X, method, k, side, sketch=dev32(torch, phi))
+        return h, O.truncate_rsvd(x64, k, phi.astype(np.float64))
+    h = amm.decompose(X, method, k, side)
+    sel = h.selection()
+    if method == "circulant":
+        return h, O.truncate_circulant(x64, k, sel)
+    if method == "cycle":
+        return h, O.truncate_cycles(x64, k, sel)
+    if side == "left":
+        return h, O.truncate_fourier_left(x64, k, forced=sel)
+    return h, O.truncate_fourier_right(x64, k, forced=sel)
+
+
+def _case(ma, mb, a, b, k, seed):
+    torch, amm = torch_cuda()
+    A, B = dev32(torch, a), dev32(torch, b)
+    hA, ta = _handle(torch, amm, A, ma, k, "left", seed)
+    hB, tb = _handle(torch, amm, B, mb, k, "right", seed)
+    C = amm.approx_matmul(hA, hB)
+    return rel(C.double().cpu().numpy(), O.mixed_product(ta, tb))
+
+
+@pytest.mark.parametrize("ma,mb", PAIRS)
+@pytest.mark.parametrize("n,k", [(64, 5), (256, 9)])
+def test_mixed_square(ma, mb, n, k):
+    g = S.rng(n + k, 7)
+    a = g.standard_normal((n, n)) + 0.5          # a dominant zero component: odd k splits a pair
+    b = S.toeplitz_uniform(n, g) + 0.1 * g.standard_normal((n, n))
+    err = _case(ma, mb, a, b, k, n)
+    assert err <= TOL, (ma, mb, n, k, err)
+
+
+@pytest.mark.parametrize("ma,mb,m,n,p", [("svd", "fourier", 100, 128, 37), ("fourier", "svd", 77, 64, 130),
+                                         ("svd", "cycle", 90, 64, 64), ("fourier", "circulant", 50, 128, 128),
+                                         ("cycle", "svd", 64, 64, 33), ("circulant", "fourier", 128, 128, 40),
+                                         ("svd", "circulant", 33, 256, 256), ("circulant", "svd", 256, 256, 7)])
+def test_mixed_rectangular_ragged(ma, mb, m, n, p):
+    """Rectangular outer sizes, including ragged column / row counts for the spectral applies."""
+    g = S.rng(m + n + p, 8)
+    a = g.standard_normal((m, n)) + 0.3
+    b = g.uniform(0, 1, (n, p))
+    err = _case(ma, mb, a, b, 6, m + p)
+    assert err <= TOL, (ma, mb, m, n, p, err)
+
+
+def test_mixed_untruncated_reproduces_product():
+    """k = n on both sides of an SVD x circulant product: the exact product."""
+    torch, amm = torch_cuda()
+    n = 64
+    g = S.rng(9, 0)
+    a, b = g.standard_normal((n, n)), g.standard_normal((n, n))
+    A, B = dev32(torch, a), dev32(torch, b)
+    phi = dev32(torch, S.sketch(n, n, 9, 0))
+    C = amm.approx_matmul(amm.decompose(A, "svd", n, "left", sketch=phi), amm.decompose(B, "circulant", n, "right"))
+    assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= 1e-5
+
+
+def test_mixed_backward_is_reported_not_built():
+    torch, amm = torch_cuda()
+    n = 32
+    g = S.rng(10, 0)
+    A, B = dev32(torch, g.standard_normal((n, n))), dev32(torch, g.standard_normal((n, n)))
+    hA = amm.decompose(A, "cycle", 3, "left")
+    hB = amm.decompose(B, "circulant", 3, "right")
+    with pytest.raises(RuntimeError, match="mixed"):
+        amm.approx_matmul_backward(hA, hB, dev32(torch, g.standard_normal((n, n))))

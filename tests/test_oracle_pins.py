@@ -227,6 +227,46 @@ def test_first_order_identity(method, k):
     assert np.abs((a @ b - m) - ta.resid @ tb.resid).max() < 1e-12 * np.abs(a @ b).max()
 
 
+_MIXED = [(x, y) for x in ("circulant", "svd", "fourier", "cycle") for y in ("circulant", "svd", "fourier", "cycle")
+          if x != y]
+
+
+def _trunc_side(method, x, k, side, seed):
+    if method == "svd":
+        return O.truncate_rsvd(x, k, S.sketch(x.shape[1], k, seed, 0 if side == "left" else 1))
+    return O.truncate(method, x, k, side=side)
+
+
+@pytest.mark.parametrize("ma,mb", _MIXED)
+def test_mixed_untruncated_is_exact(ma, mb):
+    """Mixed methods, k = n on both sides: M = AB."""
+    n = 16
+    a, b = _rand(n, 40), _rand(n, 41)
+    ta, tb = _trunc_side(ma, a, n, "left", 40), _trunc_side(mb, b, n, "right", 40)
+    assert np.abs(O.mixed_product(ta, tb) - O.exact_product_loops(a, b)).max() < 1e-12 * np.abs(a @ b).max()
+
+
+@pytest.mark.parametrize("ma,mb", _MIXED)
+def test_mixed_first_order_identity(ma, mb):
+    """Mixed methods: AB - M = dA dB (Eq. (2.1)-(2.3)) with each side's own truncation, and the real
+    part equals Re(A~) B + Re(dA) Re(B~) - Im(dA) Im(B~) term by term."""
+    n, k = 16, 5
+    a, b = _rand(n, 42), S.rng(42, 1).uniform(0, 1, (n, n))
+    ta, tb = _trunc_side(ma, a, k, "left", 42), _trunc_side(mb, b, k, "right", 42)
+    m = O.first_order(ta, tb)
+    assert np.abs((a @ b - m) - ta.resid @ tb.resid).max() < 1e-12 * np.abs(a @ b).max()
+    split = ta.approx.real @ b + ta.resid.real @ tb.approx.real - ta.resid.imag @ tb.approx.imag
+    assert np.abs(O.mixed_product(ta, tb) - split).max() < 1e-12 * np.abs(a @ b).max()
+
+
+def test_fourier_space_form_equals_transform_form():
+    """Alg. 5's transform-domain product equals Eq. (2.3) with A_s = A~_a W and B_s = W^* B~_a."""
+    n, k = 16, 3
+    a, b = _rand(n, 43), _rand(n, 44)
+    ta, tb = O.truncate_fourier_left(a, k), O.truncate_fourier_right(b, k)
+    assert np.abs(O.product("fourier", ta, tb) - O.first_order(ta, tb).real).max() < 1e-12 * np.abs(a @ b).max()
+
+
 def test_exact_product_loops():
     a, b = _rand(5, 16, m=3), _rand(4, 17, m=5)
     assert np.abs(O.exact_product_loops(a, b) - a @ b).max() < 1e-14
@@ -363,7 +403,22 @@ def test_backward_matches_bruteforce(method):
     assert np.abs(da - bda).max() < 1e-12 and np.abs(db - bdb).max() < 1e-12
 
 
-@pytest.mark.parametrize("method", ["circulant", "svd"])
+def test_fourier_backward_asymmetric_masks_bruteforce():
+    """Single-tone rows keep f but not n - f at k = 1 (exact tie, lower index first): the kept
+    set is not mirror-symmetric, M is complex, and the gradient of Re M still matches brute force."""
+    n = 8
+    l = np.arange(n)
+    a = np.stack([np.cos(2 * np.pi * (i % 3 + 1) * l / n) * (1 + i) for i in range(5)])
+    g = S.rng(31, 0)
+    b, gr = g.standard_normal((n, 6)), g.standard_normal((5, 6))
+    ta, tb = O.truncate_fourier_left(a, 1), O.truncate_fourier_right(b, 2)
+    assert not np.array_equal(ta.mask, ta.mask[:, (-np.arange(n)) % n])
+    da, db = O.fourier_backward(ta, tb, gr)
+    bda, bdb = O.brute_force_gradient("fourier", ta, tb, gr)
+    assert np.abs(da - bda).max() < 1e-12 and np.abs(db - bdb).max() < 1e-12
+
+
+@pytest.mark.parametrize("method", ["circulant", "svd", "fourier", "cycle"])
 def test_backward_finite_differences_n64(method):
     """Central finite differences of the frozen map at n = 64 (FP64) along random directions."""
     n, k = 64, 6
