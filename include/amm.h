@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define AMM_VERSION 1
+#define AMM_VERSION 2
 
 typedef enum {
   AMM_OK = 0,
@@ -75,6 +75,12 @@ typedef struct amm_opts {
   const int32_t* forced_selection;/* optional HOST array of k component indices that replaces
                                      the top-k selection (AMM_CIRCULANT, AMM_SPARSE_CYCLE);
                                      used to evaluate a selection exported elsewhere          */
+  int32_t pair_closed;            /* AMM_CIRCULANT: 1 keeps the conjugate partner n - t of every
+                                     selected component t as well (S u S-bar, at most 2k
+                                     components; usually k or k + 1), which makes A~ real and
+                                     M = Re M.  amm_handle_get_selection still returns the k
+                                     ranked components; the truncation error of amm_handle_info
+                                     is that of the closed set.  Default 0.                   */
 } amm_opts_t;
 
 typedef struct amm_info {
@@ -164,6 +170,17 @@ amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const 
 
 /* Sizes, norms and selection statistics.  Synchronises the handle's stream. */
 amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info);
+
+/*
+ * Posterior estimate of the relative error ||dA dB||_F / ||A B||_F of a computed product
+ * (Corollary 3.7, Section 3): ||dA||_F ||dB||_F / (sqrt(n) ||C||_F), n the inner dimension,
+ * with ||dA||_F, ||dB||_F the truncation errors of the two handles (amm_handle_info) and C the
+ * product written by amm_approx_matmul (device, m x p, ldc).  For independent residue entries it
+ * bounds the expected error; for structured operands it tracks the observed error.
+ * Synchronises `stream` and both handles' streams; *estimate is a host double.
+ */
+amm_status_t amm_error_estimate(amm_handle_t hA, amm_handle_t hB, const float* C, int64_t ldc,
+                                void* stream, double* estimate);
 
 /*
  * Copy the selection to host memory: circulant component indices / cycle indices in

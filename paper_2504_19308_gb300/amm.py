@@ -33,7 +33,7 @@ class AmmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("role", ctypes.c_int32), ("compute", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("sketch", ctypes.c_void_p), ("store_spectra", ctypes.c_int32),
-                ("forced_selection", ctypes.POINTER(ctypes.c_int32))]
+                ("forced_selection", ctypes.POINTER(ctypes.c_int32)), ("pair_closed", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -54,6 +54,8 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_void_p)]),
     "amm_approx_matmul": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.c_void_p]),
+    "amm_error_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "amm_approx_matmul_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                                   ctypes.c_void_p]),
@@ -169,10 +171,11 @@ class Handle:
 
 
 def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: Optional[torch.Tensor] = None,
-              seed: int = 0, forced_selection=None, compute: str = "f32") -> Handle:
+              seed: int = 0, forced_selection=None, compute: str = "f32", pair_closed: bool = False) -> Handle:
     """amm_decompose: truncated decomposition of A (method 'circulant' | 'svd' | 'fourier' | 'cycle').
 
     compute: arithmetic of the SVD GEMMs, 'f32' (FP32-accurate) or 'bf16' (BF16 tensor cores).
+    pair_closed: circulant selections closed under t -> n - t (a real truncation).
     """
     lib = load_library()
     _require_cuda(A, "A")
@@ -183,6 +186,7 @@ def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: 
     opts.role = ROLES[role]
     opts.seed = seed
     opts.compute = {"f32": 0, "bf16": 1}[compute]
+    opts.pair_closed = 1 if pair_closed else 0
     extras = []
     if sketch is not None:
         _require_cuda(sketch, "sketch")
@@ -208,6 +212,15 @@ def approx_matmul(hA: Handle, hB: Handle, out: Optional[torch.Tensor] = None) ->
     _check(load_library().amm_approx_matmul(hA.ptr, hB.ptr, out.data_ptr(), out.stride(0),
                                             _stream_ptr(out.device)), "amm_approx_matmul")
     return out
+
+
+def error_estimate(hA: Handle, hB: Handle, C: torch.Tensor) -> float:
+    """amm_error_estimate: ||dA|| ||dB|| / (sqrt(n) ||C||) (Corollary 3.7) for a computed product C."""
+    _require_cuda(C, "C")
+    est = ctypes.c_double(0.0)
+    _check(load_library().amm_error_estimate(hA.ptr, hB.ptr, C.data_ptr(), C.stride(0), _stream_ptr(C.device),
+                                             ctypes.byref(est)), "amm_error_estimate")
+    return est.value
 
 
 def approx_matmul_backward(hA: Handle, hB: Handle, dC: torch.Tensor, need_dA: bool = True, need_dB: bool = True):

@@ -3,6 +3,8 @@
 // file only validates, allocates (stream-ordered) and launches.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <atomic>
 #include <cstdarg>
@@ -186,7 +188,8 @@ static amm_status_t decompose_circulant(Handle* h, const amm_opts_t* o) {
   const bool bf16 = h->dtype == AMM_BF16;
   if ((e = cd_spectrum(n, h->A, h->lda, bf16, c.tw, c.R, c.kpart, h->stream)) != cudaSuccess)
     return cuda_fail(e, "cd_spectrum launch");
-  if ((e = cd_select(n, (int)h->k, c.kpart, c.nparts, forced, c.so, h->stream)) != cudaSuccess)
+  const bool closed = o && o->pair_closed;
+  if ((e = cd_select(n, (int)h->k, c.kpart, c.nparts, forced, c.so, h->stream, true, closed)) != cudaSuccess)
     return cuda_fail(e, "cd_select launch");
   if ((e = cd_eigen(n, c.R, c.tw, c.so.ulist, c.so.uw, c.so.counts, c.cap, 0, c.Lw, h->stream)) != cudaSuccess)
     return cuda_fail(e, "cd_eigen launch");
@@ -537,7 +540,43 @@ extern "C" amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info) {
     }
   } else if (h->method == AMM_SVD) {
     return svd_info(h, info);
+  } else if (h->method == AMM_SPARSE_FOURIER) {
+    double* d = nullptr;
+    double nr[2];
+    if ((e = dev_alloc((void**)&d, sizeof(nr), h->stream)) != cudaSuccess) return cuda_fail(e, "amm_handle_info");
+    e = ft_norms(h->ft.n, (int)h->k, h->ft.nvec, h->ft.mag, h->ft.sel, d, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nr, d, sizeof(nr), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(d, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "amm_handle_info: fourier norms");
+    info->fro2 = nr[0];
+    info->resid_fro2 = nr[0] - nr[1];  // W is unitary: the dropped entries carry the rest
   }
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_error_estimate(amm_handle_t hA, amm_handle_t hB, const float* C, int64_t ldc,
+                                           void* stream, double* estimate) {
+  if (!estimate) return fail(AMM_ERR_INVALID_ARG, "amm_error_estimate: estimate is NULL");
+  if (!C) return fail(AMM_ERR_INVALID_ARG, "amm_error_estimate: C is NULL");
+  amm_status_t s = check_pair(hA, hB);
+  if (s != AMM_OK) return s;
+  if (ldc < hB->cols) return fail(AMM_ERR_INVALID_ARG, "amm_error_estimate: ldc too small");
+  amm_info_t ia, ib;
+  if ((s = amm_handle_info(hA, &ia)) != AMM_OK) return s;
+  if ((s = amm_handle_info(hB, &ib)) != AMM_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* d = nullptr;
+  double c2 = 0.0;
+  cudaError_t e = dev_alloc((void**)&d, sizeof(double), st);
+  if (e == cudaSuccess) e = sumsq_f32(C, hA->rows, hB->cols, ldc, d, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c2, d, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dev_free(d, st);
+  if (e != cudaSuccess) return cuda_fail(e, "amm_error_estimate");
+  if (c2 <= 0.0) return fail(AMM_ERR_STATE, "amm_error_estimate: ||C||_F = 0");
+  const double ra = std::max(ia.resid_fro2, 0.0), rb = std::max(ib.resid_fro2, 0.0);
+  *estimate = std::sqrt(ra * rb) / (std::sqrt((double)hA->cols) * std::sqrt(c2));
   return AMM_OK;
 }
 

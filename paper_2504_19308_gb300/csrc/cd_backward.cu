@@ -125,6 +125,127 @@ __global__ void __launch_bounds__(256) cd_sddmm_kernel(const float2* __restrict_
   }
 }
 
+// Tiled form for dense selections (many listed t per range of n/16).  A CTA takes a window of
+// SDT_P frequencies p and a range of SDT_W component indices [T0, T0 + SDT_W): the Yh rows t - p
+// of every listed t in the range and every p in the window are the SDT_P + SDT_W - 1 consecutive
+// rows starting at T0 - p0 - SDT_P + 1.  Chunks of SDT_MC columns of those rows and of the SDT_P
+// Xh rows are copied to shared memory with cp.async, double-buffered (the next chunk is in flight
+// while the current one is used); rows are padded to SDT_MC + 1 complex (conflict-free column
+// reads) and copied raw, with the conjugation of mirrored rows applied as a sign at use.  Each
+// staged Yh element serves every listed t that reaches it, and each thread keeps its Xh row
+// chunk in registers, so a complex MAC costs one shared load.  Warp w owns p = p0 + 32 (w & 1) +
+// lane and the slots j = (w >> 1) + 4 i of the range's listed t's, in batches of 4 SDT_SLOTS.
+constexpr int SDT_P = 64, SDT_W = 256, SDT_MC = 16, SDT_NT = 256, SDT_SLOTS = 16;
+constexpr int SDT_LDM = SDT_MC + 1, SDT_YR = SDT_P + SDT_W - 1;
+constexpr size_t SDT_STAGE = (size_t)(SDT_P + SDT_YR) * SDT_LDM;  // float2 per stage
+constexpr size_t SDT_SMEM = sizeof(float2) * 2 * SDT_STAGE + sizeof(float) * (SDT_P + SDT_YR) +
+                            sizeof(int) * 2 * SDT_W + 16;
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+template <int N>
+__global__ void __launch_bounds__(SDT_NT) cd_sddmm_tiled_kernel(const float2* __restrict__ Xh,
+                                                               const float2* __restrict__ Yh,
+                                                               const int32_t* __restrict__ list,
+                                                               const int32_t* __restrict__ count,
+                                                               float2* __restrict__ K,
+                                                               const int32_t* __restrict__ gate0,
+                                                               const int32_t* __restrict__ gate1) {
+  extern __shared__ __align__(16) unsigned char sdt_raw[];
+  float2* stage = reinterpret_cast<float2*>(sdt_raw);                       // 2 x [P + YR][LDM]
+  float* sgn = reinterpret_cast<float*>(stage + 2 * SDT_STAGE);            // [P + YR] row signs
+  int* s_u = reinterpret_cast<int*>(sgn + SDT_P + SDT_YR);                  // [W]
+  int* s_t = s_u + SDT_W;                                                    // [W]
+  __shared__ int s_cnt;
+  if (gate0 != nullptr && (*gate0 == 0 || *gate1 == 0)) return;
+  const int T0 = blockIdx.x * SDT_W, p0 = blockIdx.y * SDT_P;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  const int nl = *count;
+  for (int i = threadIdx.x; i < nl; i += SDT_NT) {
+    const int t = __ldg(list + i);
+    if (t >= T0 && t < T0 + SDT_W && t <= N / 2) {
+      const int pos = atomicAdd(&s_cnt, 1);
+      s_u[pos] = i;
+      s_t[pos] = t;
+    }
+  }
+  const int rlo = T0 - p0 - SDT_P + 1;  // first staged Yh row (mod N)
+  for (int row = threadIdx.x; row < SDT_P + SDT_YR; row += SDT_NT) {
+    const int q = row < SDT_P ? p0 + row : (rlo + row - SDT_P) & (N - 1);
+    sgn[row] = q > N / 2 ? -1.f : 1.f;
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  if (cnt == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pl = (warp & 1) * 32 + lane;  // p - p0
+  const int sub = warp >> 1;
+  const float xs = sgn[pl];
+  auto load_chunk = [&](int m0, float2* buf) {
+    for (int e = threadIdx.x; e < (SDT_P + SDT_YR) * SDT_MC; e += SDT_NT) {
+      const int row = e / SDT_MC, m = e % SDT_MC;
+      const int q = row < SDT_P ? p0 + row : (rlo + row - SDT_P) & (N - 1);
+      const int qr = q > N / 2 ? N - q : q;
+      cp_async8(buf + row * SDT_LDM + m, (row < SDT_P ? Xh : Yh) + (int64_t)qr * N + m0 + m);
+    }
+    cp_async_commit();
+  };
+  for (int tb0 = 0; tb0 < cnt; tb0 += 4 * SDT_SLOTS) {
+    float2 acc[SDT_SLOTS];
+#pragma unroll
+    for (int i = 0; i < SDT_SLOTS; ++i) acc[i] = make_float2(0.f, 0.f);
+    constexpr int NCH = N / SDT_MC;
+    load_chunk(0, stage);
+    for (int c = 0; c < NCH; ++c) {
+      float2* cur = stage + (c & 1) * SDT_STAGE;
+      if (c + 1 < NCH) {
+        load_chunk((c + 1) * SDT_MC, stage + ((c + 1) & 1) * SDT_STAGE);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      float2 x[SDT_MC];
+#pragma unroll
+      for (int m = 0; m < SDT_MC; ++m) {
+        x[m] = cur[pl * SDT_LDM + m];
+        x[m].y *= xs;
+      }
+      const float2* ybase = cur + SDT_P * SDT_LDM;
+#pragma unroll
+      for (int i = 0; i < SDT_SLOTS; ++i) {
+        const int j = tb0 + sub + 4 * i;
+        if (j >= cnt) break;  // warp-uniform
+        const int yr = (s_t[j] - T0) + (SDT_P - 1) - pl;
+        const float ys = sgn[SDT_P + yr];
+        const float2* y = ybase + yr * SDT_LDM;
+#pragma unroll
+        for (int m = 0; m < SDT_MC; ++m) {
+          float2 v = y[m];
+          v.y *= ys;
+          cmac(acc[i], x[m], v);
+        }
+      }
+      __syncthreads();  // the buffer of chunk c is refilled next iteration
+    }
+#pragma unroll
+    for (int i = 0; i < SDT_SLOTS; ++i) {
+      const int j = tb0 + sub + 4 * i;
+      if (j < cnt) K[(int64_t)s_u[j] * N + p0 + pl] = acc[i];
+    }
+  }
+}
+
 // ============================================================================ component spectra
 // RX[t][j] = (1/n^2) sum_p e^{2 pi i p j/n} K[u][p] for t = list[u] <= n/2 (RX zeroed beforehand).
 template <int N, int NT>
@@ -180,6 +301,14 @@ template <int N> struct BwOps {
   }
   static cudaError_t sddmm(const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
                            float2* K, const int32_t* g0, const int32_t* g1, cudaStream_t st) {
+    if (N >= 2 * SDT_W && (int64_t)cap * 12 >= N) {  // dense enough that a staged Yh row serves several t
+      static cudaError_t attr = cudaFuncSetAttribute((const void*)cd_sddmm_tiled_kernel<N>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SDT_SMEM);
+      if (attr != cudaSuccess) return attr;
+      dim3 grid((N / 2 + SDT_W) / SDT_W, N / SDT_P);
+      cd_sddmm_tiled_kernel<N><<<grid, SDT_NT, SDT_SMEM, st>>>(Xh, Yh, list, count, K, g0, g1);
+      return cudaGetLastError();
+    }
     dim3 grid((cap + SD_UB - 1) / SD_UB, N / 8);
     cd_sddmm_kernel<N><<<grid, 256, 0, st>>>(Xh, Yh, list, count, K, g0, g1);
     return cudaGetLastError();

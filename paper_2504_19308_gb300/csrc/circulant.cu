@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(1024) cd_keyreduce_kernel(const float* __restr
 
 __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restrict__ key2, int n,
                                                           int k, const int32_t* __restrict__ forced,
-                                                          SelectOut out, int mirror, double scale) {
+                                                          SelectOut out, int mirror, double scale,
+                                                          int pair_closed) {
   extern __shared__ unsigned char sm[];
   double* key = reinterpret_cast<double*>(sm);                        // n (later: k sorted keys)
   unsigned char* in_s = reinterpret_cast<unsigned char*>(key + n);    // n
@@ -249,9 +250,13 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
     if (threadIdx.x == 0) out.norms[2] = -1.0;
     __syncthreads();
   }
-  // ||dA||^2 = ||A||^2 - scale * sum_{t in S} T[t]^2
+  // ||dA||^2 = ||A||^2 - scale * sum_{t in S} T[t]^2 (S u S-bar when the selection is pair-closed:
+  // the partner's key equals the component's own)
   part = 0.0;
-  for (int t = threadIdx.x; t < n; t += SEL_T) if (in_s[t]) part += key[t];
+  for (int t = threadIdx.x; t < n; t += SEL_T) {
+    if (in_s[t]) part += key[t];
+    if (pair_closed && in_s[t] && !in_s[(n - t) & (n - 1)]) part += key[t];
+  }
   const double kept = block_sum(part, red);
   if (threadIdx.x == 0) out.norms[1] = total * scale - kept * scale;
   // compact the selection (ascending index), then order it by (key desc, index asc)
@@ -296,6 +301,13 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
     for (int t = threadIdx.x; t < k; t += SEL_T) out.sel[t] = forced[t];
   } else if (sortable) {
     for (int t = threadIdx.x; t < k; t += SEL_T) out.sel[t] = sidx[t];
+  }
+  if (pair_closed) {  // S <- S u S-bar: every kept component with its conjugate partner, M real
+    unsigned char cl[(8192 + SEL_T - 1) / SEL_T];
+    for (int t = c0; t < c1; ++t) cl[t - c0] = in_s[t] | in_s[(n - t) & (n - 1)];
+    __syncthreads();
+    for (int t = c0; t < c1; ++t) in_s[t] = cl[t - c0];
+    __syncthreads();
   }
   // union S u S-bar (weight w_t) and unpaired set (v_t), compacted in index order
   int nu = 0, nd = 0;
@@ -393,16 +405,29 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
   __syncthreads();
   fft_smem<N, S, NT, true>(smem, tw);
   const float* fs = reinterpret_cast<const float*>(smem);
-  static_assert((N * J) % NT == 0, "whole iterations");
-#pragma unroll 8
-  for (int it = 0; it < N * J / NT; ++it) {  // unrolled: several loads in flight per thread
-    const int e = threadIdx.x + it * NT;
-    const int r = e / J, q = e % J;
-    const int c = (r - j0 - (J - 1) + q) & (N - 1);
-    const int m = J - 1 - q;
-    const float v = fs[2 * ((m >> 1) * LD + fpad(c)) + (m & 1)];
-    float* o = X + (int64_t)r * ldx + c;
-    *o = accumulate ? *o + v : v;
+  constexpr int IT = N * J / NT, B = 8;  // B outputs per batch: their loads are all in flight
+  static_assert(IT % B == 0, "whole batches");
+  for (int i0 = 0; i0 < IT; i0 += B) {
+    float* o[B];
+    float v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int e = threadIdx.x + (i0 + b) * NT;
+      const int r = e / J, q = e % J;
+      const int c = (r - j0 - (J - 1) + q) & (N - 1);
+      const int m = J - 1 - q;
+      v[b] = fs[2 * ((m >> 1) * LD + fpad(c)) + (m & 1)];
+      o[b] = X + (int64_t)r * ldx + c;
+    }
+    if (accumulate) {
+      float old[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) old[b] = *o[b];
+#pragma unroll
+      for (int b = 0; b < B; ++b) v[b] += old[b];
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) *o[b] = v[b];
   }
 }
 
@@ -476,29 +501,76 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
   constexpr float inv_n = 1.0f / (float)N;
   if (!ROW) {
     const bool vec2 = ((ldo & 1) == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);  // pairs as float2
-    for (int e = threadIdx.x; e < N * S; e += NT) {
-      const int l = e / S, s = e % S;
-      const int v = base + 2 * s;
-      float2 z = cscale(smem[s * LD + fpad(l)], inv_n);
-      float* o = out + (int64_t)l * ldo + v;
-      if (v + 1 < nvec && vec2) {
-        float2* o2 = reinterpret_cast<float2*>(o);
-        if (accumulate) { float2 old = *o2; z.x += old.x; z.y += old.y; }
-        *o2 = z;
-      } else {
-        if (v < nvec) o[0] = accumulate ? o[0] + z.x : z.x;
-        if (v + 1 < nvec) o[1] = accumulate ? o[1] + z.y : z.y;
+    constexpr int IT = N * S / NT, B = IT < 8 ? IT : 8;  // B outputs per batch, loads in flight
+    static_assert(IT % B == 0, "whole batches");
+    for (int i0 = 0; i0 < IT; i0 += B) {
+      float2 z[B];
+      float* o[B];
+      int v[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int e = threadIdx.x + (i0 + b) * NT;
+        const int l = e / S, s = e % S;
+        v[b] = base + 2 * s;
+        z[b] = cscale(smem[s * LD + fpad(l)], inv_n);
+        o[b] = out + (int64_t)l * ldo + v[b];
+      }
+      if (accumulate) {
+        float2 old[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          if (v[b] + 1 < nvec && vec2) old[b] = *reinterpret_cast<const float2*>(o[b]);
+          else old[b] = make_float2(v[b] < nvec ? o[b][0] : 0.f, v[b] + 1 < nvec ? o[b][1] : 0.f);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          z[b].x += old[b].x;
+          z[b].y += old[b].y;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (v[b] + 1 < nvec && vec2) {
+          *reinterpret_cast<float2*>(o[b]) = z[b];
+        } else {
+          if (v[b] < nvec) o[b][0] = z[b].x;
+          if (v[b] + 1 < nvec) o[b][1] = z[b].y;
+        }
       }
     }
   } else {
-    for (int e = threadIdx.x; e < N * S; e += NT) {
-      const int s = e / N, l = e % N;
-      const int v = base + 2 * s;
-      float2 z = cscale(smem[s * LD + fpad(l)], inv_n);
-      float* o0 = out + (int64_t)v * ldo + l;
-      float* o1 = o0 + ldo;
-      if (v < nvec) *o0 = accumulate ? *o0 + z.x : z.x;
-      if (v + 1 < nvec) *o1 = accumulate ? *o1 + z.y : z.y;
+    constexpr int IT = N * S / NT, B = IT < 8 ? IT : 8;  // B outputs per batch, loads in flight
+    static_assert(IT % B == 0, "whole batches");
+    for (int i0 = 0; i0 < IT; i0 += B) {
+      float2 z[B];
+      float* o0[B];
+      int v[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int e = threadIdx.x + (i0 + b) * NT;
+        const int s = e / N, l = e % N;
+        v[b] = base + 2 * s;
+        z[b] = cscale(smem[s * LD + fpad(l)], inv_n);
+        o0[b] = out + (int64_t)v[b] * ldo + l;
+      }
+      if (accumulate) {
+        float a0[B], a1[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          a0[b] = v[b] < nvec ? *o0[b] : 0.f;
+          a1[b] = v[b] + 1 < nvec ? o0[b][ldo] : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          z[b].x += a0[b];
+          z[b].y += a1[b];
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        if (v[b] < nvec) *o0[b] = z[b].x;
+        if (v[b] + 1 < nvec) o0[b][ldo] = z[b].y;
+      }
     }
   }
 }
@@ -623,7 +695,7 @@ cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const floa
 }
 
 cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_t* forced, const SelectOut& o,
-                      cudaStream_t st, bool mirror) {
+                      cudaStream_t st, bool mirror, bool pair_closed) {
   auto bytes = [](int nn) {
     return (size_t)nn * (sizeof(double) + 1) + 8 + (size_t)SEL_SORT_MAX * (sizeof(double) + sizeof(int32_t));
   };
@@ -642,7 +714,8 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   AMM_TRACE("cd_select", st);
-  cd_select_kernel<<<1, SEL_T, bytes(n), st>>>(o.key2, n, k, forced, o, mirror ? 1 : 0, mirror ? (double)n : 1.0);
+  cd_select_kernel<<<1, SEL_T, bytes(n), st>>>(o.key2, n, k, forced, o, mirror ? 1 : 0, mirror ? (double)n : 1.0,
+                                                (mirror && pair_closed) ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -45,13 +45,15 @@ __global__ void cyc_gather_kernel(const float* __restrict__ A, int64_t lda, int 
 constexpr int CYC_CW = 4;    // columns per CTA (A_s B)
 constexpr int CYC_RW = 4;    // rows per CTA (dA B_s)
 constexpr int CYC_NT = 256;
+constexpr int CYC_RG = 8;    // rows (or columns) per thread per pass of the component loop
 
 // out(:, c0..c0+3) = sum_u cyc[u][r - t_u] B(r - t_u, c)
 __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __restrict__ B, int64_t ldb, int n,
                                                                const int32_t* __restrict__ sel, int k,
                                                                const float* __restrict__ cyc, float* __restrict__ out,
                                                                int64_t ldo, int ncols) {
-  extern __shared__ float4 bp[];  // n x 4 columns
+  extern __shared__ float4 bp[];  // n x 4 columns, then the k selected cycle indices
+  int* s_sel = reinterpret_cast<int*>(bp + n);
   const int c0 = blockIdx.x * CYC_CW;
   for (int r = threadIdx.x; r < n; r += CYC_NT) {
     const float* src = B + (int64_t)r * ldb + c0;
@@ -62,24 +64,41 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __re
     v.w = c0 + 3 < ncols ? __ldg(src + 3) : 0.f;
     bp[r] = v;
   }
+  for (int u = threadIdx.x; u < k; u += CYC_NT) s_sel[u] = __ldg(sel + u);
   __syncthreads();
-  for (int r = threadIdx.x; r < n; r += CYC_NT) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 8
+  // CYC_RG rows per thread at a time, components in the outer loop: CYC_RG independent gathers
+  // of cyc in flight per component
+  for (int r0 = threadIdx.x; r0 < n; r0 += CYC_NT * CYC_RG) {
+    float4 acc[CYC_RG];
+#pragma unroll
+    for (int i = 0; i < CYC_RG; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int u = 0; u < k; ++u) {
-      const int l = (r - __ldg(sel + u)) & (n - 1);
-      const float a = __ldg(cyc + (int64_t)u * n + l);
-      const float4 b = bp[l];
-      acc.x = fmaf(a, b.x, acc.x);
-      acc.y = fmaf(a, b.y, acc.y);
-      acc.z = fmaf(a, b.z, acc.z);
-      acc.w = fmaf(a, b.w, acc.w);
+      const int t = s_sel[u];
+      const float* crow = cyc + (int64_t)u * n;
+#pragma unroll
+      for (int i = 0; i < CYC_RG; ++i) {
+        const int r = r0 + i * CYC_NT;
+        if (r < n) {
+          const int l = (r - t) & (n - 1);
+          const float a = __ldg(crow + l);
+          const float4 b = bp[l];
+          acc[i].x = fmaf(a, b.x, acc[i].x);
+          acc[i].y = fmaf(a, b.y, acc[i].y);
+          acc[i].z = fmaf(a, b.z, acc[i].z);
+          acc[i].w = fmaf(a, b.w, acc[i].w);
+        }
+      }
     }
-    float* o = out + (int64_t)r * ldo + c0;
-    if (c0 + 0 < ncols) o[0] = acc.x;
-    if (c0 + 1 < ncols) o[1] = acc.y;
-    if (c0 + 2 < ncols) o[2] = acc.z;
-    if (c0 + 3 < ncols) o[3] = acc.w;
+#pragma unroll
+    for (int i = 0; i < CYC_RG; ++i) {
+      const int r = r0 + i * CYC_NT;
+      if (r >= n) continue;
+      float* o = out + (int64_t)r * ldo + c0;
+      if (c0 + 0 < ncols) o[0] = acc[i].x;
+      if (c0 + 1 < ncols) o[1] = acc[i].y;
+      if (c0 + 2 < ncols) o[2] = acc[i].z;
+      if (c0 + 3 < ncols) o[3] = acc[i].w;
+    }
   }
 }
 
@@ -149,29 +168,45 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_col_kernel(const float* __restr
                                                             const int32_t* __restrict__ selA, int ka,
                                                             const float* __restrict__ cycA, float* __restrict__ out,
                                                             int64_t ldo) {
-  extern __shared__ float4 gp[];  // n x 4 columns
+  extern __shared__ float4 gp[];  // n x 4 columns; then the ka selected cycle indices of A
+  int* s_sel = reinterpret_cast<int*>(gp + n);
   const int c0 = blockIdx.x * CYC_CW;
   for (int r = threadIdx.x; r < n; r += CYC_NT) {
     const float* src = G + (int64_t)r * ldg + c0;
     gp[r] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
   }
+  for (int u = threadIdx.x; u < ka; u += CYC_NT) s_sel[u] = __ldg(selA + u);
   __syncthreads();
-  for (int q = threadIdx.x; q < n; q += CYC_NT) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 8
+  for (int qb = threadIdx.x; qb < n; qb += CYC_NT * CYC_RG) {
+    float4 acc[CYC_RG];
+#pragma unroll
+    for (int i = 0; i < CYC_RG; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int u = 0; u < ka; ++u) {
-      const float a = __ldg(cycA + (int64_t)u * n + q);
-      const float4 g = gp[(q + __ldg(selA + u)) & (n - 1)];
-      acc.x = fmaf(a, g.x, acc.x);
-      acc.y = fmaf(a, g.y, acc.y);
-      acc.z = fmaf(a, g.z, acc.z);
-      acc.w = fmaf(a, g.w, acc.w);
+      const int t = s_sel[u];
+      const float* arow = cycA + (int64_t)u * n;
+#pragma unroll
+      for (int i = 0; i < CYC_RG; ++i) {
+        const int q = qb + i * CYC_NT;
+        if (q < n) {
+          const float a = __ldg(arow + q);
+          const float4 g = gp[(q + t) & (n - 1)];
+          acc[i].x = fmaf(a, g.x, acc[i].x);
+          acc[i].y = fmaf(a, g.y, acc[i].y);
+          acc[i].z = fmaf(a, g.z, acc[i].z);
+          acc[i].w = fmaf(a, g.w, acc[i].w);
+        }
+      }
     }
-    float* o = out + (int64_t)q * ldo + c0;
-    o[0] = acc.x;
-    o[1] = acc.y;
-    o[2] = acc.z;
-    o[3] = acc.w;
+#pragma unroll
+    for (int i = 0; i < CYC_RG; ++i) {
+      const int q = qb + i * CYC_NT;
+      if (q >= n) continue;
+      float* o = out + (int64_t)q * ldo + c0;
+      o[0] = acc[i].x;
+      o[1] = acc[i].y;
+      o[2] = acc[i].z;
+      o[3] = acc[i].w;
+    }
   }
 }
 
@@ -225,7 +260,7 @@ cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int
                                          CYC_RW * 8192 * (int)sizeof(float));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute((const void*)cyc_bw_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               8192 * (int)sizeof(float4));
+                               (8192 * (int)sizeof(float4) + 8192 * (int)sizeof(int)));
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -245,7 +280,7 @@ cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int
   if (dB) {
     {
       AMM_TRACE_W("cyc_bw_col", st, 2.0 * ka * (double)n * n, 8.0 * n * (double)n, nullptr);
-      cyc_bw_col_kernel<<<n / CYC_CW, CYC_NT, sizeof(float4) * n, st>>>(G, ldg, n, selA, ka, cycA, dB, lddb);
+      cyc_bw_col_kernel<<<n / CYC_CW, CYC_NT, sizeof(float4) * n + sizeof(int) * ka, st>>>(G, ldg, n, selA, ka, cycA, dB, lddb);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     {
@@ -283,7 +318,7 @@ cudaError_t cyc_apply(int n, const float* A, int64_t lda, const float* B, int64_
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute((const void*)cyc_apply_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8192 * (int)sizeof(float4));
+                                         (8192 * (int)sizeof(float4) + 8192 * (int)sizeof(int)));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute((const void*)cyc_apply_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                CYC_RW * 8192 * (int)sizeof(float));
@@ -292,7 +327,7 @@ cudaError_t cyc_apply(int n, const float* A, int64_t lda, const float* B, int64_
   }
   {
     AMM_TRACE_W("cyc_apply_col", st, 2.0 * ka * (double)n * n, 8.0 * n * (double)n, nullptr);
-    cyc_apply_col_kernel<<<(n + CYC_CW - 1) / CYC_CW, CYC_NT, sizeof(float4) * n, st>>>(B, ldb, n, selA, ka, cycA, C,
+    cyc_apply_col_kernel<<<(n + CYC_CW - 1) / CYC_CW, CYC_NT, sizeof(float4) * n + sizeof(int) * ka, st>>>(B, ldb, n, selA, ka, cycA, C,
                                                                                          ldc, n);
   }
   cudaError_t e = cudaGetLastError();
@@ -318,7 +353,7 @@ __global__ void cyc_residual_kernel(const float* __restrict__ A, int64_t lda, in
 static cudaError_t cyc_attrs() {
   static cudaError_t e = [] {
     cudaError_t r = cudaFuncSetAttribute((const void*)cyc_apply_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8192 * (int)sizeof(float4));
+                                         (8192 * (int)sizeof(float4) + 8192 * (int)sizeof(int)));
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute((const void*)cyc_apply_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                CYC_RW * 8192 * (int)sizeof(float));
@@ -333,7 +368,7 @@ cudaError_t cyc_left_apply(int n, const int32_t* selA, int ka, const float* cycA
   cudaError_t e = cyc_attrs();
   if (e != cudaSuccess) return e;
   AMM_TRACE_W("cyc_apply_col", st, 2.0 * ka * (double)n * p, 8.0 * n * (double)p, nullptr);
-  cyc_apply_col_kernel<<<(unsigned)((p + CYC_CW - 1) / CYC_CW), CYC_NT, sizeof(float4) * n, st>>>(X, ldx, n, selA, ka,
+  cyc_apply_col_kernel<<<(unsigned)((p + CYC_CW - 1) / CYC_CW), CYC_NT, sizeof(float4) * n + sizeof(int) * ka, st>>>(X, ldx, n, selA, ka,
                                                                                                   cycA, C, ldc, (int)p);
   return cudaGetLastError();
 }

@@ -348,6 +348,64 @@ cudaError_t ft_product(int n, int m, int p, int k_a, int k_b, const float2* At, 
   return cudaGetLastError();
 }
 
+// ============================================================================ truncation norms
+// Per row of magnitudes |A~(i, q)|^2 (q = 0..n/2): the row's squared norm (Parseval: q and n - q
+// both count except q = 0 and q = n/2) and the squared norm of its kept entries.  Rows are
+// summed afterwards in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) ft_norm_rows_kernel(const float* __restrict__ mag, const int32_t* __restrict__ sel,
+                                                           int n, int k, double* __restrict__ part) {
+  __shared__ double red[2][8];
+  const int row = blockIdx.x, kh = n / 2 + 1;
+  const float* m = mag + (int64_t)row * kh;
+  double tot = 0.0, kept = 0.0;
+  for (int q = threadIdx.x; q < kh; q += 256) tot += (q == 0 || q == n / 2 ? 1.0 : 2.0) * (double)__ldg(m + q);
+  for (int u = threadIdx.x; u < k; u += 256) {
+    const int q = __ldg(sel + (int64_t)row * k + u);
+    kept += (double)__ldg(m + (q > n / 2 ? n - q : q));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    kept += __shfl_xor_sync(0xffffffffu, kept, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = tot;
+    red[1][threadIdx.x >> 5] = kept;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    part[2 * row] = a;
+    part[2 * row + 1] = b;
+  }
+}
+
+__global__ void ft_norm_sum_kernel(const double* __restrict__ part, int rows, double* __restrict__ out) {
+  if (threadIdx.x < 2) {
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += part[2 * r + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+cudaError_t ft_norms(int n, int k, int nvec, const float* mag, const int32_t* sel, double* out, cudaStream_t st) {
+  double* part = nullptr;
+  cudaError_t e = dev_alloc((void**)&part, sizeof(double) * 2 * (size_t)nvec, st);
+  if (e != cudaSuccess) return e;
+  {
+    AMM_TRACE("ft_norms", st);
+    ft_norm_rows_kernel<<<nvec, 256, 0, st>>>(mag, sel, n, k, part);
+  }
+  ft_norm_sum_kernel<<<1, 32, 0, st>>>(part, nvec, out);
+  e = cudaGetLastError();
+  dev_free(part, st);
+  return e;
+}
+
 // ============================================================================ mixed-method pieces
 // Dense real or imaginary part of A_s = A~_a W (the sparse rows back in the space domain):
 // part 0: y = Re(A~_a W) through the Hermitian part H(q) = (X(q) + conj X(-q))/2 of each row;

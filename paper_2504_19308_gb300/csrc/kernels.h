@@ -24,8 +24,9 @@ int cd_cols_per_cta(int n);
 cudaError_t cd_twiddles(float2* tw, int n, cudaStream_t st);
 cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const float2* tw, float2* R, float* kpart,
                         cudaStream_t st);
+// pair_closed (circulant only): the selection is closed under t -> n - t (S u S-bar), so M is real
 cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_t* forced, const SelectOut& o,
-                      cudaStream_t st, bool mirror = true);
+                      cudaStream_t st, bool mirror = true, bool pair_closed = false);
 cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* list, const float* coef,
                      const int32_t* count, int cap, int imag_coef, float2* L, cudaStream_t st);
 // inverse cycle transform of a (half) spectrum R with coefficients by mode (0: 1-g, 1: -i g,
@@ -87,6 +88,10 @@ struct FtBwArgs {
   int64_t lddb;
 };
 cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st);
+// svd.cu: *out = sum of squares of X (FP64 accumulation), stream-ordered
+cudaError_t sumsq_f32(const float* X, int64_t rows, int64_t cols, int64_t ld, double* out, cudaStream_t st);
+// fourier.cu: out[0] = ||A||_F^2 (Parseval over the half spectrum), out[1] = the kept part
+cudaError_t ft_norms(int n, int k, int nvec, const float* mag, const int32_t* sel, double* out, cudaStream_t st);
 // svd.cu: Y (cols x rows, ldy) = X^T
 cudaError_t transpose_f32(const float* X, int64_t rows, int64_t cols, int64_t ldx, float* Y, int64_t ldy,
                           cudaStream_t st);

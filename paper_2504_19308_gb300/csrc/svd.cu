@@ -496,18 +496,28 @@ static cudaError_t orthonormalize(int64_t m, int k, const float* Y, float* Q, cu
 template <typename TI, typename TO>
 __global__ void transpose_cast_kernel(const TI* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
                                       TO* __restrict__ Y, int64_t ldy) {
-  __shared__ float t[32][33];
-  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-  for (int i = threadIdx.y; i < 32; i += 8) {
-    const int64_t r = r0 + i, c = c0 + threadIdx.x;
-    float v = 0.f;
-    if (r < rows && c < cols) v = (float)X[r * ldx + c];
-    t[i][threadIdx.x] = v;
+  // 64 x 64 tile through padded shared memory; each thread moves 16 elements each way, so
+  // 16 independent loads per thread are in flight
+  __shared__ float t[64][65];
+  const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ri = threadIdx.y + 8 * i, ci = threadIdx.x + 32 * h;
+      const int64_t r = r0 + ri, c = c0 + ci;
+      t[ri][ci] = (r < rows && c < cols) ? (float)X[r * ldx + c] : 0.f;
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += 8) {
-    const int64_t c = c0 + i, r = r0 + threadIdx.x;
-    if (r < rows && c < cols) Y[c * ldy + r] = (TO)t[threadIdx.x][i];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ci = threadIdx.y + 8 * i, ri = threadIdx.x + 32 * h;
+      const int64_t c = c0 + ci, r = r0 + ri;
+      if (r < rows && c < cols) Y[c * ldy + r] = (TO)t[ri][ci];
+    }
   }
 }
 
@@ -524,9 +534,13 @@ template <typename TI, typename TO>
 static cudaError_t transpose_cast(const TI* X, int64_t rows, int64_t cols, int64_t ldx, TO* Y, int64_t ldy,
                                   cudaStream_t st) {
   AMM_TRACE_W("transpose", st, 0.0, (double)rows * cols * (sizeof(TI) + sizeof(TO)), nullptr);
-  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  dim3 grid((unsigned)((cols + 63) / 64), (unsigned)((rows + 63) / 64));
   transpose_cast_kernel<TI, TO><<<grid, dim3(32, 8), 0, st>>>(X, rows, cols, ldx, Y, ldy);
   return cudaGetLastError();
+}
+
+cudaError_t sumsq_f32(const float* X, int64_t rows, int64_t cols, int64_t ld, double* out, cudaStream_t st) {
+  return sumsq<float>(X, rows, cols, ld, out, st);
 }
 
 cudaError_t transpose_f32(const float* X, int64_t rows, int64_t cols, int64_t ldx, float* Y, int64_t ldy,

@@ -3,8 +3,9 @@
 //   C[M x N] = alpha * A[M x K] * B[N x K]^T + beta * C        (A, B K-major: row-major along K)
 //
 // One 128 x 128 output tile per CTA.  K may be split over grid.z: every split stores its partial
-// tile in a workspace and the CTA that finishes a tile last (a per-tile counter) sums the
-// partials in split order, in FP64, into C; no separate reduction launch.
+// tile in a workspace, and a reduction kernel sums the partials in split order (compensated FP32)
+// into C.  (Summing in the last CTA of each tile left one CTA per tile doing all the loads, which
+// measured slower than spreading the sum over the whole GPU.)
 // Warps 0-3 drain the accumulator from tensor memory, warp 4 drives TMA, warp 5 issues MMAs:
 //   * TMA (cp.async.bulk.tensor.2d) loads 128-row x 128-byte boxes of A and B with the 128-byte
 //     swizzle into a STAGES-deep ring, completion tracked by mbarrier transaction counts;
@@ -18,8 +19,8 @@
 //           rounded to nearest; kind::tf32 products hi*hi + hi*lo + lo*hi give products within
 //           about 2^-21 relative (the lo*lo term and the rounding of lo are dropped).  The
 //           small correction products accumulate in a second TMEM accumulator, and long K is
-//           split into chains of at most UM_TF32_MAX_KB k-blocks whose partials are summed in
-//           FP64, which bounds the rounding the tensor core's FP32 accumulation adds.
+//           split into chains of at most UM_TF32_MAX_KB k-blocks whose partials are summed with
+//           compensation, which bounds the rounding the tensor core's FP32 accumulation adds.
 // Every mbarrier wait is bounded; a wait that gives up sets *err and the CTA drains and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -179,8 +180,8 @@ __device__ __forceinline__ void split_tile(const float* raw, float* hi, float* l
 template <bool TF32>
 __global__ void __launch_bounds__(UM_THREADS, 1)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                     int K, float alpha, float beta, float* __restrict__ C, int64_t ldc,
-                     float* __restrict__ ws, int* __restrict__ tile_count, int* __restrict__ err) {
+                     int K, float alpha, float beta, float* __restrict__ C, int64_t ldc, int per,
+                     float* __restrict__ ws, int* __restrict__ err) {
   using Cfg = UmmaCfg<TF32>;
   constexpr int RAW = Cfg::RAW;
   constexpr int SLOTS = Cfg::SLOTS > 0 ? Cfg::SLOTS : 1;
@@ -198,10 +199,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * UM_BM, n0 = blockIdx.x * UM_BN;
-  // split z takes the k-blocks z, z + Z, z + 2Z, ... (Z = gridDim.z): the Z CTAs of a tile read
-  // adjacent 128-byte segments of the same rows at about the same time (DRAM page locality)
+  // split z takes a contiguous run of k-blocks (each CTA streams its row segments in order: DRAM
+  // page locality; interleaving the splits measured 2x slower)
   const int kblocks = (K + Cfg::BK - 1) / Cfg::BK;
-  const int nkb = (kblocks - (int)blockIdx.z + (int)gridDim.z - 1) / (int)gridDim.z;
+  const int kb0 = (int)blockIdx.z * per;  // the host makes every split non-empty
+  const int nkb = min(per, kblocks - kb0);
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
         if (!ok) break;
         unsigned char* st = tiles + (size_t)s * Cfg::RAW_BYTES;
         mbar_expect_tx(&full[s], 2 * Cfg::TILE_BYTES);
-        const int kx = ((int)blockIdx.z + kb * (int)gridDim.z) * Cfg::BK;
+        const int kx = (kb0 + kb) * Cfg::BK;
         tma_load_2d(st, &tmA, &full[s], kx, m0);
         tma_load_2d(st + Cfg::TILE_BYTES, &tmB, &full[s], kx, n0);
       }
@@ -345,28 +347,6 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
   if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
-  if (ws != nullptr) {
-    // split K: the CTA that stores the last partial of this tile sums all of them, in split
-    // order and in FP64, into C (the partials are published with a fence before the count)
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    if (threadIdx.x == 0) s_last = atomicAdd(&tile_count[tile], 1) == (int)gridDim.z - 1;
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      for (int e = threadIdx.x; e < UM_BM * UM_BN; e += UM_THREADS) {
-        const int row = m0 + e / UM_BN, col = n0 + e % UM_BN;
-        if (row >= M || col >= N) continue;
-        double acc = 0.0;
-        for (int z = 0; z < (int)gridDim.z; ++z) acc += (double)__ldcg(ws + ((int64_t)z * M + row) * N + col);
-        float* c = C + (int64_t)row * ldc + col;
-        *c = (beta == 0.f) ? (float)(alpha * acc) : (float)fma((double)alpha, acc, (double)beta * (double)*c);
-      }
-      if (threadIdx.x == 0) tile_count[tile] = 0;
-    }
-  }
 }
 
 // ----------------------------------------------------------------------------- host side
@@ -400,6 +380,42 @@ static cudaError_t make_map(CUtensorMap* tm, const void* base, bool tf32, int64_
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// C = alpha * sum_z ws[z] + beta * C, four consecutive outputs per thread (all split partials of
+// them in flight), summed in split order with Neumaier compensation (FP32)
+__global__ void umma_splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ ws, float alpha,
+                                          float beta, float* __restrict__ C, int64_t ldc) {
+  const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  const int64_t MN = (int64_t)M * N;
+  if (e0 >= MN) return;
+  float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+  const bool vec = (e0 + 4 <= MN) && (N % 4 == 0);
+  for (int z = 0; z < splits; ++z) {
+    const float* w = ws + (int64_t)z * MN + e0;
+    float x[4];
+    if (vec) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(w));
+      x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = e0 + j < MN ? __ldcs(w + j) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float t = sum[j] + x[j];
+      comp[j] += (fabsf(sum[j]) >= fabsf(x[j])) ? (sum[j] - t) + x[j] : (x[j] - t) + sum[j];
+      sum[j] = t;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t e = e0 + j;
+    if (e >= MN) break;
+    float* c = C + (e / N) * ldc + (e % N);
+    const float v = sum[j] + comp[j];
+    *c = (beta == 0.f) ? alpha * v : fmaf(alpha, v, beta * *c);
+  }
+}
+
 int umma_num_sms() {
   static int n = 0;
   if (!n) {
@@ -430,7 +446,7 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
   // K splits: minimise waves x per-CTA time (chain of k-blocks + a fixed prologue / epilogue cost of
   // about UM_CTA_FIXED_KB k-blocks) + the partial sums, with TF32X3 chains of at most
   // UM_TF32_MAX_KB k-blocks (the tensor core's FP32 accumulation loses up to an ulp per MMA; longer
-  // K is split and the partials are summed in FP64)
+  // K is split and the partials are summed with compensation)
   const int nsm = umma_num_sms();
   const int smin = tf32 ? std::max(1, (kblocks + UM_TF32_MAX_KB - 1) / UM_TF32_MAX_KB) : 1;
   const int smax = std::max(smin, std::min(32, kblocks / 2));
@@ -444,17 +460,12 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
       splits = s;
     }
   }
+  const int per = (kblocks + splits - 1) / splits;  // k-blocks per split
+  splits = (kblocks + per - 1) / per;               // no empty split
   float* ws = nullptr;
-  int* tile_count = nullptr;
   if (splits > 1) {
     e = dev_alloc((void**)&ws, sizeof(float) * (size_t)splits * M * N, st);
-    if (e == cudaSuccess) e = dev_alloc((void**)&tile_count, sizeof(int) * (size_t)tiles, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tile_count, 0, sizeof(int) * (size_t)tiles, st);
-    if (e != cudaSuccess) {
-      dev_free(ws, st);
-      dev_free(tile_count, st);
-      return e;
-    }
+    if (e != cudaSuccess) return e;
   }
   dim3 grid((N + UM_BN - 1) / UM_BN, (M + UM_BM - 1) / UM_BM, splits);
   {
@@ -466,19 +477,24 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
                                                   (int)UmmaCfg<true>::SMEM);
       if (a != cudaSuccess) return a;
       umma_gemm_kernel<true><<<grid, UM_THREADS, UmmaCfg<true>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
-                                                                             ws, tile_count, err);
+                                                                             per, ws, err);
     } else {
       static cudaError_t a = cudaFuncSetAttribute((const void*)umma_gemm_kernel<false>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)UmmaCfg<false>::SMEM);
       if (a != cudaSuccess) return a;
       umma_gemm_kernel<false><<<grid, UM_THREADS, UmmaCfg<false>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
-                                                                               ws, tile_count, err);
+                                                                               per, ws, err);
     }
   }
   e = cudaGetLastError();
+  if (e == cudaSuccess && splits > 1) {
+    AMM_TRACE("umma_splitk_reduce", st);
+    const int64_t quads = ((int64_t)M * N + 3) / 4;
+    umma_splitk_reduce_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, st>>>(M, N, splits, ws, alpha, beta, C, ldc);
+    e = cudaGetLastError();
+  }
   dev_free(ws, st);
-  dev_free(tile_count, st);
   return e;
 }
 

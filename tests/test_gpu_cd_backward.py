@@ -71,3 +71,17 @@ def test_cd_autograd_layer():
     rda, rdb = O.cd_backward(ta, tb, as64(gr))
     assert rel(A.grad.double().cpu().numpy(), rda) <= TOL
     assert rel(B.grad.double().cpu().numpy(), rdb) <= TOL
+
+
+@pytest.mark.parametrize("ka,kb", [(48, 45), (5, 60), (101, 3)])
+def test_cd_backward_n1024_dense_and_sparse_selections(ka, kb):
+    """n = 1024 with selections dense enough for the staged (tiled) SDDMM on one or both sides,
+    odd k splitting conjugate pairs (unpaired terms on), and a sparse side on the warp kernel."""
+    torch, amm = torch_cuda()
+    n = 1024
+    g = S.rng(n + ka + kb, 0)
+    a = g.standard_normal((n, n)) + 1.0
+    b = S.toeplitz_uniform(n, g) + 0.2 * g.standard_normal((n, n))
+    gr = g.standard_normal((n, n))
+    ea, eb, ia, ib = _case(torch, amm, a, b, gr, ka, kb)
+    assert ea <= TOL and eb <= TOL, (ea, eb, ia["n_unpaired"], ib["n_unpaired"])

@@ -183,3 +183,31 @@ def test_injected_allocation_failure():
     debug_fail_alloc_after(0)
     h = amm.decompose(A, "circulant", 4, "right")
     assert h.selection().size == 4
+
+
+@pytest.mark.parametrize("n,k", [(64, 5), (256, 9), (1024, 33)])
+def test_circulant_pair_closed_selection(n, k):
+    """pair_closed: the selection is closed under t -> n - t, A~ is real, no unpaired terms, and the
+    product equals the oracle's with the closed set S u S-bar."""
+    torch, amm = torch_cuda()
+    g = S.rng(n + k, 5)
+    a = g.standard_normal((n, n)) + 1.0   # odd k splits a pair without closure
+    b = S.toeplitz_uniform(n, g)
+    A, B = dev32(torch, a), dev32(torch, b)
+    hA = amm.decompose(A, "circulant", k, "left", pair_closed=True)
+    hB = amm.decompose(B, "circulant", k, "right", pair_closed=True)
+    C = amm.approx_matmul(hA, hB)
+    ia = hA.info()
+    assert ia["n_unpaired"] == 0
+    sa, sb = hA.selection(), hB.selection()
+    closed = lambda sel: np.unique(np.concatenate([sel, (-np.asarray(sel)) % n]))
+    ca, cb = closed(sa), closed(sb)
+    assert ia["n_union"] == len(ca)
+    a64, b64 = as64(A), as64(B)
+    ta = O.truncate_circulant(a64, len(ca), ca)
+    tb = O.truncate_circulant(b64, len(cb), cb)
+    m = O.first_order(ta, tb)
+    assert np.abs(m.imag).max() <= 1e-9 * np.abs(m.real).max()
+    assert rel(C.double().cpu().numpy(), m.real) <= TOL
+    # the truncation error reported is that of the closed set
+    assert abs(ia["resid_fro2"] - np.linalg.norm(ta.resid) ** 2) <= 1e-4 * np.linalg.norm(a64) ** 2

@@ -1,0 +1,39 @@
+"""amm_error_estimate (Corollary 3.7) against the oracle's estimate on the same truncations."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from gpu_util import as64, dev32, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("method,k", [("circulant", 3), ("cycle", 9), ("fourier", 45), ("svd", 9)])
+def test_error_estimate_matches_oracle(method, k):
+    torch, amm = torch_cuda()
+    n = 512
+    a, b = S.general_times_toeplitz(n, seed=0)
+    A, B = dev32(torch, a), dev32(torch, b)
+    sa = dev32(torch, S.sketch(n, k, 0, 0)) if method == "svd" else None
+    sb = dev32(torch, S.sketch(n, k, 0, 1)) if method == "svd" else None
+    hA = amm.decompose(A, method, k, "left", sketch=sa)
+    hB = amm.decompose(B, method, k, "right", sketch=sb)
+    C = amm.approx_matmul(hA, hB)
+    est = amm.error_estimate(hA, hB, C)
+    a64, b64 = as64(A), as64(B)
+    if method == "svd":
+        ta = O.truncate_rsvd(a64, k, S.sketch(n, k, 0, 0).astype(np.float32).astype(np.float64))
+        tb = O.truncate_rsvd(b64, k, S.sketch(n, k, 0, 1).astype(np.float32).astype(np.float64))
+    elif method == "fourier":
+        ta = O.truncate_fourier_left(a64, k, forced=hA.selection())
+        tb = O.truncate_fourier_right(b64, k, forced=hB.selection())
+    else:
+        ta = O.truncate(method, a64, k, selection=hA.selection())
+        tb = O.truncate(method, b64, k, selection=hB.selection())
+    ref = O.posterior_estimate(np.linalg.norm(ta.resid), np.linalg.norm(tb.resid),
+                               np.linalg.norm(O.first_order(ta, tb).real), n)
+    # the truncation errors come from FP32 keys / norms: a relative difference of ~1e-4 at most
+    assert abs(est - ref) <= 1e-3 * ref, (est, ref)
+    actual = np.linalg.norm(ta.resid @ tb.resid) / np.linalg.norm(a64 @ b64)
+    assert 0.5 < est / actual < 2.0, (est, actual)

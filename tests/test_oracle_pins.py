@@ -511,3 +511,38 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.undo()
     bda, _ = O.brute_force_gradient("circulant", ta, tb, g)
     assert np.abs(da - bda).max() > 1e-6
+
+
+# --------------------------------------------------------------------------- error estimation
+
+def test_posterior_estimate_tracks_observed_error():
+    """Cor. 3.7: ||dA|| ||dB|| / (sqrt(n) ||M||) overlaps the observed relative error for the
+    structured operands of Section 4 (General x Toeplitz with CD, Type-1 with rSVD)."""
+    n = 512
+    a, b = S.general_times_toeplitz(n, seed=0)
+    for k in (1, 3, 5, 9):
+        ta, tb = O.truncate("circulant", a, k), O.truncate("circulant", b, k)
+        m = O.first_order(ta, tb)
+        actual = np.linalg.norm(ta.resid @ tb.resid) / np.linalg.norm(a @ b)
+        est = O.posterior_estimate(np.linalg.norm(ta.resid), np.linalg.norm(tb.resid), np.linalg.norm(m), n)
+        assert 0.9 < est / actual < 1.1, (k, est, actual)
+    a1, b1 = S.type1(n, S.rng(1, 0)), S.type1(n, S.rng(1, 1))
+    for k in (8, 64):
+        ta, tb = O.truncate_rsvd(a1, k, S.sketch(n, k, 0, 0)), O.truncate_rsvd(b1, k, S.sketch(n, k, 0, 1))
+        m = O.first_order(ta, tb)
+        actual = np.linalg.norm(ta.resid @ tb.resid) / np.linalg.norm(a1 @ b1)
+        est = O.posterior_estimate(np.linalg.norm(ta.resid), np.linalg.norm(tb.resid), np.linalg.norm(m), n)
+        assert 0.9 < est / actual < 1.2, (k, est, actual)
+
+
+def test_posterior_estimate_bounds_gaussian_error():
+    """Independent Gaussian operands: the estimate is an upper bound of the observed error."""
+    n = 256
+    g = S.rng(n, 0)
+    a, b = g.standard_normal((n, n)), g.standard_normal((n, n))
+    for method in ("circulant", "cycle"):
+        ta, tb = O.truncate(method, a, n // 8), O.truncate(method, b, n // 8)
+        m = O.first_order(ta, tb)
+        actual = np.linalg.norm(ta.resid @ tb.resid) / np.linalg.norm(a @ b)
+        est = O.posterior_estimate(np.linalg.norm(ta.resid), np.linalg.norm(tb.resid), np.linalg.norm(m), n)
+        assert est >= actual
