@@ -113,7 +113,8 @@ amm_status_t amm_opts_init(amm_opts_t* opts);
  *   A       device pointer, rows x cols row-major, leading dimension lda, element type
  *           `dtype`.  BORROWED: the handle keeps the pointer (the residual terms and the
  *           backward read A again), so A must stay allocated and unchanged until
- *           amm_handle_destroy().
+ *           amm_handle_destroy().  (BF16 operands of AMM_SPARSE_FOURIER / AMM_SPARSE_CYCLE are
+ *           read once: the handle keeps its own FP32 copy.)
  *   method  AMM_CIRCULANT and AMM_SPARSE_CYCLE need rows == cols (square, Section 2.3:
  *           rectangular matrices are handled blockwise by the caller); the FFT length n
  *           must be a power of two in [16, 8192].

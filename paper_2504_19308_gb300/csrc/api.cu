@@ -204,16 +204,30 @@ static amm_status_t decompose_circulant(Handle* h, const amm_opts_t* o) {
   return AMM_OK;
 }
 
+// BF16 operands of the sparsifiers: the handle keeps an FP32 copy (read once from the caller's
+// BF16 matrix) and every kernel of the method runs on it in FP32.
+static cudaError_t widen_input(Handle* h) {
+  if (h->dtype != AMM_BF16) return cudaSuccess;
+  float* y = nullptr;
+  cudaError_t e = h->alloc((void**)&y, sizeof(float) * (size_t)h->rows * h->cols);
+  if (e == cudaSuccess) e = widen_bf16(h->A, h->rows, h->cols, h->lda, y, h->cols, h->stream);
+  if (e != cudaSuccess) return e;
+  h->A = y;
+  h->lda = h->cols;
+  h->dtype = AMM_F32;
+  return cudaSuccess;
+}
+
 static amm_status_t decompose_cycle(Handle* h, const amm_opts_t* o) {
   const int n = (int)h->rows;
   if (!pow2(n) || n < 16 || n > 8192)
     return fail(AMM_ERR_UNSUPPORTED_SIZE, "cycle: n=%d must be a power of two in [16, 8192]", n);
-  if (h->dtype != AMM_F32) return fail(AMM_ERR_NOT_IMPLEMENTED, "cycle: BF16 inputs are not built yet");
   auto& c = h->cy;
   const int rp = cyc_rows_per_part(n);
   c.nparts = (n + rp - 1) / rp;
   const int cap = (int)std::min<int64_t>(2 * h->k, n);
-  cudaError_t e;
+  cudaError_t e = widen_input(h);
+  if (e != cudaSuccess) return cuda_fail(e, "cycle: BF16 input");
 #define AL(ptr, bytes)                                                              \
   do {                                                                              \
     e = h->alloc((void**)&(ptr), (bytes));                                          \
@@ -263,7 +277,7 @@ static amm_status_t decompose_fourier(Handle* h, const amm_opts_t* o) {
   f.nvec = (int)(left ? h->rows : h->cols);
   if (!pow2(f.n) || f.n < 16 || f.n > 8192)
     return fail(AMM_ERR_UNSUPPORTED_SIZE, "fourier: inner dimension %d must be a power of two in [16, 8192]", f.n);
-  if (h->dtype != AMM_F32) return fail(AMM_ERR_NOT_IMPLEMENTED, "fourier: BF16 inputs are not built yet");
+  if (widen_input(h) != cudaSuccess) return cuda_fail(cudaGetLastError(), "fourier: BF16 input");
   if (o && o->forced_selection) return fail(AMM_ERR_NOT_IMPLEMENTED, "fourier: forced selection is not built");
   if (h->k > f.n) return fail(AMM_ERR_INVALID_ARG, "fourier: k=%lld > n=%d", (long long)h->k, f.n);
   cudaError_t e = twiddles(f.n, h->stream, &f.tw);

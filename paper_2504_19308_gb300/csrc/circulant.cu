@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
   __shared__ unsigned int hist[256];
   __shared__ unsigned long long s_prefix;
   __shared__ unsigned int s_need;
-  __shared__ double s_kth, s_next;
+  __shared__ double s_kth;
   const int kh = mirror ? n / 2 + 1 : n;
   for (int t = threadIdx.x; t < kh; t += SEL_T) {
     const double s = key2[t];
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
     }
     __syncthreads();
     // boundary gap: the k-th key is tau; the next key is the largest key not selected
-    if (threadIdx.x == 0) { s_kth = __longlong_as_double((long long)tau); s_next = -1.0; }
+    if (threadIdx.x == 0) s_kth = __longlong_as_double((long long)tau);
     __syncthreads();
     double nxt = -1.0;
     for (int t = threadIdx.x; t < n; t += SEL_T) if (!in_s[t]) nxt = fmax(nxt, key[t]);
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
   __syncthreads();
   fft_smem<N, S, NT, true>(smem, tw);
   const float* fs = reinterpret_cast<const float*>(smem);
-  constexpr int IT = N * J / NT, B = 8;  // B outputs per batch: their loads are all in flight
+  constexpr int IT = N * J / NT, B = IT < 8 ? IT : 8;  // B outputs per batch: loads all in flight
   static_assert(IT % B == 0, "whole batches");
   for (int i0 = 0; i0 < IT; i0 += B) {
     float* o[B];

@@ -88,6 +88,9 @@ struct FtBwArgs {
   int64_t lddb;
 };
 cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st);
+// svd.cu: Y (FP32, ldy) = X (BF16, rows x cols, ldx)
+cudaError_t widen_bf16(const void* X, int64_t rows, int64_t cols, int64_t ldx, float* Y, int64_t ldy,
+                       cudaStream_t st);
 // svd.cu: *out = sum of squares of X (FP64 accumulation), stream-ordered
 cudaError_t sumsq_f32(const float* X, int64_t rows, int64_t cols, int64_t ld, double* out, cudaStream_t st);
 // fourier.cu: out[0] = ||A||_F^2 (Parseval over the half spectrum), out[1] = the kept part

@@ -556,6 +556,11 @@ static cudaError_t cast(const TI* X, int64_t rows, int64_t cols, int64_t ldx, TO
   return cudaGetLastError();
 }
 
+cudaError_t widen_bf16(const void* X, int64_t rows, int64_t cols, int64_t ldx, float* Y, int64_t ldy,
+                       cudaStream_t st) {
+  return cast<__nv_bfloat16, float>((const __nv_bfloat16*)X, rows, cols, ldx, Y, ldy, st);
+}
+
 // Y = [X1 | X2 | 0] (rows x kpad, E): two thin matrices side by side, zero-padded to kpad columns,
 // so that one K-major GEMM evaluates X1 Z1^T + X2 Z2^T with a single pass over its output.
 template <typename T1, typename T2, typename E>

@@ -88,3 +88,17 @@ def test_cycle_backward(n, ka, kb):
     rda, rdb = O.cycle_backward(ta, tb, as64(Gt))
     assert rel(dA.double().cpu().numpy(), rda) <= TOL
     assert rel(dB.double().cpu().numpy(), rdb) <= TOL
+
+
+def test_cycle_bf16_operands():
+    """BF16 operands of the cycle sparsifier (widened to FP32 once by the handle)."""
+    torch, amm = torch_cuda()
+    n, k = 256, 9
+    a, b = S.general_times_toeplitz(n, seed=12)
+    A = torch.from_numpy(a.astype(np.float32)).cuda().bfloat16()
+    B = torch.from_numpy(b.astype(np.float32)).cuda().bfloat16()
+    hA = amm.decompose(A, "cycle", k, "left")
+    hB = amm.decompose(B, "cycle", k, "right")
+    C = amm.approx_matmul(hA, hB)
+    ref = O.cycle_matmul(as64(A), as64(B), k, sel_a=hA.selection(), sel_b=hB.selection())
+    assert rel(C.double().cpu().numpy(), ref) <= TOL

@@ -120,3 +120,18 @@ def test_fourier_backward_powerlaw_n4096_top1pct():
     a, b = S.powerlaw_pair(4096, seed=0)
     ea, eb = _backward_case(torch, amm, a, b, 41, 41, 0)
     assert ea <= TOL and eb <= TOL, (ea, eb)
+
+
+def test_fourier_bf16_operands():
+    """BF16 operands: the handle widens them to FP32 once; the product matches the oracle on the
+    BF16-rounded inputs at the FP32 tolerance."""
+    torch, amm = torch_cuda()
+    n, k = 256, 9
+    a, b = S.general_times_toeplitz(n, seed=11)
+    A = torch.from_numpy(a.astype(np.float32)).cuda().bfloat16()
+    B = torch.from_numpy(b.astype(np.float32)).cuda().bfloat16()
+    hA = amm.decompose(A, "fourier", k, "left")
+    hB = amm.decompose(B, "fourier", k, "right")
+    C = amm.approx_matmul(hA, hB)
+    ref = O.fourier_matmul(as64(A), as64(B), k, forced_a=hA.selection(), forced_b=hB.selection())
+    assert rel(C.double().cpu().numpy(), ref) <= TOL
