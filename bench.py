@@ -201,14 +201,38 @@ def run_amm(args, rank, world, local_rank):
     B2 = torch.empty_like(B)
 
     n_bwd = sum(1 for _, _, bwd in PRODUCTS if bwd)
-    grads_h = [torch.empty((N, N), dtype=torch.float32).pin_memory() for _ in range(2 * n_bwd)]
+    grads_h = [[torch.empty((N, N), dtype=torch.float32).pin_memory() for _ in range(2)] if bwd else []
+               for _, _, bwd in PRODUCTS]
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in PRODUCTS]
 
     def e2e_step():
+        # each product's result and gradients go back to the host on a copy stream while the next
+        # product computes; the step ends when every result is on the host
+        cur = torch.cuda.current_stream(dev)
         A2.copy_(a_h, non_blocking=True)
         B2.copy_(b_h, non_blocking=True)
-        grads = step(A2, B2, outs)
-        for o, oh in zip(outs + grads, outs_h + grads_h):
-            oh.copy_(o, non_blocking=True)
+        for i, (method, k, bwd) in enumerate(PRODUCTS):
+            cur.wait_event(copied[i])  # the previous step's copy of outs[i] has finished
+            sa, sb = PH[k] if method == "svd" else (None, None)
+            hA = amm.decompose(A2, method, k, "left", sketch=sa)
+            hB = amm.decompose(B2, method, k, "right", sketch=sb)
+            amm.approx_matmul(hA, hB, out=outs[i])
+            res = [outs[i]]
+            if bwd:
+                res += list(amm.approx_matmul_backward(hA, hB, G))
+            ready = torch.cuda.Event()
+            ready.record(cur)
+            copy_stream.wait_event(ready)
+            with torch.cuda.stream(copy_stream):
+                for t, th in zip(res, [outs_h[i]] + grads_h[i]):
+                    th.copy_(t, non_blocking=True)
+            for t in res[1:]:
+                t.record_stream(copy_stream)
+            copied[i].record(copy_stream)
+            hA.close()
+            hB.close()
+        cur.wait_stream(copy_stream)
 
     for _ in range(max(1, args.warmup // 2)):
         e2e_step()

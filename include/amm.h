@@ -173,6 +173,21 @@ amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const 
 amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info);
 
 /*
+ * Smallest k whose truncation meets a tolerance on the operand: ||dA||_F <= tol ||A||_F, with the
+ * components kept in the order of amm_decompose (key desc, index asc).  The truncation error of
+ * the top-k set follows from the keys alone because the components are orthogonal (circulant:
+ * Thm 2.1 / Section 2.3, ||dA||^2 = ||A||^2 - n sum_{t in S} ||R_A[t]||^2; cycles: disjoint
+ * supports).  Section 2.5 uses such truncation errors as the a-priori handle on the error of the
+ * product (more components when the estimate is not satisfactory).
+ *   A        DEVICE, n x n, lda, FP32 or BF16, n a power of two in [16, 8192]
+ *   method   AMM_CIRCULANT or AMM_SPARSE_CYCLE (else AMM_ERR_NOT_IMPLEMENTED)
+ *   tol      >= 0; *k_out in [1, n] (host)
+ * Computes the spectrum / cycle norms into temporary device memory; synchronises `stream`.
+ */
+amm_status_t amm_choose_k(const void* A, int64_t rows, int64_t cols, int64_t lda, amm_dtype_t dtype,
+                          amm_method_t method, double tol, void* stream, int64_t* k_out);
+
+/*
  * Posterior estimate of the relative error ||dA dB||_F / ||A B||_F of a computed product
  * (Corollary 3.7, Section 3): ||dA||_F ||dB||_F / (sqrt(n) ||C||_F), n the inner dimension,
  * with ||dA||_F, ||dB||_F the truncation errors of the two handles (amm_handle_info) and C the

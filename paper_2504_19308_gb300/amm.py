@@ -54,6 +54,8 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_void_p)]),
     "amm_approx_matmul": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.c_void_p]),
+    "amm_choose_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "amm_error_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "amm_approx_matmul_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -212,6 +214,21 @@ def approx_matmul(hA: Handle, hB: Handle, out: Optional[torch.Tensor] = None) ->
     _check(load_library().amm_approx_matmul(hA.ptr, hB.ptr, out.data_ptr(), out.stride(0),
                                             _stream_ptr(out.device)), "amm_approx_matmul")
     return out
+
+
+def choose_k(A: torch.Tensor, method: str, tol: float) -> int:
+    """amm_choose_k: smallest k with ||dA||_F <= tol ||A||_F (circulant or cycle truncation)."""
+    _require_cuda(A, "A")
+    k = ctypes.c_int64(0)
+    _check(load_library().amm_choose_k(A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), DTYPES[A.dtype],
+                                       METHODS[method], float(tol), _stream_ptr(A.device), ctypes.byref(k)),
+           "amm_choose_k")
+    return k.value
+
+
+def decompose_to_tolerance(A: torch.Tensor, method: str, tol: float, role: str = "left", **kw) -> Handle:
+    """Decompose A with the smallest k whose truncation error is within tol (relative Frobenius)."""
+    return decompose(A, method, choose_k(A, method, tol), role, **kw)
 
 
 def error_estimate(hA: Handle, hB: Handle, C: torch.Tensor) -> float:

@@ -569,6 +569,83 @@ extern "C" amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info) {
   return AMM_OK;
 }
 
+extern "C" amm_status_t amm_choose_k(const void* A, int64_t rows, int64_t cols, int64_t lda, amm_dtype_t dtype,
+                                     amm_method_t method, double tol, void* stream, int64_t* k_out) {
+  if (!A || !k_out) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: NULL argument");
+  if (rows != cols || !pow2((int)rows) || rows < 16 || rows > 8192)
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "amm_choose_k: A must be square with n a power of two in [16, 8192]");
+  if (lda < cols) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: lda < cols");
+  if (!(tol >= 0.0)) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: tol must be >= 0");
+  if (dtype != AMM_F32 && dtype != AMM_BF16) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: bad dtype");
+  if (method != AMM_CIRCULANT && method != AMM_SPARSE_CYCLE)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "amm_choose_k: built for AMM_CIRCULANT and AMM_SPARSE_CYCLE");
+  const int n = (int)rows;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<void*> tmp;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(&q, bytes, st);
+    if (q) tmp.push_back(q);
+    return q;
+  };
+  const bool circ = method == AMM_CIRCULANT;
+  const int kh = circ ? n / 2 + 1 : n;
+  int nparts = 0;
+  double* key2 = (double*)al(sizeof(double) * kh);
+  if (circ) {
+    const float2* tw = nullptr;
+    if (e == cudaSuccess) e = twiddles(n, st, &tw);
+    nparts = n / cd_cols_per_cta(n);
+    float2* R = (float2*)al(sizeof(float2) * (size_t)kh * n);
+    float* kpart = (float*)al(sizeof(float) * (size_t)kh * nparts);
+    if (e == cudaSuccess) e = cd_spectrum(n, A, lda, dtype == AMM_BF16, tw, R, kpart, st);
+    if (e == cudaSuccess) e = cd_keys(kh, kpart, nparts, key2, st);
+  } else {
+    const float* Af = (const float*)A;
+    int64_t ldf = lda;
+    if (dtype == AMM_BF16) {
+      float* y = (float*)al(sizeof(float) * (size_t)n * n);
+      if (e == cudaSuccess) e = widen_bf16(A, n, n, lda, y, n, st);
+      Af = y;
+      ldf = n;
+    }
+    const int rp = cyc_rows_per_part(n);
+    nparts = (n + rp - 1) / rp;
+    float* kpart = (float*)al(sizeof(float) * (size_t)nparts * n);
+    if (e == cudaSuccess) e = cyc_keys(n, Af, ldf, kpart, st);
+    if (e == cudaSuccess) e = cd_keys(n, kpart, nparts, key2, st);
+  }
+  std::vector<double> h(kh);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), key2, sizeof(double) * kh, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (void* q : tmp) dev_free(q, st);
+  if (e != cudaSuccess) return cuda_fail(e, "amm_choose_k");
+  // squared key of every component (conjugate partners share theirs); ||A||^2 and the truncation
+  // error of the top-k set follow from the orthogonality of the components (Section 2.3)
+  std::vector<std::pair<double, int>> keys(n);
+  double total = 0.0;
+  for (int t = 0; t < n; ++t) {
+    const double v = circ ? h[std::min(t, n - t) % (n / 2 + 1)] : h[t];
+    keys[t] = {v, t};
+    total += v;
+  }
+  std::sort(keys.begin(), keys.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first > y.first || (x.first == y.first && x.second < y.second);
+  });
+  double kept = 0.0;
+  int64_t k = n;
+  for (int i = 0; i < n; ++i) {
+    if (total - kept <= tol * tol * total) {
+      k = i;
+      break;
+    }
+    kept += keys[i].first;
+  }
+  *k_out = std::max<int64_t>(k, 1);
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_error_estimate(amm_handle_t hA, amm_handle_t hB, const float* C, int64_t ldc,
                                            void* stream, double* estimate) {
   if (!estimate) return fail(AMM_ERR_INVALID_ARG, "amm_error_estimate: estimate is NULL");

@@ -694,6 +694,12 @@ cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const floa
   AMM_DISPATCH_N(n, return CdOps<NN>::spectrum(A, lda, bf16, tw, R, kpart, st));
 }
 
+cudaError_t cd_keys(int kh, const float* kpart, int nparts, double* key2, cudaStream_t st) {
+  AMM_TRACE("cd_keyreduce", st);
+  cd_keyreduce_kernel<<<(kh + 31) / 32, dim3(32, 32), 0, st>>>(kpart, nparts, kh, key2);
+  return cudaGetLastError();
+}
+
 cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_t* forced, const SelectOut& o,
                       cudaStream_t st, bool mirror, bool pair_closed) {
   auto bytes = [](int nn) {

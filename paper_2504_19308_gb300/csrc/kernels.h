@@ -24,6 +24,8 @@ int cd_cols_per_cta(int n);
 cudaError_t cd_twiddles(float2* tw, int n, cudaStream_t st);
 cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const float2* tw, float2* R, float* kpart,
                         cudaStream_t st);
+// key2[t] = sum over the nparts partial rows of kpart[c][t], t < kh (fixed order, FP64)
+cudaError_t cd_keys(int kh, const float* kpart, int nparts, double* key2, cudaStream_t st);
 // pair_closed (circulant only): the selection is closed under t -> n - t (S u S-bar), so M is real
 cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_t* forced, const SelectOut& o,
                       cudaStream_t st, bool mirror = true, bool pair_closed = false);

@@ -37,3 +37,28 @@ def test_error_estimate_matches_oracle(method, k):
     assert abs(est - ref) <= 1e-3 * ref, (est, ref)
     actual = np.linalg.norm(ta.resid @ tb.resid) / np.linalg.norm(a64 @ b64)
     assert 0.5 < est / actual < 2.0, (est, actual)
+
+
+@pytest.mark.parametrize("method", ["circulant", "cycle"])
+@pytest.mark.parametrize("tol", [0.3, 0.1, 0.03])
+def test_choose_k_is_minimal(method, tol):
+    """amm_choose_k returns the smallest k whose truncation error (from the oracle's keys) is within
+    tol; near-ties of the error curve at the tolerance are allowed either way by 1e-4."""
+    torch, amm = torch_cuda()
+    n = 256
+    g = S.rng(13, 0)
+    a = S.toeplitz_uniform(n, g) + 0.05 * g.standard_normal((n, n))
+    A = dev32(torch, a)
+    k = amm.choose_k(A, method, tol)
+    a64 = as64(A)
+    if method == "circulant":
+        keys2 = O.component_keys(O.circulant_spectrum(a64)) ** 2 * n
+    else:
+        keys2 = O.cycle_keys(a64) ** 2
+    order = O.top_k(np.sqrt(keys2), n)
+    total = np.sum(a64 ** 2)
+    resid = lambda kk: (total - np.sum(keys2[order[:kk]])) / total
+    assert resid(k) <= tol ** 2 * (1 + 1e-4)
+    assert k == 1 or resid(k - 1) >= tol ** 2 * (1 - 1e-4)
+    h = amm.decompose_to_tolerance(A, method, tol)
+    assert h.k == k
