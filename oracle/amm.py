@@ -24,6 +24,8 @@ Readings taken where the paper is silent or inconsistent (each also listed in DE
   R9  Cycle sparsifier key: ||diag Lambda_j||_2 (by analogy with Alg. 3 Step 2).
   R10 Backward: selections, Q factors and masks are frozen; the gradient is that of the
       resulting bilinear map.
+  R11 Rectangular circulant operands: b x b blocks, ragged edge zero-padded, top-k per block,
+      Eq. (2.3) on the padded operands, padded rows / columns of the product dropped.
 """
 from __future__ import annotations
 
@@ -590,6 +592,100 @@ def mixed_product(ta: Truncation, tb: Truncation) -> np.ndarray:
     two operands may differ).  Eq. (2.3) with each side's space-domain truncation; for the
     Fourier sparsifier that is A_s = A~_a W (left) or B_s = W^* B~_a (right)."""
     return first_order(ta, tb).real
+
+
+# ---------------------------------------------------------------------------
+# Rectangular operands in square circulant blocks (Section 2.3: the cycle decomposition is
+# defined for square matrices and a rectangular one is handled in square blocks).  Reading R11:
+# both dimensions are cut into b x b blocks, the ragged edge is padded with zeros, every block
+# keeps its own top-k components, Eq. (2.3) is evaluated on the padded operands and the padded
+# rows / columns of the product are dropped.
+# ---------------------------------------------------------------------------
+
+
+def pad_to(a: np.ndarray, rows: int, cols: int) -> np.ndarray:
+    """a in the top-left corner of a zero rows x cols matrix."""
+    out = np.zeros((rows, cols), dtype=np.result_type(a, np.float64))
+    out[: a.shape[0], : a.shape[1]] = a
+    return out
+
+
+def ceil_to(x: int, b: int) -> int:
+    return -(-x // b) * b
+
+
+def truncate_circulant_blocked(a: np.ndarray, bs: int, k: int, selections=None) -> Truncation:
+    """Blockwise circulant truncation (reading R11).  Block (I, J) is rows I*bs.. and columns
+    J*bs.. of the zero-padded operand; `selections[I * nbc + J]` replaces its top-k selection.
+    The Truncation holds the PADDED operand and truncation; .shape0 is the original shape and
+    .blocks[I][J] the per-block truncations."""
+    ap = pad_to(a, ceil_to(a.shape[0], bs), ceil_to(a.shape[1], bs))
+    nbr, nbc = ap.shape[0] // bs, ap.shape[1] // bs
+    approx = np.zeros(ap.shape, dtype=np.complex128)
+    blocks, sels = [], []
+    for i in range(nbr):
+        row = []
+        for j in range(nbc):
+            sel = None if selections is None else selections[i * nbc + j]
+            t = truncate_circulant(ap[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs], k, sel)
+            approx[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs] = t.approx
+            row.append(t)
+            sels.append(t.sel)
+        blocks.append(row)
+    return Truncation("circulant_blocked", ap, approx, np.array(sels), blocks=blocks, bs=bs, shape0=a.shape)
+
+
+def padded(t: Truncation, rows: int, cols: int) -> Truncation:
+    """The same truncation seen on the operand padded with zeros to rows x cols: the padding is
+    zero in A, in A~ and in dA (true for every method: a zero row or column of A stays zero in
+    Q Q^T A, A P, and in the sparsifier and cycle truncations of the padded square)."""
+    out = Truncation(t.method, pad_to(t.a, rows, cols), pad_to(t.approx, rows, cols), t.sel)
+    out.shape0 = getattr(t, "shape0", t.a.shape)
+    return out
+
+
+def blocked_first_order(ta: Truncation, tb: Truncation) -> np.ndarray:
+    """Re M of Eq. (2.3) where either operand may be a blockwise circulant truncation (reading
+    R11): both are brought to the common padded shape, M is formed there and cropped to m x p."""
+    m0 = getattr(ta, "shape0", ta.a.shape)[0]
+    p0 = getattr(tb, "shape0", tb.a.shape)[1]
+    rows, inner, cols = ta.a.shape[0], max(ta.a.shape[1], tb.a.shape[0]), tb.a.shape[1]
+    pa, pb = padded(ta, rows, inner), padded(tb, inner, cols)
+    return first_order(pa, pb)[:m0, :p0].real
+
+
+def project_circulant_blocked(z: np.ndarray, t: Truncation, adjoint: bool = False) -> np.ndarray:
+    """Blockwise projection onto the selected components of every block (the adjoint keeps the
+    mirrored components n - t of each block, as for one square block)."""
+    bs = t.bs
+    out = np.zeros(z.shape, dtype=np.complex128)
+    for i, row in enumerate(t.blocks):
+        for j, tt in enumerate(row):
+            sel = mirror(tt.sel, bs) if adjoint else tt.sel
+            out[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs] = project_circulant(
+                z[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs], sel)
+    return out
+
+
+def cd_backward_blocked(ta: Truncation, tb: Truncation, g: np.ndarray):
+    """Gradients of <G, Re M> for the blockwise circulant product with the selections frozen:
+    the formulas of cd_backward on the padded operands with the blockwise adjoint projectors;
+    G is padded with zeros (the padded part of M is dropped) and the gradients are cropped."""
+    m0, n0 = ta.shape0
+    p0 = tb.shape0[1]
+    gp = pad_to(g, ta.a.shape[0], tb.a.shape[1])
+    da = gp @ tb.approx.T + project_circulant_blocked(gp @ tb.resid.T, ta, adjoint=True)
+    db = ta.approx.T @ gp + project_circulant_blocked(ta.resid.T @ gp, tb, adjoint=True)
+    return da[:m0, :n0].real, db[:n0, :p0].real
+
+
+def frozen_product_blocked(ta: Truncation, tb: Truncation, a, b) -> np.ndarray:
+    """The blockwise circulant map with frozen selections evaluated at new operands (a, b)."""
+    ap = pad_to(a, *ta.a.shape)
+    bp = pad_to(b, *tb.a.shape)
+    pa = project_circulant_blocked(ap.astype(np.complex128), ta)
+    pb = project_circulant_blocked(bp.astype(np.complex128), tb)
+    return (pa @ bp + (ap - pa) @ pb)[: ta.shape0[0], : tb.shape0[1]].real
 
 
 def backward(method: str, ta, tb, g):

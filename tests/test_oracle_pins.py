@@ -436,6 +436,108 @@ def test_backward_finite_differences_n64(method):
         assert fd_b == pytest.approx(np.sum(db * eb), rel=1e-9)
 
 
+# --------------------------------------------------------------------------- square blocks (R11)
+
+_RAGGED = [(10, 13, 7, 4), (8, 8, 12, 4), (5, 16, 9, 8), (16, 16, 16, 16)]
+
+
+@pytest.mark.parametrize("m,n,p,bs", _RAGGED)
+def test_blocked_untruncated_is_exact(m, n, p, bs):
+    """k = bs keeps every component of every padded block: the cropped product is AB exactly."""
+    g = S.rng(m * n + p, 50)
+    a, b = g.standard_normal((m, n)), g.standard_normal((n, p))
+    ta = O.truncate_circulant_blocked(a, bs, bs)
+    tb = O.truncate_circulant_blocked(b, bs, bs)
+    assert np.abs(O.blocked_first_order(ta, tb) - O.exact_product_loops(a, b)).max() < 1e-12 * np.abs(a @ b).max()
+
+
+@pytest.mark.parametrize("m,n,p,bs", _RAGGED)
+@pytest.mark.parametrize("k", [1, 3])
+def test_blocked_first_order_identity(m, n, p, bs, k):
+    """Eq. (2.1)-(2.3) on the padded operands: AB - Re M = Re(dA dB) cropped; the padding is zero
+    in A and B but not in their truncations, so a product formed without it fails this."""
+    g = S.rng(m * n + p + k, 51)
+    a, b = g.standard_normal((m, n)) + 0.5, g.uniform(0, 1, (n, p))
+    ta = O.truncate_circulant_blocked(a, bs, k)
+    tb = O.truncate_circulant_blocked(b, bs, k)
+    second = (ta.resid @ tb.resid)[:m, :p].real
+    assert np.abs((a @ b - O.blocked_first_order(ta, tb)) - second).max() < 1e-12 * np.abs(a @ b).max()
+
+
+def test_blocked_one_shift_per_block_is_exact():
+    """Block (I, J) = Re(circulant(c_IJ) D^(t_IJ)) holds only the conjugate pair t_IJ, bs - t_IJ of
+    that block (Thm 2.1): k = 2 selects that pair in every block, the truncation is exact and
+    M = AB.  A block grid read in the wrong order picks the wrong pairs."""
+    bs, nbr, nbc = 8, 2, 3
+    g = S.rng(52, 0)
+    shifts = [[1 + (i + 2 * j) % 3 for j in range(nbc)] for i in range(nbr)]
+    a = np.block([[(O.circulant(g.standard_normal(bs)) @ O.diag_D(bs, shifts[i][j])).real for j in range(nbc)]
+                  for i in range(nbr)])
+    ta = O.truncate_circulant_blocked(a, bs, 2)
+    assert [sorted(int(v) for v in t) for t in ta.sel] == [[shifts[i][j], bs - shifts[i][j]] for i in range(nbr)
+                                                           for j in range(nbc)]
+    assert np.abs(ta.resid).max() < 1e-12 * np.abs(a).max()
+    b = g.standard_normal((nbc * bs, 5))
+    tb = O.truncate_circulant_blocked(b, bs, 2)
+    assert np.abs(O.blocked_first_order(ta, tb) - a @ b).max() < 1e-12 * np.abs(a @ b).max()
+
+
+def test_blocked_truncation_error_is_parseval_per_block():
+    """Section 2.3 per block: ||dA||^2 = sum over blocks of ||A_IJ||^2 - bs sum_{t in S_IJ} T_IJ[t]^2."""
+    bs, k = 8, 3
+    a = S.rng(53, 0).standard_normal((13, 21))
+    ta = O.truncate_circulant_blocked(a, bs, k)
+    total = 0.0
+    for row in ta.blocks:
+        for t in row:
+            total += np.sum(t.a ** 2) - bs * np.sum(t.keys[t.sel] ** 2)
+    assert abs(np.linalg.norm(ta.resid) ** 2 - total) < 1e-10 * np.sum(a * a)
+
+
+def test_blocked_single_block_is_the_square_decomposition():
+    """bs = n on a square operand: one block, the truncation of Alg. 3 itself."""
+    n, k = 16, 5
+    a = _rand(n, 54)
+    tb, ts = O.truncate_circulant_blocked(a, n, k), O.truncate_circulant(a, k)
+    assert np.array_equal(tb.sel[0], ts.sel) and np.abs(tb.approx - ts.approx).max() < 1e-14
+
+
+@pytest.mark.parametrize("mb", ["svd", "fourier", "cycle"])
+def test_blocked_mixed_identity(mb):
+    """A blockwise circulant left operand times another method's right operand: AB - Re M =
+    Re(dA dB) cropped, with the other operand zero-padded along the inner dimension."""
+    m, n, p, bs, k = 11, 16, 16, 8, 3
+    g = S.rng(55, 0)
+    a, b = g.standard_normal((m, n)), g.uniform(0, 1, (n, p))
+    ta = O.truncate_circulant_blocked(a, bs, k)
+    tb = _trunc_side(mb, b, k, "right", 55)
+    second = (ta.resid[:, :n] @ tb.resid)[:m, :].real
+    assert np.abs((a @ b - O.blocked_first_order(ta, tb)) - second).max() < 1e-12 * np.abs(a @ b).max()
+
+
+def test_blocked_backward_matches_bruteforce():
+    """Reading R10 + R11: the blockwise gradients equal <G, M(E_ij)> over every basis matrix."""
+    m, n, p, bs, k = 5, 7, 6, 4, 2
+    g = S.rng(56, 0)
+    a, b, gr = g.standard_normal((m, n)), g.standard_normal((n, p)), g.standard_normal((m, p))
+    ta, tb = O.truncate_circulant_blocked(a, bs, k), O.truncate_circulant_blocked(b, bs, k)
+    da, db = O.cd_backward_blocked(ta, tb, gr)
+    f = lambda x, y: np.sum(gr * O.frozen_product_blocked(ta, tb, x, y))
+    bda = np.zeros_like(a)
+    bdb = np.zeros_like(b)
+    for i, j in itertools.product(range(m), range(n)):
+        e = np.zeros_like(a)
+        e[i, j] = 1.0
+        bda[i, j] = f(e, b) - f(np.zeros_like(a), b)
+    for i, j in itertools.product(range(n), range(p)):
+        e = np.zeros_like(b)
+        e[i, j] = 1.0
+        bdb[i, j] = f(a, e) - f(a, np.zeros_like(b))
+    assert np.abs(da - bda).max() < 1e-12 and np.abs(db - bdb).max() < 1e-12
+    # the frozen map at the operands themselves is the product
+    assert np.abs(f(a, b) - np.sum(gr * O.blocked_first_order(ta, tb))) < 1e-10
+
+
 # --------------------------------------------------------------------------- printed tables
 
 def _table_rows():
