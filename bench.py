@@ -256,9 +256,11 @@ def run_amm(args, rank, world, local_rank):
     roof = roofline(kernels, clocks)
     bf16 = bf16_form(args, A, B, G, PH, ms / args.steps, dist)
     batched = batched_form(args, dev, dist)
+    llm = llm_form(args, dev, dist)
     return {
         "value": value, "ms_per_step": ms / args.steps, "errs": errs, "kernels": kernels,
         "launches": launches, "clocks": clocks, "roofline": roof, "bf16": bf16, "batched": batched,
+        "llm": llm,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N * N * 4,
                 "d2h_bytes_per_step": (len(PRODUCTS) + 2 * n_bwd) * N * N * 4, "ms_per_step": e2e_ms / args.steps},
     }
@@ -370,6 +372,50 @@ def batched_form(args, dev, dist, count=256):
             "methods in rotation, forward" % (min(sizes), max(sizes)),
             "eager_ms": eager_ms, "graph_ms": graph_ms, "speedup": eager_ms / graph_ms,
             "value": fl / (graph_ms * 1e-3) / 1e12, "unit": UNIT}
+
+
+def llm_form(args, dev, dist):
+    """The LLM-shaped product X W: activations X (2048 x 4096, N(0,1)) by rSVD k = 256 and the weight
+    W (4096 x 11008, N(0, 0.02^2) with 0.1% heavy-tailed entries) in 4096-square circulant blocks
+    (zero-padded to 4096 x 12288), k = 128 per block; FP32 arithmetic on BF16-rounded values,
+    forward.  Timed with the weight decomposed once (a trained weight is decomposed offline) and
+    with both decompositions inside every step."""
+    import torch
+    import paper_2504_19308_gb300 as amm
+    x, w = synth.llm_shaped(seed=0)
+    X = torch.from_numpy(x.astype(np.float32)).to(dev).bfloat16().float()
+    W = torch.from_numpy(w.astype(np.float32)).to(dev).bfloat16().float()
+    del x, w
+    k, kc, bs = 256, 128, 4096
+    phi = torch.from_numpy(synth.sketch(4096, k, 0, 0).astype(np.float32)).to(dev)
+    C = torch.empty((X.shape[0], W.shape[1]), device=dev)
+    hW = amm.decompose(W, "circulant", kc, "right", block=bs)
+
+    def fwd():
+        hX = amm.decompose(X, "svd", k, "left", sketch=phi)
+        amm.approx_matmul(hX, hW, out=C)
+        hX.close()
+
+    def fwd_both():
+        hX = amm.decompose(X, "svd", k, "left", sketch=phi)
+        hW2 = amm.decompose(W, "circulant", kc, "right", block=bs)
+        amm.approx_matmul(hX, hW2, out=C)
+        hX.close()
+        hW2.close()
+
+    fwd()
+    exact = X.double() @ W.double()
+    err = float(torch.linalg.norm(C.double() - exact) / torch.linalg.norm(exact))
+    del exact
+    ms = _device_ms(fwd, max(1, args.steps // 2), args.warmup, dist)
+    ms_both = _device_ms(fwd_both, max(1, args.steps // 2), args.warmup, dist)
+    hW.close()
+    fl = 2.0 * X.shape[0] * X.shape[1] * W.shape[1]
+    return {"workload": "X 2048x4096 by rSVD k=256 times W 4096x11008 in 4096-square circulant blocks, k=128 "
+                        "per block, forward, FP32 on BF16-rounded values",
+            "ms_weight_offline": ms, "value": fl / (ms * 1e-3) / 1e12, "unit": UNIT,
+            "ms_both_decompositions": ms_both, "value_both": fl / (ms_both * 1e-3) / 1e12,
+            "approx_rel_err_vs_exact": err}
 
 
 # dram bytes per launch from the ncu capture summarised in profiles/ (None = not captured for
@@ -490,6 +536,7 @@ def main():
         cfg["kernels_ms"] = {k: round(v[1] / args.steps, 4) for k, v in r["kernels"].items()}
         cfg["bf16_form"] = r["bf16"]
         cfg["batched_form"] = r["batched"]
+        cfg["llm_blocked_form"] = r["llm"]
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,

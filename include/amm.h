@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define AMM_VERSION 2
+#define AMM_VERSION 3
 
 typedef enum {
   AMM_OK = 0,
@@ -81,6 +81,17 @@ typedef struct amm_opts {
                                      M = Re M.  amm_handle_get_selection still returns the k
                                      ranked components; the truncation error of amm_handle_info
                                      is that of the closed set.  Default 0.                   */
+  int32_t block;                  /* AMM_CIRCULANT: square block size b (a power of two in
+                                     [16, 8192]) for a rectangular operand (Section 2.3: the
+                                     cycle decomposition is defined for square matrices, larger
+                                     or rectangular ones are taken in square blocks).  Both
+                                     dimensions are cut into b x b blocks; a ragged edge is
+                                     padded with zeros (a handle-owned copy); each block keeps
+                                     its own top-k components; the product is Eq. (2.3) on the
+                                     padded operands, padded rows / columns dropped.  forced_
+                                     selection then holds k indices per block, blocks row-major,
+                                     and amm_handle_get_selection returns them in that order.
+                                     0 (default): one square decomposition.                   */
 } amm_opts_t;
 
 typedef struct amm_info {
@@ -115,10 +126,11 @@ amm_status_t amm_opts_init(amm_opts_t* opts);
  *           backward read A again), so A must stay allocated and unchanged until
  *           amm_handle_destroy().  (BF16 operands of AMM_SPARSE_FOURIER / AMM_SPARSE_CYCLE are
  *           read once: the handle keeps its own FP32 copy.)
- *   method  AMM_CIRCULANT and AMM_SPARSE_CYCLE need rows == cols (square, Section 2.3:
- *           rectangular matrices are handled blockwise by the caller); the FFT length n
- *           must be a power of two in [16, 8192].
- *   k       number of kept components (1 <= k <= min(rows, cols) for AMM_SVD; <= n else).
+ *   method  AMM_CIRCULANT and AMM_SPARSE_CYCLE need rows == cols (square, Section 2.3), except
+ *           AMM_CIRCULANT with opts->block = b > 0, which takes any rows x cols in b x b blocks;
+ *           the FFT length (n, or b) must be a power of two in [16, 8192].
+ *   k       number of kept components (1 <= k <= min(rows, cols) for AMM_SVD; <= b per block
+ *           for blocked AMM_CIRCULANT; <= n else).
  *   opts    may be NULL (defaults).
  *   stream  cudaStream_t for all work and allocations of this handle.
  *   out     receives the handle; unchanged on error.
@@ -141,7 +153,11 @@ amm_status_t amm_decompose(const void* A, int64_t rows, int64_t cols, int64_t ld
  *           B is n x p (inner dimensions must match).  The two methods may differ (the
  *           paper lets each operand use its own decomposition): C is then evaluated as
  *           Re(A~) B + (A - Re A~) Re(B~) + Im(A~) Im(B~), each term one operand's truncation
- *           applied to a dense matrix.  Mixed products need FP32 operands.
+ *           applied to a dense matrix.  Mixed products need FP32 operands.  Blocked circulant
+ *           operands (opts.block) need the same block size on both sides when both are
+ *           circulant; the product is then the sum over inner blocks J of the square first-
+ *           order products of blocks (I, J) and (J, L), and a non-circulant partner is padded
+ *           with zeros along the shared dimension.
  *   C       device pointer, m x p FP32 row-major, leading dimension ldc >= p.  Overwritten.
  *   stream  stream of the call; must be ordered after the decompositions' streams.
  */

@@ -33,7 +33,8 @@ class AmmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("role", ctypes.c_int32), ("compute", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("sketch", ctypes.c_void_p), ("store_spectra", ctypes.c_int32),
-                ("forced_selection", ctypes.POINTER(ctypes.c_int32)), ("pair_closed", ctypes.c_int32)]
+                ("forced_selection", ctypes.POINTER(ctypes.c_int32)), ("pair_closed", ctypes.c_int32),
+                ("block", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -122,13 +123,21 @@ def _require_cuda(t: torch.Tensor, name: str):
 class Handle:
     """Truncated decomposition of one operand; keeps the operand alive (the library borrows it)."""
 
-    def __init__(self, ptr: int, source: torch.Tensor, method: str, role: str, k: int, extras=()):
+    def __init__(self, ptr: int, source: torch.Tensor, method: str, role: str, k: int, extras=(), block: int = 0):
         self.ptr = ctypes.c_void_p(ptr)
         self.source = source
         self.method = method
         self.role = role
         self.k = k
+        self.block = block
         self._extras = extras  # tensors that must outlive the launch (sketch)
+
+    @property
+    def blocks(self):
+        """(block rows, block columns) of a blocked circulant handle; (1, 1) otherwise."""
+        if not self.block:
+            return 1, 1
+        return -(-self.shape[0] // self.block), -(-self.shape[1] // self.block)
 
     @property
     def shape(self):
@@ -140,17 +149,20 @@ class Handle:
         return {f: getattr(info, f) for f, _ in Info._fields_}
 
     def selection(self) -> np.ndarray:
-        """Selected components (k,), or per-row / per-column kept frequencies (rows, k) for 'fourier'."""
+        """Selected components (k,), per-block components (blocks, k) of a blocked circulant handle
+        (blocks row-major), or per-row / per-column kept frequencies (rows, k) for 'fourier'."""
         rows = 1
         if self.method == "fourier":
             rows = self.shape[0] if self.role == "left" else self.shape[1]
+        elif self.block:
+            rows = self.blocks[0] * self.blocks[1]
         cap = self.k * rows
         buf = (ctypes.c_int32 * cap)()
         cnt = ctypes.c_int64(0)
         _check(load_library().amm_handle_get_selection(self.ptr, buf, cap, ctypes.byref(cnt)),
                "amm_handle_get_selection")
         out = np.frombuffer(buf, dtype=np.int32, count=cnt.value).copy()
-        return out.reshape(rows, self.k) if self.method == "fourier" else out
+        return out.reshape(rows, self.k) if self.method == "fourier" or self.block else out
 
     def sketch(self) -> np.ndarray:
         n = self.source.shape[1]
@@ -173,11 +185,14 @@ class Handle:
 
 
 def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: Optional[torch.Tensor] = None,
-              seed: int = 0, forced_selection=None, compute: str = "f32", pair_closed: bool = False) -> Handle:
+              seed: int = 0, forced_selection=None, compute: str = "f32", pair_closed: bool = False,
+              block: int = 0) -> Handle:
     """amm_decompose: truncated decomposition of A (method 'circulant' | 'svd' | 'fourier' | 'cycle').
 
     compute: arithmetic of the SVD GEMMs, 'f32' (FP32-accurate) or 'bf16' (BF16 tensor cores).
     pair_closed: circulant selections closed under t -> n - t (a real truncation).
+    block: circulant operand of any shape in block x block squares (zero-padded edge, top-k per
+    block); forced_selection then holds k indices per block, blocks row-major.
     """
     lib = load_library()
     _require_cuda(A, "A")
@@ -189,6 +204,7 @@ def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: 
     opts.seed = seed
     opts.compute = {"f32": 0, "bf16": 1}[compute]
     opts.pair_closed = 1 if pair_closed else 0
+    opts.block = int(block)
     extras = []
     if sketch is not None:
         _require_cuda(sketch, "sketch")
@@ -197,12 +213,17 @@ def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: 
         extras.append(sketch)
     forced = None
     if forced_selection is not None:
-        forced = (ctypes.c_int32 * k)(*[int(v) for v in forced_selection])
+        flat = np.asarray(forced_selection, dtype=np.int64).reshape(-1)
+        nblk = (-(-A.shape[0] // block)) * (-(-A.shape[1] // block)) if block else 1
+        if flat.size != nblk * k:
+            raise ValueError("forced_selection needs %d entries (k per block), got %d" % (nblk * k, flat.size))
+        forced = (ctypes.c_int32 * flat.size)(*[int(v) for v in flat])
         opts.forced_selection = ctypes.cast(forced, ctypes.POINTER(ctypes.c_int32))
     out = ctypes.c_void_p(0)
     _check(lib.amm_decompose(A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), DTYPES[A.dtype], METHODS[method], k,
                              ctypes.byref(opts), _stream_ptr(A.device), ctypes.byref(out)), "amm_decompose")
-    return Handle(out.value, A, method, role, k, tuple(extras))
+    blocked = block and not (A.shape[0] == block and A.shape[1] == block)
+    return Handle(out.value, A, method, role, k, tuple(extras), int(block) if blocked else 0)
 
 
 def approx_matmul(hA: Handle, hB: Handle, out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -126,6 +126,11 @@ extern "C" amm_status_t amm_debug_fail_alloc_after(int32_t n) {
 static bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 
 void amm::Handle::release() {
+  for (amm_handle* b : blk.sub) {
+    b->release();
+    delete b;
+  }
+  blk.sub.clear();
   for (void* p : owned) dev_free(p, stream);
   owned.clear();
 }
@@ -136,7 +141,7 @@ cudaError_t amm::Handle::alloc(void** p, size_t bytes) {
   return e;
 }
 
-static amm_status_t decompose_circulant(Handle* h, const amm_opts_t* o) {
+amm_status_t amm::decompose_circulant(Handle* h, const amm_opts_t* o) {
   const int n = (int)h->rows;
   if (!pow2(n) || n < 16 || n > 8192)
     return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: n=%d must be a power of two in [16, 8192]", n);
@@ -319,7 +324,12 @@ extern "C" amm_status_t amm_decompose(const void* A, int64_t rows, int64_t cols,
                 sizeof(amm_opts_t));
   const int role = opts ? opts->role : AMM_LEFT;
   if (role != AMM_LEFT && role != AMM_RIGHT) return fail(AMM_ERR_INVALID_ARG, "amm_decompose: bad role %d", role);
-  const int64_t kmax = (method == AMM_SVD) ? std::min(rows, cols) : cols;
+  const int64_t block = opts ? opts->block : 0;
+  if (block < 0) return fail(AMM_ERR_INVALID_ARG, "amm_decompose: block=%lld < 0", (long long)block);
+  if (block > 0 && method != AMM_CIRCULANT)
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose: block is an option of AMM_CIRCULANT");
+  const bool blocked = block > 0 && !(rows == block && cols == block);
+  const int64_t kmax = (method == AMM_SVD) ? std::min(rows, cols) : blocked ? block : cols;
   if (k < 1 || k > kmax)
     return fail(AMM_ERR_INVALID_ARG, "amm_decompose: k=%lld outside [1, %lld]", (long long)k, (long long)kmax);
   Handle* h = new (std::nothrow) Handle();
@@ -336,9 +346,13 @@ extern "C" amm_status_t amm_decompose(const void* A, int64_t rows, int64_t cols,
   amm_status_t s;
   switch (method) {
     case AMM_CIRCULANT:
+      if (blocked) {
+        s = decompose_circulant_blocked(h, opts);
+        break;
+      }
       if (rows != cols) {
-        s = fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: matrix must be square (got %lldx%lld)", (long long)rows,
-                 (long long)cols);
+        s = fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: matrix must be square (got %lldx%lld; set opts.block)",
+                 (long long)rows, (long long)cols);
         break;
       }
       s = decompose_circulant(h, opts);
@@ -379,6 +393,22 @@ static amm_status_t check_pair(Handle* a, Handle* b) {
   return AMM_OK;
 }
 
+// Re M = A~_w dB_w  +  Y V  +  A B~_w for one square pair (Alg. 3 Steps 5-6 in the column /
+// row spectral form); acc = 1 adds the product to C.
+cudaError_t amm::cd_first_order(Handle* a, Handle* b, float* C, int64_t ldc, int acc, cudaStream_t st) {
+  const int n = (int)a->rows;
+  auto &ca = a->cd, &cb = b->cd;
+  cudaError_t e = cd_apply(n, false, cb.resid, n, false, n, ca.tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr,
+                           nullptr, C, ldc, acc, st);
+  if (e == cudaSuccess)
+    e = cd_apply(n, false, cb.imag, n, false, n, ca.tw, ca.so.dlist, ca.Ld, ca.so.counts + 1, ca.so.counts + 1,
+                 cb.so.counts + 1, C, ldc, 1, st);
+  if (e == cudaSuccess)
+    e = cd_apply(n, true, a->A, a->lda, a->dtype == AMM_BF16, n, ca.tw, cb.so.ulist, cb.Lw, cb.so.counts, nullptr,
+                 nullptr, C, ldc, 1, st);
+  return e;
+}
+
 extern "C" amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, float* C, int64_t ldc, void* stream) {
   Handle* a = hA;
   Handle* b = hB;
@@ -391,18 +421,8 @@ extern "C" amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, floa
   cudaError_t e;
   if (a->method != b->method) return mixed_matmul(a, b, C, ldc, st);
   if (a->method == AMM_CIRCULANT) {
-    const int n = (int)a->rows;
-    auto &ca = a->cd, &cb = b->cd;
-    // Re M = A~_w dB_w  +  Y V  +  A B~_w
-    if ((e = cd_apply(n, false, cb.resid, n, false, n, ca.tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr, nullptr, C,
-                      ldc, 0, st)) != cudaSuccess)
-      return cuda_fail(e, "cd_apply (column) launch");
-    if ((e = cd_apply(n, false, cb.imag, n, false, n, ca.tw, ca.so.dlist, ca.Ld, ca.so.counts + 1, ca.so.counts + 1,
-                      cb.so.counts + 1, C, ldc, 1, st)) != cudaSuccess)
-      return cuda_fail(e, "cd_apply (unpaired) launch");
-    if ((e = cd_apply(n, true, a->A, a->lda, a->dtype == AMM_BF16, n, ca.tw, cb.so.ulist, cb.Lw, cb.so.counts,
-                      nullptr, nullptr, C, ldc, 1, st)) != cudaSuccess)
-      return cuda_fail(e, "cd_apply (row) launch");
+    if (a->blk.b || b->blk.b) return blocked_matmul(a, b, C, ldc, st);
+    if ((e = cd_first_order(a, b, C, ldc, 0, st)) != cudaSuccess) return cuda_fail(e, "circulant product launch");
     return AMM_OK;
   }
   if (a->method == AMM_SVD) return svd_matmul(a, b, C, ldc, st);
@@ -423,8 +443,8 @@ extern "C" amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, floa
 }
 
 // Circulant backward (see cd_backward.cu for the formulas); every step is a kernel launch.
-static amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda,
-                                float* dB, int64_t lddb, cudaStream_t st) {
+amm_status_t amm::cd_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, int acc_a,
+                              float* dB, int64_t lddb, int acc_b, cudaStream_t st) {
   const int n = (int)a->rows;
   auto &ca = a->cd, &cb = b->cd;
   const float2* tw = ca.tw;
@@ -446,7 +466,8 @@ static amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ld
   if (e == cudaSuccess) e = (x)
   if (dA) {
     // G B~_w^T (rows of G, coefficient L^B_s(p)), then the projection terms of G dB^T
-    STEP(cd_apply(n, true, G, ldg, false, n, tw, cb.so.ulist, cb.Lw, cb.so.counts, nullptr, nullptr, dA, ldda, 0, st, 0));
+    STEP(cd_apply(n, true, G, ldg, false, n, tw, cb.so.ulist, cb.Lw, cb.so.counts, nullptr, nullptr, dA, ldda, acc_a,
+                  st, 0));
     STEP(bw_spectrum(n, false, G, ldg, tw, X1, st));
     STEP(bw_spectrum(n, false, cb.resid, n, tw, X2, st));
     STEP(cd_sddmm(n, X1, X2, ca.so.ulist, ca.so.counts, ca.cap, K, nullptr, nullptr, st));
@@ -460,7 +481,8 @@ static amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ld
   }
   if (dB) {
     // A~_w^T G (columns of G, coefficient L^A_t(t - p)), then the projection terms of dA^T G
-    STEP(cd_apply(n, false, G, ldg, false, n, tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr, nullptr, dB, lddb, 0, st, 1));
+    STEP(cd_apply(n, false, G, ldg, false, n, tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr, nullptr, dB, lddb, acc_b,
+                  st, 1));
     STEP(bw_spectrum(n, true, G, ldg, tw, X1, st));
     STEP(cd_residual(n, ca.R, tw, ca.so.wfull, 0, nullptr, T, st, n, 0));  // dA_w
     STEP(bw_spectrum(n, true, T, n, tw, X2, st));
@@ -492,7 +514,10 @@ extern "C" amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t
   if (a->method != b->method)
     return fail(AMM_ERR_NOT_IMPLEMENTED, "backward of a mixed-method product is not built");
   if (a->method == AMM_SVD) return svd_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
-  if (a->method == AMM_CIRCULANT) return cd_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
+  if (a->method == AMM_CIRCULANT) {
+    if (a->blk.b || b->blk.b) return blocked_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
+    return cd_backward(a, b, dC, lddc, dA, ldda, 0, dB, lddb, 0, (cudaStream_t)stream);
+  }
   if (a->method == AMM_SPARSE_CYCLE) {
     cudaError_t e = cyc_backward((int)a->rows, (const float*)a->A, a->lda, (const float*)b->A, b->lda, a->cy.so.sel,
                                  (int)a->k, a->cy.cyc, a->cy.insel, b->cy.so.sel, (int)b->k, b->cy.cyc, b->cy.insel,
@@ -536,6 +561,7 @@ extern "C" amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info) {
   info->rows = h->rows;
   info->cols = h->cols;
   info->k = h->k;
+  if (h->blk.b) return blocked_info(h, info);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "amm_handle_info: stream");
   if (h->method == AMM_CIRCULANT || h->method == AMM_SPARSE_CYCLE) {
@@ -684,6 +710,7 @@ extern "C" amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_i
   }
   if (h->method != AMM_CIRCULANT && h->method != AMM_SPARSE_CYCLE)
     return fail(AMM_ERR_STATE, "handle has no component selection");
+  if (h->blk.b) return blocked_selection(h, host_idx, cap, count);
   if (cap < h->k) return fail(AMM_ERR_INVALID_ARG, "cap=%lld < k=%lld", (long long)cap, (long long)h->k);
   const int32_t* sel = h->method == AMM_CIRCULANT ? h->cd.so.sel : h->cy.so.sel;
   cudaError_t e = cudaStreamSynchronize(h->stream);

@@ -58,6 +58,16 @@ struct amm_handle {
     int* err = nullptr;        // device flag: a bounded wait of a tensor-core kernel gave up
   } svd;
 
+  // rectangular circulant operand in b x b blocks (amm_opts_t.block): every block is a square
+  // circulant handle of its own; the ragged edge is read from a zero-padded copy
+  struct Blocks {
+    int64_t b = 0;                    // block size; 0 = one square decomposition (no blocks)
+    int64_t nbr = 0, nbc = 0;         // block rows / columns
+    const void* base = nullptr;       // padded operand (or A itself), nbr*b x nbc*b
+    int64_t ld = 0;                   // its leading dimension
+    std::vector<amm_handle*> sub;     // nbr x nbc, row-major; owned
+  } blk;
+
   void release();
   cudaError_t alloc(void** p, size_t bytes);
 };
@@ -82,6 +92,24 @@ cudaError_t svd_left_apply(Handle* a, const float* X, int64_t ldx, int64_t p, fl
 cudaError_t svd_right_apply(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc, float beta,
                             cudaStream_t st);
 cudaError_t svd_residual(Handle* a, float* D, int64_t ldd, cudaStream_t st);
+// api.cu: one square circulant block pair; acc = 1 adds to C / dA / dB instead of overwriting
+amm_status_t decompose_circulant(Handle* h, const amm_opts_t* o);
+cudaError_t cd_first_order(Handle* a, Handle* b, float* C, int64_t ldc, int acc, cudaStream_t st);
+amm_status_t cd_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, int acc_a,
+                         float* dB, int64_t lddb, int acc_b, cudaStream_t st);
+// blocked.cu
+amm_status_t decompose_circulant_blocked(Handle* h, const amm_opts_t* o);
+amm_status_t blocked_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st);
+amm_status_t blocked_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, float* dB,
+                              int64_t lddb, cudaStream_t st);
+amm_status_t blocked_info(Handle* h, amm_info_t* info);
+amm_status_t blocked_selection(Handle* h, int32_t* host_idx, int64_t cap, int64_t* count);
+// the blockwise pieces of a mixed-method product (C, D padded to whole blocks)
+cudaError_t blocked_left_apply(Handle* a, const float* X, int64_t ldx, int64_t p, float* C, int64_t ldc,
+                               cudaStream_t st);
+cudaError_t blocked_right_apply(Handle* b, const float* Y, int64_t ldy, int64_t m, bool imag, float* C,
+                                int64_t ldc, cudaStream_t st);
+cudaError_t blocked_residual(Handle* a, bool imag, float* D, int64_t ldd, cudaStream_t st);
 // mixed.cu
 amm_status_t mixed_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st);
 

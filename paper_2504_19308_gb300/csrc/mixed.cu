@@ -9,7 +9,13 @@
 // complex (circulant with a split conjugate pair, the Fourier sparsifier), the dense imaginary
 // part and the right apply of Im(B~).  SVD and cycle truncations are real: the last term then
 // vanishes and is skipped.
+//
+// A circulant operand taken in square blocks (amm_opts_t.block) is evaluated on its zero-padded
+// blocks: the product is formed on the padded shape (the other operand padded with zeros along
+// the shared dimension, which leaves its truncation zero there as well) and cropped.
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "api_internal.h"
 #include "kernels.h"
@@ -25,6 +31,7 @@ static bool can_be_complex(const Handle* h) {
 static cudaError_t left_apply(Handle* a, const float* X, int64_t ldx, int64_t p, float* C, int64_t ldc,
                               cudaStream_t st) {
   const int n = (int)a->cols;
+  if (a->blk.b) return blocked_left_apply(a, X, ldx, p, C, ldc, st);
   switch (a->method) {
     case AMM_SVD:
       return svd_left_apply(a, X, ldx, p, C, ldc, 0.f, st);
@@ -43,6 +50,7 @@ static cudaError_t left_apply(Handle* a, const float* X, int64_t ldx, int64_t p,
 static cudaError_t right_apply(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc,
                                cudaStream_t st) {
   const int n = (int)b->rows;
+  if (b->blk.b) return blocked_right_apply(b, Y, ldy, m, false, C, ldc, st);
   switch (b->method) {
     case AMM_SVD:
       return svd_right_apply(b, Y, ldy, m, C, ldc, 1.f, st);
@@ -63,6 +71,7 @@ static cudaError_t right_apply(Handle* b, const float* Y, int64_t ldy, int64_t m
 static cudaError_t right_apply_imag(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc,
                                     cudaStream_t st) {
   const int n = (int)b->rows;
+  if (b->blk.b) return blocked_right_apply(b, Y, ldy, m, true, C, ldc, st);
   if (b->method == AMM_CIRCULANT)
     return cd_apply(n, true, Y, ldy, false, m, b->cd.tw, b->cd.so.dlist, b->cd.Ld, b->cd.so.counts + 1,
                     b->cd.so.counts + 1, b->cd.so.counts + 1, C, ldc, 1, st);
@@ -74,6 +83,7 @@ static cudaError_t right_apply_imag(Handle* b, const float* Y, int64_t ldy, int6
 // D = A - Re(A~), m x n
 static cudaError_t residual(Handle* a, float* D, int64_t ldd, cudaStream_t st) {
   const int n = (int)a->cols;
+  if (a->blk.b) return blocked_residual(a, false, D, ldd, st);
   switch (a->method) {
     case AMM_SVD:
       return svd_residual(a, D, ldd, st);
@@ -91,6 +101,7 @@ static cudaError_t residual(Handle* a, float* D, int64_t ldd, cudaStream_t st) {
 // D = Im(A~), m x n (zero for a circulant selection without unpaired components)
 static cudaError_t imag_part(Handle* a, float* D, int64_t ldd, cudaStream_t st) {
   const int n = (int)a->cols;
+  if (a->blk.b) return blocked_residual(a, true, D, ldd, st);
   if (a->method == AMM_CIRCULANT) {
     cudaError_t e = cudaMemset2DAsync(D, sizeof(float) * ldd, 0, sizeof(float) * n, n, st);
     if (e != cudaSuccess) return e;
@@ -105,19 +116,50 @@ amm_status_t mixed_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStrea
   const int64_t m = a->rows, n = a->cols, p = b->cols;
   if (a->dtype != AMM_F32 || b->dtype != AMM_F32)
     return fail(AMM_ERR_NOT_IMPLEMENTED, "mixed methods: BF16 operands are not built (use FP32 inputs)");
-  float* D = nullptr;
-  cudaError_t e = dev_alloc((void**)&D, sizeof(float) * (size_t)m * n, st);
+  // padded shape: whole blocks of a blocked circulant operand (at most one side is circulant)
+  const int64_t mp = a->blk.b ? a->blk.nbr * a->blk.b : m;
+  const int64_t np = a->blk.b ? a->blk.nbc * a->blk.b : b->blk.b ? b->blk.nbr * b->blk.b : n;
+  const int64_t pp = b->blk.b ? b->blk.nbc * b->blk.b : p;
+  std::vector<void*> tmp;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](size_t elems) -> float* {
+    void* q = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(&q, sizeof(float) * elems, st);
+    if (q) tmp.push_back(q);
+    return (float*)q;
+  };
+  // dense B with np rows: the blocked operand's padded copy, or B padded with zero rows
+  const float* X = (const float*)(b->blk.b ? b->blk.base : b->A);
+  int64_t ldx = b->blk.b ? b->blk.ld : b->lda;
+  if (np != n && !b->blk.b) {
+    float* t = al((size_t)np * p);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t, 0, sizeof(float) * (size_t)np * p, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(t, sizeof(float) * p, X, sizeof(float) * ldx, sizeof(float) * p, n,
+                            cudaMemcpyDeviceToDevice, st);
+    X = t;
+    ldx = p;
+  }
+  const bool crop = mp != m || pp != p;
+  float* Cp = crop ? al((size_t)mp * pp) : C;
+  const int64_t ldcp = crop ? pp : ldc;
+  float* D = al((size_t)mp * np);
+  // a residual of an unblocked operand covers m x n; the padding columns of D stay zero
+  if (e == cudaSuccess && np != n && !a->blk.b) e = cudaMemsetAsync(D, 0, sizeof(float) * (size_t)mp * np, st);
   // C = Re(A~) B
-  if (e == cudaSuccess) e = left_apply(a, (const float*)b->A, b->lda, p, C, ldc, st);
+  if (e == cudaSuccess) e = left_apply(a, X, ldx, pp, Cp, ldcp, st);
   // C += (A - Re A~) Re(B~)
-  if (e == cudaSuccess) e = residual(a, D, n, st);
-  if (e == cudaSuccess) e = right_apply(b, D, n, m, C, ldc, st);
+  if (e == cudaSuccess) e = residual(a, D, np, st);
+  if (e == cudaSuccess) e = right_apply(b, D, np, mp, Cp, ldcp, st);
   // C += Im(A~) Im(B~)
   if (e == cudaSuccess && can_be_complex(a) && can_be_complex(b)) {
-    e = imag_part(a, D, n, st);
-    if (e == cudaSuccess) e = right_apply_imag(b, D, n, m, C, ldc, st);
+    e = imag_part(a, D, np, st);
+    if (e == cudaSuccess) e = right_apply_imag(b, D, np, mp, Cp, ldcp, st);
   }
-  dev_free(D, st);
+  if (e == cudaSuccess && crop)
+    e = cudaMemcpy2DAsync(C, sizeof(float) * ldc, Cp, sizeof(float) * ldcp, sizeof(float) * p, m,
+                          cudaMemcpyDeviceToDevice, st);
+  for (void* q : tmp) dev_free(q, st);
   if (e != cudaSuccess) return cuda_fail(e, "mixed-method product");
   return AMM_OK;
 }

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_status_strings(lib):
     assert lib.amm_status_string(0) == b"AMM_OK"
     assert lib.amm_status_string(5) == b"AMM_ERR_TIMEOUT"
-    assert lib.amm_version() == 2
+    assert lib.amm_version() == 3
 
 
 def test_argument_errors_without_gpu(lib):

@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import synth as S
-from gpu_util import TOL, as64, dev32, rel, torch_cuda
+from gpu_util import TOL, as64, check_selection, dev32, rel, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -47,3 +47,30 @@ def test_llm_shaped_rsvd_k256(compute, tol):
     ref = O.svd_matmul(as64(X), as64(W), k, pa.astype(np.float64), pb.astype(np.float64))
     err = rel(C.double().cpu().numpy(), ref)
     assert err <= tol, err
+
+
+def test_llm_shaped_mixed_rsvd_times_circulant_blocks():
+    """X W with the activations X (2048 x 4096) by rSVD k = 256 and the weight W (4096 x 11008) in
+    4096 x 4096 circulant blocks (zero-padded to 4096 x 12288), k = 128 per block.  Parity on
+    sampled output rows (the oracle evaluates only those rows of Eq. (2.3)); the selection of
+    every weight block is the oracle's top-k outside near-ties."""
+    torch, amm = torch_cuda()
+    x, w = S.llm_shaped(seed=0)
+    X = torch.from_numpy(x.astype(np.float32)).cuda().bfloat16().float()
+    W = torch.from_numpy(w.astype(np.float32)).cuda().bfloat16().float()
+    k, kc, bs = 256, 128, 4096
+    pa = S.sketch(4096, k, 0, 0).astype(np.float32)
+    hX = amm.decompose(X, "svd", k, "left", sketch=dev32(torch, pa))
+    hW = amm.decompose(W, "circulant", kc, "right", block=bs)
+    C = amm.approx_matmul(hX, hW)
+    x64, w64 = as64(X), as64(W)
+    tw = O.truncate_circulant_blocked(w64, bs, kc, selections=hW.selection())
+    top = O.truncate_circulant_blocked(w64, bs, kc)
+    for j, t in enumerate(top.blocks[0]):
+        check_selection(hW.selection()[j], t.keys, kc, ("W block", j))
+    tx = O.truncate_rsvd(x64, k, pa.astype(np.float64))
+    rows = np.sort(S.rng(1, 70).choice(2048, 48, replace=False))
+    tx_rows = O.Truncation("svd", tx.a[rows], tx.approx[rows])
+    ref = O.blocked_first_order(tx_rows, tw)
+    got = C.double().cpu().numpy()[rows]
+    assert rel(got, ref) <= TOL
