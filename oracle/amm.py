@@ -24,7 +24,7 @@ Readings taken where the paper is silent or inconsistent (each also listed in DE
   R9  Cycle sparsifier key: ||diag Lambda_j||_2 (by analogy with Alg. 3 Step 2).
   R10 Backward: selections, Q factors and masks are frozen; the gradient is that of the
       resulting bilinear map.
-  R11 Rectangular circulant operands: b x b blocks, ragged edge zero-padded, top-k per block,
+  R13 Rectangular circulant operands: b x b blocks, ragged edge zero-padded, top-k per block,
       Eq. (2.3) on the padded operands, padded rows / columns of the product dropped.
 """
 from __future__ import annotations
@@ -596,7 +596,7 @@ def mixed_product(ta: Truncation, tb: Truncation) -> np.ndarray:
 
 # ---------------------------------------------------------------------------
 # Rectangular operands in square circulant blocks (Section 2.3: the cycle decomposition is
-# defined for square matrices and a rectangular one is handled in square blocks).  Reading R11:
+# defined for square matrices and a rectangular one is handled in square blocks).  Reading R13:
 # both dimensions are cut into b x b blocks, the ragged edge is padded with zeros, every block
 # keeps its own top-k components, Eq. (2.3) is evaluated on the padded operands and the padded
 # rows / columns of the product are dropped.
@@ -615,7 +615,7 @@ def ceil_to(x: int, b: int) -> int:
 
 
 def truncate_circulant_blocked(a: np.ndarray, bs: int, k: int, selections=None) -> Truncation:
-    """Blockwise circulant truncation (reading R11).  Block (I, J) is rows I*bs.. and columns
+    """Blockwise circulant truncation (reading R13).  Block (I, J) is rows I*bs.. and columns
     J*bs.. of the zero-padded operand; `selections[I * nbc + J]` replaces its top-k selection.
     The Truncation holds the PADDED operand and truncation; .shape0 is the original shape and
     .blocks[I][J] the per-block truncations."""
@@ -646,7 +646,7 @@ def padded(t: Truncation, rows: int, cols: int) -> Truncation:
 
 def blocked_first_order(ta: Truncation, tb: Truncation) -> np.ndarray:
     """Re M of Eq. (2.3) where either operand may be a blockwise circulant truncation (reading
-    R11): both are brought to the common padded shape, M is formed there and cropped to m x p."""
+    R13): both are brought to the common padded shape, M is formed there and cropped to m x p."""
     m0 = getattr(ta, "shape0", ta.a.shape)[0]
     p0 = getattr(tb, "shape0", tb.a.shape)[1]
     rows, inner, cols = ta.a.shape[0], max(ta.a.shape[1], tb.a.shape[0]), tb.a.shape[1]

@@ -436,7 +436,7 @@ def test_backward_finite_differences_n64(method):
         assert fd_b == pytest.approx(np.sum(db * eb), rel=1e-9)
 
 
-# --------------------------------------------------------------------------- square blocks (R11)
+# --------------------------------------------------------------------------- square blocks (R13)
 
 _RAGGED = [(10, 13, 7, 4), (8, 8, 12, 4), (5, 16, 9, 8), (16, 16, 16, 16)]
 
@@ -516,7 +516,7 @@ def test_blocked_mixed_identity(mb):
 
 
 def test_blocked_backward_matches_bruteforce():
-    """Reading R10 + R11: the blockwise gradients equal <G, M(E_ij)> over every basis matrix."""
+    """Reading R10 + R13: the blockwise gradients equal <G, M(E_ij)> over every basis matrix."""
     m, n, p, bs, k = 5, 7, 6, 4, 2
     g = S.rng(56, 0)
     a, b, gr = g.standard_normal((m, n)), g.standard_normal((n, p)), g.standard_normal((m, p))
