@@ -10,6 +10,7 @@
 //   dA(r, q) = A(r, q) if (r - q) mod n is not in S_A, else 0.
 #include <cuda_runtime.h>
 
+#include "api_internal.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "trace.h"
@@ -210,44 +211,57 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_col_kernel(const float* __restr
   }
 }
 
-// dA((l + t), l) += <G(l + t, :), dB(l, :)> for t in S_A; one warp per (u, l)
-__global__ void __launch_bounds__(256) cyc_bw_proj_rows_kernel(const float* __restrict__ G, int64_t ldg,
-                                                               const float* __restrict__ B, int64_t ldb, int n,
-                                                               const int32_t* __restrict__ selA,
-                                                               const unsigned char* __restrict__ inselB,
-                                                               float* __restrict__ dA, int64_t ldda) {
-  const int u = blockIdx.y;
-  const int t = selA[u];
-  const int l = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  const float* g = G + (int64_t)((l + t) & (n - 1)) * ldg;
-  const float* b = B + (int64_t)l * ldb;
-  float acc = 0.f;
-#pragma unroll 8
-  for (int m = lane; m < n; m += 32)
-    if (!inselB[(l - m) & (n - 1)]) acc = fmaf(__ldg(g + m), __ldg(b + m), acc);
+// Selected diagonals of a product: out((l + t) mod n, l) += <X((l + t) mod n, :), Y(l, :)> for
+// t = sel[u], every l.  The projection terms of the cycle backward are of this form (the kept
+// cycles of G dB^T and of dA^T G, with the masks applied to dense residuals beforehand).  A warp
+// takes one l and CYC_DG selected t's: lanes stride the rows in float4s, each float4 of Y(l, :)
+// serves CYC_DG products.  The t-groups are the fast grid dimension, so the CTAs in flight share
+// their rows Y(l, :) through L2.  Rows 16-byte aligned (n a multiple of 4, ldx, ldy too).
+constexpr int CYC_DG = 4;
+__global__ void __launch_bounds__(256) cyc_diag_dot_kernel(const float* __restrict__ X, int64_t ldx,
+                                                           const float* __restrict__ Y, int64_t ldy, int n,
+                                                           const int32_t* __restrict__ sel, int k,
+                                                           float* __restrict__ out, int64_t ldo) {
+  const int g0 = blockIdx.x * CYC_DG;
+  const int l = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int nt = min(CYC_DG, k - g0);
+  int r[CYC_DG];
+  const float4* xr[CYC_DG];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) dA[(int64_t)((l + t) & (n - 1)) * ldda + l] += acc;
+  for (int j = 0; j < CYC_DG; ++j) {
+    r[j] = (l + __ldg(sel + g0 + (j < nt ? j : 0))) & (n - 1);
+    xr[j] = reinterpret_cast<const float4*>(X + (int64_t)r[j] * ldx);
+  }
+  const float4* yr = reinterpret_cast<const float4*>(Y + (int64_t)l * ldy);
+  float acc[CYC_DG];
+#pragma unroll
+  for (int j = 0; j < CYC_DG; ++j) acc[j] = 0.f;
+#pragma unroll 4
+  for (int m4 = lane; m4 < n / 4; m4 += 32) {
+    const float4 y = __ldg(yr + m4);
+#pragma unroll
+    for (int j = 0; j < CYC_DG; ++j) {
+      const float4 x = __ldg(xr[j] + m4);
+      acc[j] = fmaf(x.x, y.x, acc[j]);
+      acc[j] = fmaf(x.y, y.y, acc[j]);
+      acc[j] = fmaf(x.z, y.z, acc[j]);
+      acc[j] = fmaf(x.w, y.w, acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CYC_DG; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+#pragma unroll
+  for (int j = 0; j < CYC_DG; ++j)
+    if (lane == j && j < nt) out[(int64_t)r[j] * ldo + l] += acc[j];
 }
 
-// dB((l + s), l) += sum_r dA(r, l + s) G(r, l) for s in S_B; thread per l, loop over r
-__global__ void __launch_bounds__(256) cyc_bw_proj_cols_kernel(const float* __restrict__ A, int64_t lda,
-                                                               const float* __restrict__ G, int64_t ldg, int n,
-                                                               const int32_t* __restrict__ selB,
-                                                               const unsigned char* __restrict__ inselA,
-                                                               float* __restrict__ dB, int64_t lddb) {
-  const int u = blockIdx.y;
-  const int s = selB[u];
-  const int l = blockIdx.x * 256 + threadIdx.x;
-  if (l >= n) return;
-  const int q = (l + s) & (n - 1);
-  float acc = 0.f;
-#pragma unroll 8
-  for (int r = 0; r < n; ++r) {
-    const float a = inselA[(r - q) & (n - 1)] ? 0.f : __ldg(A + (int64_t)r * lda + q);
-    acc = fmaf(a, __ldg(G + (int64_t)r * ldg + l), acc);
-  }
-  dB[(int64_t)q * lddb + l] += acc;
+static cudaError_t diag_dot(const float* X, int64_t ldx, const float* Y, int64_t ldy, int n, const int32_t* sel,
+                            int k, float* out, int64_t ldo, const char* name, cudaStream_t st) {
+  AMM_TRACE_W(name, st, 2.0 * k * (double)n * n, 4.0 * n * ((double)k + (k + CYC_DG - 1) / CYC_DG) * n, nullptr);
+  cyc_diag_dot_kernel<<<dim3((k + CYC_DG - 1) / CYC_DG, n / 8), 256, 0, st>>>(X, ldx, Y, ldy, n, sel, k, out, ldo);
+  return cudaGetLastError();
 }
 
 cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int64_t ldb, const int32_t* selA, int ka,
@@ -264,32 +278,45 @@ cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  cudaError_t e = cudaSuccess;
+  // dense scratch: the masked residual of the other operand, and for dB the transposes
+  const int64_t nn = (int64_t)n * n;
+  float* T = nullptr;
+  cudaError_t e = dev_alloc((void**)&T, sizeof(float) * 3 * nn, st);
+  if (e != cudaSuccess) return e;
+  float *T0 = T, *T1 = T + nn, *T2 = T + 2 * nn;
+  auto aligned = [](const float* p, int64_t ld) { return ((uintptr_t)p & 15) == 0 && (ld & 3) == 0; };
   if (dA) {
     {
       AMM_TRACE_W("cyc_bw_row", st, 2.0 * kb * (double)n * n, 8.0 * n * (double)n, nullptr);
       cyc_bw_row_kernel<<<n / CYC_RW, CYC_NT, sizeof(float) * CYC_RW * n, st>>>(G, ldg, n, selB, kb, cycB, dA, ldda);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    {
-      AMM_TRACE_W("cyc_bw_proj_rows", st, 2.0 * ka * (double)n * n, 8.0 * ka * (double)n * n, nullptr);
-      cyc_bw_proj_rows_kernel<<<dim3(n / 8, ka), 256, 0, st>>>(G, ldg, B, ldb, n, selA, inselB, dA, ldda);
+    e = cudaGetLastError();
+    // dA((l + t), l) += <G(l + t, :), dB(l, :)> for t in S_A, dB = B with its kept cycles zeroed
+    if (e == cudaSuccess) e = cyc_residual(n, B, ldb, inselB, T0, n, st);
+    const float* Gx = G;
+    int64_t ldgx = ldg;
+    if (e == cudaSuccess && !aligned(G, ldg)) {
+      e = cudaMemcpy2DAsync(T1, sizeof(float) * n, G, sizeof(float) * ldg, sizeof(float) * n, n,
+                            cudaMemcpyDeviceToDevice, st);
+      Gx = T1;
+      ldgx = n;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e == cudaSuccess) e = diag_dot(Gx, ldgx, T0, n, n, selA, ka, dA, ldda, "cyc_bw_proj_rows", st);
   }
-  if (dB) {
+  if (dB && e == cudaSuccess) {
     {
       AMM_TRACE_W("cyc_bw_col", st, 2.0 * ka * (double)n * n, 8.0 * n * (double)n, nullptr);
       cyc_bw_col_kernel<<<n / CYC_CW, CYC_NT, sizeof(float4) * n + sizeof(int) * ka, st>>>(G, ldg, n, selA, ka, cycA, dB, lddb);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    {
-      AMM_TRACE_W("cyc_bw_proj_cols", st, 2.0 * kb * (double)n * n, 8.0 * kb * (double)n * n, nullptr);
-      cyc_bw_proj_cols_kernel<<<dim3((n + 255) / 256, kb), 256, 0, st>>>(A, lda, G, ldg, n, selB, inselA, dB, lddb);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaGetLastError();
+    // dB((l + s), l) += sum_r dA(r, l + s) G(r, l) = <dA^T(l + s, :), G^T(l, :)> for s in S_B
+    if (e == cudaSuccess) e = cyc_residual(n, A, lda, inselA, T0, n, st);
+    if (e == cudaSuccess) e = transpose_f32(T0, n, n, n, T1, n, st);
+    if (e == cudaSuccess) e = transpose_f32(G, n, n, ldg, T2, n, st);
+    if (e == cudaSuccess) e = diag_dot(T1, n, T2, n, n, selB, kb, dB, lddb, "cyc_bw_proj_cols", st);
   }
-  return cudaSuccess;
+  dev_free(T, st);
+  return e;
 }
 
 int cyc_rows_per_part(int n) { return n >= 1024 ? 64 : 16; }
@@ -342,12 +369,24 @@ cudaError_t cyc_apply(int n, const float* A, int64_t lda, const float* B, int64_
 
 // ============================================================================ mixed-method pieces
 // D = A with the kept cycles zeroed (the dense residual dA = A - A_s)
-__global__ void cyc_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
-                                    const unsigned char* __restrict__ insel, float* __restrict__ D, int64_t ldd) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)n * n) return;
-  const int r = (int)(e / n), c = (int)(e % n);
-  D[(int64_t)r * ldd + c] = insel[(r - c) & (n - 1)] ? 0.f : __ldg(A + (int64_t)r * lda + c);
+// D = A with the selected cycles zeroed: row r, four consecutive columns per thread.
+__global__ void __launch_bounds__(256) cyc_residual_kernel(const float* __restrict__ A, int64_t lda, int n,
+                                                           const unsigned char* __restrict__ insel,
+                                                           float* __restrict__ D, int64_t ldd) {
+  const int r = blockIdx.y;
+  const int c0 = (blockIdx.x * 256 + threadIdx.x) * 4;
+  if (c0 >= n) return;
+  const float* a = A + (int64_t)r * lda + c0;
+  float v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = insel[(r - c0 - i) & (n - 1)] ? 0.f : __ldg(a + i);
+  float* d = D + (int64_t)r * ldd + c0;
+  if ((((uintptr_t)d) & 15) == 0) {
+    *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = v[i];
+  }
 }
 
 static cudaError_t cyc_attrs() {
@@ -387,8 +426,7 @@ cudaError_t cyc_right_apply(int n, const int32_t* selB, int kb, const float* cyc
 cudaError_t cyc_residual(int n, const float* A, int64_t lda, const unsigned char* insel, float* D, int64_t ldd,
                          cudaStream_t st) {
   AMM_TRACE_W("cyc_residual", st, 0.0, 8.0 * n * (double)n, nullptr);
-  const int64_t tot = (int64_t)n * n;
-  cyc_residual_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A, lda, n, insel, D, ldd);
+  cyc_residual_kernel<<<dim3((n / 4 + 255) / 256, n), 256, 0, st>>>(A, lda, n, insel, D, ldd);
   return cudaGetLastError();
 }
 

@@ -251,7 +251,7 @@ __global__ void gram_reduce_kernel(int k, int splits, const double* __restrict__
 
 static cudaError_t gram_dot2(int64_t m, int k, const float* X, float* G, cudaStream_t st, int ns = 0) {
   const int tiles = ((k + 31) / 32) * ((k + 31) / 32);
-  int splits = std::max(1, std::min((int)(m / 256), (2 * num_sms() + tiles - 1) / tiles));
+  int splits = std::max(1, std::min((int)(m / 32), (2 * num_sms() + tiles - 1) / tiles));
   int kchunk = (int)((m + splits - 1) / splits);
   kchunk = ((kchunk + 31) / 32) * 32;
   splits = std::max(1, (int)((m + kchunk - 1) / kchunk));
@@ -275,22 +275,29 @@ static cudaError_t gram_dot2(int64_t m, int k, const float* X, float* G, cudaStr
 
 // ============================================================================ Cholesky + inverse (FP32, one CTA)
 // G (k x k, symmetric positive semi-definite) -> Linv = L^{-1} with G + s I = L L^T,
-// s = shift_rel * trace(G).  Shared memory holds W (k x k; L ends in its lower triangle), the
-// inverse TRANSPOSED (LiT[c][l] = Linv[l][c]) and the current column of L, so every inner loop
-// reads consecutive or broadcast words (no bank conflicts).  One warp per row in the trailing
-// update.  The inverse is built row by row: Linv[i][c] = -sum_{l=c}^{i-1} L[i][l] Linv[l][c] /
-// L[i][i], one warp per column c with the lanes splitting the sum over l.  For k > CHOL_SMEM_K
-// the same arrays live in a global work area (2 k^2 + k floats).
+// s = shift_rel * trace(G).  Blocked in 32 x 32 tiles (k padded to kp, a multiple of 32, with an
+// identity block), so that the sequential part runs inside one warp without block barriers:
+//   per block column J: warp 0 factors the diagonal tile with shuffles (lane r holds row r); the
+//   rows below solve against it (x L_JJ^T = a, a thread per row); all threads update the
+//   trailing matrix;
+//   inverse: every diagonal tile is inverted by its own warp (lane c holds column c of the
+//   inverse), then the tiles at distance d = I - J below the diagonal, for d = 1, 2, ...:
+//   T_IJ = sum_{J <= K < I} L_IK Linv_KJ (kept in the unused upper triangle of W), then
+//   Linv_IJ = -Linv_II T_IJ.
+// Rows have the odd stride kp + 1 (conflict-free column walks).  For kp > CHOL_SMEM_K the same
+// arrays live in a global work area of 2 kp (kp + 1) floats.
 constexpr int CHOL_SMEM_K = 160;
-constexpr int CHOL_T = 1024;
+constexpr int CHOL_T = 512;
+__host__ __device__ constexpr int chol_kp(int k) { return (k + 31) & ~31; }
+__host__ __device__ constexpr size_t chol_floats(int k) { return 2 * (size_t)chol_kp(k) * (chol_kp(k) + 1); }
 
 __global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const float* __restrict__ G, float shift_rel,
                                                           float* __restrict__ Linv_out, float* __restrict__ gwork) {
   extern __shared__ float sh_dyn[];
-  float* sh = (k <= CHOL_SMEM_K) ? sh_dyn : gwork;  // larger k: same layout in global memory
-  float* W = sh;              // k * k
-  float* Li = sh + k * k;     // k * k
-  float* col = Li + k * k;    // k
+  const int kp = chol_kp(k), nb = kp / 32, ldw = kp + 1;
+  float* sh = (kp <= CHOL_SMEM_K) ? sh_dyn : gwork;
+  float* W = sh;               // kp x kp (stride ldw): G + sI, then L in the lower triangle
+  float* Li = sh + kp * ldw;   // kp x kp (stride ldw): L^{-1}, lower triangle
   __shared__ float red[32];
   __shared__ float shift_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -306,47 +313,111 @@ __global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const float* __
   }
   __syncthreads();
   const float shift = shift_s;
-  for (int e = tid; e < k * k; e += CHOL_T) {
-    const int i = e / k, j = e - i * k;
-    W[e] = G[e] + (i == j ? shift : 0.f);
-    Li[e] = 0.f;
+  for (int e = tid; e < kp * kp; e += CHOL_T) {
+    const int i = e / kp, j = e - i * kp;
+    W[i * ldw + j] = (i < k && j < k) ? G[(int64_t)i * k + j] + (i == j ? shift : 0.f) : (i == j ? 1.f : 0.f);
+    Li[i * ldw + j] = 0.f;
   }
   __syncthreads();
-  // right-looking Cholesky
-  for (int j = 0; j < k; ++j) {
-    const float djj = sqrtf(fmaxf(W[j * k + j], shift));
-    const float rdj = 1.f / djj;
-    for (int i = j + tid; i < k; i += CHOL_T) {
-      const float v = (i == j) ? djj : W[i * k + j] * rdj;
-      col[i] = v;
-      W[i * k + j] = v;
-    }
-    __syncthreads();
-    for (int i = j + 1 + warp; i < k; i += CHOL_T / 32) {
-      const float ci = col[i];
-      for (int l = j + 1 + lane; l <= i; l += 32) W[i * k + l] = fmaf(-ci, col[l], W[i * k + l]);
-    }
-    __syncthreads();
-  }
-  // Linv (held transposed in Li): diagonal, then rows i = 1..k-1, one warp per column c < i
-  for (int i = tid; i < k; i += CHOL_T) Li[i * k + i] = 1.f / W[i * k + i];
-  __syncthreads();
-  for (int i = 1; i < k; ++i) {
-    const float di = Li[i * k + i];
-    const float* wrow = W + i * k;
-    for (int c = warp; c < i; c += CHOL_T / 32) {
-      const float* lcol = Li + c * k;  // Linv[.][c]
-      float s = 0.f;
-      for (int l = c + lane; l < i; l += 32) s = fmaf(wrow[l], lcol[l], s);
+  for (int J = 0; J < nb; ++J) {
+    const int j0 = 32 * J;
+    if (warp == 0) {
+      // diagonal tile: right-looking Cholesky, lane r holds row r
+      float a[32];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) Li[c * k + i] = -s * di;
+      for (int c = 0; c < 32; ++c) a[c] = (c <= lane) ? W[(j0 + lane) * ldw + j0 + c] : 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float d = sqrtf(fmaxf(__shfl_sync(0xffffffffu, a[c], c), shift));
+        const float rd = 1.f / d;
+        if (lane == c) a[c] = d;
+        else if (lane > c) a[c] *= rd;
+        const float lrc = a[c];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) {  // fixed bounds: the loop nest unrolls and a[] stays in registers
+          if (l > c) {
+            const float llc = __shfl_sync(0xffffffffu, a[c], l);
+            if (lane >= l) a[l] = fmaf(-lrc, llc, a[l]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c <= lane) W[(j0 + lane) * ldw + j0 + c] = a[c];
+    }
+    __syncthreads();
+    // panel below the tile: x L_JJ^T = a, a thread per row
+    for (int i = j0 + 32 + tid; i < kp; i += CHOL_T) {
+      float* wr = W + i * ldw + j0;
+      float x[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float* lc = W + (j0 + c) * ldw + j0;
+        float v = wr[c];
+#pragma unroll
+        for (int l = 0; l < c; ++l) v = fmaf(-x[l], lc[l], v);
+        x[c] = v * (1.f / lc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) wr[c] = x[c];
+    }
+    __syncthreads();
+    // trailing update of the lower triangle
+    const int t0 = j0 + 32, m = kp - t0;
+    for (int e = tid; e < m * m; e += CHOL_T) {
+      const int i = t0 + e / m, l = t0 + e % m;
+      if (l > i) continue;
+      const float* ri = W + i * ldw + j0;
+      const float* rl = W + l * ldw + j0;
+      float v = W[i * ldw + l];
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) v = fmaf(-ri[c], rl[c], v);
+      W[i * ldw + l] = v;
+    }
+    __syncthreads();
+  }
+  // inverse of every diagonal tile: lane c holds column c
+  for (int J = warp; J < nb; J += CHOL_T / 32) {
+    const int j0 = 32 * J;
+    float col[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const float* lr = W + (j0 + r) * ldw + j0;
+      float s = 0.f;
+#pragma unroll
+      for (int l = 0; l < r; ++l) s = fmaf(lr[l], col[l], s);
+      const float di = 1.f / lr[r];
+      col[r] = (r < lane) ? 0.f : (r == lane) ? di : -s * di;
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+      if (r >= lane) Li[(j0 + r) * ldw + j0 + lane] = col[r];
+  }
+  __syncthreads();
+  // tiles below the diagonal, by distance d
+  for (int d = 1; d < nb; ++d) {
+    const int cnt = (nb - d) * 1024;
+    for (int e = tid; e < cnt; e += CHOL_T) {
+      const int J = e >> 10, r = (e >> 5) & 31, c = e & 31, I = J + d;
+      const float* lrow = W + (32 * I + r) * ldw;
+      float s = 0.f;
+      for (int q = 32 * J; q < 32 * I; ++q) s = fmaf(lrow[q], Li[q * ldw + 32 * J + c], s);
+      W[(32 * J + r) * ldw + 32 * I + c] = s;  // T_IJ in the upper triangle
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt; e += CHOL_T) {
+      const int J = e >> 10, r = (e >> 5) & 31, c = e & 31, I = J + d;
+      const float* lirow = Li + (32 * I + r) * ldw + 32 * I;
+      float s = 0.f;
+#pragma unroll 8
+      for (int q = 0; q <= r; ++q) s = fmaf(lirow[q], W[(32 * J + q) * ldw + 32 * I + c], s);
+      Li[(32 * I + r) * ldw + 32 * J + c] = -s;
     }
     __syncthreads();
   }
   for (int e = tid; e < k * k; e += CHOL_T) {
     const int i = e / k, c = e - i * k;
-    Linv_out[e] = Li[c * k + i];
+    Linv_out[e] = (c <= i) ? Li[i * ldw + c] : 0.f;
   }
 }
 
@@ -439,17 +510,17 @@ static cudaError_t sumsq(const T* X, int64_t rows, int64_t cols, int64_t ld, dou
   return e;
 }
 
-// W: global work area of at least 2 k^2 + k floats (used when k > CHOL_SMEM_K)
+// W: global work area of at least chol_floats(k) floats (used when chol_kp(k) > CHOL_SMEM_K)
 static cudaError_t chol_inv(int k, const float* G, float shift_rel, float* W, float* Li, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute((const void*)chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (2 * CHOL_SMEM_K * CHOL_SMEM_K + CHOL_SMEM_K) * (int)sizeof(float));
+                                         (int)(chol_floats(CHOL_SMEM_K) * sizeof(float)));
     if (e != cudaSuccess) return e;
     attr = true;
   }
   AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0 * 2.0, 0.0, nullptr);
-  const size_t sm = k <= CHOL_SMEM_K ? sizeof(float) * (2 * (size_t)k * k + k) : 0;
+  const size_t sm = chol_kp(k) <= CHOL_SMEM_K ? sizeof(float) * chol_floats(k) : 0;
   chol_inv_kernel<<<1, CHOL_T, sm, st>>>(k, G, shift_rel, Li, W);
   return cudaGetLastError();
 }
@@ -470,7 +541,7 @@ static cudaError_t orthonormalize(int64_t m, int k, const float* Y, float* Q, cu
     if (e == cudaSuccess) e = dev_alloc((void**)p, sizeof(float) * cnt, st);
   };
   al(&G, (size_t)k * k);
-  al(&W, 2 * (size_t)k * k + k);
+  al(&W, chol_floats(k));
   al(&Li, (size_t)k * k);
   al(&Q1, (size_t)m * k);
   al(&Q2, (size_t)m * k);

@@ -1,6 +1,10 @@
 """Run one decomposition + first-order product (+ backward) for a profiler.
 
     python -m paper_2504_19308_gb300.profile_case --method circulant --k 256 --n 4096 [--backward] [--repeat 2]
+    python -m paper_2504_19308_gb300.profile_case --step [--repeat 2]
+
+--step runs the sweep of the n = 4096 throughput step instead (circulant k = 16/64/256, rSVD
+k = 32/128, Fourier and cycle sparsifiers k = 41, each decomposed, multiplied and differentiated).
 
 Inputs are the seeded power-law pair of the bench (sigma_i = i^-1.5 + N(0, 1e-4)), drawn as
 Gaussian-plus-spectrum matrices without QR when --fast is given (same sizes, cheaper to make).
@@ -27,6 +31,7 @@ def main():
     ap.add_argument("--backward", action="store_true")
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--fast", action="store_true")
+    ap.add_argument("--step", action="store_true")
     a = ap.parse_args()
     n, k = a.n, a.k
     if a.fast:
@@ -37,21 +42,30 @@ def main():
     dev = torch.device("cuda")
     A = torch.tensor(x, dtype=torch.float32, device=dev)
     B = torch.tensor(y, dtype=torch.float32, device=dev)
-    sa = torch.tensor(synth.sketch(n, k, 0, 0), dtype=torch.float32, device=dev) if a.method == "svd" else None
-    sb = torch.tensor(synth.sketch(n, k, 0, 1), dtype=torch.float32, device=dev) if a.method == "svd" else None
     G = torch.randn((n, n), device=dev)
+    ks = -(-n // 100)
+    cases = ([("circulant", 16, True), ("circulant", 64, True), ("circulant", 256, True), ("svd", 32, True),
+              ("svd", 128, True), ("fourier", ks, True), ("cycle", ks, True)] if a.step
+             else [(a.method, k, a.backward)])
+    sk = {}
+    for method, kk, _ in cases:
+        if method == "svd":
+            sk[kk] = tuple(torch.tensor(synth.sketch(n, kk, 0, side), dtype=torch.float32, device=dev)
+                           for side in (0, 1))
     for _ in range(a.repeat):
         torch.cuda.nvtx.range_push("case")
-        hA = amm.decompose(A, a.method, k, "left", sketch=sa)
-        hB = amm.decompose(B, a.method, k, "right", sketch=sb)
-        C = amm.approx_matmul(hA, hB)
-        if a.backward:
-            amm.approx_matmul_backward(hA, hB, G)
+        for method, kk, bwd in cases:
+            sa, sb = sk.get(kk, (None, None)) if method == "svd" else (None, None)
+            hA = amm.decompose(A, method, kk, "left", sketch=sa)
+            hB = amm.decompose(B, method, kk, "right", sketch=sb)
+            C = amm.approx_matmul(hA, hB)
+            if bwd:
+                amm.approx_matmul_backward(hA, hB, G)
+            hA.close()
+            hB.close()
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        hA.close()
-        hB.close()
-    print("ok", a.method, n, k, float(C.abs().sum()))
+    print("ok", "step" if a.step else a.method, n, k, float(C.abs().sum()))
 
 
 if __name__ == "__main__":

@@ -37,6 +37,13 @@ def test_library_exports_every_declared_symbol(lib):
         assert s in amm.SIGNATURES, "binding lacks " + s
 
 
+def test_library_resolves_every_symbol_at_load(lib):
+    """Eager binding (RTLD_NOW): a symbol the library references but no object defines fails here
+    on the CPU rather than at the first call on a GPU machine."""
+    path = os.path.join(ROOT, "paper_2504_19308_gb300", "libamm.so")
+    ctypes.CDLL(path, mode=os.RTLD_NOW | os.RTLD_LOCAL)
+
+
 def test_status_strings(lib):
     assert lib.amm_status_string(0) == b"AMM_OK"
     assert lib.amm_status_string(5) == b"AMM_ERR_TIMEOUT"

@@ -90,6 +90,32 @@ def test_cycle_backward(n, ka, kb):
     assert rel(dB.double().cpu().numpy(), rdb) <= TOL
 
 
+@pytest.mark.parametrize("n,ka,kb", [(64, 4, 3), (2048, 21, 21)])
+def test_cycle_backward_strided_gradient(n, ka, kb):
+    """Upstream gradient with an odd leading dimension (rows not 16-byte aligned) and outputs with
+    padded leading dimensions."""
+    torch, amm = torch_cuda()
+    lib = amm.load_library()
+    g = S.rng(n + ka + kb, 1)
+    a = g.standard_normal((n, n)) + np.diag(np.full(n, 3.0))
+    b = S.toeplitz_uniform(n, g)
+    gr = g.standard_normal((n, n))
+    A, B = dev32(torch, a), dev32(torch, b)
+    Gw = dev32(torch, np.concatenate([gr, np.zeros((n, 1))], axis=1))   # ldg = n + 1
+    dAw = torch.zeros((n, n + 3), device="cuda")
+    dBw = torch.zeros((n, n + 5), device="cuda")
+    hA = amm.decompose(A, "cycle", ka, "left")
+    hB = amm.decompose(B, "cycle", kb, "right")
+    st = torch.cuda.current_stream().cuda_stream
+    assert lib.amm_approx_matmul_backward(hA.ptr, hB.ptr, Gw.data_ptr(), n + 1, dAw.data_ptr(), n + 3,
+                                          dBw.data_ptr(), n + 5, st) == 0
+    ta = O.truncate_cycles(as64(A), ka, hA.selection())
+    tb = O.truncate_cycles(as64(B), kb, hB.selection())
+    rda, rdb = O.cycle_backward(ta, tb, gr.astype(np.float32).astype(np.float64))
+    assert rel(dAw[:, :n].double().cpu().numpy(), rda) <= TOL
+    assert rel(dBw[:, :n].double().cpu().numpy(), rdb) <= TOL
+
+
 def test_cycle_bf16_operands():
     """BF16 operands of the cycle sparsifier (widened to FP32 once by the handle)."""
     torch, amm = torch_cuda()
