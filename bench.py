@@ -418,9 +418,11 @@ def llm_form(args, dev, dist):
             "approx_rel_err_vs_exact": err}
 
 
-# dram bytes per launch from the ncu capture summarised in profiles/ (None = not captured for
-# the kernel as it stands)
-NCU_TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from an ncu launch list
+# of the whole step (profile_case --step), averaged over the kernel's launches in one step like the
+# achieved rate (cd_sddmm: both SDDMM kernels, 12 launches, six of them gated off); keyed by the
+# trace name, and to be dropped when the kernel changes (None = not captured as it stands)
+NCU_TRAFFIC = {"cd_sddmm": 151.6e6}
 
 
 def roofline(kernels, clocks):
