@@ -124,6 +124,9 @@ extern "C" amm_status_t amm_debug_fail_alloc_after(int32_t n) {
 
 // ----------------------------------------------------------------------------- handles
 static bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+bool amm::cd_length_ok(int64_t n) {
+  return (pow2(n) && n >= 16 && n <= 8192) || (n % 3 == 0 && pow2(n / 3) && n >= 48 && n <= 6144);
+}
 
 void amm::Handle::release() {
   for (amm_handle* b : blk.sub) {
@@ -143,8 +146,8 @@ cudaError_t amm::Handle::alloc(void** p, size_t bytes) {
 
 amm_status_t amm::decompose_circulant(Handle* h, const amm_opts_t* o) {
   const int n = (int)h->rows;
-  if (!pow2(n) || n < 16 || n > 8192)
-    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: n=%d must be a power of two in [16, 8192]", n);
+  if (!cd_length_ok(n))
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: n=%d must be 2^a in [16, 8192] or 3 * 2^a in [48, 6144]", n);
   auto& c = h->cd;
   const int J = cd_cols_per_cta(n);
   c.nparts = n / J;
@@ -598,8 +601,12 @@ extern "C" amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info) {
 extern "C" amm_status_t amm_choose_k(const void* A, int64_t rows, int64_t cols, int64_t lda, amm_dtype_t dtype,
                                      amm_method_t method, double tol, void* stream, int64_t* k_out) {
   if (!A || !k_out) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: NULL argument");
-  if (rows != cols || !pow2((int)rows) || rows < 16 || rows > 8192)
-    return fail(AMM_ERR_UNSUPPORTED_SIZE, "amm_choose_k: A must be square with n a power of two in [16, 8192]");
+  if (rows != cols)
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "amm_choose_k: A must be square (got %lldx%lld)", (long long)rows,
+                (long long)cols);
+  if (method == AMM_CIRCULANT ? !cd_length_ok(rows) : (!pow2(rows) || rows < 16 || rows > 8192))
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "amm_choose_k: n=%lld is not a supported length for this method",
+                (long long)rows);
   if (lda < cols) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: lda < cols");
   if (!(tol >= 0.0)) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: tol must be >= 0");
   if (dtype != AMM_F32 && dtype != AMM_BF16) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: bad dtype");

@@ -26,7 +26,6 @@ namespace amm {
 
 namespace {
 
-bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 int64_t ceil_div(int64_t x, int64_t b) { return (x + b - 1) / b; }
 
 // Block grid of a circulant handle; an unblocked square handle is a 1 x 1 grid of itself.
@@ -71,8 +70,9 @@ cudaError_t copy2d(float* dst, int64_t ldd, const float* src, int64_t lds, int64
 
 amm_status_t decompose_circulant_blocked(Handle* h, const amm_opts_t* o) {
   const int64_t b = o->block;
-  if (!is_pow2(b) || b < 16 || b > 8192)
-    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: block=%lld must be a power of two in [16, 8192]", (long long)b);
+  if (!cd_length_ok(b))
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: block=%lld must be 2^a in [16, 8192] or 3 * 2^a in [48, 6144]",
+                (long long)b);
   auto& g = h->blk;
   g.b = b;
   g.nbr = ceil_div(h->rows, b);

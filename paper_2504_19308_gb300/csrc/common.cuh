@@ -28,3 +28,17 @@ AMM_DEV int fpad(int e) { return e + (e >> 4); }
 __host__ __device__ constexpr int fft_padded_len(int n) { return n + n / 16; }
 
 constexpr int ilog2_c(int n) { return n <= 1 ? 0 : 1 + ilog2_c(n / 2); }
+
+// Transform lengths of the shared-memory FFT: N = 3^c 2^a.
+__host__ __device__ constexpr bool fft_len_ok(int n) {
+  return n < 1 ? false : (n % 3 == 0) ? fft_len_ok(n / 3) : ((n & (n - 1)) == 0);
+}
+// x mod N for x in [-2N, ...): the indices of cyclic shifts (a mask when N is a power of two)
+template <int N> AMM_DEV int wrapN(int x) {
+  if constexpr ((N & (N - 1)) == 0) return x & (N - 1);
+  else return (int)((unsigned)(x + 2 * N) % (unsigned)N);
+}
+// the conjugate partner n - t of component t (0 for t = 0), runtime n
+AMM_DEV int mirror_idx(int t, int n) { return t == 0 ? 0 : n - t; }
+// threads per CTA of the N-templated FFT kernels: the largest power of two dividing N, at most 512
+__host__ __device__ constexpr int fft_threads(int n) { return (n & -n) >= 512 ? 512 : (n & -n); }

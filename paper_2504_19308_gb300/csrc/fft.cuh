@@ -1,8 +1,9 @@
-// Shared-memory Stockham FFTs for power-of-two lengths (sm_103a).
+// Shared-memory Stockham FFTs for lengths N = 3^c 2^a (sm_103a).
 //
 // A CTA transforms S signals of length N that sit in shared memory, one after another,
-// each padded by fpad() (one float2 every 16).  Passes are radix 16 first, then one pass
-// of radix 2, 4 or 8 for the remaining factor.  Each pass is the Stockham autosort step
+// each padded by fpad() (one float2 every 16).  Passes are radix 3 for each factor 3, then
+// radix 16, then one pass of radix 2, 4 or 8 for the remaining factor.  Each pass is the
+// Stockham autosort step
 // (Stockham 1966; the GPU formulation of Govindaraju et al., SC 2008):
 //
 //     for every butterfly j in [0, N/R):  m = j mod Ns
@@ -95,8 +96,21 @@ template <bool INV> AMM_DEV void dft16(float2* v) {
   }
 }
 
+// DFT_3: X[k] = sum_n x[n] e^{-+2 pi i n k / 3}; with s = x1 + x2, d = x1 - x2:
+// X0 = x0 + s, X1,2 = x0 - s/2 -+ i (sqrt(3)/2) d  (forward; the inverse swaps the signs of i).
+#define AMM_H3 0.86602540378443865f  /* sqrt(3) / 2 */
+template <bool INV> AMM_DEV void dft3(float2& a0, float2& a1, float2& a2) {
+  const float2 s = cadd(a1, a2), d = csub(a1, a2);
+  const float2 m = make_float2(fmaf(-0.5f, s.x, a0.x), fmaf(-0.5f, s.y, a0.y));
+  const float2 r = INV ? make_float2(-AMM_H3 * d.y, AMM_H3 * d.x) : make_float2(AMM_H3 * d.y, -AMM_H3 * d.x);
+  a0 = cadd(a0, s);
+  a1 = cadd(m, r);
+  a2 = csub(m, r);
+}
+
 template <int R, bool INV> AMM_DEV void dft_r(float2* v) {
-  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
+  else if constexpr (R == 2) dft2<INV>(v[0], v[1]);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 8) dft8<INV>(v);
   else dft16<INV>(v);
@@ -121,7 +135,7 @@ AMM_DEV void stockham_pass(float2* buf, const float2* __restrict__ tw) {
     if (PER * NT == TOT || b < TOT) {
       const int s = b / NB, j = b % NB;
       const float2* x = buf + s * LD;
-      const int m = j & (NS - 1);
+      const int m = j % NS;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float2 a = x[fpad(j + r * NB)];
@@ -142,7 +156,7 @@ AMM_DEV void stockham_pass(float2* buf, const float2* __restrict__ tw) {
     if (PER * NT == TOT || b < TOT) {
       const int s = b / NB, j = b % NB;
       float2* y = buf + s * LD;
-      const int m = j & (NS - 1);
+      const int m = j % NS;
       const int base = (j / NS) * NS * R + m;
 #pragma unroll
       for (int r = 0; r < R; ++r) y[UNPAD_OUT ? base + r * NS : fpad(base + r * NS)] = v[i][r];
@@ -155,7 +169,7 @@ template <int N, int NS, int S, int NT, bool INV, bool UNPAD_LAST>
 struct FftPasses {
   static AMM_DEV void run(float2* buf, const float2* __restrict__ tw) {
     constexpr int LEFT = N / NS;
-    constexpr int R = (LEFT >= 16) ? 16 : LEFT;
+    constexpr int R = (LEFT % 3 == 0) ? 3 : (LEFT >= 16) ? 16 : LEFT;
     stockham_pass<N, R, NS, S, NT, INV, UNPAD_LAST && (NS * R == N)>(buf, tw);
     FftPasses<N, NS * R, S, NT, INV, UNPAD_LAST>::run(buf, tw);
   }
@@ -169,7 +183,7 @@ struct FftPasses<N, N, S, NT, INV, UNPAD_LAST> {
 // With UNPAD_LAST the result is left at plain indices (signal s still starts at s * padded len).
 template <int N, int S, int NT, bool INV, bool UNPAD_LAST = false>
 AMM_DEV void fft_smem(float2* buf, const float2* __restrict__ tw) {
-  static_assert((N & (N - 1)) == 0 && N >= 2, "power of two");
+  static_assert(fft_len_ok(N) && N >= 2, "N = 3^c 2^a");
   FftPasses<N, 1, S, NT, INV, UNPAD_LAST>::run(buf, tw);
 }
 

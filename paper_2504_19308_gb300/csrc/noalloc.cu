@@ -81,6 +81,8 @@ extern "C" amm_status_t amm_circulant_spectrum_noalloc(const float* A, int64_t n
   float* kpart = (float*)((unsigned char*)base + kTwBytes);
   const int nn = (int)n;
   const int nparts = nn / cd_cols_per_cta(nn);
+  if ((size_t)nparts * (nn / 2 + 1) * sizeof(float) > kPartBytes)
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "amm_circulant_spectrum_noalloc: key partials exceed the scratch");
   if ((e = cd_twiddles(tw, nn, st)) != cudaSuccess) return cuda_fail(e, "noalloc twiddles");
   if ((e = cd_spectrum(nn, A, lda, false, tw, (float2*)R, kpart, st)) != cudaSuccess)
     return cuda_fail(e, "noalloc spectrum");

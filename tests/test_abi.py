@@ -62,9 +62,11 @@ def test_argument_errors_without_gpu(lib):
     assert lib.amm_decompose(fake, 64, 64, 64, 0, 1, 0, ctypes.byref(opts), None, ctypes.byref(out)) == 1
     # lda < cols
     assert lib.amm_decompose(fake, 64, 64, 32, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
-    # circulant needs a square power-of-two
+    # circulant needs a square of a supported length
     assert lib.amm_decompose(fake, 64, 32, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
-    assert lib.amm_decompose(fake, 48, 48, 48, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
+    # circulant lengths are 2^a or 3 * 2^a: 40 and 80 are not
+    assert lib.amm_decompose(fake, 40, 40, 40, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
+    assert lib.amm_decompose(fake, 80, 80, 80, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
     # bad struct size
     opts.struct_size = 3
     assert lib.amm_decompose(fake, 64, 64, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1

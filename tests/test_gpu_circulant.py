@@ -157,10 +157,10 @@ def test_circulant_flat_spectrum_ties():
 
 def test_circulant_errors_do_not_launch():
     torch, amm = torch_cuda()
-    A = torch.zeros((48, 48), device="cuda")
+    A = torch.zeros((40, 40), device="cuda")
     with pytest.raises(amm.AmmError) as e:
         amm.decompose(A, "circulant", 4)
-    assert e.value.status == 2  # AMM_ERR_UNSUPPORTED_SIZE (not a power of two)
+    assert e.value.status == 2  # AMM_ERR_UNSUPPORTED_SIZE (neither 2^a nor 3 * 2^a)
     A = torch.zeros((64, 64), device="cuda")
     with pytest.raises(amm.AmmError):
         amm.decompose(A, "circulant", 0)
