@@ -330,14 +330,23 @@ def bf16_form(args, A, B, G, PH, fp32_ms, dist):
             "modes": "circulant: BF16 operands; rSVD: BF16 operands + BF16 tcgen05 GEMMs; sparsifiers: FP32"}
 
 
+def batch_sizes_for(count):
+    """Sizes of the batch: log-uniform in [128, 4096] rounded to the nearest of {2^a, 3 * 2^a}; the
+    Fourier-sparsifier items (every fourth) to the nearest power of two (its transform length)."""
+    methods = ["circulant", "svd", "fourier", "cycle"]
+    s3 = synth.batch_sizes(count, seed=0, radix3=True)
+    s2 = synth.batch_sizes(count, seed=0)
+    return [(s2[i] if methods[i % 4] == "fourier" else s3[i]) for i in range(count)], methods
+
+
 def batched_form(args, dev, dist, count=256):
-    """256 independent forward products of log-uniform sizes n in [128, 4096] (powers of two),
-    methods in rotation, k = ceil(n/32), FP32: one at a time on one stream versus one CUDA-graph
-    launch of the batch scheduler.  Operands: N(0,1) plus a rank-8 part, drawn on the device."""
+    """256 independent forward products of log-uniform sizes n in [128, 4096] (nearest 2^a or
+    3 * 2^a), methods in rotation, k = ceil(n/32), FP32: one at a time on one stream versus one
+    CUDA-graph launch of the batch scheduler.  Operands: N(0,1) plus a rank-8 part, drawn on the
+    device."""
     import torch
     import paper_2504_19308_gb300 as amm
-    sizes = synth.batch_sizes(count, seed=0)
-    methods = ["circulant", "svd", "fourier", "cycle"]
+    sizes, methods = batch_sizes_for(count)
     gen = torch.Generator(device=dev)
     gen.manual_seed(0)
     items = []
@@ -368,8 +377,9 @@ def batched_form(args, dev, dist, count=256):
     graph_ms = _device_ms(lambda: batch.run(use_graph=True), max(1, args.steps // 5), 1, dist)
     batch.close()
     fl = sum(2.0 * n ** 3 for n in sizes)
-    return {"products": count, "sizes": "n = 2^round(log2 U(ln 128, ln 4096)) (%d..%d), k = ceil(n/32), "
-            "methods in rotation, forward" % (min(sizes), max(sizes)),
+    return {"products": count, "sizes": "n = exp(U(ln 128, ln 4096)) rounded to the nearest of {2^a, 3 * 2^a} "
+            "(Fourier items: 2^a) (%d..%d, %d of the form 3 * 2^a), k = ceil(n/32), methods in rotation, forward"
+            % (min(sizes), max(sizes), sum(1 for v in sizes if v & (v - 1))),
             "eager_ms": eager_ms, "graph_ms": graph_ms, "speedup": eager_ms / graph_ms,
             "value": fl / (graph_ms * 1e-3) / 1e12, "unit": UNIT}
 

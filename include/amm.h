@@ -128,7 +128,9 @@ amm_status_t amm_opts_init(amm_opts_t* opts);
  *           read once: the handle keeps its own FP32 copy.)
  *   method  AMM_CIRCULANT and AMM_SPARSE_CYCLE need rows == cols (square, Section 2.3), except
  *           AMM_CIRCULANT with opts->block = b > 0, which takes any rows x cols in b x b blocks;
- *           the FFT length (n, or b) must be a power of two in [16, 8192].
+ *           lengths: circulant n (or b) = 2^a in [16, 8192] or 3 * 2^a in [48, 6144] (one radix-3
+ *           FFT pass); cycle sparsifier n a multiple of 4 in [16, 8192]; Fourier sparsifier inner
+ *           dimension a power of two in [16, 8192].
  *   k       number of kept components (1 <= k <= min(rows, cols) for AMM_SVD; <= b per block
  *           for blocked AMM_CIRCULANT; <= n else).
  *   opts    may be NULL (defaults).
@@ -195,7 +197,7 @@ amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info);
  * Thm 2.1 / Section 2.3, ||dA||^2 = ||A||^2 - n sum_{t in S} ||R_A[t]||^2; cycles: disjoint
  * supports).  Section 2.5 uses such truncation errors as the a-priori handle on the error of the
  * product (more components when the estimate is not satisfactory).
- *   A        DEVICE, n x n, lda, FP32 or BF16, n a power of two in [16, 8192]
+ *   A        DEVICE, n x n, lda, FP32 or BF16, n a length of the method (see amm_decompose)
  *   method   AMM_CIRCULANT or AMM_SPARSE_CYCLE (else AMM_ERR_NOT_IMPLEMENTED)
  *   tol      >= 0; *k_out in [1, n] (host)
  * Computes the spectrum / cycle norms into temporary device memory; synchronises `stream`.

@@ -124,6 +124,7 @@ extern "C" amm_status_t amm_debug_fail_alloc_after(int32_t n) {
 
 // ----------------------------------------------------------------------------- handles
 static bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+bool amm::cyc_length_ok(int64_t n) { return n >= 16 && n <= 8192 && n % 4 == 0; }
 bool amm::cd_length_ok(int64_t n) {
   return (pow2(n) && n >= 16 && n <= 8192) || (n % 3 == 0 && pow2(n / 3) && n >= 48 && n <= 6144);
 }
@@ -228,8 +229,8 @@ static cudaError_t widen_input(Handle* h) {
 
 static amm_status_t decompose_cycle(Handle* h, const amm_opts_t* o) {
   const int n = (int)h->rows;
-  if (!pow2(n) || n < 16 || n > 8192)
-    return fail(AMM_ERR_UNSUPPORTED_SIZE, "cycle: n=%d must be a power of two in [16, 8192]", n);
+  if (!cyc_length_ok(n))
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "cycle: n=%d must be a multiple of 4 in [16, 8192]", n);
   auto& c = h->cy;
   const int rp = cyc_rows_per_part(n);
   c.nparts = (n + rp - 1) / rp;
@@ -604,7 +605,7 @@ extern "C" amm_status_t amm_choose_k(const void* A, int64_t rows, int64_t cols, 
   if (rows != cols)
     return fail(AMM_ERR_UNSUPPORTED_SIZE, "amm_choose_k: A must be square (got %lldx%lld)", (long long)rows,
                 (long long)cols);
-  if (method == AMM_CIRCULANT ? !cd_length_ok(rows) : (!pow2(rows) || rows < 16 || rows > 8192))
+  if (method == AMM_CIRCULANT ? !cd_length_ok(rows) : !cyc_length_ok(rows))
     return fail(AMM_ERR_UNSUPPORTED_SIZE, "amm_choose_k: n=%lld is not a supported length for this method",
                 (long long)rows);
   if (lda < cols) return fail(AMM_ERR_INVALID_ARG, "amm_choose_k: lda < cols");

@@ -78,6 +78,8 @@ using Handle = ::amm_handle;
 amm_status_t fail(amm_status_t s, const char* fmt, ...);
 // circulant transform lengths: 2^a in [16, 8192] or 3 * 2^a in [48, 6144]
 bool cd_length_ok(int64_t n);
+// cycle-sparsifier lengths: multiples of 4 in [16, 8192]
+bool cyc_length_ok(int64_t n);
 amm_status_t cuda_fail(cudaError_t e, const char* what);
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
 void dev_free(void* p, cudaStream_t st);

@@ -42,3 +42,11 @@ template <int N> AMM_DEV int wrapN(int x) {
 AMM_DEV int mirror_idx(int t, int n) { return t == 0 ? 0 : n - t; }
 // threads per CTA of the N-templated FFT kernels: the largest power of two dividing N, at most 512
 __host__ __device__ constexpr int fft_threads(int n) { return (n & -n) >= 512 ? 512 : (n & -n); }
+// x mod n for x in [-n, 2n), runtime n; P2: n is a power of two (a mask)
+template <bool P2> AMM_DEV int cwrap(int x, int n) {
+  if constexpr (P2) return x & (n - 1);
+  else {
+    x += (x < 0) ? n : 0;
+    return x >= n ? x - n : x;
+  }
+}

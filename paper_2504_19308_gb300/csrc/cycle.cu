@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) cyc_keys_kernel(const float* __restrict__
   const int r0 = blockIdx.y * rows_per;
   float s = 0.f;
   for (int r = r0; r < min(n, r0 + rows_per); ++r) {
-    const float v = __ldg(A + (int64_t)r * lda + ((r - j) & (n - 1)));
+    const float v = __ldg(A + (int64_t)r * lda + cwrap<false>(r - j, n));
     s = fmaf(v, v, s);
   }
   part[(int64_t)blockIdx.y * n + j] = s;
@@ -39,7 +39,7 @@ __global__ void cyc_gather_kernel(const float* __restrict__ A, int64_t lda, int 
   const int u = blockIdx.y;
   const int t = sel[u];
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x)
-    cyc[(int64_t)u * n + l] = __ldg(A + (int64_t)((l + t) & (n - 1)) * lda + l);
+    cyc[(int64_t)u * n + l] = __ldg(A + (int64_t)cwrap<false>(l + t, n) * lda + l);
   if (blockIdx.x == 0 && threadIdx.x == 0) insel[t] = 1;
 }
 
@@ -49,6 +49,7 @@ constexpr int CYC_NT = 256;
 constexpr int CYC_RG = 8;    // rows (or columns) per thread per pass of the component loop
 
 // out(:, c0..c0+3) = sum_u cyc[u][r - t_u] B(r - t_u, c)
+template <bool P2>
 __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __restrict__ B, int64_t ldb, int n,
                                                                const int32_t* __restrict__ sel, int k,
                                                                const float* __restrict__ cyc, float* __restrict__ out,
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __re
       for (int i = 0; i < CYC_RG; ++i) {
         const int r = r0 + i * CYC_NT;
         if (r < n) {
-          const int l = (r - t) & (n - 1);
+          const int l = cwrap<P2>(r - t, n);
           const float a = __ldg(crow + l);
           const float4 b = bp[l];
           acc[i].x = fmaf(a, b.x, acc[i].x);
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __re
 
 // out(r0..r0+3, :) += sum_u dA(r, c + s_u) cycB[u][c]; dA = A with the kept cycles of A masked
 // (inselA), or A itself when inselA is NULL
+template <bool P2>
 __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __restrict__ A, int64_t lda, int n,
                                                                const unsigned char* __restrict__ inselA,
                                                                const int32_t* __restrict__ selB, int kb,
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __re
   for (int e = threadIdx.x; e < CYC_RW * n; e += CYC_NT) {
     const int rr = e / n, q = e % n, r = r0 + rr;
     float v = 0.f;
-    if (r < nrows && (inselA == nullptr || !inselA[(r - q) & (n - 1)])) v = __ldg(A + (int64_t)r * lda + q);
+    if (r < nrows && (inselA == nullptr || !inselA[cwrap<P2>(r - q, n)])) v = __ldg(A + (int64_t)r * lda + q);
     ar[e] = v;
   }
   __syncthreads();
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __re
     float acc[CYC_RW] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
     for (int u = 0; u < kb; ++u) {
-      const int q = (c + __ldg(selB + u)) & (n - 1);
+      const int q = cwrap<P2>(c + __ldg(selB + u), n);
       const float b = __ldg(cycB + (int64_t)u * n + c);
 #pragma unroll
       for (int rr = 0; rr < CYC_RW; ++rr) acc[rr] = fmaf(ar[rr * n + q], b, acc[rr]);
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __re
 // P_{S_B}(dA^T G)((l + s), l) = <dA(:, l + s), G(:, l)>; dA, dB are masked on the fly.
 
 // out(r0..r0+3, q) = sum_u G(r, q - s_u) cycB[u][q - s_u]
+template <bool P2>
 __global__ void __launch_bounds__(CYC_NT) cyc_bw_row_kernel(const float* __restrict__ G, int64_t ldg, int n,
                                                             const int32_t* __restrict__ selB, int kb,
                                                             const float* __restrict__ cycB, float* __restrict__ out,
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_row_kernel(const float* __restr
     float acc[CYC_RW] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
     for (int u = 0; u < kb; ++u) {
-      const int l = (q - __ldg(selB + u)) & (n - 1);
+      const int l = cwrap<P2>(q - __ldg(selB + u), n);
       const float b = __ldg(cycB + (int64_t)u * n + l);
 #pragma unroll
       for (int rr = 0; rr < CYC_RW; ++rr) acc[rr] = fmaf(gr[rr * n + l], b, acc[rr]);
@@ -165,6 +168,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_row_kernel(const float* __restr
 }
 
 // out(q, c0..c0+3) = sum_u cycA[u][q] G(q + t_u, c)
+template <bool P2>
 __global__ void __launch_bounds__(CYC_NT) cyc_bw_col_kernel(const float* __restrict__ G, int64_t ldg, int n,
                                                             const int32_t* __restrict__ selA, int ka,
                                                             const float* __restrict__ cycA, float* __restrict__ out,
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_col_kernel(const float* __restr
         const int q = qb + i * CYC_NT;
         if (q < n) {
           const float a = __ldg(arow + q);
-          const float4 g = gp[(q + t) & (n - 1)];
+          const float4 g = gp[cwrap<P2>(q + t, n)];
           acc[i].x = fmaf(a, g.x, acc[i].x);
           acc[i].y = fmaf(a, g.y, acc[i].y);
           acc[i].z = fmaf(a, g.z, acc[i].z);
@@ -211,6 +215,31 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_col_kernel(const float* __restr
   }
 }
 
+static bool pow2n(int n) { return (n & (n - 1)) == 0; }
+
+// dynamic shared memory of the apply kernels (both index forms), set once
+static cudaError_t cyc_attrs() {
+  static cudaError_t e = [] {
+    const int col = 8192 * (int)sizeof(float4) + 8192 * (int)sizeof(int), row = CYC_RW * 8192 * (int)sizeof(float);
+    const void* fs[8] = {(const void*)cyc_apply_col_kernel<true>, (const void*)cyc_apply_col_kernel<false>,
+                         (const void*)cyc_bw_col_kernel<true>, (const void*)cyc_bw_col_kernel<false>,
+                         (const void*)cyc_apply_row_kernel<true>, (const void*)cyc_apply_row_kernel<false>,
+                         (const void*)cyc_bw_row_kernel<true>, (const void*)cyc_bw_row_kernel<false>};
+    cudaError_t r = cudaSuccess;
+    for (int i = 0; i < 8 && r == cudaSuccess; ++i)
+      r = cudaFuncSetAttribute(fs[i], cudaFuncAttributeMaxDynamicSharedMemorySize, i < 4 ? col : row);
+    return r;
+  }();
+  return e;
+}
+
+// launch KERNEL<P2> with P2 = (n is a power of two)
+#define CYC_LAUNCH(KERNEL, GRID, SMEM, ...)                                     \
+  do {                                                                          \
+    if (pow2n(n)) KERNEL<true><<<(GRID), CYC_NT, (SMEM), st>>>(__VA_ARGS__);    \
+    else KERNEL<false><<<(GRID), CYC_NT, (SMEM), st>>>(__VA_ARGS__);            \
+  } while (0)
+
 // Selected diagonals of a product: out((l + t) mod n, l) += <X((l + t) mod n, :), Y(l, :)> for
 // t = sel[u], every l.  The projection terms of the cycle backward are of this form (the kept
 // cycles of G dB^T and of dA^T G, with the masks applied to dense residuals beforehand).  A warp
@@ -218,18 +247,20 @@ __global__ void __launch_bounds__(CYC_NT) cyc_bw_col_kernel(const float* __restr
 // serves CYC_DG products.  The t-groups are the fast grid dimension, so the CTAs in flight share
 // their rows Y(l, :) through L2.  Rows 16-byte aligned (n a multiple of 4, ldx, ldy too).
 constexpr int CYC_DG = 4;
+template <bool P2>
 __global__ void __launch_bounds__(256) cyc_diag_dot_kernel(const float* __restrict__ X, int64_t ldx,
                                                            const float* __restrict__ Y, int64_t ldy, int n,
                                                            const int32_t* __restrict__ sel, int k,
                                                            float* __restrict__ out, int64_t ldo) {
   const int g0 = blockIdx.x * CYC_DG;
   const int l = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (l >= n) return;  // whole warps
   const int nt = min(CYC_DG, k - g0);
   int r[CYC_DG];
   const float4* xr[CYC_DG];
 #pragma unroll
   for (int j = 0; j < CYC_DG; ++j) {
-    r[j] = (l + __ldg(sel + g0 + (j < nt ? j : 0))) & (n - 1);
+    r[j] = cwrap<P2>(l + __ldg(sel + g0 + (j < nt ? j : 0)), n);
     xr[j] = reinterpret_cast<const float4*>(X + (int64_t)r[j] * ldx);
   }
   const float4* yr = reinterpret_cast<const float4*>(Y + (int64_t)l * ldy);
@@ -260,7 +291,8 @@ __global__ void __launch_bounds__(256) cyc_diag_dot_kernel(const float* __restri
 static cudaError_t diag_dot(const float* X, int64_t ldx, const float* Y, int64_t ldy, int n, const int32_t* sel,
                             int k, float* out, int64_t ldo, const char* name, cudaStream_t st) {
   AMM_TRACE_W(name, st, 2.0 * k * (double)n * n, 4.0 * n * ((double)k + (k + CYC_DG - 1) / CYC_DG) * n, nullptr);
-  cyc_diag_dot_kernel<<<dim3((k + CYC_DG - 1) / CYC_DG, n / 8), 256, 0, st>>>(X, ldx, Y, ldy, n, sel, k, out, ldo);
+  auto kern = pow2n(n) ? cyc_diag_dot_kernel<true> : cyc_diag_dot_kernel<false>;
+  kern<<<dim3((k + CYC_DG - 1) / CYC_DG, (n + 7) / 8), 256, 0, st>>>(X, ldx, Y, ldy, n, sel, k, out, ldo);
   return cudaGetLastError();
 }
 
@@ -268,16 +300,7 @@ cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int
                          const float* cycA, const unsigned char* inselA, const int32_t* selB, int kb,
                          const float* cycB, const unsigned char* inselB, const float* G, int64_t ldg, float* dA,
                          int64_t ldda, float* dB, int64_t lddb, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)cyc_bw_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         CYC_RW * 8192 * (int)sizeof(float));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute((const void*)cyc_bw_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (8192 * (int)sizeof(float4) + 8192 * (int)sizeof(int)));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (cudaError_t ea = cyc_attrs(); ea != cudaSuccess) return ea;
   // dense scratch: the masked residual of the other operand, and for dB the transposes
   const int64_t nn = (int64_t)n * n;
   float* T = nullptr;
@@ -288,7 +311,7 @@ cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int
   if (dA) {
     {
       AMM_TRACE_W("cyc_bw_row", st, 2.0 * kb * (double)n * n, 8.0 * n * (double)n, nullptr);
-      cyc_bw_row_kernel<<<n / CYC_RW, CYC_NT, sizeof(float) * CYC_RW * n, st>>>(G, ldg, n, selB, kb, cycB, dA, ldda);
+      CYC_LAUNCH(cyc_bw_row_kernel, n / CYC_RW, sizeof(float) * CYC_RW * n, G, ldg, n, selB, kb, cycB, dA, ldda);
     }
     e = cudaGetLastError();
     // dA((l + t), l) += <G(l + t, :), dB(l, :)> for t in S_A, dB = B with its kept cycles zeroed
@@ -306,7 +329,8 @@ cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int
   if (dB && e == cudaSuccess) {
     {
       AMM_TRACE_W("cyc_bw_col", st, 2.0 * ka * (double)n * n, 8.0 * n * (double)n, nullptr);
-      cyc_bw_col_kernel<<<n / CYC_CW, CYC_NT, sizeof(float4) * n + sizeof(int) * ka, st>>>(G, ldg, n, selA, ka, cycA, dB, lddb);
+      CYC_LAUNCH(cyc_bw_col_kernel, n / CYC_CW, sizeof(float4) * n + sizeof(int) * ka, G, ldg, n, selA, ka, cycA, dB,
+                 lddb);
     }
     e = cudaGetLastError();
     // dB((l + s), l) += sum_r dA(r, l + s) G(r, l) = <dA^T(l + s, :), G^T(l, :)> for s in S_B
@@ -342,27 +366,18 @@ cudaError_t cyc_gather(int n, int k, const float* A, int64_t lda, const int32_t*
 cudaError_t cyc_apply(int n, const float* A, int64_t lda, const float* B, int64_t ldb, const int32_t* selA, int ka,
                       const float* cycA, const unsigned char* inselA, const int32_t* selB, int kb, const float* cycB,
                       float* C, int64_t ldc, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)cyc_apply_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (8192 * (int)sizeof(float4) + 8192 * (int)sizeof(int)));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute((const void*)cyc_apply_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               CYC_RW * 8192 * (int)sizeof(float));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (cudaError_t ea = cyc_attrs(); ea != cudaSuccess) return ea;
   {
     AMM_TRACE_W("cyc_apply_col", st, 2.0 * ka * (double)n * n, 8.0 * n * (double)n, nullptr);
-    cyc_apply_col_kernel<<<(n + CYC_CW - 1) / CYC_CW, CYC_NT, sizeof(float4) * n + sizeof(int) * ka, st>>>(B, ldb, n, selA, ka, cycA, C,
-                                                                                         ldc, n);
+    CYC_LAUNCH(cyc_apply_col_kernel, (n + CYC_CW - 1) / CYC_CW, sizeof(float4) * n + sizeof(int) * ka, B, ldb, n, selA,
+               ka, cycA, C, ldc, n);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   {
     AMM_TRACE_W("cyc_apply_row", st, 2.0 * kb * (double)n * n, 12.0 * n * (double)n, nullptr);
-    cyc_apply_row_kernel<<<(n + CYC_RW - 1) / CYC_RW, CYC_NT, sizeof(float) * CYC_RW * n, st>>>(
-        A, lda, n, inselA, selB, kb, cycB, C, ldc, n);
+    CYC_LAUNCH(cyc_apply_row_kernel, (n + CYC_RW - 1) / CYC_RW, sizeof(float) * CYC_RW * n, A, lda, n, inselA, selB,
+               kb, cycB, C, ldc, n);
   }
   return cudaGetLastError();
 }
@@ -379,7 +394,7 @@ __global__ void __launch_bounds__(256) cyc_residual_kernel(const float* __restri
   const float* a = A + (int64_t)r * lda + c0;
   float v[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = insel[(r - c0 - i) & (n - 1)] ? 0.f : __ldg(a + i);
+  for (int i = 0; i < 4; ++i) v[i] = insel[cwrap<false>(r - c0 - i, n)] ? 0.f : __ldg(a + i);
   float* d = D + (int64_t)r * ldd + c0;
   if ((((uintptr_t)d) & 15) == 0) {
     *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
@@ -389,26 +404,14 @@ __global__ void __launch_bounds__(256) cyc_residual_kernel(const float* __restri
   }
 }
 
-static cudaError_t cyc_attrs() {
-  static cudaError_t e = [] {
-    cudaError_t r = cudaFuncSetAttribute((const void*)cyc_apply_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (8192 * (int)sizeof(float4) + 8192 * (int)sizeof(int)));
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute((const void*)cyc_apply_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               CYC_RW * 8192 * (int)sizeof(float));
-    return r;
-  }();
-  return e;
-}
-
 // C = A_s X for X (n x p)
 cudaError_t cyc_left_apply(int n, const int32_t* selA, int ka, const float* cycA, const float* X, int64_t ldx,
                            int64_t p, float* C, int64_t ldc, cudaStream_t st) {
   cudaError_t e = cyc_attrs();
   if (e != cudaSuccess) return e;
   AMM_TRACE_W("cyc_apply_col", st, 2.0 * ka * (double)n * p, 8.0 * n * (double)p, nullptr);
-  cyc_apply_col_kernel<<<(unsigned)((p + CYC_CW - 1) / CYC_CW), CYC_NT, sizeof(float4) * n + sizeof(int) * ka, st>>>(X, ldx, n, selA, ka,
-                                                                                                  cycA, C, ldc, (int)p);
+  CYC_LAUNCH(cyc_apply_col_kernel, (unsigned)((p + CYC_CW - 1) / CYC_CW), sizeof(float4) * n + sizeof(int) * ka, X,
+             ldx, n, selA, ka, cycA, C, ldc, (int)p);
   return cudaGetLastError();
 }
 
@@ -418,8 +421,8 @@ cudaError_t cyc_right_apply(int n, const int32_t* selB, int kb, const float* cyc
   cudaError_t e = cyc_attrs();
   if (e != cudaSuccess) return e;
   AMM_TRACE_W("cyc_apply_row", st, 2.0 * kb * (double)n * m, 12.0 * n * (double)m, nullptr);
-  cyc_apply_row_kernel<<<(unsigned)((m + CYC_RW - 1) / CYC_RW), CYC_NT, sizeof(float) * CYC_RW * n, st>>>(
-      Y, ldy, n, nullptr, selB, kb, cycB, C, ldc, (int)m);
+  CYC_LAUNCH(cyc_apply_row_kernel, (unsigned)((m + CYC_RW - 1) / CYC_RW), sizeof(float) * CYC_RW * n, Y, ldy, n,
+             (const unsigned char*)nullptr, selB, kb, cycB, C, ldc, (int)m);
   return cudaGetLastError();
 }
 

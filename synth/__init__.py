@@ -164,9 +164,13 @@ def upstream_grad(m: int, p: int, seed: int = 0) -> np.ndarray:
     return rng(seed, STREAM_G).standard_normal((m, p))
 
 
-def batch_sizes(count: int = 256, seed: int = 0, lo: int = 128, hi: int = 4096):
-    """n_i = round(exp(U(ln lo, ln hi))) rounded to the nearest power of two (FFT sizes)."""
+def batch_sizes(count: int = 256, seed: int = 0, lo: int = 128, hi: int = 4096, radix3: bool = False):
+    """n_i = round(exp(U(ln lo, ln hi))) rounded to the nearest FFT size (in log distance): a power
+    of two, or with radix3 the nearest of {2^a, 3 * 2^a}.  The same draws for both roundings."""
     g = rng(seed, 7)
     u = g.uniform(math.log(lo), math.log(hi), count)
     n = np.exp(u)
-    return [int(2 ** round(math.log2(v))) for v in n]
+    if not radix3:
+        return [int(2 ** round(math.log2(v))) for v in n]
+    cands = sorted({2 ** a for a in range(4, 14)} | {3 * 2 ** a for a in range(4, 12)})
+    return [int(min(cands, key=lambda c: abs(math.log(c) - math.log(v)))) for v in n]

@@ -128,3 +128,53 @@ def test_cycle_bf16_operands():
     C = amm.approx_matmul(hA, hB)
     ref = O.cycle_matmul(as64(A), as64(B), k, sel_a=hA.selection(), sel_b=hB.selection())
     assert rel(C.double().cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("n,k", [(48, 3), (100, 5), (700, 7), (1000, 10), (3072, 31)])
+def test_cycle_general_n(n, k):
+    """Lengths that are not powers of two (multiples of 4), e.g. the paper's n = 700 experiments."""
+    torch, amm = torch_cuda()
+    a, b = S.general_times_toeplitz(n, seed=n)
+    _check(torch, amm, a, b, k, k + 1)
+
+
+@pytest.mark.parametrize("n,ka,kb", [(100, 3, 4), (700, 7, 7), (1000, 12, 9)])
+def test_cycle_backward_general_n(n, ka, kb):
+    torch, amm = torch_cuda()
+    g = S.rng(n + ka + kb, 2)
+    a = g.standard_normal((n, n)) + np.diag(np.full(n, 3.0))
+    b = S.toeplitz_uniform(n, g)
+    gr = g.standard_normal((n, n))
+    A, B, Gt = dev32(torch, a), dev32(torch, b), dev32(torch, gr)
+    hA = amm.decompose(A, "cycle", ka, "left")
+    hB = amm.decompose(B, "cycle", kb, "right")
+    dA, dB = amm.approx_matmul_backward(hA, hB, Gt)
+    ta = O.truncate_cycles(as64(A), ka, hA.selection())
+    tb = O.truncate_cycles(as64(B), kb, hB.selection())
+    rda, rdb = O.cycle_backward(ta, tb, as64(Gt))
+    assert rel(dA.double().cpu().numpy(), rda) <= TOL
+    assert rel(dB.double().cpu().numpy(), rdb) <= TOL
+
+
+@pytest.mark.parametrize("ma,mb,n", [("circulant", "cycle", 96), ("cycle", "circulant", 96), ("svd", "cycle", 100),
+                                     ("cycle", "svd", 100)])
+def test_mixed_general_n(ma, mb, n):
+    """Mixed products at lengths the Fourier sparsifier does not take (3 * 2^a, 4 x odd)."""
+    torch, amm = torch_cuda()
+    g = S.rng(n, 3)
+    a, b = g.standard_normal((n, n)) + 0.5, S.toeplitz_uniform(n, g)
+    A, B = dev32(torch, a), dev32(torch, b)
+
+    def side(method, X, role):
+        x64 = as64(X)
+        if method == "svd":
+            phi = S.sketch(n, 6, n, 0 if role == "left" else 1).astype(np.float32)
+            return amm.decompose(X, "svd", 6, role, sketch=dev32(torch, phi)), O.truncate_rsvd(x64, 6, phi.astype(np.float64))
+        h = amm.decompose(X, method, 6, role)
+        t = O.truncate_circulant(x64, 6, h.selection()) if method == "circulant" else O.truncate_cycles(x64, 6, h.selection())
+        return h, t
+
+    hA, ta = side(ma, A, "left")
+    hB, tb = side(mb, B, "right")
+    C = amm.approx_matmul(hA, hB)
+    assert rel(C.double().cpu().numpy(), O.mixed_product(ta, tb)) <= TOL
