@@ -333,12 +333,9 @@ def bf16_form(args, A, B, G, PH, fp32_ms, dist):
 
 
 def batch_sizes_for(count):
-    """Sizes of the batch: log-uniform in [128, 4096] rounded to the nearest of {2^a, 3 * 2^a}; the
-    Fourier-sparsifier items (every fourth) to the nearest power of two (its transform length)."""
-    methods = ["circulant", "svd", "fourier", "cycle"]
-    s3 = synth.batch_sizes(count, seed=0, radix3=True)
-    s2 = synth.batch_sizes(count, seed=0)
-    return [(s2[i] if methods[i % 4] == "fourier" else s3[i]) for i in range(count)], methods
+    """Sizes of the batch: log-uniform in [128, 4096] rounded to the nearest of {2^a, 3 * 2^a} (the
+    transform lengths every method takes)."""
+    return synth.batch_sizes(count, seed=0, radix3=True), ["circulant", "svd", "fourier", "cycle"]
 
 
 def batched_form(args, dev, dist, count=256):
@@ -380,7 +377,7 @@ def batched_form(args, dev, dist, count=256):
     batch.close()
     fl = sum(2.0 * n ** 3 for n in sizes)
     return {"products": count, "sizes": "n = exp(U(ln 128, ln 4096)) rounded to the nearest of {2^a, 3 * 2^a} "
-            "(Fourier items: 2^a) (%d..%d, %d of the form 3 * 2^a), k = ceil(n/32), methods in rotation, forward"
+            "(%d..%d, %d of the form 3 * 2^a), k = ceil(n/32), methods in rotation, forward"
             % (min(sizes), max(sizes), sum(1 for v in sizes if v & (v - 1))),
             "eager_ms": eager_ms, "graph_ms": graph_ms, "speedup": eager_ms / graph_ms,
             "value": fl / (graph_ms * 1e-3) / 1e12, "unit": UNIT}

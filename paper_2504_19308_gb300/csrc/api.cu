@@ -284,8 +284,9 @@ static amm_status_t decompose_fourier(Handle* h, const amm_opts_t* o) {
   const bool left = h->role == AMM_LEFT;
   f.n = (int)(left ? h->cols : h->rows);
   f.nvec = (int)(left ? h->rows : h->cols);
-  if (!pow2(f.n) || f.n < 16 || f.n > 8192)
-    return fail(AMM_ERR_UNSUPPORTED_SIZE, "fourier: inner dimension %d must be a power of two in [16, 8192]", f.n);
+  if (!cd_length_ok(f.n))
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "fourier: inner dimension %d must be 2^a in [16, 8192] or 3 * 2^a in [48, 6144]",
+                f.n);
   if (widen_input(h) != cudaSuccess) return cuda_fail(cudaGetLastError(), "fourier: BF16 input");
   if (o && o->forced_selection) return fail(AMM_ERR_NOT_IMPLEMENTED, "fourier: forced selection is not built");
   if (h->k > f.n) return fail(AMM_ERR_INVALID_ARG, "fourier: k=%lld > n=%d", (long long)h->k, f.n);

@@ -151,34 +151,10 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
       }
       __syncthreads();
       if (threadIdx.x < 32) {
-        // the bucket holding the need-th largest candidate: lane L sums buckets 255 - 8L - q,
-        // q = 0..7 (descending), a warp scan over the lanes finds the lane that crosses need
-        const int lane = threadIdx.x;
-        const unsigned need = s_need;
-        unsigned c[8], sum = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          c[q] = hist[255 - 8 * lane - q];
-          sum += c[q];
-        }
-        unsigned incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const unsigned hit = __ballot_sync(0xffffffffu, incl - sum < need && need <= incl);
-        const int src = hit ? __ffs(hit) - 1 : 31;
-        if (lane == src) {
-          unsigned acc = incl - sum;
-          int b = 255 - 8 * lane;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            b = 255 - 8 * lane - q;
-            if (acc + c[q] >= need || b == 0) break;
-            acc += c[q];
-          }
-          s_need = need - acc;
+        unsigned above;
+        const int b = radix_bucket_warp(hist, s_need, &above);
+        if (threadIdx.x == 0) {
+          s_need -= above;
           s_prefix = prefix | ((unsigned long long)b << shift);
         }
       }

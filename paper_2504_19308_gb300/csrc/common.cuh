@@ -50,3 +50,35 @@ template <bool P2> AMM_DEV int cwrap(int x, int n) {
     return x >= n ? x - n : x;
   }
 }
+
+// Radix selection step over a 256-bin histogram: the bin b where the count from the top (bin 255
+// down) first reaches need (need >= 1), and the count strictly above it in *above.  Called by one
+// full warp (lane L scans bins 255 - 8L - q, q = 0..7, a shuffle scan finds the crossing lane);
+// the result is valid on every lane.
+AMM_DEV int radix_bucket_warp(const unsigned* hist, unsigned need, unsigned* above) {
+  const int lane = threadIdx.x & 31;
+  unsigned c[8], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    c[q] = hist[255 - 8 * lane - q];
+    sum += c[q];
+  }
+  unsigned incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned hit = __ballot_sync(0xffffffffu, incl - sum < need && need <= incl);
+  const int src = hit ? __ffs(hit) - 1 : 31;
+  unsigned acc = incl - sum;
+  int b = 255 - 8 * lane;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    b = 255 - 8 * lane - q;
+    if (acc + c[q] >= need || b == 0) break;
+    acc += c[q];
+  }
+  *above = __shfl_sync(0xffffffffu, acc, src);
+  return __shfl_sync(0xffffffffu, b, src);
+}

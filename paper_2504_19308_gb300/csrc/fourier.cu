@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(NT) ft_transform_kernel(const float* __restric
     if (v >= nvec) continue;
     const float2* z = smem + (m >> 1) * LD;
     const float2 a = z[fpad(q)];
-    const float2 b = cconj(z[fpad((N - q) & (N - 1))]);
+    const float2 b = cconj(z[fpad(wrapN<N>(N - q))]);
     float2 x;
     if ((m & 1) == 0) x = cscale(cadd(a, b), 0.5f * sc);
     else { float2 d = csub(a, b); x = make_float2(0.5f * sc * d.y, -0.5f * sc * d.x); }
@@ -100,15 +100,13 @@ __global__ void __launch_bounds__(SEL_NT) ft_select_kernel(const float* __restri
       if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t need = s_need, acc = 0;
-      int b = 255;
-      for (; b > 0; --b) {
-        if (acc + hist[b] >= need) break;
-        acc += hist[b];
+    if (threadIdx.x < 32) {
+      unsigned above;
+      const int b = radix_bucket_warp(hist, s_need, &above);
+      if (threadIdx.x == 0) {
+        s_need -= above;
+        s_prefix = prefix | ((uint32_t)b << shift);
       }
-      s_need = need - acc;
-      s_prefix = prefix | ((uint32_t)b << shift);
     }
     mask |= 255u << shift;
     __syncthreads();
@@ -268,8 +266,8 @@ __global__ void __launch_bounds__(256) ft_t2_kernel(const float2* __restrict__ A
 
 // ============================================================================ launchers
 template <int N> struct FtCfg {
-  static constexpr int S = (N >= 8192) ? 2 : 4;
-  static constexpr int NT = (N >= 512) ? 512 : N;
+  static constexpr int S = (N >= 6144) ? 2 : 4;
+  static constexpr int NT = fft_threads(N);
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
 };
 
@@ -307,6 +305,14 @@ template <int N> struct FtOps {
     case 2048: { constexpr int NN = 2048; EXPR; } \
     case 4096: { constexpr int NN = 4096; EXPR; } \
     case 8192: { constexpr int NN = 8192; EXPR; } \
+    case 48: { constexpr int NN = 48; EXPR; }     \
+    case 96: { constexpr int NN = 96; EXPR; } \
+    case 192: { constexpr int NN = 192; EXPR; } \
+    case 384: { constexpr int NN = 384; EXPR; } \
+    case 768: { constexpr int NN = 768; EXPR; } \
+    case 1536: { constexpr int NN = 1536; EXPR; } \
+    case 3072: { constexpr int NN = 3072; EXPR; } \
+    case 6144: { constexpr int NN = 6144; EXPR; } \
     default: return cudaErrorInvalidValue;        \
   }
 
@@ -440,7 +446,7 @@ __global__ void __launch_bounds__(NT) ft_dense_kernel(const float2* __restrict__
           cn = make_float2(-cn.y, cn.x);
         }
         float2* zq = smem + s * LD + fpad(q);
-        float2* zn = smem + s * LD + fpad((N - q) & (N - 1));
+        float2* zn = smem + s * LD + fpad(wrapN<N>(N - q));
         *zq = cadd(*zq, cq);
         *zn = cadd(*zn, cn);
       }

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(NT) ft_bw_real_kernel(const float2* __restrict
   const int base = blockIdx.x * 2 * S;
   for (int e = threadIdx.x; e < (N / 2 + 1) * S; e += NT) {
     const int q = e / S, s = e % S;
-    const int r = (N - q) & (N - 1);
+    const int r = wrapN<N>(N - q);
     const int v0 = base + 2 * s, v1 = v0 + 1;
     float2 x0q = make_float2(0.f, 0.f), x0r = x0q, x1q = x0q, x1r = x0q;
     if (v0 < nvec) { x0q = X[(int64_t)q * nvec + v0]; x0r = X[(int64_t)r * nvec + v0]; }
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(NT) ft_bw_real_kernel(const float2* __restrict
 }
 
 template <int N> struct FtBwCfg {
-  static constexpr int S = (N >= 8192) ? 2 : 4;
-  static constexpr int NT = (N >= 512) ? 512 : N;
+  static constexpr int S = (N >= 6144) ? 2 : 4;
+  static constexpr int NT = fft_threads(N);
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
 };
 
@@ -254,6 +254,14 @@ template <int N> struct FtBwOps {
     case 2048: { constexpr int NN = 2048; EXPR; } \
     case 4096: { constexpr int NN = 4096; EXPR; } \
     case 8192: { constexpr int NN = 8192; EXPR; } \
+    case 48: { constexpr int NN = 48; EXPR; }     \
+    case 96: { constexpr int NN = 96; EXPR; } \
+    case 192: { constexpr int NN = 192; EXPR; } \
+    case 384: { constexpr int NN = 384; EXPR; } \
+    case 768: { constexpr int NN = 768; EXPR; } \
+    case 1536: { constexpr int NN = 1536; EXPR; } \
+    case 3072: { constexpr int NN = 3072; EXPR; } \
+    case 6144: { constexpr int NN = 6144; EXPR; } \
     default: return cudaErrorInvalidValue;        \
   }
 

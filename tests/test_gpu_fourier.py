@@ -135,3 +135,28 @@ def test_fourier_bf16_operands():
     C = amm.approx_matmul(hA, hB)
     ref = O.fourier_matmul(as64(A), as64(B), k, forced_a=hA.selection(), forced_b=hB.selection())
     assert rel(C.double().cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("m,n,p,k", [(40, 48, 30, 3), (100, 96, 77, 5), (200, 384, 150, 9), (64, 1536, 96, 16),
+                                     (48, 3072, 40, 31)])
+def test_fourier_radix3_lengths(m, n, p, k):
+    """Inner dimensions n = 3 * 2^a (a radix-3 pass in the row / column transforms)."""
+    torch, amm = torch_cuda()
+    g = S.rng(m + n + p, 1)
+    _check(torch, amm, g.standard_normal((m, n)) + 0.3, g.uniform(0, 1, (n, p)), k)
+
+
+@pytest.mark.parametrize("m,n,p,ka,kb", [(50, 192, 60, 4, 6), (96, 768, 80, 8, 8)])
+def test_fourier_backward_radix3(m, n, p, ka, kb):
+    torch, amm = torch_cuda()
+    g = S.rng(m + n + p, 2)
+    a, b, gr = g.standard_normal((m, n)), g.uniform(0, 1, (n, p)), g.standard_normal((m, p))
+    A, B, G = dev32(torch, a), dev32(torch, b), dev32(torch, gr)
+    hA = amm.decompose(A, "fourier", ka, "left")
+    hB = amm.decompose(B, "fourier", kb, "right")
+    dA, dB = amm.approx_matmul_backward(hA, hB, G)
+    ta = O.truncate_fourier_left(as64(A), ka, forced=hA.selection())
+    tb = O.truncate_fourier_right(as64(B), kb, forced=hB.selection())
+    rda, rdb = O.fourier_backward(ta, tb, as64(G))
+    assert rel(dA.double().cpu().numpy(), rda) <= TOL
+    assert rel(dB.double().cpu().numpy(), rdb) <= TOL

@@ -41,7 +41,7 @@ def _case(ma, mb, a, b, k, seed):
 
 
 @pytest.mark.parametrize("ma,mb", PAIRS)
-@pytest.mark.parametrize("n,k", [(64, 5), (256, 9)])
+@pytest.mark.parametrize("n,k", [(64, 5), (256, 9), (96, 7)])
 def test_mixed_square(ma, mb, n, k):
     g = S.rng(n + k, 7)
     a = g.standard_normal((n, n)) + 0.5          # a dominant zero component: odd k splits a pair
