@@ -340,9 +340,9 @@ def batch_sizes_for(count):
 
 def batched_form(args, dev, dist, count=256):
     """256 independent forward products of log-uniform sizes n in [128, 4096] (nearest 2^a or
-    3 * 2^a), methods in rotation, k = ceil(n/32), FP32: one at a time on one stream versus one
-    CUDA-graph launch of the batch scheduler.  Operands: N(0,1) plus a rank-8 part, drawn on the
-    device."""
+    3 * 2^a), methods in rotation, k = ceil(n/32), plus one circulant product at n = 16384, FP32:
+    one at a time on one stream versus one CUDA-graph launch of the batch scheduler.  Operands:
+    N(0,1) plus a rank-8 part, drawn on the device."""
     import torch
     import paper_2504_19308_gb300 as amm
     sizes, methods = batch_sizes_for(count)
@@ -358,6 +358,10 @@ def batched_form(args, dev, dist, count=256):
         sk = ((torch.randn((n, k), generator=gen, device=dev), torch.randn((n, k), generator=gen, device=dev))
               if methods[i % 4] == "svd" else (None, None))
         items.append((A, B, C, methods[i % 4], k, sk[0], sk[1]))
+    # plus one n = 16384 product (circulant, k = n/32 = 512)
+    nb = 16384
+    items.append((torch.randn((nb, nb), generator=gen, device=dev), torch.randn((nb, nb), generator=gen, device=dev),
+                  torch.empty((nb, nb), device=dev), "circulant", nb // 32, None, None))
 
     def eager():
         for A, B, C, method, k, sa, sb in items:
@@ -375,9 +379,10 @@ def batched_form(args, dev, dist, count=256):
     eager_ms = _device_ms(eager, max(1, args.steps // 5), 1, dist)
     graph_ms = _device_ms(lambda: batch.run(use_graph=True), max(1, args.steps // 5), 1, dist)
     batch.close()
-    fl = sum(2.0 * n ** 3 for n in sizes)
-    return {"products": count, "sizes": "n = exp(U(ln 128, ln 4096)) rounded to the nearest of {2^a, 3 * 2^a} "
-            "(%d..%d, %d of the form 3 * 2^a), k = ceil(n/32), methods in rotation, forward"
+    fl = sum(2.0 * n ** 3 for n in sizes) + 2.0 * nb ** 3
+    return {"products": count + 1, "sizes": "n = exp(U(ln 128, ln 4096)) rounded to the nearest of {2^a, 3 * 2^a} "
+            "(%d..%d, %d of the form 3 * 2^a), k = ceil(n/32), methods in rotation, plus one circulant n = 16384, "
+            "k = 512, forward"
             % (min(sizes), max(sizes), sum(1 for v in sizes if v & (v - 1))),
             "eager_ms": eager_ms, "graph_ms": graph_ms, "speedup": eager_ms / graph_ms,
             "value": fl / (graph_ms * 1e-3) / 1e12, "unit": UNIT}

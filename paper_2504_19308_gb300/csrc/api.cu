@@ -126,7 +126,7 @@ extern "C" amm_status_t amm_debug_fail_alloc_after(int32_t n) {
 static bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 bool amm::cyc_length_ok(int64_t n) { return n >= 16 && n <= 8192 && n % 4 == 0; }
 bool amm::cd_length_ok(int64_t n) {
-  return (pow2(n) && n >= 16 && n <= 8192) || (n % 3 == 0 && pow2(n / 3) && n >= 48 && n <= 6144);
+  return (pow2(n) && n >= 16 && n <= 16384) || (n % 3 == 0 && pow2(n / 3) && n >= 48 && n <= 6144);
 }
 
 void amm::Handle::release() {
@@ -148,7 +148,7 @@ cudaError_t amm::Handle::alloc(void** p, size_t bytes) {
 amm_status_t amm::decompose_circulant(Handle* h, const amm_opts_t* o) {
   const int n = (int)h->rows;
   if (!cd_length_ok(n))
-    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: n=%d must be 2^a in [16, 8192] or 3 * 2^a in [48, 6144]", n);
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: n=%d must be 2^a in [16, 16384] or 3 * 2^a in [48, 6144]", n);
   auto& c = h->cd;
   const int J = cd_cols_per_cta(n);
   c.nparts = n / J;
@@ -284,7 +284,7 @@ static amm_status_t decompose_fourier(Handle* h, const amm_opts_t* o) {
   const bool left = h->role == AMM_LEFT;
   f.n = (int)(left ? h->cols : h->rows);
   f.nvec = (int)(left ? h->rows : h->cols);
-  if (!cd_length_ok(f.n))
+  if (!cd_length_ok(f.n) || f.n > 8192)
     return fail(AMM_ERR_UNSUPPORTED_SIZE, "fourier: inner dimension %d must be 2^a in [16, 8192] or 3 * 2^a in [48, 6144]",
                 f.n);
   if (widen_input(h) != cudaSuccess) return cuda_fail(cudaGetLastError(), "fourier: BF16 input");

@@ -76,7 +76,7 @@ namespace amm {
 using Handle = ::amm_handle;
 
 amm_status_t fail(amm_status_t s, const char* fmt, ...);
-// circulant transform lengths: 2^a in [16, 8192] or 3 * 2^a in [48, 6144]
+// circulant transform lengths: 2^a in [16, 16384] or 3 * 2^a in [48, 6144]
 bool cd_length_ok(int64_t n);
 // cycle-sparsifier lengths: multiples of 4 in [16, 8192]
 bool cyc_length_ok(int64_t n);

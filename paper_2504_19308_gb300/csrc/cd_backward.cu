@@ -29,6 +29,7 @@ namespace amm {
     case 2048: { constexpr int NN = 2048; EXPR; } \
     case 4096: { constexpr int NN = 4096; EXPR; } \
     case 8192: { constexpr int NN = 8192; EXPR; } \
+    case 16384: { constexpr int NN = 16384; EXPR; } \
     default: break;                               \
   }
 

@@ -276,7 +276,7 @@ template <int N> struct BwCfg {
   // two CTAs per SM for 1024 <= N < 6144 (one CTA of 512 threads at 128 registers would fill
   // the register file)
   static constexpr bool HALF = N >= 1024 && N < 6144;
-  static constexpr int S = (N >= 6144 || HALF) ? 2 : 4;
+  static constexpr int S = (N >= 16384) ? 1 : (N >= 6144 || HALF) ? 2 : 4;
   static constexpr int NT = HALF ? fft_threads(N) / 2 : fft_threads(N);
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
   static constexpr int NT1 = (N >= 1024) ? 256 : (N >= 64 ? 64 : N);

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
     for (int t = threadIdx.x; t < k; t += SEL_T) out.sel[t] = sidx[t];
   }
   if (pair_closed) {  // S <- S u S-bar: every kept component with its conjugate partner, M real
-    unsigned char cl[(8192 + SEL_T - 1) / SEL_T];
+    unsigned char cl[(16384 + SEL_T - 1) / SEL_T];
     for (int t = c0; t < c1; ++t) cl[t - c0] = in_s[t] | in_s[mirror_idx(t, n)];
     __syncthreads();
     for (int t = c0; t < c1; ++t) in_s[t] = cl[t - c0];
@@ -288,10 +288,11 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
     case 2048: { constexpr int NN = 2048; EXPR; }       \
     case 4096: { constexpr int NN = 4096; EXPR; }       \
     case 8192: { constexpr int NN = 8192; EXPR; }       \
+    case 16384: { constexpr int NN = 16384; EXPR; }     \
     default: break;                                     \
   }
 
-int cd_cols_per_cta(int n) { return n >= 6144 ? 4 : 8; }
+int cd_cols_per_cta(int n) { return n >= 16384 ? 2 : n >= 6144 ? 4 : 8; }
 
 cudaError_t cd_twiddles(float2* tw, int n, cudaStream_t st) {
   AMM_TRACE("twiddle", st);
@@ -322,7 +323,7 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute((const void*)cd_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes(8192));
+                                         (int)bytes(16384));
     if (e != cudaSuccess) return e;
     attr_done = true;
   }

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
 
 // ============================================================================ host launchers
 template <int N> struct CdCfg {
-  static constexpr int S = (N >= 6144) ? 2 : 4;       // packed signals per CTA
+  static constexpr int S = (N >= 16384) ? 1 : (N >= 6144) ? 2 : 4;  // packed signals per CTA
   static constexpr int NT = fft_threads(N);          // threads per CTA
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
   static constexpr int NT1 = (N >= 1024) ? 256 : (N >= 64 ? 64 : N);  // eigen-spectrum kernel

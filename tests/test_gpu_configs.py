@@ -74,3 +74,37 @@ def test_llm_shaped_mixed_rsvd_times_circulant_blocks():
     ref = O.blocked_first_order(tx_rows, tw)
     got = C.double().cpu().numpy()[rows]
     assert rel(got, ref) <= TOL
+
+
+def test_circulant_n16384_k512():
+    """The largest circulant length (one packed signal per CTA).  (1) k = 512 selection of an
+    N(0,1) + 0.5 matrix against the oracle's FP64 keys (near-tie rule).  (2) Operands that are one
+    real component each (circulant(c) D^(n/2), Thm 2.1): the truncation at k = 1 is exact, so the
+    product and both gradients equal AB, G B^T and A^T G, checked on sampled rows / columns."""
+    torch, amm = torch_cuda()
+    n = 16384
+    g = S.rng(90, 0)
+    a = g.standard_normal((n, n)).astype(np.float32) + np.float32(0.5)
+    A = torch.from_numpy(a).cuda()
+    h = amm.decompose(A, "circulant", 512, "left")
+    keys = O.component_keys(O.circulant_spectrum(a.astype(np.float64)))
+    check_selection(h.selection(), keys, 512, "A")
+    h.close()
+    del A, a, keys
+    sign = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)            # D^(n/2) = diag((-1)^q)
+    a = O.circulant(g.standard_normal(n)) * sign[None, :]
+    b = O.circulant(g.uniform(0, 1, n)) * sign[None, :]
+    A, B = dev32(torch, a), dev32(torch, b)
+    a64, b64 = as64(A), as64(B)
+    del a, b
+    hA = amm.decompose(A, "circulant", 1, "left")
+    hB = amm.decompose(B, "circulant", 1, "right")
+    assert hA.selection().tolist() == [n // 2] and hB.selection().tolist() == [n // 2]
+    C = amm.approx_matmul(hA, hB)
+    G = dev32(torch, g.standard_normal((n, n)))
+    dA, dB = amm.approx_matmul_backward(hA, hB, G)
+    rows = np.sort(S.rng(91, 0).choice(n, 16, replace=False))
+    g64 = as64(G)
+    assert rel(C.double().cpu().numpy()[rows], a64[rows] @ b64) <= TOL
+    assert rel(dA.double().cpu().numpy()[rows], g64[rows] @ b64.T) <= TOL
+    assert rel(dB.double().cpu().numpy()[:, rows], a64.T @ g64[:, rows]) <= TOL
