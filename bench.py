@@ -358,10 +358,6 @@ def batched_form(args, dev, dist, count=256):
         sk = ((torch.randn((n, k), generator=gen, device=dev), torch.randn((n, k), generator=gen, device=dev))
               if methods[i % 4] == "svd" else (None, None))
         items.append((A, B, C, methods[i % 4], k, sk[0], sk[1]))
-    # plus one n = 16384 product (circulant, k = n/32 = 512)
-    nb = 16384
-    items.append((torch.randn((nb, nb), generator=gen, device=dev), torch.randn((nb, nb), generator=gen, device=dev),
-                  torch.empty((nb, nb), device=dev), "circulant", nb // 32, None, None))
 
     def eager():
         for A, B, C, method, k, sa, sb in items:
@@ -379,10 +375,27 @@ def batched_form(args, dev, dist, count=256):
     eager_ms = _device_ms(eager, max(1, args.steps // 5), 1, dist)
     graph_ms = _device_ms(lambda: batch.run(use_graph=True), max(1, args.steps // 5), 1, dist)
     batch.close()
-    fl = sum(2.0 * n ** 3 for n in sizes) + 2.0 * nb ** 3
-    return {"products": count + 1, "sizes": "n = exp(U(ln 128, ln 4096)) rounded to the nearest of {2^a, 3 * 2^a} "
-            "(%d..%d, %d of the form 3 * 2^a), k = ceil(n/32), methods in rotation, plus one circulant n = 16384, "
-            "k = 512, forward"
+    fl = sum(2.0 * n ** 3 for n in sizes)
+    # plus one n = 16384 product (circulant, k = n/32 = 512), timed on its own: inside the batch
+    # it would hide the launch overheads the graph removes
+    nb = 16384
+    Ab = torch.randn((nb, nb), generator=gen, device=dev)
+    Bb = torch.randn((nb, nb), generator=gen, device=dev)
+    Cb = torch.empty((nb, nb), device=dev)
+
+    def big():
+        hA = amm.decompose(Ab, "circulant", nb // 32, "left")
+        hB = amm.decompose(Bb, "circulant", nb // 32, "right")
+        amm.approx_matmul(hA, hB, out=Cb)
+        hA.close()
+        hB.close()
+
+    big_ms = _device_ms(big, max(1, args.steps // 5), 1, dist)
+    del Ab, Bb, Cb
+    return {"products": count, "n16384_circulant_k512_ms": big_ms,
+            "n16384_value": 2.0 * nb ** 3 / (big_ms * 1e-3) / 1e12, "sizes": "n = exp(U(ln 128, ln 4096)) rounded to the nearest of {2^a, 3 * 2^a} "
+            "(%d..%d, %d of the form 3 * 2^a), k = ceil(n/32), methods in rotation, forward; the extra "
+            "n = 16384 product (circulant, k = 512) timed alone"
             % (min(sizes), max(sizes), sum(1 for v in sizes if v & (v - 1))),
             "eager_ms": eager_ms, "graph_ms": graph_ms, "speedup": eager_ms / graph_ms,
             "value": fl / (graph_ms * 1e-3) / 1e12, "unit": UNIT}
