@@ -127,6 +127,7 @@ def run_amm(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     amm.load_library()
+    amm.set_autotune(True)  # kernel variants timed on first use, i.e. in the warm-up steps
     a, b, phis, g = make_inputs()
     A = torch.from_numpy(a).to(dev)
     B = torch.from_numpy(b).to(dev)
@@ -590,7 +591,9 @@ def config_block():
                         "k=16/64/256, rSVD k=32/128, Fourier and cycle sparsifiers top 1%% (k=%d)" % K_SPARSE,
             "n": N, "products": ["%s k=%d %s" % (m, k, "fwd+bwd" if b else "fwd") for m, k, b in PRODUCTS],
             "l2": "no flush: each step touches ~2 GB (inputs, spectra, residuals, GEMM panels) > 129 MB L2",
-            "parallelism": "replicas"}
+            "parallelism": "replicas",
+            "autotune": "on: the spectral-apply variant (2 or 4 packed signals per CTA) of each length, direction "
+                        "and element type is timed in the warm-up and the fastest kept"}
 
 
 def main():

@@ -296,6 +296,17 @@ amm_status_t amm_debug_gemm_tn(int32_t mode, int64_t M, int64_t N, int64_t K, fl
                                float* C, int64_t ldc, int32_t* dev_err, void* stream);
 
 /*
+ * Autotuning of kernel variants (off by default).  With on != 0, the first call of a kernel that
+ * has several compiled variants (the circulant spectral apply: two or four packed signals per CTA)
+ * for a given length, direction and element type times each variant on that call's own operands
+ * (into scratch memory; the call's result is computed afterwards by the fastest) and keeps the
+ * choice for the process.  The variants compute every output with the same operations, so the
+ * choice never changes results.  Timing synchronises the stream once per new key; calls made while
+ * their stream is being captured into a CUDA graph use the current choice without timing.
+ */
+amm_status_t amm_set_autotune(int32_t on);
+
+/*
  * Fault injection for tests: the n-th device allocation from now on (1-based) fails with
  * AMM_ERR_OOM; 0 disables.  Affects only this process.
  */

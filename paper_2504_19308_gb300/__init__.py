@@ -4,4 +4,4 @@ Python front end of libamm (include/amm.h): arXiv 2504.19308, M = A~ B + dA B~.
 """
 from .amm import (AmmError, Batch, ApproxMatmulFn, Handle, approx_matmul, approx_matmul_autograd,  # noqa: F401
                   approx_matmul_backward, choose_k, decompose, decompose_to_tolerance, error_estimate,
-                  load_library, LIB_PATH)
+                  load_library, set_autotune, LIB_PATH)

@@ -49,6 +49,7 @@ SIGNATURES = {
     "amm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "amm_last_error": (ctypes.c_char_p, []),
     "amm_version": (ctypes.c_int32, []),
+    "amm_set_autotune": (ctypes.c_int, [ctypes.c_int32]),
     "amm_opts_init": (ctypes.c_int, [ctypes.POINTER(Opts)]),
     "amm_decompose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int64, ctypes.POINTER(Opts), ctypes.c_void_p,
@@ -235,6 +236,12 @@ def approx_matmul(hA: Handle, hB: Handle, out: Optional[torch.Tensor] = None) ->
     _check(load_library().amm_approx_matmul(hA.ptr, hB.ptr, out.data_ptr(), out.stride(0),
                                             _stream_ptr(out.device)), "amm_approx_matmul")
     return out
+
+
+def set_autotune(on: bool = True):
+    """amm_set_autotune: time the compiled variants of tunable kernels on first use and keep the
+    fastest (results do not depend on the choice)."""
+    _check(load_library().amm_set_autotune(1 if on else 0), "amm_set_autotune")
 
 
 def choose_k(A: torch.Tensor, method: str, tol: float) -> int:

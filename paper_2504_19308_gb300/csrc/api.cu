@@ -116,6 +116,16 @@ extern "C" amm_status_t amm_opts_init(amm_opts_t* o) {
   return AMM_OK;
 }
 
+namespace {
+std::atomic<bool> g_autotune{false};
+}
+bool amm::amm_autotune_enabled() { return g_autotune.load(); }
+
+extern "C" amm_status_t amm_set_autotune(int32_t on) {
+  g_autotune.store(on != 0);
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_debug_fail_alloc_after(int32_t n) {
   if (n < 0) return fail(AMM_ERR_INVALID_ARG, "amm_debug_fail_alloc_after: n < 0");
   g_fail_after.store(n);

@@ -80,6 +80,8 @@ amm_status_t fail(amm_status_t s, const char* fmt, ...);
 bool cd_length_ok(int64_t n);
 // cycle-sparsifier lengths: multiples of 4 in [16, 8192]
 bool cyc_length_ok(int64_t n);
+// amm_set_autotune: kernel variants are timed on first use and the fastest kept
+bool amm_autotune_enabled();
 amm_status_t cuda_fail(cudaError_t e, const char* what);
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
 void dev_free(void* p, cudaStream_t st);

@@ -20,6 +20,9 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "circulant_kernels.cuh"
 #include "common.cuh"
 #include "fft.cuh"
@@ -291,6 +294,23 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
     case 16384: { constexpr int NN = 16384; EXPR; }     \
     default: break;                                     \
   }
+
+// ---------------------------------------------------------------------------- autotuner table
+namespace {
+std::mutex g_tune_mu;
+std::unordered_map<int, int> g_tune;
+}  // namespace
+
+int cd_tune_get(int key) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  return it == g_tune.end() ? -1 : it->second;
+}
+
+void cd_tune_set(int key, int variant) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = variant;
+}
 
 int cd_cols_per_cta(int n) { return n >= 16384 ? 2 : n >= 6144 ? 4 : 8; }
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include "api_internal.h"
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.h"
@@ -316,10 +317,19 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
 }
 
 // ============================================================================ host launchers
+// autotuner table of the spectral-apply variants (circulant.cu): -1 = not timed yet
+int cd_tune_get(int key);
+void cd_tune_set(int key, int variant);
+
 template <int N> struct CdCfg {
   static constexpr int S = (N >= 16384) ? 1 : (N >= 6144) ? 2 : 4;  // packed signals per CTA
   static constexpr int NT = fft_threads(N);          // threads per CTA
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
+  // second spectral-apply variant for the autotuner: half the packed signals and threads per CTA
+  // (more, smaller CTAs per SM; each coefficient load serves half as many signals)
+  static constexpr bool HAS_V1 = S >= 2 && NT >= 64;
+  static constexpr int S1 = HAS_V1 ? S / 2 : S, NT1A = HAS_V1 ? NT / 2 : NT;
+  static constexpr size_t SMEM1 = sizeof(float2) * S1 * fft_padded_len(N);
   static constexpr int NT1 = (N >= 1024) ? 256 : (N >= 64 ? 64 : N);  // eigen-spectrum kernel
 };
 
@@ -338,6 +348,12 @@ template <int N> static cudaError_t set_smem_attrs() {
   s((const void*)cd_apply_kernel<N, C::S, C::NT, false, false, __nv_bfloat16>, C::SMEM);
   s((const void*)cd_apply_kernel<N, C::S, C::NT, false, true, float>, C::SMEM);
   s((const void*)cd_apply_kernel<N, C::S, C::NT, true, false, float>, C::SMEM);
+  s((const void*)cd_apply_kernel<N, C::S1, C::NT1A, false, false, float>, C::SMEM1);
+  s((const void*)cd_apply_kernel<N, C::S1, C::NT1A, true, true, float>, C::SMEM1);
+  s((const void*)cd_apply_kernel<N, C::S1, C::NT1A, true, true, __nv_bfloat16>, C::SMEM1);
+  s((const void*)cd_apply_kernel<N, C::S1, C::NT1A, false, false, __nv_bfloat16>, C::SMEM1);
+  s((const void*)cd_apply_kernel<N, C::S1, C::NT1A, false, true, float>, C::SMEM1);
+  s((const void*)cd_apply_kernel<N, C::S1, C::NT1A, true, false, float>, C::SMEM1);
   s((const void*)cd_eigen_kernel<N, CdCfg<N>::NT1>, sizeof(float2) * fft_padded_len(N));
   return e;
 }
@@ -374,17 +390,17 @@ template <int N> struct CdOps {
                                                                               ldx, accumulate);
     return cudaGetLastError();
   }
-  static cudaError_t apply(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
-                           const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
-                           const int32_t* gate1, float* out, int64_t ldo, int accumulate, int rev, cudaStream_t st) {
-    static cudaError_t attr = set_smem_attrs<N>();
-    if (attr != cudaSuccess) return attr;
-    dim3 grid((unsigned)((nvec + 2 * C::S - 1) / (2 * C::S)));
+  template <int V>
+  static cudaError_t apply_v(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
+                             const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
+                             const int32_t* gate1, float* out, int64_t ldo, int accumulate, int rev, cudaStream_t st) {
+    constexpr int S_ = V ? C::S1 : C::S, NT_ = V ? C::NT1A : C::NT;
+    constexpr size_t SM_ = V ? C::SMEM1 : C::SMEM;
+    dim3 grid((unsigned)((nvec + 2 * S_ - 1) / (2 * S_)));
     const bool r = rev < 0 ? row : rev != 0;
 #define AMM_APPLY_LAUNCH(ROW_, REV_, T_)                                                                    \
-  cd_apply_kernel<N, C::S, C::NT, ROW_, REV_, T_><<<grid, C::NT, C::SMEM, st>>>((const T_*)X, ldx, tw, list, Lc, \
-                                                                                count, gate0, gate1, out, ldo,  \
-                                                                                accumulate, (int)nvec)
+  cd_apply_kernel<N, S_, NT_, ROW_, REV_, T_><<<grid, NT_, SM_, st>>>((const T_*)X, ldx, tw, list, Lc, count, gate0, \
+                                                                      gate1, out, ldo, accumulate, (int)nvec)
     if (row && r) {
       if (bf16) AMM_APPLY_LAUNCH(true, true, __nv_bfloat16);
       else AMM_APPLY_LAUNCH(true, true, float);
@@ -400,6 +416,58 @@ template <int N> struct CdOps {
     }
 #undef AMM_APPLY_LAUNCH
     return cudaGetLastError();
+  }
+  // The variant for this (N, direction, coefficient pairing, element type): the tuned choice when
+  // the autotuner has timed it, else the default.  With the autotuner on and the stream not being
+  // captured, an untimed key is timed here once on the call's own operands, writing a scratch output.
+  static int variant(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
+                     const int32_t* list, const float2* Lc, const int32_t* count, int rev, cudaStream_t st) {
+    if (!C::HAS_V1) return 0;
+    const int key = N * 8 + (row ? 4 : 0) + ((rev < 0 ? row : rev != 0) ? 2 : 0) + (bf16 ? 1 : 0);
+    const int v = cd_tune_get(key);
+    if (v >= 0 || !amm_autotune_enabled()) return v < 0 ? 0 : v;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
+    float* scratch = nullptr;
+    if (dev_alloc((void**)&scratch, sizeof(float) * (size_t)N * nvec, st) != cudaSuccess) return 0;
+    const int64_t lds = row ? N : nvec;
+    float best = 0.f;
+    int pick = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int cand = 0; cand < 2 && e == cudaSuccess; ++cand) {
+      auto run = [&]() {
+        return cand ? apply_v<1>(row, X, ldx, bf16, nvec, tw, list, Lc, count, nullptr, nullptr, scratch, lds, 0, rev, st)
+                    : apply_v<0>(row, X, ldx, bf16, nvec, tw, list, Lc, count, nullptr, nullptr, scratch, lds, 0, rev, st);
+      };
+      e = run();  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int it = 0; it < 3 && e == cudaSuccess; ++it) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (cand == 0 || ms < best)) {
+        best = ms;
+        pick = cand;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(scratch, st);
+    if (e != cudaSuccess) return 0;
+    cd_tune_set(key, pick);
+    return pick;
+  }
+  static cudaError_t apply(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
+                           const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
+                           const int32_t* gate1, float* out, int64_t ldo, int accumulate, int rev, cudaStream_t st) {
+    static cudaError_t attr = set_smem_attrs<N>();
+    if (attr != cudaSuccess) return attr;
+    const int v = gate0 ? 0 : variant(row, X, ldx, bf16, nvec, tw, list, Lc, count, rev, st);
+    if (v) return apply_v<1>(row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate, rev, st);
+    return apply_v<0>(row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate, rev, st);
   }
 };
 

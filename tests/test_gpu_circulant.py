@@ -211,3 +211,27 @@ def test_circulant_pair_closed_selection(n, k):
     assert rel(C.double().cpu().numpy(), m.real) <= TOL
     # the truncation error reported is that of the closed set
     assert abs(ia["resid_fro2"] - np.linalg.norm(ta.resid) ** 2) <= 1e-4 * np.linalg.norm(a64) ** 2
+
+
+@pytest.mark.parametrize("n", [1024, 4096])
+def test_autotuned_apply_is_bit_identical(n):
+    """The autotuner picks between spectral-apply variants that compute every output with the same
+    operations: products with tuning off, during the timing call and after it are bit-identical."""
+    torch, amm = torch_cuda()
+    g = S.rng(n, 11)
+    A, B = dev32(torch, g.standard_normal((n, n))), dev32(torch, g.standard_normal((n, n)) + 0.5)
+    hA = amm.decompose(A, "circulant", 9, "left")
+    hB = amm.decompose(B, "circulant", 9, "right")
+    amm.set_autotune(False)
+    C0 = amm.approx_matmul(hA, hB).clone()
+    G = dev32(torch, g.standard_normal((n, n)))
+    dA0, dB0 = [t.clone() for t in amm.approx_matmul_backward(hA, hB, G)]
+    try:
+        amm.set_autotune(True)
+        C1 = amm.approx_matmul(hA, hB).clone()   # times the variants of these keys
+        C2 = amm.approx_matmul(hA, hB).clone()   # uses the kept choice
+        dA1, dB1 = amm.approx_matmul_backward(hA, hB, G)
+    finally:
+        amm.set_autotune(False)
+    assert torch.equal(C0, C1) and torch.equal(C0, C2)
+    assert torch.equal(dA0, dA1) and torch.equal(dB0, dB1)
