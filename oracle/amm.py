@@ -688,6 +688,34 @@ def frozen_product_blocked(ta: Truncation, tb: Truncation, a, b) -> np.ndarray:
     return (pa @ bp + (ap - pa) @ pb)[: ta.shape0[0], : tb.shape0[1]].real
 
 
+def project(t: Truncation, x: np.ndarray, adjoint: bool = False) -> np.ndarray:
+    """The truncation's projector P (A~ = P(A)) applied to x, or its bilinear adjoint: circulant
+    P_S / P_{S-bar}, SVD Q Q^T x (self-adjoint), cycles (self-adjoint).  Reading R10: frozen."""
+    if t.method == "circulant":
+        n = x.shape[0]
+        return project_circulant(x.astype(np.complex128), mirror(t.sel, n) if adjoint else t.sel)
+    if t.method == "svd":
+        return t.Q @ (t.Q.T @ x)
+    if t.method == "cycle":
+        return project_cycles(x, t.sel)
+    raise ValueError(t.method)
+
+
+def mixed_backward(ta: Truncation, tb: Truncation, g: np.ndarray):
+    """Gradients of <G, Re M> for operands truncated by different methods (circulant, SVD, cycle),
+    projectors frozen: the first-order map M = P_A(A) B + (A - P_A(A)) P_B(B) is bilinear, and
+    dA = Re[G B~^T + P_A'(G dB^T)], dB = Re[A~^T G + P_B'(dA^T G)] with P' each operand's adjoint."""
+    da = g @ tb.approx.T + project(ta, g @ tb.resid.T, adjoint=True)
+    db = ta.approx.T @ g + project(tb, ta.resid.T @ g, adjoint=True)
+    return np.real(da), np.real(db)
+
+
+def frozen_mixed_product(ta: Truncation, tb: Truncation, a, b) -> np.ndarray:
+    """The mixed first-order map with frozen projectors evaluated at new operands (a, b)."""
+    pa, pb = project(ta, a), project(tb, b)
+    return np.real(pa @ b + (a - pa) @ pb)
+
+
 def backward(method: str, ta, tb, g):
     return {"circulant": cd_backward, "svd": svd_backward, "cycle": cycle_backward,
             "fourier": fourier_backward}[method](ta, tb, g)

@@ -403,6 +403,42 @@ def test_backward_matches_bruteforce(method):
     assert np.abs(da - bda).max() < 1e-12 and np.abs(db - bdb).max() < 1e-12
 
 
+_MIX3 = [(x, y) for x in ("circulant", "svd", "cycle") for y in ("circulant", "svd", "cycle") if x != y]
+
+
+@pytest.mark.parametrize("ma,mb", _MIX3)
+def test_mixed_backward_matches_bruteforce(ma, mb):
+    """Reading R10 for operands of different methods: the closed-form gradients (each operand's own
+    adjoint projector) equal <G, M(E_ij)> of the frozen mixed map over every basis matrix, and the
+    frozen map at the operands themselves is the mixed product."""
+    n, k = 6, 2
+    g = S.rng(57, 0)
+    a, b, gr = g.standard_normal((n, n)) + 0.3, g.standard_normal((n, n)), g.standard_normal((n, n))
+    ta, tb = _trunc_side(ma, a, k, "left", 57), _trunc_side(mb, b, k, "right", 57)
+    da, db = O.mixed_backward(ta, tb, gr)
+    f = lambda x, y: np.sum(gr * O.frozen_mixed_product(ta, tb, x, y))
+    assert abs(f(a, b) - np.sum(gr * O.mixed_product(ta, tb))) < 1e-10
+    bda, bdb = np.zeros_like(a), np.zeros_like(b)
+    for i, j in itertools.product(range(n), range(n)):
+        e = np.zeros_like(a)
+        e[i, j] = 1.0
+        bda[i, j] = f(e, b) - f(np.zeros_like(a), b)
+        bdb[i, j] = f(a, e) - f(a, np.zeros_like(b))
+    assert np.abs(da - bda).max() < 1e-12 and np.abs(db - bdb).max() < 1e-12
+
+
+def test_mixed_backward_same_method_reduces():
+    """With both operands truncated by one method the mixed formula is that method's backward."""
+    g = S.rng(58, 0)
+    n = 8
+    a, b, gr = g.standard_normal((n, n)), g.standard_normal((n, n)), g.standard_normal((n, n))
+    for method in ("circulant", "svd", "cycle"):
+        ta, tb = _truncs(method, a, b, 3, seed=58)
+        da, db = O.mixed_backward(ta, tb, gr)
+        ra, rb = O.backward(method, ta, tb, gr)
+        assert np.abs(da - ra).max() < 1e-12 and np.abs(db - rb).max() < 1e-12
+
+
 def test_fourier_backward_asymmetric_masks_bruteforce():
     """Single-tone rows keep f but not n - f at k = 1 (exact tie, lower index first): the kept
     set is not mirror-symmetric, M is complex, and the gradient of Re M still matches brute force."""
