@@ -526,8 +526,7 @@ extern "C" amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t
   if (!dC) return fail(AMM_ERR_INVALID_ARG, "backward: dC is NULL");
   if (lddc < b->cols || (dA && ldda < a->cols) || (dB && lddb < b->cols))
     return fail(AMM_ERR_INVALID_ARG, "backward: leading dimension too small");
-  if (a->method != b->method)
-    return fail(AMM_ERR_NOT_IMPLEMENTED, "backward of a mixed-method product is not built");
+  if (a->method != b->method) return mixed_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
   if (a->method == AMM_SVD) return svd_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);
   if (a->method == AMM_CIRCULANT) {
     if (a->blk.b || b->blk.b) return blocked_backward(a, b, dC, lddc, dA, ldda, dB, lddb, (cudaStream_t)stream);

@@ -98,6 +98,16 @@ cudaError_t svd_left_apply(Handle* a, const float* X, int64_t ldx, int64_t p, fl
 cudaError_t svd_right_apply(Handle* b, const float* Y, int64_t ldy, int64_t m, float* C, int64_t ldc, float beta,
                             cudaStream_t st);
 cudaError_t svd_residual(Handle* a, float* D, int64_t ldd, cudaStream_t st);
+// mixed-method backward pieces: out = G B~^T (m x n); out = A~^T G (n x p); out += Q_A Q_A^T (G D^T);
+// out += Q_B Q_B^T (D^T G)
+cudaError_t svd_rt_apply(Handle* b, const float* G, int64_t ldg, int64_t m, float* out, int64_t ldo, cudaStream_t st);
+cudaError_t svd_lt_apply(Handle* a, const float* G, int64_t ldg, int64_t p, float* out, int64_t ldo, cudaStream_t st);
+cudaError_t svd_proj_left(Handle* a, const float* G, int64_t ldg, const float* D, int64_t ldd, int64_t p, float* out,
+                          int64_t ldo, cudaStream_t st);
+cudaError_t svd_proj_right(Handle* b, const float* D, int64_t ldd, const float* G, int64_t ldg, int64_t m, float* out,
+                           int64_t ldo, cudaStream_t st);
+amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, float* dB,
+                            int64_t lddb, cudaStream_t st);
 // api.cu: one square circulant block pair; acc = 1 adds to C / dA / dB instead of overwriting
 amm_status_t decompose_circulant(Handle* h, const amm_opts_t* o);
 cudaError_t cd_first_order(Handle* a, Handle* b, float* C, int64_t ldc, int acc, cudaStream_t st);

@@ -250,7 +250,7 @@ constexpr int CYC_DG = 4;
 template <bool P2>
 __global__ void __launch_bounds__(256) cyc_diag_dot_kernel(const float* __restrict__ X, int64_t ldx,
                                                            const float* __restrict__ Y, int64_t ldy, int n,
-                                                           const int32_t* __restrict__ sel, int k,
+                                                           int len, const int32_t* __restrict__ sel, int k,
                                                            float* __restrict__ out, int64_t ldo) {
   const int g0 = blockIdx.x * CYC_DG;
   const int l = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) cyc_diag_dot_kernel(const float* __restri
 #pragma unroll
   for (int j = 0; j < CYC_DG; ++j) acc[j] = 0.f;
 #pragma unroll 4
-  for (int m4 = lane; m4 < n / 4; m4 += 32) {
+  for (int m4 = lane; m4 < len / 4; m4 += 32) {
     const float4 y = __ldg(yr + m4);
 #pragma unroll
     for (int j = 0; j < CYC_DG; ++j) {
@@ -288,11 +288,12 @@ __global__ void __launch_bounds__(256) cyc_diag_dot_kernel(const float* __restri
     if (lane == j && j < nt) out[(int64_t)r[j] * ldo + l] += acc[j];
 }
 
-static cudaError_t diag_dot(const float* X, int64_t ldx, const float* Y, int64_t ldy, int n, const int32_t* sel,
-                            int k, float* out, int64_t ldo, const char* name, cudaStream_t st) {
-  AMM_TRACE_W(name, st, 2.0 * k * (double)n * n, 4.0 * n * ((double)k + (k + CYC_DG - 1) / CYC_DG) * n, nullptr);
+// rows of len entries (a multiple of 4, 16-byte aligned rows)
+static cudaError_t diag_dot(const float* X, int64_t ldx, const float* Y, int64_t ldy, int n, int len,
+                            const int32_t* sel, int k, float* out, int64_t ldo, const char* name, cudaStream_t st) {
+  AMM_TRACE_W(name, st, 2.0 * k * (double)n * len, 4.0 * len * ((double)k + (k + CYC_DG - 1) / CYC_DG) * n, nullptr);
   auto kern = pow2n(n) ? cyc_diag_dot_kernel<true> : cyc_diag_dot_kernel<false>;
-  kern<<<dim3((k + CYC_DG - 1) / CYC_DG, (n + 7) / 8), 256, 0, st>>>(X, ldx, Y, ldy, n, sel, k, out, ldo);
+  kern<<<dim3((k + CYC_DG - 1) / CYC_DG, (n + 7) / 8), 256, 0, st>>>(X, ldx, Y, ldy, n, len, sel, k, out, ldo);
   return cudaGetLastError();
 }
 
@@ -324,7 +325,7 @@ cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int
       Gx = T1;
       ldgx = n;
     }
-    if (e == cudaSuccess) e = diag_dot(Gx, ldgx, T0, n, n, selA, ka, dA, ldda, "cyc_bw_proj_rows", st);
+    if (e == cudaSuccess) e = diag_dot(Gx, ldgx, T0, n, n, n, selA, ka, dA, ldda, "cyc_bw_proj_rows", st);
   }
   if (dB && e == cudaSuccess) {
     {
@@ -337,10 +338,35 @@ cudaError_t cyc_backward(int n, const float* A, int64_t lda, const float* B, int
     if (e == cudaSuccess) e = cyc_residual(n, A, lda, inselA, T0, n, st);
     if (e == cudaSuccess) e = transpose_f32(T0, n, n, n, T1, n, st);
     if (e == cudaSuccess) e = transpose_f32(G, n, n, ldg, T2, n, st);
-    if (e == cudaSuccess) e = diag_dot(T1, n, T2, n, n, selB, kb, dB, lddb, "cyc_bw_proj_cols", st);
+    if (e == cudaSuccess) e = diag_dot(T1, n, T2, n, n, n, selB, kb, dB, lddb, "cyc_bw_proj_cols", st);
   }
   dev_free(T, st);
   return e;
+}
+
+// ---------------------------------------------------------------------------- mixed-method backward pieces
+// out = G B_s^T (n x n, G n x n)
+cudaError_t cyc_rt_apply(int n, const float* G, int64_t ldg, const int32_t* selB, int kb, const float* cycB,
+                         float* out, int64_t ldo, cudaStream_t st) {
+  if (cudaError_t ea = cyc_attrs(); ea != cudaSuccess) return ea;
+  AMM_TRACE_W("cyc_bw_row", st, 2.0 * kb * (double)n * n, 8.0 * n * (double)n, nullptr);
+  CYC_LAUNCH(cyc_bw_row_kernel, n / CYC_RW, sizeof(float) * CYC_RW * n, G, ldg, n, selB, kb, cycB, out, ldo);
+  return cudaGetLastError();
+}
+// out = A_s^T G (n x n)
+cudaError_t cyc_lt_apply(int n, const float* G, int64_t ldg, const int32_t* selA, int ka, const float* cycA,
+                         float* out, int64_t ldo, cudaStream_t st) {
+  if (cudaError_t ea = cyc_attrs(); ea != cudaSuccess) return ea;
+  AMM_TRACE_W("cyc_bw_col", st, 2.0 * ka * (double)n * n, 8.0 * n * (double)n, nullptr);
+  CYC_LAUNCH(cyc_bw_col_kernel, n / CYC_CW, sizeof(float4) * n + sizeof(int) * ka, G, ldg, n, selA, ka, cycA, out,
+             ldo);
+  return cudaGetLastError();
+}
+// out((l + t) mod n, l) += <X((l + t) mod n, :), Y(l, :)> for the selected t (rows of len entries,
+// 16-byte aligned, len a multiple of 4)
+cudaError_t cyc_diag_project(int n, int len, const float* X, int64_t ldx, const float* Y, int64_t ldy,
+                             const int32_t* sel, int k, float* out, int64_t ldo, cudaStream_t st) {
+  return diag_dot(X, ldx, Y, ldy, n, len, sel, k, out, ldo, "cyc_proj", st);
 }
 
 int cyc_rows_per_part(int n) { return n >= 1024 ? 64 : 16; }

@@ -108,6 +108,12 @@ cudaError_t cyc_right_apply(int n, const int32_t* selB, int kb, const float* cyc
                             int64_t m, float* C, int64_t ldc, cudaStream_t st);
 cudaError_t cyc_residual(int n, const float* A, int64_t lda, const unsigned char* insel, float* D, int64_t ldd,
                          cudaStream_t st);
+cudaError_t cyc_rt_apply(int n, const float* G, int64_t ldg, const int32_t* selB, int kb, const float* cycB,
+                         float* out, int64_t ldo, cudaStream_t st);
+cudaError_t cyc_lt_apply(int n, const float* G, int64_t ldg, const int32_t* selA, int ka, const float* cycA,
+                         float* out, int64_t ldo, cudaStream_t st);
+cudaError_t cyc_diag_project(int n, int len, const float* X, int64_t ldx, const float* Y, int64_t ldy,
+                             const int32_t* sel, int k, float* out, int64_t ldo, cudaStream_t st);
 cudaError_t ft_dense(int n, const float2* At, const int32_t* sel, int k, int m, const float2* tw, int part,
                      const float* A, int64_t lda, float* D, int64_t ldd, cudaStream_t st);
 cudaError_t ft_left_apply(int n, int m, const float2* At, const int32_t* selA, int ka, const float2* tw,

@@ -164,4 +164,137 @@ amm_status_t mixed_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStrea
   return AMM_OK;
 }
 
+// ---------------------------------------------------------------------------- backward
+// Gradients of <G, Re M> with the projectors frozen, each operand by its own method:
+//   dA = Re(G B~^T) + Re P_A'(G dB^T),   dB = Re(A~^T G) + Re P_B'(dA^T G),
+// P' the bilinear adjoint of the operand's projector (circulant: the mirrored components S-bar,
+// whose real part on a real matrix is the w-weighted projection; SVD Q Q^T; cycles the kept cycles).
+// dA, dB above are the dense real residuals of the other operand.  Built for the SVD, circulant and
+// cycle methods on square operands (m = n = p): the circulant projections run as SDDMMs on
+// spectra of length n, the cycle projections as selected-diagonal dot products.
+
+namespace {
+
+struct Buf {
+  cudaStream_t st;
+  std::vector<void*> v;
+  cudaError_t e = cudaSuccess;
+  explicit Buf(cudaStream_t s) : st(s) {}
+  template <typename T>
+  T* get(size_t cnt) {
+    void* q = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(&q, sizeof(T) * cnt, st);
+    if (q) v.push_back(q);
+    return (T*)q;
+  }
+  ~Buf() {
+    for (void* q : v) dev_free(q, st);
+  }
+};
+
+// out += Re P_{S-bar}(X Y^T) (row = false) or Re P_{S-bar}(X^T Y) (row = true) for the circulant
+// handle h, X and Y n x n: component spectra from the SDDMM on column / row spectra
+cudaError_t cd_project_product(Handle* h, bool row, const float* X, int64_t ldx, const float* Y, int64_t ldy,
+                               float* out, int64_t ldo, cudaStream_t st) {
+  const int n = (int)h->rows;
+  const size_t kh = (size_t)n / 2 + 1;
+  auto& c = h->cd;
+  Buf b(st);
+  float2* X1 = b.get<float2>(kh * n);
+  float2* X2 = b.get<float2>(kh * n);
+  float2* RX = b.get<float2>(kh * n);
+  float2* K = b.get<float2>((size_t)c.cap * n);
+  if (b.e == cudaSuccess) b.e = bw_spectrum(n, row, X, ldx, c.tw, X1, st);
+  if (b.e == cudaSuccess) b.e = bw_spectrum(n, row, Y, ldy, c.tw, X2, st);
+  if (b.e == cudaSuccess) b.e = cd_sddmm(n, X1, X2, c.so.ulist, c.so.counts, c.cap, K, nullptr, nullptr, st);
+  if (b.e == cudaSuccess) b.e = cd_rho(n, K, c.tw, c.so.ulist, c.so.counts, c.cap, RX, nullptr, nullptr, st);
+  if (b.e == cudaSuccess) b.e = cd_residual(n, RX, c.tw, c.so.wfull, 2, nullptr, out, st, ldo, 1);
+  return b.e;
+}
+
+bool aligned16(const float* p, int64_t ld) { return ((uintptr_t)p & 15) == 0 && (ld & 3) == 0; }
+
+}  // namespace
+
+amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, float* dB,
+                            int64_t lddb, cudaStream_t st) {
+  const int64_t m = a->rows, n = a->cols, p = b->cols;
+  if (a->method == AMM_SPARSE_FOURIER || b->method == AMM_SPARSE_FOURIER)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "backward of a mixed-method product with the Fourier sparsifier is not built");
+  if (a->blk.b || b->blk.b)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "backward of a mixed-method product with circulant blocks is not built");
+  if (m != n || p != n)
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "backward of a mixed-method product needs square operands (%lldx%lld, "
+                "%lldx%lld)", (long long)m, (long long)n, (long long)n, (long long)p);
+  if (a->dtype != AMM_F32 || b->dtype != AMM_F32)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "mixed methods: BF16 operands are not built (use FP32 inputs)");
+  const int nn = (int)n;
+  Buf buf(st);
+  float* DA = buf.get<float>((size_t)nn * nn);  // Re dA = A - Re A~
+  float* DB = buf.get<float>((size_t)nn * nn);
+  cudaError_t e = buf.e;
+  if (e == cudaSuccess) e = residual(a, DA, nn, st);
+  if (e == cudaSuccess) e = residual(b, DB, nn, st);
+  // an aligned copy of G for the cycle projections (float4 rows)
+  const float* Ga = G;
+  int64_t ldga = ldg;
+  if (e == cudaSuccess && (a->method == AMM_SPARSE_CYCLE || b->method == AMM_SPARSE_CYCLE) && !aligned16(G, ldg)) {
+    float* t = buf.get<float>((size_t)nn * nn);
+    e = buf.e;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(t, sizeof(float) * nn, G, sizeof(float) * ldg, sizeof(float) * nn, nn,
+                            cudaMemcpyDeviceToDevice, st);
+    Ga = t;
+    ldga = nn;
+  }
+  if (dA && e == cudaSuccess) {
+    // Re(G B~^T)
+    switch (b->method) {
+      case AMM_SVD: e = svd_rt_apply(b, G, ldg, nn, dA, ldda, st); break;
+      case AMM_CIRCULANT:
+        e = cd_apply(nn, true, G, ldg, false, nn, b->cd.tw, b->cd.so.ulist, b->cd.Lw, b->cd.so.counts, nullptr,
+                     nullptr, dA, ldda, 0, st, 0);
+        break;
+      default: e = cyc_rt_apply(nn, G, ldg, b->cy.so.sel, (int)b->k, b->cy.cyc, dA, ldda, st); break;
+    }
+    // + Re P_A'(G dB^T)
+    if (e == cudaSuccess) {
+      switch (a->method) {
+        case AMM_SVD: e = svd_proj_left(a, G, ldg, DB, nn, nn, dA, ldda, st); break;
+        case AMM_CIRCULANT: e = cd_project_product(a, false, G, ldg, DB, nn, dA, ldda, st); break;
+        default: e = cyc_diag_project(nn, nn, Ga, ldga, DB, nn, a->cy.so.sel, (int)a->k, dA, ldda, st); break;
+      }
+    }
+  }
+  if (dB && e == cudaSuccess) {
+    // Re(A~^T G)
+    switch (a->method) {
+      case AMM_SVD: e = svd_lt_apply(a, G, ldg, nn, dB, lddb, st); break;
+      case AMM_CIRCULANT:
+        e = cd_apply(nn, false, G, ldg, false, nn, a->cd.tw, a->cd.so.ulist, a->cd.Lw, a->cd.so.counts, nullptr,
+                     nullptr, dB, lddb, 0, st, 1);
+        break;
+      default: e = cyc_lt_apply(nn, G, ldg, a->cy.so.sel, (int)a->k, a->cy.cyc, dB, lddb, st); break;
+    }
+    // + Re P_B'(dA^T G)
+    if (e == cudaSuccess) {
+      switch (b->method) {
+        case AMM_SVD: e = svd_proj_right(b, DA, nn, G, ldg, nn, dB, lddb, st); break;
+        case AMM_CIRCULANT: e = cd_project_product(b, true, DA, nn, G, ldg, dB, lddb, st); break;
+        default: {
+          // (dA^T G)((l + s), l) = <dA^T(l + s, :), G^T(l, :)>
+          float* DAT = buf.get<float>((size_t)nn * nn);
+          float* GT = buf.get<float>((size_t)nn * nn);
+          e = buf.e;
+          if (e == cudaSuccess) e = transpose_f32(DA, nn, nn, nn, DAT, nn, st);
+          if (e == cudaSuccess) e = transpose_f32(G, nn, nn, ldg, GT, nn, st);
+          if (e == cudaSuccess) e = cyc_diag_project(nn, nn, DAT, nn, GT, nn, b->cy.so.sel, (int)b->k, dB, lddb, st);
+        }
+      }
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mixed-method backward");
+  return AMM_OK;
+}
+
 }  // namespace amm

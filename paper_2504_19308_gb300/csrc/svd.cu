@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "api_internal.h"
 #include "common.cuh"
@@ -936,6 +937,134 @@ static cudaError_t svd_residual_t(Handle* a, float* D, int64_t ldd, cudaStream_t
   if (e == cudaSuccess)
     e = gemm_tn<E>(m, n, k, -1.f, (const E*)a->svd.Qe, k, (const E*)a->svd.ZTe, k, 1.f, D, ldd, a->svd.err, st);
   return e;
+}
+
+// Pieces of the backward of a mixed-method product (thin GEMMs on the handle's Q and Z).
+// Scratch helpers: a float buffer and a K-major copy in E of a float matrix.
+template <typename E>
+struct SvdScratch {
+  cudaStream_t st;
+  std::vector<void*> bufs;
+  cudaError_t e = cudaSuccess;
+  explicit SvdScratch(cudaStream_t s) : st(s) {}
+  float* f(size_t cnt) {
+    void* q = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(&q, sizeof(float) * cnt, st);
+    if (q) bufs.push_back(q);
+    return (float*)q;
+  }
+  // Y = X^T in E (cols x rows)
+  const E* tr(const float* X, int64_t rows, int64_t cols, int64_t ldx) {
+    void* q = nullptr;
+    if (e == cudaSuccess) e = dev_alloc(&q, sizeof(E) * rows * cols, st);
+    if (q) bufs.push_back(q);
+    if (e == cudaSuccess) e = transpose_cast<float, E>(X, rows, cols, ldx, (E*)q, rows, st);
+    return (const E*)q;
+  }
+  // X in E, K-major as it is (rows x cols, leading dimension cols when copied)
+  const E* km(const float* X, int64_t rows, int64_t cols, int64_t ldx, int64_t* ld) {
+    const E* out = nullptr;
+    E* own = nullptr;
+    if (e == cudaSuccess) e = as_kmajor<E>(X, rows, cols, ldx, &out, &own, st);
+    if (own) bufs.push_back(own);
+    *ld = own ? cols : ldx;
+    return out;
+  }
+  const E* ke(const float* X, int64_t rows, int64_t cols) {  // contiguous float -> E
+    const E* out = nullptr;
+    if (e == cudaSuccess) e = to_e<E>(nullptr, X, rows, cols, &out, st);
+    if (!std::is_same<E, float>::value && out) bufs.push_back((void*)out);
+    return out;
+  }
+  ~SvdScratch() {
+    for (void* q : bufs) dev_free(q, st);
+  }
+};
+
+// out = G B~^T = (G Z_B^T) Q_B^T, G (m x p), out (m x n)
+template <typename E>
+static cudaError_t svd_rt_apply_t(Handle* b, const float* G, int64_t ldg, int64_t m, float* out, int64_t ldo,
+                                  cudaStream_t st) {
+  const int n = (int)b->rows, p = (int)b->cols, k = (int)b->k;
+  SvdScratch<E> sc(st);
+  int64_t ldge = 0;
+  const E* ge = sc.km(G, m, p, ldg, &ldge);
+  float* T = sc.f((size_t)m * k);
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>((int)m, k, p, 1.f, ge, ldge, (const E*)b->svd.Ze, p, 0.f, T, k, b->svd.err, st);
+  const E* te = sc.ke(T, m, k);
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>((int)m, n, k, 1.f, te, k, (const E*)b->svd.Qe, k, 0.f, out, ldo, b->svd.err, st);
+  return sc.e;
+}
+
+// out = A~^T G = Z_A^T (Q_A^T G), G (m x p), out (n x p)
+template <typename E>
+static cudaError_t svd_lt_apply_t(Handle* a, const float* G, int64_t ldg, int64_t p, float* out, int64_t ldo,
+                                  cudaStream_t st) {
+  const int m = (int)a->rows, n = (int)a->cols, k = (int)a->k;
+  SvdScratch<E> sc(st);
+  const E* gt = sc.tr(G, m, p, ldg);  // p x m
+  float* T = sc.f((size_t)k * p);
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>(k, (int)p, m, 1.f, (const E*)a->svd.QTe, m, gt, m, 0.f, T, p, a->svd.err, st);
+  const E* tt = sc.tr(T, k, p, p);    // p x k
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>(n, (int)p, k, 1.f, (const E*)a->svd.ZTe, k, tt, k, 0.f, out, ldo, a->svd.err, st);
+  return sc.e;
+}
+
+// out += Q_A Q_A^T (G D^T), G (m x p), D (n x p), out (m x n)
+template <typename E>
+static cudaError_t svd_proj_left_t(Handle* a, const float* G, int64_t ldg, const float* D, int64_t ldd, int64_t p,
+                                   float* out, int64_t ldo, cudaStream_t st) {
+  const int m = (int)a->rows, n = (int)a->cols, k = (int)a->k;
+  SvdScratch<E> sc(st);
+  const E* gt = sc.tr(G, m, p, ldg);
+  float* T = sc.f((size_t)k * p);
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>(k, (int)p, m, 1.f, (const E*)a->svd.QTe, m, gt, m, 0.f, T, p, a->svd.err, st);
+  const E* te = sc.ke(T, k, p);
+  int64_t ldde = 0;
+  const E* de = sc.km(D, n, p, ldd, &ldde);
+  float* U = sc.f((size_t)k * n);
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>(k, n, (int)p, 1.f, te, p, de, ldde, 0.f, U, n, a->svd.err, st);
+  const E* ut = sc.tr(U, k, n, n);    // n x k
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>(m, n, k, 1.f, (const E*)a->svd.Qe, k, ut, k, 1.f, out, ldo, a->svd.err, st);
+  return sc.e;
+}
+
+// out += Q_B Q_B^T (D^T G), D (m x n), G (m x p), out (n x p)
+template <typename E>
+static cudaError_t svd_proj_right_t(Handle* b, const float* D, int64_t ldd, const float* G, int64_t ldg, int64_t m,
+                                    float* out, int64_t ldo, cudaStream_t st) {
+  const int n = (int)b->rows, p = (int)b->cols, k = (int)b->k;
+  SvdScratch<E> sc(st);
+  int64_t ldde = 0;
+  const E* de = sc.km(D, m, n, ldd, &ldde);
+  float* V = sc.f((size_t)m * k);
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>((int)m, k, n, 1.f, de, ldde, (const E*)b->svd.QTe, n, 0.f, V, k, b->svd.err, st);
+  const E* vt = sc.tr(V, m, k, k);    // k x m
+  const E* gt = sc.tr(G, m, p, ldg);  // p x m
+  float* U = sc.f((size_t)k * p);
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>(k, p, (int)m, 1.f, vt, m, gt, m, 0.f, U, p, b->svd.err, st);
+  const E* ut = sc.tr(U, k, p, p);    // p x k
+  if (sc.e == cudaSuccess) sc.e = gemm_tn<E>(n, p, k, 1.f, (const E*)b->svd.Qe, k, ut, k, 1.f, out, ldo, b->svd.err, st);
+  return sc.e;
+}
+
+cudaError_t svd_rt_apply(Handle* b, const float* G, int64_t ldg, int64_t m, float* out, int64_t ldo, cudaStream_t st) {
+  return b->svd.bf16 ? svd_rt_apply_t<__nv_bfloat16>(b, G, ldg, m, out, ldo, st)
+                     : svd_rt_apply_t<float>(b, G, ldg, m, out, ldo, st);
+}
+cudaError_t svd_lt_apply(Handle* a, const float* G, int64_t ldg, int64_t p, float* out, int64_t ldo, cudaStream_t st) {
+  return a->svd.bf16 ? svd_lt_apply_t<__nv_bfloat16>(a, G, ldg, p, out, ldo, st)
+                     : svd_lt_apply_t<float>(a, G, ldg, p, out, ldo, st);
+}
+cudaError_t svd_proj_left(Handle* a, const float* G, int64_t ldg, const float* D, int64_t ldd, int64_t p, float* out,
+                          int64_t ldo, cudaStream_t st) {
+  return a->svd.bf16 ? svd_proj_left_t<__nv_bfloat16>(a, G, ldg, D, ldd, p, out, ldo, st)
+                     : svd_proj_left_t<float>(a, G, ldg, D, ldd, p, out, ldo, st);
+}
+cudaError_t svd_proj_right(Handle* b, const float* D, int64_t ldd, const float* G, int64_t ldg, int64_t m, float* out,
+                           int64_t ldo, cudaStream_t st) {
+  return b->svd.bf16 ? svd_proj_right_t<__nv_bfloat16>(b, D, ldd, G, ldg, m, out, ldo, st)
+                     : svd_proj_right_t<float>(b, D, ldd, G, ldg, m, out, ldo, st);
 }
 
 cudaError_t svd_left_apply(Handle* a, const float* X, int64_t ldx, int64_t p, float* C, int64_t ldc, float beta,

@@ -75,12 +75,42 @@ def test_mixed_untruncated_reproduces_product():
     assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= 1e-5
 
 
-def test_mixed_backward_is_reported_not_built():
+MIX3 = [(x, y) for x in ("circulant", "svd", "cycle") for y in ("circulant", "svd", "cycle") if x != y]
+
+
+@pytest.mark.parametrize("ma,mb", MIX3)
+@pytest.mark.parametrize("n,k", [(64, 5), (96, 7), (256, 9)])
+def test_mixed_backward(ma, mb, n, k):
+    """dA = Re[G B~^T + P_A'(G dB^T)], dB = Re[A~^T G + P_B'(dA^T G)] with each operand's own
+    adjoint projector (frozen), against the oracle on the GPU's selections / sketches."""
+    torch, amm = torch_cuda()
+    g = S.rng(n + k, 12)
+    a = g.standard_normal((n, n)) + 0.5
+    b = S.toeplitz_uniform(n, g) + 0.1 * g.standard_normal((n, n))
+    gr = g.standard_normal((n, n))
+    A, B, G = dev32(torch, a), dev32(torch, b), dev32(torch, gr)
+    hA, ta = _handle(torch, amm, A, ma, k, "left", n)
+    hB, tb = _handle(torch, amm, B, mb, k, "right", n)
+    dA, dB = amm.approx_matmul_backward(hA, hB, G)
+    rda, rdb = O.mixed_backward(ta, tb, as64(G))
+    ea, eb = rel(dA.double().cpu().numpy(), rda), rel(dB.double().cpu().numpy(), rdb)
+    assert ea <= TOL and eb <= TOL, (ma, mb, n, ea, eb)
+
+
+def test_mixed_backward_reports_what_is_not_built():
     torch, amm = torch_cuda()
     n = 32
     g = S.rng(10, 0)
     A, B = dev32(torch, g.standard_normal((n, n))), dev32(torch, g.standard_normal((n, n)))
-    hA = amm.decompose(A, "cycle", 3, "left")
+    G = dev32(torch, g.standard_normal((n, n)))
+    hA = amm.decompose(A, "fourier", 3, "left")
     hB = amm.decompose(B, "circulant", 3, "right")
-    with pytest.raises(RuntimeError, match="mixed"):
-        amm.approx_matmul_backward(hA, hB, dev32(torch, g.standard_normal((n, n))))
+    with pytest.raises(RuntimeError, match="Fourier"):
+        amm.approx_matmul_backward(hA, hB, G)
+    # rectangular operands: the circulant / cycle projections of the mixed backward are square
+    A2 = dev32(torch, g.standard_normal((48, n)))
+    phi = dev32(torch, S.sketch(n, 3, 10, 0))
+    hA2 = amm.decompose(A2, "svd", 3, "left", sketch=phi)
+    hB2 = amm.decompose(B, "cycle", 3, "right")
+    with pytest.raises(RuntimeError, match="square"):
+        amm.approx_matmul_backward(hA2, hB2, dev32(torch, g.standard_normal((48, n))))
