@@ -179,9 +179,13 @@ amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, float* C, int64
  *   AMM_SPARSE_FOURIER  dA = Re[(dC B~_a^T + P_A(dC dB~^T)) conj(W)],
  *                       dB = Re[W (A~_a^T dC + P_B(dA~^T dC))]  with the element masks P_A, P_B
  *                       (Alg. 5 differentiated with the masks frozen).
+ *   Handles of different methods (SVD, circulant, cycle; square operands m = n = p; FP32):
+ *                       the same formulas with each operand's own P' and the other operand's
+ *                       dense residual dA / dB; the Fourier sparsifier and circulant blocks in a
+ *                       mixed pair return AMM_ERR_NOT_IMPLEMENTED, other shapes
+ *                       AMM_ERR_UNSUPPORTED_SIZE.
  *   dC  device m x p FP32 (lddc).  dA (m x n, ldda) and dB (n x p, lddb) are overwritten;
- *   either may be NULL to skip it.  Handles of different methods return
- *   AMM_ERR_NOT_IMPLEMENTED.
+ *   either may be NULL to skip it.
  */
 amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const float* dC,
                                         int64_t lddc, float* dA, int64_t ldda, float* dB,
