@@ -119,13 +119,20 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
   constexpr int J = 2 * S;
   constexpr int LD = fft_padded_len(N);
   const int j0 = blockIdx.x * J;
+  // the coefficients of all n rows, staged once: the row loads below then wait on shared memory
+  // only, not on a global load of their coefficient
+  float* coef = reinterpret_cast<float*>(smem + S * LD);
+  for (int k = threadIdx.x; k < N; k += NT) {
+    const float g = __ldg(gfull + k);
+    coef[k] = mode == 0 ? 1.f - g : g;
+  }
+  __syncthreads();
   // packed signal s: Z(k) = g_k (r_{j0+2s,k} + i r_{j0+2s+1,k}), k in [0, n)
 #pragma unroll 8
   for (int it = 0; it < N * S / NT; ++it) {
     const int e = threadIdx.x + it * NT;
     const int k = e / S, s = e % S;
-    const float g = gfull[k];
-    const float c = mode == 0 ? 1.f - g : g;
+    const float c = coef[k];
     float2 z = make_float2(0.f, 0.f);
     if (c != 0.f) {  // rows with a zero coefficient are neither read nor required to be set
       const bool mir = k > N / 2;
@@ -148,27 +155,25 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
   const float* fs = reinterpret_cast<const float*>(smem);
   constexpr int IT = N * J / NT, B = store_batch(IT);  // B outputs per batch: loads all in flight
   static_assert(IT % B == 0, "whole batches");
+  // element e of the output: row r = e / J, column c = (r - j0 - (J - 1) + q) mod n, q = e % J
+  auto addr = [&](int e) { return (int64_t)(e / J) * ldx + wrapN<N>(e / J - j0 - (J - 1) + e % J); };
+  auto value = [&](int e) {
+    const int q = e % J, m = J - 1 - q;
+    return fs[2 * ((m >> 1) * LD + fpad(wrapN<N>(e / J - j0 - (J - 1) + q))) + (m & 1)];
+  };
   for (int i0 = 0; i0 < IT; i0 += B) {
-    float* o[B];
     float v[B];
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      const int e = threadIdx.x + (i0 + b) * NT;
-      const int r = e / J, q = e % J;
-      const int c = wrapN<N>(r - j0 - (J - 1) + q);
-      const int m = J - 1 - q;
-      v[b] = fs[2 * ((m >> 1) * LD + fpad(c)) + (m & 1)];
-      o[b] = X + (int64_t)r * ldx + c;
-    }
+    for (int b = 0; b < B; ++b) v[b] = value(threadIdx.x + (i0 + b) * NT);
     if (accumulate) {
       float old[B];
 #pragma unroll
-      for (int b = 0; b < B; ++b) old[b] = *o[b];
+      for (int b = 0; b < B; ++b) old[b] = X[addr(threadIdx.x + (i0 + b) * NT)];
 #pragma unroll
       for (int b = 0; b < B; ++b) v[b] += old[b];
     }
 #pragma unroll
-    for (int b = 0; b < B; ++b) *o[b] = v[b];
+    for (int b = 0; b < B; ++b) X[addr(threadIdx.x + (i0 + b) * NT)] = v[b];
   }
 }
 
@@ -325,6 +330,7 @@ template <int N> struct CdCfg {
   static constexpr int S = (N >= 16384) ? 1 : (N >= 6144) ? 2 : 4;  // packed signals per CTA
   static constexpr int NT = fft_threads(N);          // threads per CTA
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
+  static constexpr size_t SMEM_RES = SMEM + sizeof(float) * N;  // + the staged coefficients
   // second spectral-apply variant for the autotuner: half the packed signals and threads per CTA
   // (more, smaller CTAs per SM; each coefficient load serves half as many signals)
   static constexpr bool HAS_V1 = S >= 2 && NT >= 64;
@@ -341,7 +347,7 @@ template <int N> static cudaError_t set_smem_attrs() {
   };
   s((const void*)cd_spectrum_kernel<N, C::S, C::NT, float>, C::SMEM);
   s((const void*)cd_spectrum_kernel<N, C::S, C::NT, __nv_bfloat16>, C::SMEM);
-  s((const void*)cd_residual_kernel<N, C::S, C::NT>, C::SMEM);
+  s((const void*)cd_residual_kernel<N, C::S, C::NT>, C::SMEM_RES);
   s((const void*)cd_apply_kernel<N, C::S, C::NT, false, false, float>, C::SMEM);
   s((const void*)cd_apply_kernel<N, C::S, C::NT, true, true, float>, C::SMEM);
   s((const void*)cd_apply_kernel<N, C::S, C::NT, true, true, __nv_bfloat16>, C::SMEM);
@@ -386,8 +392,8 @@ template <int N> struct CdOps {
                               const int32_t* dcount2, float* X, int64_t ldx, int accumulate, cudaStream_t st) {
     static cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
-    cd_residual_kernel<N, C::S, C::NT><<<N / (2 * C::S), C::NT, C::SMEM, st>>>(R, tw, g, mode, dcount, dcount2, X,
-                                                                              ldx, accumulate);
+    cd_residual_kernel<N, C::S, C::NT><<<N / (2 * C::S), C::NT, C::SMEM_RES, st>>>(R, tw, g, mode, dcount, dcount2,
+                                                                                  X, ldx, accumulate);
     return cudaGetLastError();
   }
   template <int V>
