@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(NT) bw_spectrum_kernel(const float* __restrict
   constexpr int LD = fft_padded_len(N);
   constexpr int KH = N / 2 + 1;
   const int base = blockIdx.x * 2 * S;
-#pragma unroll 8
+#pragma unroll 16
   for (int it = 0; it < N * S / NT; ++it) {
     const int e = threadIdx.x + it * NT;
     int s, l;

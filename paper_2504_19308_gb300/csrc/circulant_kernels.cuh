@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(NT) cd_spectrum_kernel(const T* __restrict__ A
   float* fs = reinterpret_cast<float*>(smem);
   // gather: element (r, q): column c = (r - j0 - (J-1) + q) mod n holds cycle m = J-1-q at l = c
   static_assert((N * J) % NT == 0, "whole iterations");
-#pragma unroll 8
+#pragma unroll 16
   for (int it = 0; it < N * J / NT; ++it) {  // unrolled: several loads in flight per thread
     const int e = threadIdx.x + it * NT;
     const int r = e / J, q = e % J;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
   }
   __syncthreads();
   // packed signal s: Z(k) = g_k (r_{j0+2s,k} + i r_{j0+2s+1,k}), k in [0, n)
-#pragma unroll 8
+#pragma unroll 16
   for (int it = 0; it < N * S / NT; ++it) {
     const int e = threadIdx.x + it * NT;
     const int k = e / S, s = e % S;
