@@ -188,10 +188,7 @@ def run_amm(args, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1)
     kernels, launches = trace_collect()
     clocks = clk.summary()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
 
     # ---- end to end through the public API with host buffers (H2D inputs, D2H results)
     a_h = torch.from_numpy(a).pin_memory()
@@ -246,14 +243,11 @@ def run_amm(args, rank, world, local_rank):
         e2e_step()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms)
 
     fl = work_flops(PRODUCTS)
-    value = world * fl * args.steps / (ms * 1e-3) / 1e12
-    e2e_value = world * fl * args.steps / (e2e_ms * 1e-3) / 1e12
+    value = whole_job_rate(fl * args.steps, ms * 1e-3, world)
+    e2e_value = whole_job_rate(fl * args.steps, e2e_ms * 1e-3, world)
     roof = roofline(kernels, clocks)
     bf16 = bf16_form(args, A, B, G, PH, ms / args.steps, dist)
     batched = batched_form(args, dev, dist)
@@ -267,6 +261,24 @@ def run_amm(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N * N * 4,
                 "d2h_bytes_per_step": (len(PRODUCTS) + 2 * n_bwd) * N * N * 4, "ms_per_step": e2e_ms / args.steps},
     }
+
+
+def max_over_ranks(x: float) -> float:
+    """The largest of every rank's x (the slowest rank's time); x itself without a process group.
+    NCCL reduces on the rank's GPU, gloo on the CPU."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return x
+    dev = torch.device("cuda", torch.cuda.current_device()) if tdist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(flops_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job TFLOP/s: every rank does the same work (replicas); the time is the slowest rank's."""
+    return world * flops_per_rank / seconds / 1e12
 
 
 def _device_ms(fn, steps, warmup, dist):
@@ -284,12 +296,7 @@ def _device_ms(fn, steps, warmup, dist):
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / steps
-    if dist:
-        import torch.distributed as tdist
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    return max_over_ranks(ms) if dist else ms
 
 
 def bf16_form(args, A, B, G, PH, fp32_ms, dist):
