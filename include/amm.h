@@ -210,6 +210,22 @@ amm_status_t amm_choose_k(const void* A, int64_t rows, int64_t cols, int64_t lda
                           amm_method_t method, double tol, void* stream, int64_t* k_out);
 
 /*
+ * Decompose A with the smallest k (up to k_max; k_max <= 0: no limit) whose truncation meets
+ * ||dA||_F <= tol ||A||_F (Section 2.5: add components while the error estimate is not
+ * satisfactory).  AMM_CIRCULANT / AMM_SPARSE_CYCLE: k from amm_choose_k (exact).  AMM_SVD /
+ * AMM_SPARSE_FOURIER: k doubles from 8 until a trial decomposition meets the tolerance (its error
+ * from amm_handle_info), then bisection inside the last bracket; each trial is a full
+ * decomposition (with the same opts, so the same seed or sketch rule), and the returned handle is
+ * the accepted trial.  When no k up to the cap meets tol, the handle at the cap is returned.
+ * *out receives the handle and *k_out its k (host).  Synchronises `stream`.  Circulant blocks,
+ * forced selections and caller sketches (opts->sketch, whose k is fixed) are rejected; the rSVD
+ * cap is min(rows, cols, 1024).
+ */
+amm_status_t amm_decompose_to_tolerance(const void* A, int64_t rows, int64_t cols, int64_t lda, amm_dtype_t dtype,
+                                        amm_method_t method, double tol, int64_t k_max, const amm_opts_t* opts,
+                                        void* stream, amm_handle_t* out, int64_t* k_out);
+
+/*
  * Posterior estimate of the relative error ||dA dB||_F / ||A B||_F of a computed product
  * (Corollary 3.7, Section 3): ||dA||_F ||dB||_F / (sqrt(n) ||C||_F), n the inner dimension,
  * with ||dA||_F, ||dB||_F the truncation errors of the two handles (amm_handle_info) and C the

@@ -50,6 +50,10 @@ SIGNATURES = {
     "amm_last_error": (ctypes.c_char_p, []),
     "amm_version": (ctypes.c_int32, []),
     "amm_set_autotune": (ctypes.c_int, [ctypes.c_int32]),
+    "amm_decompose_to_tolerance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                                  ctypes.POINTER(Opts), ctypes.c_void_p,
+                                                  ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]),
     "amm_opts_init": (ctypes.c_int, [ctypes.POINTER(Opts)]),
     "amm_decompose": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int64, ctypes.POINTER(Opts), ctypes.c_void_p,
@@ -254,9 +258,25 @@ def choose_k(A: torch.Tensor, method: str, tol: float) -> int:
     return k.value
 
 
-def decompose_to_tolerance(A: torch.Tensor, method: str, tol: float, role: str = "left", **kw) -> Handle:
-    """Decompose A with the smallest k whose truncation error is within tol (relative Frobenius)."""
-    return decompose(A, method, choose_k(A, method, tol), role, **kw)
+def decompose_to_tolerance(A: torch.Tensor, method: str, tol: float, role: str = "left", k_max: int = 0,
+                           seed: int = 0, compute: str = "f32", pair_closed: bool = False) -> Handle:
+    """amm_decompose_to_tolerance: the smallest k with ||dA||_F <= tol ||A||_F (exact from the keys for
+    'circulant' / 'cycle'; geometric growth and bisection over trial decompositions for 'svd' /
+    'fourier')."""
+    lib = load_library()
+    _require_cuda(A, "A")
+    opts = Opts()
+    _check(lib.amm_opts_init(ctypes.byref(opts)), "amm_opts_init")
+    opts.role = ROLES[role]
+    opts.seed = seed
+    opts.compute = {"f32": 0, "bf16": 1}[compute]
+    opts.pair_closed = 1 if pair_closed else 0
+    out, k = ctypes.c_void_p(0), ctypes.c_int64(0)
+    _check(lib.amm_decompose_to_tolerance(A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), DTYPES[A.dtype],
+                                          METHODS[method], float(tol), int(k_max), ctypes.byref(opts),
+                                          _stream_ptr(A.device), ctypes.byref(out), ctypes.byref(k)),
+           "amm_decompose_to_tolerance")
+    return Handle(out.value, A, method, role, k.value)
 
 
 def error_estimate(hA: Handle, hB: Handle, C: torch.Tensor) -> float:

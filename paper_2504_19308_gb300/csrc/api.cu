@@ -690,6 +690,85 @@ extern "C" amm_status_t amm_choose_k(const void* A, int64_t rows, int64_t cols, 
   return AMM_OK;
 }
 
+// k from a truncation tolerance (Section 2.5: more components while the error is not
+// satisfactory).  Circulant / cycle: the exact minimal k from the keys (amm_choose_k).  SVD /
+// Fourier sparsifier: k doubles from k0 until the handle's truncation error meets the tolerance,
+// then bisection inside the last bracket; every trial is a full decomposition whose error comes
+// from amm_handle_info.
+extern "C" amm_status_t amm_decompose_to_tolerance(const void* A, int64_t rows, int64_t cols, int64_t lda,
+                                                   amm_dtype_t dtype, amm_method_t method, double tol, int64_t k_max,
+                                                   const amm_opts_t* opts, void* stream, amm_handle_t* out,
+                                                   int64_t* k_out) {
+  if (!out || !k_out) return fail(AMM_ERR_INVALID_ARG, "amm_decompose_to_tolerance: NULL output");
+  if (!(tol >= 0.0)) return fail(AMM_ERR_INVALID_ARG, "amm_decompose_to_tolerance: tol must be >= 0");
+  if (opts && opts->forced_selection)
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose_to_tolerance: a forced selection fixes k");
+  amm_status_t s;
+  if (method == AMM_CIRCULANT || method == AMM_SPARSE_CYCLE) {
+    if (opts && opts->block) return fail(AMM_ERR_NOT_IMPLEMENTED, "amm_decompose_to_tolerance: circulant blocks");
+    int64_t k = 0;
+    if ((s = amm_choose_k(A, rows, cols, lda, dtype, method, tol, stream, &k)) != AMM_OK) return s;
+    if (k_max > 0) k = std::min(k, k_max);
+    if ((s = amm_decompose(A, rows, cols, lda, dtype, method, k, opts, stream, out)) != AMM_OK) return s;
+    *k_out = k;
+    return AMM_OK;
+  }
+  if (method != AMM_SVD && method != AMM_SPARSE_FOURIER)
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose_to_tolerance: bad method %d", (int)method);
+  if (opts && opts->sketch)
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose_to_tolerance: a caller sketch fixes k (use the seed)");
+  const int64_t kcap0 = method == AMM_SVD ? std::min<int64_t>(std::min(rows, cols), 1024)
+                                          : (opts && opts->role == AMM_RIGHT ? rows : cols);
+  const int64_t kcap = k_max > 0 ? std::min(k_max, kcap0) : kcap0;
+  // error of one trial; the handle is kept when it meets the tolerance
+  auto trial = [&](int64_t k, amm_handle_t* h, bool* ok) -> amm_status_t {
+    amm_status_t st = amm_decompose(A, rows, cols, lda, dtype, method, k, opts, stream, h);
+    if (st != AMM_OK) return st;
+    amm_info_t info;
+    if ((st = amm_handle_info(*h, &info)) != AMM_OK) {
+      amm_handle_destroy(*h);
+      return st;
+    }
+    *ok = std::max(info.resid_fro2, 0.0) <= tol * tol * info.fro2;
+    return AMM_OK;
+  };
+  int64_t lo = 0, hi = std::min<int64_t>(8, kcap);
+  amm_handle_t best = nullptr;
+  bool ok = false;
+  for (;;) {
+    amm_handle_t h = nullptr;
+    if ((s = trial(hi, &h, &ok)) != AMM_OK) return s;
+    if (ok || hi == kcap) {
+      best = h;
+      break;
+    }
+    amm_handle_destroy(h);
+    lo = hi;
+    hi = std::min(2 * hi, kcap);
+  }
+  // bisection in (lo, hi]: the smallest k of the bracket whose trial meets the tolerance
+  while (ok && hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    amm_handle_t h = nullptr;
+    bool okm = false;
+    if ((s = trial(mid, &h, &okm)) != AMM_OK) {
+      amm_handle_destroy(best);
+      return s;
+    }
+    if (okm) {
+      amm_handle_destroy(best);
+      best = h;
+      hi = mid;
+    } else {
+      amm_handle_destroy(h);
+      lo = mid;
+    }
+  }
+  *out = best;
+  *k_out = hi;
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_error_estimate(amm_handle_t hA, amm_handle_t hB, const float* C, int64_t ldc,
                                            void* stream, double* estimate) {
   if (!estimate) return fail(AMM_ERR_INVALID_ARG, "amm_error_estimate: estimate is NULL");

@@ -62,3 +62,33 @@ def test_choose_k_is_minimal(method, tol):
     assert k == 1 or resid(k - 1) >= tol ** 2 * (1 - 1e-4)
     h = amm.decompose_to_tolerance(A, method, tol)
     assert h.k == k
+
+
+@pytest.mark.parametrize("method,role", [("svd", "left"), ("svd", "right"), ("fourier", "left"), ("fourier", "right")])
+@pytest.mark.parametrize("tol", [0.5, 0.2])
+def test_decompose_to_tolerance_grows_k(method, role, tol):
+    """rSVD / Fourier sparsifier: k grows (doubling, then bisection) until the handle's truncation
+    error meets tol; the trial at k - 1 (same seed) does not, and the error the handle reports is
+    the oracle's for that truncation."""
+    torch, amm = torch_cuda()
+    n = 256
+    g = S.rng(14, 0)
+    sigma = np.exp(-np.arange(n) / 24.0)
+    a = S.spectrum_matrix(sigma, g) + 0.002 * g.standard_normal((n, n))
+    if method == "fourier":
+        a = a + S.toeplitz_uniform(n, g)
+    A = dev32(torch, a)
+    h = amm.decompose_to_tolerance(A, method, tol, role)
+    info = h.info()
+    assert info["resid_fro2"] <= tol ** 2 * info["fro2"] * (1 + 1e-5)
+    if h.k > 1:
+        h1 = amm.decompose(A, method, h.k - 1, role)
+        i1 = h1.info()
+        assert i1["resid_fro2"] > tol ** 2 * i1["fro2"]
+    a64 = as64(A)
+    if method == "svd":
+        t = O.truncate_rsvd(a64, h.k, h.sketch().astype(np.float64))
+    else:
+        f = O.truncate_fourier_left if role == "left" else O.truncate_fourier_right
+        t = f(a64, h.k, forced=h.selection())
+    assert info["resid_fro2"] == pytest.approx(float(np.linalg.norm(t.resid) ** 2), rel=1e-3, abs=1e-6 * info["fro2"])
