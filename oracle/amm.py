@@ -7,7 +7,7 @@ Paper: Kar, Hariprasad, Sai Gowri, Venkatapathi, "Efficient approximations of ma
 multiplication using truncated decompositions" (arXiv 2504.19308).  Section numbers,
 equations and algorithm numbers below are the paper's.
 
-Readings taken where the paper is silent or inconsistent (each also listed in the design doc):
+Readings taken where the paper is silent or inconsistent:
   R1  omega = e^{+2 pi i/n} as in Thm 2.1 (Lemma 3.10 uses the opposite sign).
   R2  The shift identity is W D^k W^* = C^k (Remark after Thm 2.1); the form printed in
       Section 2.3.2 with W^* and W swapped is taken as a typo.
