@@ -67,6 +67,13 @@ def test_argument_errors_without_gpu(lib):
     # circulant lengths are 2^a or 3 * 2^a: 40 and 80 are not
     assert lib.amm_decompose(fake, 40, 40, 40, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
     assert lib.amm_decompose(fake, 80, 80, 80, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
+    # k from a tolerance: outputs required, negative tolerance rejected, before any launch
+    k_out = ctypes.c_int64(0)
+    assert lib.amm_decompose_to_tolerance(fake, 64, 64, 64, 0, 1, 0.1, 0, None, None, None,
+                                          ctypes.byref(k_out)) == 1
+    assert lib.amm_decompose_to_tolerance(fake, 64, 64, 64, 0, 0, -1.0, 0, None, None, ctypes.byref(out),
+                                          ctypes.byref(k_out)) == 1
+    assert lib.amm_set_autotune(0) == 0
     # bad struct size
     opts.struct_size = 3
     assert lib.amm_decompose(fake, 64, 64, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1

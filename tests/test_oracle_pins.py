@@ -650,6 +650,36 @@ def test_planted_mistakes_are_caught(monkeypatch):
     bda, _ = O.brute_force_gradient("circulant", ta, tb, g)
     assert np.abs(da - bda).max() > 1e-6
 
+    # 5) blocked product that drops the padded part of the truncations (treats the padding of A~
+    #    as zero): the first-order identity on a ragged shape breaks
+    a5, b5 = S.rng(34, 0).standard_normal((10, 14)), S.rng(34, 1).uniform(0, 1, (14, 7))
+    tab, tbb = O.truncate_circulant_blocked(a5, 4, 2), O.truncate_circulant_blocked(b5, 4, 2)
+    cut = lambda t: O.Truncation(t.method, t.a, O.pad_to(t.approx[:t.shape0[0], :t.shape0[1]], *t.a.shape))
+    ta5, tb5 = cut(tab), cut(tbb)
+    ta5.shape0, tb5.shape0 = tab.shape0, tbb.shape0
+    wrong = O.blocked_first_order(ta5, tb5)
+    second = (tab.resid @ tbb.resid)[:10, :7].real
+    assert np.abs((a5 @ b5 - wrong) - second).max() > 1e-3
+
+    # 6) mixed backward projecting G B^T instead of G dB^T (the partner's operand in place of its
+    #    residual): the brute-force gradient of the frozen mixed map disagrees.  (Projecting onto S
+    #    instead of S-bar would not be a mistake here: the partner's residual is real, and on a real
+    #    matrix the two projections have the same real part.)
+    n6 = 6
+    a6, b6, g6 = (S.rng(35, i).standard_normal((n6, n6)) for i in range(3))
+    ta6 = O.truncate_circulant(a6, 3)
+    tb6 = O.truncate_rsvd(b6, 2, S.sketch(n6, 2, 35, 1))
+    tb_wrong = O.Truncation(tb6.method, tb6.a, tb6.approx, tb6.sel, Q=tb6.Q)
+    tb_wrong.resid = tb6.a
+    da6, _ = O.mixed_backward(ta6, tb_wrong, g6)
+    f = lambda x: np.sum(g6 * O.frozen_mixed_product(ta6, tb6, x, b6))
+    bda6 = np.zeros_like(a6)
+    for i, j in itertools.product(range(n6), range(n6)):
+        e = np.zeros_like(a6)
+        e[i, j] = 1.0
+        bda6[i, j] = f(e) - f(np.zeros_like(a6))
+    assert np.abs(da6 - bda6).max() > 1e-6
+
 
 # --------------------------------------------------------------------------- error estimation
 
