@@ -703,6 +703,79 @@ def test_posterior_estimate_tracks_observed_error():
         assert 0.9 < est / actual < 1.2, (k, est, actual)
 
 
+def test_posterior_constant_is_lemma31_by_monte_carlo():
+    """Lemma 3.1: for A = Q1 D1 Q2 and B = Q3 D2 Q4 with Haar factors, E||AB||_F^2 equals
+    ||D1||^2 ||D2||^2 / n, the square of the posterior estimate's constant (Cor. 3.7) applied to
+    ||D1||, ||D2|| with ||M|| = 1.  Checked by Monte Carlo at n = 8 within four standard errors.
+    The band uses the exact variance from the fourth moments of a real Haar orthogonal matrix
+    (E q^4 = 3/(n(n+2)); two entries in one row or column 1/(n(n+2)); in neither
+    (n+1)/((n-1)n(n+2))): the variance printed in the appendix assigns one value to every pair of
+    distinct entries and is negative for D1 = D2 = I, where ||AB||^2 = n is deterministic."""
+    n, trials = 8, 4000
+    g = S.rng(7, 0)
+    d1, d2 = np.exp(-np.arange(n) / 3.0), 1.0 + np.arange(n)
+    s = np.empty(trials)
+    for i in range(trials):
+        q1, q2, q3, q4 = (S.haar_orthogonal(n, g) for _ in range(4))
+        s[i] = np.sum((((q1 * d1) @ q2) @ ((q3 * d2) @ q4)) ** 2)
+    al1, al2, be1, be2 = np.sum(d1 ** 2), np.sum(d2 ** 2), np.sum(d1 ** 4), np.sum(d2 ** 4)
+    e4, erow, eoff = 3 / (n * (n + 2)), 1 / (n * (n + 2)), (n + 1) / ((n - 1) * n * (n + 2))
+    es2 = (be1 * be2 * e4 + (be1 * (al2 ** 2 - be2) + (al1 ** 2 - be1) * be2) * erow
+           + (al1 ** 2 - be1) * (al2 ** 2 - be2) * eoff)
+    mean = al1 * al2 / n
+    var = es2 - mean ** 2
+    assert abs(s.var() / var - 1) < 0.1, (s.var(), var)
+    assert abs(s.mean() - mean) <= 4 * math.sqrt(var / trials), (s.mean(), mean)
+    est = O.posterior_estimate(math.sqrt(al1), math.sqrt(al2), 1.0, n)
+    assert abs(est ** 2 - s.mean()) <= 4 * math.sqrt(var / trials)
+    # the same moments at D1 = D2 = I give zero variance
+    one = np.ones(n)
+    a, b = np.sum(one), np.sum(one)
+    v0 = b * b * e4 + 2 * b * (a * a - b) * erow + (a * a - b) ** 2 * eoff - (a * a / n) ** 2
+    assert abs(v0) < 1e-12
+
+
+# Mean and second moment of each distribution of the appendix's front-constant table.
+_MOMENTS = {"uniform01": (0.5, 1 / 3), "rademacher": (0.0, 1.0), "normal01": (0.0, 1.0),
+            "lognormal01": (math.exp(0.5), math.exp(2.0)), "student_t3": (0.0, 3.0)}
+
+
+def _front_constant(mean, m2, n):
+    """E||XY||^2 / (E||X||^2 E||Y||^2) for i.i.d. entries: each (XY)_ij sums n products with
+    second moment m2^2 and n(n-1) cross terms with mean mean^4, so the ratio is
+    1/n + (n-1) mean^4 / (n m2^2); c is its square root (the ratio concentrates as n grows)."""
+    return math.sqrt(1 / n + (n - 1) * mean ** 4 / (n * m2 ** 2))
+
+
+def test_front_constants_table():
+    """The appendix's front constants agree with the closed form from the entry moments (within
+    four printed sigmas at n = 5000) and with Monte Carlo at n = 400; for zero-mean entries the
+    constant is the posterior estimate's 1/sqrt(n) (Cor. 3.7)."""
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "front_constants.txt")) if ln.strip() and not ln.startswith("#")]
+    assert {r[0] for r in rows} == set(_MOMENTS)
+    n = 5000
+    for name, c, scaled, sigma in rows:
+        c, sigma = float(c), float(sigma)
+        closed = _front_constant(*_MOMENTS[name], n)
+        printed = c / math.sqrt(n) if scaled == "1" else c
+        assert abs(closed - printed) <= 4 * sigma, (name, closed, printed)
+        if _MOMENTS[name][0] == 0.0:
+            assert closed == pytest.approx(O.posterior_estimate(1.0, 1.0, 1.0, n), rel=1e-12)
+    gens = {"uniform01": lambda g, s: g.uniform(0.0, 1.0, s),
+            "rademacher": lambda g, s: g.choice([-1.0, 1.0], s),
+            "normal01": lambda g, s: g.standard_normal(s),
+            "lognormal01": lambda g, s: np.exp(g.standard_normal(s))}
+    m, trials = 400, 5
+    for name, gen in gens.items():
+        g = S.rng(11, 0)
+        r = np.empty(trials)
+        for i in range(trials):
+            x, y = gen(g, (m, m)), gen(g, (m, m))
+            r[i] = np.linalg.norm(x @ y) / (np.linalg.norm(x) * np.linalg.norm(y))
+        band = 4 * r.std(ddof=1) / math.sqrt(trials) + 1.0 / m ** 2
+        assert abs(r.mean() - _front_constant(*_MOMENTS[name], m)) <= band, (name, r.mean())
+
+
 def test_posterior_estimate_bounds_gaussian_error():
     """Independent Gaussian operands: the estimate is an upper bound of the observed error."""
     n = 256
