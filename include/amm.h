@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define AMM_VERSION 3
+#define AMM_VERSION 4
 
 typedef enum {
   AMM_OK = 0,
@@ -81,8 +81,9 @@ typedef struct amm_opts {
                                      M = Re M.  amm_handle_get_selection still returns the k
                                      ranked components; the truncation error of amm_handle_info
                                      is that of the closed set.  Default 0.                   */
-  int32_t block;                  /* AMM_CIRCULANT: square block size b (a power of two in
-                                     [16, 8192]) for a rectangular operand (Section 2.3: the
+  int32_t block;                  /* AMM_CIRCULANT: square block size b (a circulant length:
+                                     2^a in [16, 16384] or 3 * 2^a in [48, 6144]) for a
+                                     rectangular operand (Section 2.3: the
                                      cycle decomposition is defined for square matrices, larger
                                      or rectangular ones are taken in square blocks).  Both
                                      dimensions are cut into b x b blocks; a ragged edge is
@@ -235,6 +236,43 @@ amm_status_t amm_decompose_to_tolerance(const void* A, int64_t rows, int64_t col
  */
 amm_status_t amm_error_estimate(amm_handle_t hA, amm_handle_t hB, const float* C, int64_t ldc,
                                 void* stream, double* estimate);
+
+/*
+ * A priori estimate of the relative error ||dA dB||_F / ||A B||_F before the product is formed
+ * (Section 2.5; Lemma 3.1 and the statements after it for independent entries):
+ *     c_resid ||dA||_F ||dB||_F / (c_ab ||A||_F ||B||_F),
+ * with the truncation errors and norms of the two handles (amm_handle_info).  c_ab and c_resid
+ * are the front constants of E||X Y||_F ~ c ||X||_F ||Y||_F for the operands and for the
+ * residues: 1/sqrt(n) for zero-mean entries (n the inner dimension), 3/4 for U(0,1), 1/e for
+ * exp(N(0,1)) (appendix table of front constants).  Both must be > 0.  A residue left after the
+ * dominant component (the mean) is taken out has zero-mean entries, e.g. c_ab = 3/4 and
+ * c_resid = 1/sqrt(n) for U(0,1) operands.  Synchronises both handles' streams; *estimate is a
+ * host double.  AMM_ERR_STATE when ||A||_F ||B||_F = 0.
+ */
+amm_status_t amm_apriori_estimate(amm_handle_t hA, amm_handle_t hB, double c_ab, double c_resid,
+                                  double* estimate);
+
+/*
+ * The most suitable decomposition of one operand at a given k (Section 2.5: the relative
+ * truncation error ||dA||_F / ||A||_F of each decomposition at k components decides; A and B may
+ * use different ones, Section 1 and Section 2.5).  Each method in host_methods[0 .. n_methods)
+ * is decomposed with k and opts as by amm_decompose (opts->block is passed to AMM_CIRCULANT only),
+ * its error read with amm_handle_info, and the handle with the smallest ||dA||_F^2 / ||A||_F^2
+ * is kept (ties: the earlier candidate); the others are destroyed.  A candidate that rejects
+ * this shape or k (AMM_ERR_UNSUPPORTED_SIZE / AMM_ERR_INVALID_ARG from amm_decompose, e.g. the
+ * cycle sparsifier on a rectangular operand) is skipped; when every candidate is skipped, the
+ * last one's status is returned.  Other errors end the call with nothing kept.  The truncation
+ * error of a pair-closed circulant selection is that of the closed set, and that of a blocked
+ * circulant operand includes its padding (the operand the product uses).
+ *   host_methods  HOST array of amm_method_t values; n_methods >= 1
+ *   opts          may be NULL; forced selections and caller sketches (per method) are rejected
+ *   out           receives the kept handle; *method_out its method (host)
+ * Synchronises `stream`.
+ */
+amm_status_t amm_decompose_best_method(const void* A, int64_t rows, int64_t cols, int64_t lda,
+                                       amm_dtype_t dtype, const int32_t* host_methods,
+                                       int32_t n_methods, int64_t k, const amm_opts_t* opts,
+                                       void* stream, amm_handle_t* out, int32_t* method_out);
 
 /*
  * Copy the selection to host memory: circulant component indices / cycle indices in

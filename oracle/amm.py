@@ -478,6 +478,26 @@ def posterior_estimate(resid_a_fro, resid_b_fro, m_fro, n) -> float:
     return float(resid_a_fro * resid_b_fro / (math.sqrt(n) * m_fro))
 
 
+def apriori_estimate(resid_a_fro, resid_b_fro, a_fro, b_fro, c_ab, c_resid) -> float:
+    """Section 2.5, a priori (before the product): E||dA dB|| ~ c_resid ||dA|| ||dB|| and
+    E||AB|| ~ c_ab ||A|| ||B||, with front constants for independent entries (Section 3, appendix
+    table): 1/sqrt(n) for zero mean, 3/4 for U(0,1)."""
+    return float(c_resid * resid_a_fro * resid_b_fro / (c_ab * a_fro * b_fro))
+
+
+def best_method(a: np.ndarray, k: int, methods, phi=None, side: str = "left"):
+    """Section 2.5: the suitability of a decomposition at k components is its relative truncation
+    error ||dA||_F / ||A||_F.  Returns (method, truncation) of the smallest; ties keep the earlier
+    method of the list."""
+    best = None
+    for m in methods:
+        t = truncate(m, a, k, phi=phi, side=side)
+        r = float(np.linalg.norm(t.resid) / np.linalg.norm(a))
+        if best is None or r < best[0]:
+            best = (r, m, t)
+    return best[1], best[2]
+
+
 # ---------------------------------------------------------------------------
 # Backward of the frozen first-order map (reading R10)
 # ---------------------------------------------------------------------------

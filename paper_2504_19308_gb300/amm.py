@@ -64,6 +64,12 @@ SIGNATURES = {
                                     ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "amm_error_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "amm_apriori_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "amm_decompose_best_method": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                 ctypes.c_int64, ctypes.POINTER(Opts), ctypes.c_void_p,
+                                                 ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int32)]),
     "amm_approx_matmul_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                                   ctypes.c_void_p]),
@@ -286,6 +292,43 @@ def error_estimate(hA: Handle, hB: Handle, C: torch.Tensor) -> float:
     _check(load_library().amm_error_estimate(hA.ptr, hB.ptr, C.data_ptr(), C.stride(0), _stream_ptr(C.device),
                                              ctypes.byref(est)), "amm_error_estimate")
     return est.value
+
+
+def apriori_estimate(hA: Handle, hB: Handle, c_ab: float, c_resid: float) -> float:
+    """amm_apriori_estimate: c_resid ||dA|| ||dB|| / (c_ab ||A|| ||B||) before the product (Section 2.5),
+    with the front constants of the operands (c_ab) and of the residues (c_resid)."""
+    est = ctypes.c_double(0.0)
+    _check(load_library().amm_apriori_estimate(hA.ptr, hB.ptr, float(c_ab), float(c_resid), ctypes.byref(est)),
+           "amm_apriori_estimate")
+    return est.value
+
+
+def decompose_best_method(A: torch.Tensor, methods, k: int, role: str = "left", seed: int = 0,
+                          compute: str = "f32", pair_closed: bool = False, block: int = 0):
+    """amm_decompose_best_method: decompose A with each of `methods` at k and keep the one with the
+    smallest relative truncation error (Section 2.5).  Returns (handle, method name)."""
+    lib = load_library()
+    _require_cuda(A, "A")
+    if A.dtype not in DTYPES:
+        raise ValueError("A must be float32 or bfloat16")
+    names = list(methods)
+    if not names:
+        raise ValueError("methods is empty")
+    codes = (ctypes.c_int32 * len(names))(*[METHODS[m] for m in names])
+    opts = Opts()
+    _check(lib.amm_opts_init(ctypes.byref(opts)), "amm_opts_init")
+    opts.role = ROLES[role]
+    opts.seed = seed
+    opts.compute = {"f32": 0, "bf16": 1}[compute]
+    opts.pair_closed = 1 if pair_closed else 0
+    opts.block = int(block)
+    out, chosen = ctypes.c_void_p(0), ctypes.c_int32(-1)
+    _check(lib.amm_decompose_best_method(A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), DTYPES[A.dtype], codes,
+                                         len(names), k, ctypes.byref(opts), _stream_ptr(A.device), ctypes.byref(out),
+                                         ctypes.byref(chosen)), "amm_decompose_best_method")
+    method = {v: n for n, v in METHODS.items()}[chosen.value]
+    blocked = method == "circulant" and block and not (A.shape[0] == block and A.shape[1] == block)
+    return Handle(out.value, A, method, role, k, (), int(block) if blocked else 0), method
 
 
 def approx_matmul_backward(hA: Handle, hB: Handle, dC: torch.Tensor, need_dA: bool = True, need_dB: bool = True):

@@ -794,6 +794,95 @@ extern "C" amm_status_t amm_error_estimate(amm_handle_t hA, amm_handle_t hB, con
   return AMM_OK;
 }
 
+// A priori estimate of the relative error (Section 2.5, before the product is formed):
+// E||dA dB||_F ~ c_resid ||dA||_F ||dB||_F and E||A B||_F ~ c_ab ||A||_F ||B||_F, the constants
+// those of Section 3 for independent entries (1/sqrt(n) for zero mean; the appendix tabulates
+// others, e.g. 3/4 for U(0,1)).  Only the handles' norms enter: no device work.
+extern "C" amm_status_t amm_apriori_estimate(amm_handle_t hA, amm_handle_t hB, double c_ab, double c_resid,
+                                             double* estimate) {
+  if (!estimate) return fail(AMM_ERR_INVALID_ARG, "amm_apriori_estimate: estimate is NULL");
+  if (!(c_ab > 0.0) || !(c_resid > 0.0))
+    return fail(AMM_ERR_INVALID_ARG, "amm_apriori_estimate: the constants must be > 0");
+  amm_status_t s = check_pair(hA, hB);
+  if (s != AMM_OK) return s;
+  amm_info_t ia, ib;
+  if ((s = amm_handle_info(hA, &ia)) != AMM_OK) return s;
+  if ((s = amm_handle_info(hB, &ib)) != AMM_OK) return s;
+  if (!(ia.fro2 > 0.0) || !(ib.fro2 > 0.0)) return fail(AMM_ERR_STATE, "amm_apriori_estimate: ||A||_F ||B||_F = 0");
+  const double ra = std::max(ia.resid_fro2, 0.0), rb = std::max(ib.resid_fro2, 0.0);
+  *estimate = (c_resid * std::sqrt(ra * rb)) / (c_ab * std::sqrt(ia.fro2 * ib.fro2));
+  return AMM_OK;
+}
+
+// The most suitable of several decompositions of one operand at a given k (Section 2.5: the
+// relative truncation error ||dA||_F / ||A||_F of each candidate decides; the paper lets A and B
+// use different ones).  Candidates that do not take this shape or k are skipped.
+extern "C" amm_status_t amm_decompose_best_method(const void* A, int64_t rows, int64_t cols, int64_t lda,
+                                                  amm_dtype_t dtype, const int32_t* host_methods,
+                                                  int32_t n_methods, int64_t k, const amm_opts_t* opts,
+                                                  void* stream, amm_handle_t* out, int32_t* method_out) {
+  if (!out || !method_out) return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: NULL output");
+  if (!A) return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: A is NULL");
+  if (!host_methods || n_methods < 1)
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: no candidate methods");
+  if (rows <= 0 || cols <= 0 || lda < cols)
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: bad shape %lldx%lld, lda=%lld", (long long)rows,
+                (long long)cols, (long long)lda);
+  if (dtype != AMM_F32 && dtype != AMM_BF16) return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: bad dtype");
+  if (k < 1) return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: k=%lld < 1", (long long)k);
+  for (int32_t i = 0; i < n_methods; ++i) {
+    const int32_t m = host_methods[i];
+    if (m != AMM_SVD && m != AMM_CIRCULANT && m != AMM_SPARSE_FOURIER && m != AMM_SPARSE_CYCLE)
+      return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: bad method %d", (int)m);
+  }
+  if (opts && opts->struct_size != sizeof(amm_opts_t))
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: opts->struct_size=%u, expected %zu",
+                opts->struct_size, sizeof(amm_opts_t));
+  if (opts && (opts->forced_selection || opts->sketch))
+    return fail(AMM_ERR_INVALID_ARG, "amm_decompose_best_method: forced selections and sketches are per method");
+  amm_opts_t base;
+  amm_opts_init(&base);
+  if (opts) base = *opts;
+  amm_handle_t best = nullptr;
+  int32_t best_method = -1;
+  double best_rel = 0.0;
+  amm_status_t last = AMM_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n_methods; ++i) {
+    const amm_method_t m = (amm_method_t)host_methods[i];
+    amm_opts_t o = base;
+    if (m != AMM_CIRCULANT) o.block = 0;  // square blocks are an option of the circulant method only
+    amm_handle_t h = nullptr;
+    amm_status_t s = amm_decompose(A, rows, cols, lda, dtype, m, k, &o, stream, &h);
+    if (s == AMM_ERR_UNSUPPORTED_SIZE || s == AMM_ERR_INVALID_ARG) {  // this shape / k is not one of m's
+      last = s;
+      continue;
+    }
+    if (s != AMM_OK) {
+      if (best) amm_handle_destroy(best);
+      return s;
+    }
+    amm_info_t info;
+    if ((s = amm_handle_info(h, &info)) != AMM_OK) {
+      amm_handle_destroy(h);
+      if (best) amm_handle_destroy(best);
+      return s;
+    }
+    const double rel = info.fro2 > 0.0 ? std::max(info.resid_fro2, 0.0) / info.fro2 : 0.0;
+    if (!best || rel < best_rel) {  // ties keep the earlier candidate
+      if (best) amm_handle_destroy(best);
+      best = h;
+      best_method = (int32_t)m;
+      best_rel = rel;
+    } else {
+      amm_handle_destroy(h);
+    }
+  }
+  if (!best) return last;  // amm_last_error() holds the last candidate's reason
+  *out = best;
+  *method_out = best_method;
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t cap, int64_t* count) {
   if (!h || !host_idx || !count) return fail(AMM_ERR_INVALID_ARG, "amm_handle_get_selection: NULL argument");
   if (h->method == AMM_SPARSE_FOURIER) {

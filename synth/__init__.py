@@ -101,6 +101,24 @@ def circulant_from_column(c: np.ndarray) -> np.ndarray:
     return np.asarray(c)[(r - q) % n]
 
 
+def two_structure_cases(n: int, g) -> dict:
+    """Four n x n inputs, each built from two pieces of one kind of structure: a circulant matrix,
+    a rank-2 product of Gaussian factors, two wrapped diagonals with random entries
+    (X[(l + j) mod n, l] for j = 0, 1), and rows that are single sinusoids
+    X[r, q] = a_r cos(2 pi f_r q / n + p_r) with 0 < f_r < n/2."""
+    circ = circulant_from_column(g.standard_normal(n))
+    lowrank = g.standard_normal((n, 2)) @ g.standard_normal((2, n))
+    band = np.zeros((n, n))
+    l = np.arange(n)
+    for j in (0, 1):
+        band[(l + j) % n, l] = g.standard_normal(n)
+    f = g.integers(1, n // 2, size=n)[:, None]
+    amp = g.standard_normal(n)[:, None]
+    ph = g.uniform(0.0, 2.0 * np.pi, n)[:, None]
+    waves = amp * np.cos(2.0 * np.pi * f * l[None, :] / n + ph)
+    return {"circulant": circ, "svd": lowrank, "cycle": band, "fourier": waves}
+
+
 def gaussian(shape, g, sd=1.0):
     return sd * g.standard_normal(shape)
 

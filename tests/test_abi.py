@@ -47,7 +47,7 @@ def test_library_resolves_every_symbol_at_load(lib):
 def test_status_strings(lib):
     assert lib.amm_status_string(0) == b"AMM_OK"
     assert lib.amm_status_string(5) == b"AMM_ERR_TIMEOUT"
-    assert lib.amm_version() == 3
+    assert lib.amm_version() == 4
 
 
 def test_argument_errors_without_gpu(lib):
@@ -74,6 +74,37 @@ def test_argument_errors_without_gpu(lib):
     assert lib.amm_decompose_to_tolerance(fake, 64, 64, 64, 0, 0, -1.0, 0, None, None, ctypes.byref(out),
                                           ctypes.byref(k_out)) == 1
     assert lib.amm_set_autotune(0) == 0
+    # method choice: outputs, candidates and per-method options checked before any launch; a
+    # candidate that does not take the shape is skipped, and with none left its status returns
+    cand = (ctypes.c_int32 * 2)(1, 1)
+    chosen = ctypes.c_int32(-1)
+    assert lib.amm_decompose_best_method(fake, 64, 64, 64, 0, cand, 2, 4, None, None, None,
+                                         ctypes.byref(chosen)) == 1
+    assert lib.amm_decompose_best_method(None, 64, 64, 64, 0, cand, 2, 4, None, None, ctypes.byref(out),
+                                         ctypes.byref(chosen)) == 1
+    assert lib.amm_decompose_best_method(fake, 64, 64, 64, 0, None, 2, 4, None, None, ctypes.byref(out),
+                                         ctypes.byref(chosen)) == 1
+    assert lib.amm_decompose_best_method(fake, 64, 64, 64, 0, cand, 0, 4, None, None, ctypes.byref(out),
+                                         ctypes.byref(chosen)) == 1
+    bad = (ctypes.c_int32 * 1)(7)
+    assert lib.amm_decompose_best_method(fake, 64, 64, 64, 0, bad, 1, 4, None, None, ctypes.byref(out),
+                                         ctypes.byref(chosen)) == 1
+    forced = (ctypes.c_int32 * 4)(0, 1, 2, 3)
+    fo = amm.Opts()
+    assert lib.amm_opts_init(ctypes.byref(fo)) == 0
+    fo.forced_selection = ctypes.cast(forced, ctypes.POINTER(ctypes.c_int32))
+    assert lib.amm_decompose_best_method(fake, 64, 64, 64, 0, cand, 2, 4, ctypes.byref(fo), None, ctypes.byref(out),
+                                         ctypes.byref(chosen)) == 1
+    assert lib.amm_decompose_best_method(fake, 40, 40, 40, 0, cand, 2, 4, None, None, ctypes.byref(out),
+                                         ctypes.byref(chosen)) == 2
+    assert b"n=40" in lib.amm_last_error()
+    assert out.value in (None, 0) and chosen.value == -1
+    # a priori estimate: output, constants and handles checked on the host
+    est = ctypes.c_double(0.0)
+    assert lib.amm_apriori_estimate(None, None, 1.0, 1.0, None) == 1
+    assert lib.amm_apriori_estimate(None, None, 0.0, 1.0, ctypes.byref(est)) == 1
+    assert lib.amm_apriori_estimate(None, None, 1.0, float("nan"), ctypes.byref(est)) == 1
+    assert lib.amm_apriori_estimate(None, None, 1.0, 1.0, ctypes.byref(est)) == 1
     # bad struct size
     opts.struct_size = 3
     assert lib.amm_decompose(fake, 64, 64, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1

@@ -776,6 +776,51 @@ def test_front_constants_table():
         assert abs(r.mean() - _front_constant(*_MOMENTS[name], m)) <= band, (name, r.mean())
 
 
+def test_apriori_estimate_tracks_observed_error():
+    """Section 2.5, before the product: with the front constants of the entries (3/4 for the U(0,1)
+    operands; 1/sqrt(n) for the residues, zero-mean once the dominant component is kept) the a
+    priori estimate predicts the observed error of General x Toeplitz within 5%; for Gaussian
+    operands both constants are 1/sqrt(n) and the estimate is the ratio of the truncation errors."""
+    n = 512
+    a, b = S.general_times_toeplitz(n, seed=0)
+    na, nb = np.linalg.norm(a), np.linalg.norm(b)
+    for k in (1, 3, 5, 9):
+        ta, tb = O.truncate("circulant", a, k), O.truncate("circulant", b, k)
+        actual = np.linalg.norm(ta.resid @ tb.resid) / np.linalg.norm(a @ b)
+        est = O.apriori_estimate(np.linalg.norm(ta.resid), np.linalg.norm(tb.resid), na, nb, 0.75, 1 / math.sqrt(n))
+        assert 0.95 < est / actual < 1.05, (k, est, actual)
+    n, k = 256, 32
+    g = S.rng(n, 5)
+    a, b = g.standard_normal((n, n)), g.standard_normal((n, n))
+    for method in ("circulant", "cycle", "svd"):
+        ta = O.truncate(method, a, k, phi=S.sketch(n, k, 5, 0))
+        tb = O.truncate(method, b, k, phi=S.sketch(n, k, 5, 1))
+        actual = np.linalg.norm(ta.resid @ tb.resid) / np.linalg.norm(a @ b)
+        c = 1 / math.sqrt(n)
+        est = O.apriori_estimate(np.linalg.norm(ta.resid), np.linalg.norm(tb.resid), np.linalg.norm(a),
+                                 np.linalg.norm(b), c, c)
+        assert 0.95 < est / actual < 1.05, (method, est, actual)
+
+
+def test_best_method_special_cases():
+    """Section 2.5: each input that one decomposition represents exactly with k = 2 components (a
+    circulant matrix, rank 2, two cycles, one conjugate frequency pair per row) selects that
+    decomposition: zero truncation error, every other method far from zero, in either order."""
+    n = 32
+    cases = S.two_structure_cases(n, S.rng(41, 0))
+    order = ["circulant", "svd", "cycle", "fourier"]
+    phi = S.sketch(n, 2, 41, 0)
+    for want, a in cases.items():
+        for methods in (order, order[::-1]):
+            got, t = O.best_method(a, 2, methods, phi=phi)
+            assert got == want, (want, methods, got)
+            assert np.linalg.norm(t.resid) <= 1e-12 * np.linalg.norm(a)
+        for other in order:
+            if other != want:
+                t = O.truncate(other, a, 2, phi=phi)
+                assert np.linalg.norm(t.resid) > 1e-2 * np.linalg.norm(a), (want, other)
+
+
 def test_posterior_estimate_bounds_gaussian_error():
     """Independent Gaussian operands: the estimate is an upper bound of the observed error."""
     n = 256
