@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define AMM_VERSION 4
+#define AMM_VERSION 5
 
 typedef enum {
   AMM_OK = 0,
@@ -273,6 +273,33 @@ amm_status_t amm_decompose_best_method(const void* A, int64_t rows, int64_t cols
                                        amm_dtype_t dtype, const int32_t* host_methods,
                                        int32_t n_methods, int64_t k, const amm_opts_t* opts,
                                        void* stream, amm_handle_t* out, int32_t* method_out);
+
+/*
+ * Re dA = A - Re A~ of a handle as a dense FP32 matrix (rows x cols, leading dimension ldd >=
+ * cols, DEVICE, caller-owned, overwritten): the residue that amm_refine_product's second-level
+ * decompositions take.  FP32 operands without circulant blocks; the Fourier sparsifier as the
+ * left operand only (else AMM_ERR_NOT_IMPLEMENTED).  Asynchronous on `stream`, which must be
+ * ordered after the handle's stream.
+ */
+amm_status_t amm_handle_residual(amm_handle_t h, float* D, int64_t ldd, void* stream);
+
+/*
+ * Refinement of a computed product (Section 2.5: when the estimated error is not small enough,
+ * approximate dA dB by the same approach and add it).  For real A and B,
+ *     Re(dA dB) = Re dA Re dB - Im(A~) Im(B~),
+ * and
+ *     C += Re(A2~ Re dB + dA2 B2~) - Im(A~) Im(B~),
+ * where hA2 (role LEFT, rows x cols of A) and hB2 (role RIGHT, the shape of B) are decompositions,
+ * by any methods and k, of Re dA and Re dB as written by amm_handle_residual(hA) / (hB), and the
+ * last term (zero unless both truncations can be complex: circulant with a split conjugate pair,
+ * Fourier sparsifier) is exact.  Then A B - C = Re(dA2 dB2), the product of the second-level
+ * residues.  C (m x p, ldc, DEVICE) must hold Re M of hA, hB (amm_approx_matmul) on entry.  hA and
+ * hB: FP32, no circulant blocks (else AMM_ERR_NOT_IMPLEMENTED).  That hA2 / hB2 decompose the
+ * residues is the caller's contract; shapes and roles are checked (AMM_ERR_STATE).  Asynchronous
+ * on `stream`, which must be ordered after the four handles' streams.
+ */
+amm_status_t amm_refine_product(amm_handle_t hA, amm_handle_t hB, amm_handle_t hA2, amm_handle_t hB2,
+                                float* C, int64_t ldc, void* stream);
 
 /*
  * Copy the selection to host memory: circulant component indices / cycle indices in

@@ -26,6 +26,8 @@ Readings taken where the paper is silent or inconsistent:
       resulting bilinear map.
   R13 Rectangular circulant operands: b x b blocks, ragged edge zero-padded, top-k per block,
       Eq. (2.3) on the padded operands, padded rows / columns of the product dropped.
+  R16 Refinement of Section 2.5: the real parts of the residues are decomposed again and their
+      first-order product added; the product of the imaginary parts is added exactly.
 """
 from __future__ import annotations
 
@@ -612,6 +614,15 @@ def mixed_product(ta: Truncation, tb: Truncation) -> np.ndarray:
     two operands may differ).  Eq. (2.3) with each side's space-domain truncation; for the
     Fourier sparsifier that is A_s = A~_a W (left) or B_s = W^* B~_a (right)."""
     return first_order(ta, tb).real
+
+
+def refine(ta: Truncation, tb: Truncation, ta2: Truncation, tb2: Truncation) -> np.ndarray:
+    """Section 2.5 (after the posterior estimate): when Re M is not accurate enough, the residue
+    product dA dB is approximated by the same first-order approach and added.  For real A, B,
+    Re(dA dB) = Re dA Re dB - Im dA Im dB.  Reading R16: ta2, tb2 truncate Re dA (m x n) and
+    Re dB (n x p), their first-order product stands for the first term, and the second term
+    (non-zero only when both first truncations are complex) is added exactly."""
+    return first_order(ta, tb).real + first_order(ta2, tb2).real - ta.resid.imag @ tb.resid.imag
 
 
 # ---------------------------------------------------------------------------

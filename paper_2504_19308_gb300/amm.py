@@ -66,6 +66,9 @@ SIGNATURES = {
                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "amm_apriori_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                             ctypes.POINTER(ctypes.c_double)]),
+    "amm_handle_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "amm_refine_product": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "amm_decompose_best_method": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                                  ctypes.c_int64, ctypes.POINTER(Opts), ctypes.c_void_p,
@@ -301,6 +304,37 @@ def apriori_estimate(hA: Handle, hB: Handle, c_ab: float, c_resid: float) -> flo
     _check(load_library().amm_apriori_estimate(hA.ptr, hB.ptr, float(c_ab), float(c_resid), ctypes.byref(est)),
            "amm_apriori_estimate")
     return est.value
+
+
+def residual(h: Handle) -> torch.Tensor:
+    """amm_handle_residual: Re dA = A - Re A~ as a dense FP32 tensor of the operand's shape."""
+    out = torch.empty(h.shape, dtype=torch.float32, device=h.source.device)
+    _check(load_library().amm_handle_residual(h.ptr, out.data_ptr(), out.stride(0), _stream_ptr(out.device)),
+           "amm_handle_residual")
+    return out
+
+
+def refine_product(hA: Handle, hB: Handle, hA2: Handle, hB2: Handle, C: torch.Tensor) -> torch.Tensor:
+    """amm_refine_product: C += Re M2 - Im(A~) Im(B~) in place, hA2 / hB2 decompositions of
+    residual(hA) / residual(hB) (Section 2.5)."""
+    _require_cuda(C, "C")
+    if C.dtype != torch.float32:
+        raise ValueError("C must be float32")
+    _check(load_library().amm_refine_product(hA.ptr, hB.ptr, hA2.ptr, hB2.ptr, C.data_ptr(), C.stride(0),
+                                             _stream_ptr(C.device)), "amm_refine_product")
+    return C
+
+
+def refine(hA: Handle, hB: Handle, C: torch.Tensor, k2: int, methods=None, sketch_a=None, sketch_b=None,
+           seed: int = 0, compute: str = "f32"):
+    """Section 2.5 refinement of C = Re M: decompose Re dA and Re dB with k2 components (by the first
+    handles' methods unless `methods` = (method_a, method_b) is given) and add their first-order
+    product and the exact Im dA Im dB term to C in place.  Returns (C, hA2, hB2)."""
+    ma, mb = methods if methods is not None else (hA.method, hB.method)
+    hA2 = decompose(residual(hA), ma, k2, "left", sketch=sketch_a, seed=seed, compute=compute)
+    hB2 = decompose(residual(hB), mb, k2, "right", sketch=sketch_b, seed=seed, compute=compute)
+    refine_product(hA, hB, hA2, hB2, C)
+    return C, hA2, hB2
 
 
 def decompose_best_method(A: torch.Tensor, methods, k: int, role: str = "left", seed: int = 0,

@@ -883,6 +883,25 @@ extern "C" amm_status_t amm_decompose_best_method(const void* A, int64_t rows, i
   return AMM_OK;
 }
 
+extern "C" amm_status_t amm_handle_residual(amm_handle_t h, float* D, int64_t ldd, void* stream) {
+  if (!h || !D) return fail(AMM_ERR_INVALID_ARG, "amm_handle_residual: NULL argument");
+  if (ldd < h->cols)
+    return fail(AMM_ERR_INVALID_ARG, "amm_handle_residual: ldd=%lld < cols=%lld", (long long)ldd, (long long)h->cols);
+  return handle_residual(h, D, ldd, (cudaStream_t)stream);
+}
+
+extern "C" amm_status_t amm_refine_product(amm_handle_t hA, amm_handle_t hB, amm_handle_t hA2, amm_handle_t hB2,
+                                           float* C, int64_t ldc, void* stream) {
+  if (!C) return fail(AMM_ERR_INVALID_ARG, "amm_refine_product: C is NULL");
+  amm_status_t s = check_pair(hA, hB);
+  if (s != AMM_OK) return s;
+  if ((s = check_pair(hA2, hB2)) != AMM_OK) return s;
+  if (ldc < hB->cols) return fail(AMM_ERR_INVALID_ARG, "amm_refine_product: ldc too small");
+  if (hA2->rows != hA->rows || hA2->cols != hA->cols || hB2->rows != hB->rows || hB2->cols != hB->cols)
+    return fail(AMM_ERR_STATE, "amm_refine_product: the residues' handles must have the shapes of A and B");
+  return refine_product(hA, hB, hA2, hB2, C, ldc, (cudaStream_t)stream);
+}
+
 extern "C" amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t cap, int64_t* count) {
   if (!h || !host_idx || !count) return fail(AMM_ERR_INVALID_ARG, "amm_handle_get_selection: NULL argument");
   if (h->method == AMM_SPARSE_FOURIER) {

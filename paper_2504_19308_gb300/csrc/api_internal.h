@@ -128,6 +128,9 @@ cudaError_t blocked_right_apply(Handle* b, const float* Y, int64_t ldy, int64_t 
 cudaError_t blocked_residual(Handle* a, bool imag, float* D, int64_t ldd, cudaStream_t st);
 // mixed.cu
 amm_status_t mixed_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStream_t st);
+// D = Re dA (rows x cols, ldd); C += Re M2 - Im(A~) Im(B~) with a2, b2 decompositions of Re dA, Re dB
+amm_status_t handle_residual(Handle* h, float* D, int64_t ldd, cudaStream_t st);
+amm_status_t refine_product(Handle* a, Handle* b, Handle* a2, Handle* b2, float* C, int64_t ldc, cudaStream_t st);
 
 amm_status_t svd_get_sketch(Handle* h, float* host_phi, int64_t cap);
 }  // namespace amm

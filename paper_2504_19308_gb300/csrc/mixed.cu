@@ -297,4 +297,81 @@ amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, f
   return AMM_OK;
 }
 
+// ---------------------------------------------------------------------------- refinement
+// Section 2.5: when Re M is not accurate enough, the residue product is approximated by the same
+// first-order approach and added.  For real A, B,
+//   Re(dA dB) = Re dA Re dB - Im dA Im dB = Re dA Re dB - Im(A~) Im(B~),
+// the first term by the first-order product of decompositions of Re dA and Re dB (handles a2, b2,
+// made by the caller from amm_handle_residual), the second exactly (non-zero only when both
+// truncations can be complex).
+
+namespace {
+
+// C += T - U (U may be NULL), rows x cols
+__global__ void __launch_bounds__(256) add_diff_kernel(float* __restrict__ C, int64_t ldc, const float* __restrict__ T,
+                                                       int64_t ldt, const float* __restrict__ U, int64_t ldu,
+                                                       int64_t rows, int64_t cols) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t r = e / cols, c = e - r * cols;
+  float v = T[r * ldt + c];
+  if (U != nullptr) v -= U[r * ldu + c];
+  C[r * ldc + c] += v;
+}
+
+amm_status_t refinable(const Handle* h, const char* what) {
+  if (h->dtype != AMM_F32)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "%s: BF16 operands are not built (use FP32 inputs)", what);
+  if (h->blk.b) return fail(AMM_ERR_NOT_IMPLEMENTED, "%s: circulant blocks are not built", what);
+  return AMM_OK;
+}
+
+}  // namespace
+
+amm_status_t handle_residual(Handle* h, float* D, int64_t ldd, cudaStream_t st) {
+  amm_status_t s = refinable(h, "amm_handle_residual");
+  if (s != AMM_OK) return s;
+  if (h->method == AMM_SPARSE_FOURIER && h->role != AMM_LEFT)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "amm_handle_residual: the Fourier sparsifier's right operand is not built");
+  const int64_t m = h->rows, n = h->cols;
+  Buf buf(st);
+  float* T = buf.get<float>((size_t)m * n);  // the pieces write a dense m x n scratch, copied out
+  cudaError_t e = buf.e;
+  if (e == cudaSuccess) e = residual(h, T, n, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(D, sizeof(float) * ldd, T, sizeof(float) * n, sizeof(float) * n, m,
+                          cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "amm_handle_residual");
+  return AMM_OK;
+}
+
+amm_status_t refine_product(Handle* a, Handle* b, Handle* a2, Handle* b2, float* C, int64_t ldc, cudaStream_t st) {
+  amm_status_t s;
+  if ((s = refinable(a, "amm_refine_product")) != AMM_OK || (s = refinable(b, "amm_refine_product")) != AMM_OK)
+    return s;
+  const int64_t m = a->rows, n = a->cols, p = b->cols;
+  const bool im = can_be_complex(a) && can_be_complex(b);
+  Buf buf(st);
+  float* T = buf.get<float>((size_t)m * p);
+  float* U = im ? buf.get<float>((size_t)m * p) : nullptr;
+  float* I = im ? buf.get<float>((size_t)m * n) : nullptr;
+  if (buf.e != cudaSuccess) return cuda_fail(buf.e, "amm_refine_product: scratch");
+  // T = Re M2, the first-order product of the residues' decompositions
+  if ((s = amm_approx_matmul(a2, b2, T, p, st)) != AMM_OK) return s;
+  cudaError_t e = cudaSuccess;
+  if (im) {  // U = Im(A~) Im(B~)
+    e = cudaMemsetAsync(U, 0, sizeof(float) * (size_t)m * p, st);
+    if (e == cudaSuccess) e = imag_part(a, I, n, st);
+    if (e == cudaSuccess) e = right_apply_imag(b, I, n, m, U, p, st);
+  }
+  if (e == cudaSuccess) {
+    AMM_TRACE_W("refine_add", st, 0.0, 4.0 * (double)m * p * (im ? 4 : 3), nullptr);
+    const int64_t total = m * p;
+    add_diff_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(C, ldc, T, p, U, p, m, p);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "amm_refine_product");
+  return AMM_OK;
+}
+
 }  // namespace amm

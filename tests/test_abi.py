@@ -47,7 +47,7 @@ def test_library_resolves_every_symbol_at_load(lib):
 def test_status_strings(lib):
     assert lib.amm_status_string(0) == b"AMM_OK"
     assert lib.amm_status_string(5) == b"AMM_ERR_TIMEOUT"
-    assert lib.amm_version() == 4
+    assert lib.amm_version() == 5
 
 
 def test_argument_errors_without_gpu(lib):
@@ -99,6 +99,10 @@ def test_argument_errors_without_gpu(lib):
                                          ctypes.byref(chosen)) == 2
     assert b"n=40" in lib.amm_last_error()
     assert out.value in (None, 0) and chosen.value == -1
+    # refinement: outputs and handles checked on the host
+    assert lib.amm_handle_residual(None, fake, 64, None) == 1
+    assert lib.amm_refine_product(None, None, None, None, None, 64, None) == 1
+    assert lib.amm_refine_product(None, None, None, None, fake, 64, None) == 1
     # a priori estimate: output, constants and handles checked on the host
     est = ctypes.c_double(0.0)
     assert lib.amm_apriori_estimate(None, None, 1.0, 1.0, None) == 1

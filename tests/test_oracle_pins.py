@@ -821,6 +821,55 @@ def test_best_method_special_cases():
                 assert np.linalg.norm(t.resid) > 1e-2 * np.linalg.norm(a), (want, other)
 
 
+def test_refinement_identity():
+    """Section 2.5 refinement (reading R16): AB - refine equals Re(dA2 dB2), the product of the
+    second-level residues, for every pair of methods the library refines (complex first truncations
+    included, where the exact Im dA Im dB term is needed); an untruncated second level gives AB."""
+    n = 16
+    g = S.rng(44, 0)
+    a, b = g.standard_normal((n, n)) + 0.5, g.standard_normal((n, n)) + 0.5
+    ab = a @ b
+    scale = np.abs(ab).max()
+    pairs = [("circulant", "circulant"), ("svd", "svd"), ("cycle", "cycle"), ("svd", "circulant"),
+             ("fourier", "circulant"), ("circulant", "cycle"), ("fourier", "svd")]
+    complex_seen = False
+    for ma, mb in pairs:
+        ta = O.truncate(ma, a, 3, phi=S.sketch(n, 3, 44, 0), side="left")
+        tb = O.truncate(mb, b, 3, phi=S.sketch(n, 3, 44, 1), side="right")
+        ta2 = O.truncate(ma, ta.resid.real, 2, phi=S.sketch(n, 2, 45, 0), side="left")
+        tb2 = O.truncate(mb, tb.resid.real, 2, phi=S.sketch(n, 2, 45, 1), side="right")
+        r = O.refine(ta, tb, ta2, tb2)
+        assert np.abs((ab - r) - (ta2.resid @ tb2.resid).real).max() <= 1e-12 * scale, (ma, mb)
+        if np.abs(ta.resid.imag).max() > 0.1 and np.abs(tb.resid.imag).max() > 0.1:
+            complex_seen = True
+            wrong = (O.first_order(ta, tb) + O.first_order(ta2, tb2)).real   # without Im dA Im dB
+            assert np.abs((ab - wrong) - (ta2.resid @ tb2.resid).real).max() > 1e-3 * scale
+        fa = O.truncate(ma, ta.resid.real, n, phi=S.sketch(n, n, 46, 0), side="left")
+        fb = O.truncate(mb, tb.resid.real, n, phi=S.sketch(n, n, 46, 1), side="right")
+        assert np.abs(O.refine(ta, tb, fa, fb) - ab).max() <= 1e-11 * scale, (ma, mb)
+    assert complex_seen
+
+
+def test_refinement_of_nested_truncations_is_the_larger_truncation():
+    """For orthogonal components selected by magnitude (circulant, cycles, exact SVD) the top-k2 of
+    a real residue are the next k2 components of the operand, so refining a k truncation by k2 has
+    the error of the first-order product at k + k2: AB - refine = dA_{k+k2} dB_{k+k2}."""
+    n = 64
+    a, b = S.general_times_toeplitz(n, seed=3)
+    ab = a @ b
+    for method, k, k2 in (("circulant", 1, 4), ("cycle", 3, 5)):
+        ta, tb = O.truncate(method, a, k), O.truncate(method, b, k)
+        ta2, tb2 = O.truncate(method, ta.resid.real, k2), O.truncate(method, tb.resid.real, k2)
+        big_a, big_b = O.truncate(method, a, k + k2), O.truncate(method, b, k + k2)
+        err = ab - O.refine(ta, tb, ta2, tb2)
+        assert np.abs(err - (big_a.resid @ big_b.resid).real).max() <= 1e-11 * np.abs(ab).max(), method
+    ta, tb = O.truncate_svd_exact(a, 4), O.truncate_svd_exact(b, 4)
+    ta2, tb2 = O.truncate_svd_exact(ta.resid, 3), O.truncate_svd_exact(tb.resid, 3)
+    big_a, big_b = O.truncate_svd_exact(a, 7), O.truncate_svd_exact(b, 7)
+    err = ab - O.refine(ta, tb, ta2, tb2)
+    assert np.abs(err - big_a.resid @ big_b.resid).max() <= 1e-10 * np.abs(ab).max()
+
+
 def test_posterior_estimate_bounds_gaussian_error():
     """Independent Gaussian operands: the estimate is an upper bound of the observed error."""
     n = 256
