@@ -870,6 +870,49 @@ def test_refinement_of_nested_truncations_is_the_larger_truncation():
     assert np.abs(err - big_a.resid @ big_b.resid).max() <= 1e-10 * np.abs(ab).max()
 
 
+def test_product_wrappers_agree_with_the_pinned_forms():
+    """The per-method product helpers the GPU tests call are the pinned first-order form on the
+    truncations (transform-domain form for the Fourier sparsifier) and reproduce AB untruncated."""
+    n, k = 32, 5
+    g = S.rng(47, 0)
+    a, b = g.standard_normal((n, n)) + 0.5, g.standard_normal((n, n)) + 0.5
+    ab = a @ b
+    tol = 1e-12 * np.abs(ab).max()
+    pa, pb = S.sketch(n, k, 47, 0), S.sketch(n, k, 47, 1)
+    got = {"circulant": O.cd_matmul(a, b, k).real, "svd": O.svd_matmul(a, b, k, pa, pb).real,
+           "fourier": O.fourier_matmul(a, b, k), "cycle": O.cycle_matmul(a, b, k).real}
+    for method, m in got.items():
+        ta = O.truncate(method, a, k, phi=pa, side="left")
+        tb = O.truncate(method, b, k, phi=pb, side="right")
+        assert np.abs(m - O.product(method, ta, tb)).max() <= tol, method
+    full = {"circulant": O.cd_matmul(a, b, n).real, "svd": O.svd_matmul(a, b, n, S.sketch(n, n, 1, 0),
+                                                                          S.sketch(n, n, 1, 1)).real,
+            "fourier": O.fourier_matmul(a, b, n), "cycle": O.cycle_matmul(a, b, n).real,
+            "svd_exact": O.svd_matmul(a, b, n, None, None, exact=True).real}
+    for method, m in full.items():
+        assert np.abs(m - ab).max() <= 1e-11 * np.abs(ab).max(), method
+
+
+def test_near_tie_protocol_sets():
+    """The selection-parity protocol: keys within tau of the k-th key are ambiguous, the rest of the
+    top k certain; an exact tie has boundary gap 0; k >= n has no boundary."""
+    keys = np.array([5.0, 4.0, 3.0, 3.0, 2.0, 1.0])
+    must, maybe = O.near_tie_sets(keys, 3, 1e-6)
+    assert must == {0, 1} and maybe == {2, 3}
+    assert O.boundary_gap(keys, 3) == 0.0
+    assert O.boundary_gap(keys, 2) == pytest.approx(0.25)
+    near = np.array([5.0, 4.0, 3.0, 3.0 * (1 - 1e-7), 2.0])
+    must, maybe = O.near_tie_sets(near, 3, 1e-6)
+    assert must == {0, 1} and maybe == {2, 3}
+    must, maybe = O.near_tie_sets(near, 2, 1e-6)
+    assert must == {0} and maybe == {1}
+    assert O.near_tie_sets(keys, 6, 1e-6) == (set(range(6)), set())
+    assert O.boundary_gap(keys, 6) == float("inf")
+    # top_k: key descending, the lower index first among equal keys
+    assert O.top_k(keys, 4).tolist() == [0, 1, 2, 3]
+    assert O.top_k(np.array([1.0, 2.0, 2.0, 0.5]), 2).tolist() == [1, 2]
+
+
 def test_posterior_estimate_bounds_gaussian_error():
     """Independent Gaussian operands: the estimate is an upper bound of the observed error."""
     n = 256
