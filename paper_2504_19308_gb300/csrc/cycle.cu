@@ -74,6 +74,9 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __re
     float4 acc[CYC_RG];
 #pragma unroll
     for (int i = 0; i < CYC_RG; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // unrolled over components: the gathers of several components are issued before the FMAs
+    // that wait on them (the loads are L2 hits whose latency, not bandwidth, set the time)
+#pragma unroll 2
     for (int u = 0; u < k; ++u) {
       const int t = s_sel[u];
       const float* crow = cyc + (int64_t)u * n;
