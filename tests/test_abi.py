@@ -117,3 +117,26 @@ def test_argument_errors_without_gpu(lib):
     # NULL handles
     assert lib.amm_approx_matmul(None, None, fake, 64, None) == 1
     assert lib.amm_handle_destroy(None) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the compiled library every entry point raises."""
+    import paper_2504_19308_gb300.amm as amm
+    monkeypatch.setattr(amm, "_lib", None)
+    with pytest.raises(RuntimeError, match="libamm.so not found"):
+        amm.load_library(os.path.join(ROOT, "no_such_dir", "libamm.so"))
+
+
+def test_cpu_tensors_are_rejected(lib):
+    """The binding only marshals device pointers: host tensors are refused before any call."""
+    torch = pytest.importorskip("torch")
+    import paper_2504_19308_gb300 as amm
+    x = torch.zeros((64, 64))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        amm.decompose(x, "circulant", 4)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        amm.decompose_best_method(x, ["circulant", "svd"], 4)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        amm.decompose_to_tolerance(x, "svd", 0.1)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        amm.choose_k(x, "circulant", 0.1)
