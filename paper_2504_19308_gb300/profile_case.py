@@ -1,14 +1,16 @@
 """Run one decomposition + first-order product (+ backward) for a profiler.
 
     python -m paper_2504_19308_gb300.profile_case --method circulant --k 256 --n 4096 [--backward] [--repeat 2]
-    python -m paper_2504_19308_gb300.profile_case --step [--repeat 2]
+    python -m paper_2504_19308_gb300.profile_case --step [--repeat 2] [--trace]
 
 --step runs the sweep of the n = 4096 throughput step instead (circulant k = 16/64/256, rSVD
 k = 32/128, Fourier and cycle sparsifiers k = 41, each decomposed, multiplied and differentiated).
 
 Inputs are the seeded power-law pair of the bench (sigma_i = i^-1.5 + N(0, 1e-4)), drawn as
 Gaussian-plus-spectrum matrices without QR when --fast is given (same sizes, cheaper to make).
-Each repeat is wrapped in an NVTX range "case" so that a profiler can select it.
+Each repeat is wrapped in an NVTX range "case" so that a profiler can select it.  --trace times
+every library launch of the repeats after the first with CUDA events on its own stream (the
+library's launch trace) and prints one JSON object {kernel: [launches, total ms, ...]} per run.
 """
 import argparse
 import os
@@ -32,6 +34,7 @@ def main():
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--fast", action="store_true")
     ap.add_argument("--step", action="store_true")
+    ap.add_argument("--trace", action="store_true")
     a = ap.parse_args()
     n, k = a.n, a.k
     if a.fast:
@@ -52,7 +55,10 @@ def main():
         if method == "svd":
             sk[kk] = tuple(torch.tensor(synth.sketch(n, kk, 0, side), dtype=torch.float32, device=dev)
                            for side in (0, 1))
-    for _ in range(a.repeat):
+    for rep in range(a.repeat):
+        if a.trace and rep == 1:  # the first repeat warms up (autotuning, allocations)
+            torch.cuda.synchronize()
+            amm.trace_enable(True)
         torch.cuda.nvtx.range_push("case")
         for method, kk, bwd in cases:
             sa, sb = sk.get(kk, (None, None)) if method == "svd" else (None, None)
@@ -65,6 +71,13 @@ def main():
             hB.close()
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
+    if a.trace and a.repeat > 1:
+        import json
+        kernels, launches = amm.trace_collect()
+        amm.trace_enable(False)
+        per = a.repeat - 1
+        print(json.dumps({"repeats": per, "launches": launches,
+                          "ms_per_repeat": {name: round(v[1] / per, 4) for name, v in sorted(kernels.items())}}))
     print("ok", "step" if a.step else a.method, n, k, float(C.abs().sum()))
 
 
