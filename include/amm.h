@@ -192,7 +192,9 @@ amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const 
                                         int64_t lddc, float* dA, int64_t ldda, float* dB,
                                         int64_t lddb, void* stream);
 
-/* Sizes, norms and selection statistics.  Synchronises the handle's stream. */
+/* Sizes, norms and selection statistics: ||A||_F^2 and the truncation error ||dA||_F^2 of
+ * A = A~ + dA (Section 2, Eq. (2.1)), the gap at the top-k boundary (Alg. 3 Step 3).
+ * Synchronises the handle's stream. */
 amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info);
 
 /*
@@ -275,7 +277,8 @@ amm_status_t amm_decompose_best_method(const void* A, int64_t rows, int64_t cols
                                        void* stream, amm_handle_t* out, int32_t* method_out);
 
 /*
- * Re dA = A - Re A~ of a handle as a dense FP32 matrix (rows x cols, leading dimension ldd >=
+ * Re dA = A - Re A~ of a handle (the residue of A = A~ + dA, Section 2, Eq. (2.1)) as a dense FP32
+ * matrix (rows x cols, leading dimension ldd >=
  * cols, DEVICE, caller-owned, overwritten): the residue that amm_refine_product's second-level
  * decompositions take.  FP32 operands without circulant blocks; the Fourier sparsifier as the
  * left operand only (else AMM_ERR_NOT_IMPLEMENTED).  Asynchronous on `stream`, which must be
@@ -303,15 +306,15 @@ amm_status_t amm_refine_product(amm_handle_t hA, amm_handle_t hB, amm_handle_t h
 
 /*
  * Copy the selection to host memory: circulant component indices / cycle indices in
- * selection order (k entries); for AMM_SPARSE_FOURIER the kept frequencies of every row
- * (left operand, rows x k) or column (right operand, cols x k), ascending within each.
+ * selection order (k entries; Alg. 3 Step 3, Section 1.2.2); for AMM_SPARSE_FOURIER the kept frequencies of every row
+ * (left operand, rows x k) or column (right operand, cols x k), ascending within each (Alg. 4).
  * `cap` is the capacity of host_idx in elements; *count receives the number written.
  * Synchronises the handle's stream.
  */
 amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t cap,
                                       int64_t* count);
 
-/* Copy the rSVD test matrix phi (cols x k, row-major) to host memory.  Synchronises. */
+/* Copy the rSVD test matrix phi of Alg. 1 (cols x k, row-major) to host memory.  Synchronises. */
 amm_status_t amm_handle_get_sketch(amm_handle_t h, float* host_phi, int64_t cap);
 
 /* Release every device buffer the handle owns (stream-ordered) and the handle. */
@@ -381,7 +384,8 @@ amm_status_t amm_debug_gemm_tn(int32_t mode, int64_t M, int64_t N, int64_t K, fl
                                float* C, int64_t ldc, int32_t* dev_err, void* stream);
 
 /*
- * Autotuning of kernel variants (off by default).  With on != 0, the first call of a kernel that
+ * Autotuning of kernel variants (off by default; an implementation choice with no counterpart in
+ * the paper).  With on != 0, the first call of a kernel that
  * has several compiled variants (the circulant spectral apply: two or four packed signals per CTA)
  * for a given length, direction and element type times each variant on that call's own operands
  * (into scratch memory; the call's result is computed afterwards by the fastest) and keeps the
