@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define AMM_VERSION 5
+#define AMM_VERSION 6
 
 typedef enum {
   AMM_OK = 0,
@@ -394,6 +394,24 @@ amm_status_t amm_debug_gemm_tn(int32_t mode, int64_t M, int64_t N, int64_t K, fl
  * their stream is being captured into a CUDA graph use the current choice without timing.
  */
 amm_status_t amm_set_autotune(int32_t on);
+
+/*
+ * The autotuner's choices as text, for reuse by another process of the same build (a serving
+ * process can load the choices a tuning run made instead of timing again): a header line
+ * "amm-autotune 1", then one "key variant" line per tuned (length, direction, element type), keys
+ * ascending.  host_buf (capacity cap bytes) receives the NUL-terminated text and *len its length
+ * without the NUL, also when cap is too small (then AMM_ERR_INVALID_ARG and host_buf untouched).
+ * Host only: no device work.
+ */
+amm_status_t amm_autotune_export(char* host_buf, int64_t cap, int64_t* len);
+
+/*
+ * Install choices written by amm_autotune_export (they override entries for the same keys; a
+ * choice in the table is used whether or not autotuning is on).  Every line is checked first: a
+ * wrong header, a key whose length is not a circulant length of this build, a variant other than
+ * 0 / 1 or trailing text returns AMM_ERR_INVALID_ARG with nothing installed.  Host only.
+ */
+amm_status_t amm_autotune_import(const char* host_text);
 
 /*
  * Fault injection for tests: the n-th device allocation from now on (1-based) fails with

@@ -50,6 +50,8 @@ SIGNATURES = {
     "amm_last_error": (ctypes.c_char_p, []),
     "amm_version": (ctypes.c_int32, []),
     "amm_set_autotune": (ctypes.c_int, [ctypes.c_int32]),
+    "amm_autotune_export": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "amm_autotune_import": (ctypes.c_int, [ctypes.c_char_p]),
     "amm_decompose_to_tolerance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
                                                   ctypes.POINTER(Opts), ctypes.c_void_p,
@@ -255,6 +257,22 @@ def set_autotune(on: bool = True):
     """amm_set_autotune: time the compiled variants of tunable kernels on first use and keep the
     fastest (results do not depend on the choice)."""
     _check(load_library().amm_set_autotune(1 if on else 0), "amm_set_autotune")
+
+
+def autotune_export() -> str:
+    """amm_autotune_export: the autotuner's choices as text (for autotune_import in another process)."""
+    lib = load_library()
+    n = ctypes.c_int64(0)
+    buf = ctypes.create_string_buffer(1 << 12)
+    if lib.amm_autotune_export(buf, len(buf), ctypes.byref(n)) != 0:
+        buf = ctypes.create_string_buffer(n.value + 1)
+        _check(lib.amm_autotune_export(buf, len(buf), ctypes.byref(n)), "amm_autotune_export")
+    return buf.value.decode()
+
+
+def autotune_import(text: str):
+    """amm_autotune_import: install choices written by autotune_export (all or nothing)."""
+    _check(load_library().amm_autotune_import(text.encode()), "amm_autotune_import")
 
 
 def choose_k(A: torch.Tensor, method: str, tol: float) -> int:

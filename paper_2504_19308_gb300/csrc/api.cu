@@ -121,6 +121,24 @@ std::atomic<bool> g_autotune{false};
 }
 bool amm::amm_autotune_enabled() { return g_autotune.load(); }
 
+extern "C" amm_status_t amm_autotune_export(char* host_buf, int64_t cap, int64_t* len) {
+  if (!host_buf || !len) return fail(AMM_ERR_INVALID_ARG, "amm_autotune_export: NULL argument");
+  const std::string t = cd_tune_dump();
+  *len = (int64_t)t.size();
+  if (cap < (int64_t)t.size() + 1)
+    return fail(AMM_ERR_INVALID_ARG, "amm_autotune_export: cap=%lld < %lld", (long long)cap,
+                (long long)t.size() + 1);
+  memcpy(host_buf, t.c_str(), t.size() + 1);
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_autotune_import(const char* host_text) {
+  if (!host_text) return fail(AMM_ERR_INVALID_ARG, "amm_autotune_import: NULL argument");
+  if (!cd_tune_load(host_text, cd_length_ok))
+    return fail(AMM_ERR_INVALID_ARG, "amm_autotune_import: malformed table (nothing installed)");
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_set_autotune(int32_t on) {
   g_autotune.store(on != 0);
   return AMM_OK;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
 #include <vector>
 
 #include "../../include/amm.h"
@@ -78,6 +79,9 @@ using Handle = ::amm_handle;
 amm_status_t fail(amm_status_t s, const char* fmt, ...);
 // circulant transform lengths: 2^a in [16, 16384] or 3 * 2^a in [48, 6144]
 bool cd_length_ok(int64_t n);
+// circulant.cu: the spectral-apply autotuner's table as text, and its parser (false: malformed)
+std::string cd_tune_dump();
+bool cd_tune_load(const char* text, bool (*length_ok)(int64_t));
 // cycle-sparsifier lengths: multiples of 4 in [16, 8192]
 bool cyc_length_ok(int64_t n);
 // amm_set_autotune: kernel variants are timed on first use and the fastest kept

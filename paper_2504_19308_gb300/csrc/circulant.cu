@@ -20,8 +20,12 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
+#include <sstream>
+#include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "circulant_kernels.cuh"
 #include "common.cuh"
@@ -310,6 +314,39 @@ int cd_tune_get(int key) {
 void cd_tune_set(int key, int variant) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = variant;
+}
+
+// The table as text: a header line, then "key variant" per line in ascending key order.
+std::string cd_tune_dump() {
+  std::vector<std::pair<int, int>> v;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    v.assign(g_tune.begin(), g_tune.end());
+  }
+  std::sort(v.begin(), v.end());
+  std::string out = "amm-autotune 1\n";
+  for (const auto& kv : v) out += std::to_string(kv.first) + " " + std::to_string(kv.second) + "\n";
+  return out;
+}
+
+// Parse text written by cd_tune_dump; every entry is checked before any is installed.  A key
+// encodes (length, direction, reversed, element type) as N * 8 + flags; the variant is 0 or 1.
+bool cd_tune_load(const char* text, bool (*length_ok)(int64_t)) {
+  std::istringstream in(text);
+  std::string head, ver;
+  if (!(in >> head >> ver) || head != "amm-autotune" || ver != "1") return false;
+  std::vector<std::pair<int, int>> v;
+  long long key, var;
+  while (in >> key >> var) {
+    if (key < 0 || key > (1LL << 30) || !length_ok(key / 8) || (var != 0 && var != 1)) return false;
+    v.emplace_back((int)key, (int)var);
+  }
+  in.clear();
+  std::string rest;
+  if (in >> rest) return false;  // trailing text that is not a pair of integers
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : v) g_tune[kv.first] = kv.second;
+  return true;
 }
 
 int cd_cols_per_cta(int n) { return n >= 16384 ? 2 : n >= 6144 ? 4 : 8; }

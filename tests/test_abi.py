@@ -47,7 +47,7 @@ def test_library_resolves_every_symbol_at_load(lib):
 def test_status_strings(lib):
     assert lib.amm_status_string(0) == b"AMM_OK"
     assert lib.amm_status_string(5) == b"AMM_ERR_TIMEOUT"
-    assert lib.amm_version() == 5
+    assert lib.amm_version() == 6
 
 
 def test_argument_errors_without_gpu(lib):
@@ -140,3 +140,27 @@ def test_cpu_tensors_are_rejected(lib):
         amm.decompose_to_tolerance(x, "svd", 0.1)
     with pytest.raises(ValueError, match="CUDA tensor"):
         amm.choose_k(x, "circulant", 0.1)
+
+
+def test_autotune_table_round_trip(lib):
+    """The autotuner's table survives export / import (host only); malformed text installs nothing."""
+    import paper_2504_19308_gb300 as amm
+    key = lambda n, row, rev, bf16: n * 8 + 4 * row + 2 * rev + bf16
+    entries = {key(4096, 0, 0, 0): 1, key(4096, 1, 1, 0): 0, key(96, 0, 0, 1): 1, key(16384, 1, 1, 1): 0}
+    text = "amm-autotune 1\n" + "".join("%d %d\n" % kv for kv in sorted(entries.items()))
+    amm.autotune_import(text)
+    got = amm.autotune_export()
+    assert got.startswith("amm-autotune 1\n")
+    table = dict(tuple(map(int, ln.split())) for ln in got.splitlines()[1:])
+    assert all(table[k] == v for k, v in entries.items())
+    assert [int(ln.split()[0]) for ln in got.splitlines()[1:]] == sorted(table)
+    for bad in ("amm-autotune 2\n", "tune 1\n", "amm-autotune 1\n%d 2\n" % key(4096, 0, 0, 0),
+                "amm-autotune 1\n%d 1\n" % key(40, 0, 0, 0), "amm-autotune 1\n%d 1\nx\n" % key(512, 0, 0, 0),
+                "amm-autotune 1\n%d 0\n%d 1\n" % (key(1024, 0, 0, 0), key(80, 0, 0, 0))):
+        with pytest.raises(RuntimeError, match="malformed"):
+            amm.autotune_import(bad)
+    assert amm.autotune_export() == got                    # nothing from the rejected texts
+    small = ctypes.create_string_buffer(4)
+    n = ctypes.c_int64(0)
+    assert lib.amm_autotune_export(small, 4, ctypes.byref(n)) == 1 and n.value == len(got)
+    assert lib.amm_autotune_import(None) == 1
