@@ -49,6 +49,12 @@ extern "C" amm_status_t amm_batch_add(amm_batch_t b, const void* A, const void* 
   if (b->captured) return fail(AMM_ERR_STATE, "amm_batch_add: batch already captured into a graph");
   if (m <= 0 || n <= 0 || p <= 0 || k <= 0 || lda < n || ldb < p || ldc < p)
     return fail(AMM_ERR_INVALID_ARG, "amm_batch_add: bad sizes");
+  // checked here rather than when the batch runs, after earlier items have launched
+  if (dtype != AMM_F32 && dtype != AMM_BF16) return fail(AMM_ERR_INVALID_ARG, "amm_batch_add: bad dtype %d", dtype);
+  if (method != AMM_SVD && method != AMM_CIRCULANT && method != AMM_SPARSE_FOURIER && method != AMM_SPARSE_CYCLE)
+    return fail(AMM_ERR_INVALID_ARG, "amm_batch_add: bad method %d", (int)method);
+  if ((opts_a && opts_a->struct_size != sizeof(amm_opts_t)) || (opts_b && opts_b->struct_size != sizeof(amm_opts_t)))
+    return fail(AMM_ERR_INVALID_ARG, "amm_batch_add: opts struct_size differs from sizeof(amm_opts_t)");
   amm_batch::Item it;
   it.A = A;
   it.B = B;

@@ -164,3 +164,31 @@ def test_autotune_table_round_trip(lib):
     n = ctypes.c_int64(0)
     assert lib.amm_autotune_export(small, 4, ctypes.byref(n)) == 1 and n.value == len(got)
     assert lib.amm_autotune_import(None) == 1
+
+
+def test_batch_host_logic(lib):
+    """Batches record items on the host: arguments are checked when an item is added (before any
+    item of the batch launches); a batch that never ran is destroyed without device work."""
+    import paper_2504_19308_gb300.amm as amm
+    batch = ctypes.c_void_p(0)
+    assert lib.amm_batch_create(None) == 1
+    assert lib.amm_batch_create(ctypes.byref(batch)) == 0 and batch.value
+    fake = ctypes.c_void_p(0x1000)            # recorded, never dereferenced: the batch is not run
+    add = lambda *a: lib.amm_batch_add(batch, *a)
+    assert add(None, fake, fake, 64, 64, 64, 64, 64, 64, 0, 1, 4, None, None) == 1
+    assert add(fake, fake, fake, 64, 64, 64, 32, 64, 64, 0, 1, 4, None, None) == 1   # lda < n
+    assert add(fake, fake, fake, 64, 64, 64, 64, 64, 64, 5, 1, 4, None, None) == 1   # dtype
+    assert add(fake, fake, fake, 64, 64, 64, 64, 64, 64, 0, 9, 4, None, None) == 1   # method
+    bad = amm.Opts()
+    assert lib.amm_opts_init(ctypes.byref(bad)) == 0
+    bad.struct_size = 8
+    assert add(fake, fake, fake, 64, 64, 64, 64, 64, 64, 0, 1, 4, ctypes.byref(bad), None) == 1
+    forced = (ctypes.c_int32 * 4)(0, 1, 2, 3)
+    fo = amm.Opts()
+    assert lib.amm_opts_init(ctypes.byref(fo)) == 0
+    fo.forced_selection = ctypes.cast(forced, ctypes.POINTER(ctypes.c_int32))
+    assert add(fake, fake, fake, 64, 64, 64, 64, 64, 64, 0, 1, 4, None, ctypes.byref(fo)) == 1
+    assert add(fake, fake, fake, 64, 64, 64, 64, 64, 64, 0, 1, 4, None, None) == 0
+    assert add(fake, fake, fake, 96, 96, 96, 96, 96, 96, 1, 0, 8, None, None) == 0
+    assert lib.amm_batch_destroy(batch) == 0
+    assert lib.amm_batch_destroy(None) == 1
