@@ -192,3 +192,23 @@ def test_batch_host_logic(lib):
     assert add(fake, fake, fake, 96, 96, 96, 96, 96, 96, 1, 0, 8, None, None) == 0
     assert lib.amm_batch_destroy(batch) == 0
     assert lib.amm_batch_destroy(None) == 1
+
+
+def test_last_error_is_per_thread(lib):
+    """amm_last_error is thread-local: a failure on one thread leaves another thread's reason."""
+    import threading
+    assert lib.amm_decompose(None, 64, 64, 64, 0, 1, 4, None, None, ctypes.byref(ctypes.c_void_p(0))) == 1
+    mine = lib.amm_last_error()
+    assert b"A is NULL" in mine
+    seen = {}
+
+    def other():
+        seen["before"] = lib.amm_last_error()
+        lib.amm_batch_destroy(None)
+        seen["after"] = lib.amm_last_error()
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["before"] == b"" and b"amm_batch_destroy" in seen["after"]
+    assert lib.amm_last_error() == mine
