@@ -1,6 +1,5 @@
 """Batched products of uneven sizes: eager run, graph capture and graph replay all reproduce the
 individually computed products bit for bit."""
-import numpy as np
 import pytest
 
 import synth as S

@@ -1,5 +1,4 @@
 """GPU parity of the circulant backward (frozen selections) against the oracle's gradients."""
-import numpy as np
 import pytest
 
 import oracle as O
