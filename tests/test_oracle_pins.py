@@ -913,6 +913,40 @@ def test_near_tie_protocol_sets():
     assert O.top_k(np.array([1.0, 2.0, 2.0, 0.5]), 2).tolist() == [1, 2]
 
 
+def test_cor39_flat_residue_svd_bound():
+    """Cor. 3.9: when the singular values of dA and dB are all equal (a flat tail after the top k of
+    the exact SVD), ||dA dB||_F <= ||dA||_F ||dB||_F / sqrt(n - k)."""
+    n, k = 48, 6
+    for t in range(5):
+        g = S.rng(60, t)
+        a = S.spectrum_matrix(np.concatenate([np.linspace(50, 10, k), np.ones(n - k)]), g)
+        b = S.spectrum_matrix(np.concatenate([np.linspace(30, 5, k), np.full(n - k, 0.5)]), g)
+        ta, tb = O.truncate_svd_exact(a, k), O.truncate_svd_exact(b, k)
+        assert np.allclose(np.linalg.svd(ta.resid, compute_uv=False)[: n - k], 1.0)
+        lhs = np.linalg.norm(ta.resid @ tb.resid)
+        assert lhs <= np.linalg.norm(ta.resid) * np.linalg.norm(tb.resid) / math.sqrt(n - k) * (1 + 1e-12)
+
+
+def test_cor314_circulant_residue_layout_bounds():
+    """Cor. 3.14: ||dA dB||_F^2 <= ||dA_cyc||_2 ||dB_cyc||_2 ||dA||_F ||dB||_F and the 1 / infinity-norm
+    form of it, with dA_cyc the cycle layout of the circulant residue, on every computed instance."""
+    g = S.rng(50, 0)
+    for trial in range(18):
+        n = (16, 32, 64)[trial % 3]
+        k = 1 + trial % (n // 4)
+        if trial % 2:
+            a, b = S.general_times_toeplitz(n, seed=trial)
+        else:
+            a, b = g.standard_normal((n, n)), g.uniform(0, 1, (n, n))
+        da, db = O.truncate_circulant(a, k).resid, O.truncate_circulant(b, k).resid
+        la, lb = O.cycle_layout(da), O.cycle_layout(db)
+        fa, fb = np.linalg.norm(da), np.linalg.norm(db)
+        lhs = np.linalg.norm(da @ db)
+        assert lhs ** 2 <= np.linalg.norm(la, 2) * np.linalg.norm(lb, 2) * fa * fb * (1 + 1e-12)
+        norms = [np.linalg.norm(x, o) for x in (la, lb) for o in (np.inf, 1)]
+        assert lhs <= float(np.prod(norms)) ** 0.25 * math.sqrt(fa * fb) * (1 + 1e-12)
+
+
 def test_posterior_estimate_bounds_gaussian_error():
     """Independent Gaussian operands: the estimate is an upper bound of the observed error."""
     n = 256
