@@ -333,17 +333,27 @@ std::string cd_tune_dump() {
 // encodes (length, direction, reversed, element type) as N * 8 + flags; the variant is 0 or 1.
 bool cd_tune_load(const char* text, bool (*length_ok)(int64_t)) {
   std::istringstream in(text);
-  std::string head, ver;
-  if (!(in >> head >> ver) || head != "amm-autotune" || ver != "1") return false;
+  std::vector<std::string> tok;
+  for (std::string t; in >> t;) tok.push_back(t);
+  if (tok.size() < 2 || tok[0] != "amm-autotune" || tok[1] != "1" || tok.size() % 2 != 0) return false;
+  // a whole token of decimal digits, at most 10 of them
+  auto integer = [](const std::string& t, long long* out) {
+    if (t.empty() || t.size() > 10) return false;
+    long long x = 0;
+    for (char c : t) {
+      if (c < '0' || c > '9') return false;
+      x = x * 10 + (c - '0');
+    }
+    *out = x;
+    return true;
+  };
   std::vector<std::pair<int, int>> v;
-  long long key, var;
-  while (in >> key >> var) {
-    if (key < 0 || key > (1LL << 30) || !length_ok(key / 8) || (var != 0 && var != 1)) return false;
+  for (size_t i = 2; i < tok.size(); i += 2) {
+    long long key, var;
+    if (!integer(tok[i], &key) || !integer(tok[i + 1], &var)) return false;
+    if (key > (1LL << 30) || !length_ok(key / 8) || (var != 0 && var != 1)) return false;
     v.emplace_back((int)key, (int)var);
   }
-  in.clear();
-  std::string rest;
-  if (in >> rest) return false;  // trailing text that is not a pair of integers
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (const auto& kv : v) g_tune[kv.first] = kv.second;
   return true;

@@ -156,7 +156,9 @@ def test_autotune_table_round_trip(lib):
     assert [int(ln.split()[0]) for ln in got.splitlines()[1:]] == sorted(table)
     for bad in ("amm-autotune 2\n", "tune 1\n", "amm-autotune 1\n%d 2\n" % key(4096, 0, 0, 0),
                 "amm-autotune 1\n%d 1\n" % key(40, 0, 0, 0), "amm-autotune 1\n%d 1\nx\n" % key(512, 0, 0, 0),
-                "amm-autotune 1\n%d 0\n%d 1\n" % (key(1024, 0, 0, 0), key(80, 0, 0, 0))):
+                "amm-autotune 1\n%d 0\n%d 1\n" % (key(1024, 0, 0, 0), key(80, 0, 0, 0)),
+                "amm-autotune 1\n%d\n" % key(2048, 0, 0, 0), "amm-autotune 1\n%d 1.5\n" % key(2048, 0, 0, 0),
+                "amm-autotune 1\n-8 1\n", ""):
         with pytest.raises(RuntimeError, match="malformed"):
             amm.autotune_import(bad)
     assert amm.autotune_export() == got                    # nothing from the rejected texts
