@@ -354,6 +354,39 @@ def test_fourier_topk_rows_optimal():
         assert np.linalg.norm(tr.resid[i]) == pytest.approx(np.linalg.norm(row[~tr.mask[i]]), rel=1e-12)
 
 
+def _fourier_columns_optimal(b, tr, k):
+    """True when every column of the right Fourier truncation keeps exactly k entries of W B and
+    those entries minimise the column's residual among all k-subsets (brute force), measured in
+    the space domain through W^* (||(B - B_s) e_j|| = ||(W B - B~_a) e_j||, W unitary)."""
+    n = b.shape[0]
+    w = O.unitary_W(n)
+    bt = w @ b
+    for j in range(b.shape[1]):
+        kept = np.nonzero(tr.mask[:, j])[0]
+        if len(kept) != k:
+            return False
+        best = math.inf
+        for sub in itertools.combinations(range(n), k):
+            z = np.zeros(n, dtype=np.complex128)
+            z[list(sub)] = bt[list(sub), j]
+            best = min(best, float(np.linalg.norm(b[:, j] - np.conj(w).T @ z)))
+        if np.linalg.norm(tr.resid[:, j]) > best * (1 + 1e-10) + 1e-14:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("n,p,k", [(7, 5, 2), (8, 6, 3), (6, 9, 1)])
+def test_fourier_topk_columns_optimal(n, p, k):
+    """Section 2.4 / Alg. 5 (reading R8): the right operand keeps the top k entries of every COLUMN
+    of W B; per column these minimise the column residual (brute force over all k-subsets)."""
+    b = _rand(n, 27, m=p).T.copy()       # n x p, p != n so a row / column mix-up changes shapes
+    tr = O.truncate_fourier_right(b, k)
+    assert _fourier_columns_optimal(b, tr, k)
+    # ||dB||_F^2 is the sum of the dropped column energies of W B (Parseval per column)
+    dropped = sum(float(np.sum(np.abs(tr.T[~tr.mask[:, j], j]) ** 2)) for j in range(p))
+    assert np.linalg.norm(tr.resid) ** 2 == pytest.approx(dropped, rel=1e-12)
+
+
 def test_fourier_conjugate_ties_mirrored():
     """Reading R8: |A~(i,q)| and |A~(i,n-q)| tie exactly; the lower index wins the tie."""
     n = 8
@@ -679,6 +712,63 @@ def test_planted_mistakes_are_caught(monkeypatch):
         e[i, j] = 1.0
         bda6[i, j] = f(e) - f(np.zeros_like(a6))
     assert np.abs(da6 - bda6).max() > 1e-6
+
+    # 7) right Fourier truncation selecting per ROW of W B (per frequency, across columns) instead
+    #    of per column: the brute-force column pin fails (Section 2.4, reading R8)
+    b7 = _rand(8, 36, m=6).T.copy()
+    good_right = OA.truncate_fourier_right
+
+    def per_row(bb, kk, forced=None):
+        bt = O.unitary_W(bb.shape[0]) @ bb
+        mask = O.topk_mask_rows(np.abs(bt), kk)
+        bt_a = np.where(mask, bt, 0)
+        return O.Truncation("fourier", bb, np.conj(O.unitary_W(bb.shape[0])).T @ bt_a, None, T=bt, mask=mask,
+                            T_a=bt_a)
+
+    monkeypatch.setattr(OA, "truncate_fourier_right", per_row)
+    assert not _fourier_columns_optimal(b7, OA.truncate_fourier_right(b7, 2), 2)
+    monkeypatch.setattr(OA, "truncate_fourier_right", good_right)
+    assert _fourier_columns_optimal(b7, OA.truncate_fourier_right(b7, 2), 2)
+
+    # 8) spectral concentration mu (Def. 3.11) without the 1/n of the mean: the closed form
+    #    mu(J) = n of the all-ones residue fails
+    good_mu = OA.mu_circulant
+    monkeypatch.setattr(OA, "mu_circulant", lambda R, sel, r2: good_mu(R, sel, r2) * R.shape[0])
+    jn = np.ones((8, 8))
+    assert OA.mu_circulant(O.circulant_spectrum(jn), [], 64.0) != pytest.approx(8.0)
+    monkeypatch.setattr(OA, "mu_circulant", good_mu)
+    assert OA.mu_circulant(O.circulant_spectrum(jn), [], 64.0) == pytest.approx(8.0)
+
+
+# --------------------------------------------------------------------------- spectral concentration
+
+@pytest.mark.parametrize("n", [8, 16, 33])
+def test_mu_closed_forms(n):
+    """Def. 3.11: mu = max_i X_i / mean_i X_i (the mean of X_i is ||dA||_F^2 / n by Parseval), so
+    1 <= mu <= n.  Closed forms: a residue that is one cycle of ones (A = C^m, unit-modulus
+    eigenvalues) has mu = 1; the all-ones residue J (eigenvalues n, 0, ..., 0) has mu = n; a
+    residue alpha J + beta I has X_0 = (alpha n + beta)^2, X_i = beta^2 otherwise."""
+    cm = np.linalg.matrix_power(O.cycle_perm(n), 3 % n)
+    assert O.mu_circulant(O.circulant_spectrum(cm), [], float(n)) == pytest.approx(1.0, rel=1e-12)
+    jn = np.ones((n, n))
+    assert O.mu_circulant(O.circulant_spectrum(jn), [], float(n * n)) == pytest.approx(float(n), rel=1e-12)
+    al, be = 0.7, 1.3
+    x = al * jn + be * np.eye(n)
+    x0, xi = (al * n + be) ** 2, be ** 2
+    want = x0 / ((x0 + (n - 1) * xi) / n)
+    assert O.mu_circulant(O.circulant_spectrum(x), [], float(np.linalg.norm(x) ** 2)) == pytest.approx(want, rel=1e-12)
+    # a selection removes its components from X: Y = J + 2 C^3 D has component 0 = J and
+    # component 1 = 2 C^3 (Thm 2.1); keeping 0 leaves 2 C^3 D (mu = 1), keeping 1 leaves J (mu = n)
+    y = jn + 2.0 * (cm @ O.diag_D(n, 1))
+    ry = O.circulant_spectrum(y)
+    assert O.mu_circulant(ry, [0], 4.0 * n) == pytest.approx(1.0, rel=1e-12)
+    assert O.mu_circulant(ry, [1], float(n * n)) == pytest.approx(float(n), rel=1e-12)
+    g = S.rng(61, n)
+    for k in (1, 3):
+        a = g.standard_normal((n, n)) + 1.0
+        t = O.truncate_circulant(a, k)
+        mu = O.mu_circulant(t.R, t.sel, float(np.linalg.norm(t.resid) ** 2))
+        assert 1.0 - 1e-12 <= mu <= n * (1 + 1e-12)
 
 
 # --------------------------------------------------------------------------- error estimation
