@@ -314,6 +314,16 @@ amm_status_t amm_refine_product(amm_handle_t hA, amm_handle_t hB, amm_handle_t h
 amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t cap,
                                       int64_t* count);
 
+/*
+ * Copy the component keys to host memory: for AMM_CIRCULANT T[t] = ||R_A[t]||_2, t = 0..n-1 (Alg. 3
+ * Step 2; T[n-t] is the same double as T[t], computed once for t <= n/2), for AMM_SPARSE_CYCLE the
+ * cycle norms ||diag Lambda_j||_2 (Section 1.2.2), the values the top-k selection ranks.  `cap` is
+ * the capacity of host_keys in doubles (>= n); *count receives n.  Square handles only (blocked
+ * circulant handles: AMM_ERR_NOT_IMPLEMENTED; other methods: AMM_ERR_STATE).  Synchronises the
+ * handle's stream.
+ */
+amm_status_t amm_handle_get_keys(amm_handle_t h, double* host_keys, int64_t cap, int64_t* count);
+
 /* Copy the rSVD test matrix phi of Alg. 1 (cols x k, row-major) to host memory.  Synchronises. */
 amm_status_t amm_handle_get_sketch(amm_handle_t h, float* host_phi, int64_t cap);
 
@@ -324,8 +334,9 @@ amm_status_t amm_handle_destroy(amm_handle_t h);
  * Cycle spectrum and component keys of one square FP32 matrix WITHOUT allocating device memory.
  * The paper has no counterpart: this is an interface for callers that cannot call cudaMalloc,
  * e.g. code running while a framework captures a CUDA graph and forbids allocation there, or a
- * process whose device memory is owned entirely by another allocator.  It computes what
- * amm_decompose(..., AMM_CIRCULANT, ...) computes first (Alg. 2 and Alg. 3 Step 2):
+ * process whose device memory is owned entirely by another allocator.  It computes the spectrum
+ * and the keys that amm_decompose(..., AMM_CIRCULANT, ...) computes first, with the same kernels
+ * and the same summation order, so the keys are the doubles amm_handle_get_keys returns:
  *   R     DEVICE output, (n/2+1) x n complex64 (interleaved float pairs), row k = R_A[k],
  *         16-byte aligned; caller-owned
  *   keys  DEVICE output, n doubles, keys[t] = ||R_A[t]||_2 (t and n-t bit-identical)

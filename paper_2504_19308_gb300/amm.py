@@ -82,6 +82,8 @@ SIGNATURES = {
     "amm_handle_get_selection": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
                                                 ctypes.POINTER(ctypes.c_int64)]),
     "amm_handle_get_sketch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    "amm_handle_get_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "amm_handle_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "amm_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int32]),
     "amm_circulant_spectrum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -179,6 +181,14 @@ class Handle:
                "amm_handle_get_selection")
         out = np.frombuffer(buf, dtype=np.int32, count=cnt.value).copy()
         return out.reshape(rows, self.k) if self.method == "fourier" or self.block else out
+
+    def keys(self) -> np.ndarray:
+        """Component keys (circulant T[t] = ||R_A[t]||_2, or the cycle norms), length n."""
+        n = self.shape[0]
+        buf = (ctypes.c_double * n)()
+        cnt = ctypes.c_int64(0)
+        _check(load_library().amm_handle_get_keys(self.ptr, buf, n, ctypes.byref(cnt)), "amm_handle_get_keys")
+        return np.frombuffer(buf, dtype=np.float64, count=cnt.value).copy()
 
     def sketch(self) -> np.ndarray:
         n = self.source.shape[1]

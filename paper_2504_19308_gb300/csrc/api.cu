@@ -943,6 +943,21 @@ extern "C" amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_i
   return AMM_OK;
 }
 
+extern "C" amm_status_t amm_handle_get_keys(amm_handle_t h, double* host_keys, int64_t cap, int64_t* count) {
+  if (!h || !host_keys || !count) return fail(AMM_ERR_INVALID_ARG, "amm_handle_get_keys: NULL argument");
+  if (h->method != AMM_CIRCULANT && h->method != AMM_SPARSE_CYCLE)
+    return fail(AMM_ERR_STATE, "amm_handle_get_keys: handle has no component keys");
+  if (h->blk.b) return fail(AMM_ERR_NOT_IMPLEMENTED, "amm_handle_get_keys: blocked circulant handle");
+  const int64_t n = h->rows;
+  if (cap < n) return fail(AMM_ERR_INVALID_ARG, "amm_handle_get_keys: cap=%lld < n=%lld", (long long)cap, (long long)n);
+  const double* keys = h->method == AMM_CIRCULANT ? h->cd.so.keys : h->cy.so.keys;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(host_keys, keys, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "amm_handle_get_keys");
+  *count = n;
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_handle_get_sketch(amm_handle_t h, float* host_phi, int64_t cap) {
   if (!h || !host_phi) return fail(AMM_ERR_INVALID_ARG, "amm_handle_get_sketch: NULL argument");
   if (h->method != AMM_SVD) return fail(AMM_ERR_STATE, "handle has no sketch");

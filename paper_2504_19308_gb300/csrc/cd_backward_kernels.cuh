@@ -285,7 +285,8 @@ template <int N> struct BwCfg {
 template <int N> struct BwOps {
   using C = BwCfg<N>;
   static cudaError_t attrs() {
-    static cudaError_t e = [] {
+    static DeviceOnce once;
+    return once([] {
       cudaError_t r = cudaFuncSetAttribute((const void*)bw_spectrum_kernel<N, C::S, C::NT, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
       if (r == cudaSuccess)
@@ -295,8 +296,7 @@ template <int N> struct BwOps {
         r = cudaFuncSetAttribute((const void*)cd_rho_kernel<N, C::NT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(float2) * fft_padded_len(N)));
       return r;
-    }();
-    return e;
+    });
   }
   static cudaError_t spectrum(bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh,
                               const int32_t* g0, const int32_t* g1, cudaStream_t st) {
@@ -310,8 +310,11 @@ template <int N> struct BwOps {
   static cudaError_t sddmm(const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
                            float2* K, const int32_t* g0, const int32_t* g1, cudaStream_t st) {
     if (N >= 2 * SDT_W && (int64_t)cap * 12 >= N) {  // dense enough that a staged Yh row serves several t
-      static cudaError_t attr = cudaFuncSetAttribute((const void*)cd_sddmm_tiled_kernel<N>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SDT_SMEM);
+      static DeviceOnce once;
+      const cudaError_t attr = once([] {
+        return cudaFuncSetAttribute((const void*)cd_sddmm_tiled_kernel<N>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SDT_SMEM);
+      });
       if (attr != cudaSuccess) return attr;
       dim3 grid((N / 2 + SDT_W) / SDT_W, N / SDT_P);
       cd_sddmm_tiled_kernel<N><<<grid, SDT_NT, SDT_SMEM, st>>>(Xh, Yh, list, count, K, g0, g1);

@@ -387,13 +387,12 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
   auto bytes = [](int nn) {
     return (size_t)nn * (sizeof(double) + 1) + 8 + (size_t)SEL_SORT_MAX * (sizeof(double) + sizeof(int32_t));
   };
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)cd_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes(16384));
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  static DeviceOnce once;
+  const cudaError_t attr = once([&] {
+    return cudaFuncSetAttribute((const void*)cd_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes(16384));
+  });
+  if (attr != cudaSuccess) return attr;
   const int kh = mirror ? n / 2 + 1 : n;
   {
     AMM_TRACE("cd_keyreduce", st);

@@ -339,7 +339,7 @@ template <int N> struct CdCfg {
   static constexpr int NT1 = (N >= 1024) ? 256 : (N >= 64 ? 64 : N);  // eigen-spectrum kernel
 };
 
-template <int N> static cudaError_t set_smem_attrs() {
+template <int N> static cudaError_t set_smem_attrs_now() {
   using C = CdCfg<N>;
   cudaError_t e = cudaSuccess;
   auto s = [&](const void* f, size_t b) {
@@ -364,11 +364,17 @@ template <int N> static cudaError_t set_smem_attrs() {
   return e;
 }
 
+// the attributes above, set once per device
+template <int N> static cudaError_t set_smem_attrs() {
+  static DeviceOnce once;
+  return once([] { return set_smem_attrs_now<N>(); });
+}
+
 template <int N> struct CdOps {
   using C = CdCfg<N>;
   static cudaError_t spectrum(const void* A, int64_t lda, bool bf16, const float2* tw, float2* R, float* kpart,
                               cudaStream_t st) {
-    static cudaError_t attr = set_smem_attrs<N>();
+    const cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
     dim3 grid(N / (2 * C::S));
     if (bf16)
@@ -380,7 +386,7 @@ template <int N> struct CdOps {
   }
   static cudaError_t eigen(const float2* R, const float2* tw, const int32_t* list, const float* coef,
                            const int32_t* count, int cap, int imag_coef, float2* L, cudaStream_t st) {
-    static cudaError_t attr = set_smem_attrs<N>();
+    const cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
     constexpr int NT1 = C::NT1;
     size_t sm = sizeof(float2) * fft_padded_len(N);
@@ -390,7 +396,7 @@ template <int N> struct CdOps {
   }
   static cudaError_t residual(const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
                               const int32_t* dcount2, float* X, int64_t ldx, int accumulate, cudaStream_t st) {
-    static cudaError_t attr = set_smem_attrs<N>();
+    const cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
     cd_residual_kernel<N, C::S, C::NT><<<N / (2 * C::S), C::NT, C::SMEM_RES, st>>>(R, tw, g, mode, dcount, dcount2,
                                                                                   X, ldx, accumulate);
@@ -469,7 +475,7 @@ template <int N> struct CdOps {
   static cudaError_t apply(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
                            const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
                            const int32_t* gate1, float* out, int64_t ldo, int accumulate, int rev, cudaStream_t st) {
-    static cudaError_t attr = set_smem_attrs<N>();
+    const cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
     const int v = gate0 ? 0 : variant(row, X, ldx, bf16, nvec, tw, list, Lc, count, rev, st);
     if (v) return apply_v<1>(row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate, rev, st);

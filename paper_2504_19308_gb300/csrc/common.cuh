@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #define AMM_DEV __device__ __forceinline__
 
 // ---------------------------------------------------------------- complex float2 arithmetic
@@ -50,6 +52,27 @@ template <bool P2> AMM_DEV int cwrap(int x, int n) {
     return x >= n ? x - n : x;
   }
 }
+
+// Host: runs a setup call (kernel attributes) once per device and returns its cached result on
+// later calls with the same device current.  Kernel attributes belong to a device's context, so a
+// process-wide "done" flag would skip them on a second device.  Thread-safe.
+struct DeviceOnce {
+  std::mutex mu;
+  bool done[64] = {};
+  cudaError_t res[64] = {};
+  template <class F> cudaError_t operator()(F&& setup) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+      res[dev] = setup();
+      done[dev] = true;
+    }
+    return res[dev];
+  }
+};
 
 // Radix selection step over a 256-bin histogram: the bin b where the count from the top (bin 255
 // down) first reaches need (need >= 1), and the count strictly above it in *above.  Called by one

@@ -222,7 +222,8 @@ static bool pow2n(int n) { return (n & (n - 1)) == 0; }
 
 // dynamic shared memory of the apply kernels (both index forms), set once
 static cudaError_t cyc_attrs() {
-  static cudaError_t e = [] {
+  static DeviceOnce once;
+  return once([] {
     const int col = 8192 * (int)sizeof(float4) + 8192 * (int)sizeof(int), row = CYC_RW * 8192 * (int)sizeof(float);
     const void* fs[8] = {(const void*)cyc_apply_col_kernel<true>, (const void*)cyc_apply_col_kernel<false>,
                          (const void*)cyc_bw_col_kernel<true>, (const void*)cyc_bw_col_kernel<false>,
@@ -232,8 +233,7 @@ static cudaError_t cyc_attrs() {
     for (int i = 0; i < 8 && r == cudaSuccess; ++i)
       r = cudaFuncSetAttribute(fs[i], cudaFuncAttributeMaxDynamicSharedMemorySize, i < 4 ? col : row);
     return r;
-  }();
-  return e;
+  });
 }
 
 // launch KERNEL<P2> with P2 = (n is a power of two)

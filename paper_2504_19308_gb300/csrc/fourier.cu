@@ -275,14 +275,15 @@ template <int N> struct FtOps {
   using C = FtCfg<N>;
   static cudaError_t transform(bool row, const float* X, int64_t ldx, int nvec, const float2* tw, float2* T,
                                float2* TT, float* mag, cudaStream_t st) {
-    static cudaError_t attr = [] {
+    static DeviceOnce once;
+    const cudaError_t attr = once([] {
       cudaError_t e = cudaFuncSetAttribute((const void*)ft_transform_kernel<N, C::S, C::NT, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute((const void*)ft_transform_kernel<N, C::S, C::NT, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
       return e;
-    }();
+    });
     if (attr != cudaSuccess) return attr;
     dim3 grid((nvec + 2 * C::S - 1) / (2 * C::S));
     if (row)
@@ -469,8 +470,11 @@ template <int N> struct FtMixOps {
   using C = FtCfg<N>;
   static cudaError_t dense(const float2* At, const int32_t* sel, int k, int m, const float2* tw, int part,
                            const float* A, int64_t lda, float* D, int64_t ldd, cudaStream_t st) {
-    static cudaError_t attr = cudaFuncSetAttribute((const void*)ft_dense_kernel<N, C::S, C::NT>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    static DeviceOnce once;
+    const cudaError_t attr = once([] {
+      return cudaFuncSetAttribute((const void*)ft_dense_kernel<N, C::S, C::NT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
     if (attr != cudaSuccess) return attr;
     ft_dense_kernel<N, C::S, C::NT><<<(m + 2 * C::S - 1) / (2 * C::S), C::NT, C::SMEM, st>>>(At, sel, k, m, tw, part,
                                                                                              A, lda, D, ldd);

@@ -227,8 +227,11 @@ template <int N> struct FtBwOps {
   using C = FtBwCfg<N>;
   template <bool INV, bool OUT_ROW>
   static cudaError_t real(const float2* X, int nvec, const float2* tw, float* out, int64_t ldo, cudaStream_t st) {
-    static cudaError_t attr = cudaFuncSetAttribute((const void*)ft_bw_real_kernel<N, C::S, C::NT, INV, OUT_ROW>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    static DeviceOnce once;
+    const cudaError_t attr = once([] {
+      return cudaFuncSetAttribute((const void*)ft_bw_real_kernel<N, C::S, C::NT, INV, OUT_ROW>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    });
     if (attr != cudaSuccess) return attr;
     dim3 grid((nvec + 2 * C::S - 1) / (2 * C::S));
     ft_bw_real_kernel<N, C::S, C::NT, INV, OUT_ROW><<<grid, C::NT, C::SMEM, st>>>(X, nvec, tw, out, ldo);

@@ -13,6 +13,10 @@
 // (different streams, or different host threads) race on it; order them on one stream.  Every
 // byte a call reads from the array is written earlier by the same call, so nothing has to be
 // cleared between calls.
+//
+// The keys are reduced by the same kernel, in the same order, as in amm_decompose (cd_keys), and
+// the square root is taken in FP64 as the selection kernel takes it, so both paths return the same
+// doubles and a selection made from these keys equals amm_decompose's, exact ties included.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -27,7 +31,10 @@ constexpr int kMaxN = AMM_NOALLOC_MAX_N;
 constexpr size_t kTwBytes = sizeof(float2) * kMaxN;
 // key partials: (n / J) rows of (n/2 + 1) floats, J = 8 columns per spectrum CTA for n <= 4096
 constexpr size_t kPartBytes = sizeof(float) * (size_t)(kMaxN / 8) * (kMaxN / 2 + 1);
-static_assert(kTwBytes + kPartBytes <= AMM_NOALLOC_SCRATCH_BYTES, "scratch too small");
+// reduced squared keys, t = 0..n/2 (FP64), 256-byte aligned after the partials
+constexpr size_t kKey2Off = (kTwBytes + kPartBytes + 255) / 256 * 256;
+constexpr size_t kKey2Bytes = sizeof(double) * (kMaxN / 2 + 1);
+static_assert(kKey2Off + kKey2Bytes <= AMM_NOALLOC_SCRATCH_BYTES, "scratch too small");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[AMM_NOALLOC_SCRATCH_BYTES];
 
@@ -36,14 +43,12 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[AMM_NOALLOC_SCRATCH_BY
 std::mutex g_mu;
 void* g_addr[64] = {nullptr};
 
-// keys[t] = sqrt(sum over partial rows of kpart[c][t]) for t <= n/2, mirrored to n - t;
-// same summation order as the selection kernel of amm_decompose.
-__global__ void noalloc_keys_kernel(const float* __restrict__ kpart, int nparts, int n, double* __restrict__ keys) {
+// keys[t] = sqrt(key2[t]) for t <= n/2 (key2 reduced by cd_keys), mirrored to n - t: the values
+// the circulant selection kernel writes to a handle's keys.
+__global__ void noalloc_sqrt_mirror_kernel(const double* __restrict__ key2, int n, double* __restrict__ keys) {
   const int kh = n / 2 + 1;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < kh; t += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nparts; ++c) s += (double)kpart[(int64_t)c * kh + t];
-    const double v = sqrt(s);
+    const double v = sqrt(key2[t]);
     keys[t] = v;
     if (t > 0 && t < n - t) keys[n - t] = v;
   }
@@ -79,6 +84,7 @@ extern "C" amm_status_t amm_circulant_spectrum_noalloc(const float* A, int64_t n
   cudaStream_t st = (cudaStream_t)stream;
   float2* tw = (float2*)base;
   float* kpart = (float*)((unsigned char*)base + kTwBytes);
+  double* key2 = (double*)((unsigned char*)base + kKey2Off);
   const int nn = (int)n;
   const int nparts = nn / cd_cols_per_cta(nn);
   if ((size_t)nparts * (nn / 2 + 1) * sizeof(float) > kPartBytes)
@@ -86,7 +92,8 @@ extern "C" amm_status_t amm_circulant_spectrum_noalloc(const float* A, int64_t n
   if ((e = cd_twiddles(tw, nn, st)) != cudaSuccess) return cuda_fail(e, "noalloc twiddles");
   if ((e = cd_spectrum(nn, A, lda, false, tw, (float2*)R, kpart, st)) != cudaSuccess)
     return cuda_fail(e, "noalloc spectrum");
-  noalloc_keys_kernel<<<(nn / 2 + 256) / 256, 256, 0, st>>>(kpart, nparts, nn, keys);
+  if ((e = cd_keys(nn / 2 + 1, kpart, nparts, key2, st)) != cudaSuccess) return cuda_fail(e, "noalloc key reduction");
+  noalloc_sqrt_mirror_kernel<<<(nn / 2 + 256) / 256, 256, 0, st>>>(key2, nn, keys);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "noalloc keys");
   return AMM_OK;
 }

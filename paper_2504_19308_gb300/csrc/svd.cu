@@ -513,13 +513,12 @@ static cudaError_t sumsq(const T* X, int64_t rows, int64_t cols, int64_t ld, dou
 
 // W: global work area of at least chol_floats(k) floats (used when chol_kp(k) > CHOL_SMEM_K)
 static cudaError_t chol_inv(int k, const float* G, float shift_rel, float* W, float* Li, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(chol_floats(CHOL_SMEM_K) * sizeof(float)));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static DeviceOnce once;
+  const cudaError_t attr = once([] {
+    return cudaFuncSetAttribute((const void*)chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(chol_floats(CHOL_SMEM_K) * sizeof(float)));
+  });
+  if (attr != cudaSuccess) return attr;
   AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0 * 2.0, 0.0, nullptr);
   const size_t sm = chol_kp(k) <= CHOL_SMEM_K ? sizeof(float) * chol_floats(k) : 0;
   chol_inv_kernel<<<1, CHOL_T, sm, st>>>(k, G, shift_rel, Li, W);

@@ -32,6 +32,7 @@
 #include <mutex>
 
 #include "api_internal.h"
+#include "common.cuh"
 #include "kernels.h"
 #include "trace.h"
 
@@ -472,16 +473,20 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
     AMM_TRACE_W(tf32 ? "umma_gemm_tf32x3" : "umma_gemm_bf16", st, 2.0 * M * N * (double)K,
                 (double)elem * ((double)M * K + (double)N * K) + 4.0 * M * N, nullptr);
     if (tf32) {
-      static cudaError_t a = cudaFuncSetAttribute((const void*)umma_gemm_kernel<true>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)UmmaCfg<true>::SMEM);
+      static DeviceOnce once;
+      const cudaError_t a = once([] {
+        return cudaFuncSetAttribute((const void*)umma_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)UmmaCfg<true>::SMEM);
+      });
       if (a != cudaSuccess) return a;
       umma_gemm_kernel<true><<<grid, UM_THREADS, UmmaCfg<true>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
                                                                              per, ws, err);
     } else {
-      static cudaError_t a = cudaFuncSetAttribute((const void*)umma_gemm_kernel<false>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)UmmaCfg<false>::SMEM);
+      static DeviceOnce once;
+      const cudaError_t a = once([] {
+        return cudaFuncSetAttribute((const void*)umma_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)UmmaCfg<false>::SMEM);
+      });
       if (a != cudaSuccess) return a;
       umma_gemm_kernel<false><<<grid, UM_THREADS, UmmaCfg<false>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
                                                                                per, ws, err);

@@ -1,9 +1,11 @@
-"""Batched products of uneven sizes: eager run, graph capture and graph replay all reproduce the
-individually computed products bit for bit."""
+"""Batched products of uneven sizes: eager run, graph capture and graph replay reproduce the
+individually computed products bit for bit, and every item matches the FP64 oracle."""
+import numpy as np
 import pytest
 
+import oracle as O
 import synth as S
-from gpu_util import dev32, torch_cuda
+from gpu_util import TOL, as64, check_selection, dev32, rel, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -49,4 +51,68 @@ def test_batch_uneven_sizes_graph_replay():
     hA = amm.decompose(A0, method0, k0, "left")
     hB = amm.decompose(B0, method0, k0, "right")
     assert torch.equal(C0, amm.approx_matmul(hA, hB))
+    batch.close()
+
+
+def _oracle_item(amm, A, B, method, k, sa, sb, compute):
+    """The oracle's Re M for one batch item, on the values the GPU sees, with the selections and
+    sketches of the same decompositions made one at a time (the batch makes identical ones)."""
+    a64, b64 = as64(A), as64(B)
+    hA = amm.decompose(A, method, k, "left", sketch=sa, compute=compute)
+    hB = amm.decompose(B, method, k, "right", sketch=sb, compute=compute)
+    if method == "circulant":
+        check_selection(hA.selection(), O.component_keys(O.circulant_spectrum(a64)), k, "A")
+        ta = O.truncate_circulant(a64, k, hA.selection())
+        tb = O.truncate_circulant(b64, k, hB.selection())
+    elif method == "cycle":
+        check_selection(hA.selection(), O.cycle_keys(a64), k, "A")
+        ta = O.truncate_cycles(a64, k, hA.selection())
+        tb = O.truncate_cycles(b64, k, hB.selection())
+    elif method == "svd":
+        ta = O.truncate_rsvd(a64, k, hA.sketch().astype(np.float64))
+        tb = O.truncate_rsvd(b64, k, hB.sketch().astype(np.float64))
+    else:
+        ta = O.truncate_fourier_left(a64, k, hA.selection())
+        tb = O.truncate_fourier_right(b64, k, hB.selection())
+    hA.close()
+    hB.close()
+    return O.product(method, ta, tb)
+
+
+def test_batch_items_match_oracle():
+    """Every item of a batch of uneven products (FP32 and BF16 operands, lengths 2^a and 3 * 2^a,
+    one n = 4096 product) against the FP64 oracle: 1e-5 for FP32 arithmetic (BF16 operands of the
+    circulant / sparsifier paths are read as BF16 and computed in FP32), 3e-2 for the rSVD in the
+    BF16 tensor-core mode (operands, sketch and GEMM intermediates rounded to BF16).  Checked after
+    the eager run and after a graph replay."""
+    torch, amm = torch_cuda()
+    spec = [(96, "circulant", "f32"), (192, "svd", "f32"), (384, "cycle", "f32"), (768, "fourier", "f32"),
+            (4096, "circulant", "f32"), (1536, "svd", "bf16"), (256, "circulant", "bf16"),
+            (3072, "cycle", "bf16"), (512, "fourier", "bf16"), (128, "svd", "f32"), (48, "circulant", "f32")]
+    items, refs, tols = [], [], []
+    for i, (n, method, dt) in enumerate(spec):
+        k = max(2, -(-n // 32))
+        a, b = S.exp32_pair(n, seed=200 + i) if n <= 1536 else S.general_times_toeplitz(n, seed=200 + i)
+        A, B = dev32(torch, a), dev32(torch, b)
+        if dt == "bf16":
+            A, B = A.bfloat16(), B.bfloat16()
+        compute = "bf16" if (dt == "bf16" and method == "svd") else "f32"
+        own = method == "svd" and (i // 4) % 2 == 0     # caller sketch; else the library's Philox draw
+        sa = dev32(torch, S.sketch(n, k, 200 + i, 0)) if own else None
+        sb = dev32(torch, S.sketch(n, k, 200 + i, 1)) if own else None
+        C = torch.full((n, n), float("nan"), device="cuda")
+        items.append((A, B, C, method, k, sa, sb, compute))
+        refs.append(_oracle_item(amm, A, B, method, k, sa, sb, compute))
+        tols.append(3e-2 if compute == "bf16" else TOL)
+    batch = amm.Batch()
+    for A, B, C, method, k, sa, sb, compute in items:
+        batch.add(A, B, C, method, k, sketch_a=sa, sketch_b=sb, compute=compute)
+    for use_graph in (False, True, True):
+        for it in items:
+            it[2].fill_(float("nan"))
+        batch.run(use_graph=use_graph)
+        torch.cuda.synchronize()
+        for (A, B, C, method, k, *_), ref, tol in zip(items, refs, tols):
+            err = rel(C.double().cpu().numpy(), ref)
+            assert err <= tol, (A.shape[0], method, str(A.dtype), use_graph, err)
     batch.close()
