@@ -3,8 +3,10 @@
     python -m paper_2504_19308_gb300.profile_case --method circulant --k 256 --n 4096 [--backward] [--repeat 2]
     python -m paper_2504_19308_gb300.profile_case --step [--repeat 2] [--trace]
 
---step runs the sweep of the n = 4096 throughput step instead (circulant k = 16/64/256, rSVD
+--step runs the sweep of the n = 4096 power-law step instead (circulant k = 16/64/256, rSVD
 k = 32/128, Fourier and cycle sparsifiers k = 41, each decomposed, multiplied and differentiated).
+--le1pct runs the products of the n = 4096 General U(0,1) x Toeplitz U(0,1) step that reach <= 1%
+error (circulant k = 1/5/9, Fourier sparsifier k = 60), each decomposed, multiplied, differentiated.
 
 Inputs are the seeded power-law pair of the bench (sigma_i = i^-1.5 + N(0, 1e-4)), drawn as
 Gaussian-plus-spectrum matrices without QR when --fast is given (same sizes, cheaper to make).
@@ -34,9 +36,12 @@ def main():
     ap.add_argument("--fast", action="store_true")
     ap.add_argument("--step", action="store_true")
     ap.add_argument("--trace", action="store_true")
+    ap.add_argument("--le1pct", action="store_true")
     a = ap.parse_args()
     n, k = a.n, a.k
-    if a.fast:
+    if a.le1pct:
+        x, y = synth.general_times_toeplitz(n, seed=0)
+    elif a.fast:
         g = synth.rng(0, 0)
         x, y = g.standard_normal((n, n)) * 1e-2, g.standard_normal((n, n)) * 1e-2
     else:
@@ -46,9 +51,13 @@ def main():
     B = torch.tensor(y, dtype=torch.float32, device=dev)
     G = torch.randn((n, n), device=dev)
     ks = -(-n // 100)
-    cases = ([("circulant", 16, True), ("circulant", 64, True), ("circulant", 256, True), ("svd", 32, True),
-              ("svd", 128, True), ("fourier", ks, True), ("cycle", ks, True)] if a.step
-             else [(a.method, k, a.backward)])
+    if a.le1pct:
+        cases = [("circulant", 1, True), ("circulant", 5, True), ("circulant", 9, True), ("fourier", 60, True)]
+    elif a.step:
+        cases = [("circulant", 16, True), ("circulant", 64, True), ("circulant", 256, True), ("svd", 32, True),
+                 ("svd", 128, True), ("fourier", ks, True), ("cycle", ks, True)]
+    else:
+        cases = [(a.method, k, a.backward)]
     sk = {}
     for method, kk, _ in cases:
         if method == "svd":
@@ -77,7 +86,7 @@ def main():
         per = a.repeat - 1
         print(json.dumps({"repeats": per, "launches": launches,
                           "ms_per_repeat": {name: round(v[1] / per, 4) for name, v in sorted(kernels.items())}}))
-    print("ok", "step" if a.step else a.method, n, k, float(C.abs().sum()))
+    print("ok", "le1pct" if a.le1pct else ("step" if a.step else a.method), n, k, float(C.abs().sum()))
 
 
 if __name__ == "__main__":
