@@ -1,13 +1,21 @@
 #!/usr/bin/env python
 """Throughput of the first-order approximate product on GB300 (one JSON line on rank 0).
 
-Workload (n = 4096, FP32, synthetic): A, B = Q1 diag(i^-1.5) Q2^T + N(0, 1e-4) noise (Haar Q from
-QR of N(0,1), i = 1..n).  One step = the whole hot path over that pair for every product of
-the sweep: decompose A and B, evaluate Re(A~ B + dA B~), and run the backward where the method
-has one (every method here).  The metric is effective throughput: the FLOPs of the exact
-products the step stands for (2 n^3 per forward, 4 n^3 per backward) divided by the step time.
+Headline workload: the products of the paper's structured pair that reach <= 1% relative error
+against the exact product, forward and backward, FP32.  A = General U(0,1), B = Toeplitz U(0,1)
+(n = 4096, the generators of the paper's experiments), truncated by the circulant decomposition
+(k = 1, 5, 9), the randomized SVD (k = 16, 32) and the Fourier sparsifier (k = 5 ceil(log2 n) = 60),
+plus the n = 512 pair Q1 diag(e^{-i/32}) Q2^T + 1e-3 N(0,1) by the randomized SVD at k = 256.  One
+step = for every product: decompose A and B, evaluate Re(A~ B + dA B~), and the backward with the
+truncation frozen.  The metric is effective throughput: the FLOPs of the exact products the step
+stands for (2 n^3 per forward, 4 n^3 per backward) divided by the step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amm|reference]
+
+Beside the headline the line carries the forms the metric compares with it (the same step with BF16
+operands, the same step as one batch captured into a CUDA graph, both together), the n = 4096
+power-law sweep, the 8192-square autograd layer, the 256-product uneven batch, the LLM-shaped
+blocked product and cuBLAS exact products for context.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 Multi-GPU: replicas (each rank runs the same independent step; no collective in the data
@@ -35,13 +43,21 @@ import synth  # noqa: E402
 METRIC = "effective 2n³/t TFLOP/s at ≤1% rel. error; BF16/batched vs plain FP32 fwd+bwd"
 UNIT = "TFLOP/s"
 N = 4096
-# (method, k, backward) -- the sweep of the n = 4096 workload; the sparsifiers keep the top 1%
-# (k = ceil(0.01 n) = 41 frequencies per row / column, or 41 cycles)
+N_SMALL = 512
+K_FOURIER = 5 * math.ceil(math.log2(N))
+# (method, k, pair): "gt" = General U(0,1) x Toeplitz U(0,1) at n = 4096; "exp32" = the n = 512 pair
+HEADLINE = [("circulant", 1, "gt"), ("circulant", 5, "gt"), ("circulant", 9, "gt"), ("svd", 16, "gt"),
+            ("svd", 32, "gt"), ("fourier", K_FOURIER, "gt"), ("svd", 256, "exp32")]
+PAIR_N = {"gt": N, "exp32": N_SMALL}
+# the n = 4096 power-law sweep (sigma_i = i^-1.5 plus N(0, 1e-4) noise): circulant k = 16/64/256,
+# rSVD k = 32/128 and the sparsifiers at the top 1% (k = ceil(0.01 n) = 41); its error is ~94-99%
 K_SPARSE = math.ceil(0.01 * N)
-PRODUCTS = [("circulant", 16, True), ("circulant", 64, True), ("circulant", 256, True),
-            ("svd", 32, True), ("svd", 128, True), ("fourier", K_SPARSE, True), ("cycle", K_SPARSE, True)]
-FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x 2 (FMA) x max SM clock
+SWEEP = [("circulant", 16, "pl"), ("circulant", 64, "pl"), ("circulant", 256, "pl"), ("svd", 32, "pl"),
+         ("svd", 128, "pl"), ("fourier", K_SPARSE, "pl"), ("cycle", K_SPARSE, "pl")]
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate
+FP32_LANES_PER_SM = 128     # FP32 FMA lanes per SM (4 sub-partitions x 32)
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+ORACLE_SAMPLE = ("circulant", 5)  # the product of the headline step the CPU oracle times
 
 
 def peaks():
@@ -52,11 +68,12 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def work_flops(products):
-    fl = 0.0
-    for _, _, bwd in products:
-        fl += 2.0 * N ** 3 + (4.0 * N ** 3 if bwd else 0.0)
-    return fl
+def work_flops(products, with_bwd=True):
+    return sum(2.0 * PAIR_N.get(p, N) ** 3 * (3.0 if with_bwd else 1.0) for _, _, p in products)
+
+
+def label(method, k, pair):
+    return "%s_k%d%s" % (method, k, "" if pair in ("gt", "pl") else "_n%d" % PAIR_N[pair])
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -110,159 +127,24 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- inputs
-def make_inputs():
-    a, b = synth.powerlaw_pair(N, seed=0)
-    phis = {k: (synth.sketch(N, k, 0, 0).astype(np.float32), synth.sketch(N, k, 0, 1).astype(np.float32))
-            for _, k, _ in PRODUCTS}
-    g = synth.upstream_grad(N, N, seed=0).astype(np.float32)
-    return a.astype(np.float32), b.astype(np.float32), phis, g
+def make_pairs():
+    """FP32 host operands and upstream gradients of the headline step, per pair."""
+    a, b = synth.general_times_toeplitz(N, seed=0)
+    a5, b5 = synth.exp32_pair(N_SMALL, seed=0)
+    out = {}
+    for key, (x, y) in (("gt", (a, b)), ("exp32", (a5, b5))):
+        n = PAIR_N[key]
+        out[key] = (x.astype(np.float32), y.astype(np.float32), synth.upstream_grad(n, n, seed=0).astype(np.float32))
+    return out
 
 
-# ----------------------------------------------------------------------------- GPU arm
-def run_amm(args, rank, world, local_rank):
-    import torch
-    import paper_2504_19308_gb300 as amm
-    from paper_2504_19308_gb300.amm import trace_collect, trace_enable
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    amm.load_library()
-    amm.set_autotune(True)  # kernel variants timed on first use, i.e. in the warm-up steps
-    a, b, phis, g = make_inputs()
-    A = torch.from_numpy(a).to(dev)
-    B = torch.from_numpy(b).to(dev)
-    G = torch.from_numpy(g).to(dev)
-    PH = {k: (torch.from_numpy(pa).to(dev), torch.from_numpy(pb).to(dev)) for k, (pa, pb) in phis.items()}
-    C = torch.empty((N, N), dtype=torch.float32, device=dev)
-    dist = world > 1
-    if dist:
-        import torch.distributed as tdist
-
-    def step(A, B, outs=None):
-        grads = []
-        for i, (method, k, bwd) in enumerate(PRODUCTS):
-            sa, sb = PH[k] if method == "svd" else (None, None)
-            hA = amm.decompose(A, method, k, "left", sketch=sa)
-            hB = amm.decompose(B, method, k, "right", sketch=sb)
-            out = C if outs is None else outs[i]
-            amm.approx_matmul(hA, hB, out=out)
-            if bwd:
-                grads += list(amm.approx_matmul_backward(hA, hB, G))
-            hA.close()
-            hB.close()
-        return grads
-
-    # accuracy of every product of the step against the exact FP64 product (outside timing)
-    exact = (A.double() @ B.double())
-    errs = {}
-    for method, k, _ in PRODUCTS:
-        sa, sb = PH[k] if method == "svd" else (None, None)
-        hA = amm.decompose(A, method, k, "left", sketch=sa)
-        hB = amm.decompose(B, method, k, "right", sketch=sb)
-        Ck = amm.approx_matmul(hA, hB)
-        errs["%s_k%d" % (method, k)] = float(torch.linalg.norm(Ck.double() - exact) / torch.linalg.norm(exact))
-    del exact
-
-    for _ in range(args.warmup):
-        step(A, B)
-    torch.cuda.synchronize()
-    trace_collect()  # drop anything recorded so far
-
-    # ---- timed region (device-resident inputs)
-    if dist:
-        tdist.barrier()
-    torch.cuda.synchronize()
-    trace_enable(True)
-    with ClockSampler(local_rank) as clk:
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("timed")
-        ev0.record()
-        for _ in range(args.steps):
-            step(A, B)
-        ev1.record()
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-    trace_enable(False)
-    if dist:
-        tdist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    kernels, launches = trace_collect()
-    clocks = clk.summary()
-    ms = max_over_ranks(ms)
-
-    # ---- end to end through the public API with host buffers (H2D inputs, D2H results)
-    a_h = torch.from_numpy(a).pin_memory()
-    b_h = torch.from_numpy(b).pin_memory()
-    outs = [torch.empty((N, N), dtype=torch.float32, device=dev) for _ in PRODUCTS]
-    outs_h = [torch.empty((N, N), dtype=torch.float32).pin_memory() for _ in PRODUCTS]
-    A2 = torch.empty_like(A)
-    B2 = torch.empty_like(B)
-
-    n_bwd = sum(1 for _, _, bwd in PRODUCTS if bwd)
-    grads_h = [[torch.empty((N, N), dtype=torch.float32).pin_memory() for _ in range(2)] if bwd else []
-               for _, _, bwd in PRODUCTS]
-    copy_stream = torch.cuda.Stream(device=dev)
-    copied = [torch.cuda.Event() for _ in PRODUCTS]
-
-    def e2e_step():
-        # each product's result and gradients go back to the host on a copy stream while the next
-        # product computes; the step ends when every result is on the host
-        cur = torch.cuda.current_stream(dev)
-        A2.copy_(a_h, non_blocking=True)
-        B2.copy_(b_h, non_blocking=True)
-        for i, (method, k, bwd) in enumerate(PRODUCTS):
-            cur.wait_event(copied[i])  # the previous step's copy of outs[i] has finished
-            sa, sb = PH[k] if method == "svd" else (None, None)
-            hA = amm.decompose(A2, method, k, "left", sketch=sa)
-            hB = amm.decompose(B2, method, k, "right", sketch=sb)
-            amm.approx_matmul(hA, hB, out=outs[i])
-            res = [outs[i]]
-            if bwd:
-                res += list(amm.approx_matmul_backward(hA, hB, G))
-            ready = torch.cuda.Event()
-            ready.record(cur)
-            copy_stream.wait_event(ready)
-            with torch.cuda.stream(copy_stream):
-                for t, th in zip(res, [outs_h[i]] + grads_h[i]):
-                    th.copy_(t, non_blocking=True)
-            for t in res[1:]:
-                t.record_stream(copy_stream)
-            copied[i].record(copy_stream)
-            hA.close()
-            hB.close()
-        cur.wait_stream(copy_stream)
-
-    for _ in range(max(1, args.warmup // 2)):
-        e2e_step()
-    torch.cuda.synchronize()
-    if dist:
-        tdist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3
-    e2e_ms = max_over_ranks(e2e_ms)
-
-    fl = work_flops(PRODUCTS)
-    value = whole_job_rate(fl * args.steps, ms * 1e-3, world)
-    e2e_value = whole_job_rate(fl * args.steps, e2e_ms * 1e-3, world)
-    roof = roofline(kernels, clocks)
-    bf16 = bf16_form(args, A, B, G, PH, ms / args.steps, dist)
-    batched = batched_form(args, dev, dist)
-    llm = llm_form(args, dev, dist)
-    le1 = le1pct_form(args, dev, dist)
-    gemm = exact_gemm_context(args, dist)
-    return {
-        "value": value, "ms_per_step": ms / args.steps, "errs": errs, "kernels": kernels,
-        "launches": launches, "clocks": clocks, "roofline": roof, "bf16": bf16, "batched": batched,
-        "llm": llm, "le1": le1, "gemm": gemm,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N * N * 4,
-                "d2h_bytes_per_step": (len(PRODUCTS) + 2 * n_bwd) * N * N * 4, "ms_per_step": e2e_ms / args.steps},
-    }
+def make_sketches(products, sizes):
+    return {(m, k, p): (synth.sketch(sizes[p], k, 0, 0).astype(np.float32),
+                        synth.sketch(sizes[p], k, 0, 1).astype(np.float32))
+            for m, k, p in products if m == "svd"}
 
 
+# ----------------------------------------------------------------------------- timing helpers
 def max_over_ranks(x: float) -> float:
     """The largest of every rank's x (the slowest rank's time); x itself without a process group.
     NCCL reduces on the rank's GPU, gloo on the CPU."""
@@ -281,63 +163,319 @@ def whole_job_rate(flops_per_rank: float, seconds: float, world: int) -> float:
     return world * flops_per_rank / seconds / 1e12
 
 
-def _device_ms(fn, steps, warmup, dist):
+def _barrier(dist):
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+
+
+def timed_steps(fn, steps, warmup, dist, flush=None):
+    """CUDA-event times (ms) of `steps` calls of fn after `warmup` untimed ones, on the current
+    stream: (total of the bracketed region, per-step list).  With flush, a buffer larger than L2 is
+    written before every step, outside the per-step events (the total is then the sum of steps)."""
     import torch
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
-    if dist:
-        import torch.distributed as tdist
-        tdist.barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(steps):
-        fn()
-    ev1.record()
+    _barrier(dist)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / steps
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+    if flush is None:
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        marks[0].record()
+        for i in range(steps):
+            fn()
+            marks[i + 1].record()
+        torch.cuda.synchronize()
+        per = [marks[i].elapsed_time(marks[i + 1]) for i in range(steps)]
+        total = marks[0].elapsed_time(marks[-1])
+    else:
+        for i in range(steps):
+            flush()
+            evs[2 * i].record()
+            fn()
+            evs[2 * i + 1].record()
+        torch.cuda.synchronize()
+        per = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(steps)]
+        total = sum(per)
+    return (max_over_ranks(total) if dist else total), per
+
+
+def _device_ms(fn, steps, warmup, dist):
+    """Median per-call CUDA-event time (ms) of fn."""
+    _, per = timed_steps(fn, steps, warmup, dist)
+    ms = statistics.median(per)
     return max_over_ranks(ms) if dist else ms
 
 
-def bf16_form(args, A, B, G, PH, fp32_ms, dist):
-    """The same fwd+bwd step in the BF16 precision mode: BF16 operands for the circulant and rSVD
-    products and BF16 tensor-core GEMMs (FP32 accumulation) for the rSVD; the sparsifiers keep FP32
-    operands (their BF16 inputs are not built).  Reported beside the FP32 step with the
-    approximation error of each product against the exact FP64 product."""
+# ----------------------------------------------------------------------------- GPU arm
+class Step:
+    """The products of one step on device-resident operands: decompose both, product, backward."""
+
+    def __init__(self, torch, amm, products, ops, sketches, bf16=False):
+        self.torch, self.amm, self.products, self.ops, self.sk, self.bf16 = torch, amm, products, ops, sketches, bf16
+
+    def one(self, method, k, pair, out=None, grads=True):
+        A, B, G = self.ops[pair]
+        sa, sb = self.sk.get((method, k, pair), (None, None))
+        comp = "bf16" if (self.bf16 and method == "svd") else "f32"
+        hA = self.amm.decompose(A, method, k, "left", sketch=sa, compute=comp)
+        hB = self.amm.decompose(B, method, k, "right", sketch=sb, compute=comp)
+        C = self.amm.approx_matmul(hA, hB, out=out)
+        g = self.amm.approx_matmul_backward(hA, hB, G) if grads else None
+        hA.close()
+        hB.close()
+        return C, g
+
+    def __call__(self):
+        for method, k, pair in self.products:
+            self.one(method, k, pair)
+
+    def errors(self):
+        torch = self.torch
+        exact = {}
+        errs = {}
+        for method, k, pair in self.products:
+            A, B, _ = self.ops[pair]
+            if pair not in exact:
+                exact[pair] = A.double() @ B.double()
+            C, _ = self.one(method, k, pair, grads=False)
+            errs[label(method, k, pair)] = float(torch.linalg.norm(C.double() - exact[pair]) /
+                                                 torch.linalg.norm(exact[pair]))
+        return errs
+
+
+def device_ops(torch, dev, pairs, bf16=False):
+    out = {}
+    for key, (a, b, g) in pairs.items():
+        A, B, G = (torch.from_numpy(x).to(dev) for x in (a, b, g))
+        out[key] = (A.bfloat16(), B.bfloat16(), G) if bf16 else (A, B, G)
+    return out
+
+
+def run_amm(args, rank, world, local_rank):
     import torch
     import paper_2504_19308_gb300 as amm
-    A16, B16 = A.bfloat16(), B.bfloat16()
+    from paper_2504_19308_gb300.amm import trace_collect, trace_enable
 
-    def operands(method):
-        return (A16, B16) if method in ("circulant", "svd") else (A, B)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    amm.load_library()
+    amm.set_autotune(True)  # kernel variants timed on first use, i.e. in the warm-up steps
+    dist = world > 1
+    pairs = make_pairs()
+    sk_host = make_sketches(HEADLINE, PAIR_N)
+    sk = {key: tuple(torch.from_numpy(x).to(dev) for x in v) for key, v in sk_host.items()}
+    ops = device_ops(torch, dev, pairs)
+    step = Step(torch, amm, HEADLINE, ops, sk)
+    errs = step.errors()
 
-    def step():
-        for method, k, bwd in PRODUCTS:
-            sa, sb = PH[k] if method == "svd" else (None, None)
-            x, y = operands(method)
-            hA = amm.decompose(x, method, k, "left", sketch=sa, compute="bf16" if method == "svd" else "f32")
-            hB = amm.decompose(y, method, k, "right", sketch=sb, compute="bf16" if method == "svd" else "f32")
-            amm.approx_matmul(hA, hB)
-            if bwd:
-                amm.approx_matmul_backward(hA, hB, G)
-            hA.close()
-            hB.close()
+    # ---- timed region (device-resident inputs; every step touches > 1 GB, above the 129 MB L2)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    trace_collect()  # drop anything recorded so far
+    _barrier(dist)
+    torch.cuda.synchronize()
+    trace_enable(True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        ms, per = timed_steps(step, args.steps, 0, dist)
+        torch.cuda.nvtx.range_pop()
+    trace_enable(False)
+    kernels, launches = trace_collect()
+    clocks = clk.summary()
+    _barrier(dist)
 
-    exact = A.double() @ B.double()
-    errs = {}
-    for method, k, _ in PRODUCTS:
-        sa, sb = PH[k] if method == "svd" else (None, None)
-        x, y = operands(method)
-        hA = amm.decompose(x, method, k, "left", sketch=sa, compute="bf16" if method == "svd" else "f32")
-        hB = amm.decompose(y, method, k, "right", sketch=sb, compute="bf16" if method == "svd" else "f32")
-        Ck = amm.approx_matmul(hA, hB)
-        errs["%s_k%d" % (method, k)] = float(torch.linalg.norm(Ck.double() - exact) / torch.linalg.norm(exact))
-    del exact
+    # ---- the same step with L2 flushed before every step
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    fl_total, fl_per = timed_steps(step, args.steps, 1, dist, flush=lambda: flush_buf.fill_(1.0))
+    del flush_buf
+
+    # ---- end to end through the public API with host buffers (H2D inputs, D2H results)
+    e2e = e2e_form(args, torch, amm, dev, pairs, sk, dist)
+
+    fl = work_flops(HEADLINE)
+    value = whole_job_rate(fl * args.steps, ms * 1e-3, world)
+    roof = roofline(kernels, clocks, dev)
+    plain_ms = statistics.median(per)
+    forms = {
+        "bf16_form": bf16_form(args, torch, amm, dev, pairs, sk, plain_ms, dist),
+        "batched_form": batched_form(args, torch, amm, dev, pairs, sk, plain_ms, dist, bf16=False),
+        "bf16_batched_form": batched_form(args, torch, amm, dev, pairs, sk, plain_ms, dist, bf16=True),
+        "powerlaw_sweep_form": sweep_form(args, torch, amm, dev, dist),
+        "autograd_layer_form": autograd_form(args, torch, amm, dev, dist),
+        "batch256_form": batch256_form(args, dev, dist),
+        "llm_blocked_form": llm_form(args, dev, dist),
+        "exact_gemm_context": exact_gemm_context(args, dist),
+    }
+    return {"value": value, "ms_per_step": ms / args.steps, "median_ms_per_step": plain_ms, "errs": errs,
+            "kernels": kernels, "launches": launches, "clocks": clocks, "roofline": roof,
+            "l2_flushed": {"median_ms_per_step": statistics.median(fl_per),
+                           "value": whole_job_rate(fl * args.steps, fl_total * 1e-3, world), "unit": UNIT,
+                           "flush": "%d MiB written before every step, outside the step's events"
+                                    % (L2_FLUSH_BYTES >> 20)},
+            "forms": forms, "e2e": e2e}
+
+
+def e2e_form(args, torch, amm, dev, pairs, sk, dist):
+    """The headline step through the public Python API with every input (A, B, upstream gradient)
+    copied from pinned host memory each step, and every product and both gradients copied back to
+    pinned host memory; the copies of one product's results run on a copy stream while the next
+    product computes.  Wall time from the host; the step ends when all results are on the host."""
+    host = {key: tuple(torch.from_numpy(x).pin_memory() for x in v) for key, v in pairs.items()}
+    devbuf = {key: tuple(torch.empty(x.shape, dtype=torch.float32, device=dev) for x in v) for key, v in host.items()}
+    outs = [torch.empty((PAIR_N[p], PAIR_N[p]), dtype=torch.float32, device=dev) for _, _, p in HEADLINE]
+    outs_h = [[torch.empty((PAIR_N[p], PAIR_N[p]), dtype=torch.float32).pin_memory() for _ in range(3)]
+              for _, _, p in HEADLINE]
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in HEADLINE]
+    step = Step(torch, amm, HEADLINE, devbuf, sk)
+
+    def one_step():
+        cur = torch.cuda.current_stream(dev)
+        for key in host:
+            for h, d in zip(host[key], devbuf[key]):
+                d.copy_(h, non_blocking=True)
+        for i, (method, k, pair) in enumerate(HEADLINE):
+            cur.wait_event(copied[i])  # the previous step's copy of outs[i] has finished
+            C, (dA, dB) = step.one(method, k, pair, out=outs[i])
+            ready = torch.cuda.Event()
+            ready.record(cur)
+            copy_stream.wait_event(ready)
+            with torch.cuda.stream(copy_stream):
+                for t, th in zip((C, dA, dB), outs_h[i]):
+                    th.copy_(t, non_blocking=True)
+            for t in (dA, dB):
+                t.record_stream(copy_stream)
+            copied[i].record(copy_stream)
+        cur.wait_stream(copy_stream)
+
+    for _ in range(max(1, args.warmup // 2)):
+        one_step()
+    torch.cuda.synchronize()
+    _barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    e2e_ms = max_over_ranks(e2e_ms) if dist else e2e_ms
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    h2d = sum(x.numel() * 4 for v in host.values() for x in v)
+    d2h = sum(3 * PAIR_N[p] ** 2 * 4 for _, _, p in HEADLINE)
+    return {"value": whole_job_rate(work_flops(HEADLINE) * args.steps, e2e_ms * 1e-3, world), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
+
+
+def bf16_form(args, torch, amm, dev, pairs, sk, fp32_ms, dist):
+    """The headline step in the BF16 precision mode: BF16 operands for every product, BF16 tcgen05
+    GEMMs with FP32 accumulation for the rSVD; the circulant spectra and applies read BF16 and
+    compute in FP32; the Fourier sparsifier widens its BF16 operand once to an FP32 copy."""
+    step = Step(torch, amm, HEADLINE, device_ops(torch, dev, pairs, bf16=True), sk, bf16=True)
+    errs = step.errors()
     ms = _device_ms(step, args.steps, args.warmup, dist)
-    fl = work_flops(PRODUCTS)
-    return {"ms_per_step": ms, "value": fl / (ms * 1e-3) / 1e12, "unit": UNIT, "speedup_vs_fp32": fp32_ms / ms,
-            "approx_rel_err_vs_exact": errs,
-            "modes": "circulant: BF16 operands; rSVD: BF16 operands + BF16 tcgen05 GEMMs; sparsifiers: FP32"}
+    return {"median_ms_per_step": ms, "value": work_flops(HEADLINE) / (ms * 1e-3) / 1e12, "unit": UNIT,
+            "speedup_vs_fp32": fp32_ms / ms, "approx_rel_err_vs_exact": errs,
+            "all_le_1pct": all(v <= 0.01 for v in errs.values()),
+            "modes": "BF16 operands; rSVD: BF16 tcgen05 GEMMs; circulant: BF16 reads, FP32 FFTs; Fourier: "
+                     "widened to FP32 once"}
+
+
+def batched_form(args, torch, amm, dev, pairs, sk, fp32_ms, dist, bf16=False):
+    """The headline step as one batch (amm_batch_add_grad: decompose, product and backward of every
+    product) launched as one CUDA graph, against the plain FP32 step (one product at a time on one
+    stream).  Errors from the batch's own outputs."""
+    ops = device_ops(torch, dev, pairs, bf16=bf16)
+    batch = amm.Batch()
+    outs = []
+    for method, k, pair in HEADLINE:
+        A, B, G = ops[pair]
+        n = PAIR_N[pair]
+        C = torch.empty((n, n), device=dev)
+        dA = torch.empty((n, n), device=dev)
+        dB = torch.empty((n, n), device=dev)
+        sa, sb = sk.get((method, k, pair), (None, None))
+        batch.add(A, B, C, method, k, sketch_a=sa, sketch_b=sb,
+                  compute="bf16" if (bf16 and method == "svd") else "f32", dC=G, dA=dA, dB=dB)
+        outs.append(C)
+    batch.run(use_graph=True)  # eager pass + capture + first launch
+    torch.cuda.synchronize()
+    errs = {}
+    exact = {}
+    for (method, k, pair), C in zip(HEADLINE, outs):
+        A, B, _ = ops[pair]
+        if pair not in exact:
+            exact[pair] = A.double() @ B.double()
+        errs[label(method, k, pair)] = float(torch.linalg.norm(C.double() - exact[pair]) /
+                                             torch.linalg.norm(exact[pair]))
+    del exact
+    ms = _device_ms(lambda: batch.run(use_graph=True), args.steps, max(1, args.warmup), dist)
+    batch.close()
+    return {"median_ms_per_step": ms, "value": work_flops(HEADLINE) / (ms * 1e-3) / 1e12, "unit": UNIT,
+            "speedup_vs_fp32": fp32_ms / ms, "approx_rel_err_vs_exact": errs,
+            "all_le_1pct": all(v <= 0.01 for v in errs.values()),
+            "mode": ("BF16 operands, " if bf16 else "FP32, ") + "one CUDA graph of the batch scheduler "
+                    "(8 forked streams)"}
+
+
+def sweep_form(args, torch, amm, dev, dist):
+    """The n = 4096 power-law workload (sigma_i = i^-1.5 plus N(0, 1e-4) noise, variance reading):
+    circulant k = 16/64/256, rSVD k = 32/128, Fourier and cycle sparsifiers at the top 1%, fwd+bwd.
+    Its noise dominates its signal, so every product is far from 1% error (reported)."""
+    a, b = synth.powerlaw_pair(N, seed=0)
+    g = synth.upstream_grad(N, N, seed=0)
+    ops = {"pl": tuple(torch.from_numpy(x.astype(np.float32)).to(dev) for x in (a, b, g))}
+    del a, b, g
+    sk = {key: tuple(torch.from_numpy(x).to(dev) for x in v) for key, v in make_sketches(SWEEP, {"pl": N}).items()}
+    step = Step(torch, amm, SWEEP, ops, sk)
+    errs = step.errors()
+    ms = _device_ms(step, max(3, args.steps // 2), max(1, args.warmup), dist)
+    fl = sum(6.0 * N ** 3 for _ in SWEEP)
+    return {"workload": "powerlaw n=4096 FP32: A,B = Q1 diag(i^-1.5) Q2^T + N(0,1e-4); circulant k=16/64/256, "
+                        "rSVD k=32/128, Fourier and cycle sparsifiers top 1%% (k=%d), fwd+bwd" % K_SPARSE,
+            "median_ms_per_step": ms, "value": fl / (ms * 1e-3) / 1e12, "unit": UNIT,
+            "approx_rel_err_vs_exact": errs}
+
+
+def autograd_form(args, torch, amm, dev, dist):
+    """The differentiation workload as an autograd layer: A 8192 x 8192 = Q1 diag(e^{-i/256}) Q2^T
+    (noise-free, Haar factors from a QR drawn on the device), B 8192 x 4096 and the upstream
+    gradient N(0,1); rSVD k = 128; forward and backward through torch.autograd (the library's
+    adjoint kernels).  Effective rate: 2 m n p forward + 4 m n p backward over the time."""
+    n, p, k = 8192, 4096, 128
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+
+    def haar(m):
+        q, r = torch.linalg.qr(torch.randn((m, m), generator=gen, device=dev))
+        return q * torch.sign(torch.diagonal(r))[None, :]
+
+    sig = torch.exp(-torch.arange(n, device=dev, dtype=torch.float32) / 256.0)
+    A = ((haar(n) * sig[None, :]) @ haar(n).T).contiguous()
+    B = torch.randn((n, p), generator=gen, device=dev)
+    G = torch.randn((n, p), generator=gen, device=dev)
+    sa = torch.randn((n, k), generator=gen, device=dev)
+    sb = torch.randn((p, k), generator=gen, device=dev)
+    Ar = A.clone().requires_grad_(True)
+    Br = B.clone().requires_grad_(True)
+
+    def fwd_bwd():
+        Ar.grad = None
+        Br.grad = None
+        C = amm.approx_matmul_autograd(Ar, Br, "svd", k, sketch_a=sa, sketch_b=sb)
+        C.backward(G)
+
+    C = amm.approx_matmul_autograd(A, B, "svd", k, sketch_a=sa, sketch_b=sb)
+    exact = A.double() @ B.double()
+    err = float(torch.linalg.norm(C.double() - exact) / torch.linalg.norm(exact))
+    del exact, C
+    ms = _device_ms(fwd_bwd, max(3, args.steps // 2), max(1, args.warmup), dist)
+    fl = 6.0 * n * n * p
+    return {"workload": "A 8192x8192 sigma_i=e^{-i/256} (noise-free), B 8192x4096 N(0,1), G N(0,1); rSVD k=128; "
+                        "fwd+bwd through torch.autograd", "median_ms": ms, "value": fl / (ms * 1e-3) / 1e12,
+            "unit": UNIT, "approx_rel_err_vs_exact": err}
 
 
 def batch_sizes_for(count):
@@ -346,7 +484,7 @@ def batch_sizes_for(count):
     return synth.batch_sizes(count, seed=0, radix3=True), ["circulant", "svd", "fourier", "cycle"]
 
 
-def batched_form(args, dev, dist, count=256):
+def batch256_form(args, dev, dist, count=256):
     """256 independent forward products of log-uniform sizes n in [128, 4096] (nearest 2^a or
     3 * 2^a), methods in rotation, k = ceil(n/32), plus one circulant product at n = 16384, FP32:
     one at a time on one stream versus one CUDA-graph launch of the batch scheduler.  Operands:
@@ -380,8 +518,9 @@ def batched_form(args, dev, dist, count=256):
         batch.add(A, B, C, method, k, sketch_a=sa, sketch_b=sb)
     batch.run(use_graph=True)  # eager pass + capture
     torch.cuda.synchronize()
-    eager_ms = _device_ms(eager, max(1, args.steps // 5), 1, dist)
-    graph_ms = _device_ms(lambda: batch.run(use_graph=True), max(1, args.steps // 5), 1, dist)
+    reps = max(3, args.steps // 5)
+    eager_ms = _device_ms(eager, reps, 1, dist)
+    graph_ms = _device_ms(lambda: batch.run(use_graph=True), reps, 1, dist)
     batch.close()
     fl = sum(2.0 * n ** 3 for n in sizes)
     # plus one n = 16384 product (circulant, k = n/32 = 512), timed on its own: inside the batch
@@ -398,10 +537,11 @@ def batched_form(args, dev, dist, count=256):
         hA.close()
         hB.close()
 
-    big_ms = _device_ms(big, max(1, args.steps // 5), 1, dist)
+    big_ms = _device_ms(big, reps, 1, dist)
     del Ab, Bb, Cb
     return {"products": count, "n16384_circulant_k512_ms": big_ms,
-            "n16384_value": 2.0 * nb ** 3 / (big_ms * 1e-3) / 1e12, "sizes": "n = exp(U(ln 128, ln 4096)) rounded to the nearest of {2^a, 3 * 2^a} "
+            "n16384_value": 2.0 * nb ** 3 / (big_ms * 1e-3) / 1e12,
+            "sizes": "n = exp(U(ln 128, ln 4096)) rounded to the nearest of {2^a, 3 * 2^a} "
             "(%d..%d, %d of the form 3 * 2^a), k = ceil(n/32), methods in rotation, forward; the extra "
             "n = 16384 product (circulant, k = 512) timed alone"
             % (min(sizes), max(sizes), sum(1 for v in sizes if v & (v - 1))),
@@ -442,8 +582,9 @@ def llm_form(args, dev, dist):
     exact = X.double() @ W.double()
     err = float(torch.linalg.norm(C.double() - exact) / torch.linalg.norm(exact))
     del exact
-    ms = _device_ms(fwd, max(1, args.steps // 2), args.warmup, dist)
-    ms_both = _device_ms(fwd_both, max(1, args.steps // 2), args.warmup, dist)
+    reps = max(3, args.steps // 2)
+    ms = _device_ms(fwd, reps, args.warmup, dist)
+    ms_both = _device_ms(fwd_both, reps, args.warmup, dist)
     hW.close()
     fl = 2.0 * X.shape[0] * X.shape[1] * W.shape[1]
     return {"workload": "X 2048x4096 by rSVD k=256 times W 4096x11008 in 4096-square circulant blocks, k=128 "
@@ -451,47 +592,6 @@ def llm_form(args, dev, dist):
             "ms_weight_offline": ms, "value": fl / (ms * 1e-3) / 1e12, "unit": UNIT,
             "ms_both_decompositions": ms_both, "value_both": fl / (ms_both * 1e-3) / 1e12,
             "approx_rel_err_vs_exact": err}
-
-
-def le1pct_form(args, dev, dist):
-    """The metric's accuracy qualifier on the paper's own structured pair: General U(0,1) x Toeplitz
-    U(0,1) at n = 4096 (the experiments' generators), where truncations reach <= 1% error.
-    Circulant k = 1, 5, 9 and the Fourier sparsifier at k = 5 ceil(log2 n) = 60, forward and
-    backward.  Each product's error against the exact FP64 product is reported; the rate counts
-    the products at <= 1% error (2 n^3 forward + 4 n^3 backward each over their step time)."""
-    import torch
-    import paper_2504_19308_gb300 as amm
-    a, b = synth.general_times_toeplitz(N, seed=0)
-    A = torch.from_numpy(a.astype(np.float32)).to(dev)
-    B = torch.from_numpy(b.astype(np.float32)).to(dev)
-    del a, b
-    G = torch.randn((N, N), device=dev, generator=torch.Generator(device=dev).manual_seed(4))
-    ks = 5 * math.ceil(math.log2(N))
-    prods = [("circulant", 1), ("circulant", 5), ("circulant", 9), ("fourier", ks)]
-    exact = A.double() @ B.double()
-    errs = {}
-    for method, k in prods:
-        hA, hB = amm.decompose(A, method, k, "left"), amm.decompose(B, method, k, "right")
-        C = amm.approx_matmul(hA, hB)
-        errs["%s_k%d" % (method, k)] = float(torch.linalg.norm(C.double() - exact) / torch.linalg.norm(exact))
-        hA.close()
-        hB.close()
-    del exact
-    ok = [(m, k) for m, k in prods if errs["%s_k%d" % (m, k)] <= 0.01]
-
-    def step():
-        for method, k in ok:
-            hA, hB = amm.decompose(A, method, k, "left"), amm.decompose(B, method, k, "right")
-            amm.approx_matmul(hA, hB)
-            amm.approx_matmul_backward(hA, hB, G)
-            hA.close()
-            hB.close()
-
-    ms = _device_ms(step, args.steps, args.warmup, dist) if ok else float("nan")
-    fl = 6.0 * N ** 3 * len(ok)
-    return {"workload": "General U(0,1) x Toeplitz U(0,1), n=4096 FP32, fwd+bwd", "approx_rel_err_vs_exact": errs,
-            "products_at_le1pct": ["%s k=%d" % p for p in ok], "ms_per_step": ms,
-            "value": fl / (ms * 1e-3) / 1e12 if ok else None, "unit": UNIT}
 
 
 def exact_gemm_context(args, dist):
@@ -507,42 +607,86 @@ def exact_gemm_context(args, dist):
     try:
         for name, tf32, x, y in (("fp32", False, A, B), ("tf32", True, A, B), ("bf16", False, A.bfloat16(), B.bfloat16())):
             torch.backends.cuda.matmul.allow_tf32 = tf32
-            ms = _device_ms(lambda: x @ y, max(3, args.steps), args.warmup, dist)
+            ms = _device_ms(lambda: x @ y, max(5, args.steps), args.warmup, dist)
             out[name] = {"ms": ms, "TFLOP/s": 2.0 * N ** 3 / (ms * 1e-3) / 1e12}
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
     return out
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from an ncu launch list
-# of the whole step (profile_case --step), averaged over the kernel's launches in one step like the
-# achieved rate (cd_sddmm: both SDDMM kernels, 12 launches, six of them gated off); keyed by the
-# trace name, and to be dropped when the kernel changes (None = not captured as it stands)
-NCU_TRAFFIC = {"cd_sddmm": 151.6e6}
+# ----------------------------------------------------------------------------- roofline
+# trace label of the library -> the kernel function it launches
+KERNEL_OF = {
+    "cd_spectrum": "cd_spectrum_kernel", "bw_row_spectrum": "bw_spectrum_kernel",
+    "bw_col_spectrum": "bw_spectrum_kernel", "cd_residual": "cd_residual_kernel",
+    "cd_residual_imag": "cd_residual_kernel", "cd_project": "cd_residual_kernel",
+    "cd_apply_col": "cd_apply_kernel", "cd_apply_row": "cd_apply_kernel", "cd_apply_unpaired": "cd_apply_kernel",
+    "cd_sddmm": "cd_sddmm_kernel", "cd_sddmm_tiled": "cd_sddmm_tiled_kernel", "cd_rho": "cd_rho_kernel",
+    "cd_eigen": "cd_eigen_kernel", "cd_select": "cd_select_kernel", "cd_keyreduce": "cd_keyreduce_kernel",
+    "umma_gemm_tf32x3": "umma_gemm_kernel<true>", "umma_gemm_bf16": "umma_gemm_kernel<false>",
+    "umma_splitk_reduce": "umma_splitk_reduce_kernel", "ft_row_transform": "ft_transform_kernel",
+    "ft_col_transform": "ft_transform_kernel", "ft_t1": "ft_t1_kernel", "ft_t2": "ft_t2_kernel",
+    "cyc_apply_col": "cyc_apply_col_kernel", "cyc_apply_row": "cyc_apply_row_kernel",
+}
+# Family of a kernel for the per-family roofline entries.
+FAMILY_OF = {
+    "cd_spectrum_kernel": "fft", "bw_spectrum_kernel": "fft", "cd_residual_kernel": "fft",
+    "ft_transform_kernel": "fft", "cd_apply_kernel": "spectral_apply", "cd_sddmm_kernel": "sddmm",
+    "cd_sddmm_tiled_kernel": "sddmm", "umma_gemm_kernel<true>": "tcgen05_gemm",
+    "umma_gemm_kernel<false>": "tcgen05_gemm", "ft_t1_kernel": "sparsifier_apply", "ft_t2_kernel": "sparsifier_apply",
+    "cyc_apply_col_kernel": "sparsifier_apply", "cyc_apply_row_kernel": "sparsifier_apply",
+}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one-kernel ncu captures
+# (3 launches each of the headline step, profile_case --le1pct), keyed by kernel; an entry is dropped
+# when its kernel changes (None = not captured as it stands)
+NCU_TRAFFIC = {}
 
 
-def roofline(kernels, clocks):
-    """Roofline of the kernel that takes most of the timed region.
+def fp32_peak(dev, clocks):
+    """FP32 FMA peak (TFLOP/s) of this GPU: SMs (device attribute) x 128 FP32 lanes x 2 FLOP per FMA
+    x the maximum SM clock (sampled by nvidia-smi, else the measured peaks file)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or peaks()[0].get("sm_max_mhz") or 2070.0
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz" % (
+        sms, FP32_LANES_PER_SM, mhz)
 
-    The bound is the resource the kernel's algorithmic work needs longest on: HBM bytes against
-    the measured copy bandwidth, or FLOPs against the pipe that executes them (FP32 FMA lanes for
-    SIMT kernels; the TF32 tensor rate / 3 for the TF32x3 GEMM, which issues three MMAs per
-    product).  Peaks for a kernel timed inside a long step: the sustained tensor figure.
-    """
+
+def kernel_totals(kernels):
+    """Trace labels merged into kernel functions: {kernel: [launches, ms, flops, bytes]}."""
+    out = {}
+    for lab, (launches, ms, flops, bytes_) in kernels.items():
+        name = KERNEL_OF.get(lab, lab)
+        t = out.setdefault(name, [0, 0.0, 0.0, 0.0])
+        t[0] += launches
+        t[1] += ms
+        t[2] += flops
+        t[3] += bytes_
+    return out
+
+
+def roof_entry(name, tot, dev, clocks):
+    """Roofline of one kernel: the bound is the resource its algorithmic work needs longest on (HBM
+    bytes against the measured copy bandwidth, or FLOPs against the pipe that executes them: FP32
+    FMA lanes for SIMT kernels, the TF32 tensor rate / 3 for the TF32x3 GEMM, the BF16 tensor rate
+    for the BF16 GEMM; sustained figures, the kernels run inside a long step)."""
+    launches, ms, flops, bytes_ = tot
     pk, src = peaks()
-    name, (launches, ms, flops, bytes_) = max(kernels.items(), key=lambda kv: kv[1][1])
     hbm = pk["hbm_gbs"]
-    if name.startswith("umma_gemm_tf32"):
-        cpeak, cunit, cbound = pk["bf16_tflops_sustained"] * TF32_PER_BF16 / 3.0, "tensor", \
-            "%s: bf16_tflops_sustained x %.3f (nominal TF32:BF16) / 3 (TF32x3)" % (src, TF32_PER_BF16)
-    elif name.startswith("umma_gemm_bf16"):
+    if name == "umma_gemm_kernel<true>":
+        cpeak, cunit = pk["bf16_tflops_sustained"] * TF32_PER_BF16 / 3.0, "tensor"
+        cbound = "%s: bf16_tflops_sustained x %.3f (nominal TF32:BF16) / 3 (TF32x3)" % (src, TF32_PER_BF16)
+    elif name == "umma_gemm_kernel<false>":
         cpeak, cunit, cbound = pk["bf16_tflops_sustained"], "tensor", "%s: bf16_tflops_sustained" % src
     else:
-        cpeak, cunit, cbound = FP32_ALU_PEAK, "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-    t_mem = bytes_ / (hbm * 1e9)
-    t_cmp = flops / (cpeak * 1e12)
+        cpeak, cbound = fp32_peak(dev, clocks)
+        cunit = "alu"
     base = {"kernel": name, "traffic": NCU_TRAFFIC.get(name), "launches": launches, "avg_launch_ms": ms / launches,
             "algorithmic_bytes_per_launch": bytes_ / launches, "algorithmic_flops_per_launch": flops / launches}
+    t_mem = bytes_ / (hbm * 1e9)
+    t_cmp = flops / (cpeak * 1e12)
+    if bytes_ == 0 and flops == 0:
+        return dict(base, bound="latency", achieved=None, peak=None, unit=None, frac=None)
     if t_mem >= t_cmp:
         achieved = bytes_ / (ms * 1e-3) / 1e9
         return dict(base, bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
@@ -552,16 +696,48 @@ def roofline(kernels, clocks):
                 peak_source=cbound)
 
 
+def roofline(kernels, clocks, dev):
+    """The dominant kernel's roofline (the kernel function with the largest total time in the timed
+    region), plus one entry per kernel family (the family's kernel with the largest time)."""
+    tot = kernel_totals(kernels)
+    name = max(tot, key=lambda k: tot[k][1])
+    out = roof_entry(name, tot[name], dev, clocks)
+    fams = {}
+    for k, v in tot.items():
+        f = FAMILY_OF.get(k)
+        if f and (f not in fams or v[1] > tot[fams[f]][1]):
+            fams[f] = k
+    out["families"] = {f: roof_entry(k, tot[k], dev, clocks) for f, k in sorted(fams.items())}
+    out["share_of_step"] = tot[name][1] / sum(v[1] for v in tot.values())
+    return out
+
+
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(seconds_hint: float = 20.0):
-    """Time the FP64 oracle on one forward circulant product (k = 16) of the same n = 4096 pair."""
+def _oracle_operands():
+    a, b = synth.general_times_toeplitz(N, seed=0)
+    g = synth.upstream_grad(N, N, seed=0)
+    return (a.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64),
+            g.astype(np.float32).astype(np.float64))
+
+
+def oracle_product(a64, b64, g64):
+    """One product of the headline step on the FP64 oracle: circulant k = 5 forward and backward."""
     import oracle
-    a, b, _, _ = make_inputs()
-    a64, b64 = a.astype(np.float64), b.astype(np.float64)
+    _, k = ORACLE_SAMPLE
+    _, _, ta, tb = oracle.cd_matmul(a64, b64, k, full=True)
+    oracle.cd_backward(ta, tb, g64)
+
+
+ORACLE_SAMPLE_TEXT = ("one product of the step per sample: circulant k=5 forward and backward of the n=4096 "
+                      "General x Toeplitz pair, FP64 oracle (numpy)")
+
+
+def oracle_sample():
+    ops = _oracle_operands()
     t0 = time.perf_counter()
-    oracle.cd_matmul(a64, b64, 16)
+    oracle_product(*ops)
     dt = time.perf_counter() - t0
-    return dt, 2.0 * N ** 3 / dt / 1e12
+    return dt, 6.0 * N ** 3 / dt / 1e12
 
 
 def cpu_cores():
@@ -574,30 +750,30 @@ def cpu_cores():
 def run_reference(args, rank):
     if rank != 0:
         return None
-    import oracle
-    a, b, _, _ = make_inputs()
-    a64, b64 = a.astype(np.float64), b.astype(np.float64)
+    ops = _oracle_operands()
     for _ in range(args.warmup):
-        oracle.cd_matmul(a64, b64, 16)
+        oracle_product(*ops)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.cd_matmul(a64, b64, 16)
+        oracle_product(*ops)
     dt = time.perf_counter() - t0
-    value = 2.0 * N ** 3 * args.steps / dt / 1e12
-    sample = "one forward circulant product (k=16) of the n=4096 pair per step, FP64 oracle (numpy)"
+    value = 6.0 * N ** 3 * args.steps / dt / 1e12
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_block(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": ORACLE_SAMPLE_TEXT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def config_block():
-    return {"workload": "powerlaw n=4096 FP32: A,B = Q1 diag(i^-1.5) Q2^T + N(0,1e-4); fwd+bwd sweep: circulant "
-                        "k=16/64/256, rSVD k=32/128, Fourier and cycle sparsifiers top 1%% (k=%d)" % K_SPARSE,
-            "n": N, "products": ["%s k=%d %s" % (m, k, "fwd+bwd" if b else "fwd") for m, k, b in PRODUCTS],
-            "l2": "no flush: each step touches ~2 GB (inputs, spectra, residuals, GEMM panels) > 129 MB L2",
+    return {"workload": "<=1%% error step: General U(0,1) x Toeplitz U(0,1) n=4096 FP32 by circulant k=1/5/9, rSVD "
+                        "k=16/32, Fourier sparsifier k=%d; plus n=512 Q1 diag(e^{-i/32}) Q2^T + 1e-3 N(0,1) by rSVD "
+                        "k=256; each decomposed, multiplied and differentiated (fwd+bwd)" % K_FOURIER,
+            "n": N, "products": ["%s k=%d n=%d fwd+bwd" % (m, k, PAIR_N[p]) for m, k, p in HEADLINE],
+            "l2": "no flush in the headline: each step touches > 1 GB (inputs, spectra, residuals, GEMM panels), "
+                  "above the 129 MB L2; an L2-flushed variant is reported beside it",
             "parallelism": "replicas",
             "autotune": "on: the spectral-apply variant (2 or 4 packed signals per CTA) of each length, direction "
                         "and element type is timed in the warm-up and the fastest kept"}
@@ -606,7 +782,7 @@ def config_block():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="amm", choices=["amm", "reference"])
     args = ap.parse_args()
@@ -629,16 +805,14 @@ def main():
         if world == 1:
             dt, val = oracle_sample()
             cpu = {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                   "sample": "one forward circulant product (k=16) of the same n=4096 pair, FP64 oracle, "
-                             "%.1f s" % dt}
+                   "sample": ORACLE_SAMPLE_TEXT + ", %.1f s" % dt}
         cfg = config_block()
         cfg["approx_rel_err_vs_exact"] = r["errs"]
+        cfg["all_le_1pct"] = all(v <= 0.01 for v in r["errs"].values())
+        cfg["median_ms_per_step"] = r["median_ms_per_step"]
+        cfg["l2_flushed"] = r["l2_flushed"]
         cfg["kernels_ms"] = {k: round(v[1] / args.steps, 4) for k, v in r["kernels"].items()}
-        cfg["bf16_form"] = r["bf16"]
-        cfg["batched_form"] = r["batched"]
-        cfg["llm_blocked_form"] = r["llm"]
-        cfg["le1pct_form"] = r["le1"]
-        cfg["exact_gemm_context"] = r["gemm"]
+        cfg.update(r["forms"])
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,

@@ -370,6 +370,18 @@ amm_status_t amm_batch_add(amm_batch_t batch, const void* A, const void* B, floa
                            int64_t n, int64_t p, int64_t lda, int64_t ldb, int64_t ldc,
                            amm_dtype_t dtype, amm_method_t method, int64_t k,
                            const amm_opts_t* opts_a, const amm_opts_t* opts_b);
+/*
+ * amm_batch_add with the backward of the item: after the product, the run also writes the frozen-
+ * truncation gradients of <dC, Re M> (as amm_approx_matmul_backward) to dA (m x n, ldda) and / or
+ * dB (n x p, lddb) -- device, caller-owned, overwritten; one of them may be NULL -- from dC (m x p,
+ * lddc).  Same mixed-method and shape limits as amm_approx_matmul_backward (checked when the batch
+ * runs).
+ */
+amm_status_t amm_batch_add_grad(amm_batch_t batch, const void* A, const void* B, float* C, int64_t m,
+                                int64_t n, int64_t p, int64_t lda, int64_t ldb, int64_t ldc,
+                                amm_dtype_t dtype, amm_method_t method, int64_t k,
+                                const amm_opts_t* opts_a, const amm_opts_t* opts_b, const float* dC,
+                                int64_t lddc, float* dA, int64_t ldda, float* dB, int64_t lddb);
 amm_status_t amm_batch_run(amm_batch_t batch, void* stream, int32_t use_graph);
 amm_status_t amm_batch_destroy(amm_batch_t batch);
 

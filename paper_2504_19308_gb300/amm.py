@@ -97,6 +97,12 @@ SIGNATURES = {
                                      ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                      ctypes.POINTER(Opts), ctypes.POINTER(Opts)]),
+    "amm_batch_add_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                          ctypes.POINTER(Opts), ctypes.POINTER(Opts), ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_int64]),
     "amm_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "amm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "amm_trace_enable": (ctypes.c_int, [ctypes.c_int32]),
@@ -438,9 +444,12 @@ class Batch:
         self.keep = []
 
     def add(self, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, method: str, k: int,
-            sketch_a: Optional[torch.Tensor] = None, sketch_b: Optional[torch.Tensor] = None, compute: str = "f32"):
-        for t, nm in ((A, "A"), (B, "B"), (C, "C")):
-            _require_cuda(t, nm)
+            sketch_a: Optional[torch.Tensor] = None, sketch_b: Optional[torch.Tensor] = None, compute: str = "f32",
+            dC: Optional[torch.Tensor] = None, dA: Optional[torch.Tensor] = None, dB: Optional[torch.Tensor] = None):
+        """One product C = Re M; with dC given, also its backward into dA and / or dB (amm_batch_add_grad)."""
+        for t, nm in ((A, "A"), (B, "B"), (C, "C"), (dC, "dC"), (dA, "dA"), (dB, "dB")):
+            if t is not None:
+                _require_cuda(t, nm)
         oa, ob = Opts(), Opts()
         lib = load_library()
         _check(lib.amm_opts_init(ctypes.byref(oa)), "amm_opts_init")
@@ -450,10 +459,19 @@ class Batch:
             oa.sketch = sketch_a.data_ptr()
         if sketch_b is not None:
             ob.sketch = sketch_b.data_ptr()
-        self.keep += [A, B, C, sketch_a, sketch_b]
-        _check(lib.amm_batch_add(self.ptr, A.data_ptr(), B.data_ptr(), C.data_ptr(), A.shape[0], A.shape[1],
-                                 B.shape[1], A.stride(0), B.stride(0), C.stride(0), DTYPES[A.dtype], METHODS[method],
-                                 k, ctypes.byref(oa), ctypes.byref(ob)), "amm_batch_add")
+        self.keep += [A, B, C, sketch_a, sketch_b, dC, dA, dB]
+        if dC is None:
+            _check(lib.amm_batch_add(self.ptr, A.data_ptr(), B.data_ptr(), C.data_ptr(), A.shape[0], A.shape[1],
+                                     B.shape[1], A.stride(0), B.stride(0), C.stride(0), DTYPES[A.dtype],
+                                     METHODS[method], k, ctypes.byref(oa), ctypes.byref(ob)), "amm_batch_add")
+            return
+        _check(lib.amm_batch_add_grad(self.ptr, A.data_ptr(), B.data_ptr(), C.data_ptr(), A.shape[0], A.shape[1],
+                                      B.shape[1], A.stride(0), B.stride(0), C.stride(0), DTYPES[A.dtype],
+                                      METHODS[method], k, ctypes.byref(oa), ctypes.byref(ob), dC.data_ptr(),
+                                      dC.stride(0), dA.data_ptr() if dA is not None else None,
+                                      dA.stride(0) if dA is not None else 0,
+                                      dB.data_ptr() if dB is not None else None,
+                                      dB.stride(0) if dB is not None else 0), "amm_batch_add_grad")
 
     def run(self, use_graph: bool = True):
         dev = self.keep[0].device

@@ -1,6 +1,7 @@
 // Batches of independent first-order products of uneven sizes (for example the layers of an
-// LLM-shaped stack).  amm_batch_run executes every item (decompose A, decompose B, product,
-// release) on a small pool of streams forked from the caller's stream.  With use_graph the first
+// LLM-shaped stack).  amm_batch_run executes every item (decompose A, decompose B, product, the
+// backward for items added with amm_batch_add_grad, release) on a small pool of streams forked
+// from the caller's stream.  With use_graph the first
 // run executes eagerly once (building twiddle tables and setting kernel attributes, which must
 // not happen inside a capture), then captures the same work into one CUDA graph; every later
 // run is a single graph launch.  Device memory of the handles is stream-ordered, so inside the
@@ -21,6 +22,11 @@ struct amm_batch {
     int64_t m, n, p, lda, ldb, ldc, k;
     int dtype, method;
     amm_opts_t oa, ob;
+    // optional backward of the item (amm_batch_add_grad): dC in, dA / dB out (either may be NULL)
+    const float* dC = nullptr;
+    float* dA = nullptr;
+    float* dB = nullptr;
+    int64_t lddc = 0, ldda = 0, lddb = 0;
   };
   std::vector<Item> items;
   int nstreams = 8;
@@ -80,6 +86,28 @@ extern "C" amm_status_t amm_batch_add(amm_batch_t b, const void* A, const void* 
   return AMM_OK;
 }
 
+extern "C" amm_status_t amm_batch_add_grad(amm_batch_t b, const void* A, const void* B, float* C, int64_t m,
+                                           int64_t n, int64_t p, int64_t lda, int64_t ldb, int64_t ldc,
+                                           amm_dtype_t dtype, amm_method_t method, int64_t k,
+                                           const amm_opts_t* opts_a, const amm_opts_t* opts_b, const float* dC,
+                                           int64_t lddc, float* dA, int64_t ldda, float* dB, int64_t lddb) {
+  if (!b || !dC || (!dA && !dB)) return fail(AMM_ERR_INVALID_ARG, "amm_batch_add_grad: NULL dC, or both dA and dB NULL");
+  if (lddc < p || (dA && ldda < n) || (dB && lddb < p))
+    return fail(AMM_ERR_INVALID_ARG, "amm_batch_add_grad: bad leading dimension");
+  const size_t before = b->captured ? 0 : b->items.size();
+  amm_status_t st = amm_batch_add(b, A, B, C, m, n, p, lda, ldb, ldc, dtype, method, k, opts_a, opts_b);
+  if (st != AMM_OK) return st;
+  if (b->items.size() != before + 1) return fail(AMM_ERR_STATE, "amm_batch_add_grad: item not recorded");
+  auto& it = b->items.back();
+  it.dC = dC;
+  it.lddc = lddc;
+  it.dA = dA;
+  it.ldda = ldda;
+  it.dB = dB;
+  it.lddb = lddb;
+  return AMM_OK;
+}
+
 static amm_status_t run_items(amm_batch* b, cudaStream_t parent) {
   cudaError_t e;
   if (b->streams.empty()) {
@@ -108,6 +136,8 @@ static amm_status_t run_items(amm_batch* b, cudaStream_t parent) {
     if (st == AMM_OK)
       st = amm_decompose(it.B, it.n, it.p, it.ldb, (amm_dtype_t)it.dtype, (amm_method_t)it.method, it.k, &it.ob, s, &hb);
     if (st == AMM_OK) st = amm_approx_matmul(ha, hb, it.C, it.ldc, s);
+    if (st == AMM_OK && it.dC)
+      st = amm_approx_matmul_backward(ha, hb, it.dC, it.lddc, it.dA, it.ldda, it.dB, it.lddb, s);
     if (ha) amm_handle_destroy(ha);
     if (hb) amm_handle_destroy(hb);
   }

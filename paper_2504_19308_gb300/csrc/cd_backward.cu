@@ -45,7 +45,8 @@ cudaError_t cd_sddmm(int n, const float2* Xh, const float2* Yh, const int32_t* l
                      float2* K, const int32_t* gate0, const int32_t* gate1, cudaStream_t st) {
   // work per listed component (those with t <= n/2 are formed, about half): n dot products of
   // length n, 8 FLOP per complex MAC
-  AMM_TRACE_W("cd_sddmm", st, 4.0 * n * (double)n, 0.0, count);
+  const bool tiled = n >= 2 * SDT_W && (int64_t)cap * 12 >= n;  // the variant BwOps<N>::sddmm launches
+  AMM_TRACE_W(tiled ? "cd_sddmm_tiled" : "cd_sddmm", st, 4.0 * n * (double)n, 0.0, count);
   AMM_BW_DISPATCH(n, return BwOps<NN>::sddmm(Xh, Yh, list, count, cap, K, gate0, gate1, st));
   return cd_sddmm_r3(n, Xh, Yh, list, count, cap, K, gate0, gate1, st);
 }

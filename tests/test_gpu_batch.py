@@ -116,3 +116,50 @@ def test_batch_items_match_oracle():
             err = rel(C.double().cpu().numpy(), ref)
             assert err <= tol, (A.shape[0], method, str(A.dtype), use_graph, err)
     batch.close()
+
+
+def test_batch_backward_items_match_single_calls_and_oracle():
+    """Items added with their backward (amm_batch_add_grad) write the gradients of the frozen map:
+    bit for bit those of amm_approx_matmul_backward on the same decompositions, and the oracle's
+    gradients within 1e-5, eager and replayed from the graph."""
+    torch, amm = torch_cuda()
+    spec = [(128, "circulant"), (96, "svd"), (256, "cycle"), (192, "fourier"), (512, "circulant")]
+    items, refs = [], []
+    for i, (n, method) in enumerate(spec):
+        k = max(2, n // 32)
+        a, b = S.exp32_pair(n, seed=300 + i)
+        A, B = dev32(torch, a), dev32(torch, b)
+        G = dev32(torch, S.upstream_grad(n, n, 300 + i))
+        sa = dev32(torch, S.sketch(n, k, 300 + i, 0)) if method == "svd" else None
+        sb = dev32(torch, S.sketch(n, k, 300 + i, 1)) if method == "svd" else None
+        hA = amm.decompose(A, method, k, "left", sketch=sa)
+        hB = amm.decompose(B, method, k, "right", sketch=sb)
+        C1 = amm.approx_matmul(hA, hB).clone()
+        dA1, dB1 = amm.approx_matmul_backward(hA, hB, G)
+        a64, b64, g64 = as64(A), as64(B), as64(G)
+        if method == "svd":
+            ta, tb = O.truncate_rsvd(a64, k, as64(sa)), O.truncate_rsvd(b64, k, as64(sb))
+        elif method == "fourier":
+            ta = O.truncate_fourier_left(a64, k, hA.selection())
+            tb = O.truncate_fourier_right(b64, k, hB.selection())
+        else:
+            ta = O.truncate(method, a64, k, selection=hA.selection())
+            tb = O.truncate(method, b64, k, selection=hB.selection())
+        rda, rdb = O.backward(method, ta, tb, g64)
+        assert rel(dA1.double().cpu().numpy(), rda) <= TOL and rel(dB1.double().cpu().numpy(), rdb) <= TOL
+        refs.append((C1, dA1.clone(), dB1.clone()))
+        items.append((A, B, torch.empty_like(A), method, k, sa, sb, G, torch.empty_like(A), torch.empty_like(B)))
+        hA.close()
+        hB.close()
+    batch = amm.Batch()
+    for A, B, C, method, k, sa, sb, G, dA, dB in items:
+        batch.add(A, B, C, method, k, sketch_a=sa, sketch_b=sb, dC=G, dA=dA, dB=dB)
+    for use_graph in (False, True, True):
+        for it in items:
+            for t in (it[2], it[8], it[9]):
+                t.fill_(float("nan"))
+        batch.run(use_graph=use_graph)
+        torch.cuda.synchronize()
+        for it, (C1, dA1, dB1) in zip(items, refs):
+            assert torch.equal(it[2], C1) and torch.equal(it[8], dA1) and torch.equal(it[9], dB1), (it[3], use_graph)
+    batch.close()
