@@ -210,11 +210,14 @@ __global__ void __launch_bounds__(256) ft_t1_kernel(const float2* __restrict__ A
 }
 
 // ============================================================================ T2 = Re((A~ - A~_a) B~_a)
-// CTA: CB columns x 256 rows; thread per row i, CB accumulators; A~(i, q) read from At^T.
-// maskT NULL: nothing of A~ is excluded (the dense left operand of a mixed product).  IMAG: the
-// imaginary part instead of the real part.
+// CTA: CB columns x 512 rows; a thread takes rows i, i + 1 (one 16-byte load of A~^T(q, i..i+1)
+// per kept entry when m is even) with CB accumulators each; A~(i, q) read from At^T.  Entries kept
+// in A~_a are zeroed after the load (no branch between the mask and the operand load, so the
+// loads of consecutive kept entries stay in flight together).  maskT NULL: nothing of A~ is
+// excluded (the dense left operand of a mixed product).  IMAG: the imaginary part instead of the
+// real part.
 constexpr int T2_CB = 8;
-template <bool IMAG>
+template <bool IMAG, bool VEC>
 __global__ void __launch_bounds__(256) ft_t2_kernel(const float2* __restrict__ AtT, const uint32_t* __restrict__ maskT,
                                                     int mask_words, const int32_t* __restrict__ selB, int k,
                                                     const float2* __restrict__ Bt, int n, int m, int p,
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(256) ft_t2_kernel(const float2* __restrict__ A
   int32_t* qs = reinterpret_cast<int32_t*>(sm);                   // CB x k
   float2* bs = reinterpret_cast<float2*>(qs + T2_CB * k + (T2_CB * k & 1));
   const int c0 = blockIdx.x * T2_CB;
-  const int i = blockIdx.y * 256 + threadIdx.x;
+  const int i = 2 * (blockIdx.y * 256 + threadIdx.x);
   for (int e = threadIdx.x; e < T2_CB * k; e += 256) {
     const int cc = e / k, c = c0 + cc;
     int q = 0;
@@ -239,29 +242,61 @@ __global__ void __launch_bounds__(256) ft_t2_kernel(const float2* __restrict__ A
   }
   __syncthreads();
   if (i >= m) return;
-  float acc[T2_CB];
+  const bool two = i + 1 < m;
+  float acc0[T2_CB], acc1[T2_CB];
 #pragma unroll
-  for (int cc = 0; cc < T2_CB; ++cc) acc[cc] = 0.f;
+  for (int cc = 0; cc < T2_CB; ++cc) acc0[cc] = acc1[cc] = 0.f;
 #pragma unroll
   for (int cc = 0; cc < T2_CB; ++cc) {
-#pragma unroll 8
+#pragma unroll 4
     for (int u = 0; u < k; ++u) {
       const int q = qs[cc * k + u];
-      if (maskT != nullptr) {
-        const uint32_t w = __ldg(maskT + (int64_t)q * mask_words + (i >> 5));
-        if ((w >> (i & 31)) & 1u) continue;  // (i, q) kept in A~_a: not part of the residue
-      }
       const bool mir = q > n / 2;
-      float2 a = __ldg(AtT + (int64_t)(mir ? n - q : q) * m + i);
-      if (mir) a.y = -a.y;
+      const float2* row = AtT + (int64_t)(mir ? n - q : q) * m + i;
+      float2 a0, a1;
+      if (VEC) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(row));
+        a0 = make_float2(a.x, a.y);
+        a1 = make_float2(a.z, a.w);
+      } else {
+        a0 = __ldg(row);
+        a1 = two ? __ldg(row + 1) : make_float2(0.f, 0.f);
+      }
+      if (mir) { a0.y = -a0.y; a1.y = -a1.y; }
+      if (maskT != nullptr) {  // (i, q) kept in A~_a: not part of the residue
+        const uint32_t w = __ldg(maskT + (int64_t)q * mask_words + (i >> 5));
+        if ((w >> (i & 31)) & 1u) a0 = make_float2(0.f, 0.f);
+        if ((w >> ((i + 1) & 31)) & 1u) a1 = make_float2(0.f, 0.f);
+      }
       const float2 b = bs[cc * k + u];
-      if (IMAG) acc[cc] = fmaf(a.x, b.y, fmaf(a.y, b.x, acc[cc]));
-      else acc[cc] = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc[cc]));
+      if (IMAG) {
+        acc0[cc] = fmaf(a0.x, b.y, fmaf(a0.y, b.x, acc0[cc]));
+        acc1[cc] = fmaf(a1.x, b.y, fmaf(a1.y, b.x, acc1[cc]));
+      } else {
+        acc0[cc] = fmaf(a0.x, b.x, fmaf(-a0.y, b.y, acc0[cc]));
+        acc1[cc] = fmaf(a1.x, b.x, fmaf(-a1.y, b.y, acc1[cc]));
+      }
     }
   }
 #pragma unroll
-  for (int cc = 0; cc < T2_CB; ++cc)
-    if (c0 + cc < p) C[(int64_t)i * ldc + c0 + cc] += acc[cc];
+  for (int cc = 0; cc < T2_CB; ++cc) {
+    if (c0 + cc < p) {
+      C[(int64_t)i * ldc + c0 + cc] += acc0[cc];
+      if (two) C[(int64_t)(i + 1) * ldc + c0 + cc] += acc1[cc];
+    }
+  }
+}
+
+// T2 launch: rows in pairs (512 per CTA), the 16-byte form when every A~^T row starts 16-byte aligned
+template <bool IMAG>
+static void ft_t2_launch(const float2* AtT, const uint32_t* maskT, int mask_words, const int32_t* selB, int k,
+                         const float2* Bt, int n, int m, int p, float* C, int64_t ldc, cudaStream_t st) {
+  dim3 grid((p + T2_CB - 1) / T2_CB, (m + 511) / 512);
+  const size_t sm = (size_t)T2_CB * k * (4 + 8) + 8;
+  if ((m % 2) == 0 && (reinterpret_cast<uintptr_t>(AtT) & 15) == 0)
+    ft_t2_kernel<IMAG, true><<<grid, 256, sm, st>>>(AtT, maskT, mask_words, selB, k, Bt, n, m, p, C, ldc);
+  else
+    ft_t2_kernel<IMAG, false><<<grid, 256, sm, st>>>(AtT, maskT, mask_words, selB, k, Bt, n, m, p, C, ldc);
 }
 
 // ============================================================================ launchers
@@ -348,9 +383,7 @@ cudaError_t ft_product(int n, int m, int p, int k_a, int k_b, const float2* At, 
   if (e != cudaSuccess) return e;
   {
     AMM_TRACE_W("ft_t2", st, 8.0 * m * (double)p * k_b, 12.0 * m * (double)p * k_b + 8.0 * m * p, nullptr);
-    dim3 grid((p + T2_CB - 1) / T2_CB, (m + 255) / 256);
-    size_t sm = (size_t)T2_CB * k_b * (4 + 8) + 8;
-    ft_t2_kernel<false><<<grid, 256, sm, st>>>(AtT, maskT, mask_words, selB, k_b, Bt, n, m, p, C, ldc);
+    ft_t2_launch<false>(AtT, maskT, mask_words, selB, k_b, Bt, n, m, p, C, ldc, st);
   }
   return cudaGetLastError();
 }
@@ -521,10 +554,8 @@ cudaError_t ft_right_apply(int n, int p, const float2* Bt, const int32_t* selB, 
   if (e == cudaSuccess) {
     AMM_TRACE_W(imag ? "ft_t2_imag" : "ft_t2", st, 8.0 * m * (double)p * kb, 12.0 * m * (double)p * kb + 8.0 * m * p,
                 nullptr);
-    dim3 grid((p + T2_CB - 1) / T2_CB, (m + 255) / 256);
-    const size_t sm = (size_t)T2_CB * kb * (4 + 8) + 8;
-    if (imag) ft_t2_kernel<true><<<grid, 256, sm, st>>>(YtT, nullptr, 0, selB, kb, Bt, n, m, p, C, ldc);
-    else ft_t2_kernel<false><<<grid, 256, sm, st>>>(YtT, nullptr, 0, selB, kb, Bt, n, m, p, C, ldc);
+    if (imag) ft_t2_launch<true>(YtT, nullptr, 0, selB, kb, Bt, n, m, p, C, ldc, st);
+    else ft_t2_launch<false>(YtT, nullptr, 0, selB, kb, Bt, n, m, p, C, ldc, st);
     e = cudaGetLastError();
   }
   dev_free(Yt, st);

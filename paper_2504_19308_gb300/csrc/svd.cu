@@ -422,6 +422,140 @@ __global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const float* __
   }
 }
 
+// ============================================================================ Cholesky for 160 < kp <= 256
+// The two work arrays of chol_inv_kernel do not fit in shared memory beyond kp = 160, and in
+// global memory one CTA waits on every access.  Here the factorisation keeps only the lower
+// triangle, packed (row i at i (i + 1) / 2: 132 KB at kp = 256), in one CTA with the same blocked
+// steps as above, and writes L to global memory; the inverse is then formed by one CTA per
+// 32-column block J by blocked forward substitution, X_I = L_II^{-1} (E_IJ - sum_{J <= K < I} L_IK X_K)
+// for I = J, J + 1, ... (E the identity), with its column block X in shared memory.
+constexpr int CHOL_PACKED_K = 256;
+__host__ __device__ constexpr size_t chol_packed_floats(int kp) { return (size_t)kp * (kp + 1) / 2; }
+AMM_DEV int tri(int i) { return i * (i + 1) / 2; }
+
+__global__ void __launch_bounds__(CHOL_T) chol_factor_packed_kernel(int k, const float* __restrict__ G, float shift_rel,
+                                                                   float* __restrict__ L) {
+  extern __shared__ float W[];  // packed lower triangle of G + sI, then of L
+  const int kp = chol_kp(k), nb = kp / 32;
+  __shared__ float red[32];
+  __shared__ float shift_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float tr = 0.f;
+  for (int i = tid; i < k; i += CHOL_T) tr += G[(int64_t)i * k + i];
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if (lane == 0) red[warp] = tr;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < CHOL_T / 32; ++w) t += red[w];
+    shift_s = fmaxf(shift_rel * t, 1e-30f);
+  }
+  __syncthreads();
+  const float shift = shift_s;
+  for (int i = warp; i < kp; i += CHOL_T / 32)
+    for (int j = lane; j <= i; j += 32)
+      W[tri(i) + j] = (i < k && j < k) ? G[(int64_t)i * k + j] + (i == j ? shift : 0.f) : (i == j ? 1.f : 0.f);
+  __syncthreads();
+  for (int J = 0; J < nb; ++J) {
+    const int j0 = 32 * J;
+    if (warp == 0) {  // diagonal tile, lane r holds row j0 + r
+      float a[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) a[c] = (c <= lane) ? W[tri(j0 + lane) + j0 + c] : 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float d = sqrtf(fmaxf(__shfl_sync(0xffffffffu, a[c], c), shift));
+        const float rd = 1.f / d;
+        if (lane == c) a[c] = d;
+        else if (lane > c) a[c] *= rd;
+        const float lrc = a[c];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) {
+          if (l > c) {
+            const float llc = __shfl_sync(0xffffffffu, a[c], l);
+            if (lane >= l) a[l] = fmaf(-lrc, llc, a[l]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c <= lane) W[tri(j0 + lane) + j0 + c] = a[c];
+    }
+    __syncthreads();
+    for (int i = j0 + 32 + tid; i < kp; i += CHOL_T) {  // panel: x L_JJ^T = a, a thread per row
+      float* wr = W + tri(i) + j0;
+      float x[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float* lc = W + tri(j0 + c) + j0;
+        float v = wr[c];
+#pragma unroll
+        for (int l = 0; l < c; ++l) v = fmaf(-x[l], lc[l], v);
+        x[c] = v * (1.f / lc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) wr[c] = x[c];
+    }
+    __syncthreads();
+    const int t0 = j0 + 32, m = kp - t0;
+    for (int e = tid; e < m * m; e += CHOL_T) {  // trailing update of the lower triangle
+      const int i = t0 + e / m, l = t0 + e % m;
+      if (l > i) continue;
+      const float* ri = W + tri(i) + j0;
+      const float* rl = W + tri(l) + j0;
+      float v = W[tri(i) + l];
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) v = fmaf(-ri[c], rl[c], v);
+      W[tri(i) + l] = v;
+    }
+    __syncthreads();
+  }
+  for (int i = warp; i < kp; i += CHOL_T / 32)
+    for (int j = lane; j < kp; j += 32) L[(int64_t)i * kp + j] = j <= i ? W[tri(i) + j] : 0.f;
+}
+
+// CTA J: columns 32 J .. 32 J + 31 of L^{-1} (kp x kp, L from chol_factor_packed_kernel), written to
+// Linv (k x k, row-major, the leading k rows / columns).  256 threads.
+constexpr int TRINV_T = 256;
+__global__ void __launch_bounds__(TRINV_T) chol_trinv_kernel(int k, const float* __restrict__ L,
+                                                            float* __restrict__ Linv) {
+  const int kp = chol_kp(k), nb = kp / 32, J = blockIdx.x, j0 = 32 * J;
+  __shared__ float X[CHOL_PACKED_K][33];  // rows j0.. of the column block (row i at X[i - j0])
+  __shared__ float Lt[32][33];            // the diagonal tile L_II
+  __shared__ float T[32][33];             // right-hand side of the tile solve
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int I = J; I < nb; ++I) {
+    const int i0 = 32 * I;
+    for (int e = tid; e < 1024; e += TRINV_T) {
+      const int r = e >> 5, c = e & 31;
+      Lt[r][c] = L[(int64_t)(i0 + r) * kp + i0 + c];
+      // T = E_IJ - sum_{J <= K < I} L_IK X_K (row r, column c)
+      const float* lrow = L + (int64_t)(i0 + r) * kp;
+      float s = (I == J && r == c) ? 1.f : 0.f;
+      for (int q = j0; q < i0; ++q) s = fmaf(-__ldg(lrow + q), X[q - j0][c], s);
+      T[r][c] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {  // L_II X_I = T by forward substitution, lane c holds column c
+      float x[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        float v = T[r][lane];
+#pragma unroll
+        for (int l = 0; l < r; ++l) v = fmaf(-Lt[r][l], x[l], v);
+        x[r] = v / Lt[r][r];
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) X[i0 - j0 + r][lane] = x[r];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < k * 32; e += TRINV_T) {
+    const int i = e >> 5, c = j0 + (e & 31);
+    if (c < k) Linv[(int64_t)i * k + c] = i >= j0 ? X[i - j0][e & 31] : 0.f;
+  }
+}
+
 // ============================================================================ Philox sketch
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011) keyed by the seed, counter = element
 // group; Box-Muller turns each pair of uniforms into two N(0,1) draws.
@@ -511,14 +645,31 @@ static cudaError_t sumsq(const T* X, int64_t rows, int64_t cols, int64_t ld, dou
   return e;
 }
 
-// W: global work area of at least chol_floats(k) floats (used when chol_kp(k) > CHOL_SMEM_K)
+// W: global work area of at least chol_floats(k) floats (used when chol_kp(k) > CHOL_SMEM_K; for
+// kp <= CHOL_PACKED_K it holds L between the factorisation and the inverse)
 static cudaError_t chol_inv(int k, const float* G, float shift_rel, float* W, float* Li, cudaStream_t st) {
   static DeviceOnce once;
   const cudaError_t attr = once([] {
-    return cudaFuncSetAttribute((const void*)chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(chol_floats(CHOL_SMEM_K) * sizeof(float)));
+    cudaError_t e = cudaFuncSetAttribute((const void*)chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(chol_floats(CHOL_SMEM_K) * sizeof(float)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)chol_factor_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(chol_packed_floats(CHOL_PACKED_K) * sizeof(float)));
+    return e;
   });
   if (attr != cudaSuccess) return attr;
+  const int kp = chol_kp(k);
+  if (kp > CHOL_SMEM_K && kp <= CHOL_PACKED_K) {
+    {
+      AMM_TRACE_W("chol_factor", st, (double)k * k * k / 3.0 * 2.0, 0.0, nullptr);
+      chol_factor_packed_kernel<<<1, CHOL_T, sizeof(float) * chol_packed_floats(kp), st>>>(k, G, shift_rel, W);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    AMM_TRACE_W("chol_trinv", st, (double)k * k * k / 3.0 * 2.0, 0.0, nullptr);
+    chol_trinv_kernel<<<kp / 32, TRINV_T, 0, st>>>(k, W, Li);
+    return cudaGetLastError();
+  }
   AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0 * 2.0, 0.0, nullptr);
   const size_t sm = chol_kp(k) <= CHOL_SMEM_K ? sizeof(float) * chol_floats(k) : 0;
   chol_inv_kernel<<<1, CHOL_T, sm, st>>>(k, G, shift_rel, Li, W);
