@@ -36,11 +36,9 @@ __device__ __forceinline__ float2 half_spec(const float2* __restrict__ T, int n,
 //   G B~_a^T :  D = G^T [p][m], T = B~ [n/2+1][p], mask = B~_a bits  -> XAT[q][i]
 //   A~_a^T G :  D = G [m][p],   T = A~^T [n/2+1][m], mask = A~_a bits -> XB[q][c]
 // CTA per (q, 1024 outputs): the mask row is compacted in shared memory chunk by chunk (index and
-// coefficient per set bit), then every thread streams the selected rows of D for its 4 consecutive
-// outputs (one 16-byte load per row when VEC).
+// coefficient per set bit), then every thread streams the selected rows of D for its 4 outputs.
 constexpr int MW_CHUNK = 64;  // mask words per chunk (2048 bits)
 constexpr int MW_RPT = 4;     // outputs per thread
-template <bool VEC>
 __global__ void __launch_bounds__(256) ft_bw_maskwalk_kernel(const float* __restrict__ D, int64_t ldd, int nout,
                                                              const float2* __restrict__ T, int64_t ldt,
                                                              const uint32_t* __restrict__ mask, int mw, int n,
@@ -49,7 +47,7 @@ __global__ void __launch_bounds__(256) ft_bw_maskwalk_kernel(const float* __rest
   __shared__ float2 s_val[MW_CHUNK * 32];
   __shared__ int32_t s_off[MW_CHUNK + 1];
   const int q = blockIdx.y;
-  const int v0 = blockIdx.x * (256 * MW_RPT) + MW_RPT * threadIdx.x;
+  const int v0 = blockIdx.x * (256 * MW_RPT) + threadIdx.x;
   const uint32_t* mrow = mask + (int64_t)q * mw;
   float2 acc[MW_RPT];
 #pragma unroll
@@ -85,24 +83,17 @@ __global__ void __launch_bounds__(256) ft_bw_maskwalk_kernel(const float* __rest
     }
     __syncthreads();
     const int cnt = s_off[MW_CHUNK];
-    if (v0 < nout) {
-#pragma unroll 4
-      for (int e = 0; e < cnt; ++e) {
-        const int x = s_idx[e];
-        const float2 c = s_val[e];
-        const float* drow = D + (int64_t)x * ldd + v0;
-        float d[MW_RPT];
-        if (VEC) {
-          const float4 d4 = __ldg(reinterpret_cast<const float4*>(drow));
-          d[0] = d4.x; d[1] = d4.y; d[2] = d4.z; d[3] = d4.w;
-        } else {
+    for (int e = 0; e < cnt; ++e) {
+      const int x = s_idx[e];
+      const float2 c = s_val[e];
+      const float* drow = D + (int64_t)x * ldd;
 #pragma unroll
-          for (int r = 0; r < MW_RPT; ++r) d[r] = v0 + r < nout ? __ldg(drow + r) : 0.f;
-        }
-#pragma unroll
-        for (int r = 0; r < MW_RPT; ++r) {
-          acc[r].x = fmaf(d[r], c.x, acc[r].x);
-          acc[r].y = fmaf(d[r], c.y, acc[r].y);
+      for (int r = 0; r < MW_RPT; ++r) {
+        const int v = v0 + r * 256;
+        if (v < nout) {
+          const float d = __ldg(drow + v);
+          acc[r].x = fmaf(d, c.x, acc[r].x);
+          acc[r].y = fmaf(d, c.y, acc[r].y);
         }
       }
     }
@@ -110,17 +101,14 @@ __global__ void __launch_bounds__(256) ft_bw_maskwalk_kernel(const float* __rest
   }
 #pragma unroll
   for (int r = 0; r < MW_RPT; ++r) {
-    const int v = v0 + r;
+    const int v = v0 + r * 256;
     if (v < nout) out[(int64_t)q * nout + v] = acc[r];
   }
 }
 
 // ============================================================================ P_A(G dB~^T)
 // For each kept (i, q) of A~_a:  XAT[q][i] += sum_c G(i, c) B~(q, c) [(q, c) not kept in B~_a].
-// CTA per row i (G row shared through L1), warp per kept entry, lanes over c, two consecutive c per
-// lane (one 8-byte load of G and one 16-byte load of B~ when VEC).  Entries kept in B~_a are zeroed
-// after the loads: no branch sits between the mask and the operand loads.
-template <bool VEC>
+// CTA per row i (G row shared through L1), warp per kept entry, lanes over c.
 __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__ G, int64_t ldg,
                                                        const float2* __restrict__ Bt, const uint32_t* __restrict__ maskB,
                                                        int mwB, const int32_t* __restrict__ selA, int ka, int n, int m,
@@ -134,24 +122,12 @@ __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__
     const float2* brow = Bt + (int64_t)(mir ? n - q : q) * p;
     const uint32_t* mrow = maskB + (int64_t)q * mwB;
     float ax = 0.f, ay = 0.f;
-#pragma unroll 4
-    for (int c = 2 * lane; c < p; c += 64) {
-      float2 g, b0, b1;
-      if (VEC) {
-        g = __ldg(reinterpret_cast<const float2*>(grow + c));
-        const float4 b = __ldg(reinterpret_cast<const float4*>(brow + c));
-        b0 = make_float2(b.x, b.y);
-        b1 = make_float2(b.z, b.w);
-      } else {
-        g = make_float2(__ldg(grow + c), c + 1 < p ? __ldg(grow + c + 1) : 0.f);
-        b0 = __ldg(brow + c);
-        b1 = c + 1 < p ? __ldg(brow + c + 1) : make_float2(0.f, 0.f);
-      }
-      const uint32_t w = __ldg(mrow + (c >> 5));
-      if ((w >> (c & 31)) & 1u) g.x = 0.f;          // kept in B~_a: not in dB~
-      if ((w >> ((c + 1) & 31)) & 1u) g.y = 0.f;
-      ax = fmaf(g.x, b0.x, fmaf(g.y, b1.x, ax));
-      ay = fmaf(g.x, b0.y, fmaf(g.y, b1.y, ay));
+    for (int c = lane; c < p; c += 32) {
+      if ((__ldg(mrow + (c >> 5)) >> (c & 31)) & 1u) continue;  // kept in B~_a: not in dB~
+      const float g = __ldg(grow + c);
+      const float2 b = __ldg(brow + c);
+      ax = fmaf(g, b.x, ax);
+      ay = fmaf(g, b.y, ay);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -168,9 +144,7 @@ __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__
 
 // ============================================================================ P_B(dA~^T G)
 // For each kept (q, c) of B~_a:  XB[q][c] += sum_i A~(i, q) [(i, q) not kept in A~_a] G(i, c).
-// CTA per column c (GT row shared through L1), warp per kept entry, lanes over i, two consecutive
-// i per lane; masked entries zeroed after the loads as above.
-template <bool VEC>
+// CTA per column c (GT row shared through L1), warp per kept entry, lanes over i.
 __global__ void __launch_bounds__(256) ft_bw_pb_kernel(const float* __restrict__ GT, const float2* __restrict__ AtT,
                                                        const uint32_t* __restrict__ maskA, int mwA,
                                                        const int32_t* __restrict__ selB, int kb, int n, int m, int p,
@@ -184,24 +158,12 @@ __global__ void __launch_bounds__(256) ft_bw_pb_kernel(const float* __restrict__
     const float2* arow = AtT + (int64_t)(mir ? n - q : q) * m;
     const uint32_t* mrow = maskA + (int64_t)q * mwA;
     float ax = 0.f, ay = 0.f;
-#pragma unroll 4
-    for (int i = 2 * lane; i < m; i += 64) {
-      float2 g, a0, a1;
-      if (VEC) {
-        g = __ldg(reinterpret_cast<const float2*>(grow + i));
-        const float4 a = __ldg(reinterpret_cast<const float4*>(arow + i));
-        a0 = make_float2(a.x, a.y);
-        a1 = make_float2(a.z, a.w);
-      } else {
-        g = make_float2(__ldg(grow + i), i + 1 < m ? __ldg(grow + i + 1) : 0.f);
-        a0 = __ldg(arow + i);
-        a1 = i + 1 < m ? __ldg(arow + i + 1) : make_float2(0.f, 0.f);
-      }
-      const uint32_t w = __ldg(mrow + (i >> 5));
-      if ((w >> (i & 31)) & 1u) g.x = 0.f;          // kept in A~_a: not in dA~
-      if ((w >> ((i + 1) & 31)) & 1u) g.y = 0.f;
-      ax = fmaf(g.x, a0.x, fmaf(g.y, a1.x, ax));
-      ay = fmaf(g.x, a0.y, fmaf(g.y, a1.y, ay));
+    for (int i = lane; i < m; i += 32) {
+      if ((__ldg(mrow + (i >> 5)) >> (i & 31)) & 1u) continue;  // kept in A~_a: not in dA~
+      const float g = __ldg(grow + i);
+      const float2 a = __ldg(arow + i);
+      ax = fmaf(g, a.x, ax);
+      ay = fmaf(g, a.y, ay);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -313,12 +275,6 @@ static cudaError_t ft_bw_real(int n, bool inv, const float2* X, int nvec, const 
   AMM_FTB_DISPATCH(n, return FtBwOps<NN>::fwd_cols(X, nvec, tw, out, ldo, st));
 }
 
-// rows of D (leading dimension ldd) read 4 floats at a time from a multiple of 4: every row start
-// 16-byte aligned and the row length a multiple of 4
-static bool vec4(const float* D, int64_t ldd, int nout) {
-  return ((uintptr_t)D & 15) == 0 && ldd % 4 == 0 && nout % 4 == 0;
-}
-
 cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
   const int n = a.n, m = a.m, p = a.p;
   const int mwA = (m + 31) / 32, mwB = (p + 31) / 32;
@@ -332,17 +288,13 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
   if (e == cudaSuccess && a.dA) {
     {
       AMM_TRACE_W("ft_bw_gba", st, 4.0 * p * (double)a.kb * m, 4.0 * p * (double)a.kb * m + 8.0 * n * m, nullptr);
-      const dim3 grid((m + 256 * MW_RPT - 1) / (256 * MW_RPT), n);
-      if (vec4(GT, m, m)) ft_bw_maskwalk_kernel<true><<<grid, 256, 0, st>>>(GT, m, m, a.Bt, p, a.maskB, mwB, n, XAT);
-      else ft_bw_maskwalk_kernel<false><<<grid, 256, 0, st>>>(GT, m, m, a.Bt, p, a.maskB, mwB, n, XAT);
+      ft_bw_maskwalk_kernel<<<dim3((m + 256 * MW_RPT - 1) / (256 * MW_RPT), n), 256, 0, st>>>(
+          GT, m, m, a.Bt, p, a.maskB, mwB, n, XAT);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
       AMM_TRACE_W("ft_bw_pa", st, 4.0 * m * (double)a.ka * p, 12.0 * m * (double)a.ka * p, nullptr);
-      if (p % 2 == 0 && a.ldg % 2 == 0 && ((uintptr_t)a.G & 7) == 0 && ((uintptr_t)a.Bt & 15) == 0)
-        ft_bw_pa_kernel<true><<<m, 256, 0, st>>>(a.G, a.ldg, a.Bt, a.maskB, mwB, a.selA, a.ka, n, m, p, XAT);
-      else
-        ft_bw_pa_kernel<false><<<m, 256, 0, st>>>(a.G, a.ldg, a.Bt, a.maskB, mwB, a.selA, a.ka, n, m, p, XAT);
+      ft_bw_pa_kernel<<<m, 256, 0, st>>>(a.G, a.ldg, a.Bt, a.maskB, mwB, a.selA, a.ka, n, m, p, XAT);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = ft_bw_real(n, true, XAT, m, a.tw, a.dA, a.ldda, st);
@@ -350,17 +302,13 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
   if (e == cudaSuccess && a.dB) {
     {
       AMM_TRACE_W("ft_bw_aag", st, 4.0 * m * (double)a.ka * p, 4.0 * m * (double)a.ka * p + 8.0 * n * p, nullptr);
-      const dim3 grid((p + 256 * MW_RPT - 1) / (256 * MW_RPT), n);
-      if (vec4(a.G, a.ldg, p)) ft_bw_maskwalk_kernel<true><<<grid, 256, 0, st>>>(a.G, a.ldg, p, a.AtT, m, a.maskA, mwA, n, XB);
-      else ft_bw_maskwalk_kernel<false><<<grid, 256, 0, st>>>(a.G, a.ldg, p, a.AtT, m, a.maskA, mwA, n, XB);
+      ft_bw_maskwalk_kernel<<<dim3((p + 256 * MW_RPT - 1) / (256 * MW_RPT), n), 256, 0, st>>>(
+          a.G, a.ldg, p, a.AtT, m, a.maskA, mwA, n, XB);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
       AMM_TRACE_W("ft_bw_pb", st, 4.0 * p * (double)a.kb * m, 12.0 * p * (double)a.kb * m, nullptr);
-      if (m % 2 == 0 && ((uintptr_t)a.AtT & 15) == 0)
-        ft_bw_pb_kernel<true><<<p, 256, 0, st>>>(GT, a.AtT, a.maskA, mwA, a.selB, a.kb, n, m, p, XB);
-      else
-        ft_bw_pb_kernel<false><<<p, 256, 0, st>>>(GT, a.AtT, a.maskA, mwA, a.selB, a.kb, n, m, p, XB);
+      ft_bw_pb_kernel<<<p, 256, 0, st>>>(GT, a.AtT, a.maskA, mwA, a.selB, a.kb, n, m, p, XB);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = ft_bw_real(n, false, XB, p, a.tw, a.dB, a.lddb, st);

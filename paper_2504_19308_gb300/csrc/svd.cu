@@ -289,6 +289,44 @@ static cudaError_t gram_dot2(int64_t m, int k, const float* X, float* G, cudaStr
 // arrays live in a global work area of 2 kp (kp + 1) floats.
 constexpr int CHOL_SMEM_K = 160;
 constexpr int CHOL_T = 512;
+
+// Trailing update of a blocked Cholesky step: W(i, l) -= sum_{c < 32} W(i, j0 + c) W(l, j0 + c) for
+// j0 + 32 <= l <= i < kp (idx(i, j) locates element (i, j)).  Each thread takes 4 x 4 blocks of the
+// lower triangle, so a pair of loads feeds four FMAs instead of one.
+template <class IDX>
+AMM_DEV void chol_trailing(float* W, IDX idx, int j0, int kp) {
+  const int t0 = j0 + 32, mb = (kp - t0) / 4;
+  const int nblk = mb * (mb + 1) / 2;
+  for (int b = threadIdx.x; b < nblk; b += CHOL_T) {
+    int bi = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);  // b -> block (bi, bl), bl <= bi
+    while (bi * (bi + 1) / 2 > b) --bi;
+    while ((bi + 1) * (bi + 2) / 2 <= b) ++bi;
+    const int bl = b - bi * (bi + 1) / 2;
+    const int i0 = t0 + 4 * bi, l0 = t0 + 4 * bl;
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) {
+      float a[4], bb[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = W[idx(i0 + r, j0 + c)];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bb[q] = W[idx(l0 + q, j0 + c)];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(a[r], bb[q], acc[r][q]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (l0 + q <= i0 + r) W[idx(i0 + r, l0 + q)] -= acc[r][q];
+  }
+}
 __host__ __device__ constexpr int chol_kp(int k) { return (k + 31) & ~31; }
 __host__ __device__ constexpr size_t chol_floats(int k) { return 2 * (size_t)chol_kp(k) * (chol_kp(k) + 1); }
 
@@ -363,18 +401,7 @@ __global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const float* __
       for (int c = 0; c < 32; ++c) wr[c] = x[c];
     }
     __syncthreads();
-    // trailing update of the lower triangle
-    const int t0 = j0 + 32, m = kp - t0;
-    for (int e = tid; e < m * m; e += CHOL_T) {
-      const int i = t0 + e / m, l = t0 + e % m;
-      if (l > i) continue;
-      const float* ri = W + i * ldw + j0;
-      const float* rl = W + l * ldw + j0;
-      float v = W[i * ldw + l];
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c) v = fmaf(-ri[c], rl[c], v);
-      W[i * ldw + l] = v;
-    }
+    chol_trailing(W, [ldw](int i, int j) { return i * ldw + j; }, j0, kp);  // trailing lower triangle
     __syncthreads();
   }
   // inverse of every diagonal tile: lane c holds column c
@@ -497,17 +524,7 @@ __global__ void __launch_bounds__(CHOL_T) chol_factor_packed_kernel(int k, const
       for (int c = 0; c < 32; ++c) wr[c] = x[c];
     }
     __syncthreads();
-    const int t0 = j0 + 32, m = kp - t0;
-    for (int e = tid; e < m * m; e += CHOL_T) {  // trailing update of the lower triangle
-      const int i = t0 + e / m, l = t0 + e % m;
-      if (l > i) continue;
-      const float* ri = W + tri(i) + j0;
-      const float* rl = W + tri(l) + j0;
-      float v = W[tri(i) + l];
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c) v = fmaf(-ri[c], rl[c], v);
-      W[tri(i) + l] = v;
-    }
+    chol_trailing(W, [](int i, int j) { return tri(i) + j; }, j0, kp);  // trailing lower triangle
     __syncthreads();
   }
   for (int i = warp; i < kp; i += CHOL_T / 32)
@@ -515,44 +532,73 @@ __global__ void __launch_bounds__(CHOL_T) chol_factor_packed_kernel(int k, const
 }
 
 // CTA J: columns 32 J .. 32 J + 31 of L^{-1} (kp x kp, L from chol_factor_packed_kernel), written to
-// Linv (k x k, row-major, the leading k rows / columns).  256 threads.
+// Linv (k x k, row-major, the leading k rows / columns).  256 threads.  For each block row I the
+// rows i0 .. i0 + 31 of L, columns j0 .. i0 + 31, are first copied to shared memory (coalesced),
+// then T = E_IJ - sum_K L_IK X_K is formed there (a thread takes four consecutive columns of one
+// row) and warp 0 solves L_II X_I = T.
 constexpr int TRINV_T = 256;
+constexpr int TRINV_LDX = 36;                       // X row stride (16-byte rows)
+constexpr int TRINV_LDL = CHOL_PACKED_K + 1;        // staged L row stride (odd: conflict-free rows)
+constexpr size_t TRINV_SMEM = sizeof(float) * ((size_t)CHOL_PACKED_K * TRINV_LDX + 32 * TRINV_LDL + 32 * 33);
 __global__ void __launch_bounds__(TRINV_T) chol_trinv_kernel(int k, const float* __restrict__ L,
                                                             float* __restrict__ Linv) {
+  extern __shared__ float sm_trinv[];
+  float* X = sm_trinv;                              // rows j0.. of the column block, [i - j0][c]
+  float* Lr = X + CHOL_PACKED_K * TRINV_LDX;        // staged block row of L, [r][q - j0]
+  float* T = Lr + 32 * TRINV_LDL;                   // right-hand side of the tile solve, [r][c]
   const int kp = chol_kp(k), nb = kp / 32, J = blockIdx.x, j0 = 32 * J;
-  __shared__ float X[CHOL_PACKED_K][33];  // rows j0.. of the column block (row i at X[i - j0])
-  __shared__ float Lt[32][33];            // the diagonal tile L_II
-  __shared__ float T[32][33];             // right-hand side of the tile solve
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int I = J; I < nb; ++I) {
-    const int i0 = 32 * I;
-    for (int e = tid; e < 1024; e += TRINV_T) {
-      const int r = e >> 5, c = e & 31;
-      Lt[r][c] = L[(int64_t)(i0 + r) * kp + i0 + c];
-      // T = E_IJ - sum_{J <= K < I} L_IK X_K (row r, column c)
-      const float* lrow = L + (int64_t)(i0 + r) * kp;
-      float s = (I == J && r == c) ? 1.f : 0.f;
-      for (int q = j0; q < i0; ++q) s = fmaf(-__ldg(lrow + q), X[q - j0][c], s);
-      T[r][c] = s;
+    const int i0 = 32 * I, w = i0 + 32 - j0;        // staged width: columns j0 .. i0 + 31
+    for (int e = tid; e < 32 * w; e += TRINV_T) {
+      const int r = e / w, q = e - r * w;
+      Lr[r * TRINV_LDL + q] = __ldg(L + (int64_t)(i0 + r) * kp + j0 + q);
+    }
+    __syncthreads();
+    {
+      const int r = tid >> 3, c4 = (tid & 7) * 4;   // row r, columns c4 .. c4 + 3
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      if (I == J) {
+        s0 = (r == c4) ? 1.f : 0.f;
+        s1 = (r == c4 + 1) ? 1.f : 0.f;
+        s2 = (r == c4 + 2) ? 1.f : 0.f;
+        s3 = (r == c4 + 3) ? 1.f : 0.f;
+      }
+      const float* lr = Lr + r * TRINV_LDL;
+#pragma unroll 4
+      for (int q = 0; q < i0 - j0; ++q) {
+        const float a = lr[q];
+        const float4 x = *reinterpret_cast<const float4*>(X + q * TRINV_LDX + c4);
+        s0 = fmaf(-a, x.x, s0);
+        s1 = fmaf(-a, x.y, s1);
+        s2 = fmaf(-a, x.z, s2);
+        s3 = fmaf(-a, x.w, s3);
+      }
+      float* t = T + r * 33 + c4;
+      t[0] = s0;
+      t[1] = s1;
+      t[2] = s2;
+      t[3] = s3;
     }
     __syncthreads();
     if (warp == 0) {  // L_II X_I = T by forward substitution, lane c holds column c
+      const float* lt = Lr + (i0 - j0);             // the diagonal tile L_II: lt[r * TRINV_LDL + l]
       float x[32];
 #pragma unroll
       for (int r = 0; r < 32; ++r) {
-        float v = T[r][lane];
+        float v = T[r * 33 + lane];
 #pragma unroll
-        for (int l = 0; l < r; ++l) v = fmaf(-Lt[r][l], x[l], v);
-        x[r] = v / Lt[r][r];
+        for (int l = 0; l < r; ++l) v = fmaf(-lt[r * TRINV_LDL + l], x[l], v);
+        x[r] = v / lt[r * TRINV_LDL + r];
       }
 #pragma unroll
-      for (int r = 0; r < 32; ++r) X[i0 - j0 + r][lane] = x[r];
+      for (int r = 0; r < 32; ++r) X[(i0 - j0 + r) * TRINV_LDX + lane] = x[r];
     }
     __syncthreads();
   }
   for (int e = tid; e < k * 32; e += TRINV_T) {
     const int i = e >> 5, c = j0 + (e & 31);
-    if (c < k) Linv[(int64_t)i * k + c] = i >= j0 ? X[i - j0][e & 31] : 0.f;
+    if (c < k) Linv[(int64_t)i * k + c] = i >= j0 ? X[(i - j0) * TRINV_LDX + (e & 31)] : 0.f;
   }
 }
 
@@ -655,6 +701,9 @@ static cudaError_t chol_inv(int k, const float* G, float shift_rel, float* W, fl
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute((const void*)chol_factor_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(chol_packed_floats(CHOL_PACKED_K) * sizeof(float)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)chol_trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)TRINV_SMEM);
     return e;
   });
   if (attr != cudaSuccess) return attr;
@@ -667,7 +716,7 @@ static cudaError_t chol_inv(int k, const float* G, float shift_rel, float* W, fl
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     AMM_TRACE_W("chol_trinv", st, (double)k * k * k / 3.0 * 2.0, 0.0, nullptr);
-    chol_trinv_kernel<<<kp / 32, TRINV_T, 0, st>>>(k, W, Li);
+    chol_trinv_kernel<<<kp / 32, TRINV_T, TRINV_SMEM, st>>>(k, W, Li);
     return cudaGetLastError();
   }
   AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0 * 2.0, 0.0, nullptr);

@@ -2,7 +2,9 @@
 //
 //   C[M x N] = alpha * A[M x K] * B[N x K]^T + beta * C        (A, B K-major: row-major along K)
 //
-// One 128 x 128 output tile per CTA.  K may be split over grid.z: every split stores its partial
+// One 128 x BN output tile per CTA, BN = 128, or the smallest of 16 / 32 / 64 that covers N when
+// N is that thin (the sketch and projection GEMMs of Alg. 1 have N = k): the MMAs, the B tiles and,
+// in the TF32X3 mode, the hi / lo split of B then scale with k instead of a fixed 128.  K may be split over grid.z: every split stores its partial
 // tile in a workspace, and a reduction kernel sums the partials in split order (compensated FP32)
 // into C.  (Summing in the last CTA of each tile left one CTA per tile doing all the loads, which
 // measured slower than spreading the sum over the whole GPU.)
@@ -30,6 +32,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "api_internal.h"
 #include "common.cuh"
@@ -38,7 +41,7 @@
 
 namespace amm {
 
-constexpr int UM_BM = 128, UM_BN = 128;
+constexpr int UM_BM = 128;
 constexpr int UM_THREADS = 192;
 constexpr int UM_TF32_MAX_KB = 16;  // longest TF32X3 accumulation chain, in 32-wide k-blocks
 constexpr int UM_CTA_FIXED_KB = 8;  // per-CTA set-up and epilogue cost, in k-blocks (split choice)
@@ -117,6 +120,20 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 32 consecutive accumulator columns of this warp's 32 TMEM lanes
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -139,17 +156,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // BF16 tiles go from the TMA ring straight to the MMAs.  TF32X3 tiles are split into hi/lo by
 // the four epilogue warps, which release the raw stage as soon as it is read, so TMA keeps
 // RAW stages in flight while the MMAs work from the split ring.
-template <bool TF32>
+template <bool TF32, int BN>
 struct UmmaCfg {
+  static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128, "tile widths of the M = 128 MMA used here");
   static constexpr int ELEM = TF32 ? 4 : 2;
   static constexpr int BK = 128 / ELEM;                      // one 128-byte swizzle atom of K
   static constexpr int MMA_K = 32 / ELEM;                    // K per tcgen05.mma
-  static constexpr int TILE_BYTES = UM_BM * 128;             // 16 KiB per operand tile
-  static constexpr int RAW = TF32 ? 3 : 5;                   // TMA stages
-  static constexpr int RAW_BYTES = 2 * TILE_BYTES;           // A, B
-  static constexpr int SLOTS = TF32 ? 2 : 0;                 // split slots
-  static constexpr int SLOT_BYTES = 4 * TILE_BYTES;          // A hi, B hi, A lo, B lo
+  static constexpr int A_BYTES = UM_BM * 128;                // 16 KiB A tile
+  static constexpr int B_BYTES = BN * 128;                   // BN rows of B (a multiple of 1024 bytes)
+  static constexpr int RAW = TF32 ? (BN == 128 ? 3 : 4) : (BN == 128 ? 5 : 7);  // TMA stages
+  static constexpr int RAW_BYTES = A_BYTES + B_BYTES;        // A, B
+  static constexpr int SLOTS = TF32 ? (BN >= 64 ? 2 : 3) : 0;  // split slots
+  static constexpr int SLOT_BYTES = 2 * RAW_BYTES;           // A hi, B hi, A lo, B lo
+  // accumulator columns (TF32X3: main + correction), a power of two >= 32 as tcgen05.alloc requires
+  static constexpr uint32_t TMEM_COLS = (TF32 ? 2 * BN : BN) < 32 ? 32u : (uint32_t)(TF32 ? 2 * BN : BN);
   static constexpr size_t SMEM = 1024 + (size_t)RAW * RAW_BYTES + (size_t)SLOTS * SLOT_BYTES + 256;
+  static_assert(SMEM <= 232448, "dynamic shared memory per CTA");
 };
 
 // Round to the nearest TF32 value (10 fraction bits, ties away from zero); Inf and NaN pass.
@@ -178,12 +200,15 @@ __device__ __forceinline__ void split_tile(const float* raw, float* hi, float* l
   }
 }
 
-template <bool TF32>
+// TRANS: the kernel computes C^T = B A^T (its M, N are the caller's N, M) and stores C itself:
+// element (i, j) of its tile goes to C[j * ldc + i], so a warp's 32 lanes (consecutive i) write 128
+// contiguous bytes per column j; split partials are kept in C's own [z][N][M] layout.
+template <bool TF32, int BN, bool TRANS>
 __global__ void __launch_bounds__(UM_THREADS, 1)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                      int K, float alpha, float beta, float* __restrict__ C, int64_t ldc, int per,
                      float* __restrict__ ws, int* __restrict__ err) {
-  using Cfg = UmmaCfg<TF32>;
+  using Cfg = UmmaCfg<TF32, BN>;
   constexpr int RAW = Cfg::RAW;
   constexpr int SLOTS = Cfg::SLOTS > 0 ? Cfg::SLOTS : 1;
   extern __shared__ unsigned char smem_raw[];
@@ -199,7 +224,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * UM_BM, n0 = blockIdx.x * UM_BN;
+  const int m0 = blockIdx.y * UM_BM, n0 = blockIdx.x * BN;
   // split z takes a contiguous run of k-blocks (each CTA streams its row segments in order: DRAM
   // page locality; interleaving the splits measured 2x slower)
   const int kblocks = (K + Cfg::BK - 1) / Cfg::BK;
@@ -219,8 +244,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     mbar_init(accum, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  constexpr uint32_t TMEM_COLS = TF32 ? 256 : 128;
-  if (warp == 0) {  // TMEM: 128 lanes x 128 FP32 columns per accumulator
+  constexpr uint32_t TMEM_COLS = Cfg::TMEM_COLS;
+  if (warp == 0) {  // TMEM: 128 lanes x BN FP32 columns per accumulator
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -240,17 +265,17 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
         ok = mbar_wait(&empty[s], ph ^ 1);
         if (!ok) break;
         unsigned char* st = tiles + (size_t)s * Cfg::RAW_BYTES;
-        mbar_expect_tx(&full[s], 2 * Cfg::TILE_BYTES);
+        mbar_expect_tx(&full[s], Cfg::A_BYTES + Cfg::B_BYTES);
         const int kx = (kb0 + kb) * Cfg::BK;
         tma_load_2d(st, &tmA, &full[s], kx, m0);
-        tma_load_2d(st + Cfg::TILE_BYTES, &tmB, &full[s], kx, n0);
+        tma_load_2d(st + Cfg::A_BYTES, &tmB, &full[s], kx, n0);
       }
       if (!ok) atomicExch(&s_fail, 1);
     }
   } else if (warp == 5) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = umma_idesc(TF32 ? 2u : 1u, UM_BM, UM_BN);
+      constexpr uint32_t idesc = umma_idesc(TF32 ? 2u : 1u, UM_BM, BN);
       for (int kb = 0; kb < nkb && ok; ++kb) {
         unsigned char* st;
         if constexpr (TF32) {
@@ -264,16 +289,16 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
         }
         if (!ok) break;
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + Cfg::TILE_BYTES);
-        const uint32_t a_lo = smem_u32(st + 2 * Cfg::TILE_BYTES), b_lo = smem_u32(st + 3 * Cfg::TILE_BYTES);
+        const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + Cfg::A_BYTES);
+        const uint32_t a_lo = smem_u32(st + Cfg::RAW_BYTES), b_lo = smem_u32(st + Cfg::RAW_BYTES + Cfg::A_BYTES);
 #pragma unroll
         for (int k = 0; k < Cfg::BK / Cfg::MMA_K; ++k) {
           const uint32_t off = k * 32;  // 32-byte K slice inside the swizzle atom
           const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
           umma<TF32>(tmem, umma_desc(a_hi + off), umma_desc(b_hi + off), idesc, acc);
-          if constexpr (TF32) {  // correction products into their own accumulator (columns 128..255)
-            umma<TF32>(tmem + 128u, umma_desc(a_hi + off), umma_desc(b_lo + off), idesc, acc);
-            umma<TF32>(tmem + 128u, umma_desc(a_lo + off), umma_desc(b_hi + off), idesc, 1u);
+          if constexpr (TF32) {  // correction products into their own accumulator (columns BN..2 BN-1)
+            umma<TF32>(tmem + (uint32_t)BN, umma_desc(a_hi + off), umma_desc(b_lo + off), idesc, acc);
+            umma<TF32>(tmem + (uint32_t)BN, umma_desc(a_lo + off), umma_desc(b_hi + off), idesc, 1u);
           }
         }
         // the slot / stage is free once these MMAs have read it
@@ -293,9 +318,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
         if (!ok) break;
         const float* raw = reinterpret_cast<const float*>(tiles + (size_t)s * Cfg::RAW_BYTES);
         float* slot = reinterpret_cast<float*>(slots + (size_t)t * Cfg::SLOT_BYTES);
-        constexpr int TF = Cfg::TILE_BYTES / 4;
-        split_tile(raw, slot, slot + 2 * TF, TF, threadIdx.x, 128);                // A -> A hi, A lo
-        split_tile(raw + TF, slot + TF, slot + 3 * TF, TF, threadIdx.x, 128);      // B -> B hi, B lo
+        constexpr int AF = Cfg::A_BYTES / 4, BF = Cfg::B_BYTES / 4, RF = Cfg::RAW_BYTES / 4;
+        split_tile(raw, slot, slot + RF, AF, threadIdx.x, 128);                    // A -> A hi, A lo
+        split_tile(raw + AF, slot + AF, slot + RF + AF, BF, threadIdx.x, 128);     // B -> B hi, B lo
         mbar_arrive(&empty[s]);                                                    // raw stage read
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async proxy (MMA)
         mbar_arrive(&sfull[t]);
@@ -306,23 +331,45 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       tc_fence_after();
       // Every MMA has completed (accum), so the stage buffers are free: each warp transposes its
       // 32 x 32 accumulator chunks through a padded shared tile and stores whole row segments
-      // (lane = column), so every store instruction writes 128 contiguous bytes.
+      // (lane = column), so every store instruction writes 128 contiguous bytes.  TRANS stores
+      // straight from the registers (lane = row of the kernel's tile = column of C).
       float* stage = reinterpret_cast<float*>(tiles) + warp * (32 * 33);
+      const int trow = m0 + warp * 32 + lane;
       const int col_base = n0 + lane;
-      for (int c0 = 0; c0 < UM_BN; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      constexpr int CW = BN < 32 ? BN : 32;  // accumulator columns per TMEM load
+      for (int c0 = 0; c0 < BN; c0 += CW) {
+        float v[CW];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        if constexpr (CW == 16) tmem_ld16(ta, v);
+        else tmem_ld32(ta, v);
         if constexpr (TF32) {
-          float w[32];
-          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 128u + (uint32_t)c0, w);
+          float w[CW];
+          if constexpr (CW == 16) tmem_ld16(ta + (uint32_t)BN, w);
+          else tmem_ld32(ta + (uint32_t)BN, w);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] += w[j];
+          for (int j = 0; j < CW; ++j) v[j] += w[j];
+        }
+        if constexpr (TRANS) {
+          if (trow < M) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              const int col = n0 + c0 + j;
+              if (col >= N) break;
+              if (ws) {
+                ws[((int64_t)blockIdx.z * N + col) * M + trow] = v[j];
+              } else {
+                float* d = C + (int64_t)col * ldc + trow;
+                *d = (beta == 0.f) ? alpha * v[j] : fmaf(alpha, v[j], beta * *d);
+              }
+            }
+          }
+          continue;
         }
 #pragma unroll
-        for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
+        for (int j = 0; j < CW; ++j) stage[lane * 33 + j] = v[j];
         __syncwarp();
         const int col = col_base + c0;
-        if (col < N) {
+        if (lane < CW && col < N) {
           for (int r = 0; r < 32; ++r) {
             const int row = m0 + warp * 32 + r;
             if (row >= M) break;
@@ -366,13 +413,14 @@ static cudaError_t get_encoder() {
   return cudaSuccess;
 }
 
-// 2-D map over a row-major (rows x cols) matrix, box = 128 rows x 128 bytes, 128-byte swizzle,
+// 2-D map over a row-major (rows x cols) matrix, box = box_rows rows x 128 bytes, 128-byte swizzle,
 // out-of-range reads return zero (ragged M / N / K edges).
-static cudaError_t make_map(CUtensorMap* tm, const void* base, bool tf32, int64_t rows, int64_t cols, int64_t ld) {
+static cudaError_t make_map(CUtensorMap* tm, const void* base, bool tf32, int64_t rows, int64_t cols, int64_t ld,
+                            int box_rows) {
   const int elem = tf32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * elem)};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)UM_BM};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(tm, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                         const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -438,11 +486,20 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
     return cudaErrorInvalidValue;
   cudaError_t e = get_encoder();
   if (e != cudaSuccess) return e;
+  // a thin M with a wide N: compute C^T = B A^T so that the thin side is the tile width
+  const bool trans = M <= 64 && N > 64;
+  if (trans) {
+    std::swap(M, N);
+    std::swap(A, B);
+    std::swap(lda, ldb);
+  }
+  // the narrowest tile that covers a thin N (one column of tiles), else 128 columns
+  const int bn = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
   CUtensorMap ta, tb;
-  if ((e = make_map(&ta, A, tf32, M, K, lda)) != cudaSuccess) return e;
-  if ((e = make_map(&tb, B, tf32, N, K, ldb)) != cudaSuccess) return e;
+  if ((e = make_map(&ta, A, tf32, M, K, lda, UM_BM)) != cudaSuccess) return e;
+  if ((e = make_map(&tb, B, tf32, N, K, ldb, bn)) != cudaSuccess) return e;
   const int bk = 128 / elem;
-  const int tiles = ((M + UM_BM - 1) / UM_BM) * ((N + UM_BN - 1) / UM_BN);
+  const int tiles = ((M + UM_BM - 1) / UM_BM) * ((N + bn - 1) / bn);
   const int kblocks = (K + bk - 1) / bk;
   // K splits: minimise waves x per-CTA time (chain of k-blocks + a fixed prologue / epilogue cost of
   // about UM_CTA_FIXED_KB k-blocks) + the partial sums, with TF32X3 chains of at most
@@ -468,35 +525,56 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
     e = dev_alloc((void**)&ws, sizeof(float) * (size_t)splits * M * N, st);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((N + UM_BN - 1) / UM_BN, (M + UM_BM - 1) / UM_BM, splits);
+  dim3 grid((N + bn - 1) / bn, (M + UM_BM - 1) / UM_BM, splits);
   {
     AMM_TRACE_W(tf32 ? "umma_gemm_tf32x3" : "umma_gemm_bf16", st, 2.0 * M * N * (double)K,
                 (double)elem * ((double)M * K + (double)N * K) + 4.0 * M * N, nullptr);
-    if (tf32) {
+    auto launch = [&](auto tf32_c, auto bn_c) -> cudaError_t {
+      constexpr bool T = decltype(tf32_c)::value;
+      constexpr int BN = decltype(bn_c)::value;
+      using Cfg = UmmaCfg<T, BN>;
       static DeviceOnce once;
       const cudaError_t a = once([] {
-        return cudaFuncSetAttribute((const void*)umma_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)UmmaCfg<true>::SMEM);
+        cudaError_t r = cudaFuncSetAttribute((const void*)umma_gemm_kernel<T, BN, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        if (r == cudaSuccess)
+          r = cudaFuncSetAttribute((const void*)umma_gemm_kernel<T, BN, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        return r;
       });
       if (a != cudaSuccess) return a;
-      umma_gemm_kernel<true><<<grid, UM_THREADS, UmmaCfg<true>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
-                                                                             per, ws, err);
-    } else {
-      static DeviceOnce once;
-      const cudaError_t a = once([] {
-        return cudaFuncSetAttribute((const void*)umma_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)UmmaCfg<false>::SMEM);
-      });
-      if (a != cudaSuccess) return a;
-      umma_gemm_kernel<false><<<grid, UM_THREADS, UmmaCfg<false>::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
-                                                                               per, ws, err);
+      if (trans)
+        umma_gemm_kernel<T, BN, true><<<grid, UM_THREADS, Cfg::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc, per,
+                                                                          ws, err);
+      else
+        umma_gemm_kernel<T, BN, false><<<grid, UM_THREADS, Cfg::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc, per,
+                                                                           ws, err);
+      return cudaSuccess;
+    };
+    using I16 = std::integral_constant<int, 16>;
+    using I32 = std::integral_constant<int, 32>;
+    using I64 = std::integral_constant<int, 64>;
+    using I128 = std::integral_constant<int, 128>;
+    cudaError_t la;
+    if (tf32)
+      la = bn == 16 ? launch(std::true_type{}, I16{}) : bn == 32 ? launch(std::true_type{}, I32{})
+         : bn == 64 ? launch(std::true_type{}, I64{}) : launch(std::true_type{}, I128{});
+    else
+      la = bn == 16 ? launch(std::false_type{}, I16{}) : bn == 32 ? launch(std::false_type{}, I32{})
+         : bn == 64 ? launch(std::false_type{}, I64{}) : launch(std::false_type{}, I128{});
+    if (la != cudaSuccess) {
+      dev_free(ws, st);
+      return la;
     }
   }
   e = cudaGetLastError();
   if (e == cudaSuccess && splits > 1) {
     AMM_TRACE("umma_splitk_reduce", st);
     const int64_t quads = ((int64_t)M * N + 3) / 4;
-    umma_splitk_reduce_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, st>>>(M, N, splits, ws, alpha, beta, C, ldc);
+    // partials are in C's layout: (caller's) M rows x N columns
+    const int Mc = trans ? N : M, Nc = trans ? M : N;
+    umma_splitk_reduce_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, st>>>(Mc, Nc, splits, ws, alpha, beta, C,
+                                                                               ldc);
     e = cudaGetLastError();
   }
   dev_free(ws, st);

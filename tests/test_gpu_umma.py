@@ -31,7 +31,12 @@ def _padded(torch, x, dtype, mult):
 
 
 SHAPES = [(128, 128, 64), (128, 128, 32), (256, 384, 1024), (200, 130, 100), (4096, 128, 4096),
-          (128, 4096, 512), (1000, 777, 333)]
+          (128, 4096, 512), (1000, 777, 333),
+          # thin N: the 16 / 32 / 64-wide tiles, ragged N and M, K splits
+          (4096, 16, 4096), (4096, 32, 512), (1000, 17, 333), (256, 64, 1024), (300, 8, 96), (512, 40, 256),
+          (128, 1, 64), (2048, 48, 4096),
+          # thin M, wide N: computed as C^T = B A^T and stored transposed
+          (16, 4096, 4096), (32, 777, 333), (48, 256, 1024), (1, 300, 64)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
