@@ -33,12 +33,16 @@ __global__ void __launch_bounds__(NT) cd_spectrum_kernel(const T* __restrict__ A
   constexpr int LD = fft_padded_len(N);
   const int j0 = blockIdx.x * J;
   float* fs = reinterpret_cast<float*>(smem);
-  // gather: element (r, q): column c = (r - j0 - (J-1) + q) mod n holds cycle m = J-1-q at l = c
+  // gather: element (r, q): column c = (r - j0 - (J-1) + q) mod n holds cycle m = J-1-q at l = c.
+  // With J = 8 a warp covers four rows; they are taken as r, r + 1, r + 8, r + 9 (a permutation of
+  // each 16 consecutive rows), whose shared-memory stores fall on disjoint banks.
   static_assert((N * J) % NT == 0, "whole iterations");
 #pragma unroll 16
   for (int it = 0; it < N * J / NT; ++it) {  // unrolled: several loads in flight per thread
     const int e = threadIdx.x + it * NT;
-    const int r = e / J, q = e % J;
+    const int r0 = e / J, q = e % J;
+    const int r = (J == 8 && N % 16 == 0) ? ((r0 & ~15) | (((r0 >> 2) & 3) << 1) | (r0 & 1) | (((r0 >> 1) & 1) << 3))
+                                          : r0;
     const int c = wrapN<N>(r - j0 - (J - 1) + q);
     const int m = J - 1 - q;
     const float v = ld_as_float<T>(A + (int64_t)r * lda + c);

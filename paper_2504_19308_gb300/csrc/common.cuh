@@ -27,7 +27,10 @@ AMM_DEV float2 cmul_i(float2 a, int s) { return s > 0 ? make_float2(-a.y, a.x) :
 // Padded shared-memory index for FFT buffers: one float2 of padding every 16 elements.
 // Makes the stride-R stores of the first radix-R Stockham pass bank-conflict free.
 AMM_DEV int fpad(int e) { return e + (e >> 4); }
-__host__ __device__ constexpr int fft_padded_len(int n) { return n + n / 16; }
+// Stride between the signals of a CTA: the padded length plus 4 float2, so that the same index of
+// four consecutive signals falls on four different groups of 8 banks (2 * stride = 8 mod 32 for
+// n >= 256) -- the reads of one frequency across the packed signals are then conflict free.
+__host__ __device__ constexpr int fft_padded_len(int n) { return n + n / 16 + 4; }
 
 constexpr int ilog2_c(int n) { return n <= 1 ? 0 : 1 + ilog2_c(n / 2); }
 

@@ -13,7 +13,8 @@
 //
 // which leaves the result in natural order.  Loads of a pass complete (barrier) before
 // its stores, so the same buffer is read and written.  Twiddles come from a table
-// tw[m] = e^{-2 pi i m / N} built once per N in double precision and rounded to float.
+// tw[m] = e^{-2 pi i m / N} built once per N in double precision and rounded to float; a
+// butterfly reads the powers 1, 2, 4, 8 of its twiddle and multiplies out the others.
 // Forward = unnormalised DFT (sign -); inverse = sign +, no 1/N (callers scale).
 #pragma once
 #include "common.cuh"
@@ -116,6 +117,38 @@ template <int R, bool INV> AMM_DEV void dft_r(float2* v) {
   else dft16<INV>(v);
 }
 
+// ----------------------------------------------------------------------------- twiddle powers
+// w[r] = tw[r * base] (r = 1 .. R-1) for a butterfly of radix R, conjugated for INV.  The powers
+// 1, 2, 4, 8 are read from the table and the others formed as products of at most three of them
+// (w3 = w1 w2, w5 = w4 w1, ..., w15 = w8 (w4 w3)): four loads instead of fifteen through the L1
+// pipe for R = 16, at a cost of a few ulp in the formed twiddles.
+template <int R, bool INV>
+AMM_DEV void twiddle_powers(const float2* __restrict__ tw, int base, float2* w) {
+  auto ld = [&](int r) {
+    float2 v = __ldg(tw + r * base);
+    if (INV) v.y = -v.y;
+    return v;
+  };
+  if constexpr (R <= 3) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r] = ld(r);
+  } else {
+    w[1] = ld(1);
+    w[2] = ld(2);
+    w[3] = cmul(w[1], w[2]);
+    if constexpr (R >= 8) {
+      w[4] = ld(4);
+#pragma unroll
+      for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+    }
+    if constexpr (R >= 16) {
+      w[8] = ld(8);
+#pragma unroll
+      for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- one Stockham pass
 // S signals of length N, signal s at buf + s * fft_padded_len(N), NT threads cooperating.
 // UNPAD_OUT: store the pass's output at plain (unpadded) indices.  Used for the last pass of a
@@ -136,14 +169,12 @@ AMM_DEV void stockham_pass(float2* buf, const float2* __restrict__ tw) {
       const int s = b / NB, j = b % NB;
       const float2* x = buf + s * LD;
       const int m = j % NS;
+      float2 w[R];
+      if (NS > 1) twiddle_powers<R, INV>(tw, m * TWS, w);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float2 a = x[fpad(j + r * NB)];
-        if (NS > 1 && r > 0) {
-          float2 w = __ldg(tw + r * m * TWS);
-          if (INV) w.y = -w.y;
-          a = cmul(a, w);
-        }
+        if (NS > 1 && r > 0) a = cmul(a, w[r]);
         v[i][r] = a;
       }
       dft_r<R, INV>(v[i]);

@@ -374,7 +374,10 @@ cudaError_t ft_product(int n, int m, int p, int k_a, int k_b, const float2* At, 
                        const int32_t* selA, const uint32_t* maskT, int mask_words, const float2* Bt,
                        const int32_t* selB, float* C, int64_t ldc, cudaStream_t st) {
   {
-    AMM_TRACE_W("ft_t1", st, 8.0 * m * (double)p * k_a, 8.0 * m * (double)p * k_a + 4.0 * m * p, nullptr);
+    // work: the real part of each kept product (2 FMAs); bytes: the minimal HBM traffic (kept entries
+    // of A~, the half spectrum B~, C written)
+    AMM_TRACE_W("ft_t1", st, 4.0 * m * (double)p * k_a, 12.0 * m * (double)k_a + 8.0 * (n / 2 + 1.0) * p + 4.0 * m * p,
+                nullptr);
     dim3 grid((p + 255) / 256, (m + T1_RB - 1) / T1_RB);
     size_t sm = (size_t)T1_RB * k_a * (4 + 8) + 8;
     ft_t1_kernel<<<grid, 256, sm, st>>>(At, selA, k_a, Bt, n, m, p, C, ldc);
@@ -382,7 +385,9 @@ cudaError_t ft_product(int n, int m, int p, int k_a, int k_b, const float2* At, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   {
-    AMM_TRACE_W("ft_t2", st, 8.0 * m * (double)p * k_b, 12.0 * m * (double)p * k_b + 8.0 * m * p, nullptr);
+    // bytes: A~^T and its mask, the kept entries of B~, C read and written
+    AMM_TRACE_W("ft_t2", st, 4.0 * m * (double)p * k_b,
+                8.0 * (n / 2 + 1.0) * m + n * (double)m / 8 + 12.0 * p * (double)k_b + 8.0 * m * p, nullptr);
     ft_t2_launch<false>(AtT, maskT, mask_words, selB, k_b, Bt, n, m, p, C, ldc, st);
   }
   return cudaGetLastError();
@@ -531,7 +536,8 @@ cudaError_t ft_left_apply(int n, int m, const float2* At, const int32_t* selA, i
   if (e == cudaSuccess) e = dev_alloc((void**)&mag, sizeof(float) * kh * p, st);
   if (e == cudaSuccess) e = ft_transform(n, false, X, ldx, p, tw, Xt, nullptr, mag, st);
   if (e == cudaSuccess) {
-    AMM_TRACE_W("ft_t1", st, 8.0 * m * (double)p * ka, 8.0 * m * (double)p * ka + 4.0 * m * p, nullptr);
+    AMM_TRACE_W("ft_t1", st, 4.0 * m * (double)p * ka, 12.0 * m * (double)ka + 8.0 * (n / 2 + 1.0) * p + 4.0 * m * p,
+                nullptr);
     dim3 grid((p + 255) / 256, (m + T1_RB - 1) / T1_RB);
     ft_t1_kernel<<<grid, 256, (size_t)T1_RB * ka * (4 + 8) + 8, st>>>(At, selA, ka, Xt, n, m, p, C, ldc);
     e = cudaGetLastError();
@@ -552,8 +558,8 @@ cudaError_t ft_right_apply(int n, int p, const float2* Bt, const int32_t* selB, 
   if (e == cudaSuccess) e = dev_alloc((void**)&mag, sizeof(float) * kh * m, st);
   if (e == cudaSuccess) e = ft_transform(n, true, Y, ldy, m, tw, Yt, YtT, mag, st);
   if (e == cudaSuccess) {
-    AMM_TRACE_W(imag ? "ft_t2_imag" : "ft_t2", st, 8.0 * m * (double)p * kb, 12.0 * m * (double)p * kb + 8.0 * m * p,
-                nullptr);
+    AMM_TRACE_W(imag ? "ft_t2_imag" : "ft_t2", st, 4.0 * m * (double)p * kb,
+                8.0 * (n / 2 + 1.0) * m + 12.0 * p * (double)kb + 8.0 * m * p, nullptr);
     if (imag) ft_t2_launch<true>(YtT, nullptr, 0, selB, kb, Bt, n, m, p, C, ldc, st);
     else ft_t2_launch<false>(YtT, nullptr, 0, selB, kb, Bt, n, m, p, C, ldc, st);
     e = cudaGetLastError();

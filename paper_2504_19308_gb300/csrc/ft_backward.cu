@@ -275,6 +275,9 @@ static cudaError_t ft_bw_real(int n, bool inv, const float2* X, int nvec, const 
   AMM_FTB_DISPATCH(n, return FtBwOps<NN>::fwd_cols(X, nvec, tw, out, ldo, st));
 }
 
+// Trace work of the kernels below: FLOPs of the real or complex products actually formed, bytes the
+// minimal HBM traffic (each operand read once, each output written once); the kernels themselves
+// are bound by L2 gathers, which neither figure counts.
 cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
   const int n = a.n, m = a.m, p = a.p;
   const int mwA = (m + 31) / 32, mwB = (p + 31) / 32;
@@ -287,13 +290,15 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
   if (e == cudaSuccess) e = transpose_f32(a.G, m, p, a.ldg, GT, m, st);
   if (e == cudaSuccess && a.dA) {
     {
-      AMM_TRACE_W("ft_bw_gba", st, 4.0 * p * (double)a.kb * m, 4.0 * p * (double)a.kb * m + 8.0 * n * m, nullptr);
+      AMM_TRACE_W("ft_bw_gba", st, 4.0 * p * (double)a.kb * m, 4.0 * m * (double)p + 8.0 * p * (double)a.kb + 8.0 * n * m,
+                  nullptr);
       ft_bw_maskwalk_kernel<<<dim3((m + 256 * MW_RPT - 1) / (256 * MW_RPT), n), 256, 0, st>>>(
           GT, m, m, a.Bt, p, a.maskB, mwB, n, XAT);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      AMM_TRACE_W("ft_bw_pa", st, 4.0 * m * (double)a.ka * p, 12.0 * m * (double)a.ka * p, nullptr);
+      AMM_TRACE_W("ft_bw_pa", st, 4.0 * m * (double)a.ka * p,
+                  4.0 * m * (double)p + 8.0 * (n / 2 + 1.0) * p + 16.0 * m * (double)a.ka, nullptr);
       ft_bw_pa_kernel<<<m, 256, 0, st>>>(a.G, a.ldg, a.Bt, a.maskB, mwB, a.selA, a.ka, n, m, p, XAT);
       e = cudaGetLastError();
     }
@@ -301,13 +306,15 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
   }
   if (e == cudaSuccess && a.dB) {
     {
-      AMM_TRACE_W("ft_bw_aag", st, 4.0 * m * (double)a.ka * p, 4.0 * m * (double)a.ka * p + 8.0 * n * p, nullptr);
+      AMM_TRACE_W("ft_bw_aag", st, 4.0 * m * (double)a.ka * p, 4.0 * m * (double)p + 8.0 * m * (double)a.ka + 8.0 * n * p,
+                  nullptr);
       ft_bw_maskwalk_kernel<<<dim3((p + 256 * MW_RPT - 1) / (256 * MW_RPT), n), 256, 0, st>>>(
           a.G, a.ldg, p, a.AtT, m, a.maskA, mwA, n, XB);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      AMM_TRACE_W("ft_bw_pb", st, 4.0 * p * (double)a.kb * m, 12.0 * p * (double)a.kb * m, nullptr);
+      AMM_TRACE_W("ft_bw_pb", st, 4.0 * p * (double)a.kb * m,
+                  4.0 * m * (double)p + 8.0 * (n / 2 + 1.0) * m + 16.0 * p * (double)a.kb, nullptr);
       ft_bw_pb_kernel<<<p, 256, 0, st>>>(GT, a.AtT, a.maskA, mwA, a.selB, a.kb, n, m, p, XB);
       e = cudaGetLastError();
     }
