@@ -277,14 +277,19 @@ def run_amm(args, rank, world, local_rank):
     trace_collect()  # drop anything recorded so far
     _barrier(dist)
     torch.cuda.synchronize()
-    trace_enable(True)
     with ClockSampler(local_rank) as clk:
         torch.cuda.nvtx.range_push("timed")
         ms, per = timed_steps(step, args.steps, 0, dist)
         torch.cuda.nvtx.range_pop()
+    clocks = clk.summary()
+    _barrier(dist)
+    # ---- the same steps again with the library's launch trace (CUDA events on every launch's own
+    # stream): per-kernel times, launch count.  Kept out of the timed region above: the trace's
+    # events and per-launch count copies lengthen a step by about a tenth.
+    trace_enable(True)
+    traced_ms, _ = timed_steps(step, args.steps, 0, dist)
     trace_enable(False)
     kernels, launches = trace_collect()
-    clocks = clk.summary()
     _barrier(dist)
 
     # ---- the same step with L2 flushed before every step
@@ -311,6 +316,7 @@ def run_amm(args, rank, world, local_rank):
     }
     return {"value": value, "ms_per_step": ms / args.steps, "median_ms_per_step": plain_ms, "errs": errs,
             "kernels": kernels, "launches": launches, "clocks": clocks, "roofline": roof,
+            "traced_ms_per_step": traced_ms / args.steps,
             "l2_flushed": {"median_ms_per_step": statistics.median(fl_per),
                            "value": whole_job_rate(fl * args.steps, fl_total * 1e-3, world), "unit": UNIT,
                            "flush": "%d MiB written before every step, outside the step's events"
@@ -812,6 +818,8 @@ def main():
         cfg["median_ms_per_step"] = r["median_ms_per_step"]
         cfg["l2_flushed"] = r["l2_flushed"]
         cfg["kernels_ms"] = {k: round(v[1] / args.steps, 4) for k, v in r["kernels"].items()}
+        cfg["kernel_times"] = ("per-kernel times, launch count and roofline from a traced repeat of the timed steps "
+                               "(CUDA events on each launch's stream; %.2f ms per traced step)" % r["traced_ms_per_step"])
         cfg.update(r["forms"])
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,

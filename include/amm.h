@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define AMM_VERSION 6
+#define AMM_VERSION 7
 
 typedef enum {
   AMM_OK = 0,
@@ -71,7 +71,15 @@ typedef struct amm_opts {
   uint64_t seed;                  /* seed of the rSVD test matrix when `sketch` is NULL      */
   const float* sketch;            /* optional DEVICE pointer to phi (cols x k, row-major,
                                      N(0,1) entries) for AMM_SVD; copied at decompose time   */
-  int32_t store_spectra;          /* reserved: 1 keeps spectra for the backward (default)    */
+  int32_t store_spectra;          /* AMM_CIRCULANT: 1 (default) keeps the half spectrum R
+                                     ((n/2+1) x n complex; 64 MiB at n = 4096) and the key
+                                     partials in the handle; 0 releases both when amm_decompose
+                                     is done.  The product and the backward never read R (the
+                                     backward forms the spectra it needs from dense matrices in
+                                     every call); the dense residual of a mixed-method product,
+                                     amm_handle_residual and amm_refine_product then compute R
+                                     again from A, which the handle borrows (one more spectrum
+                                     pass).  Results are identical either way.                */
   const int32_t* forced_selection;/* optional HOST array of k component indices that replaces
                                      the top-k selection (AMM_CIRCULANT, AMM_SPARSE_CYCLE);
                                      used to evaluate a selection exported elsewhere          */
@@ -326,6 +334,32 @@ amm_status_t amm_handle_get_keys(amm_handle_t h, double* host_keys, int64_t cap,
 
 /* Copy the rSVD test matrix phi of Alg. 1 (cols x k, row-major) to host memory.  Synchronises. */
 amm_status_t amm_handle_get_sketch(amm_handle_t h, float* host_phi, int64_t cap);
+
+/*
+ * A decomposition carried to another process (Section 4: a trained weight is decomposed once,
+ * ahead of the products that use it).  amm_handle_export writes the handle's device state -- every
+ * factor, spectrum, selection and workspace its products and backward read, and how each refers to
+ * the operand -- into a host byte string; amm_handle_import rebuilds a handle from it without
+ * recomputing anything, so the imported handle's products and gradients are bit-identical to the
+ * original's.
+ *   export: host_buf (capacity cap bytes) receives the string and *len its length; when host_buf
+ *           is NULL or cap is too small, *len is still set and AMM_ERR_INVALID_ARG returned (call
+ *           once to size the buffer).  Synchronises the handle's stream.
+ *   import: host_buf / len as exported by a library of the same AMM_VERSION; A the same operand
+ *           (DEVICE, rows x cols, lda, dtype as at export -- the handle borrows it again, so it must
+ *           stay allocated and unchanged until amm_handle_destroy; lda and dtype are checked only
+ *           when the handle reads A, which a sparsifier handle of a BF16 operand does not).  Device
+ *           memory is allocated stream-ordered on `stream`; *out receives the handle.  A string of
+ *           another format or version, a truncated string or a shape mismatch returns an error with
+ *           nothing allocated.
+ */
+amm_status_t amm_handle_export(amm_handle_t h, void* host_buf, int64_t cap, int64_t* len);
+amm_status_t amm_handle_import(const void* host_buf, int64_t len, const void* A, int64_t rows, int64_t cols,
+                               int64_t lda, amm_dtype_t dtype, void* stream, amm_handle_t* out);
+
+/* Device memory the handle owns, in bytes (its factors, spectra, selections and workspaces; the
+ * borrowed input not included; blocks of a blocked circulant handle summed).  Host only. */
+amm_status_t amm_handle_device_bytes(amm_handle_t h, int64_t* bytes);
 
 /* Release every device buffer the handle owns (stream-ordered) and the handle. */
 amm_status_t amm_handle_destroy(amm_handle_t h);

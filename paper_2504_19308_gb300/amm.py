@@ -85,6 +85,12 @@ SIGNATURES = {
     "amm_handle_get_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                            ctypes.POINTER(ctypes.c_int64)]),
     "amm_handle_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "amm_handle_device_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "amm_handle_export": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64)]),
+    "amm_handle_import": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
     "amm_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int32]),
     "amm_circulant_spectrum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -188,6 +194,21 @@ class Handle:
         out = np.frombuffer(buf, dtype=np.int32, count=cnt.value).copy()
         return out.reshape(rows, self.k) if self.method == "fourier" or self.block else out
 
+    def export(self) -> bytes:
+        """amm_handle_export: the decomposition's device state as bytes (reusable in another process)."""
+        lib = load_library()
+        n = ctypes.c_int64(0)
+        lib.amm_handle_export(self.ptr, None, 0, ctypes.byref(n))
+        buf = ctypes.create_string_buffer(max(1, n.value))
+        _check(lib.amm_handle_export(self.ptr, buf, n.value, ctypes.byref(n)), "amm_handle_export")
+        return buf.raw[: n.value]
+
+    def device_bytes(self) -> int:
+        """Device memory the handle owns (amm_handle_device_bytes)."""
+        b = ctypes.c_int64(0)
+        _check(load_library().amm_handle_device_bytes(self.ptr, ctypes.byref(b)), "amm_handle_device_bytes")
+        return b.value
+
     def keys(self) -> np.ndarray:
         """Component keys (circulant T[t] = ||R_A[t]||_2, or the cycle norms), length n."""
         n = self.shape[0]
@@ -218,13 +239,15 @@ class Handle:
 
 def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: Optional[torch.Tensor] = None,
               seed: int = 0, forced_selection=None, compute: str = "f32", pair_closed: bool = False,
-              block: int = 0) -> Handle:
+              block: int = 0, store_spectra: bool = True) -> Handle:
     """amm_decompose: truncated decomposition of A (method 'circulant' | 'svd' | 'fourier' | 'cycle').
 
     compute: arithmetic of the SVD GEMMs, 'f32' (FP32-accurate) or 'bf16' (BF16 tensor cores).
     pair_closed: circulant selections closed under t -> n - t (a real truncation).
     block: circulant operand of any shape in block x block squares (zero-padded edge, top-k per
     block); forced_selection then holds k indices per block, blocks row-major.
+    store_spectra: False releases a circulant handle's half spectrum after the decomposition
+    (recomputed from A where a mixed product or the residual export needs it).
     """
     lib = load_library()
     _require_cuda(A, "A")
@@ -237,6 +260,7 @@ def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: 
     opts.compute = {"f32": 0, "bf16": 1}[compute]
     opts.pair_closed = 1 if pair_closed else 0
     opts.block = int(block)
+    opts.store_spectra = 1 if store_spectra else 0
     extras = []
     if sketch is not None:
         _require_cuda(sketch, "sketch")
@@ -256,6 +280,19 @@ def decompose(A: torch.Tensor, method: str, k: int, role: str = "left", sketch: 
                              ctypes.byref(opts), _stream_ptr(A.device), ctypes.byref(out)), "amm_decompose")
     blocked = block and not (A.shape[0] == block and A.shape[1] == block)
     return Handle(out.value, A, method, role, k, tuple(extras), int(block) if blocked else 0)
+
+
+def import_handle(blob: bytes, A: torch.Tensor, method: str, k: int, role: str = "left", block: int = 0) -> Handle:
+    """amm_handle_import: a handle rebuilt from amm_handle_export's bytes, borrowing A (the same
+    operand; method / k / role / block describe the exported handle for the binding's bookkeeping)."""
+    lib = load_library()
+    _require_cuda(A, "A")
+    out = ctypes.c_void_p(0)
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    _check(lib.amm_handle_import(buf, len(blob), A.data_ptr(), A.shape[0], A.shape[1], A.stride(0), DTYPES[A.dtype],
+                                 _stream_ptr(A.device), ctypes.byref(out)), "amm_handle_import")
+    blocked = block and not (A.shape[0] == block and A.shape[1] == block)
+    return Handle(out.value, A, method, role, k, (), int(block) if blocked else 0)
 
 
 def approx_matmul(hA: Handle, hB: Handle, out: Optional[torch.Tensor] = None) -> torch.Tensor:

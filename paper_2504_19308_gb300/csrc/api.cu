@@ -165,11 +165,53 @@ void amm::Handle::release() {
   blk.sub.clear();
   for (void* p : owned) dev_free(p, stream);
   owned.clear();
+  owned_bytes.clear();
 }
 
 cudaError_t amm::Handle::alloc(void** p, size_t bytes) {
   cudaError_t e = dev_alloc(p, bytes, stream);
-  if (e == cudaSuccess) owned.push_back(*p);
+  if (e == cudaSuccess) {
+    owned.push_back(*p);
+    owned_bytes.push_back(bytes);
+  }
+  return e;
+}
+
+void amm::Handle::release_one(void* p) {
+  for (size_t i = 0; i < owned.size(); ++i)
+    if (owned[i] == p) {
+      dev_free(p, stream);
+      owned.erase(owned.begin() + i);
+      owned_bytes.erase(owned_bytes.begin() + i);
+      return;
+    }
+}
+
+int64_t amm::Handle::device_bytes() const {
+  int64_t s = 0;
+  for (size_t b : owned_bytes) s += (int64_t)b;
+  for (const amm_handle* b : blk.sub) s += b->device_bytes();
+  return s;
+}
+
+cudaError_t amm::cd_spectrum_of(Handle* h, const float2** R, float2** temp, cudaStream_t st) {
+  *temp = nullptr;
+  if (h->cd.R) {
+    *R = h->cd.R;
+    return cudaSuccess;
+  }
+  const int n = (int)h->rows;
+  const size_t kh = (size_t)n / 2 + 1;
+  float* kpart = nullptr;
+  cudaError_t e = dev_alloc((void**)temp, sizeof(float2) * kh * n, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&kpart, sizeof(float) * kh * h->cd.nparts, st);
+  if (e == cudaSuccess) e = cd_spectrum(n, h->A, h->lda, h->dtype == AMM_BF16, h->cd.tw, *temp, kpart, st);
+  if (kpart) dev_free(kpart, st);
+  if (e != cudaSuccess && *temp) {
+    dev_free(*temp, st);
+    *temp = nullptr;
+  }
+  *R = *temp;
   return e;
 }
 
@@ -237,6 +279,12 @@ amm_status_t amm::decompose_circulant(Handle* h, const amm_opts_t* o) {
       return cuda_fail(e, "cd_residual launch");
     if ((e = cd_residual(n, c.R, c.tw, c.so.vfull, 1, c.so.counts + 1, c.imag, h->stream)) != cudaSuccess)
       return cuda_fail(e, "cd_residual launch");
+  }
+  if (o && o->store_spectra == 0) {  // the products and the backward do not read R again
+    h->release_one(c.R);
+    h->release_one(c.kpart);
+    c.R = nullptr;
+    c.kpart = nullptr;
   }
   return AMM_OK;
 }
@@ -940,6 +988,12 @@ extern "C" amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_i
   if (e == cudaSuccess) e = cudaMemcpy(host_idx, sel, sizeof(int32_t) * h->k, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "amm_handle_get_selection");
   *count = h->k;
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_handle_device_bytes(amm_handle_t h, int64_t* bytes) {
+  if (!h || !bytes) return fail(AMM_ERR_INVALID_ARG, "amm_handle_device_bytes: NULL argument");
+  *bytes = h->device_bytes();
   return AMM_OK;
 }
 

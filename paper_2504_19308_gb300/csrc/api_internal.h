@@ -15,6 +15,7 @@ struct amm_handle {
   int dtype = AMM_F32, method = AMM_CIRCULANT, role = AMM_LEFT, compute = AMM_F32;
   cudaStream_t stream = nullptr;
   std::vector<void*> owned;  // device buffers released by amm_handle_destroy
+  std::vector<size_t> owned_bytes;  // their sizes
 
   struct Circulant {
     const float2* tw = nullptr;   // twiddle table (process-wide cache, not owned)
@@ -71,6 +72,8 @@ struct amm_handle {
 
   void release();
   cudaError_t alloc(void** p, size_t bytes);
+  void release_one(void* p);   // one owned buffer, stream-ordered
+  int64_t device_bytes() const;  // bytes of the owned buffers (blocks included)
 };
 
 namespace amm {
@@ -90,6 +93,9 @@ amm_status_t cuda_fail(cudaError_t e, const char* what);
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
 void dev_free(void* p, cudaStream_t st);
 cudaError_t twiddles(int n, cudaStream_t st, const float2** out);
+// The half spectrum of a square circulant handle: its stored R, or (store_spectra = 0) R computed
+// again from the borrowed operand into *temp, which the caller releases with dev_free.
+cudaError_t cd_spectrum_of(Handle* h, const float2** R, float2** temp, cudaStream_t st);
 
 // svd.cu
 amm_status_t decompose_svd(Handle* h, const amm_opts_t* o);

@@ -254,8 +254,13 @@ cudaError_t blocked_residual(Handle* a, bool imag, float* D, int64_t ldd, cudaSt
       Handle* s = g.at(i, j);
       const auto& c = s->cd;
       float* Dij = D + i * bs * ldd + j * bs;
-      e = imag ? cd_residual(bs, c.R, c.tw, c.so.vfull, 1, c.so.counts + 1, Dij, st, ldd, 0)
-               : cd_residual(bs, c.R, c.tw, c.so.wfull, 0, nullptr, Dij, st, ldd, 0);
+      const float2* R = nullptr;
+      float2* temp = nullptr;
+      e = cd_spectrum_of(s, &R, &temp, st);
+      if (e == cudaSuccess)
+        e = imag ? cd_residual(bs, R, c.tw, c.so.vfull, 1, c.so.counts + 1, Dij, st, ldd, 0)
+                 : cd_residual(bs, R, c.tw, c.so.wfull, 0, nullptr, Dij, st, ldd, 0);
+      if (temp) dev_free(temp, st);
     }
   return e;
 }

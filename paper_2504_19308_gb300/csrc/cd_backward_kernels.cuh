@@ -64,31 +64,25 @@ __global__ void __launch_bounds__(NT) bw_spectrum_kernel(const float* __restrict
 
 // ============================================================================ SDDMM on spectra
 // K[u][p] = sum_m Xh(p, m) Yh((t_u - p) mod n, m) for t_u <= n/2, p = 0..n-1.  Half-spectrum rows
-// q > n/2 are conj(row n - q).  A CTA of 8 warps takes two p and a block of SD_UB listed
-// components; the four warps of one p each stride over a quarter of m (lanes over m), so each Xh
-// element is loaded once for SD_UB products (9 bytes per complex MAC instead of 16), the SD_UB
-// independent loads of Yh overlap, and a warp's chain of dependent L2 round trips is a quarter of
-// a row long.  The four partial sums are added in warp order (deterministic).  The component
-// blocks are the fast grid dimension: the CTAs in flight share a narrow window of p, so the Xh
-// rows of the window and the Yh rows t - p (each used by every t whose window covers it) stay in
-// L2 while the spectra themselves (2 x 64 MiB at n = 4096) do not fit.
+// q > n/2 are conj(row n - q).  One warp per (p, block of SD_UB listed components); lanes stride
+// over m, so each Xh element is loaded once for SD_UB products (9 bytes per complex MAC instead
+// of 16) and the SD_UB independent loads of Yh overlap.  The component blocks are the fast grid
+// dimension: the CTAs in flight share a narrow window of p, so the Xh rows of the window and
+// the Yh rows t - p (each used by every t whose window covers it) stay in L2 while the spectra
+// themselves (2 x 64 MiB at n = 4096) do not fit.
 constexpr int SD_UB = 8;
-constexpr int SD_MSPLIT = 4;  // warps per p
 template <int N>
 __global__ void __launch_bounds__(256) cd_sddmm_kernel(const float2* __restrict__ Xh, const float2* __restrict__ Yh,
                                                        const int32_t* __restrict__ list,
                                                        const int32_t* __restrict__ count, float2* __restrict__ K,
                                                        const int32_t* __restrict__ gate0,
                                                        const int32_t* __restrict__ gate1) {
-  __shared__ float2 part[8][SD_UB];
   if (gate0 != nullptr && (*gate0 == 0 || *gate1 == 0)) return;
   const int cnt = *count;
   const int u0 = blockIdx.x * SD_UB;
   if (u0 >= cnt) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.y * (8 / SD_MSPLIT) + warp / SD_MSPLIT;
-  constexpr int MQ = N / SD_MSPLIT;               // m range of one warp (a multiple of 32 for N >= 128)
-  const int mlo = (warp % SD_MSPLIT) * MQ;
+  const int p = blockIdx.y * 8 + warp;
   const bool xm = p > N / 2;
   const float2* xr = Xh + (int64_t)(xm ? N - p : p) * N;
   const float xs = xm ? -1.f : 1.f;
@@ -110,7 +104,7 @@ __global__ void __launch_bounds__(256) cd_sddmm_kernel(const float2* __restrict_
 #pragma unroll
   for (int j = 0; j < SD_UB; ++j) acc[j] = make_float2(0.f, 0.f);
 #pragma unroll 2
-  for (int m = mlo + lane; m < mlo + MQ; m += 32) {
+  for (int m = lane; m < N; m += 32) {
     float2 x = __ldg(xr + m);
     x.y *= xs;
 #pragma unroll
@@ -131,14 +125,8 @@ __global__ void __launch_bounds__(256) cd_sddmm_kernel(const float2* __restrict_
   }
   if (lane == 0) {
 #pragma unroll
-    for (int j = 0; j < SD_UB; ++j) part[warp][j] = acc[j];
-  }
-  __syncthreads();
-  if (warp % SD_MSPLIT == 0 && lane < SD_UB && u0 + lane < cnt && __ldg(list + u0 + lane) <= N / 2) {
-    float2 v = part[warp][lane];
-#pragma unroll
-    for (int w = 1; w < SD_MSPLIT; ++w) v = cadd(v, part[warp + w][lane]);
-    K[(int64_t)(u0 + lane) * N + p] = v;
+    for (int j = 0; j < SD_UB; ++j)
+      if (act[j]) K[(int64_t)(u0 + j) * N + p] = acc[j];
   }
 }
 
@@ -285,12 +273,17 @@ __global__ void __launch_bounds__(NT) cd_rho_kernel(const float2* __restrict__ K
 
 // ============================================================================ launchers
 template <int N> struct BwCfg {
-  // two CTAs per SM for 1024 <= N < 6144 (one CTA of 512 threads at 128 registers would fill
-  // the register file)
+  // row spectra: two CTAs per SM for 1024 <= N < 6144 (one CTA of 512 threads at 128 registers
+  // would fill the register file); column spectra: four signals per 512-thread CTA, measured
+  // faster at N = 4096 (60 vs 70 us; the row form the other way round, 47 vs 54 us)
   static constexpr bool HALF = N >= 1024 && N < 6144;
-  static constexpr int S = (N >= 16384) ? 1 : (N >= 6144 || HALF) ? 2 : 4;
+  static constexpr int S_FULL = (N >= 16384) ? 1 : (N >= 6144) ? 2 : 4;
+  static constexpr int S = HALF ? 2 : S_FULL;                      // row spectra
   static constexpr int NT = HALF ? fft_threads(N) / 2 : fft_threads(N);
+  static constexpr int S_COL = S_FULL;                             // column spectra
+  static constexpr int NT_COL = fft_threads(N);
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
+  static constexpr size_t SMEM_COL = sizeof(float2) * S_COL * fft_padded_len(N);
   static constexpr int NT1 = (N >= 1024) ? 256 : (N >= 64 ? 64 : N);
 };
 
@@ -302,8 +295,8 @@ template <int N> struct BwOps {
       cudaError_t r = cudaFuncSetAttribute((const void*)bw_spectrum_kernel<N, C::S, C::NT, true>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
       if (r == cudaSuccess)
-        r = cudaFuncSetAttribute((const void*)bw_spectrum_kernel<N, C::S, C::NT, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        r = cudaFuncSetAttribute((const void*)bw_spectrum_kernel<N, C::S_COL, C::NT_COL, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_COL);
       if (r == cudaSuccess)
         r = cudaFuncSetAttribute((const void*)cd_rho_kernel<N, C::NT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(float2) * fft_padded_len(N)));
@@ -314,9 +307,11 @@ template <int N> struct BwOps {
                               const int32_t* g0, const int32_t* g1, cudaStream_t st) {
     cudaError_t e = attrs();
     if (e != cudaSuccess) return e;
-    dim3 grid(N / (2 * C::S));
-    if (row) bw_spectrum_kernel<N, C::S, C::NT, true><<<grid, C::NT, C::SMEM, st>>>(X, ldx, tw, Xh, g0, g1);
-    else bw_spectrum_kernel<N, C::S, C::NT, false><<<grid, C::NT, C::SMEM, st>>>(X, ldx, tw, Xh, g0, g1);
+    if (row)
+      bw_spectrum_kernel<N, C::S, C::NT, true><<<N / (2 * C::S), C::NT, C::SMEM, st>>>(X, ldx, tw, Xh, g0, g1);
+    else
+      bw_spectrum_kernel<N, C::S_COL, C::NT_COL, false><<<N / (2 * C::S_COL), C::NT_COL, C::SMEM_COL, st>>>(
+          X, ldx, tw, Xh, g0, g1);
     return cudaGetLastError();
   }
   static cudaError_t sddmm(const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
@@ -332,7 +327,7 @@ template <int N> struct BwOps {
       cd_sddmm_tiled_kernel<N><<<grid, SDT_NT, SDT_SMEM, st>>>(Xh, Yh, list, count, K, g0, g1);
       return cudaGetLastError();
     }
-    dim3 grid((cap + SD_UB - 1) / SD_UB, N / (8 / SD_MSPLIT));
+    dim3 grid((cap + SD_UB - 1) / SD_UB, N / 8);
     cd_sddmm_kernel<N><<<grid, 256, 0, st>>>(Xh, Yh, list, count, K, g0, g1);
     return cudaGetLastError();
   }

@@ -87,8 +87,14 @@ static cudaError_t residual(Handle* a, float* D, int64_t ldd, cudaStream_t st) {
   switch (a->method) {
     case AMM_SVD:
       return svd_residual(a, D, ldd, st);
-    case AMM_CIRCULANT:
-      return cd_residual(n, a->cd.R, a->cd.tw, a->cd.so.wfull, 0, nullptr, D, st, ldd, 0);
+    case AMM_CIRCULANT: {
+      const float2* R = nullptr;
+      float2* temp = nullptr;
+      cudaError_t e = cd_spectrum_of(a, &R, &temp, st);
+      if (e == cudaSuccess) e = cd_residual(n, R, a->cd.tw, a->cd.so.wfull, 0, nullptr, D, st, ldd, 0);
+      if (temp) dev_free(temp, st);
+      return e;
+    }
     case AMM_SPARSE_CYCLE:
       return cyc_residual(n, (const float*)a->A, a->lda, a->cy.insel, D, ldd, st);
     case AMM_SPARSE_FOURIER:
@@ -105,7 +111,12 @@ static cudaError_t imag_part(Handle* a, float* D, int64_t ldd, cudaStream_t st) 
   if (a->method == AMM_CIRCULANT) {
     cudaError_t e = cudaMemset2DAsync(D, sizeof(float) * ldd, 0, sizeof(float) * n, n, st);
     if (e != cudaSuccess) return e;
-    return cd_residual(n, a->cd.R, a->cd.tw, a->cd.so.vfull, 1, a->cd.so.counts + 1, D, st, ldd, 0);
+    const float2* R = nullptr;
+    float2* temp = nullptr;
+    e = cd_spectrum_of(a, &R, &temp, st);
+    if (e == cudaSuccess) e = cd_residual(n, R, a->cd.tw, a->cd.so.vfull, 1, a->cd.so.counts + 1, D, st, ldd, 0);
+    if (temp) dev_free(temp, st);
+    return e;
   }
   if (a->method == AMM_SPARSE_FOURIER)
     return ft_dense(n, a->ft.T, a->ft.sel, (int)a->k, (int)a->rows, a->ft.tw, 1, nullptr, 0, D, ldd, st);

@@ -47,7 +47,7 @@ def test_library_resolves_every_symbol_at_load(lib):
 def test_status_strings(lib):
     assert lib.amm_status_string(0) == b"AMM_OK"
     assert lib.amm_status_string(5) == b"AMM_ERR_TIMEOUT"
-    assert lib.amm_version() == 6
+    assert lib.amm_version() == 7
 
 
 def test_argument_errors_without_gpu(lib):

@@ -235,3 +235,39 @@ def test_autotuned_apply_is_bit_identical(n):
         amm.set_autotune(False)
     assert torch.equal(C0, C1) and torch.equal(C0, C2)
     assert torch.equal(dA0, dA1) and torch.equal(dB0, dB1)
+
+
+def test_store_spectra_off_gives_identical_results_with_less_memory():
+    """opts.store_spectra = 0 releases the half spectrum R after the decomposition: the product and
+    the backward (which never read R) are bit-identical, the dense residual of a mixed product and
+    the residual export recompute R from A and match too, and the handle holds at least R's
+    (n/2+1) n complex values less device memory."""
+    torch, amm = torch_cuda()
+    n, k = 1024, 9
+    a, b = S.general_times_toeplitz(n, seed=11)
+    A, B = dev32(torch, a), dev32(torch, b)
+    G = dev32(torch, S.upstream_grad(n, n, 11))
+    keep = [amm.decompose(A, "circulant", k, "left"), amm.decompose(B, "circulant", k, "right")]
+    drop = [amm.decompose(A, "circulant", k, "left", store_spectra=False),
+            amm.decompose(B, "circulant", k, "right", store_spectra=False)]
+    for hk, hd in zip(keep, drop):
+        assert hd.device_bytes() <= hk.device_bytes() - (n // 2 + 1) * n * 8
+        assert np.array_equal(hk.selection(), hd.selection())
+    assert torch.equal(amm.approx_matmul(*keep), amm.approx_matmul(*drop))
+    for gk, gd in zip(amm.approx_matmul_backward(*keep, G), amm.approx_matmul_backward(*drop, G)):
+        assert torch.equal(gk, gd)
+    sk = dev32(torch, S.sketch(n, 16, 11, 1))
+    hs = amm.decompose(B, "svd", 16, "right", sketch=sk)
+    assert torch.equal(amm.approx_matmul(keep[0], hs), amm.approx_matmul(drop[0], hs))
+    assert torch.equal(amm.residual(keep[0]), amm.residual(drop[0]))
+    ref = O.truncate_circulant(as64(A), k, keep[0].selection())
+    assert rel(amm.residual(drop[0]).double().cpu().numpy(), ref.resid.real) <= TOL
+    # blocked circulant LEFT operand of a mixed product: its dense residual needs every block's
+    # spectrum, recomputed per block
+    W = dev32(torch, S.rng(12, 1).standard_normal((384, 512)) + 0.5)
+    hy = amm.decompose(dev32(torch, S.rng(12, 0).standard_normal((512, 256))), "svd", 16, "right",
+                       sketch=dev32(torch, S.sketch(256, 16, 12, 1)))
+    wk = amm.decompose(W, "circulant", 5, "left", block=128)
+    wd = amm.decompose(W, "circulant", 5, "left", block=128, store_spectra=False)
+    assert wd.device_bytes() < wk.device_bytes()
+    assert torch.equal(amm.approx_matmul(wk, hy), amm.approx_matmul(wd, hy))
