@@ -74,12 +74,12 @@ typedef struct amm_opts {
   int32_t store_spectra;          /* AMM_CIRCULANT: 1 (default) keeps the half spectrum R
                                      ((n/2+1) x n complex; 64 MiB at n = 4096) and the key
                                      partials in the handle; 0 releases both when amm_decompose
-                                     is done.  The product and the backward never read R (the
-                                     backward forms the spectra it needs from dense matrices in
-                                     every call); the dense residual of a mixed-method product,
-                                     amm_handle_residual and amm_refine_product then compute R
-                                     again from A, which the handle borrows (one more spectrum
-                                     pass).  Results are identical either way.                */
+                                     is done.  The product never reads R; the backward of
+                                     the left operand's gradient dB, the dense residual of a
+                                     mixed-method product, amm_handle_residual and
+                                     amm_refine_product then compute R again from A, which the
+                                     handle borrows (one more spectrum pass per call).  Results
+                                     are identical either way.                                 */
   const int32_t* forced_selection;/* optional HOST array of k component indices that replaces
                                      the top-k selection (AMM_CIRCULANT, AMM_SPARSE_CYCLE);
                                      used to evaluate a selection exported elsewhere          */
@@ -392,8 +392,9 @@ amm_status_t amm_circulant_spectrum_noalloc(const float* A, int64_t n, int64_t l
  * amm_batch_add records one product C = Re(A~ B + dA B~) (A m x n, B n x p, device pointers,
  * caller-owned; the same method, k and element type for both operands; opts_a / opts_b may be
  * NULL, their role is set by the batch).  amm_batch_run executes every item -- decompose both
- * operands, product, release -- on a pool of streams forked from `stream` and joined back into
- * it.  With use_graph != 0 the first run executes the items once eagerly and then records the
+ * operands, product, release -- on a pool of 16 streams forked from `stream` and joined back into
+ * it, the items in descending order of m n p, each on the stream with the least work so far (the
+ * results do not depend on the order).  With use_graph != 0 the first run executes the items once eagerly and then records the
  * same work into one CUDA graph; that run and every later run launch the graph.  Pointers and
  * sizes are baked into the graph: rerun with the same buffers (their contents may change).
  * After the first graph run no item can be added.
@@ -442,13 +443,18 @@ amm_status_t amm_debug_gemm_tn(int32_t mode, int64_t M, int64_t N, int64_t K, fl
 
 /*
  * Autotuning of kernel variants (off by default; an implementation choice with no counterpart in
- * the paper).  With on != 0, the first call of a kernel that
- * has several compiled variants (the circulant spectral apply: two or four packed signals per CTA)
- * for a given length, direction and element type times each variant on that call's own operands
- * (into scratch memory; the call's result is computed afterwards by the fastest) and keeps the
- * choice for the process.  The variants compute every output with the same operations, so the
- * choice never changes results.  Timing synchronises the stream once per new key; calls made while
- * their stream is being captured into a CUDA graph use the current choice without timing.
+ * the paper).  With on != 0, the first call of a kernel that has several compiled variants -- the
+ * circulant spectral apply (per length, direction, coefficient pairing and element type), the
+ * inverse cycle transform and the column and row half spectra of the backward (per length): a
+ * full or a halved number of packed signals (and threads) per CTA -- times each variant on that
+ * call's own operands (into scratch memory; the call's result is computed afterwards by the
+ * fastest) and keeps the choice for the process.  The variants compute every output with the same
+ * operations, so the choice never changes results.  Timing synchronises the stream once per new
+ * key; calls made while their stream is being captured into a CUDA graph use the current choice
+ * without timing.  Untuned keys use defaults measured on GB300.  When the environment variable
+ * AMM_TUNE_CACHE names a file, the table is loaded from it at first use (a file that does not
+ * parse is ignored) and written back, in the text form of amm_autotune_export, after every new
+ * choice, so later processes start tuned.
  */
 amm_status_t amm_set_autotune(int32_t on);
 
@@ -464,9 +470,12 @@ amm_status_t amm_autotune_export(char* host_buf, int64_t cap, int64_t* len);
 
 /*
  * Install choices written by amm_autotune_export (they override entries for the same keys; a
- * choice in the table is used whether or not autotuning is on).  Every line is checked first: a
- * wrong header, a key whose length is not a circulant length of this build, a variant other than
- * 0 / 1 or trailing text returns AMM_ERR_INVALID_ARG with nothing installed.  Host only.
+ * choice in the table is used whether or not autotuning is on).  A key is kernel << 24 | length << 3
+ * | flags (kernel 0: spectral apply, flags = 4 row + 2 reversed pairing + BF16; kernels 1, 2, 3:
+ * inverse cycle transform, column and row backward spectra, flags 0).  Every line is checked
+ * first: a wrong header, an unknown kernel, flags on a kernel without them, a length that is not a
+ * circulant length of this build, a variant other than 0 / 1 or trailing text returns
+ * AMM_ERR_INVALID_ARG with nothing installed.  Host only.
  */
 amm_status_t amm_autotune_import(const char* host_text);
 

@@ -560,18 +560,24 @@ amm_status_t amm::cd_backward(Handle* a, Handle* b, const float* G, int64_t ldg,
     STEP(cd_rho(n, K, tw, ca.so.dlist, ca.so.counts + 1, ca.cap, RX, ca.so.counts + 1, cb.so.counts + 1, st));
     STEP(cd_residual(n, RX, tw, ca.so.vfull, 3, ca.so.counts + 1, dA, st, ldda, 1, cb.so.counts + 1));
   }
+  // the dense dA_w and Im A~ below come from A's half spectrum: the stored one, or (store_spectra = 0)
+  // computed again from A
+  const float2* RA = nullptr;
+  float2* RA_temp = nullptr;
+  if (dB && e == cudaSuccess) e = cd_spectrum_of(a, &RA, &RA_temp, st);
+  if (RA_temp) tmp.push_back(RA_temp);
   if (dB) {
     // A~_w^T G (columns of G, coefficient L^A_t(t - p)), then the projection terms of dA^T G
     STEP(cd_apply(n, false, G, ldg, false, n, tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr, nullptr, dB, lddb, acc_b,
                   st, 1));
     STEP(bw_spectrum(n, true, G, ldg, tw, X1, st));
-    STEP(cd_residual(n, ca.R, tw, ca.so.wfull, 0, nullptr, T, st, n, 0));  // dA_w
+    STEP(cd_residual(n, RA, tw, ca.so.wfull, 0, nullptr, T, st, n, 0));  // dA_w
     STEP(bw_spectrum(n, true, T, n, tw, X2, st));
     STEP(cd_sddmm(n, X2, X1, cb.so.ulist, cb.so.counts, cb.cap, K, nullptr, nullptr, st));
     STEP(cd_rho(n, K, tw, cb.so.ulist, cb.so.counts, cb.cap, RX, nullptr, nullptr, st));
     STEP(cd_residual(n, RX, tw, cb.so.wfull, 2, nullptr, dB, st, lddb, 1));
     // unpaired: (i v_s) R_s(Y_A^T G) D^s with Y_A = Im A~
-    STEP(cd_residual(n, ca.R, tw, ca.so.vfull, 1, ca.so.counts + 1, T, st, n, 0, cb.so.counts + 1));
+    STEP(cd_residual(n, RA, tw, ca.so.vfull, 1, ca.so.counts + 1, T, st, n, 0, cb.so.counts + 1));
     STEP(bw_spectrum(n, true, T, n, tw, X2, st, ca.so.counts + 1, cb.so.counts + 1));
     STEP(cd_sddmm(n, X2, X1, cb.so.dlist, cb.so.counts + 1, cb.cap, K, ca.so.counts + 1, cb.so.counts + 1, st));
     STEP(cd_rho(n, K, tw, cb.so.dlist, cb.so.counts + 1, cb.cap, RX, ca.so.counts + 1, cb.so.counts + 1, st));

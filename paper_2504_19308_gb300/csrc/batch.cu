@@ -1,14 +1,16 @@
 // Batches of independent first-order products of uneven sizes (for example the layers of an
 // LLM-shaped stack).  amm_batch_run executes every item (decompose A, decompose B, product, the
-// backward for items added with amm_batch_add_grad, release) on a small pool of streams forked
-// from the caller's stream.  With use_graph the first
+// backward for items added with amm_batch_add_grad, release) on a pool of 16 streams forked from
+// the caller's stream, the largest items first, each on the least loaded stream.  With use_graph the first
 // run executes eagerly once (building twiddle tables and setting kernel attributes, which must
 // not happen inside a capture), then captures the same work into one CUDA graph; every later
 // run is a single graph launch.  Device memory of the handles is stream-ordered, so inside the
 // graph it becomes graph allocation nodes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "../../include/amm.h"
@@ -29,7 +31,7 @@ struct amm_batch {
     int64_t lddc = 0, ldda = 0, lddb = 0;
   };
   std::vector<Item> items;
-  int nstreams = 8;
+  int nstreams = 16;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;  // one per stream (join) + fork
   cudaGraphExec_t exec = nullptr;
@@ -127,10 +129,24 @@ static amm_status_t run_items(amm_batch* b, cudaStream_t parent) {
   if ((e = cudaEventRecord(fork, parent)) != cudaSuccess) return cuda_fail(e, "batch fork");
   for (cudaStream_t s : b->streams)
     if ((e = cudaStreamWaitEvent(s, fork, 0)) != cudaSuccess) return cuda_fail(e, "batch fork wait");
+  // Longest first: items in descending order of their exact-product work m n p, each on the worker
+  // stream with the least work assigned so far (greedy longest-processing-time list scheduling), so
+  // the large products start first and the small ones fill the other streams around them.  Every
+  // item runs the same kernels whatever its stream, so the results do not depend on the order.
+  std::vector<size_t> order(b->items.size());
+  std::iota(order.begin(), order.end(), (size_t)0);
+  auto work = [&](size_t i) {
+    const auto& it = b->items[i];
+    return (double)it.m * (double)it.n * (double)it.p * (it.dC ? 3.0 : 1.0);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return work(x) > work(y); });
+  std::vector<double> load(b->streams.size(), 0.0);
   amm_status_t st = AMM_OK;
-  for (size_t i = 0; i < b->items.size() && st == AMM_OK; ++i) {
-    auto& it = b->items[i];
-    cudaStream_t s = b->streams[i % b->streams.size()];
+  for (size_t oi = 0; oi < order.size() && st == AMM_OK; ++oi) {
+    auto& it = b->items[order[oi]];
+    const size_t si = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[si] += work(order[oi]);
+    cudaStream_t s = b->streams[si];
     amm_handle_t ha = nullptr, hb = nullptr;
     st = amm_decompose(it.A, it.m, it.n, it.lda, (amm_dtype_t)it.dtype, (amm_method_t)it.method, it.k, &it.oa, s, &ha);
     if (st == AMM_OK)

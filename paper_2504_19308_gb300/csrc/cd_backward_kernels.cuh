@@ -21,6 +21,7 @@
 #include "fft.cuh"
 #include "kernels.h"
 #include "trace.h"
+#include "tune.cuh"
 
 namespace amm {
 
@@ -273,17 +274,17 @@ __global__ void __launch_bounds__(NT) cd_rho_kernel(const float2* __restrict__ K
 
 // ============================================================================ launchers
 template <int N> struct BwCfg {
-  // row spectra: two CTAs per SM for 1024 <= N < 6144 (one CTA of 512 threads at 128 registers
-  // would fill the register file); column spectra: four signals per 512-thread CTA, measured
-  // faster at N = 4096 (60 vs 70 us; the row form the other way round, 47 vs 54 us)
-  static constexpr bool HALF = N >= 1024 && N < 6144;
-  static constexpr int S_FULL = (N >= 16384) ? 1 : (N >= 6144) ? 2 : 4;
-  static constexpr int S = HALF ? 2 : S_FULL;                      // row spectra
-  static constexpr int NT = HALF ? fft_threads(N) / 2 : fft_threads(N);
-  static constexpr int S_COL = S_FULL;                             // column spectra
-  static constexpr int NT_COL = fft_threads(N);
+  // variant 0: S signals per CTA of fft_threads(N); variant 1: half the signals and threads (two
+  // CTAs per SM where one 512-thread CTA at 128 registers would fill the register file).  Both are
+  // autotuned per direction; defaults measured at N = 4096: columns variant 0 (60 vs 70 us), rows
+  // variant 1 for 1024 <= N < 6144 (47 vs 54 us)
+  static constexpr int S = (N >= 16384) ? 1 : (N >= 6144) ? 2 : 4;
+  static constexpr int NT = fft_threads(N);
+  static constexpr bool HAS_V1 = S >= 2 && NT >= 64;
+  static constexpr int S1 = HAS_V1 ? S / 2 : S, NT1S = HAS_V1 ? NT / 2 : NT;
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
-  static constexpr size_t SMEM_COL = sizeof(float2) * S_COL * fft_padded_len(N);
+  static constexpr size_t SMEM1 = sizeof(float2) * S1 * fft_padded_len(N);
+  static constexpr int ROW_DEFAULT = (HAS_V1 && N >= 1024 && N < 6144) ? 1 : 0;
   static constexpr int NT1 = (N >= 1024) ? 256 : (N >= 64 ? 64 : N);
 };
 
@@ -292,27 +293,50 @@ template <int N> struct BwOps {
   static cudaError_t attrs() {
     static DeviceOnce once;
     return once([] {
-      cudaError_t r = cudaFuncSetAttribute((const void*)bw_spectrum_kernel<N, C::S, C::NT, true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-      if (r == cudaSuccess)
-        r = cudaFuncSetAttribute((const void*)bw_spectrum_kernel<N, C::S_COL, C::NT_COL, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_COL);
+      cudaError_t r = cudaSuccess;
+      for (const void* f : {(const void*)bw_spectrum_kernel<N, C::S, C::NT, true>,
+                            (const void*)bw_spectrum_kernel<N, C::S, C::NT, false>})
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      for (const void* f : {(const void*)bw_spectrum_kernel<N, C::S1, C::NT1S, true>,
+                            (const void*)bw_spectrum_kernel<N, C::S1, C::NT1S, false>})
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM1);
       if (r == cudaSuccess)
         r = cudaFuncSetAttribute((const void*)cd_rho_kernel<N, C::NT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(float2) * fft_padded_len(N)));
       return r;
     });
   }
+  template <int V>
+  static cudaError_t spectrum_v(bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh,
+                                const int32_t* g0, const int32_t* g1, cudaStream_t st) {
+    constexpr int S_ = V ? C::S1 : C::S, NT_ = V ? C::NT1S : C::NT;
+    constexpr size_t SM_ = V ? C::SMEM1 : C::SMEM;
+    if (row) bw_spectrum_kernel<N, S_, NT_, true><<<N / (2 * S_), NT_, SM_, st>>>(X, ldx, tw, Xh, g0, g1);
+    else bw_spectrum_kernel<N, S_, NT_, false><<<N / (2 * S_), NT_, SM_, st>>>(X, ldx, tw, Xh, g0, g1);
+    return cudaGetLastError();
+  }
   static cudaError_t spectrum(bool row, const float* X, int64_t ldx, const float2* tw, float2* Xh,
                               const int32_t* g0, const int32_t* g1, cudaStream_t st) {
     cudaError_t e = attrs();
     if (e != cudaSuccess) return e;
-    if (row)
-      bw_spectrum_kernel<N, C::S, C::NT, true><<<N / (2 * C::S), C::NT, C::SMEM, st>>>(X, ldx, tw, Xh, g0, g1);
-    else
-      bw_spectrum_kernel<N, C::S_COL, C::NT_COL, false><<<N / (2 * C::S_COL), C::NT_COL, C::SMEM_COL, st>>>(
-          X, ldx, tw, Xh, g0, g1);
-    return cudaGetLastError();
+    int v = 0;
+    if (C::HAS_V1 && g0 == nullptr) {  // gated launches use the current choice (the gate may skip the work)
+      float2* scratch = nullptr;
+      v = tune_pick(tune_key(row ? TUNE_BW_ROW : TUNE_BW_COL, N, 0), 2, row ? C::ROW_DEFAULT : 0, st,
+                    [&](int cand) -> cudaError_t {
+                      if (!scratch) {
+                        cudaError_t e2 = dev_alloc((void**)&scratch, sizeof(float2) * (N / 2 + 1) * (size_t)N, st);
+                        if (e2 != cudaSuccess) return e2;
+                      }
+                      return cand ? spectrum_v<1>(row, X, ldx, tw, scratch, nullptr, nullptr, st)
+                                  : spectrum_v<0>(row, X, ldx, tw, scratch, nullptr, nullptr, st);
+                    });
+      if (scratch) dev_free(scratch, st);
+    } else if (C::HAS_V1) {
+      const int t = cd_tune_get(tune_key(row ? TUNE_BW_ROW : TUNE_BW_COL, N, 0));
+      v = t >= 0 ? t : (row ? C::ROW_DEFAULT : 0);
+    }
+    return v ? spectrum_v<1>(row, X, ldx, tw, Xh, g0, g1, st) : spectrum_v<0>(row, X, ldx, tw, Xh, g0, g1, st);
   }
   static cudaError_t sddmm(const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
                            float2* K, const int32_t* g0, const int32_t* g1, cudaStream_t st) {

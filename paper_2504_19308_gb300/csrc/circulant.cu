@@ -21,6 +21,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -300,24 +303,56 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
   }
 
 // ---------------------------------------------------------------------------- autotuner table
+static bool cd_tune_parse(const char* text, bool (*length_ok)(int64_t));
+// The table persists across processes through the text file named by the environment variable
+// AMM_TUNE_CACHE: the first lookup loads it (a file that does not parse is ignored), and every
+// newly timed choice rewrites it (written to a temporary name, then renamed).
 namespace {
 std::mutex g_tune_mu;
 std::unordered_map<int, int> g_tune;
+std::once_flag g_tune_loaded;
+
+const char* tune_cache_path() {
+  const char* p = std::getenv("AMM_TUNE_CACHE");
+  return (p && *p) ? p : nullptr;
+}
+
+void tune_cache_load() {
+  const char* path = tune_cache_path();
+  if (!path) return;
+  std::ifstream f(path);
+  if (!f) return;
+  std::string text((std::istreambuf_iterator<char>(f)), std::istreambuf_iterator<char>());
+  cd_tune_parse(text.c_str(), cd_length_ok);
+}
 }  // namespace
 
 int cd_tune_get(int key) {
+  std::call_once(g_tune_loaded, tune_cache_load);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(key);
   return it == g_tune.end() ? -1 : it->second;
 }
 
 void cd_tune_set(int key, int variant) {
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = variant;
+  std::call_once(g_tune_loaded, tune_cache_load);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = variant;
+  }
+  if (const char* path = tune_cache_path()) {
+    const std::string tmp = std::string(path) + ".tmp";
+    {
+      std::ofstream f(tmp, std::ios::trunc);
+      f << cd_tune_dump();
+    }
+    std::rename(tmp.c_str(), path);
+  }
 }
 
 // The table as text: a header line, then "key variant" per line in ascending key order.
 std::string cd_tune_dump() {
+  std::call_once(g_tune_loaded, tune_cache_load);
   std::vector<std::pair<int, int>> v;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -329,9 +364,18 @@ std::string cd_tune_dump() {
   return out;
 }
 
-// Parse text written by cd_tune_dump; every entry is checked before any is installed.  A key
-// encodes (length, direction, reversed, element type) as N * 8 + flags; the variant is 0 or 1.
+// Parse text written by cd_tune_dump; every entry is checked before any is installed.  A key is
+// kernel << 24 | N << 3 | flags (tune.cuh): kernel 0, the spectral apply, with flags (direction,
+// reversed pairing, element type); kernels 1-3 (inverse cycle transform, column and row backward
+// spectra) with flags 0.  The variant is 0 or 1.
+static bool cd_tune_parse(const char* text, bool (*length_ok)(int64_t));
+
 bool cd_tune_load(const char* text, bool (*length_ok)(int64_t)) {
+  std::call_once(g_tune_loaded, tune_cache_load);
+  return cd_tune_parse(text, length_ok);
+}
+
+static bool cd_tune_parse(const char* text, bool (*length_ok)(int64_t)) {
   std::istringstream in(text);
   std::vector<std::string> tok;
   for (std::string t; in >> t;) tok.push_back(t);
@@ -351,7 +395,9 @@ bool cd_tune_load(const char* text, bool (*length_ok)(int64_t)) {
   for (size_t i = 2; i < tok.size(); i += 2) {
     long long key, var;
     if (!integer(tok[i], &key) || !integer(tok[i + 1], &var)) return false;
-    if (key > (1LL << 30) || !length_ok(key / 8) || (var != 0 && var != 1)) return false;
+    const long long kid = key >> 24, n = (key >> 3) & 0x1FFFFF, flags = key & 7;
+    if (kid > TUNE_BW_ROW || (kid != TUNE_APPLY && flags != 0) || !length_ok(n) || (var != 0 && var != 1))
+      return false;
     v.emplace_back((int)key, (int)var);
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -408,6 +454,7 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
 
 cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* list, const float* coef,
                      const int32_t* count, int cap, int imag_coef, float2* L, cudaStream_t st) {
+  if (!R || !L) return cudaErrorInvalidValue;
   AMM_TRACE("cd_eigen", st);
   AMM_DISPATCH_POW2(n, return CdOps<NN>::eigen(R, tw, list, coef, count, cap, imag_coef, L, st));
   return cd_eigen_r3(n, R, tw, list, coef, count, cap, imag_coef, L, st);
@@ -415,6 +462,7 @@ cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* li
 
 cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
                         float* X, cudaStream_t st, int64_t ldx, int accumulate, const int32_t* dcount2) {
+  if (!R || !X) return cudaErrorInvalidValue;  // e.g. a released spectrum (store_spectra = 0) not recomputed
   if (ldx <= 0) ldx = n;
   AMM_TRACE_W(mode == 0 ? "cd_residual" : (mode == 1 ? "cd_residual_imag" : "cd_project"), st, 0.0,
               (mode & 1) ? 0.0 : (n / 2 + 1.0) * n * 8 + (double)n * n * 4 * (accumulate ? 2 : 1), nullptr);

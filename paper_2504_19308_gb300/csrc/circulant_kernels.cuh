@@ -11,6 +11,7 @@
 #include "fft.cuh"
 #include "kernels.h"
 #include "trace.h"
+#include "tune.cuh"
 
 namespace amm {
 
@@ -326,18 +327,18 @@ __global__ void __launch_bounds__(NT) cd_apply_kernel(const T* __restrict__ X, i
 }
 
 // ============================================================================ host launchers
-// autotuner table of the spectral-apply variants (circulant.cu): -1 = not timed yet
-int cd_tune_get(int key);
-void cd_tune_set(int key, int variant);
 
 template <int N> struct CdCfg {
   static constexpr int S = (N >= 16384) ? 1 : (N >= 6144) ? 2 : 4;  // packed signals per CTA
   static constexpr int NT = fft_threads(N);          // threads per CTA
   static constexpr size_t SMEM = sizeof(float2) * S * fft_padded_len(N);
-  // inverse cycle transform: two packed signals per 512-thread CTA at N = 4096 (measured 96 vs 115 us
-  // with four), the spectral configuration elsewhere
-  static constexpr int S_RES = (N == 4096) ? 2 : S;
-  static constexpr size_t SMEM_RES = sizeof(float2) * S_RES * fft_padded_len(N) + sizeof(float) * N;  // + coefficients
+  // inverse cycle transform: the spectral configuration (variant 0) or half the packed signals at
+  // the same threads (variant 1, measured faster at N = 4096: 96 vs 115 us); autotuned, variant 1
+  // by default at N = 4096
+  static constexpr int S_RES1 = S >= 2 ? S / 2 : S;
+  static constexpr bool HAS_RES1 = S >= 2;
+  static constexpr size_t SMEM_RES = sizeof(float2) * S * fft_padded_len(N) + sizeof(float) * N;  // + coefficients
+  static constexpr size_t SMEM_RES1 = sizeof(float2) * S_RES1 * fft_padded_len(N) + sizeof(float) * N;
   // second spectral-apply variant for the autotuner: half the packed signals and threads per CTA
   // (more, smaller CTAs per SM; each coefficient load serves half as many signals)
   static constexpr bool HAS_V1 = S >= 2 && NT >= 64;
@@ -354,7 +355,8 @@ template <int N> static cudaError_t set_smem_attrs_now() {
   };
   s((const void*)cd_spectrum_kernel<N, C::S, C::NT, float>, C::SMEM);
   s((const void*)cd_spectrum_kernel<N, C::S, C::NT, __nv_bfloat16>, C::SMEM);
-  s((const void*)cd_residual_kernel<N, C::S_RES, C::NT>, C::SMEM_RES);
+  s((const void*)cd_residual_kernel<N, C::S, C::NT>, C::SMEM_RES);
+  s((const void*)cd_residual_kernel<N, C::S_RES1, C::NT>, C::SMEM_RES1);
   s((const void*)cd_apply_kernel<N, C::S, C::NT, false, false, float>, C::SMEM);
   s((const void*)cd_apply_kernel<N, C::S, C::NT, true, true, float>, C::SMEM);
   s((const void*)cd_apply_kernel<N, C::S, C::NT, true, true, __nv_bfloat16>, C::SMEM);
@@ -401,13 +403,35 @@ template <int N> struct CdOps {
     cd_eigen_kernel<N, NT1><<<cap, NT1, sm, st>>>(R, tw, list, coef, count, imag_coef, L);
     return cudaGetLastError();
   }
+  template <int V>
+  static cudaError_t residual_v(const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
+                                const int32_t* dcount2, float* X, int64_t ldx, int accumulate, cudaStream_t st) {
+    constexpr int S_ = V ? C::S_RES1 : C::S;
+    constexpr size_t SM_ = V ? C::SMEM_RES1 : C::SMEM_RES;
+    cd_residual_kernel<N, S_, C::NT><<<N / (2 * S_), C::NT, SM_, st>>>(R, tw, g, mode, dcount, dcount2, X, ldx,
+                                                                       accumulate);
+    return cudaGetLastError();
+  }
   static cudaError_t residual(const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
                               const int32_t* dcount2, float* X, int64_t ldx, int accumulate, cudaStream_t st) {
     const cudaError_t attr = set_smem_attrs<N>();
     if (attr != cudaSuccess) return attr;
-    cd_residual_kernel<N, C::S_RES, C::NT><<<N / (2 * C::S_RES), C::NT, C::SMEM_RES, st>>>(R, tw, g, mode, dcount,
-                                                                                          dcount2, X, ldx, accumulate);
-    return cudaGetLastError();
+    int v = 0;
+    if (C::HAS_RES1) {
+      // timed on the dense-residual form (mode 0, a scratch output): the variants differ in CTA shape only
+      float* scratch = nullptr;
+      v = tune_pick(tune_key(TUNE_RESIDUAL, N, 0), 2, N == 4096 ? 1 : 0, st, [&](int cand) -> cudaError_t {
+        if (!scratch) {
+          cudaError_t e = dev_alloc((void**)&scratch, sizeof(float) * (size_t)N * N, st);
+          if (e != cudaSuccess) return e;
+        }
+        return cand ? residual_v<1>(R, tw, g, 0, nullptr, nullptr, scratch, N, 0, st)
+                    : residual_v<0>(R, tw, g, 0, nullptr, nullptr, scratch, N, 0, st);
+      });
+      if (scratch) dev_free(scratch, st);
+    }
+    return v ? residual_v<1>(R, tw, g, mode, dcount, dcount2, X, ldx, accumulate, st)
+             : residual_v<0>(R, tw, g, mode, dcount, dcount2, X, ldx, accumulate, st);
   }
   template <int V>
   static cudaError_t apply_v(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
@@ -442,42 +466,19 @@ template <int N> struct CdOps {
   static int variant(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
                      const int32_t* list, const float2* Lc, const int32_t* count, int rev, cudaStream_t st) {
     if (!C::HAS_V1) return 0;
-    const int key = N * 8 + (row ? 4 : 0) + ((rev < 0 ? row : rev != 0) ? 2 : 0) + (bf16 ? 1 : 0);
-    const int v = cd_tune_get(key);
-    if (v >= 0 || !amm_autotune_enabled()) return v < 0 ? 0 : v;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
-    float* scratch = nullptr;
-    if (dev_alloc((void**)&scratch, sizeof(float) * (size_t)N * nvec, st) != cudaSuccess) return 0;
+    const int key = tune_key(TUNE_APPLY, N, (row ? 4 : 0) + ((rev < 0 ? row : rev != 0) ? 2 : 0) + (bf16 ? 1 : 0));
     const int64_t lds = row ? N : nvec;
-    float best = 0.f;
-    int pick = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    for (int cand = 0; cand < 2 && e == cudaSuccess; ++cand) {
-      auto run = [&]() {
-        return cand ? apply_v<1>(row, X, ldx, bf16, nvec, tw, list, Lc, count, nullptr, nullptr, scratch, lds, 0, rev, st)
-                    : apply_v<0>(row, X, ldx, bf16, nvec, tw, list, Lc, count, nullptr, nullptr, scratch, lds, 0, rev, st);
-      };
-      e = run();  // warm-up
-      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-      for (int it = 0; it < 3 && e == cudaSuccess; ++it) e = run();
-      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e == cudaSuccess && (cand == 0 || ms < best)) {
-        best = ms;
-        pick = cand;
+    float* scratch = nullptr;
+    const int v = tune_pick(key, 2, 0, st, [&](int cand) -> cudaError_t {
+      if (!scratch) {
+        cudaError_t e = dev_alloc((void**)&scratch, sizeof(float) * (size_t)N * nvec, st);
+        if (e != cudaSuccess) return e;
       }
-    }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    dev_free(scratch, st);
-    if (e != cudaSuccess) return 0;
-    cd_tune_set(key, pick);
-    return pick;
+      return cand ? apply_v<1>(row, X, ldx, bf16, nvec, tw, list, Lc, count, nullptr, nullptr, scratch, lds, 0, rev, st)
+                  : apply_v<0>(row, X, ldx, bf16, nvec, tw, list, Lc, count, nullptr, nullptr, scratch, lds, 0, rev, st);
+    });
+    if (scratch) dev_free(scratch, st);
+    return v;
   }
   static cudaError_t apply(bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
                            const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,

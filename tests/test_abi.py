@@ -168,6 +168,46 @@ def test_autotune_table_round_trip(lib):
     assert lib.amm_autotune_import(None) == 1
 
 
+def test_autotune_keys_of_the_other_kernels(lib):
+    """Keys carry a kernel id above bit 24 (1: inverse cycle transform, 2 / 3: column / row backward
+    spectra, which have no flags); unknown ids and flags on those kernels are rejected."""
+    import paper_2504_19308_gb300 as amm
+    k = lambda kid, n, flags=0: (kid << 24) | (n << 3) | flags
+    amm.autotune_import("amm-autotune 1\n%d 1\n%d 0\n%d 1\n" % (k(1, 4096), k(2, 3072), k(3, 1024)))
+    table = dict(tuple(map(int, ln.split())) for ln in amm.autotune_export().splitlines()[1:])
+    assert table[k(1, 4096)] == 1 and table[k(2, 3072)] == 0 and table[k(3, 1024)] == 1
+    for bad in ("amm-autotune 1\n%d 1\n" % k(4, 4096), "amm-autotune 1\n%d 1\n" % k(1, 4096, 2),
+                "amm-autotune 1\n%d 1\n" % k(2, 40)):
+        with pytest.raises(RuntimeError, match="malformed"):
+            amm.autotune_import(bad)
+
+
+def _tune_child(env_path, code):
+    import subprocess
+    import sys
+    env = dict(os.environ, AMM_TUNE_CACHE=env_path)
+    r = subprocess.run([sys.executable, "-c", "import sys; sys.path.insert(0, %r)\n" % ROOT + code], env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return r.stdout
+
+
+def test_autotune_cache_file_is_loaded_at_first_use(lib, tmp_path):
+    """AMM_TUNE_CACHE names a text file of exported choices: a new process sees them before it tunes
+    anything; a file that does not parse is ignored (an empty table), not an error."""
+    path = str(tmp_path / "tune.txt")
+    k = 4096 * 8 + 4
+    with open(path, "w") as f:
+        f.write("amm-autotune 1\n%d 1\n%d 0\n" % (k, (1 << 24) | (4096 << 3)))
+    out = _tune_child(path, "import paper_2504_19308_gb300 as amm\nprint(amm.autotune_export())")
+    table = dict(tuple(map(int, ln.split())) for ln in out.strip().splitlines()[1:])
+    assert table == {k: 1, (1 << 24) | (4096 << 3): 0}
+    with open(path, "w") as f:
+        f.write("not a table\n")
+    out = _tune_child(path, "import paper_2504_19308_gb300 as amm\nprint(amm.autotune_export())")
+    assert out.strip() == "amm-autotune 1"
+
+
 def test_batch_host_logic(lib):
     """Batches record items on the host: arguments are checked when an item is added (before any
     item of the batch launches); a batch that never ran is destroyed without device work."""
