@@ -88,7 +88,8 @@ int64_t borrowed_extent(const Handle* h) {
   return (h->rows > 0 ? (h->rows - 1) * h->lda + h->cols : 0) * es;
 }
 
-cudaError_t write_node(Handle* h, const char* A0, const Outer& outer, Writer& w) {
+// A0 / ext: the caller's operand and its extent in bytes (the blocks of a blocked handle point into it)
+cudaError_t write_node(Handle* h, const char* A0, int64_t ext, const Outer& outer, Writer& w) {
   w.put<int32_t>(h->method);
   w.put<int32_t>(h->role);
   w.put<int32_t>(h->dtype);
@@ -117,7 +118,6 @@ cudaError_t write_node(Handle* h, const char* A0, const Outer& outer, Writer& w)
     int64_t offset;
   };
   std::vector<Ref> refs;
-  const int64_t ext = borrowed_extent(h);
   for (void** fp : fields) {
     const char* v = (const char*)*fp;
     Ref r{F_NULL, -1, 0};
@@ -165,7 +165,7 @@ cudaError_t write_node(Handle* h, const char* A0, const Outer& outer, Writer& w)
     }
   w.put<int32_t>((int32_t)h->blk.sub.size());
   for (Handle* s : h->blk.sub) {
-    cudaError_t e = write_node(s, A0, mine, w);
+    cudaError_t e = write_node(s, A0, ext, mine, w);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -290,7 +290,7 @@ extern "C" amm_status_t amm_handle_export(amm_handle_t h, void* host_buf, int64_
   w.put<uint32_t>(kMagic);
   w.put<int32_t>(kFormat);
   w.put<int32_t>(AMM_VERSION);
-  e = write_node(h, (const char*)h->A, Outer{}, w);
+  e = write_node(h, (const char*)h->A, borrowed_extent(h), Outer{}, w);
   if (e == cudaErrorInvalidValue) return fail(AMM_ERR_STATE, "amm_handle_export: a field points outside the handle");
   if (e != cudaSuccess) return cuda_fail(e, "amm_handle_export: download");
   *len = (int64_t)w.out.size();

@@ -48,13 +48,16 @@ def test_export_import_same_process_bit_identical():
         hB.close()
         C = amm.approx_matmul(iA, iB)
         assert torch.isfinite(C).all()
-    # a blocked circulant weight with ragged edges (its blocks read a zero-padded copy)
-    hx = amm.decompose(dev32(torch, S.rng(21, 4).standard_normal((256, 384))), "svd", 16, "left",
-                       sketch=dev32(torch, S.sketch(384, 16, 21, 0)))
-    hw = amm.decompose(W, "circulant", 5, "right", block=128)
-    iw = amm.import_handle(hw.export(), W, "circulant", 5, "right", block=128)
-    assert torch.equal(amm.approx_matmul(hx, hw), amm.approx_matmul(hx, iw))
-    assert np.array_equal(hw.selection(), iw.selection())
+    # blocked circulant weights: blocks of the operand itself (384 x 640 in 128-blocks) and of a
+    # zero-padded copy (400 x 600 padded to 512 x 640)
+    for Wb in (W, dev32(torch, S.rng(21, 5).standard_normal((400, 600)) + 0.5)):
+        kx = Wb.shape[0]
+        hx = amm.decompose(dev32(torch, S.rng(21, 4).standard_normal((256, kx))), "svd", 16, "left",
+                           sketch=dev32(torch, S.sketch(kx, 16, 21, 0)))
+        hw = amm.decompose(Wb, "circulant", 5, "right", block=128)
+        iw = amm.import_handle(hw.export(), Wb, "circulant", 5, "right", block=128)
+        assert torch.equal(amm.approx_matmul(hx, hw), amm.approx_matmul(hx, iw))
+        assert np.array_equal(hw.selection(), iw.selection())
 
 
 def test_import_rejects_malformed_strings_and_other_operands():
