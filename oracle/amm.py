@@ -338,7 +338,7 @@ def truncate_fourier_left(a: np.ndarray, k: int, forced=None) -> Truncation:
     mask = topk_mask_rows(magnitudes_mirrored_rows(at), k, forced)
     at_a = np.where(mask, at, 0)
     # space-domain form A_s = A~_a W, so that A_s B = A~_a (W B) (Alg. 5 line 5)
-    return Truncation("fourier", a, at_a @ unitary_W(n), None, T=at, mask=mask, T_a=at_a)
+    return Truncation("fourier", a, at_a @ unitary_W(n), None, T=at, mask=mask, T_a=at_a, side="left")
 
 
 def truncate_fourier_right(b: np.ndarray, k: int, forced=None) -> Truncation:
@@ -348,7 +348,7 @@ def truncate_fourier_right(b: np.ndarray, k: int, forced=None) -> Truncation:
     mask = topk_mask_rows(magnitudes_mirrored_rows(bt.T), k, forced).T
     bt_a = np.where(mask, bt, 0)
     # space-domain form B_s = W^* B~_a, so that dA B_s = (A~ - A~_a) B~_a (Alg. 5 line 6)
-    return Truncation("fourier", b, np.conj(unitary_W(n)).T @ bt_a, None, T=bt, mask=mask, T_a=bt_a)
+    return Truncation("fourier", b, np.conj(unitary_W(n)).T @ bt_a, None, T=bt, mask=mask, T_a=bt_a, side="right")
 
 
 def cycle_keys(a: np.ndarray) -> np.ndarray:
@@ -721,7 +721,14 @@ def frozen_product_blocked(ta: Truncation, tb: Truncation, a, b) -> np.ndarray:
 
 def project(t: Truncation, x: np.ndarray, adjoint: bool = False) -> np.ndarray:
     """The truncation's projector P (A~ = P(A)) applied to x, or its bilinear adjoint: circulant
-    P_S / P_{S-bar}, SVD Q Q^T x (self-adjoint), cycles (self-adjoint).  Reading R10: frozen."""
+    P_S / P_{S-bar}, SVD Q Q^T x (self-adjoint), cycles (self-adjoint), Fourier sparsifier with its
+    element mask M frozen (Section 2.4): left P(X) = (M o (X W^*)) W, adjoint (M o (X W)) conj(W);
+    right P(X) = W^* (M o (W X)), adjoint W (M o (conj(W) X)) (W is symmetric).  Reading R10."""
+    if t.method == "fourier":
+        w = unitary_W(x.shape[1] if t.side == "left" else x.shape[0])
+        if t.side == "left":
+            return np.where(t.mask, x @ (w if adjoint else np.conj(w).T), 0) @ (np.conj(w) if adjoint else w)
+        return (w if adjoint else np.conj(w).T) @ np.where(t.mask, (np.conj(w) if adjoint else w) @ x, 0)
     if t.method == "circulant":
         n = x.shape[0]
         return project_circulant(x.astype(np.complex128), mirror(t.sel, n) if adjoint else t.sel)
@@ -733,8 +740,8 @@ def project(t: Truncation, x: np.ndarray, adjoint: bool = False) -> np.ndarray:
 
 
 def mixed_backward(ta: Truncation, tb: Truncation, g: np.ndarray):
-    """Gradients of <G, Re M> for operands truncated by different methods (circulant, SVD, cycle),
-    projectors frozen: the first-order map M = P_A(A) B + (A - P_A(A)) P_B(B) is bilinear, and
+    """Gradients of <G, Re M> for operands truncated by different methods (circulant, SVD, cycle,
+    Fourier sparsifier), projectors frozen: the first-order map M = P_A(A) B + (A - P_A(A)) P_B(B) is bilinear, and
     dA = Re[G B~^T + P_A'(G dB^T)], dB = Re[A~^T G + P_B'(dA^T G)] with P' each operand's adjoint."""
     da = g @ tb.approx.T + project(ta, g @ tb.resid.T, adjoint=True)
     db = ta.approx.T @ g + project(tb, ta.resid.T @ g, adjoint=True)

@@ -439,7 +439,7 @@ def test_backward_matches_bruteforce(method):
 _MIX3 = [(x, y) for x in ("circulant", "svd", "cycle") for y in ("circulant", "svd", "cycle") if x != y]
 
 
-@pytest.mark.parametrize("ma,mb", _MIX3)
+@pytest.mark.parametrize("ma,mb", _MIXED)
 def test_mixed_backward_matches_bruteforce(ma, mb):
     """Reading R10 for operands of different methods: the closed-form gradients (each operand's own
     adjoint projector) equal <G, M(E_ij)> of the frozen mixed map over every basis matrix, and the
@@ -460,12 +460,26 @@ def test_mixed_backward_matches_bruteforce(ma, mb):
     assert np.abs(da - bda).max() < 1e-12 and np.abs(db - bdb).max() < 1e-12
 
 
+def test_fourier_projector_is_the_truncation():
+    """Section 2.4 with the element masks frozen: P(A) = A~ on both sides, P is idempotent, and the
+    adjoint satisfies <Y, P(X)> = <P'(Y), X> for the plain (bilinear) pairing, on rectangular shapes."""
+    g = S.rng(62, 0)
+    a, b = g.standard_normal((5, 8)), g.standard_normal((8, 7))
+    ta, tb = O.truncate_fourier_left(a, 3), O.truncate_fourier_right(b, 2)
+    for t, x0, shape in ((ta, a, a.shape), (tb, b, b.shape)):
+        assert np.abs(O.project(t, x0) - t.approx).max() < 1e-13
+        x, y = g.standard_normal(shape), g.standard_normal(shape)
+        px = O.project(t, x)
+        assert np.abs(O.project(t, px) - px).max() < 1e-13
+        assert abs(np.sum(y * px) - np.sum(O.project(t, y, adjoint=True) * x)) < 1e-12
+
+
 def test_mixed_backward_same_method_reduces():
     """With both operands truncated by one method the mixed formula is that method's backward."""
     g = S.rng(58, 0)
     n = 8
     a, b, gr = g.standard_normal((n, n)), g.standard_normal((n, n)), g.standard_normal((n, n))
-    for method in ("circulant", "svd", "cycle"):
+    for method in ("circulant", "svd", "cycle", "fourier"):
         ta, tb = _truncs(method, a, b, 3, seed=58)
         da, db = O.mixed_backward(ta, tb, gr)
         ra, rb = O.backward(method, ta, tb, gr)
@@ -738,6 +752,30 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert OA.mu_circulant(O.circulant_spectrum(jn), [], 64.0) != pytest.approx(8.0)
     monkeypatch.setattr(OA, "mu_circulant", good_mu)
     assert OA.mu_circulant(O.circulant_spectrum(jn), [], 64.0) == pytest.approx(8.0)
+
+    # 9) Fourier adjoint projector with the conjugations swapped ((M o (X W^*)) W instead of
+    #    (M o (X W)) conj(W), i.e. the projector itself): the mixed backward leaves brute force once
+    #    the partner's residual is complex (a circulant selection that splits a conjugate pair; on
+    #    a real argument the two maps have the same real part)
+    n9 = 6
+    a9, b9, g9 = (S.rng(37, i).standard_normal((n9, n9)) for i in range(3))
+    k9 = next(k for k in range(1, n9) if set(O.truncate_circulant(b9, k).sel.tolist()) !=
+              set(O.mirror(O.truncate_circulant(b9, k).sel, n9).tolist()))
+    ta9, tb9 = O.truncate_fourier_left(a9, 2), O.truncate_circulant(b9, k9)
+    assert np.abs(tb9.resid.imag).max() > 1e-6
+    good_project = OA.project
+    monkeypatch.setattr(OA, "project", lambda t, x, adjoint=False: good_project(t, x, False)
+                        if t.method == "fourier" else good_project(t, x, adjoint))
+    da9, _ = OA.mixed_backward(ta9, tb9, g9)
+    monkeypatch.setattr(OA, "project", good_project)
+    f9 = lambda x: np.sum(g9 * O.frozen_mixed_product(ta9, tb9, x, b9))
+    bda9 = np.zeros_like(a9)
+    for i, j in itertools.product(range(n9), range(n9)):
+        e = np.zeros_like(a9)
+        e[i, j] = 1.0
+        bda9[i, j] = f9(e) - f9(np.zeros_like(a9))
+    assert np.abs(da9 - bda9).max() > 1e-6
+    assert np.abs(OA.mixed_backward(ta9, tb9, g9)[0] - bda9).max() < 1e-12
 
 
 # --------------------------------------------------------------------------- spectral concentration
