@@ -471,8 +471,9 @@ amm_status_t amm_autotune_export(char* host_buf, int64_t cap, int64_t* len);
 /*
  * Install choices written by amm_autotune_export (they override entries for the same keys; a
  * choice in the table is used whether or not autotuning is on).  A key is kernel << 24 | length << 3
- * | flags (kernel 0: spectral apply, flags = 4 row + 2 reversed pairing + BF16; kernels 1, 2, 3:
- * inverse cycle transform, column and row backward spectra, flags 0).  Every line is checked
+ * | flags (kernel 0: spectral apply, flags = 4 row + 2 reversed pairing + BF16; kernel 1: inverse
+ * cycle transform, flag 1 = accumulating form; kernels 2, 3: column and row backward spectra,
+ * flags 0).  Every line is checked
  * first: a wrong header, an unknown kernel, flags on a kernel without them, a length that is not a
  * circulant length of this build, a variant other than 0 / 1 or trailing text returns
  * AMM_ERR_INVALID_ARG with nothing installed.  Host only.

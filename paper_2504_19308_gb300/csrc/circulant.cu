@@ -366,8 +366,9 @@ std::string cd_tune_dump() {
 
 // Parse text written by cd_tune_dump; every entry is checked before any is installed.  A key is
 // kernel << 24 | N << 3 | flags (tune.cuh): kernel 0, the spectral apply, with flags (direction,
-// reversed pairing, element type); kernels 1-3 (inverse cycle transform, column and row backward
-// spectra) with flags 0.  The variant is 0 or 1.
+// reversed pairing, element type); kernel 1, the inverse cycle transform, with flag 1 for its
+// accumulating form; kernels 2-3 (column and row backward spectra) with flags 0.  The variant is
+// 0 or 1.
 static bool cd_tune_parse(const char* text, bool (*length_ok)(int64_t));
 
 bool cd_tune_load(const char* text, bool (*length_ok)(int64_t)) {
@@ -396,7 +397,8 @@ static bool cd_tune_parse(const char* text, bool (*length_ok)(int64_t)) {
     long long key, var;
     if (!integer(tok[i], &key) || !integer(tok[i + 1], &var)) return false;
     const long long kid = key >> 24, n = (key >> 3) & 0x1FFFFF, flags = key & 7;
-    if (kid > TUNE_BW_ROW || (kid != TUNE_APPLY && flags != 0) || !length_ok(n) || (var != 0 && var != 1))
+    const long long max_flags = kid == TUNE_APPLY ? 7 : kid == TUNE_RESIDUAL ? 1 : 0;
+    if (kid > TUNE_BW_ROW || flags > max_flags || !length_ok(n) || (var != 0 && var != 1))
       return false;
     v.emplace_back((int)key, (int)var);
   }

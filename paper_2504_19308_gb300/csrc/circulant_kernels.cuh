@@ -418,15 +418,19 @@ template <int N> struct CdOps {
     if (attr != cudaSuccess) return attr;
     int v = 0;
     if (C::HAS_RES1) {
-      // timed on the dense-residual form (mode 0, a scratch output): the variants differ in CTA shape only
+      // one key for the overwriting and one for the accumulating form (flag 1: the read-modify-write
+      // of 16-byte row segments favours the full variant); timed with mode 0 on a scratch output --
+      // the variants differ in CTA shape only
+      const int acc = accumulate ? 1 : 0;
       float* scratch = nullptr;
-      v = tune_pick(tune_key(TUNE_RESIDUAL, N, 0), 2, N == 4096 ? 1 : 0, st, [&](int cand) -> cudaError_t {
+      v = tune_pick(tune_key(TUNE_RESIDUAL, N, acc), 2, (N == 4096 && !acc) ? 1 : 0, st, [&](int cand) -> cudaError_t {
         if (!scratch) {
           cudaError_t e = dev_alloc((void**)&scratch, sizeof(float) * (size_t)N * N, st);
+          if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, sizeof(float) * (size_t)N * N, st);
           if (e != cudaSuccess) return e;
         }
-        return cand ? residual_v<1>(R, tw, g, 0, nullptr, nullptr, scratch, N, 0, st)
-                    : residual_v<0>(R, tw, g, 0, nullptr, nullptr, scratch, N, 0, st);
+        return cand ? residual_v<1>(R, tw, g, 0, nullptr, nullptr, scratch, N, acc, st)
+                    : residual_v<0>(R, tw, g, 0, nullptr, nullptr, scratch, N, acc, st);
       });
       if (scratch) dev_free(scratch, st);
     }

@@ -176,8 +176,9 @@ def test_autotune_keys_of_the_other_kernels(lib):
     amm.autotune_import("amm-autotune 1\n%d 1\n%d 0\n%d 1\n" % (k(1, 4096), k(2, 3072), k(3, 1024)))
     table = dict(tuple(map(int, ln.split())) for ln in amm.autotune_export().splitlines()[1:])
     assert table[k(1, 4096)] == 1 and table[k(2, 3072)] == 0 and table[k(3, 1024)] == 1
+    amm.autotune_import("amm-autotune 1\n%d 0\n" % k(1, 4096, 1))     # the accumulating residual form
     for bad in ("amm-autotune 1\n%d 1\n" % k(4, 4096), "amm-autotune 1\n%d 1\n" % k(1, 4096, 2),
-                "amm-autotune 1\n%d 1\n" % k(2, 40)):
+                "amm-autotune 1\n%d 1\n" % k(2, 4096, 1), "amm-autotune 1\n%d 1\n" % k(2, 40)):
         with pytest.raises(RuntimeError, match="malformed"):
             amm.autotune_import(bad)
 
