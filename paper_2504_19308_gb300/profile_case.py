@@ -7,10 +7,15 @@
 k = 32/128, Fourier and cycle sparsifiers k = 41, each decomposed, multiplied and differentiated).
 --le1pct runs the products of the n = 4096 General U(0,1) x Toeplitz U(0,1) step that reach <= 1%
 error (circulant k = 1/5/9, Fourier sparsifier k = 60), each decomposed, multiplied, differentiated.
+--headline runs the throughput step of the bench: those four, the randomized SVD at k = 16 and 32 on
+the same pair, and the randomized SVD at k = 256 on the n = 512 pair Q1 diag(e^{-i/32}) Q2^T +
+1e-3 N(0,1), each decomposed, multiplied and differentiated.
 
 Inputs are the seeded power-law pair of the bench (sigma_i = i^-1.5 + N(0, 1e-4)), drawn as
 Gaussian-plus-spectrum matrices without QR when --fast is given (same sizes, cheaper to make).
-Each repeat is wrapped in an NVTX range "case" so that a profiler can select it.  --trace times
+The autotuner is on (as in the bench), so the first repeat times the kernel variants; it is
+wrapped in an NVTX range "warmup", every later repeat in a range "case" that a profiler can
+select (ncu --nvtx --nvtx-include "case/").  --trace times
 every library launch of the repeats after the first with CUDA events on its own stream (the
 library's launch trace) and prints one JSON object {kernel: [launches, total ms, ...]} per run.
 """
@@ -37,9 +42,10 @@ def main():
     ap.add_argument("--step", action="store_true")
     ap.add_argument("--trace", action="store_true")
     ap.add_argument("--le1pct", action="store_true")
+    ap.add_argument("--headline", action="store_true")
     a = ap.parse_args()
     n, k = a.n, a.k
-    if a.le1pct:
+    if a.le1pct or a.headline:
         x, y = synth.general_times_toeplitz(n, seed=0)
     elif a.fast:
         g = synth.rng(0, 0)
@@ -47,11 +53,20 @@ def main():
     else:
         x, y = synth.powerlaw_pair(n, seed=0)
     dev = torch.device("cuda")
+    amm.load_library()
+    amm.set_autotune(True)
     A = torch.tensor(x, dtype=torch.float32, device=dev)
     B = torch.tensor(y, dtype=torch.float32, device=dev)
     G = torch.randn((n, n), device=dev)
     ks = -(-n // 100)
-    if a.le1pct:
+    small = None
+    if a.headline:
+        cases = [("circulant", 1, True), ("circulant", 5, True), ("circulant", 9, True), ("svd", 16, True),
+                 ("svd", 32, True), ("fourier", 60, True)]
+        x5, y5 = synth.exp32_pair(512, seed=0)
+        small = (torch.tensor(x5, dtype=torch.float32, device=dev), torch.tensor(y5, dtype=torch.float32, device=dev),
+                 torch.randn((512, 512), device=dev))
+    elif a.le1pct:
         cases = [("circulant", 1, True), ("circulant", 5, True), ("circulant", 9, True), ("fourier", 60, True)]
     elif a.step:
         cases = [("circulant", 16, True), ("circulant", 64, True), ("circulant", 256, True), ("svd", 32, True),
@@ -63,11 +78,12 @@ def main():
         if method == "svd":
             sk[kk] = tuple(torch.tensor(synth.sketch(n, kk, 0, side), dtype=torch.float32, device=dev)
                            for side in (0, 1))
+    sk_small = tuple(torch.tensor(synth.sketch(512, 256, 0, side), dtype=torch.float32, device=dev) for side in (0, 1))
     for rep in range(a.repeat):
         if a.trace and rep == 1:  # the first repeat warms up (autotuning, allocations)
             torch.cuda.synchronize()
             amm.trace_enable(True)
-        torch.cuda.nvtx.range_push("case")
+        torch.cuda.nvtx.range_push("warmup" if rep == 0 and a.repeat > 1 else "case")
         for method, kk, bwd in cases:
             sa, sb = sk.get(kk, (None, None)) if method == "svd" else (None, None)
             hA = amm.decompose(A, method, kk, "left", sketch=sa)
@@ -75,6 +91,13 @@ def main():
             C = amm.approx_matmul(hA, hB)
             if bwd:
                 amm.approx_matmul_backward(hA, hB, G)
+            hA.close()
+            hB.close()
+        if small is not None:  # rSVD k = 256 on the n = 512 pair
+            hA = amm.decompose(small[0], "svd", 256, "left", sketch=sk_small[0])
+            hB = amm.decompose(small[1], "svd", 256, "right", sketch=sk_small[1])
+            amm.approx_matmul(hA, hB)
+            amm.approx_matmul_backward(hA, hB, small[2])
             hA.close()
             hB.close()
         torch.cuda.nvtx.range_pop()
@@ -86,7 +109,8 @@ def main():
         per = a.repeat - 1
         print(json.dumps({"repeats": per, "launches": launches,
                           "ms_per_repeat": {name: round(v[1] / per, 4) for name, v in sorted(kernels.items())}}))
-    print("ok", "le1pct" if a.le1pct else ("step" if a.step else a.method), n, k, float(C.abs().sum()))
+    print("ok", "headline" if a.headline else "le1pct" if a.le1pct else ("step" if a.step else a.method), n, k,
+          float(C.abs().sum()))
 
 
 if __name__ == "__main__":
