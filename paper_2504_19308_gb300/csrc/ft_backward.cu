@@ -108,11 +108,13 @@ __global__ void __launch_bounds__(256) ft_bw_maskwalk_kernel(const float* __rest
 
 // ============================================================================ P_A(G dB~^T)
 // For each kept (i, q) of A~_a:  XAT[q][i] += sum_c G(i, c) B~(q, c) [(q, c) not kept in B~_a].
-// CTA per row i (G row shared through L1), warp per kept entry, lanes over c.
+// CTA per row i (G row shared through L1), warp per kept entry, lanes over c.  maskB NULL: no
+// entry excluded (B~ the transform of a dense residual, for mixed-method gradients); imag: the sum
+// is multiplied by i before it is added.
 __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__ G, int64_t ldg,
                                                        const float2* __restrict__ Bt, const uint32_t* __restrict__ maskB,
                                                        int mwB, const int32_t* __restrict__ selA, int ka, int n, int m,
-                                                       int p, float2* __restrict__ XAT) {
+                                                       int p, float2* __restrict__ XAT, int imag) {
   const int i = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float* grow = G + (int64_t)i * ldg;
@@ -120,10 +122,10 @@ __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__
     const int q = __ldg(selA + (int64_t)i * ka + u);
     const bool mir = q > n / 2;
     const float2* brow = Bt + (int64_t)(mir ? n - q : q) * p;
-    const uint32_t* mrow = maskB + (int64_t)q * mwB;
+    const uint32_t* mrow = maskB ? maskB + (int64_t)q * mwB : nullptr;
     float ax = 0.f, ay = 0.f;
     for (int c = lane; c < p; c += 32) {
-      if ((__ldg(mrow + (c >> 5)) >> (c & 31)) & 1u) continue;  // kept in B~_a: not in dB~
+      if (maskB != nullptr && ((__ldg(mrow + (c >> 5)) >> (c & 31)) & 1u)) continue;  // kept in B~_a: not in dB~
       const float g = __ldg(grow + c);
       const float2 b = __ldg(brow + c);
       ax = fmaf(g, b.x, ax);
@@ -137,18 +139,20 @@ __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__
     if (lane == 0) {
       float2* x = XAT + (int64_t)q * m + i;
       const float2 v = *x;
-      *x = make_float2(v.x + ax, v.y + (mir ? -ay : ay));
+      const float2 d = make_float2(ax, mir ? -ay : ay);
+      *x = imag ? make_float2(v.x - d.y, v.y + d.x) : make_float2(v.x + d.x, v.y + d.y);
     }
   }
 }
 
 // ============================================================================ P_B(dA~^T G)
 // For each kept (q, c) of B~_a:  XB[q][c] += sum_i A~(i, q) [(i, q) not kept in A~_a] G(i, c).
-// CTA per column c (GT row shared through L1), warp per kept entry, lanes over i.
+// CTA per column c (GT row shared through L1), warp per kept entry, lanes over i.  maskA NULL: no
+// entry excluded; imag: the sum is multiplied by i before it is added (as for ft_bw_pa_kernel).
 __global__ void __launch_bounds__(256) ft_bw_pb_kernel(const float* __restrict__ GT, const float2* __restrict__ AtT,
                                                        const uint32_t* __restrict__ maskA, int mwA,
                                                        const int32_t* __restrict__ selB, int kb, int n, int m, int p,
-                                                       float2* __restrict__ XB) {
+                                                       float2* __restrict__ XB, int imag) {
   const int c = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float* grow = GT + (int64_t)c * m;
@@ -156,10 +160,10 @@ __global__ void __launch_bounds__(256) ft_bw_pb_kernel(const float* __restrict__
     const int q = __ldg(selB + (int64_t)c * kb + u);
     const bool mir = q > n / 2;
     const float2* arow = AtT + (int64_t)(mir ? n - q : q) * m;
-    const uint32_t* mrow = maskA + (int64_t)q * mwA;
+    const uint32_t* mrow = maskA ? maskA + (int64_t)q * mwA : nullptr;
     float ax = 0.f, ay = 0.f;
     for (int i = lane; i < m; i += 32) {
-      if ((__ldg(mrow + (i >> 5)) >> (i & 31)) & 1u) continue;  // kept in A~_a: not in dA~
+      if (maskA != nullptr && ((__ldg(mrow + (i >> 5)) >> (i & 31)) & 1u)) continue;  // kept in A~_a: not in dA~
       const float g = __ldg(grow + i);
       const float2 a = __ldg(arow + i);
       ax = fmaf(g, a.x, ax);
@@ -173,7 +177,8 @@ __global__ void __launch_bounds__(256) ft_bw_pb_kernel(const float* __restrict__
     if (lane == 0) {
       float2* x = XB + (int64_t)q * p + c;
       const float2 v = *x;
-      *x = make_float2(v.x + ax, v.y + (mir ? -ay : ay));
+      const float2 d = make_float2(ax, mir ? -ay : ay);
+      *x = imag ? make_float2(v.x - d.y, v.y + d.x) : make_float2(v.x + d.x, v.y + d.y);
     }
   }
 }
@@ -299,7 +304,7 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
     if (e == cudaSuccess) {
       AMM_TRACE_W("ft_bw_pa", st, 4.0 * m * (double)a.ka * p,
                   4.0 * m * (double)p + 8.0 * (n / 2 + 1.0) * p + 16.0 * m * (double)a.ka, nullptr);
-      ft_bw_pa_kernel<<<m, 256, 0, st>>>(a.G, a.ldg, a.Bt, a.maskB, mwB, a.selA, a.ka, n, m, p, XAT);
+      ft_bw_pa_kernel<<<m, 256, 0, st>>>(a.G, a.ldg, a.Bt, a.maskB, mwB, a.selA, a.ka, n, m, p, XAT, 0);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = ft_bw_real(n, true, XAT, m, a.tw, a.dA, a.ldda, st);
@@ -315,7 +320,7 @@ cudaError_t ft_backward(const FtBwArgs& a, cudaStream_t st) {
     if (e == cudaSuccess) {
       AMM_TRACE_W("ft_bw_pb", st, 4.0 * p * (double)a.kb * m,
                   4.0 * m * (double)p + 8.0 * (n / 2 + 1.0) * m + 16.0 * p * (double)a.kb, nullptr);
-      ft_bw_pb_kernel<<<p, 256, 0, st>>>(GT, a.AtT, a.maskA, mwA, a.selB, a.kb, n, m, p, XB);
+      ft_bw_pb_kernel<<<p, 256, 0, st>>>(GT, a.AtT, a.maskA, mwA, a.selB, a.kb, n, m, p, XB, 0);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = ft_bw_real(n, false, XB, p, a.tw, a.dB, a.lddb, st);

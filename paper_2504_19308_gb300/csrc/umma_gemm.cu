@@ -164,14 +164,18 @@ struct UmmaCfg {
   static constexpr int MMA_K = 32 / ELEM;                    // K per tcgen05.mma
   static constexpr int A_BYTES = UM_BM * 128;                // 16 KiB A tile
   static constexpr int B_BYTES = BN * 128;                   // BN rows of B (a multiple of 1024 bytes)
-  static constexpr int RAW = TF32 ? (BN == 128 ? 3 : 4) : (BN == 128 ? 5 : 7);  // TMA stages
+  // the thinnest tiles run two CTAs per SM (each CTA's prologue, pipeline fill and epilogue then
+  // overlap the other's streaming), with the ring depth cut to fit: BN = 16 in both modes, BN = 32
+  // in BF16
+  static constexpr int CTAS = (BN == 16 || (!TF32 && BN == 32)) ? 2 : 1;
+  static constexpr int RAW = TF32 ? (BN == 128 ? 3 : BN == 16 ? 2 : 4) : (CTAS == 2 ? 5 : BN == 128 ? 5 : 7);  // TMA stages
   static constexpr int RAW_BYTES = A_BYTES + B_BYTES;        // A, B
-  static constexpr int SLOTS = TF32 ? (BN >= 64 ? 2 : 3) : 0;  // split slots
+  static constexpr int SLOTS = TF32 ? (BN == 32 ? 3 : 2) : 0;  // split slots
   static constexpr int SLOT_BYTES = 2 * RAW_BYTES;           // A hi, B hi, A lo, B lo
   // accumulator columns (TF32X3: main + correction), a power of two >= 32 as tcgen05.alloc requires
   static constexpr uint32_t TMEM_COLS = (TF32 ? 2 * BN : BN) < 32 ? 32u : (uint32_t)(TF32 ? 2 * BN : BN);
   static constexpr size_t SMEM = 1024 + (size_t)RAW * RAW_BYTES + (size_t)SLOTS * SLOT_BYTES + 256;
-  static_assert(SMEM <= 232448, "dynamic shared memory per CTA");
+  static_assert(SMEM * CTAS <= 232448, "dynamic shared memory per SM");
 };
 
 // Round to the nearest TF32 value (10 fraction bits, ties away from zero); Inf and NaN pass.
@@ -204,7 +208,7 @@ __device__ __forceinline__ void split_tile(const float* raw, float* hi, float* l
 // element (i, j) of its tile goes to C[j * ldc + i], so a warp's 32 lanes (consecutive i) write 128
 // contiguous bytes per column j; split partials are kept in C's own [z][N][M] layout.
 template <bool TF32, int BN, bool TRANS>
-__global__ void __launch_bounds__(UM_THREADS, 1)
+__global__ void __launch_bounds__(UM_THREADS, UmmaCfg<TF32, BN>::CTAS)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                      int K, float alpha, float beta, float* __restrict__ C, int64_t ldc, int per,
                      float* __restrict__ ws, int* __restrict__ err) {
@@ -505,7 +509,7 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
   // about UM_CTA_FIXED_KB k-blocks) + the partial sums, with TF32X3 chains of at most
   // UM_TF32_MAX_KB k-blocks (the tensor core's FP32 accumulation loses up to an ulp per MMA; longer
   // K is split and the partials are summed with compensation)
-  const int nsm = umma_num_sms();
+  const int nsm = umma_num_sms() * ((bn == 16 || (!tf32 && bn == 32)) ? 2 : 1);  // CTAs resident at once (UmmaCfg::CTAS)
   const int smin = tf32 ? std::max(1, (kblocks + UM_TF32_MAX_KB - 1) / UM_TF32_MAX_KB) : 1;
   const int smax = std::max(smin, std::min(32, kblocks / 2));
   int splits = smin;
