@@ -188,10 +188,16 @@ amm_status_t amm_approx_matmul(amm_handle_t hA, amm_handle_t hB, float* C, int64
  *   AMM_SPARSE_FOURIER  dA = Re[(dC B~_a^T + P_A(dC dB~^T)) conj(W)],
  *                       dB = Re[W (A~_a^T dC + P_B(dA~^T dC))]  with the element masks P_A, P_B
  *                       (Alg. 5 differentiated with the masks frozen).
- *   Handles of different methods (SVD, circulant, cycle; square operands m = n = p; FP32):
+ *   Handles of different methods (any pair of SVD, circulant, cycle, Fourier; FP32):
  *                       the same formulas with each operand's own P' and the other operand's
- *                       dense residual dA / dB; the Fourier sparsifier and circulant blocks in a
- *                       mixed pair return AMM_ERR_NOT_IMPLEMENTED, other shapes
+ *                       residual dB = Re dB - i Im B~ (likewise dA), so beside the plain terms
+ *                       Im P_A'(dC (Im B~)^T) and Im P_B'((Im A~)^T dC) enter when both
+ *                       truncations can be complex (circulant with a split pair, Fourier).
+ *                       Unblocked pairs need square operands (m = n = p).  With one operand in
+ *                       circulant blocks (opts.block) M is formed on the zero-padded shape and
+ *                       cropped: dC is padded with zeros, the blocked projection runs per block
+ *                       on b-wide pieces of the inner sums and the gradients are cropped; any
+ *                       m, n, p then, except a cycle partner (square).  Other shapes return
  *                       AMM_ERR_UNSUPPORTED_SIZE.
  *   dC  device m x p FP32 (lddc).  dA (m x n, ldda) and dB (n x p, lddb) are overwritten;
  *   either may be NULL to skip it.
@@ -288,9 +294,8 @@ amm_status_t amm_decompose_best_method(const void* A, int64_t rows, int64_t cols
  * Re dA = A - Re A~ of a handle (the residue of A = A~ + dA, Section 2, Eq. (2.1)) as a dense FP32
  * matrix (rows x cols, leading dimension ldd >=
  * cols, DEVICE, caller-owned, overwritten): the residue that amm_refine_product's second-level
- * decompositions take.  FP32 operands without circulant blocks; the Fourier sparsifier as the
- * left operand only (else AMM_ERR_NOT_IMPLEMENTED).  Asynchronous on `stream`, which must be
- * ordered after the handle's stream.
+ * decompositions take.  FP32 operands without circulant blocks (else AMM_ERR_NOT_IMPLEMENTED).
+ * Asynchronous on `stream`, which must be ordered after the handle's stream.
  */
 amm_status_t amm_handle_residual(amm_handle_t h, float* D, int64_t ldd, void* stream);
 

@@ -748,6 +748,51 @@ def mixed_backward(ta: Truncation, tb: Truncation, g: np.ndarray):
     return np.real(da), np.real(db)
 
 
+def _project_any(t: Truncation, x: np.ndarray, adjoint: bool = False) -> np.ndarray:
+    if t.method == "circulant_blocked":
+        return project_circulant_blocked(x.astype(np.complex128), t, adjoint)
+    return project(t, x, adjoint)
+
+
+def _adjoint_within(t: Truncation, y: np.ndarray) -> np.ndarray:
+    """t's adjoint projector on the leading part of y that has t's operand shape (the padded shape
+    of a blockwise circulant truncation), zero on the rest of y."""
+    r, c = t.a.shape
+    out = np.zeros(y.shape, dtype=np.complex128)
+    out[:r, :c] = _project_any(t, y[:r, :c], adjoint=True)
+    return out
+
+
+def blocked_mixed_backward(ta: Truncation, tb: Truncation, g: np.ndarray):
+    """Gradients of <G, Re M> when one operand is a blockwise circulant truncation and the other
+    is truncated by another method (readings R10 and R13), projectors frozen.  M is formed on the
+    common padded shape and cropped (blocked_first_order), so with G_p = G padded with zeros and
+    both operands padded to that shape,
+        dA = crop Re[G_p B~_p^T + P_A'(G_p dB_p^T)],   dB = crop Re[A~_p^T G_p + P_B'(dA_p^T G_p)],
+    each adjoint acting on its own operand's shape (blockwise for the blocked one)."""
+    m0, n0 = getattr(ta, "shape0", ta.a.shape)
+    p0 = getattr(tb, "shape0", tb.a.shape)[1]
+    rows, inner, cols = ta.a.shape[0], max(ta.a.shape[1], tb.a.shape[0]), tb.a.shape[1]
+    pa, pb = padded(ta, rows, inner), padded(tb, inner, cols)
+    gp = pad_to(g, rows, cols)
+    da = gp @ pb.approx.T + _adjoint_within(ta, gp @ pb.resid.T)
+    db = pa.approx.T @ gp + _adjoint_within(tb, pa.resid.T @ gp)
+    return np.real(da)[:m0, :n0], np.real(db)[:n0, :p0]
+
+
+def frozen_blocked_mixed_product(ta: Truncation, tb: Truncation, a, b) -> np.ndarray:
+    """The mixed map with a blockwise circulant operand, projectors frozen, at new operands (a, b):
+    each operand padded to its truncation's shape and projected, then both padded to the common
+    shape, M formed there and cropped."""
+    m0 = getattr(ta, "shape0", ta.a.shape)[0]
+    p0 = getattr(tb, "shape0", tb.a.shape)[1]
+    rows, inner, cols = ta.a.shape[0], max(ta.a.shape[1], tb.a.shape[0]), tb.a.shape[1]
+    qa = pad_to(_project_any(ta, pad_to(a, *ta.a.shape)), rows, inner)
+    qb = pad_to(_project_any(tb, pad_to(b, *tb.a.shape)), inner, cols)
+    ap, bp = pad_to(a, rows, inner), pad_to(b, inner, cols)
+    return np.real(qa @ bp + (ap - qa) @ qb)[:m0, :p0]
+
+
 def frozen_mixed_product(ta: Truncation, tb: Truncation, a, b) -> np.ndarray:
     """The mixed first-order map with frozen projectors evaluated at new operands (a, b)."""
     pa, pb = project(ta, a), project(tb, b)

@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(256) ft_bw_maskwalk_kernel(const float* __rest
 // ============================================================================ P_A(G dB~^T)
 // For each kept (i, q) of A~_a:  XAT[q][i] += sum_c G(i, c) B~(q, c) [(q, c) not kept in B~_a].
 // CTA per row i (G row shared through L1), warp per kept entry, lanes over c.  maskB NULL: no
-// entry excluded (B~ the transform of a dense residual, for mixed-method gradients); imag: the sum
-// is multiplied by i before it is added.
+// entry excluded (B~ the transform of a dense residual, for mixed-method gradients); imag = +1 / -1:
+// the sum is multiplied by +i / -i before it is added.
 __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__ G, int64_t ldg,
                                                        const float2* __restrict__ Bt, const uint32_t* __restrict__ maskB,
                                                        int mwB, const int32_t* __restrict__ selA, int ka, int n, int m,
@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__
       float2* x = XAT + (int64_t)q * m + i;
       const float2 v = *x;
       const float2 d = make_float2(ax, mir ? -ay : ay);
-      *x = imag ? make_float2(v.x - d.y, v.y + d.x) : make_float2(v.x + d.x, v.y + d.y);
+      *x = imag > 0 ? make_float2(v.x - d.y, v.y + d.x)
+                    : imag < 0 ? make_float2(v.x + d.y, v.y - d.x) : make_float2(v.x + d.x, v.y + d.y);
     }
   }
 }
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) ft_bw_pa_kernel(const float* __restrict__
 // ============================================================================ P_B(dA~^T G)
 // For each kept (q, c) of B~_a:  XB[q][c] += sum_i A~(i, q) [(i, q) not kept in A~_a] G(i, c).
 // CTA per column c (GT row shared through L1), warp per kept entry, lanes over i.  maskA NULL: no
-// entry excluded; imag: the sum is multiplied by i before it is added (as for ft_bw_pa_kernel).
+// entry excluded; imag = +1 / -1: the sum is multiplied by +i / -i before it is added.
 __global__ void __launch_bounds__(256) ft_bw_pb_kernel(const float* __restrict__ GT, const float2* __restrict__ AtT,
                                                        const uint32_t* __restrict__ maskA, int mwA,
                                                        const int32_t* __restrict__ selB, int kb, int n, int m, int p,
@@ -178,7 +179,8 @@ __global__ void __launch_bounds__(256) ft_bw_pb_kernel(const float* __restrict__
       float2* x = XB + (int64_t)q * p + c;
       const float2 v = *x;
       const float2 d = make_float2(ax, mir ? -ay : ay);
-      *x = imag ? make_float2(v.x - d.y, v.y + d.x) : make_float2(v.x + d.x, v.y + d.y);
+      *x = imag > 0 ? make_float2(v.x - d.y, v.y + d.x)
+                    : imag < 0 ? make_float2(v.x + d.y, v.y - d.x) : make_float2(v.x + d.x, v.y + d.y);
     }
   }
 }
@@ -248,6 +250,9 @@ template <int N> struct FtBwOps {
   static cudaError_t fwd_cols(const float2* X, int nvec, const float2* tw, float* out, int64_t ldo, cudaStream_t st) {
     return real<false, false>(X, nvec, tw, out, ldo, st);
   }
+  static cudaError_t inv_cols(const float2* X, int nvec, const float2* tw, float* out, int64_t ldo, cudaStream_t st) {
+    return real<true, false>(X, nvec, tw, out, ldo, st);
+  }
 };
 
 #define AMM_FTB_DISPATCH(n, EXPR)                 \
@@ -278,6 +283,191 @@ static cudaError_t ft_bw_real(int n, bool inv, const float2* X, int nvec, const 
   AMM_TRACE_W(inv ? "ft_bw_idft_rows" : "ft_bw_dft_cols", st, 0.0, (double)n * nvec * 12, nullptr);
   if (inv) { AMM_FTB_DISPATCH(n, return FtBwOps<NN>::inv_rows(X, nvec, tw, out, ldo, st)); }
   AMM_FTB_DISPATCH(n, return FtBwOps<NN>::fwd_cols(X, nvec, tw, out, ldo, st));
+}
+
+// out[l][v] = n^{-1/2} Re sum_q X(q, v) e^{+2 pi i q l/n}: the inverse transform of each column of
+// X [n][nvec], written as a column (the dense form of a right Fourier truncation)
+static cudaError_t ft_bw_real_inv_cols(int n, const float2* X, int nvec, const float2* tw, float* out, int64_t ldo,
+                                       cudaStream_t st) {
+  AMM_TRACE_W("ft_idft_cols", st, 0.0, (double)n * nvec * 12, nullptr);
+  AMM_FTB_DISPATCH(n, return FtBwOps<NN>::inv_cols(X, nvec, tw, out, ldo, st));
+}
+
+// ============================================================================ mixed-method pieces
+// out[r][c] += t[r][c]
+__global__ void ft_add_kernel(float* __restrict__ out, int64_t ldo, const float* __restrict__ t, int64_t ldt,
+                              int64_t rows, int64_t cols) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t r = e / cols, c = e - r * cols;
+  out[r * ldo + c] += t[r * ldt + c];
+}
+
+// d[r][c] -= t[r][c]
+__global__ void ft_sub_kernel(float* __restrict__ d, int64_t ldd, const float* __restrict__ t, int64_t ldt,
+                              int64_t rows, int64_t cols) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t r = e / cols, c = e - r * cols;
+  d[r * ldd + c] -= t[r * ldt + c];
+}
+
+static cudaError_t add_into(float* out, int64_t ldo, const float* t, int64_t ldt, int64_t rows, int64_t cols,
+                            cudaStream_t st) {
+  const int64_t cnt = rows * cols;
+  ft_add_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(out, ldo, t, ldt, rows, cols);
+  return cudaGetLastError();
+}
+
+// X[q][c] = f * B~(q, c) on the kept entries of each column (selB [p][kb]), 0 elsewhere, q = 0..n-1;
+// f = 1 (part 0) or -i (part 1).  One thread per kept entry; X must be zero on entry.
+__global__ void ft_scatter_cols_kernel(const float2* __restrict__ Bt, const int32_t* __restrict__ selB, int kb, int n,
+                                       int p, int part, float2* __restrict__ X) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)p * kb) return;
+  const int c = (int)(e / kb);
+  const int q = __ldg(selB + e);
+  const float2 v = half_spec(Bt, n, q, p, c);
+  X[(int64_t)q * p + c] = part ? make_float2(v.y, -v.x) : v;
+}
+
+// Dense parts of a right Fourier truncation B_s = W^* B~_a (n x p): part 0 writes D = B - Re B_s,
+// part 1 D = Im B_s.
+cudaError_t ft_right_dense(int n, int p, const float2* Bt, const int32_t* selB, int kb, const float2* tw, int part,
+                           const float* B, int64_t ldb, float* D, int64_t ldd, cudaStream_t st) {
+  float2* X = nullptr;
+  float* Y = nullptr;
+  cudaError_t e = dev_alloc((void**)&X, sizeof(float2) * (size_t)n * p, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(float2) * (size_t)n * p, st);
+  if (e == cudaSuccess) {
+    ft_scatter_cols_kernel<<<(unsigned)(((int64_t)p * kb + 255) / 256), 256, 0, st>>>(Bt, selB, kb, n, p, part, X);
+    e = cudaGetLastError();
+  }
+  if (part == 0) {
+    if (e == cudaSuccess) e = dev_alloc((void**)&Y, sizeof(float) * (size_t)n * p, st);
+    if (e == cudaSuccess) e = ft_bw_real_inv_cols(n, X, p, tw, Y, p, st);  // Re(W^* X)
+    if (e == cudaSuccess) e = cudaMemcpy2DAsync(D, sizeof(float) * ldd, B, sizeof(float) * ldb, sizeof(float) * p, n,
+                                                cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {  // D -= Y
+      const int64_t cnt = (int64_t)n * p;
+      ft_sub_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(D, ldd, Y, p, n, p);
+      e = cudaGetLastError();
+    }
+  } else if (e == cudaSuccess) {
+    e = ft_bw_real_inv_cols(n, X, p, tw, D, ldd, st);  // Re(W^* (-i X)) = Im(W^* X)
+  }
+  dev_free(X, st);
+  if (Y) dev_free(Y, st);
+  return e;
+}
+
+// out = Re(G B~^T) for a right Fourier truncation (G m x p, out m x n): the sparse x dense product
+// over the kept entries of B~_a, then the inverse row transforms (the first term of dA above)
+cudaError_t ft_rt_apply_bw(int n, int m, int p, const float2* Bt, const uint32_t* maskB, int kb, const float2* tw,
+                           const float* G, int64_t ldg, float* out, int64_t ldo, cudaStream_t st) {
+  const int mwB = (p + 31) / 32;
+  float *GT = nullptr;
+  float2* XAT = nullptr;
+  cudaError_t e = dev_alloc((void**)&GT, sizeof(float) * (size_t)p * m, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&XAT, sizeof(float2) * (size_t)n * m, st);
+  if (e == cudaSuccess) e = transpose_f32(G, m, p, ldg, GT, m, st);
+  if (e == cudaSuccess) {
+    AMM_TRACE_W("ft_bw_gba", st, 4.0 * p * (double)kb * m, 4.0 * m * (double)p + 8.0 * p * (double)kb + 8.0 * n * m,
+                nullptr);
+    ft_bw_maskwalk_kernel<<<dim3((m + 256 * MW_RPT - 1) / (256 * MW_RPT), n), 256, 0, st>>>(GT, m, m, Bt, p, maskB,
+                                                                                           mwB, n, XAT);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = ft_bw_real(n, true, XAT, m, tw, out, ldo, st);
+  dev_free(GT, st);
+  dev_free(XAT, st);
+  return e;
+}
+
+// out = Re(A~^T G) for a left Fourier truncation (G m x p, out n x p): the sparse x dense product
+// over the kept entries of A~_a, then the forward column transforms (the first term of dB above)
+cudaError_t ft_lt_apply_bw(int n, int m, int p, const float2* AtT, const uint32_t* maskA, int ka, const float2* tw,
+                           const float* G, int64_t ldg, float* out, int64_t ldo, cudaStream_t st) {
+  const int mwA = (m + 31) / 32;
+  float2* XB = nullptr;
+  cudaError_t e = dev_alloc((void**)&XB, sizeof(float2) * (size_t)n * p, st);
+  if (e == cudaSuccess) {
+    AMM_TRACE_W("ft_bw_aag", st, 4.0 * m * (double)ka * p, 4.0 * m * (double)p + 8.0 * m * (double)ka + 8.0 * n * p,
+                nullptr);
+    ft_bw_maskwalk_kernel<<<dim3((p + 256 * MW_RPT - 1) / (256 * MW_RPT), n), 256, 0, st>>>(G, ldg, p, AtT, m, maskA,
+                                                                                           mwA, n, XB);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = ft_bw_real(n, false, XB, p, tw, out, ldo, st);
+  dev_free(XB, st);
+  return e;
+}
+
+// out (m x n) += Re P_A'(G D^T) for a left Fourier truncation with kept entries selA (m x ka), where
+// D = Dre + s i Dim (n x p, Dim may be NULL; s = sign_im = +1 / -1) and P_A'(Y) = (M o (Y W)) conj(W):
+// (Y W)(i, q) = sum_c G(i, c) (W D)(q, c) is sampled at the kept (i, q) from the column transforms
+// of D, and the last step is the inverse row transform.
+cudaError_t ft_proj_left(int n, int m, int p, const int32_t* selA, int ka, const float2* tw, const float* G,
+                         int64_t ldg, const float* Dre, const float* Dim, int sign_im, int64_t ldd, float* out,
+                         int64_t ldo, cudaStream_t st) {
+  const size_t kh = (size_t)n / 2 + 1;
+  float2 *T = nullptr, *XAT = nullptr;
+  float *mag = nullptr, *Y = nullptr;
+  cudaError_t e = dev_alloc((void**)&T, sizeof(float2) * kh * p, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&mag, sizeof(float) * kh * p, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&XAT, sizeof(float2) * (size_t)n * m, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&Y, sizeof(float) * (size_t)m * n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(XAT, 0, sizeof(float2) * (size_t)n * m, st);
+  for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+    const float* D = part ? Dim : Dre;
+    if (!D) continue;
+    e = ft_transform(n, false, D, ldd, p, tw, T, nullptr, mag, st);  // W D, half spectrum [kh][p]
+    if (e == cudaSuccess) {
+      AMM_TRACE_W("ft_bw_pa", st, 4.0 * m * (double)ka * p, 4.0 * m * (double)p + 8.0 * kh * p, nullptr);
+      ft_bw_pa_kernel<<<m, 256, 0, st>>>(G, ldg, T, nullptr, 0, selA, ka, n, m, p, XAT, part ? sign_im : 0);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = ft_bw_real(n, true, XAT, m, tw, Y, n, st);
+  if (e == cudaSuccess) e = add_into(out, ldo, Y, n, m, n, st);
+  for (void* q : {(void*)T, (void*)mag, (void*)XAT, (void*)Y})
+    if (q) dev_free(q, st);
+  return e;
+}
+
+// out (n x p) += Re P_B'(D^T G) for a right Fourier truncation with kept entries selB (p x kb), where
+// D = Dre + s i Dim (m x n) and P_B'(Y) = W (M o (conj(W) Y)): (conj(W) Y)(q, c) = sum_i (D W^*)(i, q)
+// G(i, c) is sampled at the kept (q, c) from the row transforms of D, and the last step is the
+// forward column transform.
+cudaError_t ft_proj_right(int n, int m, int p, const int32_t* selB, int kb, const float2* tw, const float* Dre,
+                          const float* Dim, int sign_im, int64_t ldd, const float* G, int64_t ldg, float* out,
+                          int64_t ldo, cudaStream_t st) {
+  const size_t kh = (size_t)n / 2 + 1;
+  float2 *T = nullptr, *TT = nullptr, *XB = nullptr;
+  float *mag = nullptr, *GT = nullptr, *Y = nullptr;
+  cudaError_t e = dev_alloc((void**)&T, sizeof(float2) * kh * m, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&TT, sizeof(float2) * kh * m, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&mag, sizeof(float) * kh * m, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&GT, sizeof(float) * (size_t)p * m, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&XB, sizeof(float2) * (size_t)n * p, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&Y, sizeof(float) * (size_t)n * p, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(XB, 0, sizeof(float2) * (size_t)n * p, st);
+  if (e == cudaSuccess) e = transpose_f32(G, m, p, ldg, GT, m, st);
+  for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+    const float* D = part ? Dim : Dre;
+    if (!D) continue;
+    e = ft_transform(n, true, D, ldd, m, tw, T, TT, mag, st);  // D W^*, transposed half spectrum [kh][m]
+    if (e == cudaSuccess) {
+      AMM_TRACE_W("ft_bw_pb", st, 4.0 * p * (double)kb * m, 4.0 * m * (double)p + 8.0 * kh * m, nullptr);
+      ft_bw_pb_kernel<<<p, 256, 0, st>>>(GT, TT, nullptr, 0, selB, kb, n, m, p, XB, part ? sign_im : 0);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = ft_bw_real(n, false, XB, p, tw, Y, p, st);
+  if (e == cudaSuccess) e = add_into(out, ldo, Y, p, n, p, st);
+  for (void* q : {(void*)T, (void*)TT, (void*)mag, (void*)GT, (void*)XB, (void*)Y})
+    if (q) dev_free(q, st);
+  return e;
 }
 
 // Trace work of the kernels below: FLOPs of the real or complex products actually formed, bytes the

@@ -120,6 +120,20 @@ cudaError_t ft_left_apply(int n, int m, const float2* At, const int32_t* selA, i
                           const float* X, int64_t ldx, int p, float* C, int64_t ldc, cudaStream_t st);
 cudaError_t ft_right_apply(int n, int p, const float2* Bt, const int32_t* selB, int kb, const float2* tw,
                            const float* Y, int64_t ldy, int m, bool imag, float* C, int64_t ldc, cudaStream_t st);
+// ft_backward.cu, pieces of the mixed-method backward with a Fourier operand (D = B - Re B_s
+// for part 0, Im B_s for part 1; sign_im multiplies the imaginary part Dim of the dense factor)
+cudaError_t ft_right_dense(int n, int p, const float2* Bt, const int32_t* selB, int kb, const float2* tw, int part,
+                           const float* B, int64_t ldb, float* D, int64_t ldd, cudaStream_t st);
+cudaError_t ft_rt_apply_bw(int n, int m, int p, const float2* Bt, const uint32_t* maskB, int kb, const float2* tw,
+                           const float* G, int64_t ldg, float* out, int64_t ldo, cudaStream_t st);
+cudaError_t ft_lt_apply_bw(int n, int m, int p, const float2* AtT, const uint32_t* maskA, int ka, const float2* tw,
+                           const float* G, int64_t ldg, float* out, int64_t ldo, cudaStream_t st);
+cudaError_t ft_proj_left(int n, int m, int p, const int32_t* selA, int ka, const float2* tw, const float* G,
+                         int64_t ldg, const float* Dre, const float* Dim, int sign_im, int64_t ldd, float* out,
+                         int64_t ldo, cudaStream_t st);
+cudaError_t ft_proj_right(int n, int m, int p, const int32_t* selB, int kb, const float2* tw, const float* Dre,
+                          const float* Dim, int sign_im, int64_t ldd, const float* G, int64_t ldg, float* out,
+                          int64_t ldo, cudaStream_t st);
 
 // umma_gemm.cu: C = alpha A B^T + beta C on tcgen05 tensor cores (A, B K-major);
 // tf32 = FP32 inputs with TF32 hi/lo splitting, else BF16 inputs.  err: device flag.

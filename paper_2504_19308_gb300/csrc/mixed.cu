@@ -180,9 +180,15 @@ amm_status_t mixed_matmul(Handle* a, Handle* b, float* C, int64_t ldc, cudaStrea
 //   dA = Re(G B~^T) + Re P_A'(G dB^T),   dB = Re(A~^T G) + Re P_B'(dA^T G),
 // P' the bilinear adjoint of the operand's projector (circulant: the mirrored components S-bar,
 // whose real part on a real matrix is the w-weighted projection; SVD Q Q^T; cycles the kept cycles).
-// dA, dB above are the dense real residuals of the other operand.  Built for the SVD, circulant and
-// cycle methods on square operands (m = n = p): the circulant projections run as SDDMMs on
-// spectra of length n, the cycle projections as selected-diagonal dot products.
+// dA, dB above are the residuals of the other operand, dB = Re dB - i Im B~ (Im B~ = 0 for SVD and
+// cycles), and every projector is linear over the complex numbers, so
+//   Re P_A'(G dB^T) = Re P_A'(G (Re dB)^T) + Im P_A'(G (Im B~)^T)
+// (and likewise for dB).  The imaginary term is non-zero only when both truncations can be complex
+// (a circulant with a split conjugate pair and a Fourier sparsifier).  Built for all pairs of the
+// SVD, circulant, cycle and Fourier methods on square operands (m = n = p): the circulant
+// projections run as SDDMMs on spectra of length n (the imaginary term over the unpaired
+// components, gated on the device), the cycle projections as selected-diagonal dot products, the
+// Fourier ones as sampled products on the transforms of the dense factor.
 
 namespace {
 
@@ -203,10 +209,13 @@ struct Buf {
   }
 };
 
-// out += Re P_{S-bar}(X Y^T) (row = false) or Re P_{S-bar}(X^T Y) (row = true) for the circulant
-// handle h, X and Y n x n: component spectra from the SDDMM on column / row spectra
+// out += Re P_{S-bar}(Z) (unpaired = false) or out -= Im P_S(Z) (unpaired = true: the unpaired
+// components t with weight v_t, skipped on the device when there are none) for the circulant handle
+// h and Z = X Y^T (row = false) or X^T Y (row = true), X and Y n x n: component spectra from the
+// SDDMM on column / row spectra.  For real Z, P_{S-bar}(Z) = conj P_S(Z), so the second form is
+// Re(-i P_{S-bar}(Z)).
 cudaError_t cd_project_product(Handle* h, bool row, const float* X, int64_t ldx, const float* Y, int64_t ldy,
-                               float* out, int64_t ldo, cudaStream_t st) {
+                               float* out, int64_t ldo, cudaStream_t st, bool unpaired = false) {
   const int n = (int)h->rows;
   const size_t kh = (size_t)n / 2 + 1;
   auto& c = h->cd;
@@ -215,25 +224,40 @@ cudaError_t cd_project_product(Handle* h, bool row, const float* X, int64_t ldx,
   float2* X2 = b.get<float2>(kh * n);
   float2* RX = b.get<float2>(kh * n);
   float2* K = b.get<float2>((size_t)c.cap * n);
-  if (b.e == cudaSuccess) b.e = bw_spectrum(n, row, X, ldx, c.tw, X1, st);
-  if (b.e == cudaSuccess) b.e = bw_spectrum(n, row, Y, ldy, c.tw, X2, st);
-  if (b.e == cudaSuccess) b.e = cd_sddmm(n, X1, X2, c.so.ulist, c.so.counts, c.cap, K, nullptr, nullptr, st);
-  if (b.e == cudaSuccess) b.e = cd_rho(n, K, c.tw, c.so.ulist, c.so.counts, c.cap, RX, nullptr, nullptr, st);
-  if (b.e == cudaSuccess) b.e = cd_residual(n, RX, c.tw, c.so.wfull, 2, nullptr, out, st, ldo, 1);
+  const int32_t* list = unpaired ? c.so.dlist : c.so.ulist;
+  const int32_t* count = unpaired ? c.so.counts + 1 : c.so.counts;
+  // the gated kernels read both gates whenever the first is given: pass the unpaired count twice
+  const int32_t* gate = unpaired ? c.so.counts + 1 : nullptr;
+  if (b.e == cudaSuccess) b.e = bw_spectrum(n, row, X, ldx, c.tw, X1, st, gate, gate);
+  if (b.e == cudaSuccess) b.e = bw_spectrum(n, row, Y, ldy, c.tw, X2, st, gate, gate);
+  if (b.e == cudaSuccess) b.e = cd_sddmm(n, X1, X2, list, count, c.cap, K, gate, gate, st);
+  if (b.e == cudaSuccess) b.e = cd_rho(n, K, c.tw, list, count, c.cap, RX, gate, gate, st);
+  if (b.e == cudaSuccess)
+    b.e = unpaired ? cd_residual(n, RX, c.tw, c.so.vfull, 3, count, out, st, ldo, 1)
+                   : cd_residual(n, RX, c.tw, c.so.wfull, 2, nullptr, out, st, ldo, 1);
   return b.e;
 }
 
 bool aligned16(const float* p, int64_t ld) { return ((uintptr_t)p & 15) == 0 && (ld & 3) == 0; }
 
+// D = B - Re(B~) / Im(B~) of the right operand b, n x p (a right Fourier handle holds column
+// transforms; the other methods' truncations do not depend on the side)
+cudaError_t right_dense(Handle* b, bool imag, float* D, int64_t ldd, cudaStream_t st) {
+  if (b->method == AMM_SPARSE_FOURIER)
+    return ft_right_dense(b->ft.n, (int)b->cols, b->ft.T, b->ft.sel, (int)b->k, b->ft.tw, imag ? 1 : 0,
+                          (const float*)b->A, b->lda, D, ldd, st);
+  return imag ? imag_part(b, D, ldd, st) : residual(b, D, ldd, st);
+}
+
 }  // namespace
+
+amm_status_t mixed_backward_blocked(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda,
+                                    float* dB, int64_t lddb, cudaStream_t st);
 
 amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda, float* dB,
                             int64_t lddb, cudaStream_t st) {
   const int64_t m = a->rows, n = a->cols, p = b->cols;
-  if (a->method == AMM_SPARSE_FOURIER || b->method == AMM_SPARSE_FOURIER)
-    return fail(AMM_ERR_NOT_IMPLEMENTED, "backward of a mixed-method product with the Fourier sparsifier is not built");
-  if (a->blk.b || b->blk.b)
-    return fail(AMM_ERR_NOT_IMPLEMENTED, "backward of a mixed-method product with circulant blocks is not built");
+  if (a->blk.b || b->blk.b) return mixed_backward_blocked(a, b, G, ldg, dA, ldda, dB, lddb, st);
   if (m != n || p != n)
     return fail(AMM_ERR_UNSUPPORTED_SIZE, "backward of a mixed-method product needs square operands (%lldx%lld, "
                 "%lldx%lld)", (long long)m, (long long)n, (long long)n, (long long)p);
@@ -241,11 +265,17 @@ amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, f
     return fail(AMM_ERR_NOT_IMPLEMENTED, "mixed methods: BF16 operands are not built (use FP32 inputs)");
   const int nn = (int)n;
   Buf buf(st);
-  float* DA = buf.get<float>((size_t)nn * nn);  // Re dA = A - Re A~
-  float* DB = buf.get<float>((size_t)nn * nn);
+  // the imaginary parts enter only when both truncations can be complex
+  const bool cplx = can_be_complex(a) && can_be_complex(b);
+  float* DA = dB ? buf.get<float>((size_t)nn * nn) : nullptr;  // Re dA = A - Re A~
+  float* DB = dA ? buf.get<float>((size_t)nn * nn) : nullptr;  // Re dB = B - Re B~
+  float* IA = dB && cplx ? buf.get<float>((size_t)nn * nn) : nullptr;  // Im A~
+  float* IB = dA && cplx ? buf.get<float>((size_t)nn * nn) : nullptr;  // Im B~
   cudaError_t e = buf.e;
-  if (e == cudaSuccess) e = residual(a, DA, nn, st);
-  if (e == cudaSuccess) e = residual(b, DB, nn, st);
+  if (e == cudaSuccess && DA) e = residual(a, DA, nn, st);
+  if (e == cudaSuccess && DB) e = right_dense(b, false, DB, nn, st);
+  if (e == cudaSuccess && IA) e = imag_part(a, IA, nn, st);
+  if (e == cudaSuccess && IB) e = right_dense(b, true, IB, nn, st);
   // an aligned copy of G for the cycle projections (float4 rows)
   const float* Ga = G;
   int64_t ldga = ldg;
@@ -266,13 +296,22 @@ amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, f
         e = cd_apply(nn, true, G, ldg, false, nn, b->cd.tw, b->cd.so.ulist, b->cd.Lw, b->cd.so.counts, nullptr,
                      nullptr, dA, ldda, 0, st, 0);
         break;
+      case AMM_SPARSE_FOURIER:
+        e = ft_rt_apply_bw(nn, nn, nn, b->ft.T, b->ft.maskT, (int)b->k, b->ft.tw, G, ldg, dA, ldda, st);
+        break;
       default: e = cyc_rt_apply(nn, G, ldg, b->cy.so.sel, (int)b->k, b->cy.cyc, dA, ldda, st); break;
     }
-    // + Re P_A'(G dB^T)
+    // + Re P_A'(G dB^T) = Re P_A'(G (Re dB)^T) + Im P_A'(G (Im B~)^T)
     if (e == cudaSuccess) {
       switch (a->method) {
         case AMM_SVD: e = svd_proj_left(a, G, ldg, DB, nn, nn, dA, ldda, st); break;
-        case AMM_CIRCULANT: e = cd_project_product(a, false, G, ldg, DB, nn, dA, ldda, st); break;
+        case AMM_CIRCULANT:
+          e = cd_project_product(a, false, G, ldg, DB, nn, dA, ldda, st);
+          if (e == cudaSuccess && IB) e = cd_project_product(a, false, G, ldg, IB, nn, dA, ldda, st, true);
+          break;
+        case AMM_SPARSE_FOURIER:
+          e = ft_proj_left(nn, nn, nn, a->ft.sel, (int)a->k, a->ft.tw, G, ldg, DB, IB, -1, nn, dA, ldda, st);
+          break;
         default: e = cyc_diag_project(nn, nn, Ga, ldga, DB, nn, a->cy.so.sel, (int)a->k, dA, ldda, st); break;
       }
     }
@@ -285,13 +324,22 @@ amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, f
         e = cd_apply(nn, false, G, ldg, false, nn, a->cd.tw, a->cd.so.ulist, a->cd.Lw, a->cd.so.counts, nullptr,
                      nullptr, dB, lddb, 0, st, 1);
         break;
+      case AMM_SPARSE_FOURIER:
+        e = ft_lt_apply_bw(nn, nn, nn, a->ft.TT, a->ft.maskT, (int)a->k, a->ft.tw, G, ldg, dB, lddb, st);
+        break;
       default: e = cyc_lt_apply(nn, G, ldg, a->cy.so.sel, (int)a->k, a->cy.cyc, dB, lddb, st); break;
     }
-    // + Re P_B'(dA^T G)
+    // + Re P_B'(dA^T G) = Re P_B'((Re dA)^T G) + Im P_B'((Im A~)^T G)
     if (e == cudaSuccess) {
       switch (b->method) {
         case AMM_SVD: e = svd_proj_right(b, DA, nn, G, ldg, nn, dB, lddb, st); break;
-        case AMM_CIRCULANT: e = cd_project_product(b, true, DA, nn, G, ldg, dB, lddb, st); break;
+        case AMM_CIRCULANT:
+          e = cd_project_product(b, true, DA, nn, G, ldg, dB, lddb, st);
+          if (e == cudaSuccess && IA) e = cd_project_product(b, true, IA, nn, G, ldg, dB, lddb, st, true);
+          break;
+        case AMM_SPARSE_FOURIER:
+          e = ft_proj_right(nn, nn, nn, b->ft.sel, (int)b->k, b->ft.tw, DA, IA, -1, nn, G, ldg, dB, lddb, st);
+          break;
         default: {
           // (dA^T G)((l + s), l) = <dA^T(l + s, :), G^T(l, :)>
           float* DAT = buf.get<float>((size_t)nn * nn);
@@ -342,13 +390,11 @@ amm_status_t refinable(const Handle* h, const char* what) {
 amm_status_t handle_residual(Handle* h, float* D, int64_t ldd, cudaStream_t st) {
   amm_status_t s = refinable(h, "amm_handle_residual");
   if (s != AMM_OK) return s;
-  if (h->method == AMM_SPARSE_FOURIER && h->role != AMM_LEFT)
-    return fail(AMM_ERR_NOT_IMPLEMENTED, "amm_handle_residual: the Fourier sparsifier's right operand is not built");
   const int64_t m = h->rows, n = h->cols;
   Buf buf(st);
   float* T = buf.get<float>((size_t)m * n);  // the pieces write a dense m x n scratch, copied out
   cudaError_t e = buf.e;
-  if (e == cudaSuccess) e = residual(h, T, n, st);
+  if (e == cudaSuccess) e = h->role == AMM_LEFT ? residual(h, T, n, st) : right_dense(h, false, T, n, st);
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(D, sizeof(float) * ldd, T, sizeof(float) * n, sizeof(float) * n, m,
                           cudaMemcpyDeviceToDevice, st);
@@ -382,6 +428,160 @@ amm_status_t refine_product(Handle* a, Handle* b, Handle* a2, Handle* b2, float*
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return cuda_fail(e, "amm_refine_product");
+  return AMM_OK;
+}
+
+// ---------------------------------------------------------------------------- backward with blocks
+// One operand a blockwise circulant truncation (b x b blocks of its zero-padded copy), the other
+// truncated by another method.  As in the product, M is formed on the padded shape and cropped,
+// so with G_p = G padded with zeros and the unblocked operand padded with zeros along the inner
+// dimension (its truncation and residual are zero there):
+//   dA = crop Re[G_p B~_p^T + P_A'(G_p dB_p^T)],   dB = crop Re[A~_p^T G_p + P_B'(dA_p^T G_p)].
+// The blocked operand's terms run block by block on the square kernels with every inner sum cut
+// into b-wide pieces (block IJ of G_p dB_p^T is sum_L G_IL dB_JL^T); the other operand's terms are
+// its pieces of the unblocked mixed backward on the cropped factors (dA_p^T G_p cropped to n x p
+// is dA^T G over the first m rows, the padded rows of G_p being zero).  Im B~ (Im A~) enters the
+// blocked projection only beside a Fourier operand, whose truncation is complex; the SVD and cycle
+// projectors are real, so their imaginary terms vanish.
+amm_status_t mixed_backward_blocked(Handle* a, Handle* b, const float* G, int64_t ldg, float* dA, int64_t ldda,
+                                    float* dB, int64_t lddb, cudaStream_t st) {
+  const int64_t m = a->rows, n = a->cols, p = b->cols;
+  const bool left = a->blk.b != 0;  // the blocked circulant is A (else B)
+  Handle* c = left ? a : b;
+  Handle* o = left ? b : a;
+  if (a->dtype != AMM_F32 || b->dtype != AMM_F32)
+    return fail(AMM_ERR_NOT_IMPLEMENTED, "mixed methods: BF16 operands are not built (use FP32 inputs)");
+  if (o->method == AMM_SPARSE_CYCLE && (m != n || n != p))
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "backward of a blocked circulant x cycle product needs square operands "
+                "(%lldx%lld, %lldx%lld)", (long long)m, (long long)n, (long long)n, (long long)p);
+  const int64_t bs = c->blk.b;
+  const int bsi = (int)bs;
+  const int64_t mq = (m + bs - 1) / bs * bs, nq = (n + bs - 1) / bs * bs, pq = (p + bs - 1) / bs * bs;
+  auto sub = [&](int64_t i, int64_t j) { return (Handle*)c->blk.sub[(size_t)(i * c->blk.nbc + j)]; };
+  const bool cplx = o->method == AMM_SPARSE_FOURIER;
+  Buf buf(st);
+#define STEP(x) \
+  if (buf.e == cudaSuccess) buf.e = (x)
+  auto zeros = [&](int64_t r, int64_t cols) {
+    float* q = buf.get<float>((size_t)(r * cols));
+    STEP(cudaMemsetAsync(q, 0, sizeof(float) * (size_t)(r * cols), st));
+    return q;
+  };
+  auto put = [&](float* dst, int64_t ldd, const float* src, int64_t lds, int64_t r, int64_t cols) {
+    STEP(cudaMemcpy2DAsync(dst, sizeof(float) * ldd, src, sizeof(float) * lds, sizeof(float) * cols, r,
+                           cudaMemcpyDeviceToDevice, st));
+  };
+  float* Gq = zeros(mq, pq);  // G_p, rows and columns cut into b-wide pieces
+  put(Gq, pq, G, ldg, m, p);
+  if (left) {
+    const int64_t nbr = c->blk.nbr, nbc = c->blk.nbc, nbl = pq / bs;
+    if (dA) {
+      float* DBq = zeros(nq, pq);                  // Re dB in the n x p corner
+      float* IBq = cplx ? zeros(nq, pq) : nullptr;  // Im B~
+      float* Dq = zeros(mq, nq);                   // dA on the padded shape
+      STEP(right_dense(b, false, DBq, pq, st));
+      if (IBq) STEP(right_dense(b, true, IBq, pq, st));
+      switch (b->method) {  // Re(G B~^T), the m x n corner
+        case AMM_SVD: STEP(svd_rt_apply(b, G, ldg, m, Dq, nq, st)); break;
+        case AMM_SPARSE_FOURIER:
+          STEP(ft_rt_apply_bw((int)n, (int)m, (int)p, b->ft.T, b->ft.maskT, (int)b->k, b->ft.tw, G, ldg, Dq, nq, st));
+          break;
+        default: STEP(cyc_rt_apply((int)n, G, ldg, b->cy.so.sel, (int)b->k, b->cy.cyc, Dq, nq, st)); break;
+      }
+      for (int64_t i = 0; i < nbr; ++i)
+        for (int64_t j = 0; j < nbc; ++j)
+          for (int64_t l = 0; l < nbl; ++l) {
+            const float* Gil = Gq + i * bs * pq + l * bs;
+            float* Dij = Dq + i * bs * nq + j * bs;
+            STEP(cd_project_product(sub(i, j), false, Gil, pq, DBq + j * bs * pq + l * bs, pq, Dij, nq, st));
+            if (IBq) STEP(cd_project_product(sub(i, j), false, Gil, pq, IBq + j * bs * pq + l * bs, pq, Dij, nq, st, true));
+          }
+      put(dA, ldda, Dq, nq, m, n);
+    }
+    if (dB) {
+      float* Eq = zeros(nq, pq);  // Re(A~_p^T G_p), block column j = sum_i A~_ij^T G_i
+      for (int64_t j = 0; j < nbc; ++j)
+        for (int64_t i = 0; i < nbr; ++i) {
+          const Handle* s = sub(i, j);
+          STEP(cd_apply(bsi, false, Gq + i * bs * pq, pq, false, pq, s->cd.tw, s->cd.so.ulist, s->cd.Lw,
+                        s->cd.so.counts, nullptr, nullptr, Eq + j * bs * pq, pq, i > 0, st, 1));
+        }
+      put(dB, lddb, Eq, pq, n, p);
+      float* DAq = buf.get<float>((size_t)(mq * nq));               // Re dA_p
+      float* IAq = cplx ? buf.get<float>((size_t)(mq * nq)) : nullptr;  // Im A~_p
+      STEP(blocked_residual(a, false, DAq, nq, st));
+      if (IAq) STEP(blocked_residual(a, true, IAq, nq, st));
+      switch (b->method) {  // + Re P_B'(dA^T G) over the first m rows and n columns
+        case AMM_SVD: STEP(svd_proj_right(b, DAq, nq, G, ldg, m, dB, lddb, st)); break;
+        case AMM_SPARSE_FOURIER:
+          STEP(ft_proj_right((int)n, (int)m, (int)p, b->ft.sel, (int)b->k, b->ft.tw, DAq, IAq, -1, nq, G, ldg, dB,
+                             lddb, st));
+          break;
+        default: {  // square: the selected diagonals of dA^T G
+          float* DAT = buf.get<float>((size_t)(n * n));
+          float* GT = buf.get<float>((size_t)(n * n));
+          STEP(transpose_f32(DAq, n, n, nq, DAT, n, st));
+          STEP(transpose_f32(G, n, n, ldg, GT, n, st));
+          STEP(cyc_diag_project((int)n, (int)n, DAT, n, GT, n, b->cy.so.sel, (int)b->k, dB, lddb, st));
+        }
+      }
+    }
+  } else {
+    const int64_t nbr = c->blk.nbr, nbc = c->blk.nbc, nbi = mq / bs;
+    if (dA) {
+      float* Dq = zeros(m, nq);  // Re(G_p B~_p^T), block column j = sum_l G_l B~_jl^T
+      for (int64_t j = 0; j < nbr; ++j)
+        for (int64_t l = 0; l < nbc; ++l) {
+          const Handle* s = sub(j, l);
+          STEP(cd_apply(bsi, true, Gq + l * bs, pq, false, m, s->cd.tw, s->cd.so.ulist, s->cd.Lw, s->cd.so.counts,
+                        nullptr, nullptr, Dq + j * bs, nq, l > 0, st, 0));
+        }
+      put(dA, ldda, Dq, nq, m, n);
+      float* DBq = buf.get<float>((size_t)(nq * pq));               // Re dB_p
+      float* IBq = cplx ? buf.get<float>((size_t)(nq * pq)) : nullptr;  // Im B~_p
+      STEP(blocked_residual(b, false, DBq, pq, st));
+      if (IBq) STEP(blocked_residual(b, true, IBq, pq, st));
+      switch (a->method) {  // + Re P_A'(G dB^T) over the first n rows and p columns
+        case AMM_SVD: STEP(svd_proj_left(a, G, ldg, DBq, pq, p, dA, ldda, st)); break;
+        case AMM_SPARSE_FOURIER:
+          STEP(ft_proj_left((int)n, (int)m, (int)p, a->ft.sel, (int)a->k, a->ft.tw, G, ldg, DBq, IBq, -1, pq, dA,
+                            ldda, st));
+          break;
+        default:  // square: the selected diagonals of G dB^T (rows of Gq and DBq are 16-byte aligned)
+          STEP(cyc_diag_project((int)n, (int)n, Gq, pq, DBq, pq, a->cy.so.sel, (int)a->k, dA, ldda, st));
+          break;
+      }
+    }
+    if (dB) {
+      switch (a->method) {  // Re(A~^T G)
+        case AMM_SVD: STEP(svd_lt_apply(a, G, ldg, p, dB, lddb, st)); break;
+        case AMM_SPARSE_FOURIER:
+          STEP(ft_lt_apply_bw((int)n, (int)m, (int)p, a->ft.TT, a->ft.maskT, (int)a->k, a->ft.tw, G, ldg, dB, lddb,
+                              st));
+          break;
+        default: STEP(cyc_lt_apply((int)n, G, ldg, a->cy.so.sel, (int)a->k, a->cy.cyc, dB, lddb, st)); break;
+      }
+      float* DAq = zeros(mq, nq);                  // Re dA in the m x n corner
+      float* IAq = cplx ? zeros(mq, nq) : nullptr;  // Im A~
+      STEP(residual(a, DAq, nq, st));
+      if (IAq) STEP(imag_part(a, IAq, nq, st));
+      float* Eq = zeros(nq, pq);  // Re P_B'(dA_p^T G_p), block jl = sum_i P_jl'(dA_ij^T G_il)
+      for (int64_t j = 0; j < nbr; ++j)
+        for (int64_t l = 0; l < nbc; ++l)
+          for (int64_t i = 0; i < nbi; ++i) {
+            const float* Gil = Gq + i * bs * pq + l * bs;
+            float* Ejl = Eq + j * bs * pq + l * bs;
+            STEP(cd_project_product(sub(j, l), true, DAq + i * bs * nq + j * bs, nq, Gil, pq, Ejl, pq, st));
+            if (IAq) STEP(cd_project_product(sub(j, l), true, IAq + i * bs * nq + j * bs, nq, Gil, pq, Ejl, pq, st, true));
+          }
+      if (buf.e == cudaSuccess) {
+        add_diff_kernel<<<(unsigned)((n * p + 255) / 256), 256, 0, st>>>(dB, lddb, Eq, pq, nullptr, 0, n, p);
+        buf.e = cudaGetLastError();
+      }
+    }
+  }
+#undef STEP
+  if (buf.e != cudaSuccess) return cuda_fail(buf.e, "mixed-method backward with circulant blocks");
   return AMM_OK;
 }
 

@@ -124,6 +124,54 @@ def test_blocked_mixed(other, blocked_side):
     assert err <= TOL, (other, blocked_side, err)
 
 
+def _mixed_shapes(other, blocked_side):
+    if other == "svd":
+        return (90, 128, 200) if blocked_side == "right" else (200, 100, 128)
+    if other == "cycle":  # square, in 2 x 2 blocks
+        return 128, 128, 128
+    return (70, 128, 200) if blocked_side == "right" else (200, 128, 50)
+
+
+@pytest.mark.parametrize("other", ["svd", "fourier", "cycle"])
+@pytest.mark.parametrize("blocked_side", ["left", "right"])
+def test_blocked_mixed_backward(other, blocked_side):
+    """Gradients of the blocked x other-method product with the projectors frozen: G padded with
+    zeros, each block's adjoint on b-wide pieces of the inner sums, the gradients cropped; k = 6
+    splits conjugate pairs in some blocks, so beside the Fourier sparsifier the imaginary parts
+    enter as well.  Also one gradient at a time."""
+    torch, amm = torch_cuda()
+    m, n, p = _mixed_shapes(other, blocked_side)
+    a, b = _pair(m, n, p, 66)
+    gr = S.rng(66, 1).standard_normal((m, p))
+    A, B, G = dev32(torch, a), dev32(torch, b), dev32(torch, gr)
+    k, bs = 6, 64
+    if blocked_side == "left":
+        hA = amm.decompose(A, "circulant", k, "left", block=bs)
+        ta = _oracle_trunc(hA, as64(A), bs, k)
+        hB, tb = _other(torch, amm, B, other, k, "right", 66)
+    else:
+        hA, ta = _other(torch, amm, A, other, k, "left", 66)
+        hB = amm.decompose(B, "circulant", k, "right", block=bs)
+        tb = _oracle_trunc(hB, as64(B), bs, k)
+    rda, rdb = O.blocked_mixed_backward(ta, tb, as64(G))
+    dA, dB = amm.approx_matmul_backward(hA, hB, G)
+    ea, eb = rel(dA.double().cpu().numpy(), rda), rel(dB.double().cpu().numpy(), rdb)
+    assert ea <= TOL and eb <= TOL, (other, blocked_side, ea, eb)
+    dA1, _ = amm.approx_matmul_backward(hA, hB, G, need_dB=False)
+    _, dB1 = amm.approx_matmul_backward(hA, hB, G, need_dA=False)
+    assert rel(dA1.double().cpu().numpy(), rda) <= TOL and rel(dB1.double().cpu().numpy(), rdb) <= TOL
+
+
+def test_blocked_cycle_backward_needs_square():
+    torch, amm = torch_cuda()
+    a, b = _pair(96, 128, 128, 67)
+    A, B = dev32(torch, a), dev32(torch, b)
+    hA = amm.decompose(A, "circulant", 4, "left", block=64)
+    hB = amm.decompose(B, "cycle", 4, "right")
+    with pytest.raises(RuntimeError, match="square"):
+        amm.approx_matmul_backward(hA, hB, dev32(torch, np.ones((96, 128))))
+
+
 def test_blocked_argument_errors():
     torch, amm = torch_cuda()
     a, b = _pair(64, 128, 64, 66)

@@ -75,10 +75,7 @@ def test_mixed_untruncated_reproduces_product():
     assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= 1e-5
 
 
-MIX3 = [(x, y) for x in ("circulant", "svd", "cycle") for y in ("circulant", "svd", "cycle") if x != y]
-
-
-@pytest.mark.parametrize("ma,mb", MIX3)
+@pytest.mark.parametrize("ma,mb", PAIRS)
 @pytest.mark.parametrize("n,k", [(64, 5), (96, 7), (256, 9)])
 def test_mixed_backward(ma, mb, n, k):
     """dA = Re[G B~^T + P_A'(G dB^T)], dB = Re[A~^T G + P_B'(dA^T G)] with each operand's own
@@ -97,16 +94,47 @@ def test_mixed_backward(ma, mb, n, k):
     assert ea <= TOL and eb <= TOL, (ma, mb, n, ea, eb)
 
 
+def _split_selection(n):
+    """k = 5 circulant components with two split conjugate pairs (1 without n - 1, 3 without n - 3)."""
+    return [0, 1, 5, n - 5, 3]
+
+
+@pytest.mark.parametrize("circ_left", [True, False])
+@pytest.mark.parametrize("n", [64, 96])
+def test_mixed_backward_split_pair_with_fourier(circ_left, n):
+    """Circulant x Fourier with a split conjugate pair: both truncations are complex, so the
+    imaginary parts Im A~, Im B~ enter the adjoint projections; also one gradient at a time."""
+    torch, amm = torch_cuda()
+    g = S.rng(n, 13)
+    a = g.standard_normal((n, n)) + 0.5
+    b = S.toeplitz_uniform(n, g) + 0.1 * g.standard_normal((n, n))
+    gr = g.standard_normal((n, n))
+    A, B, G = dev32(torch, a), dev32(torch, b), dev32(torch, gr)
+    sel = _split_selection(n)
+    if circ_left:
+        hA = amm.decompose(A, "circulant", 5, "left", forced_selection=sel)
+        ta = O.truncate_circulant(as64(A), 5, sel)
+        hB, tb = _handle(torch, amm, B, "fourier", 6, "right", n)
+    else:
+        hA, ta = _handle(torch, amm, A, "fourier", 6, "left", n)
+        hB = amm.decompose(B, "circulant", 5, "right", forced_selection=sel)
+        tb = O.truncate_circulant(as64(B), 5, sel)
+    assert np.abs(np.imag(ta.approx)).max() > 1e-3 and np.abs(np.imag(tb.approx)).max() > 1e-3
+    rda, rdb = O.mixed_backward(ta, tb, as64(G))
+    dA, dB = amm.approx_matmul_backward(hA, hB, G)
+    ea, eb = rel(dA.double().cpu().numpy(), rda), rel(dB.double().cpu().numpy(), rdb)
+    assert ea <= TOL and eb <= TOL, (circ_left, n, ea, eb)
+    dA1, none_b = amm.approx_matmul_backward(hA, hB, G, need_dB=False)
+    none_a, dB1 = amm.approx_matmul_backward(hA, hB, G, need_dA=False)
+    assert none_b is None and none_a is None
+    assert rel(dA1.double().cpu().numpy(), rda) <= TOL and rel(dB1.double().cpu().numpy(), rdb) <= TOL
+
+
 def test_mixed_backward_reports_what_is_not_built():
     torch, amm = torch_cuda()
     n = 32
     g = S.rng(10, 0)
-    A, B = dev32(torch, g.standard_normal((n, n))), dev32(torch, g.standard_normal((n, n)))
-    G = dev32(torch, g.standard_normal((n, n)))
-    hA = amm.decompose(A, "fourier", 3, "left")
-    hB = amm.decompose(B, "circulant", 3, "right")
-    with pytest.raises(RuntimeError, match="Fourier"):
-        amm.approx_matmul_backward(hA, hB, G)
+    B = dev32(torch, g.standard_normal((n, n)))
     # rectangular operands: the circulant / cycle projections of the mixed backward are square
     A2 = dev32(torch, g.standard_normal((48, n)))
     phi = dev32(torch, S.sketch(n, 3, 10, 0))

@@ -621,6 +621,38 @@ def test_blocked_backward_matches_bruteforce():
     assert np.abs(f(a, b) - np.sum(gr * O.blocked_first_order(ta, tb))) < 1e-10
 
 
+@pytest.mark.parametrize("other", ["svd", "fourier", "cycle"])
+@pytest.mark.parametrize("blocked_left", [True, False])
+def test_blocked_mixed_backward_matches_bruteforce(other, blocked_left):
+    """Readings R10 + R13 for a blockwise circulant operand beside another method: the gradients
+    equal <G, M(E_ij)> of the frozen padded-and-cropped map over every basis matrix, and the frozen
+    map at the operands themselves is the blocked mixed product (ragged blocks on both sides)."""
+    bs, k = 4, 2
+    m, n, p = (5, 6, 6) if other == "cycle" else (5, 6, 7)
+    if other == "cycle" and not blocked_left:
+        m = 6
+    g = S.rng(58, int(blocked_left))
+    a, b, gr = g.standard_normal((m, n)) + 0.3, g.standard_normal((n, p)), g.standard_normal((m, p))
+    if blocked_left:
+        ta, tb = O.truncate_circulant_blocked(a, bs, k), _trunc_side(other, b, k, "right", 58)
+    else:
+        ta, tb = _trunc_side(other, a, k, "left", 58), O.truncate_circulant_blocked(b, bs, k)
+    da, db = O.blocked_mixed_backward(ta, tb, gr)
+    assert da.shape == (m, n) and db.shape == (n, p)
+    f = lambda x, y: np.sum(gr * O.frozen_blocked_mixed_product(ta, tb, x, y))
+    assert abs(f(a, b) - np.sum(gr * O.blocked_first_order(ta, tb))) < 1e-10
+    bda, bdb = np.zeros_like(a), np.zeros_like(b)
+    for i, j in itertools.product(range(m), range(n)):
+        e = np.zeros_like(a)
+        e[i, j] = 1.0
+        bda[i, j] = f(e, b) - f(np.zeros_like(a), b)
+    for i, j in itertools.product(range(n), range(p)):
+        e = np.zeros_like(b)
+        e[i, j] = 1.0
+        bdb[i, j] = f(a, e) - f(a, np.zeros_like(b))
+    assert np.abs(da - bda).max() < 1e-12 and np.abs(db - bdb).max() < 1e-12
+
+
 # --------------------------------------------------------------------------- printed tables
 
 def _table_rows():
