@@ -128,12 +128,12 @@ cudaError_t ft_rt_apply_bw(int n, int m, int p, const float2* Bt, const uint32_t
                            const float* G, int64_t ldg, float* out, int64_t ldo, cudaStream_t st);
 cudaError_t ft_lt_apply_bw(int n, int m, int p, const float2* AtT, const uint32_t* maskA, int ka, const float2* tw,
                            const float* G, int64_t ldg, float* out, int64_t ldo, cudaStream_t st);
-cudaError_t ft_proj_left(int n, int m, int p, const int32_t* selA, int ka, const float2* tw, const float* G,
-                         int64_t ldg, const float* Dre, const float* Dim, int sign_im, int64_t ldd, float* out,
-                         int64_t ldo, cudaStream_t st);
-cudaError_t ft_proj_right(int n, int m, int p, const int32_t* selB, int kb, const float2* tw, const float* Dre,
-                          const float* Dim, int sign_im, int64_t ldd, const float* G, int64_t ldg, float* out,
-                          int64_t ldo, cudaStream_t st);
+cudaError_t ft_proj_left(int n, int m, int p, const int32_t* selA, const uint32_t* maskA, int ka, const float2* tw,
+                         const float* G, int64_t ldg, const float* Dre, const float* Dim, int sign_im, int64_t ldd,
+                         float* out, int64_t ldo, cudaStream_t st);
+cudaError_t ft_proj_right(int n, int m, int p, const int32_t* selB, const uint32_t* maskB, int kb,
+                          const float2* tw, const float* Dre, const float* Dim, int sign_im, int64_t ldd,
+                          const float* G, int64_t ldg, float* out, int64_t ldo, cudaStream_t st);
 
 // umma_gemm.cu: C = alpha A B^T + beta C on tcgen05 tensor cores (A, B K-major);
 // tf32 = FP32 inputs with TF32 hi/lo splitting, else BF16 inputs.  err: device flag.

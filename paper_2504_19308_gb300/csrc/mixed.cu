@@ -310,7 +310,8 @@ amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, f
           if (e == cudaSuccess && IB) e = cd_project_product(a, false, G, ldg, IB, nn, dA, ldda, st, true);
           break;
         case AMM_SPARSE_FOURIER:
-          e = ft_proj_left(nn, nn, nn, a->ft.sel, (int)a->k, a->ft.tw, G, ldg, DB, IB, -1, nn, dA, ldda, st);
+          e = ft_proj_left(nn, nn, nn, a->ft.sel, a->ft.maskT, (int)a->k, a->ft.tw, G, ldg, DB, IB, -1, nn, dA, ldda,
+                           st);
           break;
         default: e = cyc_diag_project(nn, nn, Ga, ldga, DB, nn, a->cy.so.sel, (int)a->k, dA, ldda, st); break;
       }
@@ -338,7 +339,8 @@ amm_status_t mixed_backward(Handle* a, Handle* b, const float* G, int64_t ldg, f
           if (e == cudaSuccess && IA) e = cd_project_product(b, true, IA, nn, G, ldg, dB, lddb, st, true);
           break;
         case AMM_SPARSE_FOURIER:
-          e = ft_proj_right(nn, nn, nn, b->ft.sel, (int)b->k, b->ft.tw, DA, IA, -1, nn, G, ldg, dB, lddb, st);
+          e = ft_proj_right(nn, nn, nn, b->ft.sel, b->ft.maskT, (int)b->k, b->ft.tw, DA, IA, -1, nn, G, ldg, dB, lddb,
+                            st);
           break;
         default: {
           // (dA^T G)((l + s), l) = <dA^T(l + s, :), G^T(l, :)>
@@ -494,7 +496,8 @@ amm_status_t mixed_backward_blocked(Handle* a, Handle* b, const float* G, int64_
             const float* Gil = Gq + i * bs * pq + l * bs;
             float* Dij = Dq + i * bs * nq + j * bs;
             STEP(cd_project_product(sub(i, j), false, Gil, pq, DBq + j * bs * pq + l * bs, pq, Dij, nq, st));
-            if (IBq) STEP(cd_project_product(sub(i, j), false, Gil, pq, IBq + j * bs * pq + l * bs, pq, Dij, nq, st, true));
+            if (IBq)
+              STEP(cd_project_product(sub(i, j), false, Gil, pq, IBq + j * bs * pq + l * bs, pq, Dij, nq, st, true));
           }
       put(dA, ldda, Dq, nq, m, n);
     }
@@ -514,8 +517,8 @@ amm_status_t mixed_backward_blocked(Handle* a, Handle* b, const float* G, int64_
       switch (b->method) {  // + Re P_B'(dA^T G) over the first m rows and n columns
         case AMM_SVD: STEP(svd_proj_right(b, DAq, nq, G, ldg, m, dB, lddb, st)); break;
         case AMM_SPARSE_FOURIER:
-          STEP(ft_proj_right((int)n, (int)m, (int)p, b->ft.sel, (int)b->k, b->ft.tw, DAq, IAq, -1, nq, G, ldg, dB,
-                             lddb, st));
+          STEP(ft_proj_right((int)n, (int)m, (int)p, b->ft.sel, b->ft.maskT, (int)b->k, b->ft.tw, DAq, IAq, -1, nq,
+                             G, ldg, dB, lddb, st));
           break;
         default: {  // square: the selected diagonals of dA^T G
           float* DAT = buf.get<float>((size_t)(n * n));
@@ -544,8 +547,8 @@ amm_status_t mixed_backward_blocked(Handle* a, Handle* b, const float* G, int64_
       switch (a->method) {  // + Re P_A'(G dB^T) over the first n rows and p columns
         case AMM_SVD: STEP(svd_proj_left(a, G, ldg, DBq, pq, p, dA, ldda, st)); break;
         case AMM_SPARSE_FOURIER:
-          STEP(ft_proj_left((int)n, (int)m, (int)p, a->ft.sel, (int)a->k, a->ft.tw, G, ldg, DBq, IBq, -1, pq, dA,
-                            ldda, st));
+          STEP(ft_proj_left((int)n, (int)m, (int)p, a->ft.sel, a->ft.maskT, (int)a->k, a->ft.tw, G, ldg, DBq, IBq, -1,
+                            pq, dA, ldda, st));
           break;
         default:  // square: the selected diagonals of G dB^T (rows of Gq and DBq are 16-byte aligned)
           STEP(cyc_diag_project((int)n, (int)n, Gq, pq, DBq, pq, a->cy.so.sel, (int)a->k, dA, ldda, st));
@@ -572,7 +575,8 @@ amm_status_t mixed_backward_blocked(Handle* a, Handle* b, const float* G, int64_
             const float* Gil = Gq + i * bs * pq + l * bs;
             float* Ejl = Eq + j * bs * pq + l * bs;
             STEP(cd_project_product(sub(j, l), true, DAq + i * bs * nq + j * bs, nq, Gil, pq, Ejl, pq, st));
-            if (IAq) STEP(cd_project_product(sub(j, l), true, IAq + i * bs * nq + j * bs, nq, Gil, pq, Ejl, pq, st, true));
+            if (IAq)
+              STEP(cd_project_product(sub(j, l), true, IAq + i * bs * nq + j * bs, nq, Gil, pq, Ejl, pq, st, true));
           }
       if (buf.e == cudaSuccess) {
         add_diff_kernel<<<(unsigned)((n * p + 255) / 256), 256, 0, st>>>(dB, lddb, Eq, pq, nullptr, 0, n, p);
