@@ -633,6 +633,8 @@ KERNEL_OF = {
     "umma_splitk_reduce": "umma_splitk_reduce_kernel", "ft_row_transform": "ft_transform_kernel",
     "ft_col_transform": "ft_transform_kernel", "ft_t1": "ft_t1_kernel", "ft_t2": "ft_t2_kernel",
     "cyc_apply_col": "cyc_apply_col_kernel", "cyc_apply_row": "cyc_apply_row_kernel",
+    "ft_bw_gba": "ft_bw_spmm_kernel", "ft_bw_aag": "ft_bw_spmm_kernel", "ft_bw_pa": "ft_bw_sampled_kernel",
+    "ft_bw_pb": "ft_bw_sampled_kernel", "ft_bw_idft_rows": "ft_bw_real_kernel", "ft_bw_dft_cols": "ft_bw_real_kernel",
 }
 # Family of a kernel for the per-family roofline entries.
 FAMILY_OF = {
@@ -641,11 +643,17 @@ FAMILY_OF = {
     "cd_sddmm_tiled_kernel": "sddmm", "umma_gemm_kernel<true>": "tcgen05_gemm",
     "umma_gemm_kernel<false>": "tcgen05_gemm", "ft_t1_kernel": "sparsifier_apply", "ft_t2_kernel": "sparsifier_apply",
     "cyc_apply_col_kernel": "sparsifier_apply", "cyc_apply_row_kernel": "sparsifier_apply",
+    "ft_bw_spmm_kernel": "sparsifier_backward", "ft_bw_sampled_kernel": "sparsifier_backward",
 }
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one-kernel ncu captures
-# (3 launches each of the headline step, profile_case --le1pct), keyed by kernel; an entry is dropped
-# when its kernel changes (None = not captured as it stands)
-NCU_TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, averaged over every launch of
+# the kernel in one headline step (profile_case --headline, the seven products timed here), from one
+# single-pass ncu capture (profiles/dram_headline_step_kernels.md); an entry is dropped when its
+# kernel changes (absent = not captured as it stands)
+NCU_TRAFFIC = {
+    "umma_gemm_kernel<true>": 25.94e6, "cd_apply_kernel": 89.17e6, "cd_residual_kernel": 41.89e6,
+    "cd_sddmm_kernel": 93.72e6, "ft_t2_kernel": 89.15e6, "bw_spectrum_kernel": 58.31e6,
+    "cd_spectrum_kernel": 93.69e6, "ft_bw_spmm_kernel": 143.51e6, "ft_bw_sampled_kernel": 310.32e6,
+}
 
 
 def fp32_peak(dev, clocks):
