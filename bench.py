@@ -423,7 +423,7 @@ def batched_form(args, torch, amm, dev, pairs, sk, fp32_ms, dist, bf16=False):
             "speedup_vs_fp32": fp32_ms / ms, "approx_rel_err_vs_exact": errs,
             "all_le_1pct": all(v <= 0.01 for v in errs.values()),
             "mode": ("BF16 operands, " if bf16 else "FP32, ") + "one CUDA graph of the batch scheduler "
-                    "(8 forked streams)"}
+                    "(16 forked streams)"}
 
 
 def sweep_form(args, torch, amm, dev, dist):
