@@ -45,6 +45,7 @@ constexpr int UM_BM = 128;
 constexpr int UM_THREADS = 192;
 constexpr int UM_TF32_MAX_KB = 16;  // longest TF32X3 accumulation chain, in 32-wide k-blocks
 constexpr int UM_CTA_FIXED_KB = 8;  // per-CTA set-up and epilogue cost, in k-blocks (split choice)
+constexpr int UM_SHORT_KB = 4;      // k-blocks up to which a wide output takes the short ring
 constexpr uint32_t UM_SPIN_LIMIT = 1u << 26;  // ~ seconds of polling, then give up
 
 // ----------------------------------------------------------------------------- PTX wrappers
@@ -156,7 +157,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // BF16 tiles go from the TMA ring straight to the MMAs.  TF32X3 tiles are split into hi/lo by
 // the four epilogue warps, which release the raw stage as soon as it is read, so TMA keeps
 // RAW stages in flight while the MMAs work from the split ring.
-template <bool TF32, int BN>
+// SHORT: a ring for products of at most UM_SHORT_KB k-blocks (two TMA stages, one split slot), so
+// that two CTAs fit per SM and one CTA's prologue and epilogue overlap the other's work; used for
+// the wide outputs of short contractions (the n x n product of two n x 2k factors).
+template <bool TF32, int BN, bool SHORT = false>
 struct UmmaCfg {
   static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128, "tile widths of the M = 128 MMA used here");
   static constexpr int ELEM = TF32 ? 4 : 2;
@@ -167,10 +171,11 @@ struct UmmaCfg {
   // the thinnest tiles run two CTAs per SM (each CTA's prologue, pipeline fill and epilogue then
   // overlap the other's streaming), with the ring depth cut to fit: BN = 16 in both modes, BN = 32
   // in BF16
-  static constexpr int CTAS = (BN == 16 || (!TF32 && BN == 32)) ? 2 : 1;
-  static constexpr int RAW = TF32 ? (BN == 128 ? 3 : BN == 16 ? 2 : 4) : (CTAS == 2 ? 5 : BN == 128 ? 5 : 7);  // TMA stages
+  static constexpr int CTAS = (SHORT || BN == 16 || (!TF32 && BN == 32)) ? 2 : 1;
+  static constexpr int RAW = SHORT ? 2
+                             : TF32 ? (BN == 128 ? 3 : BN == 16 ? 2 : 4) : (CTAS == 2 ? 5 : BN == 128 ? 5 : 7);  // TMA stages
   static constexpr int RAW_BYTES = A_BYTES + B_BYTES;        // A, B
-  static constexpr int SLOTS = TF32 ? (BN == 32 ? 3 : 2) : 0;  // split slots
+  static constexpr int SLOTS = TF32 ? (SHORT ? 1 : BN == 32 ? 3 : 2) : 0;  // split slots
   static constexpr int SLOT_BYTES = 2 * RAW_BYTES;           // A hi, B hi, A lo, B lo
   // accumulator columns (TF32X3: main + correction), a power of two >= 32 as tcgen05.alloc requires
   static constexpr uint32_t TMEM_COLS = (TF32 ? 2 * BN : BN) < 32 ? 32u : (uint32_t)(TF32 ? 2 * BN : BN);
@@ -207,12 +212,12 @@ __device__ __forceinline__ void split_tile(const float* raw, float* hi, float* l
 // TRANS: the kernel computes C^T = B A^T (its M, N are the caller's N, M) and stores C itself:
 // element (i, j) of its tile goes to C[j * ldc + i], so a warp's 32 lanes (consecutive i) write 128
 // contiguous bytes per column j; split partials are kept in C's own [z][N][M] layout.
-template <bool TF32, int BN, bool TRANS>
-__global__ void __launch_bounds__(UM_THREADS, UmmaCfg<TF32, BN>::CTAS)
+template <bool TF32, int BN, bool TRANS, bool SHORT = false>
+__global__ void __launch_bounds__(UM_THREADS, UmmaCfg<TF32, BN, SHORT>::CTAS)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                      int K, float alpha, float beta, float* __restrict__ C, int64_t ldc, int per,
                      float* __restrict__ ws, int* __restrict__ err) {
-  using Cfg = UmmaCfg<TF32, BN>;
+  using Cfg = UmmaCfg<TF32, BN, SHORT>;
   constexpr int RAW = Cfg::RAW;
   constexpr int SLOTS = Cfg::SLOTS > 0 ? Cfg::SLOTS : 1;
   extern __shared__ unsigned char smem_raw[];
@@ -497,8 +502,12 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
     std::swap(A, B);
     std::swap(lda, ldb);
   }
-  // the narrowest tile that covers a thin N (one column of tiles), else 128 columns
-  const int bn = N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  // the narrowest tile that covers a thin N (one column of tiles), else 128 columns; a short K with
+  // a wide output takes 64-column tiles on the two-CTA short ring
+  const int bk0 = 128 / elem;
+  const bool shortk = (K + bk0 - 1) / bk0 <= UM_SHORT_KB && N > 64 &&
+                      (int64_t)((M + UM_BM - 1) / UM_BM) * ((N + 63) / 64) >= 4 * (int64_t)umma_num_sms();
+  const int bn = shortk ? 64 : N <= 16 ? 16 : N <= 32 ? 32 : N <= 64 ? 64 : 128;
   CUtensorMap ta, tb;
   if ((e = make_map(&ta, A, tf32, M, K, lda, UM_BM)) != cudaSuccess) return e;
   if ((e = make_map(&tb, B, tf32, N, K, ldb, bn)) != cudaSuccess) return e;
@@ -509,7 +518,7 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
   // about UM_CTA_FIXED_KB k-blocks) + the partial sums, with TF32X3 chains of at most
   // UM_TF32_MAX_KB k-blocks (the tensor core's FP32 accumulation loses up to an ulp per MMA; longer
   // K is split and the partials are summed with compensation)
-  const int nsm = umma_num_sms() * ((bn == 16 || (!tf32 && bn == 32)) ? 2 : 1);  // CTAs resident at once (UmmaCfg::CTAS)
+  const int nsm = umma_num_sms() * ((shortk || bn == 16 || (!tf32 && bn == 32)) ? 2 : 1);  // resident CTAs (UmmaCfg::CTAS)
   const int smin = tf32 ? std::max(1, (kblocks + UM_TF32_MAX_KB - 1) / UM_TF32_MAX_KB) : 1;
   const int smax = std::max(smin, std::min(32, kblocks / 2));
   int splits = smin;
@@ -533,39 +542,43 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
   {
     AMM_TRACE_W(tf32 ? "umma_gemm_tf32x3" : "umma_gemm_bf16", st, 2.0 * M * N * (double)K,
                 (double)elem * ((double)M * K + (double)N * K) + 4.0 * M * N, nullptr);
-    auto launch = [&](auto tf32_c, auto bn_c) -> cudaError_t {
+    auto launch = [&](auto tf32_c, auto bn_c, auto short_c) -> cudaError_t {
       constexpr bool T = decltype(tf32_c)::value;
       constexpr int BN = decltype(bn_c)::value;
-      using Cfg = UmmaCfg<T, BN>;
+      constexpr bool SH = decltype(short_c)::value;
+      using Cfg = UmmaCfg<T, BN, SH>;
       static DeviceOnce once;
       const cudaError_t a = once([] {
-        cudaError_t r = cudaFuncSetAttribute((const void*)umma_gemm_kernel<T, BN, false>,
+        cudaError_t r = cudaFuncSetAttribute((const void*)umma_gemm_kernel<T, BN, false, SH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
         if (r == cudaSuccess)
-          r = cudaFuncSetAttribute((const void*)umma_gemm_kernel<T, BN, true>,
+          r = cudaFuncSetAttribute((const void*)umma_gemm_kernel<T, BN, true, SH>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
         return r;
       });
       if (a != cudaSuccess) return a;
       if (trans)
-        umma_gemm_kernel<T, BN, true><<<grid, UM_THREADS, Cfg::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc, per,
-                                                                          ws, err);
+        umma_gemm_kernel<T, BN, true, SH><<<grid, UM_THREADS, Cfg::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
+                                                                              per, ws, err);
       else
-        umma_gemm_kernel<T, BN, false><<<grid, UM_THREADS, Cfg::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc, per,
-                                                                           ws, err);
+        umma_gemm_kernel<T, BN, false, SH><<<grid, UM_THREADS, Cfg::SMEM, st>>>(ta, tb, M, N, K, alpha, beta, C, ldc,
+                                                                               per, ws, err);
       return cudaSuccess;
     };
     using I16 = std::integral_constant<int, 16>;
     using I32 = std::integral_constant<int, 32>;
     using I64 = std::integral_constant<int, 64>;
     using I128 = std::integral_constant<int, 128>;
+    using NO = std::false_type;
     cudaError_t la;
     if (tf32)
-      la = bn == 16 ? launch(std::true_type{}, I16{}) : bn == 32 ? launch(std::true_type{}, I32{})
-         : bn == 64 ? launch(std::true_type{}, I64{}) : launch(std::true_type{}, I128{});
+      la = shortk ? launch(std::true_type{}, I64{}, std::true_type{})
+         : bn == 16 ? launch(std::true_type{}, I16{}, NO{}) : bn == 32 ? launch(std::true_type{}, I32{}, NO{})
+         : bn == 64 ? launch(std::true_type{}, I64{}, NO{}) : launch(std::true_type{}, I128{}, NO{});
     else
-      la = bn == 16 ? launch(std::false_type{}, I16{}) : bn == 32 ? launch(std::false_type{}, I32{})
-         : bn == 64 ? launch(std::false_type{}, I64{}) : launch(std::false_type{}, I128{});
+      la = shortk ? launch(std::false_type{}, I64{}, std::true_type{})
+         : bn == 16 ? launch(std::false_type{}, I16{}, NO{}) : bn == 32 ? launch(std::false_type{}, I32{}, NO{})
+         : bn == 64 ? launch(std::false_type{}, I64{}, NO{}) : launch(std::false_type{}, I128{}, NO{});
     if (la != cudaSuccess) {
       dev_free(ws, st);
       return la;

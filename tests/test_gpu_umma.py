@@ -36,7 +36,9 @@ SHAPES = [(128, 128, 64), (128, 128, 32), (256, 384, 1024), (200, 130, 100), (40
           (4096, 16, 4096), (4096, 32, 512), (1000, 17, 333), (256, 64, 1024), (300, 8, 96), (512, 40, 256),
           (128, 1, 64), (2048, 48, 4096),
           # thin M, wide N: computed as C^T = B A^T and stored transposed
-          (16, 4096, 4096), (32, 777, 333), (48, 256, 1024), (1, 300, 64)]
+          (16, 4096, 4096), (32, 777, 333), (48, 256, 1024), (1, 300, 64),
+          # short K with a wide output: 64-column tiles on the two-CTA short ring (ragged K and N too)
+          (4096, 4096, 64), (4096, 4096, 32), (2048, 3000, 100), (1200, 4100, 120)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
@@ -63,6 +65,18 @@ def test_umma_tf32x3_fp32_accuracy(M, N, K):
     # FP32 level: a length-K FP32 dot product carries ~sqrt(K) * 2^-24 relative rounding error;
     # a TF32-only product would be ~1e-3
     assert err <= 4 * np.sqrt(K) * 2.0 ** -24, err
+
+
+def test_umma_short_ring_alpha_beta():
+    """The short ring with beta != 0 (C read back) and alpha != 1."""
+    torch, amm = torch_cuda()
+    M, N, K = 4096, 2048, 96
+    a = torch.randn((M, K), device="cuda")
+    b = torch.randn((N, K), device="cuda")
+    c0 = torch.randn((M, N), device="cuda")
+    C = _gemm(torch, amm, 0, a, b, c0=c0, alpha=1.5, beta=-0.25)
+    ref = 1.5 * (a.double() @ b.double().T) - 0.25 * c0.double()
+    assert float(torch.linalg.norm(C.double() - ref) / torch.linalg.norm(ref)) <= 4 * np.sqrt(K) * 2.0 ** -24
 
 
 def test_umma_alpha_beta():
