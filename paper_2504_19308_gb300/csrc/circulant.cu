@@ -155,9 +155,18 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
       for (int b = threadIdx.x; b < 256; b += SEL_T) hist[b] = 0;
       __syncthreads();
       const unsigned long long prefix = s_prefix;
-      for (int t = threadIdx.x; t < n; t += SEL_T) {
-        const unsigned long long kb = (unsigned long long)__double_as_longlong(key[t]);
-        if ((kb & mask) == prefix) atomicAdd(&hist[(kb >> shift) & 255ull], 1u);
+      // lanes of a warp that fall into the same bucket add together: one atomic per bucket and warp
+      // (the leading bytes of the keys crowd into few buckets)
+      for (int t0 = 0; t0 < n; t0 += SEL_T) {
+        const int t = t0 + threadIdx.x;
+        const unsigned long long kb = t < n ? (unsigned long long)__double_as_longlong(key[t]) : 0ull;
+        const bool part = t < n && (kb & mask) == prefix;
+        const unsigned pm = __ballot_sync(0xffffffffu, part);
+        if (part) {
+          const unsigned bkt = (unsigned)((kb >> shift) & 255ull);
+          const unsigned peers = __match_any_sync(pm, bkt);
+          if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bkt], (unsigned)__popc(peers));
+        }
       }
       __syncthreads();
       if (threadIdx.x < 32) {

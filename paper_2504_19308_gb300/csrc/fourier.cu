@@ -78,13 +78,32 @@ __global__ void __launch_bounds__(NT) ft_transform_kernel(const float* __restric
 // with key == tau, written in ascending q.
 constexpr int SEL_NT = 256;
 
+// Exclusive scan of x over the SEL_NT threads of the CTA (warp shuffles, then the warp totals);
+// s_warp: SEL_NT / 32 ints of shared memory.  Every thread must call it; ends with a barrier.
+__device__ __forceinline__ int sel_block_scan(int x, int* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int y = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, y, o);
+    if (lane >= o) y += t;
+  }
+  if (lane == 31) s_warp[warp] = y;
+  __syncthreads();
+  int before = 0;
+#pragma unroll
+  for (int w = 0; w < SEL_NT / 32; ++w) before += w < warp ? s_warp[w] : 0;
+  __syncthreads();  // s_warp may be reused by the next call
+  return before + y - x;
+}
+
 __global__ void __launch_bounds__(SEL_NT) ft_select_kernel(const float* __restrict__ mag, int n, int k,
                                                            int32_t* __restrict__ sel, uint32_t* __restrict__ maskT,
                                                            int mask_words) {
   extern __shared__ uint32_t keys[];  // kh
   __shared__ uint32_t hist[256];
   __shared__ uint32_t s_prefix, s_need;
-  __shared__ int scan[SEL_NT];
+  __shared__ int s_warp[SEL_NT / 32];
   const int row = blockIdx.x;
   const int kh = n / 2 + 1;
   for (int q = threadIdx.x; q < kh; q += SEL_NT) keys[q] = __float_as_uint(mag[(int64_t)row * kh + q]);
@@ -95,9 +114,24 @@ __global__ void __launch_bounds__(SEL_NT) ft_select_kernel(const float* __restri
     for (int b = threadIdx.x; b < 256; b += SEL_NT) hist[b] = 0;
     __syncthreads();
     const uint32_t prefix = s_prefix;
-    for (int q = threadIdx.x; q < n; q += SEL_NT) {
-      const uint32_t key = keys[q <= n / 2 ? q : n - q];
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    // each stored key q in [0, n/2] stands for q and n - q: counted twice here, q = 0 and q = n/2
+    // (their own mirrors) corrected below.  Lanes that fall into the same bucket add together (one
+    // atomic per bucket and warp: the leading bytes of the magnitudes crowd into few buckets).
+    for (int q0 = 0; q0 < kh; q0 += SEL_NT) {
+      const int q = q0 + threadIdx.x;
+      const uint32_t key = q < kh ? keys[q] : 0u;
+      const bool part = q < kh && (key & mask) == prefix;
+      const unsigned pm = __ballot_sync(0xffffffffu, part);
+      if (part) {
+        const uint32_t bkt = (key >> shift) & 255u;
+        const unsigned peers = __match_any_sync(pm, bkt);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bkt], 2u * __popc(peers));
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if ((keys[0] & mask) == prefix) hist[(keys[0] >> shift) & 255u] -= 1u;
+      if ((n & 1) == 0 && (keys[n / 2] & mask) == prefix) hist[(keys[n / 2] >> shift) & 255u] -= 1u;
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -119,16 +153,7 @@ __global__ void __launch_bounds__(SEL_NT) ft_select_kernel(const float* __restri
   int eq = 0;
   for (int q = q0; q < q1; ++q) eq += keys[q <= n / 2 ? q : n - q] == tau;
   // exclusive scan of eq counts
-  scan[threadIdx.x] = eq;
-  __syncthreads();
-  for (int o = 1; o < SEL_NT; o <<= 1) {
-    int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
-    __syncthreads();
-    scan[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int eq_before = scan[threadIdx.x] - eq;
-  __syncthreads();
+  const int eq_before = sel_block_scan(eq, s_warp);
   // count taken entries in the chunk
   int taken = 0;
   {
@@ -139,15 +164,7 @@ __global__ void __launch_bounds__(SEL_NT) ft_select_kernel(const float* __restri
       else if (key == tau) { if ((uint32_t)e < need_eq) ++taken; ++e; }
     }
   }
-  scan[threadIdx.x] = taken;
-  __syncthreads();
-  for (int o = 1; o < SEL_NT; o <<= 1) {
-    int v = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
-    __syncthreads();
-    scan[threadIdx.x] += v;
-    __syncthreads();
-  }
-  int pos = scan[threadIdx.x] - taken;
+  int pos = sel_block_scan(taken, s_warp);
   int e = eq_before;
   for (int q = q0; q < q1; ++q) {
     const uint32_t key = keys[q <= n / 2 ? q : n - q];

@@ -240,14 +240,26 @@ __global__ void __launch_bounds__(256) gram_dot2_kernel(int k, int m, const floa
 }
 
 // G = sum of partials; with ns = 1 the output is -(G - I)/2 (Newton-Schulz correction factor),
-// formed from the double sum so that the small entries of G - I keep their accuracy.
-__global__ void gram_reduce_kernel(int k, int splits, const double* __restrict__ ws, float* __restrict__ G, int ns) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= k * k) return;
+// formed from the double sum so that the small entries of G - I keep their accuracy.  The order of
+// the additions is fixed for a given split count.  WARP: one warp per entry, lane l summing the
+// partials l, l + 32, ... and a fixed shuffle tree adding the lanes (a thin Gram at n = 4096 has
+// 128 partials per entry); otherwise one thread per entry (few partials, many entries).
+template <bool WARP>
+__global__ void __launch_bounds__(256) gram_reduce_kernel(int k, int splits, const double* __restrict__ ws,
+                                                          float* __restrict__ G, int ns) {
+  const int e = WARP ? blockIdx.x * 8 + (threadIdx.x >> 5) : blockIdx.x * 256 + threadIdx.x;
+  const int lane = WARP ? threadIdx.x & 31 : 0;
+  if (e >= k * k) return;  // WARP: e is uniform across the warp
   double s = 0.0;
-  for (int z = 0; z < splits; ++z) s += ws[(int64_t)z * k * k + e];
-  if (ns) s = -0.5 * (s - ((e / k) == (e % k) ? 1.0 : 0.0));
-  G[e] = (float)s;
+  for (int z = lane; z < splits; z += WARP ? 32 : 1) s += ws[(int64_t)z * k * k + e];
+  if (WARP) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  if (lane == 0) {
+    if (ns) s = -0.5 * (s - ((e / k) == (e % k) ? 1.0 : 0.0));
+    G[e] = (float)s;
+  }
 }
 
 static cudaError_t gram_dot2(int64_t m, int k, const float* X, float* G, cudaStream_t st, int ns = 0) {
@@ -267,7 +279,8 @@ static cudaError_t gram_dot2(int64_t m, int k, const float* X, float* G, cudaStr
   e = cudaGetLastError();
   if (e == cudaSuccess) {
     AMM_TRACE("gram_reduce", st);
-    gram_reduce_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(k, splits, ws, G, ns);
+    if (splits >= 32) gram_reduce_kernel<true><<<(k * k + 7) / 8, 256, 0, st>>>(k, splits, ws, G, ns);
+    else gram_reduce_kernel<false><<<(k * k + 255) / 256, 256, 0, st>>>(k, splits, ws, G, ns);
     e = cudaGetLastError();
   }
   dev_free(ws, st);
