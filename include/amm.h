@@ -137,9 +137,12 @@ amm_status_t amm_opts_init(amm_opts_t* opts);
  *           read once: the handle keeps its own FP32 copy.)
  *   method  AMM_CIRCULANT and AMM_SPARSE_CYCLE need rows == cols (square, Section 2.3), except
  *           AMM_CIRCULANT with opts->block = b > 0, which takes any rows x cols in b x b blocks;
- *           lengths: circulant n (or b) 2^a in [16, 16384] or 3 * 2^a in [48, 6144] (one radix-3
- *           FFT pass); the Fourier sparsifier's inner dimension the same up to 8192; cycle
- *           sparsifier n a multiple of 4 in [16, 8192].
+ *           lengths: circulant n (or b) any integer in [16, 4096], and above that 2^a up to
+ *           16384 or 3 * 2^a up to 6144 (Thm 2.1 holds for every n: 2^a and 3 * 2^a run the fused
+ *           Stockham kernels, every other length chirp-z (Bluestein) transforms with the steps
+ *           between them as separate passes, slower); the Fourier sparsifier's inner dimension
+ *           2^a in [16, 8192] or 3 * 2^a in [48, 6144]; cycle sparsifier n a multiple of 4 in
+ *           [16, 8192].
  *   k       number of kept components (1 <= k <= min(rows, cols) for AMM_SVD; <= b per block
  *           for blocked AMM_CIRCULANT; <= n else).
  *   opts    may be NULL (defaults).

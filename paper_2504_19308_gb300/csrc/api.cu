@@ -134,7 +134,7 @@ extern "C" amm_status_t amm_autotune_export(char* host_buf, int64_t cap, int64_t
 
 extern "C" amm_status_t amm_autotune_import(const char* host_text) {
   if (!host_text) return fail(AMM_ERR_INVALID_ARG, "amm_autotune_import: NULL argument");
-  if (!cd_tune_load(host_text, cd_length_ok))
+  if (!cd_tune_load(host_text, cd_fft_length_ok))
     return fail(AMM_ERR_INVALID_ARG, "amm_autotune_import: malformed table (nothing installed)");
   return AMM_OK;
 }
@@ -153,9 +153,10 @@ extern "C" amm_status_t amm_debug_fail_alloc_after(int32_t n) {
 // ----------------------------------------------------------------------------- handles
 static bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 bool amm::cyc_length_ok(int64_t n) { return n >= 16 && n <= 8192 && n % 4 == 0; }
-bool amm::cd_length_ok(int64_t n) {
+bool amm::cd_fft_length_ok(int64_t n) {
   return (pow2(n) && n >= 16 && n <= 16384) || (n % 3 == 0 && pow2(n / 3) && n >= 48 && n <= 6144);
 }
+bool amm::cd_length_ok(int64_t n) { return cd_fft_length_ok(n) || cd_any_length_ok(n); }
 
 void amm::Handle::release() {
   for (amm_handle* b : blk.sub) {
@@ -218,10 +219,10 @@ cudaError_t amm::cd_spectrum_of(Handle* h, const float2** R, float2** temp, cuda
 amm_status_t amm::decompose_circulant(Handle* h, const amm_opts_t* o) {
   const int n = (int)h->rows;
   if (!cd_length_ok(n))
-    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: n=%d must be 2^a in [16, 16384] or 3 * 2^a in [48, 6144]", n);
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: n=%d must be in [16, 4096], or 2^a up to 16384", n);
   auto& c = h->cd;
   const int J = cd_cols_per_cta(n);
-  c.nparts = n / J;
+  c.nparts = (n + J - 1) / J;
   c.cap = (int)std::min<int64_t>(2 * h->k, n);
   cudaError_t e = twiddles(n, h->stream, &c.tw);
   if (e != cudaSuccess) return cuda_fail(e, "twiddle table");
@@ -360,7 +361,7 @@ static amm_status_t decompose_fourier(Handle* h, const amm_opts_t* o) {
   const bool left = h->role == AMM_LEFT;
   f.n = (int)(left ? h->cols : h->rows);
   f.nvec = (int)(left ? h->rows : h->cols);
-  if (!cd_length_ok(f.n) || f.n > 8192)
+  if (!cd_fft_length_ok(f.n) || f.n > 8192)
     return fail(AMM_ERR_UNSUPPORTED_SIZE, "fourier: inner dimension %d must be 2^a in [16, 8192] or 3 * 2^a in [48, 6144]",
                 f.n);
   if (widen_input(h) != cudaSuccess) return cuda_fail(cudaGetLastError(), "fourier: BF16 input");
@@ -712,7 +713,7 @@ extern "C" amm_status_t amm_choose_k(const void* A, int64_t rows, int64_t cols, 
   if (circ) {
     const float2* tw = nullptr;
     if (e == cudaSuccess) e = twiddles(n, st, &tw);
-    nparts = n / cd_cols_per_cta(n);
+    nparts = (n + cd_cols_per_cta(n) - 1) / cd_cols_per_cta(n);
     float2* R = (float2*)al(sizeof(float2) * (size_t)kh * n);
     float* kpart = (float*)al(sizeof(float) * (size_t)kh * nparts);
     if (e == cudaSuccess) e = cd_spectrum(n, A, lda, dtype == AMM_BF16, tw, R, kpart, st);

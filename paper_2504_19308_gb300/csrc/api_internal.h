@@ -81,7 +81,8 @@ using Handle = ::amm_handle;
 
 amm_status_t fail(amm_status_t s, const char* fmt, ...);
 // circulant transform lengths: 2^a in [16, 16384] or 3 * 2^a in [48, 6144]
-bool cd_length_ok(int64_t n);
+bool cd_length_ok(int64_t n);      // the circulant method: fixed FFT lengths or any n in [16, 4096]
+bool cd_fft_length_ok(int64_t n);  // the fixed lengths 2^a in [16, 16384], 3 * 2^a in [48, 6144]
 // circulant.cu: the spectral-apply autotuner's table as text, and its parser (false: malformed)
 std::string cd_tune_dump();
 bool cd_tune_load(const char* text, bool (*length_ok)(int64_t));

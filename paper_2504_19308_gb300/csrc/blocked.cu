@@ -71,7 +71,7 @@ cudaError_t copy2d(float* dst, int64_t ldd, const float* src, int64_t lds, int64
 amm_status_t decompose_circulant_blocked(Handle* h, const amm_opts_t* o) {
   const int64_t b = o->block;
   if (!cd_length_ok(b))
-    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: block=%lld must be 2^a in [16, 16384] or 3 * 2^a in [48, 6144]",
+    return fail(AMM_ERR_UNSUPPORTED_SIZE, "circulant: block=%lld must be in [16, 4096], or 2^a up to 16384",
                 (long long)b);
   auto& g = h->blk;
   g.b = b;

@@ -38,7 +38,8 @@ cudaError_t bw_spectrum(int n, bool row, const float* X, int64_t ldx, const floa
   AMM_TRACE_W(row ? "bw_row_spectrum" : "bw_col_spectrum", st, 0.0, (double)n * n * 4 + (n / 2 + 1.0) * n * 8,
               nullptr);
   AMM_BW_DISPATCH(n, return BwOps<NN>::spectrum(row, X, ldx, tw, Xh, gate0, gate1, st));
-  return bw_spectrum_r3(n, row, X, ldx, tw, Xh, gate0, gate1, st);
+  if (cd_r3_length(n)) return bw_spectrum_r3(n, row, X, ldx, tw, Xh, gate0, gate1, st);
+  return bw_spectrum_any(n, row, X, ldx, Xh, gate0, gate1, st);
 }
 
 cudaError_t cd_sddmm(int n, const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count, int cap,
@@ -48,14 +49,16 @@ cudaError_t cd_sddmm(int n, const float2* Xh, const float2* Yh, const int32_t* l
   const bool tiled = n >= 2 * SDT_W && (int64_t)cap * 12 >= n;  // the variant BwOps<N>::sddmm launches
   AMM_TRACE_W(tiled ? "cd_sddmm_tiled" : "cd_sddmm", st, 4.0 * n * (double)n, 0.0, count);
   AMM_BW_DISPATCH(n, return BwOps<NN>::sddmm(Xh, Yh, list, count, cap, K, gate0, gate1, st));
-  return cd_sddmm_r3(n, Xh, Yh, list, count, cap, K, gate0, gate1, st);
+  if (cd_r3_length(n)) return cd_sddmm_r3(n, Xh, Yh, list, count, cap, K, gate0, gate1, st);
+  return cd_sddmm_any(n, Xh, Yh, list, count, cap, K, gate0, gate1, st);
 }
 
 cudaError_t cd_rho(int n, const float2* K, const float2* tw, const int32_t* list, const int32_t* count, int cap,
                    float2* RX, const int32_t* gate0, const int32_t* gate1, cudaStream_t st) {
   AMM_TRACE("cd_rho", st);
   AMM_BW_DISPATCH(n, return BwOps<NN>::rho(K, tw, list, count, cap, RX, gate0, gate1, st));
-  return cd_rho_r3(n, K, tw, list, count, cap, RX, gate0, gate1, st);
+  if (cd_r3_length(n)) return cd_rho_r3(n, K, tw, list, count, cap, RX, gate0, gate1, st);
+  return cd_rho_any(n, K, list, count, cap, RX, gate0, gate1, st);
 }
 
 }  // namespace amm

@@ -332,7 +332,7 @@ void tune_cache_load() {
   std::ifstream f(path);
   if (!f) return;
   std::string text((std::istreambuf_iterator<char>(f)), std::istreambuf_iterator<char>());
-  cd_tune_parse(text.c_str(), cd_length_ok);
+  cd_tune_parse(text.c_str(), cd_fft_length_ok);
 }
 }  // namespace
 
@@ -430,7 +430,8 @@ cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const floa
   AMM_TRACE_W("cd_spectrum", st, 0.0,
               (double)n * n * (bf16 ? 2 : 4) + (n / 2 + 1.0) * n * 8 + (double)(n / J) * (n / 2 + 1) * 4, nullptr);
   AMM_DISPATCH_POW2(n, return CdOps<NN>::spectrum(A, lda, bf16, tw, R, kpart, st));
-  return cd_spectrum_r3(n, A, lda, bf16, tw, R, kpart, st);
+  if (cd_r3_length(n)) return cd_spectrum_r3(n, A, lda, bf16, tw, R, kpart, st);
+  return cd_spectrum_any(n, A, lda, bf16, R, kpart, st);
 }
 
 cudaError_t cd_keys(int kh, const float* kpart, int nparts, double* key2, cudaStream_t st) {
@@ -468,7 +469,8 @@ cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* li
   if (!R || !L) return cudaErrorInvalidValue;
   AMM_TRACE("cd_eigen", st);
   AMM_DISPATCH_POW2(n, return CdOps<NN>::eigen(R, tw, list, coef, count, cap, imag_coef, L, st));
-  return cd_eigen_r3(n, R, tw, list, coef, count, cap, imag_coef, L, st);
+  if (cd_r3_length(n)) return cd_eigen_r3(n, R, tw, list, coef, count, cap, imag_coef, L, st);
+  return cd_eigen_any(n, R, list, coef, count, cap, imag_coef, L, st);
 }
 
 cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
@@ -478,7 +480,8 @@ cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g
   AMM_TRACE_W(mode == 0 ? "cd_residual" : (mode == 1 ? "cd_residual_imag" : "cd_project"), st, 0.0,
               (mode & 1) ? 0.0 : (n / 2 + 1.0) * n * 8 + (double)n * n * 4 * (accumulate ? 2 : 1), nullptr);
   AMM_DISPATCH_POW2(n, return CdOps<NN>::residual(R, tw, g, mode, dcount, dcount2, X, ldx, accumulate, st));
-  return cd_residual_r3(n, R, tw, g, mode, dcount, dcount2, X, ldx, accumulate, st);
+  if (cd_r3_length(n)) return cd_residual_r3(n, R, tw, g, mode, dcount, dcount2, X, ldx, accumulate, st);
+  return cd_residual_any(n, R, g, mode, dcount, dcount2, X, ldx, accumulate, st);
 }
 
 cudaError_t cd_apply(int n, bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
@@ -489,7 +492,9 @@ cudaError_t cd_apply(int n, bool row, const void* X, int64_t ldx, bool bf16, int
               (double)n * nvec * (bf16 ? 2 : 4) + (double)n * nvec * 4 * (accumulate ? 2 : 1), count);
   AMM_DISPATCH_POW2(n, return CdOps<NN>::apply(row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out,
                                                ldo, accumulate, rev, st));
-  return cd_apply_r3(n, row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate, rev, st);
+  if (cd_r3_length(n))
+    return cd_apply_r3(n, row, X, ldx, bf16, nvec, tw, list, Lc, count, gate0, gate1, out, ldo, accumulate, rev, st);
+  return cd_apply_any(n, row, X, ldx, bf16, nvec, list, Lc, count, gate0, gate1, out, ldo, accumulate, rev, st);
 }
 
 }  // namespace amm

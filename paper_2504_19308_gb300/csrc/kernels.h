@@ -21,6 +21,28 @@ struct SelectOut {
 };
 
 int cd_cols_per_cta(int n);
+// lengths of the fused kernels: 3 * 2^a in [48, 6144] (circulant_r3.cu; 2^a in circulant.cu)
+inline bool cd_r3_length(int64_t n) {
+  return n % 3 == 0 && n >= 48 && n <= 6144 && ((n / 3) & (n / 3 - 1)) == 0;
+}
+// circulant_any.cu: every other length n in [16, CD_ANY_MAX_N], by chirp-z (Bluestein) DFTs; the
+// same steps, outputs and layouts as the fixed-length wrappers below
+constexpr int CD_ANY_MAX_N = 4096;
+bool cd_any_length_ok(int64_t n);
+cudaError_t cd_spectrum_any(int n, const void* A, int64_t lda, bool bf16, float2* R, float* kpart, cudaStream_t st);
+cudaError_t cd_eigen_any(int n, const float2* R, const int32_t* list, const float* coef, const int32_t* count,
+                         int cap, int imag_coef, float2* L, cudaStream_t st);
+cudaError_t cd_residual_any(int n, const float2* R, const float* g, int mode, const int32_t* dcount,
+                            const int32_t* dcount2, float* X, int64_t ldx, int accumulate, cudaStream_t st);
+cudaError_t cd_apply_any(int n, bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const int32_t* list,
+                         const float2* Lc, const int32_t* count, const int32_t* gate0, const int32_t* gate1,
+                         float* out, int64_t ldo, int accumulate, int rev, cudaStream_t st);
+cudaError_t bw_spectrum_any(int n, bool row, const float* X, int64_t ldx, float2* Xh, const int32_t* gate0,
+                            const int32_t* gate1, cudaStream_t st);
+cudaError_t cd_sddmm_any(int n, const float2* Xh, const float2* Yh, const int32_t* list, const int32_t* count,
+                         int cap, float2* K, const int32_t* gate0, const int32_t* gate1, cudaStream_t st);
+cudaError_t cd_rho_any(int n, const float2* K, const int32_t* list, const int32_t* count, int cap, float2* RX,
+                       const int32_t* gate0, const int32_t* gate1, cudaStream_t st);
 cudaError_t cd_twiddles(float2* tw, int n, cudaStream_t st);
 cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const float2* tw, float2* R, float* kpart,
                         cudaStream_t st);

@@ -64,9 +64,10 @@ def test_argument_errors_without_gpu(lib):
     assert lib.amm_decompose(fake, 64, 64, 32, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
     # circulant needs a square of a supported length
     assert lib.amm_decompose(fake, 64, 32, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
-    # circulant lengths are 2^a or 3 * 2^a: 40 and 80 are not
-    assert lib.amm_decompose(fake, 40, 40, 40, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
-    assert lib.amm_decompose(fake, 80, 80, 80, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
+    # circulant lengths: any n in [16, 4096], above that 2^a or 3 * 2^a only (4100 and 6000 are not)
+    assert lib.amm_decompose(fake, 4100, 4100, 4100, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
+    assert lib.amm_decompose(fake, 6000, 6000, 6000, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
+    assert lib.amm_decompose(fake, 12, 12, 12, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 2
     # k from a tolerance: outputs required, negative tolerance rejected, before any launch
     k_out = ctypes.c_int64(0)
     assert lib.amm_decompose_to_tolerance(fake, 64, 64, 64, 0, 1, 0.1, 0, None, None, None,
@@ -95,9 +96,9 @@ def test_argument_errors_without_gpu(lib):
     fo.forced_selection = ctypes.cast(forced, ctypes.POINTER(ctypes.c_int32))
     assert lib.amm_decompose_best_method(fake, 64, 64, 64, 0, cand, 2, 4, ctypes.byref(fo), None, ctypes.byref(out),
                                          ctypes.byref(chosen)) == 1
-    assert lib.amm_decompose_best_method(fake, 40, 40, 40, 0, cand, 2, 4, None, None, ctypes.byref(out),
+    assert lib.amm_decompose_best_method(fake, 4100, 4100, 4100, 0, cand, 2, 4, None, None, ctypes.byref(out),
                                          ctypes.byref(chosen)) == 2
-    assert b"n=40" in lib.amm_last_error()
+    assert b"n=4100" in lib.amm_last_error()
     assert out.value in (None, 0) and chosen.value == -1
     # refinement: outputs and handles checked on the host
     assert lib.amm_handle_residual(None, fake, 64, None) == 1

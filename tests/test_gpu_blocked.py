@@ -176,8 +176,8 @@ def test_blocked_argument_errors():
     torch, amm = torch_cuda()
     a, b = _pair(64, 128, 64, 66)
     A, B = dev32(torch, a), dev32(torch, b)
-    with pytest.raises(RuntimeError, match="block=40"):
-        amm.decompose(A, "circulant", 3, "left", block=40)
+    with pytest.raises(RuntimeError, match="block=5000"):  # above 4096 and not 2^a
+        amm.decompose(A, "circulant", 3, "left", block=5000)
     with pytest.raises(RuntimeError, match="block"):
         amm.decompose(A, "svd", 3, "left", block=64)
     with pytest.raises(RuntimeError, match="k="):

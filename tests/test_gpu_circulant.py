@@ -157,10 +157,13 @@ def test_circulant_flat_spectrum_ties():
 
 def test_circulant_errors_do_not_launch():
     torch, amm = torch_cuda()
-    A = torch.zeros((40, 40), device="cuda")
+    A = torch.zeros((4100, 4100), device="cuda")  # above 4096 and neither 2^a nor 3 * 2^a
     with pytest.raises(amm.AmmError) as e:
         amm.decompose(A, "circulant", 4)
-    assert e.value.status == 2  # AMM_ERR_UNSUPPORTED_SIZE (neither 2^a nor 3 * 2^a)
+    assert e.value.status == 2  # AMM_ERR_UNSUPPORTED_SIZE
+    with pytest.raises(amm.AmmError) as e:
+        amm.decompose(torch.zeros((12, 12), device="cuda"), "circulant", 4)
+    assert e.value.status == 2
     A = torch.zeros((64, 64), device="cuda")
     with pytest.raises(amm.AmmError):
         amm.decompose(A, "circulant", 0)

@@ -74,7 +74,7 @@ def test_cycle_decomposition_sums_to_A(n):
 
 # --------------------------------------------------------------------------- circulant decomposition
 
-@pytest.mark.parametrize("n", [4, 6, 8, 12, 16])
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8, 9, 12, 15, 16])
 def test_thm21_components_sum_to_A(n):
     """Thm 2.1: A = sum_k R_k D^k, with dense explicitly formed components."""
     a = _rand(n, 1)
@@ -189,7 +189,7 @@ def test_truncation_error_from_keys():
 
 # --------------------------------------------------------------------------- products
 
-@pytest.mark.parametrize("n,k", [(16, 1), (16, 3), (16, 4), (16, 8), (32, 5), (32, 12)])
+@pytest.mark.parametrize("n,k", [(16, 1), (16, 3), (16, 4), (16, 8), (32, 5), (32, 12), (15, 3), (17, 4), (21, 6)])
 def test_alg3_fft_form_equals_explicit(n, k):
     """Alg. 3 (FFT form, shifts and conjugates as printed) equals the explicit dense A~B + dA B~."""
     a, b = _rand(n, 12), S.rng(12, 1).uniform(0, 1, (n, n))
