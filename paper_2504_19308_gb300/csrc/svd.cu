@@ -193,6 +193,129 @@ static cudaError_t sgemm(bool ta, bool tb, int M, int N, int K, float alpha, con
   return e;
 }
 
+// ============================================================================ skinny SIMT GEMMs
+// The shapes a 128-row tensor-core tile (or the 128 x 128 SIMT tile above) mostly wastes:
+//   short contraction: C = alpha A op(B) + beta C with K <= SK_KMAX and a thin output (M or N at
+//     most 64), e.g. Y L^{-T} in CholeskyQR (m x k times k x k) or Q_A (Z_A Q_B) in the product;
+//   tiny output: M, N <= 64 with a long K, e.g. Z_A Q_B (k x k over n).
+// A is M x K row-major; B is N x K (BT) or K x N.  FP32 arithmetic: every output of the short
+// form is one FMA chain over k in order; the tiny form cuts K into TK_C-wide chunks (one CTA
+// each, FMA chain per chunk) whose partials splitk_reduce_kernel sums in FP64 in chunk order.
+// Both are deterministic.
+constexpr int SK_TM = 32, SK_TN = 64, SK_KMAX = 64;
+constexpr int TK_MAX = 64, TK_C = 64;
+
+template <typename TIn>
+__device__ __forceinline__ float ld_elem(const TIn* p) {
+  if constexpr (sizeof(TIn) == 2) return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
+  else return __ldg(reinterpret_cast<const float*>(p));
+}
+
+template <bool BT, typename TIn>
+__global__ void __launch_bounds__(256) gemm_shortk_kernel(int M, int N, int K, float alpha, const TIn* __restrict__ A,
+                                                          int64_t lda, const TIn* __restrict__ B, int64_t ldb,
+                                                          float beta, float* __restrict__ C, int64_t ldc) {
+  __shared__ float As[SK_TM][SK_KMAX + 1];
+  __shared__ float Bs[SK_KMAX][SK_TN + 1];
+  const int m0 = blockIdx.y * SK_TM, n0 = blockIdx.x * SK_TN;
+  for (int e = threadIdx.x; e < SK_TM * K; e += 256) {  // rows of A along k: coalesced
+    const int r = e / K, kk = e % K;
+    As[r][kk] = m0 + r < M ? ld_elem(A + (int64_t)(m0 + r) * lda + kk) : 0.f;
+  }
+  for (int e = threadIdx.x; e < SK_TN * K; e += 256) {
+    if (BT) {
+      const int j = e / K, kk = e % K;
+      Bs[kk][j] = n0 + j < N ? ld_elem(B + (int64_t)(n0 + j) * ldb + kk) : 0.f;
+    } else {
+      const int kk = e / SK_TN, j = e % SK_TN;
+      Bs[kk][j] = n0 + j < N ? ld_elem(B + (int64_t)kk * ldb + n0 + j) : 0.f;
+    }
+  }
+  __syncthreads();
+  // thread: column j, rows rb, rb + 4, ..., rb + 28 (a warp shares its rows: broadcast reads of As)
+  const int j = threadIdx.x & (SK_TN - 1), rb = threadIdx.x / SK_TN;
+  constexpr int RPT = SK_TM / (256 / SK_TN);
+  float acc[RPT];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) acc[i] = 0.f;
+  for (int kk = 0; kk < K; ++kk) {
+    const float b = Bs[kk][j];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) acc[i] = fmaf(As[rb + 4 * i][kk], b, acc[i]);
+  }
+  const int col = n0 + j;
+  if (col >= N) return;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int row = m0 + rb + 4 * i;
+    if (row >= M) break;
+    float* c = C + (int64_t)row * ldc + col;
+    *c = (beta == 0.f) ? alpha * acc[i] : fmaf(alpha, acc[i], beta * *c);
+  }
+}
+
+// ws[chunk][i][j] = sum over the chunk's k of A(i, k) B(j, k), B stored N x K
+template <typename TIn>
+__global__ void __launch_bounds__(256) gemm_tiny_kernel(int M, int N, int K, const TIn* __restrict__ A, int64_t lda,
+                                                        const TIn* __restrict__ B, int64_t ldb, float* __restrict__ ws) {
+  __shared__ float As[TK_MAX][TK_C + 1];
+  __shared__ float Bs[TK_MAX][TK_C + 1];
+  const int k0 = blockIdx.x * TK_C;
+  const int kn = min(TK_C, K - k0);
+  for (int e = threadIdx.x; e < M * TK_C; e += 256) {
+    const int r = e / TK_C, kk = e % TK_C;
+    As[r][kk] = kk < kn ? ld_elem(A + (int64_t)r * lda + k0 + kk) : 0.f;
+  }
+  for (int e = threadIdx.x; e < N * TK_C; e += 256) {
+    const int r = e / TK_C, kk = e % TK_C;
+    Bs[r][kk] = kk < kn ? ld_elem(B + (int64_t)r * ldb + k0 + kk) : 0.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < M * N; e += 256) {
+    const int i = e / N, j = e % N;
+    float acc = 0.f;
+#pragma unroll 8
+    for (int kk = 0; kk < kn; ++kk) acc = fmaf(As[i][kk], Bs[j][kk], acc);
+    ws[(int64_t)blockIdx.x * M * N + e] = acc;
+  }
+}
+
+// splitk_reduce_kernel is defined above; both forms return false when the shape is not theirs
+template <typename TIn>
+static bool skinny_gemm(bool bt, int M, int N, int K, float alpha, const TIn* A, int64_t lda, const TIn* B,
+                        int64_t ldb, float beta, float* C, int64_t ldc, cudaStream_t st, cudaError_t* err) {
+  if (M <= 0 || N <= 0 || K <= 0) return false;
+  if (K <= SK_KMAX && (M <= 64 || N <= 64)) {
+    AMM_TRACE_W("gemm_shortk", st, 2.0 * M * N * (double)K,
+                (double)sizeof(TIn) * ((double)M * K + (double)K * N) + 4.0 * M * N * (beta != 0.f ? 2 : 1), nullptr);
+    const dim3 grid((unsigned)((N + SK_TN - 1) / SK_TN), (unsigned)((M + SK_TM - 1) / SK_TM));
+    if (bt) gemm_shortk_kernel<true, TIn><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else gemm_shortk_kernel<false, TIn><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    *err = cudaGetLastError();
+    return true;
+  }
+  if (bt && M <= TK_MAX && N <= TK_MAX && K > SK_KMAX) {
+    const int chunks = (K + TK_C - 1) / TK_C;
+    float* ws = nullptr;
+    cudaError_t e = dev_alloc((void**)&ws, sizeof(float) * (size_t)chunks * M * N, st);
+    if (e == cudaSuccess) {
+      AMM_TRACE_W("gemm_tiny", st, 2.0 * M * N * (double)K, (double)sizeof(TIn) * ((double)M + N) * K, nullptr);
+      gemm_tiny_kernel<TIn><<<chunks, 256, 0, st>>>(M, N, K, A, lda, B, ldb, ws);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      AMM_TRACE("splitk_reduce", st);
+      splitk_reduce_kernel<<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, st>>>(M, N, chunks, ws, alpha, beta, C,
+                                                                                       ldc);
+      e = cudaGetLastError();
+    }
+    if (ws) dev_free(ws, st);
+    *err = e;
+    return true;
+  }
+  return false;
+}
+
 // ============================================================================ compensated Gram (FP32)
 // G = X^T X for X (m x k, FP32).  Each thread accumulates its dot products with error-free
 // transformations (TwoProduct via fma and TwoSum: Ogita, Rump, Oishi, "Accurate sum and dot
@@ -765,12 +888,14 @@ static cudaError_t orthonormalize(int64_t m, int k, const float* Y, float* Q, cu
     e = gram_dot2(m, k, src, G, st);
     if (e == cudaSuccess) e = chol_inv(k, G, pass == 0 ? shift1 : 1e-7f, W, Li, st);
     if (e == cudaSuccess)
-      e = sgemm<float>(false, true, (int)m, k, k, 1.f, src, k, Li, k, 0.f, dsts[pass], k, st);  // src Linv^T
+      if (!skinny_gemm<float>(true, (int)m, k, k, 1.f, src, k, Li, k, 0.f, dsts[pass], k, st, &e))
+        e = sgemm<float>(false, true, (int)m, k, k, 1.f, src, k, Li, k, 0.f, dsts[pass], k, st);  // src Linv^T
     src = dsts[pass];
   }
   if (e == cudaSuccess) e = gram_dot2(m, k, Q2, G, st, 1);  // G <- -(Q2^T Q2 - I) / 2
   if (e == cudaSuccess) e = cudaMemcpyAsync(Q, Q2, sizeof(float) * (size_t)m * k, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = sgemm<float>(false, false, (int)m, k, k, 1.f, Q2, k, G, k, 1.f, Q, k, st);
+  if (e == cudaSuccess && !skinny_gemm<float>(false, (int)m, k, k, 1.f, Q2, k, G, k, 1.f, Q, k, st, &e))
+    e = sgemm<float>(false, false, (int)m, k, k, 1.f, Q2, k, G, k, 1.f, Q, k, st);
   for (float* p : {G, W, Li, Q1, Q2}) dev_free(p, st);
   return e;
 }
@@ -878,6 +1003,8 @@ static int pad8(int k) { return (k + 7) / 8 * 8; }
 template <typename E>
 static cudaError_t gemm_tn(int M, int N, int K, float alpha, const E* A, int64_t lda, const E* B, int64_t ldb,
                            float beta, float* C, int64_t ldc, int* err, cudaStream_t st) {
+  cudaError_t se = cudaSuccess;
+  if (skinny_gemm<E>(true, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, &se)) return se;
   const bool aligned = ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && (lda * sizeof(E)) % 16 == 0 &&
                        (ldb * sizeof(E)) % 16 == 0;
   if (aligned && K > 0)

@@ -163,9 +163,15 @@ def test_best_method_matches_oracle_choice():
 def test_best_method_skips_candidates_that_do_not_take_the_shape():
     torch, amm = torch_cuda()
     g = S.rng(43, 0)
-    A = dev32(torch, g.uniform(0.0, 1.0, (100, 100)))   # 100: neither 2^a nor 3 * 2^a
+    # not square (no circulant without blocks) and an inner dimension of 100 (neither 2^a nor
+    # 3 * 2^a: no Fourier sparsifier)
+    A = dev32(torch, g.uniform(0.0, 1.0, (96, 100)))
     h, got = amm.decompose_best_method(A, ["circulant", "fourier", "svd"], 4)
     assert got == "svd"
+    # a square 100 x 100 takes the circulant method (any n up to 4096), still not the sparsifier
+    A2 = dev32(torch, g.uniform(0.0, 1.0, (100, 100)))
+    h, got = amm.decompose_best_method(A2, ["fourier", "circulant"], 4)
+    assert got == "circulant"
     R = dev32(torch, g.uniform(0.0, 1.0, (96, 200)))    # the cycle sparsifier needs a square
     h, got = amm.decompose_best_method(R, ["cycle", "svd"], 4)
     assert got == "svd"
