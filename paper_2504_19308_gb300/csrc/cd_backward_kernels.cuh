@@ -104,16 +104,31 @@ __global__ void __launch_bounds__(256) cd_sddmm_kernel(const float2* __restrict_
   float2 acc[SD_UB];
 #pragma unroll
   for (int j = 0; j < SD_UB; ++j) acc[j] = make_float2(0.f, 0.f);
-#pragma unroll 2
-  for (int m = lane; m < N; m += 32) {
-    float2 x = __ldg(xr + m);
-    x.y *= xs;
+  // SD_MU consecutive m of the lane's sequence m = lane, lane + 32, ... per step: their Xh loads,
+  // then per component their Yh loads, are issued together (few listed components leave a warp
+  // with little else to overlap); every accumulator still adds its products in increasing m
+  constexpr int SD_MU = 4;
+  for (int m0 = lane; m0 < N; m0 += 32 * SD_MU) {
+    float2 x[SD_MU];
+#pragma unroll
+    for (int q = 0; q < SD_MU; ++q) {
+      const int m = m0 + 32 * q;
+      x[q] = m < N ? __ldg(xr + m) : make_float2(0.f, 0.f);
+      x[q].y *= xs;
+    }
 #pragma unroll
     for (int j = 0; j < SD_UB; ++j) {
       if (!act[j]) continue;  // warp-uniform
-      float2 y = __ldg(yr[j] + m);
-      y.y *= ys[j];
-      cmac(acc[j], x, y);
+      float2 y[SD_MU];
+#pragma unroll
+      for (int q = 0; q < SD_MU; ++q) {
+        const int m = m0 + 32 * q;
+        y[q] = m < N ? __ldg(yr[j] + m) : make_float2(0.f, 0.f);
+        y[q].y *= ys[j];
+      }
+#pragma unroll
+      for (int q = 0; q < SD_MU; ++q)
+        if (m0 + 32 * q < N) cmac(acc[j], x[q], y[q]);
     }
   }
 #pragma unroll
