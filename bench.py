@@ -519,15 +519,25 @@ def batch256_form(args, dev, dist, count=256):
             hA.close()
             hB.close()
 
-    batch = amm.Batch()
-    for A, B, C, method, k, sa, sb in items:
-        batch.add(A, B, C, method, k, sketch_a=sa, sketch_b=sb)
-    batch.run(use_graph=True)  # eager pass + capture
-    torch.cuda.synchronize()
+    def make_batch(persistent):
+        b = amm.Batch()
+        b.set_persistent(persistent)
+        for A, B, C, method, k, sa, sb in items:
+            b.add(A, B, C, method, k, sketch_a=sa, sketch_b=sb)
+        b.run(use_graph=True)  # eager pass + capture
+        torch.cuda.synchronize()
+        return b
+
+    batch, pool = make_batch(True), make_batch(False)
     reps = max(3, args.steps // 5)
     eager_ms = _device_ms(eager, reps, 1, dist)
     graph_ms = _device_ms(lambda: batch.run(use_graph=True), reps, 1, dist)
+    pool_ms = _device_ms(lambda: pool.run(use_graph=True), reps, 1, dist)
+    status, _, _, n_persistent = batch.status()
+    if status != 0:
+        raise RuntimeError("batch: the persistent executor reported status %d" % status)
     batch.close()
+    pool.close()
     fl = sum(2.0 * n ** 3 for n in sizes)
     # plus one n = 16384 product (circulant, k = n/32 = 512), timed on its own: inside the batch
     # it would hide the launch overheads the graph removes
@@ -552,6 +562,7 @@ def batch256_form(args, dev, dist, count=256):
             "n = 16384 product (circulant, k = 512) timed alone"
             % (min(sizes), max(sizes), sum(1 for v in sizes if v & (v - 1))),
             "eager_ms": eager_ms, "graph_ms": graph_ms, "speedup": eager_ms / graph_ms,
+            "graph_ms_stream_pool_only": pool_ms, "persistent_products": n_persistent,
             "value": fl / (graph_ms * 1e-3) / 1e12, "unit": UNIT}
 
 

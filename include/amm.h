@@ -402,10 +402,17 @@ amm_status_t amm_circulant_spectrum_noalloc(const float* A, int64_t n, int64_t l
  * NULL, their role is set by the batch).  amm_batch_run executes every item -- decompose both
  * operands, product, release -- on a pool of 16 streams forked from `stream` and joined back into
  * it, the items in descending order of m n p, each on the stream with the least work so far (the
- * results do not depend on the order).  With use_graph != 0 the first run executes the items once eagerly and then records the
- * same work into one CUDA graph; that run and every later run launch the graph.  Pointers and
- * sizes are baked into the graph: rerun with the same buffers (their contents may change).
- * After the first graph run no item can be added.
+ * results do not depend on the order).  Forward products of the cycle sparsifier (AMM_SPARSE_CYCLE,
+ * FP32, square n x n with n <= 4096) run instead in one persistent launch: its CTAs take
+ * (product, stage, tile) tasks -- cycle keys, key reduction, selection, gather of the kept
+ * cycles, the column panels of A_s B, the row panels of dA B_s -- from a device queue written stage
+ * by stage (largest product first), each task waiting (bounded) for the product's previous stage;
+ * that launch takes its place in the order above with the summed work of its products, and its
+ * results are bit-identical to amm_decompose + amm_approx_matmul.  With use_graph != 0 the first
+ * run executes the items once eagerly and then records the same work into one CUDA graph; that
+ * run and every later run launch the graph.  Pointers and sizes are baked into the graph: rerun
+ * with the same buffers (their contents may change).  After the first graph run no item can be
+ * added.
  */
 typedef struct amm_batch* amm_batch_t;
 amm_status_t amm_batch_create(amm_batch_t* out);
@@ -427,6 +434,23 @@ amm_status_t amm_batch_add_grad(amm_batch_t batch, const void* A, const void* B,
                                 int64_t lddc, float* dA, int64_t ldda, float* dB, int64_t lddb);
 amm_status_t amm_batch_run(amm_batch_t batch, void* stream, int32_t use_graph);
 amm_status_t amm_batch_destroy(amm_batch_t batch);
+/*
+ * The persistent executor of the cycle-sparsifier items: on != 0 (the default) runs them in the
+ * persistent launch, 0 on the stream pool like every other item.  wait_limit_ns (> 0; default 2e9)
+ * bounds each wait of a task for its product's previous stage: a wait that runs out stops the
+ * launch and is reported by amm_batch_status.  Before the first graph run only
+ * (AMM_ERR_STATE after).  Host only.
+ */
+amm_status_t amm_batch_set_persistent(amm_batch_t batch, int32_t on, int64_t wait_limit_ns);
+/*
+ * Waits for the last amm_batch_run's stream, then reports the persistent launch's control block:
+ * *status = AMM_OK, or AMM_ERR_TIMEOUT when a task's wait ran out (the products' results are
+ * then incomplete), with *item the batch index of the product and *stage the stage (0 keys,
+ * 1 key reduction, 2 selection, 3 gather, 4 column panels, 5 row panels) whose completion it
+ * waited for (-1 when none); *persistent_products = how many items the persistent launch runs.
+ */
+amm_status_t amm_batch_status(amm_batch_t batch, int32_t* status, int64_t* item, int32_t* stage,
+                              int32_t* persistent_products);
 
 /*
  * Launch tracing for measurement.  While enabled, every kernel launch the library makes is
@@ -487,6 +511,16 @@ amm_status_t amm_autotune_export(char* host_buf, int64_t cap, int64_t* len);
  * AMM_ERR_INVALID_ARG with nothing installed.  Host only.
  */
 amm_status_t amm_autotune_import(const char* host_text);
+
+/*
+ * Test hook for the bounded waits of the batch's persistent executor: runs it (one CTA) on a queue
+ * whose only task waits for a stage that no task completes, on `stream`, and synchronises.  The
+ * wait gives up after limit_ns (in (0, 5e9]) and the launch returns; *status_out receives the
+ * control block's status (AMM_ERR_TIMEOUT) and *stage_out the stage waited for (4).  No GPU
+ * fault: the kernel returns normally.
+ */
+amm_status_t amm_debug_persistent_wait_timeout(int64_t limit_ns, void* stream, int32_t* status_out,
+                                               int32_t* stage_out);
 
 /*
  * Fault injection for tests: the n-th device allocation from now on (1-based) fails with

@@ -110,6 +110,13 @@ SIGNATURES = {
                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_int64]),
     "amm_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "amm_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    "amm_batch_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "amm_debug_persistent_wait_timeout": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p,
+                                                         ctypes.POINTER(ctypes.c_int32),
+                                                         ctypes.POINTER(ctypes.c_int32)]),
     "amm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "amm_trace_enable": (ctypes.c_int, [ctypes.c_int32]),
     "amm_trace_collect": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
@@ -513,6 +520,18 @@ class Batch:
     def run(self, use_graph: bool = True):
         dev = self.keep[0].device
         _check(load_library().amm_batch_run(self.ptr, _stream_ptr(dev), 1 if use_graph else 0), "amm_batch_run")
+
+    def set_persistent(self, on: bool = True, wait_limit_ns: int = 2_000_000_000):
+        """Cycle-sparsifier items in the persistent work-queue launch (default) or on the stream pool."""
+        _check(load_library().amm_batch_set_persistent(self.ptr, 1 if on else 0, int(wait_limit_ns)),
+               "amm_batch_set_persistent")
+
+    def status(self):
+        """(status, item, stage, persistent_products) of the last run's persistent launch (waits for it)."""
+        st, it, sg, npq = ctypes.c_int32(0), ctypes.c_int64(-1), ctypes.c_int32(-1), ctypes.c_int32(0)
+        _check(load_library().amm_batch_status(self.ptr, ctypes.byref(st), ctypes.byref(it), ctypes.byref(sg),
+                                               ctypes.byref(npq)), "amm_batch_status")
+        return st.value, it.value, sg.value, npq.value
 
     def close(self):
         if self.ptr is not None and self.ptr.value:

@@ -1,7 +1,10 @@
 // Batches of independent first-order products of uneven sizes (for example the layers of an
 // LLM-shaped stack).  amm_batch_run executes every item (decompose A, decompose B, product, the
 // backward for items added with amm_batch_add_grad, release) on a pool of 16 streams forked from
-// the caller's stream, the largest items first, each on the least loaded stream.  With use_graph the first
+// the caller's stream, the largest items first, each on the least loaded stream.  The forward
+// cycle-sparsifier products (FP32, square, n <= 4096) run instead in one persistent launch that
+// takes (product, stage, tile) tasks from a device queue (batch_persistent.cu); that launch is
+// placed on the pool like one item whose work is theirs.  With use_graph the first
 // run executes eagerly once (building twiddle tables and setting kernel attributes, which must
 // not happen inside a capture), then captures the same work into one CUDA graph; every later
 // run is a single graph launch.  Device memory of the handles is stream-ordered, so inside the
@@ -15,6 +18,7 @@
 
 #include "../../include/amm.h"
 #include "api_internal.h"
+#include "persistent.h"
 
 struct amm_batch {
   struct Item {
@@ -37,6 +41,13 @@ struct amm_batch {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   bool captured = false;
+  // persistent executor of the cycle-sparsifier items
+  bool persistent = true;
+  uint64_t wait_limit_ns = 2000000000ull;
+  amm::PqPlan* pq = nullptr;
+  size_t pq_built_for = 0;         // item count the plan was built for
+  std::vector<size_t> pq_items;    // batch indices of the plan's products
+  cudaStream_t last_parent = nullptr;
 };
 
 using namespace amm;
@@ -110,6 +121,29 @@ extern "C" amm_status_t amm_batch_add_grad(amm_batch_t b, const void* A, const v
   return AMM_OK;
 }
 
+// (Re)build the persistent plan for the batch's eligible items when the item list changed.  Not
+// called inside a capture (the first graph run executes eagerly first).
+static amm_status_t plan_persistent(amm_batch* b) {
+  if (!b->persistent || b->pq_built_for == b->items.size()) return AMM_OK;
+  amm::pq_destroy(b->pq);  // cudaFree waits for earlier runs
+  b->pq = nullptr;
+  b->pq_items.clear();
+  std::vector<amm::PqDesc> descs;
+  for (size_t i = 0; i < b->items.size(); ++i) {
+    const auto& it = b->items[i];
+    if (!amm::pq_eligible(it.method, it.dtype, it.m, it.n, it.p, it.dC != nullptr) || it.k > it.n) continue;
+    descs.push_back(amm::PqDesc{(const float*)it.A, (const float*)it.B, it.C, it.lda, it.ldb, it.ldc, it.n, it.k});
+    b->pq_items.push_back(i);
+  }
+  cudaError_t e = amm::pq_build(descs, &b->pq);
+  if (e != cudaSuccess) {
+    b->pq_items.clear();
+    return cuda_fail(e, "batch: persistent executor set-up");
+  }
+  b->pq_built_for = b->items.size();
+  return AMM_OK;
+}
+
 static amm_status_t run_items(amm_batch* b, cudaStream_t parent) {
   cudaError_t e;
   if (b->streams.empty()) {
@@ -139,14 +173,32 @@ static amm_status_t run_items(amm_batch* b, cudaStream_t parent) {
     const auto& it = b->items[i];
     return (double)it.m * (double)it.n * (double)it.p * (it.dC ? 3.0 : 1.0);
   };
-  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return work(x) > work(y); });
+  std::vector<double> wk(b->items.size());
+  for (size_t i = 0; i < b->items.size(); ++i) wk[i] = work(i);
+  amm_status_t st = plan_persistent(b);
+  if (st != AMM_OK) return st;
+  // the persistent launch stands in the order for its products: their summed work, once
+  std::vector<char> in_pq(b->items.size(), 0);
+  double pq_w = 0.0;
+  for (size_t i : b->pq_items) {
+    in_pq[i] = 1;
+    pq_w += wk[i];
+  }
+  const size_t PQ = (size_t)-1;
+  order.erase(std::remove_if(order.begin(), order.end(), [&](size_t i) { return in_pq[i] != 0; }), order.end());
+  if (b->pq) order.push_back(PQ);
+  auto wof = [&](size_t i) { return i == PQ ? pq_w : wk[i]; };
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return wof(x) > wof(y); });
   std::vector<double> load(b->streams.size(), 0.0);
-  amm_status_t st = AMM_OK;
   for (size_t oi = 0; oi < order.size() && st == AMM_OK; ++oi) {
-    auto& it = b->items[order[oi]];
     const size_t si = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
-    load[si] += work(order[oi]);
+    load[si] += wof(order[oi]);
     cudaStream_t s = b->streams[si];
+    if (order[oi] == PQ) {
+      if ((e = amm::pq_launch(b->pq, s, b->wait_limit_ns)) != cudaSuccess) st = cuda_fail(e, "batch: persistent launch");
+      continue;
+    }
+    auto& it = b->items[order[oi]];
     amm_handle_t ha = nullptr, hb = nullptr;
     st = amm_decompose(it.A, it.m, it.n, it.lda, (amm_dtype_t)it.dtype, (amm_method_t)it.method, it.k, &it.oa, s, &ha);
     if (st == AMM_OK)
@@ -165,9 +217,38 @@ static amm_status_t run_items(amm_batch* b, cudaStream_t parent) {
   return st;
 }
 
+extern "C" amm_status_t amm_batch_set_persistent(amm_batch_t b, int32_t on, int64_t wait_limit_ns) {
+  if (!b) return fail(AMM_ERR_INVALID_ARG, "amm_batch_set_persistent: NULL batch");
+  if (b->captured) return fail(AMM_ERR_STATE, "amm_batch_set_persistent: batch already captured into a graph");
+  if (wait_limit_ns <= 0) return fail(AMM_ERR_INVALID_ARG, "amm_batch_set_persistent: wait_limit_ns must be > 0");
+  if ((on != 0) != b->persistent) {
+    amm::pq_destroy(b->pq);
+    b->pq = nullptr;
+    b->pq_items.clear();
+    b->pq_built_for = 0;
+  }
+  b->persistent = on != 0;
+  b->wait_limit_ns = (uint64_t)wait_limit_ns;
+  return AMM_OK;
+}
+
+extern "C" amm_status_t amm_batch_status(amm_batch_t b, int32_t* status, int64_t* item, int32_t* stage,
+                                         int32_t* persistent_products) {
+  if (!b || !status || !item || !stage || !persistent_products)
+    return fail(AMM_ERR_INVALID_ARG, "amm_batch_status: NULL argument");
+  *persistent_products = (int32_t)b->pq_items.size();
+  cudaError_t e = b->last_parent ? cudaStreamSynchronize(b->last_parent) : cudaSuccess;
+  int32_t it = -1;
+  if (e == cudaSuccess) e = amm::pq_status(b->pq, status, &it, stage);
+  if (e != cudaSuccess) return cuda_fail(e, "amm_batch_status");
+  *item = (it >= 0 && (size_t)it < b->pq_items.size()) ? (int64_t)b->pq_items[(size_t)it] : -1;
+  return AMM_OK;
+}
+
 extern "C" amm_status_t amm_batch_run(amm_batch_t b, void* stream, int32_t use_graph) {
   if (!b) return fail(AMM_ERR_INVALID_ARG, "amm_batch_run: NULL batch");
   cudaStream_t parent = (cudaStream_t)stream;
+  b->last_parent = parent;
   if (!use_graph) return run_items(b, parent);
   cudaError_t e;
   if (!b->captured) {
@@ -204,6 +285,7 @@ extern "C" amm_status_t amm_batch_destroy(amm_batch_t b) {
   if (!b) return fail(AMM_ERR_INVALID_ARG, "amm_batch_destroy: NULL batch");
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  amm::pq_destroy(b->pq);
   for (auto s : b->streams) cudaStreamDestroy(s);
   for (auto ev : b->events) cudaEventDestroy(ev);
   delete b;

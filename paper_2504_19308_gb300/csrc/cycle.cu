@@ -12,103 +12,33 @@
 
 #include "api_internal.h"
 #include "common.cuh"
+#include "cycle_kernels.cuh"
 #include "kernels.h"
 #include "trace.h"
 
 namespace amm {
 
-// part[rb][j] = sum over rows r of block rb of A(r, (r - j) mod n)^2 (thread per cycle j:
-// a warp reads 32 consecutive columns of one row).
 __global__ void __launch_bounds__(256) cyc_keys_kernel(const float* __restrict__ A, int64_t lda, int n, int rows_per,
                                                        float* __restrict__ part) {
-  const int j = blockIdx.x * 256 + threadIdx.x;
-  if (j >= n) return;
-  const int r0 = blockIdx.y * rows_per;
-  float s = 0.f;
-  for (int r = r0; r < min(n, r0 + rows_per); ++r) {
-    const float v = __ldg(A + (int64_t)r * lda + cwrap<false>(r - j, n));
-    s = fmaf(v, v, s);
-  }
-  part[(int64_t)blockIdx.y * n + j] = s;
+  cyc_keys_tile(A, lda, n, rows_per, part, blockIdx.x, blockIdx.y);
 }
 
-// cyc[u][l] = A((l + t_u) mod n, l) for the k selected cycles; insel[t] = 1 for selected t.
 __global__ void cyc_gather_kernel(const float* __restrict__ A, int64_t lda, int n, int k,
                                   const int32_t* __restrict__ sel, float* __restrict__ cyc,
                                   unsigned char* __restrict__ insel) {
-  const int u = blockIdx.y;
-  const int t = sel[u];
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x)
-    cyc[(int64_t)u * n + l] = __ldg(A + (int64_t)cwrap<false>(l + t, n) * lda + l);
-  if (blockIdx.x == 0 && threadIdx.x == 0) insel[t] = 1;
+  cyc_gather_tile<false>(A, lda, n, sel, cyc, insel, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x,
+                  gridDim.x * blockDim.x, blockIdx.x == 0);
 }
 
-constexpr int CYC_CW = 4;    // columns per CTA (A_s B)
-constexpr int CYC_RW = 4;    // rows per CTA (dA B_s)
-constexpr int CYC_NT = 256;
-constexpr int CYC_RG = 8;    // rows (or columns) per thread per pass of the component loop
-
-// out(:, c0..c0+3) = sum_u cyc[u][r - t_u] B(r - t_u, c)
 template <bool P2>
 __global__ void __launch_bounds__(CYC_NT) cyc_apply_col_kernel(const float* __restrict__ B, int64_t ldb, int n,
                                                                const int32_t* __restrict__ sel, int k,
                                                                const float* __restrict__ cyc, float* __restrict__ out,
                                                                int64_t ldo, int ncols) {
   extern __shared__ float4 bp[];  // n x 4 columns, then the k selected cycle indices
-  int* s_sel = reinterpret_cast<int*>(bp + n);
-  const int c0 = blockIdx.x * CYC_CW;
-  for (int r = threadIdx.x; r < n; r += CYC_NT) {
-    const float* src = B + (int64_t)r * ldb + c0;
-    float4 v;
-    v.x = c0 + 0 < ncols ? __ldg(src + 0) : 0.f;
-    v.y = c0 + 1 < ncols ? __ldg(src + 1) : 0.f;
-    v.z = c0 + 2 < ncols ? __ldg(src + 2) : 0.f;
-    v.w = c0 + 3 < ncols ? __ldg(src + 3) : 0.f;
-    bp[r] = v;
-  }
-  for (int u = threadIdx.x; u < k; u += CYC_NT) s_sel[u] = __ldg(sel + u);
-  __syncthreads();
-  // CYC_RG rows per thread at a time, components in the outer loop: CYC_RG independent gathers
-  // of cyc in flight per component
-  for (int r0 = threadIdx.x; r0 < n; r0 += CYC_NT * CYC_RG) {
-    float4 acc[CYC_RG];
-#pragma unroll
-    for (int i = 0; i < CYC_RG; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    // unrolled over components: the gathers of several components are issued before the FMAs
-    // that wait on them (the loads are L2 hits whose latency, not bandwidth, set the time)
-#pragma unroll 2
-    for (int u = 0; u < k; ++u) {
-      const int t = s_sel[u];
-      const float* crow = cyc + (int64_t)u * n;
-#pragma unroll
-      for (int i = 0; i < CYC_RG; ++i) {
-        const int r = r0 + i * CYC_NT;
-        if (r < n) {
-          const int l = cwrap<P2>(r - t, n);
-          const float a = __ldg(crow + l);
-          const float4 b = bp[l];
-          acc[i].x = fmaf(a, b.x, acc[i].x);
-          acc[i].y = fmaf(a, b.y, acc[i].y);
-          acc[i].z = fmaf(a, b.z, acc[i].z);
-          acc[i].w = fmaf(a, b.w, acc[i].w);
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < CYC_RG; ++i) {
-      const int r = r0 + i * CYC_NT;
-      if (r >= n) continue;
-      float* o = out + (int64_t)r * ldo + c0;
-      if (c0 + 0 < ncols) o[0] = acc[i].x;
-      if (c0 + 1 < ncols) o[1] = acc[i].y;
-      if (c0 + 2 < ncols) o[2] = acc[i].z;
-      if (c0 + 3 < ncols) o[3] = acc[i].w;
-    }
-  }
+  cyc_apply_col_tile<P2, false>(B, ldb, n, sel, k, cyc, out, ldo, ncols, blockIdx.x, bp);
 }
 
-// out(r0..r0+3, :) += sum_u dA(r, c + s_u) cycB[u][c]; dA = A with the kept cycles of A masked
-// (inselA), or A itself when inselA is NULL
 template <bool P2>
 __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __restrict__ A, int64_t lda, int n,
                                                                const unsigned char* __restrict__ inselA,
@@ -116,27 +46,7 @@ __global__ void __launch_bounds__(CYC_NT) cyc_apply_row_kernel(const float* __re
                                                                const float* __restrict__ cycB, float* __restrict__ out,
                                                                int64_t ldo, int nrows) {
   extern __shared__ float ar[];  // CYC_RW x n, masked dA
-  const int r0 = blockIdx.x * CYC_RW;
-  for (int e = threadIdx.x; e < CYC_RW * n; e += CYC_NT) {
-    const int rr = e / n, q = e % n, r = r0 + rr;
-    float v = 0.f;
-    if (r < nrows && (inselA == nullptr || !inselA[cwrap<P2>(r - q, n)])) v = __ldg(A + (int64_t)r * lda + q);
-    ar[e] = v;
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < n; c += CYC_NT) {
-    float acc[CYC_RW] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-    for (int u = 0; u < kb; ++u) {
-      const int q = cwrap<P2>(c + __ldg(selB + u), n);
-      const float b = __ldg(cycB + (int64_t)u * n + c);
-#pragma unroll
-      for (int rr = 0; rr < CYC_RW; ++rr) acc[rr] = fmaf(ar[rr * n + q], b, acc[rr]);
-    }
-#pragma unroll
-    for (int rr = 0; rr < CYC_RW; ++rr)
-      if (r0 + rr < nrows) out[(int64_t)(r0 + rr) * ldo + c] += acc[rr];
-  }
+  cyc_apply_row_tile<P2, false>(A, lda, n, inselA, selB, kb, cycB, out, ldo, nrows, blockIdx.x, ar);
 }
 
 // ============================================================================ backward (selections frozen)

@@ -234,6 +234,17 @@ def test_batch_host_logic(lib):
     assert add(fake, fake, fake, 64, 64, 64, 64, 64, 64, 0, 1, 4, None, ctypes.byref(fo)) == 1
     assert add(fake, fake, fake, 64, 64, 64, 64, 64, 64, 0, 1, 4, None, None) == 0
     assert add(fake, fake, fake, 96, 96, 96, 96, 96, 96, 1, 0, 8, None, None) == 0
+    # the persistent executor's switch and wait limit: checked on the host, no device work
+    assert lib.amm_batch_set_persistent(None, 1, 10**9) == 1
+    assert lib.amm_batch_set_persistent(batch, 1, 0) == 1
+    assert lib.amm_batch_set_persistent(batch, 0, 10**9) == 0
+    assert lib.amm_batch_set_persistent(batch, 1, 5 * 10**8) == 0
+    st, it, sg, npq = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    assert lib.amm_batch_status(batch, None, ctypes.byref(it), ctypes.byref(sg), ctypes.byref(npq)) == 1
+    assert lib.amm_batch_status(batch, ctypes.byref(st), ctypes.byref(it), ctypes.byref(sg), ctypes.byref(npq)) == 0
+    assert (st.value, it.value, sg.value, npq.value) == (0, -1, -1, 0)   # never ran
+    assert lib.amm_debug_persistent_wait_timeout(0, None, ctypes.byref(st), ctypes.byref(sg)) == 1
+    assert lib.amm_debug_persistent_wait_timeout(10**6, None, None, ctypes.byref(sg)) == 1
     assert lib.amm_batch_destroy(batch) == 0
     assert lib.amm_batch_destroy(None) == 1
 

@@ -163,3 +163,75 @@ def test_batch_backward_items_match_single_calls_and_oracle():
         for it, (C1, dA1, dB1) in zip(items, refs):
             assert torch.equal(it[2], C1) and torch.equal(it[8], dA1) and torch.equal(it[9], dB1), (it[3], use_graph)
     batch.close()
+
+
+def test_batch_persistent_cycle_items_bit_identical_and_oracle():
+    """The cycle-sparsifier items of a batch run in the persistent work-queue launch: lengths 2^a and
+    others divisible by 4 (the paper's n = 700 among them), k from 1 to n, beside items of the other
+    methods.  Their products equal the stream-pool run and single calls bit for bit, eager and as a
+    replayed graph, and match the FP64 oracle; the launch reports no timeout."""
+    torch, amm = torch_cuda()
+    spec = [(16, 1, "cycle"), (700, 22, "cycle"), (4096, 128, "cycle"), (100, 100, "cycle"), (1020, 33, "cycle"),
+            (256, 8, "circulant"), (64, 64, "cycle"), (512, 16, "svd"), (2048, 7, "cycle"), (1536, 48, "cycle")]
+    items = []
+    for i, (n, k, method) in enumerate(spec):
+        a, b = S.exp32_pair(n, seed=300 + i) if n <= 1536 else S.general_times_toeplitz(n, seed=300 + i)
+        A, B = dev32(torch, a), dev32(torch, b)
+        sa = dev32(torch, S.sketch(n, k, 300 + i, 0)) if method == "svd" else None
+        sb = dev32(torch, S.sketch(n, k, 300 + i, 1)) if method == "svd" else None
+        items.append([A, B, torch.full((n, n), float("nan"), device="cuda"), method, k, sa, sb])
+    singles = []
+    for A, B, C, method, k, sa, sb in items:
+        hA = amm.decompose(A, method, k, "left", sketch=sa)
+        hB = amm.decompose(B, method, k, "right", sketch=sb)
+        singles.append(amm.approx_matmul(hA, hB).clone())
+    pool = amm.Batch()
+    pool.set_persistent(False)
+    pers = amm.Batch()
+    pool_c = []
+    for A, B, C, method, k, sa, sb in items:
+        Cp = torch.full_like(C, float("nan"))
+        pool_c.append(Cp)
+        pool.add(A, B, Cp, method, k, sketch_a=sa, sketch_b=sb)
+        pers.add(A, B, C, method, k, sketch_a=sa, sketch_b=sb)
+    pool.run(use_graph=False)
+    for use_graph in (False, True, True):
+        for it in items:
+            it[2].fill_(float("nan"))
+        pers.run(use_graph=use_graph)
+        status, item, stage, npq = pers.status()
+        assert (status, item, stage) == (0, -1, -1)
+        assert npq == sum(1 for s in spec if s[2] == "cycle")
+        torch.cuda.synchronize()
+        for (A, B, C, method, k, *_), Cp, ref in zip(items, pool_c, singles):
+            assert torch.equal(C, ref), (A.shape[0], method, k, use_graph)
+            assert torch.equal(Cp, ref), (A.shape[0], method, k)
+    assert pool.status()[3] == 0
+    for (A, B, C, method, k, sa, sb), (n, *_) in zip(items, spec):
+        if method == "cycle" and n <= 1536:
+            ref = _oracle_item(amm, A, B, method, k, sa, sb, "f32")
+            assert rel(C.double().cpu().numpy(), ref) <= TOL, (n, k)
+    pool.close()
+    pers.close()
+
+
+def test_batch_persistent_wait_runs_out_and_reports_timeout():
+    """A task whose dependency never completes: the executor's bounded wait gives up after the
+    limit, the launch returns with AMM_ERR_TIMEOUT and the stage it waited for (4, the column
+    panels), and the device keeps working (a product afterwards is exact)."""
+    import ctypes
+    import time
+    torch, amm = torch_cuda()
+    lib = amm.load_library()
+    st, stage = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    t0 = time.perf_counter()
+    assert lib.amm_debug_persistent_wait_timeout(20_000_000, torch.cuda.current_stream().cuda_stream,
+                                                 ctypes.byref(st), ctypes.byref(stage)) == 0
+    waited = time.perf_counter() - t0
+    assert st.value == 5 and stage.value == 4
+    assert 0.015 <= waited < 5.0
+    n = 64
+    a, b = S.exp32_pair(n, seed=9)
+    A, B = dev32(torch, a), dev32(torch, b)
+    C = amm.approx_matmul(amm.decompose(A, "cycle", n, "left"), amm.decompose(B, "cycle", n, "right"))
+    assert rel(C.double().cpu().numpy(), as64(A) @ as64(B)) <= TOL
