@@ -100,8 +100,11 @@ __device__ double block_sum(double v, double* red) {
 // Cycle keys (mirror = 0): partial rows hold all n cycles, ||A||^2 = sum T^2 (scale = 1).
 // key2[t] = sum_c part[c][t] over the partial rows in a fixed order: 32 x 32 threads per CTA,
 // thread (x, y) sums rows y, y+32, ..., then row 0 of the tile adds the 32 column sums in order.
+// keys (optional): keys[t] = sqrt(key2[t]) in FP64, mirrored to keys[n - t] when mirror (the
+// reported keys; taking the roots here spreads them over the CTAs instead of the selection's one).
 __global__ void __launch_bounds__(1024) cd_keyreduce_kernel(const float* __restrict__ part, int nparts, int kh,
-                                                            double* __restrict__ key2) {
+                                                            double* __restrict__ key2, double* __restrict__ keys,
+                                                            int n, int mirror) {
   __shared__ double sm[32][33];
   const int t = blockIdx.x * 32 + threadIdx.x;
   double s = 0.0;
@@ -113,6 +116,11 @@ __global__ void __launch_bounds__(1024) cd_keyreduce_kernel(const float* __restr
     double v = 0.0;
     for (int y = 0; y < 32; ++y) v += sm[y][threadIdx.x];
     key2[t] = v;
+    if (keys) {
+      const double r = sqrt(v);
+      keys[t] = r;
+      if (mirror && t > 0 && t < n - t) keys[n - t] = r;
+    }
   }
 }
 
@@ -137,11 +145,8 @@ __global__ void __launch_bounds__(SEL_T) cd_select_kernel(const double* __restri
   }
   for (int t = threadIdx.x; t < n; t += SEL_T) in_s[t] = 0;
   __syncthreads();
-  double part = 0.0;
-  for (int t = threadIdx.x; t < n; t += SEL_T) {
-    part += key[t];
-    out.keys[t] = sqrt(key[t]);
-  }
+  double part = 0.0;  // (out.keys, the roots, were written by cd_keyreduce_kernel)
+  for (int t = threadIdx.x; t < n; t += SEL_T) part += key[t];
   const double total = block_sum(part, red);
   if (threadIdx.x == 0) out.norms[0] = total * scale;
   // chunk ownership for compactions: thread owns [c0, c1)
@@ -436,7 +441,7 @@ cudaError_t cd_spectrum(int n, const void* A, int64_t lda, bool bf16, const floa
 
 cudaError_t cd_keys(int kh, const float* kpart, int nparts, double* key2, cudaStream_t st) {
   AMM_TRACE("cd_keyreduce", st);
-  cd_keyreduce_kernel<<<(kh + 31) / 32, dim3(32, 32), 0, st>>>(kpart, nparts, kh, key2);
+  cd_keyreduce_kernel<<<(kh + 31) / 32, dim3(32, 32), 0, st>>>(kpart, nparts, kh, key2, nullptr, 0, 0);
   return cudaGetLastError();
 }
 
@@ -454,7 +459,7 @@ cudaError_t cd_select(int n, int k, const float* kpart, int nparts, const int32_
   const int kh = mirror ? n / 2 + 1 : n;
   {
     AMM_TRACE("cd_keyreduce", st);
-    cd_keyreduce_kernel<<<(kh + 31) / 32, dim3(32, 32), 0, st>>>(kpart, nparts, kh, o.key2);
+    cd_keyreduce_kernel<<<(kh + 31) / 32, dim3(32, 32), 0, st>>>(kpart, nparts, kh, o.key2, o.keys, n, mirror ? 1 : 0);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

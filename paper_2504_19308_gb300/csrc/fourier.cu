@@ -209,10 +209,13 @@ __global__ void __launch_bounds__(256) ft_t1_kernel(const float2* __restrict__ A
   float acc[T1_RB];
 #pragma unroll
   for (int rr = 0; rr < T1_RB; ++rr) acc[rr] = 0.f;
+  // entry u of all T1_RB rows together (each row's kept entries are in ascending q): rows that keep
+  // the same frequencies load the same B~ rows in one step (merged in L1); every accumulator still
+  // adds its row's entries in order
+#pragma unroll 2
+  for (int u = 0; u < k; ++u) {
 #pragma unroll
-  for (int rr = 0; rr < T1_RB; ++rr) {
-#pragma unroll 8
-    for (int u = 0; u < k; ++u) {
+    for (int rr = 0; rr < T1_RB; ++rr) {
       const int q = qs[rr * k + u];
       const float2 a = as[rr * k + u];
       const bool mir = q > n / 2;
@@ -263,10 +266,13 @@ __global__ void __launch_bounds__(256) ft_t2_kernel(const float2* __restrict__ A
   float acc0[T2_CB], acc1[T2_CB];
 #pragma unroll
   for (int cc = 0; cc < T2_CB; ++cc) acc0[cc] = acc1[cc] = 0.f;
+  // entry u of all T2_CB columns together: each column's kept entries are in ascending q, and
+  // columns with similar spectra keep mostly the same frequencies, so the loads of one step hit
+  // the same A~^T rows (merged in L1); every accumulator still adds its column's entries in order
+#pragma unroll 2
+  for (int u = 0; u < k; ++u) {
 #pragma unroll
-  for (int cc = 0; cc < T2_CB; ++cc) {
-#pragma unroll 4
-    for (int u = 0; u < k; ++u) {
+    for (int cc = 0; cc < T2_CB; ++cc) {
       const int q = qs[cc * k + u];
       const bool mir = q > n / 2;
       const float2* row = AtT + (int64_t)(mir ? n - q : q) * m + i;

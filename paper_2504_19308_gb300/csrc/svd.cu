@@ -132,6 +132,7 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
   if (e >= (int64_t)M * N) return;
   const int row = (int)(e / N), col = (int)(e % N);
   double s = 0.0;
+#pragma unroll 8
   for (int z = 0; z < splits; ++z) s += (double)ws[(int64_t)z * M * N + e];
   float* c = C + (int64_t)row * ldc + col;
   *c = (beta == 0.f) ? (float)(alpha * s) : (float)fma((double)alpha, s, (double)beta * *c);
@@ -197,13 +198,16 @@ static cudaError_t sgemm(bool ta, bool tb, int M, int N, int K, float alpha, con
 // The shapes a 128-row tensor-core tile (or the 128 x 128 SIMT tile above) mostly wastes:
 //   short contraction: C = alpha A op(B) + beta C with K <= SK_KMAX and a thin output (M or N at
 //     most 64), e.g. Y L^{-T} in CholeskyQR (m x k times k x k) or Q_A (Z_A Q_B) in the product;
-//   tiny output: M, N <= 64 with a long K, e.g. Z_A Q_B (k x k over n).
+//   split contraction: 64 x 64 output tiles with K cut into ranges of at most TK_KPER (shorter when
+//     there are too few tiles to fill the GPU twice over), e.g. a tiny
+//     output over a long K (Z_A Q_B, k x k over n) or CholeskyQR's m x k by k x k applies for
+//     64 < k <= 256.
 // A is M x K row-major; B is N x K (BT) or K x N.  FP32 arithmetic: every output of the short
-// form is one FMA chain over k in order; the tiny form cuts K into TK_C-wide chunks (one CTA
-// each, FMA chain per chunk) whose partials splitk_reduce_kernel sums in FP64 in chunk order.
+// form is one FMA chain over k in order; the split form keeps one FMA chain per K range (staged
+// 64 k at a time) and splitk_reduce_kernel sums the ranges' partials in FP64 in range order.
 // Both are deterministic.
 constexpr int SK_TM = 32, SK_TN = 64, SK_KMAX = 64;
-constexpr int TK_MAX = 64, TK_C = 64;
+constexpr int TK_T = 64, TK_C = 64, TK_KPER = 256;
 
 template <typename TIn>
 __device__ __forceinline__ float ld_elem(const TIn* p) {
@@ -254,33 +258,82 @@ __global__ void __launch_bounds__(256) gemm_shortk_kernel(int M, int N, int K, f
   }
 }
 
-// ws[chunk][i][j] = sum over the chunk's k of A(i, k) B(j, k), B stored N x K
-template <typename TIn>
-__global__ void __launch_bounds__(256) gemm_tiny_kernel(int M, int N, int K, const TIn* __restrict__ A, int64_t lda,
-                                                        const TIn* __restrict__ B, int64_t ldb, float* __restrict__ ws) {
-  __shared__ float As[TK_MAX][TK_C + 1];
-  __shared__ float Bs[TK_MAX][TK_C + 1];
-  const int k0 = blockIdx.x * TK_C;
-  const int kn = min(TK_C, K - k0);
-  for (int e = threadIdx.x; e < M * TK_C; e += 256) {
-    const int r = e / TK_C, kk = e % TK_C;
-    As[r][kk] = kk < kn ? ld_elem(A + (int64_t)r * lda + k0 + kk) : 0.f;
+// ws[z][i][j] = sum over the K range z of A(i, k) op(B)(k, j) for the 64 x 64 output tile
+// (blockIdx.y, blockIdx.x); thread: column j, rows rb, rb + 4, ..., rb + 60.
+template <bool BT, typename TIn>
+__global__ void __launch_bounds__(256) gemm_splitk_kernel(int M, int N, int K, int kper, const TIn* __restrict__ A,
+                                                          int64_t lda, const TIn* __restrict__ B, int64_t ldb,
+                                                          float* __restrict__ ws) {
+  __shared__ float As[TK_T][TK_C + 1];
+  __shared__ float Bs[TK_T][TK_C + 1];  // [j][k]
+  const int m0 = blockIdx.y * TK_T, n0 = blockIdx.x * TK_T;
+  const int kbeg = blockIdx.z * kper, kend = min(K, kbeg + kper);
+  const int j = threadIdx.x & (TK_T - 1), rb = threadIdx.x / TK_T;
+  constexpr int RPT = TK_T / (256 / TK_T);
+  float acc[RPT];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) acc[i] = 0.f;
+  for (int k0 = kbeg; k0 < kend; k0 += TK_C) {
+    const int kn = min(TK_C, kend - k0);
+    __syncthreads();  // the previous chunk's reads are done
+    for (int e = threadIdx.x; e < TK_T * TK_C; e += 256) {
+      const int r = e / TK_C, kk = e % TK_C;
+      As[r][kk] = (m0 + r < M && kk < kn) ? ld_elem(A + (int64_t)(m0 + r) * lda + k0 + kk) : 0.f;
+    }
+    for (int e = threadIdx.x; e < TK_T * TK_C; e += 256) {
+      if (BT) {
+        const int r = e / TK_C, kk = e % TK_C;
+        Bs[r][kk] = (n0 + r < N && kk < kn) ? ld_elem(B + (int64_t)(n0 + r) * ldb + k0 + kk) : 0.f;
+      } else {
+        const int kk = e / TK_T, r = e % TK_T;
+        Bs[r][kk] = (n0 + r < N && kk < kn) ? ld_elem(B + (int64_t)(k0 + kk) * ldb + n0 + r) : 0.f;
+      }
+    }
+    __syncthreads();
+    for (int kk = 0; kk < kn; ++kk) {
+      const float b = Bs[j][kk];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) acc[i] = fmaf(As[rb + 4 * i][kk], b, acc[i]);
+    }
   }
-  for (int e = threadIdx.x; e < N * TK_C; e += 256) {
-    const int r = e / TK_C, kk = e % TK_C;
-    Bs[r][kk] = kk < kn ? ld_elem(B + (int64_t)r * ldb + k0 + kk) : 0.f;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < M * N; e += 256) {
-    const int i = e / N, j = e % N;
-    float acc = 0.f;
-#pragma unroll 8
-    for (int kk = 0; kk < kn; ++kk) acc = fmaf(As[i][kk], Bs[j][kk], acc);
-    ws[(int64_t)blockIdx.x * M * N + e] = acc;
+  const int col = n0 + j;
+  if (col >= N) return;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const int row = m0 + rb + 4 * i;
+    if (row >= M) break;
+    ws[((int64_t)blockIdx.z * M + row) * N + col] = acc[i];
   }
 }
 
-// splitk_reduce_kernel is defined above; both forms return false when the shape is not theirs
+template <typename TIn>
+static cudaError_t gemm_splitk(bool bt, int M, int N, int K, float alpha, const TIn* A, int64_t lda, const TIn* B,
+                               int64_t ldb, float beta, float* C, int64_t ldc, cudaStream_t st) {
+  const int tiles = ((M + TK_T - 1) / TK_T) * ((N + TK_T - 1) / TK_T);
+  int kper = TK_KPER;  // a multiple of TK_C
+  while (kper > TK_C && (int64_t)tiles * ((K + kper - 1) / kper) < 2 * (int64_t)num_sms()) kper /= 2;
+  const int ranges = (K + kper - 1) / kper;
+  float* ws = nullptr;
+  cudaError_t e = dev_alloc((void**)&ws, sizeof(float) * (size_t)ranges * M * N, st);
+  if (e == cudaSuccess) {
+    AMM_TRACE_W("gemm_splitk", st, 2.0 * M * N * (double)K, (double)sizeof(TIn) * ((double)M + N) * K, nullptr);
+    const dim3 grid((unsigned)((N + TK_T - 1) / TK_T), (unsigned)((M + TK_T - 1) / TK_T), (unsigned)ranges);
+    if (bt) gemm_splitk_kernel<true, TIn><<<grid, 256, 0, st>>>(M, N, K, kper, A, lda, B, ldb, ws);
+    else gemm_splitk_kernel<false, TIn><<<grid, 256, 0, st>>>(M, N, K, kper, A, lda, B, ldb, ws);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    AMM_TRACE("splitk_reduce", st);
+    splitk_reduce_kernel<<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, st>>>(M, N, ranges, ws, alpha, beta, C,
+                                                                                     ldc);
+    e = cudaGetLastError();
+  }
+  if (ws) dev_free(ws, st);
+  return e;
+}
+
+// the short form for K <= SK_KMAX with a thin output, the split form for a tiny output (M, N <= 64)
+// over a longer K; false when the shape is neither
 template <typename TIn>
 static bool skinny_gemm(bool bt, int M, int N, int K, float alpha, const TIn* A, int64_t lda, const TIn* B,
                         int64_t ldb, float beta, float* C, int64_t ldc, cudaStream_t st, cudaError_t* err) {
@@ -294,23 +347,8 @@ static bool skinny_gemm(bool bt, int M, int N, int K, float alpha, const TIn* A,
     *err = cudaGetLastError();
     return true;
   }
-  if (bt && M <= TK_MAX && N <= TK_MAX && K > SK_KMAX) {
-    const int chunks = (K + TK_C - 1) / TK_C;
-    float* ws = nullptr;
-    cudaError_t e = dev_alloc((void**)&ws, sizeof(float) * (size_t)chunks * M * N, st);
-    if (e == cudaSuccess) {
-      AMM_TRACE_W("gemm_tiny", st, 2.0 * M * N * (double)K, (double)sizeof(TIn) * ((double)M + N) * K, nullptr);
-      gemm_tiny_kernel<TIn><<<chunks, 256, 0, st>>>(M, N, K, A, lda, B, ldb, ws);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-      AMM_TRACE("splitk_reduce", st);
-      splitk_reduce_kernel<<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, st>>>(M, N, chunks, ws, alpha, beta, C,
-                                                                                       ldc);
-      e = cudaGetLastError();
-    }
-    if (ws) dev_free(ws, st);
-    *err = e;
+  if (M <= TK_T && N <= TK_T) {
+    *err = gemm_splitk<TIn>(bt, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
     return true;
   }
   return false;
@@ -585,6 +623,49 @@ __global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const float* __
   }
 }
 
+// ============================================================================ Cholesky for k <= 32
+// One warp, the 32 x 32 tile in shared memory (rows padded to 33 floats), loops kept rolled: the
+// fully unrolled register form of chol_inv_kernel's diagonal tile is some thousands of instructions
+// that a single warp runs once, so for one tile its time went to instruction fetch (and the other
+// fifteen warps of that kernel to the barriers).  Same arithmetic as chol_inv_kernel on one tile:
+// right-looking factorisation of G + sI (s = shift_rel tr(G)), then column c of L^{-1} by forward
+// substitution in lane c.
+__global__ void __launch_bounds__(32) chol_inv32_kernel(int k, const float* __restrict__ G, float shift_rel,
+                                                        float* __restrict__ Linv_out) {
+  __shared__ float W[32][33];   // G + sI, then L (lower triangle)
+  __shared__ float Li[32][33];  // L^{-1} (lower triangle)
+  const int lane = threadIdx.x;
+  float tr = lane < k ? G[(int64_t)lane * k + lane] : 0.f;
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  const float shift = fmaxf(shift_rel * tr, 1e-30f);
+  for (int i = 0; i < 32; ++i)
+    W[i][lane] = (i < k && lane < k) ? G[(int64_t)i * k + lane] + (i == lane ? shift : 0.f) : (i == lane ? 1.f : 0.f);
+  __syncwarp();
+  for (int c = 0; c < 32; ++c) {  // lane r owns row r
+    const float d = sqrtf(fmaxf(W[c][c], shift));
+    const float rd = 1.f / d;
+    __syncwarp();
+    if (lane == c) W[c][c] = d;
+    else if (lane > c) W[lane][c] *= rd;
+    __syncwarp();
+    if (lane > c) {
+      const float lrc = W[lane][c];
+      for (int l = c + 1; l <= lane; ++l) W[lane][l] = fmaf(-lrc, W[l][c], W[lane][l]);
+    }
+    __syncwarp();
+  }
+  // lane c: column c of L^{-1}, rows r = c .. 31 (the entries above the diagonal are zero)
+  for (int r = 0; r < 32; ++r) {
+    float sum = 0.f;
+    for (int l = lane; l < r; ++l) sum = fmaf(W[r][l], Li[l][lane], sum);
+    const float di = 1.f / W[r][r];
+    Li[r][lane] = (r < lane) ? 0.f : (r == lane) ? di : -sum * di;
+  }
+  __syncwarp();
+  for (int i = 0; i < k; ++i)
+    if (lane < k) Linv_out[(int64_t)i * k + lane] = (lane <= i) ? Li[i][lane] : 0.f;
+}
+
 // ============================================================================ Cholesky for 160 < kp <= 256
 // The two work arrays of chol_inv_kernel do not fit in shared memory beyond kp = 160, and in
 // global memory one CTA waits on every access.  Here the factorisation keeps only the lower
@@ -856,6 +937,10 @@ static cudaError_t chol_inv(int k, const float* G, float shift_rel, float* W, fl
     return cudaGetLastError();
   }
   AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0 * 2.0, 0.0, nullptr);
+  if (kp == 32) {
+    chol_inv32_kernel<<<1, 32, 0, st>>>(k, G, shift_rel, Li);
+    return cudaGetLastError();
+  }
   const size_t sm = chol_kp(k) <= CHOL_SMEM_K ? sizeof(float) * chol_floats(k) : 0;
   chol_inv_kernel<<<1, CHOL_T, sm, st>>>(k, G, shift_rel, Li, W);
   return cudaGetLastError();
@@ -888,14 +973,14 @@ static cudaError_t orthonormalize(int64_t m, int k, const float* Y, float* Q, cu
     e = gram_dot2(m, k, src, G, st);
     if (e == cudaSuccess) e = chol_inv(k, G, pass == 0 ? shift1 : 1e-7f, W, Li, st);
     if (e == cudaSuccess)
-      if (!skinny_gemm<float>(true, (int)m, k, k, 1.f, src, k, Li, k, 0.f, dsts[pass], k, st, &e))
-        e = sgemm<float>(false, true, (int)m, k, k, 1.f, src, k, Li, k, 0.f, dsts[pass], k, st);  // src Linv^T
+      if (!skinny_gemm<float>(true, (int)m, k, k, 1.f, src, k, Li, k, 0.f, dsts[pass], k, st, &e))  // src Linv^T
+        e = gemm_splitk<float>(true, (int)m, k, k, 1.f, src, k, Li, k, 0.f, dsts[pass], k, st);
     src = dsts[pass];
   }
   if (e == cudaSuccess) e = gram_dot2(m, k, Q2, G, st, 1);  // G <- -(Q2^T Q2 - I) / 2
   if (e == cudaSuccess) e = cudaMemcpyAsync(Q, Q2, sizeof(float) * (size_t)m * k, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && !skinny_gemm<float>(false, (int)m, k, k, 1.f, Q2, k, G, k, 1.f, Q, k, st, &e))
-    e = sgemm<float>(false, false, (int)m, k, k, 1.f, Q2, k, G, k, 1.f, Q, k, st);
+    e = gemm_splitk<float>(false, (int)m, k, k, 1.f, Q2, k, G, k, 1.f, Q, k, st);
   for (float* p : {G, W, Li, Q1, Q2}) dev_free(p, st);
   return e;
 }
