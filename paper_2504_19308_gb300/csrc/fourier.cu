@@ -209,13 +209,10 @@ __global__ void __launch_bounds__(256) ft_t1_kernel(const float2* __restrict__ A
   float acc[T1_RB];
 #pragma unroll
   for (int rr = 0; rr < T1_RB; ++rr) acc[rr] = 0.f;
-  // entry u of all T1_RB rows together (each row's kept entries are in ascending q): rows that keep
-  // the same frequencies load the same B~ rows in one step (merged in L1); every accumulator still
-  // adds its row's entries in order
-#pragma unroll 2
-  for (int u = 0; u < k; ++u) {
 #pragma unroll
-    for (int rr = 0; rr < T1_RB; ++rr) {
+  for (int rr = 0; rr < T1_RB; ++rr) {
+#pragma unroll 8
+    for (int u = 0; u < k; ++u) {
       const int q = qs[rr * k + u];
       const float2 a = as[rr * k + u];
       const bool mir = q > n / 2;

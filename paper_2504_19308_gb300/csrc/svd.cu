@@ -623,49 +623,6 @@ __global__ void __launch_bounds__(CHOL_T) chol_inv_kernel(int k, const float* __
   }
 }
 
-// ============================================================================ Cholesky for k <= 32
-// One warp, the 32 x 32 tile in shared memory (rows padded to 33 floats), loops kept rolled: the
-// fully unrolled register form of chol_inv_kernel's diagonal tile is some thousands of instructions
-// that a single warp runs once, so for one tile its time went to instruction fetch (and the other
-// fifteen warps of that kernel to the barriers).  Same arithmetic as chol_inv_kernel on one tile:
-// right-looking factorisation of G + sI (s = shift_rel tr(G)), then column c of L^{-1} by forward
-// substitution in lane c.
-__global__ void __launch_bounds__(32) chol_inv32_kernel(int k, const float* __restrict__ G, float shift_rel,
-                                                        float* __restrict__ Linv_out) {
-  __shared__ float W[32][33];   // G + sI, then L (lower triangle)
-  __shared__ float Li[32][33];  // L^{-1} (lower triangle)
-  const int lane = threadIdx.x;
-  float tr = lane < k ? G[(int64_t)lane * k + lane] : 0.f;
-  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-  const float shift = fmaxf(shift_rel * tr, 1e-30f);
-  for (int i = 0; i < 32; ++i)
-    W[i][lane] = (i < k && lane < k) ? G[(int64_t)i * k + lane] + (i == lane ? shift : 0.f) : (i == lane ? 1.f : 0.f);
-  __syncwarp();
-  for (int c = 0; c < 32; ++c) {  // lane r owns row r
-    const float d = sqrtf(fmaxf(W[c][c], shift));
-    const float rd = 1.f / d;
-    __syncwarp();
-    if (lane == c) W[c][c] = d;
-    else if (lane > c) W[lane][c] *= rd;
-    __syncwarp();
-    if (lane > c) {
-      const float lrc = W[lane][c];
-      for (int l = c + 1; l <= lane; ++l) W[lane][l] = fmaf(-lrc, W[l][c], W[lane][l]);
-    }
-    __syncwarp();
-  }
-  // lane c: column c of L^{-1}, rows r = c .. 31 (the entries above the diagonal are zero)
-  for (int r = 0; r < 32; ++r) {
-    float sum = 0.f;
-    for (int l = lane; l < r; ++l) sum = fmaf(W[r][l], Li[l][lane], sum);
-    const float di = 1.f / W[r][r];
-    Li[r][lane] = (r < lane) ? 0.f : (r == lane) ? di : -sum * di;
-  }
-  __syncwarp();
-  for (int i = 0; i < k; ++i)
-    if (lane < k) Linv_out[(int64_t)i * k + lane] = (lane <= i) ? Li[i][lane] : 0.f;
-}
-
 // ============================================================================ Cholesky for 160 < kp <= 256
 // The two work arrays of chol_inv_kernel do not fit in shared memory beyond kp = 160, and in
 // global memory one CTA waits on every access.  Here the factorisation keeps only the lower
@@ -937,10 +894,6 @@ static cudaError_t chol_inv(int k, const float* G, float shift_rel, float* W, fl
     return cudaGetLastError();
   }
   AMM_TRACE_W("chol_inv", st, (double)k * k * k / 3.0 * 2.0 * 2.0, 0.0, nullptr);
-  if (kp == 32) {
-    chol_inv32_kernel<<<1, 32, 0, st>>>(k, G, shift_rel, Li);
-    return cudaGetLastError();
-  }
   const size_t sm = chol_kp(k) <= CHOL_SMEM_K ? sizeof(float) * chol_floats(k) : 0;
   chol_inv_kernel<<<1, CHOL_T, sm, st>>>(k, G, shift_rel, Li, W);
   return cudaGetLastError();

@@ -169,13 +169,14 @@ struct UmmaCfg {
   static constexpr int A_BYTES = UM_BM * 128;                // 16 KiB A tile
   static constexpr int B_BYTES = BN * 128;                   // BN rows of B (a multiple of 1024 bytes)
   // the thinnest tiles run two CTAs per SM (each CTA's prologue, pipeline fill and epilogue then
-  // overlap the other's streaming), with the ring depth cut to fit: BN = 16 in both modes, BN = 32
-  // in BF16
-  static constexpr int CTAS = (SHORT || BN == 16 || (!TF32 && BN == 32)) ? 2 : 1;
+  // overlap the other's streaming), with the ring depth cut to fit: BN = 16 and 32 in both modes
+  // (TF32X3 at BN = 32: three TMA stages and one split slot, 101.6 KB)
+  static constexpr int CTAS = (SHORT || BN == 16 || BN == 32) ? 2 : 1;
   static constexpr int RAW = SHORT ? 2
-                             : TF32 ? (BN == 128 ? 3 : BN == 16 ? 2 : 4) : (CTAS == 2 ? 5 : BN == 128 ? 5 : 7);  // TMA stages
+                             : TF32 ? (BN == 128 ? 3 : BN == 16 ? 2 : BN == 32 ? 3 : 4)
+                                    : (CTAS == 2 ? 5 : BN == 128 ? 5 : 7);  // TMA stages
   static constexpr int RAW_BYTES = A_BYTES + B_BYTES;        // A, B
-  static constexpr int SLOTS = TF32 ? (SHORT ? 1 : BN == 32 ? 3 : 2) : 0;  // split slots
+  static constexpr int SLOTS = TF32 ? (SHORT || BN == 32 ? 1 : 2) : 0;  // split slots
   static constexpr int SLOT_BYTES = 2 * RAW_BYTES;           // A hi, B hi, A lo, B lo
   // accumulator columns (TF32X3: main + correction), a power of two >= 32 as tcgen05.alloc requires
   static constexpr uint32_t TMEM_COLS = (TF32 ? 2 * BN : BN) < 32 ? 32u : (uint32_t)(TF32 ? 2 * BN : BN);
@@ -518,7 +519,7 @@ cudaError_t umma_gemm_tn(bool tf32, int M, int N, int K, float alpha, const void
   // about UM_CTA_FIXED_KB k-blocks) + the partial sums, with TF32X3 chains of at most
   // UM_TF32_MAX_KB k-blocks (the tensor core's FP32 accumulation loses up to an ulp per MMA; longer
   // K is split and the partials are summed with compensation)
-  const int nsm = umma_num_sms() * ((shortk || bn == 16 || (!tf32 && bn == 32)) ? 2 : 1);  // resident CTAs (UmmaCfg::CTAS)
+  const int nsm = umma_num_sms() * ((shortk || bn == 16 || bn == 32) ? 2 : 1);  // resident CTAs (UmmaCfg::CTAS)
   const int smin = tf32 ? std::max(1, (kblocks + UM_TF32_MAX_KB - 1) / UM_TF32_MAX_KB) : 1;
   const int smax = std::max(smin, std::min(32, kblocks / 2));
   int splits = smin;
