@@ -75,109 +75,7 @@ __global__ void __launch_bounds__(NT) ft_transform_kernel(const float* __restric
 // Keys are the float bit patterns of |z|^2 (non-negative, so unsigned order = numeric order) of
 // the virtual row q = 0..n-1 with key(q) = mag[min(q, n-q)].  Four 8-bit MSB radix passes find
 // the k-th largest key tau exactly; the selection is {key > tau} plus the lowest-index entries
-// with key == tau, written in ascending q.
-constexpr int SEL_NT = 256;
-
-// Exclusive scan of x over the SEL_NT threads of the CTA (warp shuffles, then the warp totals);
-// s_warp: SEL_NT / 32 ints of shared memory.  Every thread must call it; ends with a barrier.
-__device__ __forceinline__ int sel_block_scan(int x, int* s_warp) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int y = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, y, o);
-    if (lane >= o) y += t;
-  }
-  if (lane == 31) s_warp[warp] = y;
-  __syncthreads();
-  int before = 0;
-#pragma unroll
-  for (int w = 0; w < SEL_NT / 32; ++w) before += w < warp ? s_warp[w] : 0;
-  __syncthreads();  // s_warp may be reused by the next call
-  return before + y - x;
-}
-
-__global__ void __launch_bounds__(SEL_NT) ft_select_kernel(const float* __restrict__ mag, int n, int k,
-                                                           int32_t* __restrict__ sel, uint32_t* __restrict__ maskT,
-                                                           int mask_words) {
-  extern __shared__ uint32_t keys[];  // kh
-  __shared__ uint32_t hist[256];
-  __shared__ uint32_t s_prefix, s_need;
-  __shared__ int s_warp[SEL_NT / 32];
-  const int row = blockIdx.x;
-  const int kh = n / 2 + 1;
-  for (int q = threadIdx.x; q < kh; q += SEL_NT) keys[q] = __float_as_uint(mag[(int64_t)row * kh + q]);
-  if (threadIdx.x == 0) { s_prefix = 0; s_need = (uint32_t)k; }
-  __syncthreads();
-  uint32_t mask = 0;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int b = threadIdx.x; b < 256; b += SEL_NT) hist[b] = 0;
-    __syncthreads();
-    const uint32_t prefix = s_prefix;
-    // each stored key q in [0, n/2] stands for q and n - q: counted twice here, q = 0 and q = n/2
-    // (their own mirrors) corrected below.  Lanes that fall into the same bucket add together (one
-    // atomic per bucket and warp: the leading bytes of the magnitudes crowd into few buckets).
-    for (int q0 = 0; q0 < kh; q0 += SEL_NT) {
-      const int q = q0 + threadIdx.x;
-      const uint32_t key = q < kh ? keys[q] : 0u;
-      const bool part = q < kh && (key & mask) == prefix;
-      const unsigned pm = __ballot_sync(0xffffffffu, part);
-      if (part) {
-        const uint32_t bkt = (key >> shift) & 255u;
-        const unsigned peers = __match_any_sync(pm, bkt);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bkt], 2u * __popc(peers));
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if ((keys[0] & mask) == prefix) hist[(keys[0] >> shift) & 255u] -= 1u;
-      if ((n & 1) == 0 && (keys[n / 2] & mask) == prefix) hist[(keys[n / 2] >> shift) & 255u] -= 1u;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      unsigned above;
-      const int b = radix_bucket_warp(hist, s_need, &above);
-      if (threadIdx.x == 0) {
-        s_need -= above;
-        s_prefix = prefix | ((uint32_t)b << shift);
-      }
-    }
-    mask |= 255u << shift;
-    __syncthreads();
-  }
-  const uint32_t tau = s_prefix;
-  const uint32_t need_eq = s_need;  // how many entries equal to tau are taken (lowest q first)
-  // each thread owns a contiguous chunk of q
-  const int chunk = (n + SEL_NT - 1) / SEL_NT;
-  const int q0 = threadIdx.x * chunk, q1 = min(n, q0 + chunk);
-  int eq = 0;
-  for (int q = q0; q < q1; ++q) eq += keys[q <= n / 2 ? q : n - q] == tau;
-  // exclusive scan of eq counts
-  const int eq_before = sel_block_scan(eq, s_warp);
-  // count taken entries in the chunk
-  int taken = 0;
-  {
-    int e = eq_before;
-    for (int q = q0; q < q1; ++q) {
-      const uint32_t key = keys[q <= n / 2 ? q : n - q];
-      if (key > tau) ++taken;
-      else if (key == tau) { if ((uint32_t)e < need_eq) ++taken; ++e; }
-    }
-  }
-  int pos = sel_block_scan(taken, s_warp);
-  int e = eq_before;
-  for (int q = q0; q < q1; ++q) {
-    const uint32_t key = keys[q <= n / 2 ? q : n - q];
-    bool take = false;
-    if (key > tau) take = true;
-    else if (key == tau) { take = (uint32_t)e < need_eq; ++e; }
-    if (take) {
-      if (pos < k) sel[(int64_t)row * k + pos] = q;
-      ++pos;
-      if (maskT) atomicOr(maskT + (int64_t)q * mask_words + (row >> 5), 1u << (row & 31));
-    }
-  }
-}
+// with key == tau, written in ascending q.  One warp per row (ft_select_warp_kernel below).
 
 // ============================================================================ T1 = Re(A~_a B~)
 // CTA: RB rows x 256 columns; thread per column, RB accumulators.
@@ -379,6 +277,75 @@ cudaError_t ft_transform(int n, bool row, const float* X, int64_t ldx, int nvec,
   AMM_FT_DISPATCH(n, return FtOps<NN>::transform(row, X, ldx, nvec, tw, T, TT, mag, st));
 }
 
+// The selection with one warp per row (SELW_ROWS rows per CTA): the radix passes of a row
+// synchronise its warp only and the rows of a CTA proceed independently (a CTA per row waiting at
+// block barriers between the short steps measured 10% slower).  Keys in shared memory per warp,
+// the 256-bin histogram per warp; the entries are then taken in rounds of 32 consecutive q
+// (ballots give the order): tau, the lowest-q rule for ties, ascending q.
+constexpr int SELW_ROWS = 4;
+__global__ void __launch_bounds__(32 * SELW_ROWS) ft_select_warp_kernel(const float* __restrict__ mag, int n,
+                                                                       int k, int rows, int32_t* __restrict__ sel,
+                                                                       uint32_t* __restrict__ maskT,
+                                                                       int mask_words) {
+  extern __shared__ uint32_t selw_sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kh = n / 2 + 1;
+  const int kpad = (kh + 3) & ~3;
+  uint32_t* keys = selw_sm + warp * (kpad + 256);
+  uint32_t* hist = keys + kpad;
+  const int row = blockIdx.x * SELW_ROWS + warp;
+  if (row >= rows) return;  // whole warps: nothing below synchronises across warps
+  for (int q = lane; q < kh; q += 32) keys[q] = __float_as_uint(__ldg(mag + (int64_t)row * kh + q));
+  uint32_t prefix = 0, need = (uint32_t)k, mask = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int b = lane; b < 256; b += 32) hist[b] = 0;
+    __syncwarp();
+    // each stored key stands for q and n - q (counted twice), q = 0 and q = n/2 corrected below
+    for (int q0 = 0; q0 < kh; q0 += 32) {
+      const int q = q0 + lane;
+      const uint32_t key = q < kh ? keys[q] : 0u;
+      const bool part = q < kh && (key & mask) == prefix;
+      const unsigned pm = __ballot_sync(0xffffffffu, part);
+      if (part) {
+        const uint32_t bkt = (key >> shift) & 255u;
+        const unsigned peers = __match_any_sync(pm, bkt);
+        if (lane == __ffs(peers) - 1) atomicAdd(&hist[bkt], 2u * __popc(peers));
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      if ((keys[0] & mask) == prefix) hist[(keys[0] >> shift) & 255u] -= 1u;
+      if ((n & 1) == 0 && (keys[n / 2] & mask) == prefix) hist[(keys[n / 2] >> shift) & 255u] -= 1u;
+    }
+    __syncwarp();
+    unsigned above;
+    const int b = radix_bucket_warp(hist, need, &above);
+    need -= above;
+    prefix |= (uint32_t)b << shift;
+    mask |= 255u << shift;
+    __syncwarp();
+  }
+  const uint32_t tau = prefix;
+  const uint32_t need_eq = need;  // how many entries equal to tau are taken (lowest q first)
+  uint32_t eq_seen = 0, pos = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int q0 = 0; q0 < n && pos < (uint32_t)k; q0 += 32) {
+    const int q = q0 + lane;
+    const uint32_t key = q < n ? keys[q <= n / 2 ? q : n - q] : 0u;
+    const bool gt = q < n && key > tau, eq = q < n && key == tau;
+    const unsigned eqm = __ballot_sync(0xffffffffu, eq);
+    const bool take = gt || (eq && eq_seen + (uint32_t)__popc(eqm & lt) < need_eq);
+    const unsigned tm = __ballot_sync(0xffffffffu, take);
+    if (take) {
+      const uint32_t at = pos + (uint32_t)__popc(tm & lt);
+      if (at < (uint32_t)k) sel[(int64_t)row * k + at] = q;
+      if (maskT) atomicOr(maskT + (int64_t)q * mask_words + (row >> 5), 1u << (row & 31));
+    }
+    eq_seen += (uint32_t)__popc(eqm);
+    pos += (uint32_t)__popc(tm);
+  }
+}
+
 cudaError_t ft_select(int n, int k, int rows, const float* mag, int32_t* sel, uint32_t* maskT, int mask_words,
                       cudaStream_t st) {
   AMM_TRACE_W("ft_select", st, 0.0, (double)rows * (n / 2 + 1) * 4, nullptr);
@@ -386,7 +353,16 @@ cudaError_t ft_select(int n, int k, int rows, const float* mag, int32_t* sel, ui
     cudaError_t e = cudaMemsetAsync(maskT, 0, sizeof(uint32_t) * (size_t)n * mask_words, st);
     if (e != cudaSuccess) return e;
   }
-  ft_select_kernel<<<rows, SEL_NT, sizeof(uint32_t) * (n / 2 + 1), st>>>(mag, n, k, sel, maskT, mask_words);
+  const int kpad = (n / 2 + 1 + 3) & ~3;
+  const size_t smw = sizeof(uint32_t) * (size_t)SELW_ROWS * (kpad + 256);
+  static DeviceOnce once;
+  const cudaError_t attr = once([] {
+    return cudaFuncSetAttribute((const void*)ft_select_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(uint32_t) * SELW_ROWS * ((8192 / 2 + 1 + 3) / 4 * 4 + 256)));
+  });
+  if (attr != cudaSuccess) return attr;
+  ft_select_warp_kernel<<<(rows + SELW_ROWS - 1) / SELW_ROWS, 32 * SELW_ROWS, smw, st>>>(mag, n, k, rows, sel, maskT,
+                                                                                        mask_words);
   return cudaGetLastError();
 }
 
