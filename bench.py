@@ -637,6 +637,8 @@ KERNEL_OF = {
     "cd_spectrum": "cd_spectrum_kernel", "bw_row_spectrum": "bw_spectrum_kernel",
     "bw_col_spectrum": "bw_spectrum_kernel", "cd_residual": "cd_residual_kernel",
     "cd_residual_imag": "cd_residual_kernel", "cd_project": "cd_residual_kernel",
+    "cd_residual_direct": "cd_resid_direct_kernel", "cd_residual_imag_direct": "cd_resid_direct_kernel",
+    "cd_project_direct": "cd_resid_direct_kernel",
     "cd_apply_col": "cd_apply_kernel", "cd_apply_row": "cd_apply_kernel", "cd_apply_unpaired": "cd_apply_kernel",
     "cd_sddmm": "cd_sddmm_kernel", "cd_sddmm_tiled": "cd_sddmm_tiled_kernel", "cd_rho": "cd_rho_kernel",
     "cd_eigen": "cd_eigen_kernel", "cd_select": "cd_select_kernel", "cd_keyreduce": "cd_keyreduce_kernel",
@@ -650,6 +652,7 @@ KERNEL_OF = {
 # Family of a kernel for the per-family roofline entries.
 FAMILY_OF = {
     "cd_spectrum_kernel": "fft", "bw_spectrum_kernel": "fft", "cd_residual_kernel": "fft",
+    "cd_resid_direct_kernel": "fft",
     "ft_transform_kernel": "fft", "cd_apply_kernel": "spectral_apply", "cd_sddmm_kernel": "sddmm",
     "cd_sddmm_tiled_kernel": "sddmm", "umma_gemm_kernel<true>": "tcgen05_gemm",
     "umma_gemm_kernel<false>": "tcgen05_gemm", "ft_t1_kernel": "sparsifier_apply", "ft_t2_kernel": "sparsifier_apply",
@@ -662,8 +665,8 @@ FAMILY_OF = {
 # kernel changes (absent = not captured as it stands)
 NCU_TRAFFIC = {
     "umma_gemm_kernel<true>": 32.23e6, "cd_apply_kernel": 87.88e6, "cd_residual_kernel": 41.94e6,
-    "cd_sddmm_kernel": 76.41e6, "bw_spectrum_kernel": 58.31e6, "cd_spectrum_kernel": 93.69e6,
-    "ft_bw_spmm_kernel": 143.51e6, "ft_bw_sampled_kernel": 310.32e6,
+    "cd_resid_direct_kernel": 39.09e6, "cd_sddmm_kernel": 76.41e6, "bw_spectrum_kernel": 58.31e6,
+    "cd_spectrum_kernel": 93.69e6, "ft_bw_spmm_kernel": 143.51e6, "ft_bw_sampled_kernel": 310.32e6,
 }
 
 

@@ -216,6 +216,22 @@ cudaError_t amm::cd_spectrum_of(Handle* h, const float2** R, float2** temp, cuda
   return e;
 }
 
+// The inverse cycle transform of a circulant handle's listed components (mode as cd_residual; odd
+// modes the unpaired set with v, even modes S u S-bar with w): term by term when there are few of
+// them (2k <= 18), by FFTs over the whole spectrum otherwise.  Mode 0 reads the operand A itself
+// (A - sum w comp) on the direct path.
+static cudaError_t resid_of(Handle* h, const float2* R, int mode, const void* A, int64_t lda, bool bf16, float* X,
+                            int64_t ldx, int accumulate, const int32_t* dcount, const int32_t* dcount2,
+                            cudaStream_t st) {
+  auto& c = h->cd;
+  const int n = (int)h->rows;
+  const bool odd = (mode & 1) != 0;
+  if (cd_residual_direct_ok(h->k) && (mode != 0 || A != nullptr))
+    return cd_residual_direct(n, R, c.tw, odd ? c.so.dlist : c.so.ulist, odd ? c.so.dv : c.so.uw,
+                              c.so.counts + (odd ? 1 : 0), mode, A, lda, bf16, X, ldx, accumulate, dcount, dcount2, st);
+  return cd_residual(n, R, c.tw, odd ? c.so.vfull : c.so.wfull, mode, dcount, X, st, ldx, accumulate, dcount2);
+}
+
 amm_status_t amm::decompose_circulant(Handle* h, const amm_opts_t* o) {
   const int n = (int)h->rows;
   if (!cd_length_ok(n))
@@ -276,9 +292,10 @@ amm_status_t amm::decompose_circulant(Handle* h, const amm_opts_t* o) {
   if ((e = cd_eigen(n, c.R, c.tw, c.so.dlist, c.so.dv, c.so.counts + 1, c.cap, 1, c.Ld, h->stream)) != cudaSuccess)
     return cuda_fail(e, "cd_eigen launch");
   if (h->role == AMM_RIGHT) {
-    if ((e = cd_residual(n, c.R, c.tw, c.so.wfull, 0, nullptr, c.resid, h->stream)) != cudaSuccess)
+    if ((e = resid_of(h, c.R, 0, h->A, h->lda, bf16, c.resid, n, 0, nullptr, nullptr, h->stream)) != cudaSuccess)
       return cuda_fail(e, "cd_residual launch");
-    if ((e = cd_residual(n, c.R, c.tw, c.so.vfull, 1, c.so.counts + 1, c.imag, h->stream)) != cudaSuccess)
+    if ((e = resid_of(h, c.R, 1, nullptr, 0, false, c.imag, n, 0, c.so.counts + 1, nullptr, h->stream)) !=
+        cudaSuccess)
       return cuda_fail(e, "cd_residual launch");
   }
   if (o && o->store_spectra == 0) {  // the products and the backward do not read R again
@@ -554,12 +571,12 @@ amm_status_t amm::cd_backward(Handle* a, Handle* b, const float* G, int64_t ldg,
     STEP(bw_spectrum(n, false, cb.resid, n, tw, X2, st));
     STEP(cd_sddmm(n, X1, X2, ca.so.ulist, ca.so.counts, ca.cap, K, nullptr, nullptr, st));
     STEP(cd_rho(n, K, tw, ca.so.ulist, ca.so.counts, ca.cap, RX, nullptr, nullptr, st));
-    STEP(cd_residual(n, RX, tw, ca.so.wfull, 2, nullptr, dA, st, ldda, 1));
+    STEP(resid_of(a, RX, 2, nullptr, 0, false, dA, ldda, 1, nullptr, nullptr, st));
     // unpaired: (i v_t) R_t(G V_B^T) D^t, only when both selections split a pair (device gates)
     STEP(bw_spectrum(n, false, cb.imag, n, tw, X2, st, ca.so.counts + 1, cb.so.counts + 1));
     STEP(cd_sddmm(n, X1, X2, ca.so.dlist, ca.so.counts + 1, ca.cap, K, ca.so.counts + 1, cb.so.counts + 1, st));
     STEP(cd_rho(n, K, tw, ca.so.dlist, ca.so.counts + 1, ca.cap, RX, ca.so.counts + 1, cb.so.counts + 1, st));
-    STEP(cd_residual(n, RX, tw, ca.so.vfull, 3, ca.so.counts + 1, dA, st, ldda, 1, cb.so.counts + 1));
+    STEP(resid_of(a, RX, 3, nullptr, 0, false, dA, ldda, 1, ca.so.counts + 1, cb.so.counts + 1, st));
   }
   // the dense dA_w and Im A~ below come from A's half spectrum: the stored one, or (store_spectra = 0)
   // computed again from A
@@ -572,17 +589,17 @@ amm_status_t amm::cd_backward(Handle* a, Handle* b, const float* G, int64_t ldg,
     STEP(cd_apply(n, false, G, ldg, false, n, tw, ca.so.ulist, ca.Lw, ca.so.counts, nullptr, nullptr, dB, lddb, acc_b,
                   st, 1));
     STEP(bw_spectrum(n, true, G, ldg, tw, X1, st));
-    STEP(cd_residual(n, RA, tw, ca.so.wfull, 0, nullptr, T, st, n, 0));  // dA_w
+    STEP(resid_of(a, RA, 0, a->A, a->lda, a->dtype == AMM_BF16, T, n, 0, nullptr, nullptr, st));  // dA_w
     STEP(bw_spectrum(n, true, T, n, tw, X2, st));
     STEP(cd_sddmm(n, X2, X1, cb.so.ulist, cb.so.counts, cb.cap, K, nullptr, nullptr, st));
     STEP(cd_rho(n, K, tw, cb.so.ulist, cb.so.counts, cb.cap, RX, nullptr, nullptr, st));
-    STEP(cd_residual(n, RX, tw, cb.so.wfull, 2, nullptr, dB, st, lddb, 1));
+    STEP(resid_of(b, RX, 2, nullptr, 0, false, dB, lddb, 1, nullptr, nullptr, st));
     // unpaired: (i v_s) R_s(Y_A^T G) D^s with Y_A = Im A~
-    STEP(cd_residual(n, RA, tw, ca.so.vfull, 1, ca.so.counts + 1, T, st, n, 0, cb.so.counts + 1));
+    STEP(resid_of(a, RA, 1, nullptr, 0, false, T, n, 0, ca.so.counts + 1, cb.so.counts + 1, st));
     STEP(bw_spectrum(n, true, T, n, tw, X2, st, ca.so.counts + 1, cb.so.counts + 1));
     STEP(cd_sddmm(n, X2, X1, cb.so.dlist, cb.so.counts + 1, cb.cap, K, ca.so.counts + 1, cb.so.counts + 1, st));
     STEP(cd_rho(n, K, tw, cb.so.dlist, cb.so.counts + 1, cb.cap, RX, ca.so.counts + 1, cb.so.counts + 1, st));
-    STEP(cd_residual(n, RX, tw, cb.so.vfull, 3, cb.so.counts + 1, dB, st, lddb, 1, ca.so.counts + 1));
+    STEP(resid_of(b, RX, 3, nullptr, 0, false, dB, lddb, 1, cb.so.counts + 1, ca.so.counts + 1, st));
   }
 #undef STEP
   for (void* q : tmp) dev_free(q, st);

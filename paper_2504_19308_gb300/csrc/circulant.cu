@@ -489,6 +489,118 @@ cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g
   return cd_residual_any(n, R, g, mode, dcount, dcount2, X, ldx, accumulate, st);
 }
 
+// ============================================================================ direct inverse cycle transform
+// The dense sum of a few listed components, without FFTs:
+//   X(r, c) (+)= sum_{u < count} Re(g'_u r_{j, t_u} omega^{t_u c}),   j = (r - c) mod n,
+// with r_{j, t} = R[t][j] (row n - t conjugated for t > n/2) and omega = e^{+2 pi i/n} (the inverse
+// transform of Alg. 2's spectrum, term by term).  g'_u by mode as in cd_residual: 0 -> -w_u added
+// to the operand A itself (A - sum w comp = the residual of (1 - w)), 1 -> -i v_u, 2 -> w_u,
+// 3 -> +i v_u.  A CTA takes RD_ROWS rows x 256 columns: the cycles j = r - c it meets form one
+// window of 256 + RD_ROWS - 1 consecutive j per listed component, staged in shared memory (each
+// spectrum value then serves up to RD_ROWS outputs), and a thread takes one column, so each
+// omega^{t c} serves all of its rows.  Gates as cd_residual: odd modes write nothing when *dcount
+// is zero, every mode when *dcount2 is zero.
+constexpr int RD_ROWS = 32;
+constexpr int RD_MAX_U = 18;  // 2k at most: the direct form is taken for k <= 9
+constexpr int RD_WIN = 256 + RD_ROWS - 1;
+
+template <typename T>
+__global__ void __launch_bounds__(256) cd_resid_direct_kernel(int n, const float2* __restrict__ R,
+                                                              const float2* __restrict__ tw,
+                                                              const int32_t* __restrict__ list,
+                                                              const float* __restrict__ coef,
+                                                              const int32_t* __restrict__ count, int mode,
+                                                              const T* __restrict__ A, int64_t lda,
+                                                              float* __restrict__ X, int64_t ldx, int accumulate,
+                                                              const int32_t* __restrict__ dcount,
+                                                              const int32_t* __restrict__ dcount2) {
+  __shared__ float2 s_r[RD_MAX_U][RD_WIN];  // s_r[u][w] = r_{j0 + w, t_u} (conjugated for t_u > n/2)
+  __shared__ int s_t[RD_MAX_U];
+  __shared__ float s_g[RD_MAX_U];
+  if ((mode & 1) && dcount != nullptr && *dcount == 0) return;
+  if (dcount2 != nullptr && *dcount2 == 0) return;
+  const int cnt = min(*count, RD_MAX_U);
+  const int c0 = blockIdx.x * 256, r0 = blockIdx.y * RD_ROWS;
+  const int c = c0 + threadIdx.x;
+  // the column's base values first (A for the residual, X when accumulating), all loads in flight
+  // together and overlapping the staging below; the listed terms are then added to them
+  float acc[RD_ROWS];
+#pragma unroll
+  for (int i = 0; i < RD_ROWS; ++i) {
+    const int r = r0 + i;
+    float v = 0.f;
+    if (c < n && r < n) {
+      if (mode == 0) v = ld_as_float<T>(A + (int64_t)r * lda + c);
+      else if (accumulate) v = X[(int64_t)r * ldx + c];
+    }
+    acc[i] = v;
+  }
+  const int j0 = (((r0 - c0 - 255) % n) + n) % n;  // the smallest r - c of the tile, mod n
+  if (threadIdx.x < cnt) {
+    s_t[threadIdx.x] = __ldg(list + threadIdx.x);
+    s_g[threadIdx.x] = __ldg(coef + threadIdx.x);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < cnt * RD_WIN; e += 256) {
+    const int u = e / RD_WIN, w = e - u * RD_WIN;
+    const int t = s_t[u];
+    const bool mir = t > n / 2;
+    const int j = (j0 + w) % n;
+    float2 v = __ldg(R + (int64_t)(mir ? n - t : t) * n + j);
+    if (mir) v.y = -v.y;
+    s_r[u][w] = v;
+  }
+  __syncthreads();
+  if (c >= n) return;
+  const bool p2 = (n & (n - 1)) == 0;
+  for (int u = 0; u < cnt; ++u) {
+    const int t = s_t[u];
+    const float g = s_g[u];
+    // e^{-2 pi i t c/n} (omega^{t c} is its conjugate); t c < n^2 <= 2^28: 32-bit index arithmetic
+    const unsigned tc = (unsigned)t * (unsigned)c;
+    const float2 w = __ldg(tw + (p2 ? (tc & (unsigned)(n - 1)) : tc % (unsigned)n));
+    const float2* rw = s_r[u] + (255 - threadIdx.x);  // row r0 + i meets window entry 255 - tid + i
+    // z = v conj(w): Re z = v.x w.x + v.y w.y, Im z = v.y w.x - v.x w.y; even modes add g' Re z,
+    // odd modes Re(-+ i v z) = +- v Im z
+    if (mode & 1) {
+      const float gx = (mode == 1 ? g : -g) * w.x, gy = (mode == 1 ? g : -g) * w.y;
+#pragma unroll
+      for (int i = 0; i < RD_ROWS; ++i) acc[i] = fmaf(rw[i].y, gx, fmaf(-rw[i].x, gy, acc[i]));
+    } else {
+      const float gx = (mode == 0 ? -g : g) * w.x, gy = (mode == 0 ? -g : g) * w.y;
+#pragma unroll
+      for (int i = 0; i < RD_ROWS; ++i) acc[i] = fmaf(rw[i].x, gx, fmaf(rw[i].y, gy, acc[i]));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RD_ROWS; ++i) {
+    const int r = r0 + i;
+    if (r >= n) break;
+    X[(int64_t)r * ldx + c] = acc[i];
+  }
+}
+
+bool cd_residual_direct_ok(int64_t k) { return 2 * k <= RD_MAX_U; }
+
+cudaError_t cd_residual_direct(int n, const float2* R, const float2* tw, const int32_t* list, const float* coef,
+                               const int32_t* count, int mode, const void* A, int64_t lda, bool bf16, float* X,
+                               int64_t ldx, int accumulate, const int32_t* dcount, const int32_t* dcount2,
+                               cudaStream_t st) {
+  if (!R || !X || !tw || (mode == 0 && !A)) return cudaErrorInvalidValue;
+  if (ldx <= 0) ldx = n;
+  AMM_TRACE_W(mode == 0 ? "cd_residual_direct" : (mode == 1 ? "cd_residual_imag_direct" : "cd_project_direct"), st, 0.0,
+              (mode & 1) ? 0.0 : (double)n * n * 4 * (accumulate || mode == 0 ? 2 : 1), nullptr);
+  const dim3 grid((unsigned)((n + 255) / 256), (unsigned)((n + RD_ROWS - 1) / RD_ROWS));
+  if (bf16)
+    cd_resid_direct_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, R, tw, list, coef, count, mode,
+                                                               (const __nv_bfloat16*)A, lda, X, ldx, accumulate,
+                                                               dcount, dcount2);
+  else
+    cd_resid_direct_kernel<float><<<grid, 256, 0, st>>>(n, R, tw, list, coef, count, mode, (const float*)A, lda, X,
+                                                        ldx, accumulate, dcount, dcount2);
+  return cudaGetLastError();
+}
+
 cudaError_t cd_apply(int n, bool row, const void* X, int64_t ldx, bool bf16, int64_t nvec, const float2* tw,
                      const int32_t* list, const float2* Lc, const int32_t* count, const int32_t* gate0,
                      const int32_t* gate1, float* out, int64_t ldo, int accumulate, cudaStream_t st, int rev) {

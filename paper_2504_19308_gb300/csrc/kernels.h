@@ -57,6 +57,14 @@ cudaError_t cd_eigen(int n, const float2* R, const float2* tw, const int32_t* li
 // 2: g, 3: +i g); writes or adds X((c+j) mod n, c), leading dimension ldx (0 = n).  Rows of R
 // whose coefficient is zero are not read.  Odd modes skip when *dcount == 0; any mode skips
 // when dcount2 is given and *dcount2 == 0.
+// The inverse cycle transform of the listed components only (list / coef / *count: S u S-bar with w,
+// or the unpaired set with v), evaluated term by term without FFTs; mode 0 needs the operand A
+// (dtype bf16 or FP32).  Taken for few components (cd_residual_direct_ok(k): 2k small).
+bool cd_residual_direct_ok(int64_t k);
+cudaError_t cd_residual_direct(int n, const float2* R, const float2* tw, const int32_t* list, const float* coef,
+                               const int32_t* count, int mode, const void* A, int64_t lda, bool bf16, float* X,
+                               int64_t ldx, int accumulate, const int32_t* dcount, const int32_t* dcount2,
+                               cudaStream_t st);
 cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g, int mode, const int32_t* dcount,
                         float* X, cudaStream_t st, int64_t ldx = 0, int accumulate = 0,
                         const int32_t* dcount2 = nullptr);
