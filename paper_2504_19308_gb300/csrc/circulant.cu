@@ -500,7 +500,7 @@ cudaError_t cd_residual(int n, const float2* R, const float2* tw, const float* g
 // spectrum value then serves up to RD_ROWS outputs), and a thread takes one column, so each
 // omega^{t c} serves all of its rows.  Gates as cd_residual: odd modes write nothing when *dcount
 // is zero, every mode when *dcount2 is zero.
-constexpr int RD_ROWS = 32;
+constexpr int RD_ROWS = 16;
 constexpr int RD_MAX_U = 18;  // 2k at most: the direct form is taken for k <= 9
 constexpr int RD_WIN = 256 + RD_ROWS - 1;
 
