@@ -427,8 +427,6 @@ cudaError_t pq_status(PqPlan* p, int32_t* status, int32_t* item, int32_t* stage)
   return cudaSuccess;
 }
 
-double pq_work(const PqPlan* p) { return p ? p->work : 0.0; }
-int pq_grid(const PqPlan* p) { return p ? p->grid : 0; }
 
 void pq_destroy(PqPlan* p) {
   if (!p) return;

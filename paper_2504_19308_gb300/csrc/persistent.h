@@ -26,8 +26,6 @@ cudaError_t pq_build(const std::vector<PqDesc>& items, PqPlan** out);
 cudaError_t pq_launch(PqPlan* p, cudaStream_t st, uint64_t limit_ns);
 // The control block after the launch has completed (the caller synchronises first).
 cudaError_t pq_status(PqPlan* p, int32_t* status, int32_t* item, int32_t* stage);
-double pq_work(const PqPlan* p);
-int pq_grid(const PqPlan* p);
 void pq_destroy(PqPlan* p);
 
 }  // namespace amm
