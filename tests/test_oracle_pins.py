@@ -198,6 +198,23 @@ def test_alg3_fft_form_equals_explicit(n, k):
     assert np.abs(m - m3).max() < 1e-12 * np.abs(m).max()
 
 
+@pytest.mark.parametrize("n,k", [(16, 2), (16, 5), (15, 4), (32, 7)])
+def test_real_part_is_never_worse(n, k):
+    """Reading R5: a selection that splits a conjugate pair makes M complex; AB is real, so
+    ||AB - Re M||^2 = ||AB - M||^2 - ||Im M||^2 exactly, and the product returned (Re M) is never
+    further from AB than M.  Random data ranks the components apart, so the pair split is forced
+    through the selection argument."""
+    a, b = _rand(n, 40 + k), S.rng(41 + k, 1).uniform(0, 1, (n, n))
+    sel = np.array([0] + [1 + j for j in range(k - 1)], dtype=np.int64)  # 1..k-1 without partners
+    re_m, m, _, _ = O.cd_matmul(a, b, k, sel_a=sel, sel_b=sel, full=True)
+    exact = a @ b
+    im = np.linalg.norm(m.imag)
+    assert im > 1e-6 * np.linalg.norm(m)  # the split pairs leave an imaginary part
+    e_re, e_c = np.linalg.norm(exact - re_m), np.linalg.norm(exact - m)
+    assert e_re <= e_c
+    assert abs(e_re ** 2 - (e_c ** 2 - im ** 2)) <= 1e-10 * e_c ** 2
+
+
 def _truncs(method, a, b, k, seed=0):
     n = a.shape[1]
     if method == "svd":
