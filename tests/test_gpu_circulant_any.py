@@ -42,6 +42,17 @@ def test_circulant_any_length_product(n, k):
                                                abs=1e-6 * info["fro2"])
 
 
+def test_circulant_any_length_longest_chirp():
+    """n = 3000 > 2048: the chirp-z convolutions run at the longest power-of-two length, 8192."""
+    torch, amm = torch_cuda()
+    n, k = 3000, 3
+    g = S.rng(n, 29)
+    a = g.uniform(0, 1, (n, n))
+    b = S.toeplitz_uniform(n, g)
+    err, *_ = _product(torch, amm, a, b, k)
+    assert err <= TOL, err
+
+
 @pytest.mark.parametrize("n,k", [(300, 37), (1000, 125), (999, 64)])
 def test_circulant_any_length_dense_selection(n, k):
     """Many components (k up to n/8): the spectral MAC runs over a long coefficient list."""
