@@ -108,3 +108,39 @@ def test_circulant_n16384_k512():
     assert rel(C.double().cpu().numpy()[rows], a64[rows] @ b64) <= TOL
     assert rel(dA.double().cpu().numpy()[rows], g64[rows] @ b64.T) <= TOL
     assert rel(dB.double().cpu().numpy()[:, rows], a64.T @ g64[:, rows]) <= TOL
+
+
+
+@pytest.mark.parametrize("method", ["circulant", "svd", "fourier", "cycle"])
+def test_zero_operand_gives_zero_product_and_gradient(method):
+    """The degenerate operand A = 0 (every key of A ties at zero; the rSVD sketch Y = A phi is zero):
+    the product and dB are exactly zero and nothing is NaN.  For the selection methods the tied
+    selection of A follows the key order (index ascending) and dA matches the oracle's frozen
+    gradient; for the rSVD, orth(0) spans nothing, so A~ = 0 and dA = G B~^T."""
+    torch, amm = torch_cuda()
+    n, k = 64, 4
+    g = S.rng(44, 0)
+    b, gr = g.standard_normal((n, n)), g.standard_normal((n, n))
+    A = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    B, G = dev32(torch, b), dev32(torch, gr)
+    svd = method == "svd"
+    phi = dev32(torch, S.sketch(n, k, 44, 0).astype(np.float32)) if svd else None
+    psi = S.sketch(n, k, 44, 1).astype(np.float32) if svd else None
+    hA = amm.decompose(A, method, k, "left", sketch=phi)
+    hB = amm.decompose(B, method, k, "right", sketch=None if psi is None else dev32(torch, psi))
+    C = amm.approx_matmul(hA, hB)
+    dA, dB = amm.approx_matmul_backward(hA, hB, G)
+    for t in (C, dA, dB):
+        assert bool(torch.isfinite(t).all())
+    assert float(C.abs().max()) == 0.0 and float(dB.abs().max()) == 0.0
+    a64, b64, g64 = np.zeros((n, n)), as64(B), as64(G)
+    if svd:
+        tb = O.truncate_rsvd(b64, k, psi.astype(np.float64))
+        assert rel(dA.double().cpu().numpy(), g64 @ tb.approx.T) <= TOL
+        return
+    if method != "fourier":
+        assert sorted(hA.selection().tolist()) == list(range(k))
+    ta = O.truncate(method, a64, k, selection=hA.selection(), side="left")
+    tb = O.truncate(method, b64, k, selection=hB.selection(), side="right")
+    rda, _ = O.backward(method, ta, tb, g64)
+    assert rel(dA.double().cpu().numpy(), rda) <= TOL
