@@ -60,6 +60,11 @@ def test_argument_errors_without_gpu(lib):
     assert lib.amm_decompose(None, 64, 64, 64, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
     # k = 0
     assert lib.amm_decompose(fake, 64, 64, 64, 0, 1, 0, ctypes.byref(opts), None, ctypes.byref(out)) == 1
+    # empty operands, for every method
+    for method in range(4):
+        assert lib.amm_decompose(fake, 0, 64, 64, 0, method, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
+        assert lib.amm_decompose(fake, 64, 0, 64, 0, method, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
+        assert b"empty matrix" in lib.amm_last_error()
     # lda < cols
     assert lib.amm_decompose(fake, 64, 64, 32, 0, 1, 4, ctypes.byref(opts), None, ctypes.byref(out)) == 1
     # circulant needs a square of a supported length
