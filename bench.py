@@ -665,7 +665,7 @@ FAMILY_OF = {
 # kernel changes (absent = not captured as it stands)
 NCU_TRAFFIC = {
     "umma_gemm_kernel<true>": 32.23e6, "cd_apply_kernel": 87.88e6, "cd_residual_kernel": 41.94e6,
-    "cd_resid_direct_kernel": 39.09e6, "cd_sddmm_kernel": 76.41e6, "bw_spectrum_kernel": 58.31e6,
+    "cd_sddmm_kernel": 76.41e6, "bw_spectrum_kernel": 58.31e6,
     "cd_spectrum_kernel": 93.69e6, "ft_bw_spmm_kernel": 143.51e6, "ft_bw_sampled_kernel": 310.32e6,
 }
 
