@@ -45,7 +45,7 @@ typedef enum {
   AMM_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed */
   AMM_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up (batch scheduler) */
   AMM_ERR_STATE = 6,            /* handles do not fit together (role, shape, method) */
-  AMM_ERR_NOT_IMPLEMENTED = 7   /* valid request for a feature this build does not provide */
+  AMM_ERR_NOT_IMPLEMENTED = 7   /* valid request for a feature the library does not provide */
 } amm_status_t;
 
 /* The truncated decompositions of the paper. */
@@ -507,7 +507,7 @@ amm_status_t amm_autotune_export(char* host_buf, int64_t cap, int64_t* len);
  * cycle transform, flag 1 = accumulating form; kernels 2, 3: column and row backward spectra,
  * flags 0).  Every line is checked
  * first: a wrong header, an unknown kernel, flags on a kernel without them, a length that is not a
- * circulant length of this build, a variant other than 0 / 1 or trailing text returns
+ * circulant length the library supports, a variant other than 0 / 1 or trailing text returns
  * AMM_ERR_INVALID_ARG with nothing installed.  Host only.
  */
 amm_status_t amm_autotune_import(const char* host_text);
