@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_library_resolves_every_symbol_at_load(lib):
     """Eager binding (RTLD_NOW): a symbol the library references but no object defines fails here
-    on the CPU rather than at the first call on a GPU machine."""
+    on the CPU rather than at the first call on a machine with a GPU."""
     path = os.path.join(ROOT, "paper_2504_19308_gb300", "libamm.so")
     ctypes.CDLL(path, mode=os.RTLD_NOW | os.RTLD_LOCAL)
 
