@@ -149,10 +149,10 @@ amm_status_t amm_opts_init(amm_opts_t* opts);
  *   stream  cudaStream_t for all work and allocations of this handle.
  *   out     receives the handle; unchanged on error.
  *
- * Circulant: computes the cycle spectrum R (Alg. 2), keys T[t] = ||R_A[t]||_2 (Alg. 3
- * Step 2), the top-k selection ordered by (key desc, index asc) (Step 3), the eigen-
- * spectra L_t = F R_A[t] of the selected components (Step 4), and, for the RIGHT role,
- * the dense residual dB (Step 6, for the other operand).
+ * Circulant: computes the cycle spectrum R (Alg. 2) and then, following Alg. 3, the keys
+ * T[t] = ||R_A[t]||_2, the top-k selection ordered by (key desc, index asc), the eigen-
+ * spectra L_t = F R_A[t] of the selected components, and, for the RIGHT role, the dense
+ * residual dB (for the other operand's first-order term).
  * SVD: Y = A phi, Q = orth(Y), X = Q^T A (Alg. 1, without the small SVD, which does not
  * change A~ = Q Q^T A).
  */
@@ -210,7 +210,7 @@ amm_status_t amm_approx_matmul_backward(amm_handle_t hA, amm_handle_t hB, const 
                                         int64_t lddb, void* stream);
 
 /* Sizes, norms and selection statistics: ||A||_F^2 and the truncation error ||dA||_F^2 of
- * A = A~ + dA (Section 2, Eq. (2.1)), the gap at the top-k boundary (Alg. 3 Step 3).
+ * A = A~ + dA (Section 2, Eq. (2.1)), the gap at the top-k boundary (Alg. 3's selection).
  * Synchronises the handle's stream. */
 amm_status_t amm_handle_info(amm_handle_t h, amm_info_t* info);
 
@@ -322,7 +322,7 @@ amm_status_t amm_refine_product(amm_handle_t hA, amm_handle_t hB, amm_handle_t h
 
 /*
  * Copy the selection to host memory: circulant component indices / cycle indices in
- * selection order (k entries; Alg. 3 Step 3, Section 1.2.2); for AMM_SPARSE_FOURIER the kept frequencies of every row
+ * selection order (k entries; Alg. 3, Section 1.2.2); for AMM_SPARSE_FOURIER the kept frequencies of every row
  * (left operand, rows x k) or column (right operand, cols x k), ascending within each (Alg. 4).
  * `cap` is the capacity of host_idx in elements; *count receives the number written.
  * Synchronises the handle's stream.
@@ -331,8 +331,8 @@ amm_status_t amm_handle_get_selection(amm_handle_t h, int32_t* host_idx, int64_t
                                       int64_t* count);
 
 /*
- * Copy the component keys to host memory: for AMM_CIRCULANT T[t] = ||R_A[t]||_2, t = 0..n-1 (Alg. 3
- * Step 2; T[n-t] is the same double as T[t], computed once for t <= n/2), for AMM_SPARSE_CYCLE the
+ * Copy the component keys to host memory: for AMM_CIRCULANT T[t] = ||R_A[t]||_2, t = 0..n-1 (Alg. 3;
+ * T[n-t] is the same double as T[t], computed once for t <= n/2), for AMM_SPARSE_CYCLE the
  * cycle norms ||diag Lambda_j||_2 (Section 1.2.2), the values the top-k selection ranks.  `cap` is
  * the capacity of host_keys in doubles (>= n); *count receives n.  Square handles only (blocked
  * circulant handles: AMM_ERR_NOT_IMPLEMENTED; other methods: AMM_ERR_STATE).  Synchronises the

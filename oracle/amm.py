@@ -21,7 +21,7 @@ Readings taken where the paper is silent or inconsistent:
       (Alg. 1 as printed).  Only A~ = Q Q^T A enters M, so QR/SVD signs do not matter.
   R8  Fourier sparsifier: top-k per ROW of A W^* and per COLUMN of W B (Section 2.4 text),
       constant k; magnitudes of conjugate partners mirrored as in R6.
-  R9  Cycle sparsifier key: ||diag Lambda_j||_2 (by analogy with Alg. 3 Step 2).
+  R9  Cycle sparsifier key: ||diag Lambda_j||_2 (by analogy with Alg. 3's component keys).
   R10 Backward: selections, Q factors and masks are frozen; the gradient is that of the
       resulting bilinear map.
   R13 Rectangular circulant operands: b x b blocks, ragged edge zero-padded, top-k per block,
@@ -206,7 +206,7 @@ def reconstruct(R: np.ndarray, sel) -> np.ndarray:
 
 
 def component_keys(R: np.ndarray) -> np.ndarray:
-    """T[k] = ||R_A[k]||_2 (Alg. 3 Step 2), evaluated for k <= n/2 and mirrored (reading R6)."""
+    """T[k] = ||R_A[k]||_2 (the keys of Alg. 3), evaluated for k <= n/2 and mirrored (reading R6)."""
     n = R.shape[0]
     t = np.zeros(n)
     for k in range(n // 2 + 1):
@@ -217,12 +217,12 @@ def component_keys(R: np.ndarray) -> np.ndarray:
 
 
 def eigen_spectrum(R: np.ndarray, t: int) -> np.ndarray:
-    """L_t = sqrt(n) W R_A[t] = F R_A[t], the eigenvalues of R_t (Alg. 3 Step 4)."""
+    """L_t = sqrt(n) W R_A[t] = F R_A[t], the eigenvalues of R_t (Alg. 3)."""
     return fft_cols(R[t].reshape(-1, 1)).ravel()
 
 
 # ---------------------------------------------------------------------------
-# Selection (Alg. 3 Step 3, Alg. 4) -- reading R6
+# Selection (Alg. 3, Alg. 4) -- reading R6
 # ---------------------------------------------------------------------------
 
 
@@ -281,7 +281,7 @@ class Truncation:
 
 
 def truncate_circulant(a: np.ndarray, k: int, selection=None) -> Truncation:
-    """A~ = sum_{t in S} R_t D^t with S = top-k of T (Alg. 2 + Alg. 3 Steps 1-3)."""
+    """A~ = sum_{t in S} R_t D^t with S = top-k of T (Alg. 2, then Alg. 3's keys and selection)."""
     R = circulant_spectrum(a)
     keys = component_keys(R)
     sel = np.asarray(selection, dtype=np.int64) if selection is not None else top_k(keys, k)
@@ -332,22 +332,22 @@ def topk_mask_rows(mag: np.ndarray, k: int, forced=None) -> np.ndarray:
 
 
 def truncate_fourier_left(a: np.ndarray, k: int, forced=None) -> Truncation:
-    """A~ = A W^* kept on its top-k entries per row (Alg. 5 lines 1, 3; Alg. 4)."""
+    """A~ = A W^* kept on its top-k entries per row (Alg. 5's row transforms and selection; Alg. 4)."""
     n = a.shape[1]
     at = a @ np.conj(unitary_W(n)).T
     mask = topk_mask_rows(magnitudes_mirrored_rows(at), k, forced)
     at_a = np.where(mask, at, 0)
-    # space-domain form A_s = A~_a W, so that A_s B = A~_a (W B) (Alg. 5 line 5)
+    # space-domain form A_s = A~_a W, so that A_s B = A~_a (W B) (Alg. 5's first product)
     return Truncation("fourier", a, at_a @ unitary_W(n), None, T=at, mask=mask, T_a=at_a, side="left")
 
 
 def truncate_fourier_right(b: np.ndarray, k: int, forced=None) -> Truncation:
-    """B~ = W B kept on its top-k entries per column (Alg. 5 lines 2, 4; reading R8)."""
+    """B~ = W B kept on its top-k entries per column (Alg. 5's column transforms and selection; reading R8)."""
     n = b.shape[0]
     bt = unitary_W(n) @ b
     mask = topk_mask_rows(magnitudes_mirrored_rows(bt.T), k, forced).T
     bt_a = np.where(mask, bt, 0)
-    # space-domain form B_s = W^* B~_a, so that dA B_s = (A~ - A~_a) B~_a (Alg. 5 line 6)
+    # space-domain form B_s = W^* B~_a, so that dA B_s = (A~ - A~_a) B~_a (Alg. 5's second product)
     return Truncation("fourier", b, np.conj(unitary_W(n)).T @ bt_a, None, T=bt, mask=mask, T_a=bt_a, side="right")
 
 
@@ -407,8 +407,8 @@ def cd_matmul(a, b, ka, kb=None, sel_a=None, sel_b=None, full=False):
 def cd_matmul_alg3(a, b, ka, kb=None, sel_a=None, sel_b=None) -> np.ndarray:
     """Alg. 3 evaluated as printed (FFT form); returns the complex M.
 
-    Step 5: M = IFFT( sum_t diag(L_A[t]) C^{In_A[t]} FFT(B) ),
-    Step 6: M += ( IFFT( sum_t (C^{In_B[t]})^* diag(conj L_B[t]) FFT(dA^*) ) )^*.
+    zeroth-order term:  M = IFFT( sum_t diag(L_A[t]) C^{In_A[t]} FFT(B) ),
+    first-order term:   M += ( IFFT( sum_t (C^{In_B[t]})^* diag(conj L_B[t]) FFT(dA^*) ) )^*.
     (C^t Y)(p, :) = Y((p - t) mod n, :), i.e. np.roll(Y, t, axis=0).
     """
     n = a.shape[0]

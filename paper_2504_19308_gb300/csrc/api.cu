@@ -492,7 +492,7 @@ static amm_status_t check_pair(Handle* a, Handle* b) {
   return AMM_OK;
 }
 
-// Re M = A~_w dB_w  +  Y V  +  A B~_w for one square pair (Alg. 3 Steps 5-6 in the column /
+// Re M = A~_w dB_w  +  Y V  +  A B~_w for one square pair (Alg. 3's two terms in the column /
 // row spectral form); acc = 1 adds the product to C.
 cudaError_t amm::cd_first_order(Handle* a, Handle* b, float* C, int64_t ldc, int acc, cudaStream_t st) {
   const int n = (int)a->rows;

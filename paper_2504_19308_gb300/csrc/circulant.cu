@@ -15,7 +15,7 @@
 //   Re(A~_S B + dA_S B~_S) = A~_w dB_w + Y V + A B~_w,
 //   A~_w = sum_t w_t R_t D^t (= Re A~_S),  Y = Im A~_S = sum_t (-i v_t) R_t D^t,  V = Im B~_S.
 // The three terms are spectral applies (k complex MACs per output spectrum entry):
-//   column apply  (Alg. 3 Step 5): F(sum_t c_t R_t D^t X)(p,:) = sum_t c_t L_t(p) (F X)((p-t) mod n, :)
+//   column apply  (Alg. 3, zeroth-order term): F(sum_t c_t R_t D^t X)(p,:) = sum_t c_t L_t(p) (F X)((p-t) mod n, :)
 //   row apply     (X B~ by rows):  F_row(X sum_s c_s R_s D^s)(:,p) = sum_s c_s L_s((s-p) mod n) (F_row X)(:, (p-s) mod n)
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>

@@ -9,7 +9,7 @@
 // a circular convolution evaluated with power-of-two FFTs of length L >= 2n - 1 (L. I. Bluestein,
 // "A linear filtering approach to the computation of the discrete Fourier transform", 1970).  The
 // steps around the transforms -- the cycle gather of Alg. 7, the spectrum split and key partials,
-// the spectral MAC of Alg. 3 Steps 5-6, the inverse cycle transform, the backward SDDMM and the
+// the spectral MAC of Alg. 3's applies, the inverse cycle transform, the backward SDDMM and the
 // component spectra -- are separate small kernels that pass their operands through global
 // scratch, one pass per step, where the fixed-length paths fuse them into one kernel: this is the
 // general-length path, not the fast one.
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(256) any_scale_rows_kernel(const float2* __res
   L[(int64_t)u * n + p] = imag ? make_float2(c * y.y, -c * y.x) : cscale(y, c);
 }
 
-// Spectral MAC of the apply (Alg. 3 Steps 5-6): Y[s][p] = sum_u Lc[u][i_u(p)] Xh[s][(p - t_u) mod n]
+// Spectral MAC of the apply (Alg. 3): Y[s][p] = sum_u Lc[u][i_u(p)] Xh[s][(p - t_u) mod n]
 // with i_u(p) = (t_u - p) mod n (rev) or p.  CTA per packed signal s, its spectrum staged in
 // shared memory.
 __global__ void __launch_bounds__(256) any_mac_kernel(const float2* __restrict__ Xh, int n,

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(NT) cd_residual_kernel(const float2* __restric
 }
 
 // ============================================================================ K5: spectral apply
-// COL: out(:, c0..c0+2S) (+)= (sum_u Lc_u-weighted) applied to X's columns (Alg. 3 Step 5).
+// COL: out(:, c0..c0+2S) (+)= (sum_u Lc_u-weighted) applied to X's columns (Alg. 3, zeroth-order term).
 // ROW: out(r0..r0+2S, :) (+)= rows of X times (sum_s c_s R_s D^s).
 // Packed pairs of real columns/rows form complex signals; the output pair comes out of one
 // inverse FFT as (real, imag).  Coefficients Lc[u][p] = c_u L_{t_u}(p) (c conjugate-symmetric).

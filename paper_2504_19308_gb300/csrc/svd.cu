@@ -4,7 +4,7 @@
 //   Y = X phi                      FP32 GEMM
 //   Q = orth(Y)                    CholeskyQR2 in FP64 (k x k Gram, Cholesky, triangular apply)
 //   Z = Q^T X                      FP32 GEMM            ->  X~ = Q Z = Q Q^T X
-// The small SVD of Z (Alg. 1 steps 8-10) rotates Q and Z by the same k x k factors and does
+// The small SVD of Z that ends Alg. 1 rotates Q and Z by the same k x k factors and does
 // not change X~, so the product does not need it.
 //
 // Product (A m x n left, B n x p right), with A~ = Q_A Z_A and B~ = Q_B Z_B:

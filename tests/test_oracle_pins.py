@@ -95,7 +95,7 @@ def test_components_frobenius_orthogonal():
 
 @pytest.mark.parametrize("n", [8, 9, 64, 128])
 def test_parseval_keys(n):
-    """||R_k D^k||_F^2 = n T[k]^2 and sum_k n T[k]^2 = ||A||_F^2 (Remark, Alg. 3 Step 2)."""
+    """||R_k D^k||_F^2 = n T[k]^2 and sum_k n T[k]^2 = ||A||_F^2 (Remark, Alg. 3's keys)."""
     a = _rand(n, 3)
     keys = O.component_keys(O.circulant_spectrum(a))
     assert abs(n * np.sum(keys ** 2) - np.sum(a * a)) < 1e-10 * np.sum(a * a)
@@ -126,7 +126,7 @@ def test_thm25_least_squares():
 
 
 def test_eigen_spectrum_diagonalises_component():
-    """Alg. 3 Step 4: L_t = F R_A[t] are the eigenvalues of R_t: R_t = F^{-1} diag(L_t) F."""
+    """Alg. 3: L_t = F R_A[t] are the eigenvalues of R_t: R_t = F^{-1} diag(L_t) F."""
     n = 16
     R = O.circulant_spectrum(_rand(n, 6))
     f = O.dft_matrix(n)
