@@ -138,15 +138,16 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
   *c = (beta == 0.f) ? (float)(alpha * s) : (float)fma((double)alpha, s, (double)beta * *c);
 }
 
-static int g_num_sms = 0;
+// SM count of the current device, queried once per process (thread-safe static initialisation);
+// 152, GB300's count, only if the query fails
 static int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
-  }
-  return g_num_sms;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 152;
+  }();
+  return n;
 }
 
 // Host launcher: picks a deterministic split of K when the output has too few tiles.

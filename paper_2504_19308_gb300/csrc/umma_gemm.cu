@@ -475,14 +475,15 @@ __global__ void umma_splitk_reduce_kernel(int M, int N, int splits, const float*
   }
 }
 
+// SM count of the current device, queried once per process (thread-safe static initialisation);
+// 152, GB300's count, only if the query fails
 int umma_num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 152;
+  }();
   return n;
 }
 
