@@ -14,6 +14,7 @@ PEAKS = {"hbm_gbs": 7000.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1800
 
 def _summary(tmp_path, lines):
     cs = bench.ClockSampler(0)
+    os.unlink(cs.path)
     cs.path = str(tmp_path / "clocks.csv")
     cs.proc = object()  # a sampler that ran: summary() reads its file
     with open(cs.path, "w") as f:
@@ -43,7 +44,10 @@ def test_clock_summary_slowdowns_and_unreadable_fields(tmp_path):
 
 
 def test_clock_summary_without_nvidia_smi():
-    assert bench.ClockSampler(0).summary()["reasons"] == ["nvidia-smi unavailable"]
+    cs = bench.ClockSampler(0)
+    assert os.path.exists(cs.path)
+    assert cs.summary()["reasons"] == ["nvidia-smi unavailable"]
+    assert not os.path.exists(cs.path)
 
 
 @pytest.fixture
@@ -90,3 +94,13 @@ def test_roofline_dominant_kernel_and_families(fixed_peaks):
     assert set(fams) == {"spectral_apply", "fft", "tcgen05_gemm", "sparsifier_apply"}
     assert fams["fft"]["kernel"] == "cd_spectrum_kernel"  # the family's longest kernel
     assert fams["tcgen05_gemm"]["bound"] == "tensor"
+
+
+def test_clock_sampler_without_the_tool_reports_and_cleans_up(monkeypatch):
+    def no_tool(*a, **k):
+        raise FileNotFoundError("nvidia-smi")
+    monkeypatch.setattr(bench.subprocess, "Popen", no_tool)
+    with bench.ClockSampler(0) as clk:
+        pass
+    assert clk.f.closed
+    assert clk.summary()["reasons"] == ["nvidia-smi unavailable"] and not os.path.exists(clk.path)
