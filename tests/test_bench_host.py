@@ -104,3 +104,16 @@ def test_clock_sampler_without_the_tool_reports_and_cleans_up(monkeypatch):
         pass
     assert clk.f.closed
     assert clk.summary()["reasons"] == ["nvidia-smi unavailable"] and not os.path.exists(clk.path)
+
+
+def test_clock_rejection_rules():
+    ok = {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert bench.clock_rejection(ok) == []
+    assert bench.clock_rejection(dict(ok, reasons=["sw_power_cap"])) == []
+    assert bench.clock_rejection(dict(ok, sm_mhz=1500.0, reasons=["sw_power_cap"])) == []  # capped, kept
+    assert bench.clock_rejection(dict(ok, reasons=["sw_power_cap", "hw_slowdown"])) == ["hw_slowdown"]
+    assert bench.clock_rejection(dict(ok, reasons=["sw_thermal_slowdown"])) == ["sw_thermal_slowdown"]
+    stuck = bench.clock_rejection(dict(ok, sm_mhz=1200.0))
+    assert len(stuck) == 1 and "no reason" in stuck[0]
+    assert bench.clock_rejection({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}) == []
+    assert bench.clock_rejection(None) == []
