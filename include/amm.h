@@ -25,6 +25,10 @@
  *    truncation keeps one of two complex-conjugate components but not the other,
  *    M is complex; the library returns Re(M) (real inputs make A B real, so the
  *    real part is never a worse approximation).
+ *  - Devices: calls run on the calling thread's current CUDA device, and a handle
+ *    must be used on the device it was made on.  Kernel attributes are set once per
+ *    device; the SM count that sizes grids and K splits is read once per process
+ *    (from the first device used), as are the autotuner's choices.
  */
 #ifndef AMM_H
 #define AMM_H
